@@ -1,0 +1,197 @@
+/*
+ * hps.h -- C ABI of libhps.so, a GB300 (sm_103a) implementation of the
+ * multigrid-preconditioned Hierarchical Poincare-Steklov (HPS) skeleton solver
+ * for the variable-coefficient Helmholtz problem
+ *
+ *     -Lap u - kappa^2 (1 - b(x)) u = s  in (0,1)^2,   du/dn + i eta u = t  on the boundary
+ *
+ * ("Towards a Multigrid Preconditioner Interpretation of Hierarchical
+ * Poincare-Steklov Solvers", arXiv 2511.00735, section 2, eq. diffhelm).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Complex numbers are interleaved (re, im) doubles (C99 double complex /
+ *  numpy complex128).  Lower-precision internals (the mixed path) are hidden.
+ *
+ *  Elements: e = ix + nx*iy (x fastest).  Element nodes: tensor GLL grid of
+ *  order N, node(i,j) = i*(N+1) + j (x index slow), physical coordinates
+ *  x = ix*h + (xi_i + 1) h/2, h = 1/nx.  q = N-1 edge (non-corner) nodes per
+ *  side; sides ordered l, r, b, t; along a side by increasing coordinate.
+ *
+ *  Skeleton ("face") order, length n_skel = 2 * nfaces * q: vertical faces
+ *  v(ix,iy) (between (ix,iy) and (ix+1,iy)) numbered ix + (nx-1)*iy, then
+ *  horizontal faces h(ix,iy) (between (ix,iy) and (ix,iy+1)) numbered
+ *  (nx-1)*ny + ix + nx*iy.  Face f holds [incoming impedance of the
+ *  left/bottom element on its side r/t ; incoming impedance of the right/top
+ *  element on its side l/b], q values each: index (2f + slot) q + k.
+ *  Row k of M is the outgoing relation (section 3.2, eq. localiti) of the
+ *  element across the face from unknown k, so M = I + Pi T and
+ *      M g = RHS,  RHS_k = -( H^(e)_a + sum_{b on the boundary} T^(e)_{ab} t_b ).
+ *
+ *  Boundary-data order, length n_bdry = 4 nx q: domain sides left (ix = 0,
+ *  iy = 0..ny-1), right, bottom (iy = 0, ix = 0..nx-1), top; each element side
+ *  with its q edge nodes by increasing coordinate.
+ *
+ *  Batches of right-hand sides are RHS-major: [nrhs][n] complex128.
+ *
+ *  Pointers: "device" arguments must be device (or managed) memory of the
+ *  context's device; "host or device" arguments are classified with
+ *  cudaPointerGetAttributes.  The caller owns every buffer it passes; the
+ *  library owns the leaf maps, the merge tree and its workspaces until
+ *  hps_destroy, a new hps_mesh or hps_set_coeff.
+ *
+ *  Streams: every call enqueues on the context's stream (hps_create); calls
+ *  return after enqueueing except where stated (hps_gmres_solve reads scalars
+ *  back every outer iteration and returns when the solve is done).  One
+ *  context per stream; a context is not thread-safe.
+ *
+ *  Errors: every call returns HPS_OK (0) or a negative status below; nothing
+ *  aborts, traps or throws across the ABI.  hps_last_error(ctx) gives a
+ *  message for the last failure on that context.  There is no CPU fallback:
+ *  without a usable CUDA device hps_create returns HPS_ENODEV.
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hps_ctx hps_ctx;
+
+enum {
+  HPS_OK = 0,
+  HPS_EINVAL = -1,      /* bad argument (size, pointer, order, state)            */
+  HPS_ENOMEM = -2,      /* device allocation failed                              */
+  HPS_ENOTBUILT = -3,   /* a prerequisite call (mesh, coeff, leaves, merges) missing */
+  HPS_ENOTCONV = -4,    /* FGMRES stopped before the tolerance (info still filled) */
+  HPS_ETIMEOUT = -5,    /* a bounded device wait gave up                         */
+  HPS_ECUDA = -6,       /* a CUDA runtime call failed                            */
+  HPS_ENODEV = -7,      /* no usable CUDA device                                 */
+  HPS_EUNSUPPORTED = -8,/* valid input this build does not handle (stated in the message) */
+  HPS_ENUMERIC = -9     /* a factorisation broke down (non-positive pivot, zero pivot) */
+};
+
+enum { HPS_FP64 = 0, HPS_MIXED = 1 };
+
+/* Per-solve report of hps_gmres_solve. */
+typedef struct {
+  int outer_iterations;     /* FGMRES iterations (max over right-hand sides)         */
+  int converged;            /* number of right-hand sides with true residual <= tol  */
+  double max_rel_residual;  /* max over RHS of ||RHS - M g||_2 / ||RHS||_2 (explicit, FP64) */
+  int* iterations;          /* optional caller array [nrhs]: iterations per RHS (may be NULL) */
+  double* rel_residual;     /* optional caller array [nrhs]: explicit residual per RHS (may be NULL) */
+  double ms_rhs;            /* device time of the RHS assembly                        */
+  double ms_solve;          /* wall time of the FGMRES loop                           */
+} hps_info;
+
+/* Device-memory allocator used for every library-owned buffer.  alloc returns
+ * a device pointer of at least `bytes` bytes aligned to 256 bytes, or NULL;
+ * free releases it.  Default: cudaMalloc / cudaFree. */
+typedef void* (*hps_alloc_fn)(size_t bytes, void* user);
+typedef void (*hps_free_fn)(void* ptr, void* user);
+
+/* Create a context on `device`, enqueuing on `stream` (a cudaStream_t, NULL =
+ * the legacy default stream).  *ctx receives the handle.  HPS_ENODEV when the
+ * device cannot be used. */
+int hps_create(hps_ctx** ctx, int device, void* stream);
+
+/* Release every library-owned buffer and the context (safe on NULL). */
+int hps_destroy(hps_ctx* ctx);
+
+/* Replace the allocator (before hps_mesh; EINVAL afterwards). */
+int hps_set_allocator(hps_ctx* ctx, hps_alloc_fn alloc, hps_free_fn free_fn, void* user);
+
+/* Message of the last failure on ctx (static storage of the context). */
+const char* hps_last_error(hps_ctx* ctx);
+const char* hps_strerror(int status);
+
+/* Structured mesh of nx x ny square elements with tensor GLL grids of order N
+ * (section 3).  Requires nx == ny == 2^k (k >= 1) so that the nested-dissection
+ * levels alternate x, y, x, y (section 4.2, Fig. 1), and 2 <= N <= 16.
+ * Builds every index map on the host and uploads it.  Invalidates coefficient,
+ * leaves and tree. */
+int hps_mesh(hps_ctx* ctx, int nx, int ny, int N);
+
+/* Sizes after hps_mesh: skeleton unknowns, boundary-data length, number of
+ * merge levels L = log2(nx*ny), and the device bytes currently held. */
+int hps_sizes(hps_ctx* ctx, long long* n_skel, long long* n_bdry, int* levels,
+              long long* bytes_held);
+
+/* Host arrays [E][(N+1)^2]: physical coordinates of every element node
+ * (the points where the caller samples b). */
+int hps_node_coords(hps_ctx* ctx, double* x, double* y);
+
+/* Host arrays [n_bdry]: coordinates and outward normal of every physical
+ * boundary node, in boundary-data order (where the caller evaluates t). */
+int hps_boundary_points(hps_ctx* ctx, double* x, double* y, double* nx, double* ny);
+
+/* Host int32 arrays [E*4*q] indexed by element-side position
+ * p = (e*4 + side)*q + k: skel_in[p] = skeleton unknown incoming to e there,
+ * skel_out[p] = skeleton unknown incoming to the neighbour across it,
+ * bdry[p] = boundary-data index; -1 where not applicable.  Any may be NULL. */
+int hps_index_maps(hps_ctx* ctx, int* skel_in, int* skel_out, int* bdry);
+
+/* Coefficient c = kappa^2 (1 - b) (section 2).  b: [E][(N+1)^2] doubles at
+ * the points of hps_node_coords, host or device.  eta is the impedance
+ * parameter (the paper takes eta = kappa).  Invalidates leaves and tree. */
+int hps_set_coeff(hps_ctx* ctx, double kappa, double eta, const double* b);
+
+/* Build every leaf impedance-to-impedance map T = I_o L^{-1} I(:, iota_Gamma)
+ * (section 3.1, eq. ItIOperator), one batched launch over the elements, FP64
+ * result kept on the device in side order l, r, b, t.  `precision` selects the
+ * precision of the merge tree built later (HPS_FP64 or HPS_MIXED); the leaf
+ * maps themselves are FP64 in both (the outer matvec needs them).
+ * HPS_EUNSUPPORTED if an element's interior operator is not provably
+ * positive definite (kappa^2 (1-b) too large for the element size): this build
+ * eliminates the interior nodes by a real Cholesky factorisation. */
+int hps_build_leaves(hps_ctx* ctx, int precision);
+
+/* Host copy of leaf maps e0 .. e0+count-1: [count][4q][4q] complex128, row-major. */
+int hps_leaf_T(hps_ctx* ctx, int e0, int count, void* T_host);
+
+/* Nested-dissection merges l = 1..L_exact (section 4.1 eq. globalfacesystem,
+ * section 4.2): per level, batched pair merges T_pair = D - C A^{-1} B with
+ * the interface blocks A kept (inverted) for the preconditioner.  0 <= L_exact
+ * <= L.  exact_coarse != 0 also inverts the coarse system M_{L_exact+1}
+ * densely (direct HPS when combined with L_exact = L-1; section 4.2). */
+int hps_merge_levels(hps_ctx* ctx, int L_exact, int exact_coarse);
+
+/* Host copy of the ItI map of subdomain `sub` after `stage` merges (stage 0 =
+ * leaves), in the subdomain's natural boundary order l, r, b, t:
+ * [n][n] complex128, n = 2 (a+b) q for an a x b element block. */
+int hps_stage_T(hps_ctx* ctx, int stage, int sub, void* T_host);
+
+/* RHS of M g = RHS from boundary data (section 3.2; sources s = 0):
+ * t [nrhs][n_bdry] -> rhs [nrhs][n_skel], both device, complex128. */
+int hps_rhs(hps_ctx* ctx, const void* t, void* rhs, int nrhs);
+
+/* y = M x for x, y [nrhs][n_skel] device complex128 (FP64, leaf maps). */
+int hps_skel_matvec(hps_ctx* ctx, const void* x, void* y, int nrhs);
+
+/* z = MG(M) r (section 4.3): the V-cycle over the merged levels 1..L_exact
+ * (smoother A^{-1}, restriction, prolongation), the coarse system solved by
+ * inner_iters unpreconditioned GMRES steps from zero (or exactly when the tree
+ * was built with exact_coarse).  r, z [nrhs][n_skel] device complex128. */
+int hps_precond_apply(hps_ctx* ctx, const void* r, void* z, int nrhs, int inner_iters);
+
+/* Solve M g = RHS(t) for nrhs right-hand sides by flexible GMRES (restart
+ * `restart`, zero initial guess, at most max_outer restart cycles) with MG(M)
+ * as the preconditioner (inner_iters coarse GMRES steps), until
+ * ||RHS - M g||_2 <= tol ||RHS||_2 per right-hand side (section 4.3, 5).
+ * inner_iters < 0 runs unpreconditioned FGMRES.  t [nrhs][n_bdry] and
+ * g_out [nrhs][n_skel] are complex128, host or device.  s must be NULL (this
+ * build takes sources s = 0; HPS_EUNSUPPORTED otherwise).  info may be NULL.
+ * HPS_ENOTCONV when a right-hand side did not reach tol (g_out and info are
+ * filled). */
+int hps_gmres_solve(hps_ctx* ctx, const void* t, const void* s, int nrhs, double tol,
+                    int inner_iters, int restart, int max_outer, void* g_out,
+                    hps_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPS_H */

@@ -1,0 +1,509 @@
+// C ABI of libhps: context, mesh and index maps, coefficient, leaf build,
+// RHS / matvec / preconditioner entry points and the FP64 flexible GMRES.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "skel.cuh"
+
+namespace hps {
+
+
+int fail(hps_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(hps_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(c, HPS_ENOMEM, m);
+  return fail(c, HPS_ECUDA, m);
+}
+
+void* dev_alloc(hps_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, c->alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    c->allocs.push_back({p, bytes});
+    c->bytes_held += bytes;
+  }
+  return p;
+}
+
+void dev_free(hps_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i) {
+    if (c->allocs[i].p == p) {
+      c->bytes_held -= c->allocs[i].bytes;
+      c->allocs.erase(c->allocs.begin() + i);
+      break;
+    }
+  }
+  if (c->free_fn) c->free_fn(p, c->alloc_user);
+  else cudaFree(p);
+}
+
+template <typename T>
+T* dev_upload(hps_ctx* c, const std::vector<T>& v) {
+  T* p = static_cast<T*>(dev_alloc(c, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  if (!p) return nullptr;
+  if (!v.empty() && cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+  return p;
+}
+template int* dev_upload<int>(hps_ctx*, const std::vector<int>&);
+template double* dev_upload<double>(hps_ctx*, const std::vector<double>&);
+template GemmDesc* dev_upload<GemmDesc>(hps_ctx*, const std::vector<GemmDesc>&);
+
+#define FREE(ptr)            \
+  do {                       \
+    dev_free(c, (void*)ptr); \
+    ptr = nullptr;           \
+  } while (0)
+
+void free_solver(hps_ctx* c) {
+  FREE(c->fg_V); FREE(c->fg_Z); FREE(c->fg_x); FREE(c->fg_w); FREE(c->fg_rhs); FREE(c->fg_t);
+  FREE(c->fg_h); FREE(c->fg_part); FREE(c->fg_y); FREE(c->fg_floor);
+  FREE(c->pv_in); FREE(c->pv_out);
+  if (c->pin_h) cudaFreeHost(c->pin_h);
+  if (c->pin_y) cudaFreeHost(c->pin_y);
+  if (c->pin_floor) cudaFreeHost(c->pin_floor);
+  c->pin_h = nullptr; c->pin_y = nullptr; c->pin_floor = nullptr;
+  c->fg_restart = c->fg_nrhs = c->pv_nrhs = 0;
+}
+
+void free_tree(hps_ctx* c) {
+  for (auto& s : c->stages) {
+    FREE(s.d_es); FREE(s.T); FREE(s.vec);
+  }
+  for (auto& l : c->levels) {
+    FREE(l.d_dst); FREE(l.d_up); FREE(l.W); FREE(l.d_mdesc); FREE(l.d_sdesc);
+  }
+  c->stages.clear();
+  c->levels.clear();
+  FREE(c->coarse.d_mask); FREE(c->coarse.d_cnb); FREE(c->coarse.d_upos); FREE(c->coarse.d_ucnb);
+  FREE(c->coarse.Winv); FREE(c->coarse.d_desc);
+  c->coarse = Coarse();
+  FREE(c->ws_X1); FREE(c->ws_X2); FREE(c->d_piv); FREE(c->d_lu);
+  FREE(c->sw_tmp); FREE(c->sw_tmp2); FREE(c->sw_zt);
+  FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);
+  FREE(c->cg_nrm); FREE(c->cg_y); FREE(c->cg_g); FREE(c->cg_s); FREE(c->cg_part);
+  FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c);
+  FREE(c->ex_r); FREE(c->ex_e);
+  c->ws_X_elems = 0;
+  c->nrhs_cap = 0;
+  c->cg_k = c->cg_nrhs = c->ex_nrhs = 0;
+  c->have_tree = false;
+}
+
+// ---------------------------------------------------------------------------
+// Reference GLL rule on [-1, 1] (nodes -1, +1 and the roots of P_N', weights
+// 2 / (N (N+1) P_N(x)^2), differentiation matrix from the Lagrange basis),
+// written here independently of any other implementation in the repository.
+// ---------------------------------------------------------------------------
+static void legendre_pair(int N, double x, double& pN, double& pNm1) {
+  double a = 1.0, b = x;
+  if (N == 0) { pN = 1.0; pNm1 = 0.0; return; }
+  for (int k = 1; k < N; ++k) {
+    const double nxt = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+    a = b;
+    b = nxt;
+  }
+  pN = b;
+  pNm1 = a;
+}
+
+static void gll_build(int N, std::vector<double>& x, std::vector<double>& w, std::vector<double>& D) {
+  x.assign(N + 1, 0.0);
+  w.assign(N + 1, 0.0);
+  D.assign((N + 1) * (N + 1), 0.0);
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int j = 1; j < N; ++j) {
+    double t = -std::cos(M_PI * j / N);
+    for (int it = 0; it < 100; ++it) {
+      double p, pm;
+      legendre_pair(N, t, p, pm);
+      const double dp = N * (pm - t * p) / (1.0 - t * t);
+      const double d2 = (2.0 * t * dp - N * (N + 1.0) * p) / (1.0 - t * t);
+      const double dx = dp / d2;
+      t -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    x[j] = t;
+  }
+  std::vector<double> P(N + 1);
+  for (int j = 0; j <= N; ++j) {
+    double pm;
+    legendre_pair(N, x[j], P[j], pm);
+    w[j] = 2.0 / (N * (N + 1.0) * P[j] * P[j]);
+  }
+  for (int i = 0; i <= N; ++i)
+    for (int j = 0; j <= N; ++j)
+      if (i != j) D[i * (N + 1) + j] = P[i] / (P[j] * (x[i] - x[j]));
+  D[0] = -N * (N + 1.0) / 4.0;
+  D[N * (N + 1) + N] = N * (N + 1.0) / 4.0;
+}
+
+// Smallest eigenvalue of the symmetric matrix A (n x n, row-major) by cyclic Jacobi rotations.
+static double min_eig_sym(std::vector<double> A, int n) {
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = cs * akp - sn * akq;
+          A[k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = cs * apk - sn * aqk;
+          A[q * n + k] = sn * apk + cs * aqk;
+        }
+      }
+  }
+  double m = A[0];
+  for (int i = 1; i < n; ++i) m = std::min(m, A[i * n + i]);
+  return m;
+}
+
+static inline int opp_side(int s) { return s ^ 1; }
+
+}  // namespace hps
+
+using namespace hps;
+
+#define CHECK_CTX(c)                                  \
+  do {                                                \
+    if (!(c)) return HPS_EINVAL;                      \
+    cudaError_t e0_ = cudaSetDevice((c)->device);     \
+    if (e0_ != cudaSuccess) return cuda_fail(c, e0_, "cudaSetDevice"); \
+  } while (0)
+
+extern "C" {
+
+const char* hps_strerror(int s) {
+  switch (s) {
+    case HPS_OK: return "ok";
+    case HPS_EINVAL: return "invalid argument";
+    case HPS_ENOMEM: return "device allocation failed";
+    case HPS_ENOTBUILT: return "prerequisite call missing";
+    case HPS_ENOTCONV: return "FGMRES did not reach the tolerance";
+    case HPS_ETIMEOUT: return "bounded device wait gave up";
+    case HPS_ECUDA: return "CUDA runtime error";
+    case HPS_ENODEV: return "no usable CUDA device";
+    case HPS_EUNSUPPORTED: return "input not supported by this build";
+    case HPS_ENUMERIC: return "factorisation broke down";
+    default: return "unknown status";
+  }
+}
+
+const char* hps_last_error(hps_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int hps_create(hps_ctx** out, int device, void* stream) {
+  if (!out) return HPS_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return HPS_ENODEV;
+  }
+  if (device < 0 || device >= n) return HPS_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ENODEV;
+  }
+  hps_ctx* c = new hps_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess) {
+    delete c;
+    return HPS_ENOMEM;
+  }
+  cudaMemset(c->d_flag, 0, sizeof(int));
+  *out = c;
+  return HPS_OK;
+}
+
+int hps_destroy(hps_ctx* c) {
+  if (!c) return HPS_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_tree(c);
+  free_solver(c);
+  while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
+  cudaFree(c->d_flag);
+  delete c;
+  return HPS_OK;
+}
+
+int hps_set_allocator(hps_ctx* c, hps_alloc_fn a, hps_free_fn f, void* user) {
+  if (!c) return HPS_EINVAL;
+  if (c->have_mesh || !c->allocs.empty()) return fail(c, HPS_EINVAL, "allocator must be set before hps_mesh");
+  if ((a == nullptr) != (f == nullptr)) return fail(c, HPS_EINVAL, "alloc and free must both be set or both NULL");
+  c->alloc = a;
+  c->free_fn = f;
+  c->alloc_user = user;
+  return HPS_OK;
+}
+
+int hps_mesh(hps_ctx* c, int nx, int ny, int N) {
+  CHECK_CTX(c);
+  if (nx != ny || nx < 2 || (nx & (nx - 1)) != 0)
+    return fail(c, HPS_EINVAL, "nx == ny == 2^k with k >= 1 required");
+  if (N < 2 || N > 16) return fail(c, HPS_EINVAL, "2 <= N <= 16 required");
+  cudaStreamSynchronize(c->stream);
+  free_tree(c);
+  free_solver(c);
+  while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
+  c->d_es_nb = c->d_es_in = c->d_es_out = c->d_es_bdry = c->d_bdry_rows = nullptr;
+  c->d_Dref = c->d_Kref = c->d_wref = nullptr;
+  c->d_c = nullptr;
+  c->d_T = nullptr;
+  c->have_mesh = c->have_coeff = c->have_leaves = c->have_tree = false;
+
+  c->nx = nx; c->ny = ny; c->N = N; c->q = N - 1; c->E = nx * ny; c->nb = 4 * c->q;
+  int k = 0;
+  while ((1 << k) < nx) ++k;
+  c->L = 2 * k;
+  c->h = 1.0 / nx;
+  const int q = c->q, E = c->E;
+  const long long nfaces = (long long)(nx - 1) * ny + (long long)nx * (ny - 1);
+  c->n_skel = 2 * nfaces * q;
+  c->n_bdry = 2LL * (nx + ny) * q;
+  c->n_es = (long long)E * c->nb;
+
+  gll_build(N, c->xi, c->wref, c->Dref);
+  const int n1 = N + 1;
+  c->Kref.assign(n1 * n1, 0.0);
+  for (int i = 0; i < n1; ++i)
+    for (int j = 0; j < n1; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < n1; ++l) s += c->Dref[l * n1 + i] * c->wref[l] * c->Dref[l * n1 + j];
+      c->Kref[i * n1 + j] = s;
+    }
+  // mu_min of K_ii w.r.t. W_ii: eigenvalues of W^{-1/2} K W^{-1/2} on the interior nodes
+  std::vector<double> S(q * q);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j)
+      S[i * q + j] = c->Kref[(i + 1) * n1 + (j + 1)] / std::sqrt(c->wref[i + 1] * c->wref[j + 1]);
+  c->mu_min = min_eig_sym(S, q);
+
+  // element-side maps
+  c->es_nb.assign(c->n_es, -1);
+  c->es_in.assign(c->n_es, -1);
+  c->es_out.assign(c->n_es, -1);
+  c->es_bdry.assign(c->n_es, -1);
+  auto face_v = [&](int ix, int iy) { return (long long)ix + (long long)(nx - 1) * iy; };
+  auto face_h = [&](int ix, int iy) { return (long long)(nx - 1) * ny + ix + (long long)nx * iy; };
+  for (int e = 0; e < E; ++e) {
+    const int ix = e % nx, iy = e / nx;
+    for (int s = 0; s < 4; ++s) {
+      int nbe = -1;
+      long long f = -1;
+      int slot = 0, bpos = -1;
+      if (s == 0) {
+        if (ix > 0) { nbe = e - 1; f = face_v(ix - 1, iy); slot = 1; } else bpos = iy;
+      } else if (s == 1) {
+        if (ix < nx - 1) { nbe = e + 1; f = face_v(ix, iy); slot = 0; } else bpos = ny + iy;
+      } else if (s == 2) {
+        if (iy > 0) { nbe = e - nx; f = face_h(ix, iy - 1); slot = 1; } else bpos = 2 * ny + ix;
+      } else {
+        if (iy < ny - 1) { nbe = e + nx; f = face_h(ix, iy); slot = 0; } else bpos = 2 * ny + nx + ix;
+      }
+      for (int kk = 0; kk < q; ++kk) {
+        const long long p = ((long long)e * 4 + s) * q + kk;
+        if (nbe >= 0) {
+          c->es_nb[p] = (int)(((long long)nbe * 4 + opp_side(s)) * q + kk);
+          c->es_in[p] = (int)((2 * f + slot) * q + kk);
+        } else {
+          c->es_bdry[p] = bpos * q + kk;
+        }
+      }
+    }
+  }
+  for (long long p = 0; p < c->n_es; ++p)
+    if (c->es_nb[p] >= 0) c->es_out[p] = c->es_in[c->es_nb[p]];
+
+  std::vector<int> brow(c->n_bdry);
+  for (long long i = 0; i < c->n_bdry; ++i) brow[i] = (int)i;
+  c->d_es_nb = dev_upload(c, c->es_nb);
+  c->d_es_in = dev_upload(c, c->es_in);
+  c->d_es_out = dev_upload(c, c->es_out);
+  c->d_es_bdry = dev_upload(c, c->es_bdry);
+  c->d_bdry_rows = dev_upload(c, brow);
+  c->d_Dref = dev_upload(c, c->Dref);
+  c->d_Kref = dev_upload(c, c->Kref);
+  c->d_wref = dev_upload(c, c->wref);
+  if (!c->d_es_nb || !c->d_es_in || !c->d_es_out || !c->d_es_bdry || !c->d_bdry_rows || !c->d_Dref || !c->d_Kref ||
+      !c->d_wref)
+    return fail(c, HPS_ENOMEM, "index maps");
+  c->have_mesh = true;
+  return HPS_OK;
+}
+
+int hps_sizes(hps_ctx* c, long long* n_skel, long long* n_bdry, int* levels, long long* bytes_held) {
+  if (!c) return HPS_EINVAL;
+  if (!c->have_mesh) return fail(c, HPS_ENOTBUILT, "hps_mesh first");
+  if (n_skel) *n_skel = c->n_skel;
+  if (n_bdry) *n_bdry = c->n_bdry;
+  if (levels) *levels = c->L;
+  if (bytes_held) *bytes_held = (long long)c->bytes_held;
+  return HPS_OK;
+}
+
+int hps_node_coords(hps_ctx* c, double* x, double* y) {
+  if (!c || !x || !y) return HPS_EINVAL;
+  if (!c->have_mesh) return fail(c, HPS_ENOTBUILT, "hps_mesh first");
+  const int n1 = c->N + 1;
+  for (int e = 0; e < c->E; ++e) {
+    const int ix = e % c->nx, iy = e / c->nx;
+    for (int i = 0; i < n1; ++i)
+      for (int j = 0; j < n1; ++j) {
+        const long long o = (long long)e * n1 * n1 + i * n1 + j;
+        x[o] = ix * c->h + (c->xi[i] + 1.0) * c->h / 2.0;
+        y[o] = iy * c->h + (c->xi[j] + 1.0) * c->h / 2.0;
+      }
+  }
+  return HPS_OK;
+}
+
+int hps_boundary_points(hps_ctx* c, double* x, double* y, double* nxo, double* nyo) {
+  if (!c || !x || !y || !nxo || !nyo) return HPS_EINVAL;
+  if (!c->have_mesh) return fail(c, HPS_ENOTBUILT, "hps_mesh first");
+  const int q = c->q;
+  for (int e = 0; e < c->E; ++e) {
+    const int ix = e % c->nx, iy = e / c->nx;
+    for (int s = 0; s < 4; ++s)
+      for (int k = 0; k < q; ++k) {
+        const long long p = ((long long)e * 4 + s) * q + k;
+        const int b = c->es_bdry[p];
+        if (b < 0) continue;
+        const double t = (c->xi[k + 1] + 1.0) * c->h / 2.0;
+        double X, Y, NX, NY;
+        if (s == 0) { X = ix * c->h; Y = iy * c->h + t; NX = -1; NY = 0; }
+        else if (s == 1) { X = (ix + 1) * c->h; Y = iy * c->h + t; NX = 1; NY = 0; }
+        else if (s == 2) { X = ix * c->h + t; Y = iy * c->h; NX = 0; NY = -1; }
+        else { X = ix * c->h + t; Y = (iy + 1) * c->h; NX = 0; NY = 1; }
+        x[b] = X; y[b] = Y; nxo[b] = NX; nyo[b] = NY;
+      }
+  }
+  return HPS_OK;
+}
+
+int hps_index_maps(hps_ctx* c, int* skel_in, int* skel_out, int* bdry) {
+  if (!c) return HPS_EINVAL;
+  if (!c->have_mesh) return fail(c, HPS_ENOTBUILT, "hps_mesh first");
+  if (skel_in) std::memcpy(skel_in, c->es_in.data(), sizeof(int) * c->n_es);
+  if (skel_out) std::memcpy(skel_out, c->es_out.data(), sizeof(int) * c->n_es);
+  if (bdry) std::memcpy(bdry, c->es_bdry.data(), sizeof(int) * c->n_es);
+  return HPS_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int hps_set_coeff(hps_ctx* c, double kappa, double eta, const double* b) {
+  CHECK_CTX(c);
+  if (!c->have_mesh) return fail(c, HPS_ENOTBUILT, "hps_mesh first");
+  if (!b || !std::isfinite(kappa) || !std::isfinite(eta) || eta == 0.0)
+    return fail(c, HPS_EINVAL, "b non-null, finite kappa, finite non-zero eta required");
+  const long long nn = (long long)c->E * (c->N + 1) * (c->N + 1);
+  std::vector<double> bh(nn);
+  if (is_device_ptr(b)) {
+    HPS_CK(c, cudaMemcpy(bh.data(), b, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(bh.data(), b, sizeof(double) * nn);
+  }
+  c->c_host.resize(nn);
+  for (long long i = 0; i < nn; ++i) {
+    if (!std::isfinite(bh[i])) return fail(c, HPS_EINVAL, "non-finite coefficient sample");
+    c->c_host[i] = kappa * kappa * (1.0 - bh[i]);
+  }
+  cudaStreamSynchronize(c->stream);
+  free_tree(c);
+  if (c->d_c) FREE(c->d_c);
+  if (c->d_T) FREE(c->d_T);
+  c->have_leaves = false;
+  c->d_c = dev_upload(c, c->c_host);
+  if (!c->d_c) return fail(c, HPS_ENOMEM, "coefficient");
+  c->kappa = kappa;
+  c->eta = eta;
+  c->have_coeff = true;
+  return HPS_OK;
+}
+
+int hps_build_leaves(hps_ctx* c, int precision) {
+  CHECK_CTX(c);
+  if (!c->have_coeff) return fail(c, HPS_ENOTBUILT, "hps_set_coeff first");
+  if (precision != HPS_FP64 && precision != HPS_MIXED) return fail(c, HPS_EINVAL, "precision");
+  // positive-definiteness of the interior operator (leaf.cu): max c (h/2)^2 < 2 mu_min
+  const double cmax = *std::max_element(c->c_host.begin(), c->c_host.end());
+  const double bound = 2.0 * c->mu_min / (0.25 * c->h * c->h);
+  if (cmax >= 0.98 * bound)
+    return fail(c, HPS_EUNSUPPORTED,
+                "kappa^2 (1 - b) = " + std::to_string(cmax) + " reaches the interior Dirichlet bound " +
+                    std::to_string(bound) + " of these elements; this build eliminates the interior by Cholesky");
+  cudaStreamSynchronize(c->stream);
+  free_tree(c);
+  if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
+  if (!c->d_T) return fail(c, HPS_ENOMEM, "leaf maps");
+  const int grid = std::min(c->E, std::max(1, c->num_sms));
+  double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
+  if (!Ascr) return fail(c, HPS_ENOMEM, "leaf scratch");
+  LeafParams p;
+  p.N = c->N; p.q = c->q; p.ni = c->q * c->q; p.nb = c->nb; p.E = c->E; p.cw = 8;
+  p.h = c->h; p.eta = c->eta;
+  p.c = c->d_c; p.Dh = c->d_Dref; p.Kh = c->d_Kref; p.wh = c->d_wref;
+  p.Ascr = Ascr; p.T = c->d_T; p.flag = c->d_flag;
+  HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  HPS_CK(c, launch_leaf(p, grid, c->stream));
+  int flag = 0;
+  HPS_CK(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HPS_CK(c, cudaStreamSynchronize(c->stream));
+  dev_free(c, Ascr);
+  if (flag) return fail(c, HPS_ENUMERIC, "non-positive Cholesky pivot in element " + std::to_string(flag - 1));
+  c->precision = precision;
+  c->have_leaves = true;
+  return HPS_OK;
+}
+
+int hps_leaf_T(hps_ctx* c, int e0, int count, void* T_host) {
+  CHECK_CTX(c);
+  if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
+  if (!T_host || e0 < 0 || count < 0 || e0 + count > c->E) return fail(c, HPS_EINVAL, "element range");
+  HPS_CK(c, cudaStreamSynchronize(c->stream));
+  HPS_CK(c, cudaMemcpy(T_host, c->d_T + (size_t)e0 * c->nb * c->nb, sizeof(double2) * (size_t)count * c->nb * c->nb,
+                       cudaMemcpyDeviceToHost));
+  return HPS_OK;
+}
+
+}  // extern "C"

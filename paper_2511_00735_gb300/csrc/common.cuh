@@ -1,0 +1,106 @@
+// Shared device helpers: interleaved complex arithmetic in double / float,
+// the batched-GEMM descriptor and launch declarations of every kernel family.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hps {
+
+template <typename R> struct cplx;
+template <> struct cplx<double> { using T = double2; };
+template <> struct cplx<float> { using T = float2; };
+template <typename R> using c_t = typename cplx<R>::T;
+
+template <typename R>
+__host__ __device__ __forceinline__ c_t<R> mk(R a, R b) {
+  c_t<R> z;
+  z.x = a;
+  z.y = b;
+  return z;
+}
+template <typename R>
+__host__ __device__ __forceinline__ c_t<R> czero() { return mk<R>(R(0), R(0)); }
+
+template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) {
+  T z; z.x = a.x + b.x; z.y = a.y + b.y; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) {
+  T z; z.x = a.x - b.x; z.y = a.y - b.y; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+  T z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+// acc += a * b
+template <typename T> __host__ __device__ __forceinline__ void cfma(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ void cfma_conj(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+template <typename T> __host__ __device__ __forceinline__ T cscale(T a, decltype(a.x) s) {
+  T z; z.x = a.x * s; z.y = a.y * s; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ decltype(T().x) cabs1(T a) {
+  return fabs(a.x) + fabs(a.y);
+}
+// 1 / a, scaled to avoid overflow in |a|^2
+template <typename T> __host__ __device__ __forceinline__ T cinv(T a) {
+  auto s = fabs(a.x) > fabs(a.y) ? fabs(a.x) : fabs(a.y);
+  T z;
+  if (s == 0) { z.x = 0; z.y = 0; return z; }
+  auto ar = a.x / s, ai = a.y / s;
+  auto d = (ar * ar + ai * ai) * s;
+  z.x = ar / d;
+  z.y = -ai / d;
+  return z;
+}
+template <typename D, typename S>
+__host__ __device__ __forceinline__ c_t<D> cvt(c_t<S> a) {
+  return mk<D>(D(a.x), D(a.y));
+}
+
+// One batched-GEMM problem: C(m x n) = beta * C0 + alpha * A(m x k) * B(k x n).
+// Operand X starts at element (x_r * ldx + x_c) of its base pointer; all
+// matrices are row-major complex.  rmap / cmap >= 0 give offsets into the
+// launch's map array: row i of C is written to row c_r + map[rmap + i], column
+// j to c_c + map[cmap + j].  n < 0 means "the launch's n" (number of RHS).
+struct GemmDesc {
+  int a_r, a_c, b_r, b_c, c0_r, c0_c, c_r, c_c;
+  int m, n, k;
+  int rmap, cmap;
+};
+
+template <typename R> struct GemmArgs {
+  const c_t<R>* A;
+  const c_t<R>* B;
+  const c_t<R>* C0;  // may be null: no beta term
+  c_t<R>* C;
+  long long lda, ldb, ldc0, ldc;
+  c_t<R> alpha, beta;
+  const GemmDesc* desc;  // device array [nbatch]
+  int nbatch;
+  const int* maps;       // device
+  int n_launch;          // value of n for descriptors with n < 0
+};
+
+template <typename R>
+cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s);
+
+// Gauss-Jordan inversion of nmat augmented matrices W = [S | I] (m x 2m, row-major,
+// matrix b at W + b*m*2m).  Partial pivoting; on exit W(:, m:2m) = S^{-1}.
+// flag: device int, set to 1 if a zero pivot was met.
+// piv_ws: device ints [nmat * GJ_NB]; lu_ws: device [nmat * GJ_NB * GJ_NB] elements.
+constexpr int GJ_NB = 16;
+template <typename R>
+cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag,
+                      cudaStream_t s);
+
+}  // namespace hps

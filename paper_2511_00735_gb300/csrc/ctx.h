@@ -1,0 +1,152 @@
+// Library context: mesh geometry, index maps, the leaf maps, the merge tree
+// and solver workspaces.  Host-side only (compiled by nvcc as C++).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hps.h"
+#include "common.cuh"
+
+namespace hps {
+
+// Merge-level GEMM roles (see merge.cu for the formulas).
+enum MergeRole { MS = 0, MR, MX1A, MX1B, MX2A, MX2B, MOA, MOB, MOC, MOD, N_MROLE };
+enum SweepRole { UP1 = 0, UP2, UP3, UP4, UP5, DN1, DN2, DN3, DN4, DN5, N_SROLE };
+
+struct Stage {
+  int a = 0, b = 0;          // element block size of each subdomain
+  int gx = 0, gy = 0;        // subdomain grid
+  int nsub = 0, n = 0;       // subdomains, boundary length 2 (a + b) q
+  std::vector<int> es;       // [nsub * n] storage position -> element-side index
+  int* d_es = nullptr;       // device copy (stage 0 and coarse stage)
+  void* T = nullptr;         // [nsub][n][n] ItI maps, tree precision
+  void* vec = nullptr;       // [nsub * n][nrhs_cap] sweep vector, tree precision
+};
+
+struct Level {               // merge l: stage l-1 -> stage l
+  int dir = 0;               // 0: x-merge, 1: y-merge
+  int npairs = 0, m = 0, n = 0, p = 0;
+  std::vector<int> i1, i2;   // children of pair P (stage l-1 subdomain indices)
+  int* d_dst = nullptr;      // [npairs][2p] storage position in the merged subdomain of [E1; E2]
+  int* d_up = nullptr;       // [npairs * 2p] merged row -> child row (down-sweep copy)
+  void* W = nullptr;         // [npairs][m][2m]: [S | I] -> [. | S^{-1}]
+  GemmDesc* d_mdesc = nullptr;  // [N_MROLE][npairs]
+  GemmDesc* d_sdesc = nullptr;  // [N_SROLE][npairs]
+};
+
+struct Coarse {
+  int n_int = 0;             // interior (unknown) positions over all coarse subdomains
+  int* d_mask = nullptr;     // [nsub] interior-side bits
+  int off[5] = {0, 0, 0, 0, 0};
+  int* d_cnb = nullptr;      // [nsub*n] stage row across the face (-1 on the physical boundary)
+  int* d_upos = nullptr;     // [n_int] stage row of unknown u
+  int* d_ucnb = nullptr;     // [n_int] stage row across from unknown u
+  void* Winv = nullptr;      // exact coarse: [n_int][2 n_int] -> right half = M_c^{-1}
+  GemmDesc* d_desc = nullptr;  // exact coarse: the one GEMM descriptor
+  bool exact = false;
+};
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace hps
+
+struct hps_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  hps_alloc_fn alloc = nullptr;
+  hps_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::string err;
+  int num_sms = 0;
+  std::vector<hps::Alloc> allocs;
+  size_t bytes_held = 0;
+
+  // mesh
+  bool have_mesh = false;
+  int nx = 0, ny = 0, N = 0, q = 0, E = 0, nb = 0, L = 0;
+  long long n_skel = 0, n_bdry = 0, n_es = 0;
+  double h = 0;
+  std::vector<double> xi, wref, Dref, Kref;    // reference GLL rule, D, K = D^T W D
+  std::vector<int> es_nb, es_in, es_out, es_bdry;
+  int *d_es_nb = nullptr, *d_es_in = nullptr, *d_es_out = nullptr, *d_es_bdry = nullptr;
+  int* d_bdry_rows = nullptr;  // [n_bdry] identity helper for boundary transposes
+  double *d_Dref = nullptr, *d_Kref = nullptr, *d_wref = nullptr;
+  double mu_min = 0;           // smallest eigenvalue of K_ii w.r.t. W_ii (reference element)
+
+  // coefficient
+  bool have_coeff = false;
+  double kappa = 0, eta = 0;
+  std::vector<double> c_host;
+  double* d_c = nullptr;
+
+  // leaves
+  bool have_leaves = false;
+  int precision = HPS_FP64;
+  double2* d_T = nullptr;      // [E][nb][nb] FP64, side order l, r, b, t
+  int* d_flag = nullptr;
+
+  // tree
+  bool have_tree = false;
+  int L_exact = 0;
+  std::vector<hps::Stage> stages;
+  std::vector<hps::Level> levels;  // levels[l] for l = 1..L_exact (levels[0] unused)
+  hps::Coarse coarse;
+  int nrhs_cap = 0;                // sweep buffers sized for this many columns
+  void* ws_X1 = nullptr;           // merge workspaces
+  void* ws_X2 = nullptr;
+  size_t ws_X_elems = 0;
+  int* d_piv = nullptr;
+  void* d_lu = nullptr;
+  void* sw_tmp = nullptr;          // sweep temporaries [max npairs*m][nrhs], [max npairs*2m][nrhs]
+  void* sw_tmp2 = nullptr;
+  void* sw_zt = nullptr;
+  // coarse GMRES
+  int cg_k = 0, cg_nrhs = 0;
+  void *cg_V = nullptr, *cg_w = nullptr, *cg_W = nullptr, *cg_H = nullptr, *cg_h1 = nullptr, *cg_h2 = nullptr;
+  void *cg_nrm = nullptr, *cg_y = nullptr, *cg_g = nullptr, *cg_s = nullptr, *cg_part = nullptr;
+  void *cg_beta = nullptr, *cg_floor = nullptr, *cg_c = nullptr;
+  // exact coarse scratch
+  void *ex_r = nullptr, *ex_e = nullptr;
+  int ex_nrhs = 0;
+
+  // FP64 solver workspaces
+  int fg_restart = 0, fg_nrhs = 0;
+  double2 *fg_V = nullptr, *fg_Z = nullptr, *fg_x = nullptr, *fg_w = nullptr, *fg_rhs = nullptr, *fg_t = nullptr;
+  double2 *fg_h = nullptr, *fg_part = nullptr, *fg_y = nullptr;
+  double* fg_floor = nullptr;
+  double2* pin_h = nullptr;  // pinned host mirror of fg_h
+  double2* pin_y = nullptr;
+  double* pin_floor = nullptr;
+  double2 *pv_in = nullptr, *pv_out = nullptr;  // precond_apply/matvec ES staging
+  int pv_nrhs = 0;
+};
+
+namespace hps {
+
+int fail(hps_ctx* c, int code, const std::string& msg);
+int cuda_fail(hps_ctx* c, cudaError_t e, const char* what);
+void* dev_alloc(hps_ctx* c, size_t bytes);
+void dev_free(hps_ctx* c, void* p);
+template <typename T> T* dev_upload(hps_ctx* c, const std::vector<T>& v);
+void free_tree(hps_ctx* c);
+void free_solver(hps_ctx* c);
+int ensure_sweep_buffers(hps_ctx* c, int nrhs);
+
+// tree operations (merge.cu)
+int build_tree(hps_ctx* c, int L_exact, int exact_coarse);
+template <typename R>
+int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int inner_iters);
+
+}  // namespace hps
+
+#define HPS_CK(ctx, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return hps::cuda_fail(ctx, e_, #call); \
+  } while (0)

@@ -1,0 +1,223 @@
+// Batched leaf impedance-to-impedance maps (section 3.1, eq. ItIOperator), FP64.
+//
+// The paper defines T = I_o L^{-1} I(:, iota_Gamma) with L the element matrix
+// whose boundary rows are the incoming impedance operator I_i = Dn + i eta and
+// whose interior rows are those of L~ = K(x)M + M(x)K - diag(c) M(x)M.  Solving
+// L y = e_gamma by block elimination of the interior unknowns gives the same T:
+//
+//   interior rows:  L~_iG y_G + L~_ii y_i = 0       =>  y_i = -Z y_G,  Z = L~_ii^{-1} L~_iG
+//   boundary rows:  (Dn_GG - Dn_Gi Z + i eta) y_G = e_gamma
+//   => Y_G = P^{-1},  P = A + i eta I,  A = Dn_GG - Dn_Gi Z   (real, 4q x 4q)
+//   => T = I_o Y = Dn Y - i eta Y_G = I - 2 i eta P^{-1}.
+//
+// L~_ii is real and symmetric; it is positive definite when
+// c < lambda_min(K(x)M + M(x)K, M(x)M) on the interior (the host checks this
+// with a rigorous bound before launching), so Z comes from a real Cholesky
+// factorisation in shared memory (packed lower triangle, 203 KB at N = 16).
+// The 4q x 4q complex P is inverted by Gauss-Jordan with partial pivoting.
+//
+// One persistent CTA per SM (the factor needs almost all of the 227 KB of
+// shared memory); CTAs stride over the elements.
+#include "common.cuh"
+#include "dense.cuh"
+#include "skel.cuh"
+
+namespace hps {
+
+namespace {
+
+__device__ __forceinline__ int pk(int i, int j) { return i * (i + 1) / 2 + j; }  // j <= i
+
+__global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1, cw = p.cw;
+  const int npk = ni * (ni + 1) / 2;
+  double* Lp = reinterpret_cast<double*>(smem_raw);   // packed lower triangle of L~_ii
+  double* Bc = Lp + npk;                              // [ni][cw] chunk of right-hand sides
+  double* colk = Bc + ni * cw;                        // [ni] column k of the factor
+  // tables live past both the factor region and the Gauss-Jordan region
+  const int reg0 = max(npk + ni * cw + ni, 2 * nb * 2 * nb);
+  double* sD = Lp + reg0;                             // [n1*n1] physical D
+  double* sK = sD + n1 * n1;                          // [n1*n1] reference K (h-invariant)
+  double* sw = sK + n1 * n1;                          // [n1] reference weights
+  double* sc = sw + n1;                               // [n1*n1] c of this element
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const double h2 = 0.25 * p.h * p.h;                 // (h/2)^2
+  const double dsc = 2.0 / p.h;
+  double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
+
+  for (int l = tid; l < n1 * n1; l += nth) {
+    sD[l] = dsc * p.Dh[l];
+    sK[l] = p.Kh[l];
+  }
+  for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
+
+  for (int e = blockIdx.x; e < p.E; e += gridDim.x) {
+    __syncthreads();
+    for (int l = tid; l < n1 * n1; l += nth) sc[l] = p.c[(long long)e * n1 * n1 + l];
+    __syncthreads();
+    // ---- assemble L~_ii: interior node I = (i-1) q + (j-1), i, j in 1..q ----
+    // L~[(i,j),(i',j')] = K^[i,i'] w^_j d_jj' + w^_i K^[j,j'] d_ii' - c_ij (h/2)^2 w^_i w^_j d_IJ
+    for (int l = tid; l < npk; l += nth) {
+      // invert pk: row r with r(r+1)/2 <= l
+      int r = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+      while (r * (r + 1) / 2 > l) --r;
+      while ((r + 1) * (r + 2) / 2 <= l) ++r;
+      const int cc = l - r * (r + 1) / 2;
+      const int i = r / q + 1, j = r % q + 1, i2 = cc / q + 1, j2 = cc % q + 1;
+      double v = 0.0;
+      if (j == j2) v += sK[i * n1 + i2] * sw[j];
+      if (i == i2) v += sw[i] * sK[j * n1 + j2];
+      if (r == cc) v -= sc[i * n1 + j] * h2 * sw[i] * sw[j];
+      Lp[l] = v;
+    }
+    __syncthreads();
+    // ---- right-looking Cholesky, column scaling deferred by one step ----
+    double prev_rs = 0.0;
+    for (int k = 0; k < ni; ++k) {
+      for (int i = k + tid; i < ni; i += nth) colk[i] = Lp[pk(i, k)];
+      __syncthreads();
+      double dk = colk[k];
+      if (!(dk > 0.0)) {
+        if (tid == 0) atomicCAS(p.flag, 0, e + 1);
+        dk = 1.0;
+      }
+      const double inv = 1.0 / dk;
+      if (k > 0)
+        for (int i = k - 1 + tid; i < ni; i += nth) Lp[pk(i, k - 1)] *= prev_rs;
+      const int warp = tid / 32, lane = tid % 32, nw = nth / 32;
+      for (int i = k + 1 + warp; i < ni; i += nw) {
+        const double f = colk[i] * inv;
+        double* row = Lp + pk(i, 0);
+        for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= f * colk[j];
+      }
+      prev_rs = 1.0 / sqrt(dk);
+      __syncthreads();
+    }
+    if (tid == 0) Lp[pk(ni - 1, ni - 1)] *= prev_rs;
+    __syncthreads();
+
+    // ---- Z = L~_ii^{-1} L~_iG by chunks of cw columns, A = Dn_GG - Dn_Gi Z ----
+    for (int g0 = 0; g0 < nb; g0 += cw) {
+      const int w = nb - g0 < cw ? nb - g0 : cw;
+      for (int l = tid; l < ni * cw; l += nth) Bc[l] = 0.0;
+      __syncthreads();
+      // L~_iG columns: l(j'): K^[i,0] w^_j' at (i,j'); r(j'): K^[i,N] w^_j';
+      //                b(i'): w^_i' K^[j,0] at (i',j);  t(i'): w^_i' K^[j,N]
+      for (int l = tid; l < w * q; l += nth) {
+        const int cc = l / q, t = l % q + 1;  // t runs along the interior line
+        const int g = g0 + cc, side = g / q, s = g % q + 1;
+        int I;
+        double v;
+        if (side == 0) { I = (t - 1) * q + (s - 1); v = sK[t * n1 + 0] * sw[s]; }
+        else if (side == 1) { I = (t - 1) * q + (s - 1); v = sK[t * n1 + N] * sw[s]; }
+        else if (side == 2) { I = (s - 1) * q + (t - 1); v = sw[s] * sK[t * n1 + 0]; }
+        else { I = (s - 1) * q + (t - 1); v = sw[s] * sK[t * n1 + N]; }
+        Bc[I * cw + cc] = v;
+      }
+      __syncthreads();
+      // forward: L y = b (diagonal division deferred)
+      for (int k = 0; k < ni - 1; ++k) {
+        const double inv = 1.0 / Lp[pk(k, k)];
+        const int cnt = (ni - k - 1) * w;
+        for (int l = tid; l < cnt; l += nth) {
+          const int i = k + 1 + l / w, cc = l % w;
+          Bc[i * cw + cc] -= Lp[pk(i, k)] * (Bc[k * cw + cc] * inv);
+        }
+        __syncthreads();
+      }
+      for (int l = tid; l < ni * w; l += nth) {
+        const int i = l / w, cc = l % w;
+        Bc[i * cw + cc] /= Lp[pk(i, i)];
+      }
+      __syncthreads();
+      // backward: L^T x = y
+      for (int k = ni - 1; k > 0; --k) {
+        const double inv = 1.0 / Lp[pk(k, k)];
+        const double* row = Lp + pk(k, 0);
+        const int cnt = k * w;
+        for (int l = tid; l < cnt; l += nth) {
+          const int i = l / w, cc = l % w;
+          Bc[i * cw + cc] -= row[i] * (Bc[k * cw + cc] * inv);
+        }
+        __syncthreads();
+      }
+      for (int l = tid; l < ni * w; l += nth) {
+        const int i = l / w, cc = l % w;
+        Bc[i * cw + cc] /= Lp[pk(i, i)];
+      }
+      __syncthreads();
+      // A(:, chunk): Dn rows l(j): -D[0,i'] on (i',j); r(j): D[N,i']; b(i): -D[0,j'] on (i,j'); t(i): D[N,j']
+      for (int l = tid; l < nb * w; l += nth) {
+        const int g = l / w, cc = l % w, gc = g0 + cc;
+        const int side = g / q, s = g % q + 1;
+        double acc = 0.0;
+        for (int t = 1; t <= q; ++t) {
+          int I;
+          double dcoef;
+          if (side == 0) { I = (t - 1) * q + (s - 1); dcoef = -sD[0 * n1 + t]; }
+          else if (side == 1) { I = (t - 1) * q + (s - 1); dcoef = sD[N * n1 + t]; }
+          else if (side == 2) { I = (s - 1) * q + (t - 1); dcoef = -sD[0 * n1 + t]; }
+          else { I = (s - 1) * q + (t - 1); dcoef = sD[N * n1 + t]; }
+          acc += dcoef * Bc[I * cw + cc];
+        }
+        // Dn_GG: same-position node and the opposite side's node on the same line
+        const int sidec = gc / q, sc2 = gc % q + 1;
+        double dgg = 0.0;
+        if (sc2 == s) {
+          const bool xside = side < 2, xsidec = sidec < 2;
+          if (xside == xsidec) {
+            const int rowN = (side == 0 || side == 2) ? 0 : N;     // which D row
+            const int colN = (sidec == 0 || sidec == 2) ? 0 : N;   // which node column
+            const double sg = (side == 0 || side == 2) ? -1.0 : 1.0;
+            dgg = sg * sD[rowN * n1 + colN];
+          }
+        }
+        A[g * nb + gc] = dgg - acc;
+      }
+      __syncthreads();
+    }
+
+    // ---- P = A + i eta I, Gauss-Jordan [P | I] -> P^{-1}, T = I - 2 i eta P^{-1} ----
+    double2* W = reinterpret_cast<double2*>(smem_raw);  // reuses the factor's space
+    const int ld = 2 * nb;
+    for (int l = tid; l < nb * ld; l += nth) {
+      const int g = l / ld, j = l % ld;
+      double2 v = make_double2(0.0, 0.0);
+      if (j < nb) {
+        v.x = A[g * nb + j];
+        if (j == g) v.y = p.eta;
+      } else if (j - nb == g) {
+        v.x = 1.0;
+      }
+      W[l] = v;
+    }
+    __syncthreads();
+    gj_smem<double>(W, nb, ld, ld, nullptr);
+    double2* To = p.T + (long long)e * nb * nb;
+    for (int l = tid; l < nb * nb; l += nth) {
+      const int g = l / nb, j = l % nb;
+      const double2 y = W[g * ld + nb + j];
+      To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * p.eta * y.y, -2.0 * p.eta * y.x);
+    }
+  }
+}
+
+}  // namespace
+
+size_t leaf_smem_bytes(int N, int cw) {
+  const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
+  const size_t r1 = (size_t)ni * (ni + 1) / 2 + (size_t)ni * cw + ni;
+  const size_t r2 = (size_t)2 * nb * 2 * nb;  // double2 [nb][2 nb] in doubles
+  return sizeof(double) * ((r1 > r2 ? r1 : r2) + 3 * n1 * n1 + n1);
+}
+
+cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
+  const size_t smem = leaf_smem_bytes(p.N, p.cw);
+  cudaError_t err = cudaFuncSetAttribute(leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  leaf_kernel<<<grid, 256, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace hps

@@ -1,0 +1,581 @@
+// Nested-dissection merge tree and the multigrid V-cycle (sections 4.1-4.3).
+//
+// Stage k (k merges done) tiles the mesh with a x b element blocks,
+// a = 2^ceil(k/2), b = 2^floor(k/2) (x-merges at odd levels, y-merges at even
+// levels, Fig. 1).  Each subdomain's ItI map is stored "interface first": the
+// side that the next merge eliminates comes first, then the other sides in the
+// order l, r, b, t; the last stage (the coarse level) keeps l, r, b, t.
+//
+// Merge l pairs s1 (left/bottom) with s2 (right/top); interface alpha of s1 and
+// beta of s2 (m unknowns each), outer parts E1, E2 (p = n - m each).  With the
+// transmission condition in_2 = -out_1, in_1 = -out_2 the interface unknowns
+// x = (in1_alpha, in2_beta) satisfy A x = f - B y with
+//     A = [[I, T2_bb], [T1_aa, I]],   B y = (T2_bE2 y2, T1_aE1 y1),
+// and A is reduced to its Schur complement S = I - T2_bb T1_aa:
+//     x1 = S^{-1} (f1 - T2_bb f2),  x2 = f2 - T1_aa x1.
+// The merged map (eq. globalfacesystem) T_pair = D - C A^{-1} B becomes
+//     X1 = S^{-1} [ -T2_bb T1_aE1 | T2_bE2 ],   X2 = [ T1_aE1 | 0 ] - T1_aa X1,
+//     T_pair = [[T1_E1E1, 0], [0, T2_E2E2]] - [[T1_E1a X1], [T2_E2b X2]].
+//
+// V-cycle (section 4.3, MG(M) = F + P MG(S) R (I - M F)): residuals live in
+// "outgoing" coordinates (the residual of the equation owned by side p), so
+// every step touches one pair only:
+//   up:    z1 = S^{-1}(f1 - T2_bb f2), z2 = f2 - T1_aa z1,  f1 = rho2_beta, f2 = rho1_alpha,
+//          rho'_E1 = rho1_E1 - T1_E1a z1,  rho'_E2 = rho2_E2 - T2_E2b z2;
+//   down:  h1 = f1 - T2_bE2 e2_E2,  h2 = f2 - T1_aE1 e1_E1,
+//          x1 = S^{-1}(h1 - T2_bb h2),  x2 = h2 - T1_aa x1   (= A^{-1}(r_x - B e)).
+// The coarse system M_{L_exact+1} = I + Pi T_c is solved by a fixed number of
+// GMRES steps from zero (or by a dense inverse).
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "skel.cuh"
+
+namespace hps {
+
+namespace {
+
+void natural_es(const hps_ctx* c, int sx, int sy, int a, int b, std::vector<int>& out) {
+  out.clear();
+  const int q = c->q, nx = c->nx;
+  const int ix0 = sx * a, iy0 = sy * b;
+  auto es = [&](int e, int s, int k) { return (e * 4 + s) * q + k; };
+  for (int t = 0; t < b; ++t)
+    for (int k = 0; k < q; ++k) out.push_back(es(ix0 + nx * (iy0 + t), 0, k));
+  for (int t = 0; t < b; ++t)
+    for (int k = 0; k < q; ++k) out.push_back(es(ix0 + a - 1 + nx * (iy0 + t), 1, k));
+  for (int t = 0; t < a; ++t)
+    for (int k = 0; k < q; ++k) out.push_back(es(ix0 + t + nx * iy0, 2, k));
+  for (int t = 0; t < a; ++t)
+    for (int k = 0; k < q; ++k) out.push_back(es(ix0 + t + nx * (iy0 + b - 1), 3, k));
+}
+
+// side ranges [lo, hi) in natural order
+void side_range(int a, int b, int q, int side, int& lo, int& hi) {
+  const int o[5] = {0, b * q, 2 * b * q, 2 * b * q + a * q, 2 * (a + b) * q};
+  lo = o[side];
+  hi = o[side + 1];
+}
+
+size_t csize(int prec) { return prec == HPS_FP64 ? sizeof(double2) : sizeof(float2); }
+
+template <typename R>
+cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long lda, const void* B, long long ldb,
+                 const void* C0, long long ldc0, void* C, long long ldc, double alpha, const int* maps, int mmax,
+                 int nmax, int n_launch) {
+  GemmArgs<R> a;
+  a.A = static_cast<const c_t<R>*>(A);
+  a.B = static_cast<const c_t<R>*>(B);
+  a.C0 = static_cast<const c_t<R>*>(C0);
+  a.C = static_cast<c_t<R>*>(C);
+  a.lda = lda;
+  a.ldb = ldb;
+  a.ldc0 = ldc0;
+  a.ldc = ldc;
+  a.alpha = mk<R>(R(alpha), R(0));
+  a.beta = mk<R>(R(1), R(0));
+  a.desc = d;
+  a.nbatch = nb;
+  a.maps = maps;
+  a.n_launch = n_launch;
+  return launch_gemm<R>(a, mmax, nmax, c->stream);
+}
+
+GemmDesc D(int a_r, int a_c, int b_r, int b_c, int c0_r, int c0_c, int c_r, int c_c, int m, int n, int k, int rmap = -1,
+           int cmap = -1) {
+  GemmDesc d;
+  d.a_r = a_r; d.a_c = a_c; d.b_r = b_r; d.b_c = b_c; d.c0_r = c0_r; d.c0_c = c0_c; d.c_r = c_r; d.c_c = c_c;
+  d.m = m; d.n = n; d.k = k; d.rmap = rmap; d.cmap = cmap;
+  return d;
+}
+
+template <typename R>
+int build_tree_t(hps_ctx* c, int L_exact, int exact) {
+  using C = c_t<R>;
+  const int q = c->q;
+  c->L_exact = L_exact;
+  c->stages.assign(L_exact + 1, Stage());
+  c->levels.assign(L_exact + 1, Level());
+  std::vector<std::vector<int>> inv(L_exact + 1);
+  std::vector<int> nat;
+  // ---- stage geometry and storage orders ----
+  for (int k = 0; k <= L_exact; ++k) {
+    Stage& S = c->stages[k];
+    S.a = 1 << ((k + 1) / 2);
+    S.b = 1 << (k / 2);
+    S.gx = c->nx / S.a;
+    S.gy = c->ny / S.b;
+    S.nsub = S.gx * S.gy;
+    S.n = 2 * (S.a + S.b) * q;
+    S.es.assign((size_t)S.nsub * S.n, -1);
+    inv[k].assign(c->n_es, -1);
+    for (int sy = 0; sy < S.gy; ++sy)
+      for (int sx = 0; sx < S.gx; ++sx) {
+        const int s = sx + S.gx * sy;
+        natural_es(c, sx, sy, S.a, S.b, nat);
+        std::vector<int> order;
+        if (k < L_exact) {
+          const bool xm = ((k + 1) % 2) == 1;
+          const int role = xm ? sx % 2 : sy % 2;
+          const int iface = xm ? (role == 0 ? 1 : 0) : (role == 0 ? 3 : 2);
+          int lo, hi;
+          side_range(S.a, S.b, q, iface, lo, hi);
+          for (int i = lo; i < hi; ++i) order.push_back(i);
+          for (int sd = 0; sd < 4; ++sd) {
+            if (sd == iface) continue;
+            side_range(S.a, S.b, q, sd, lo, hi);
+            for (int i = lo; i < hi; ++i) order.push_back(i);
+          }
+        } else {
+          for (int i = 0; i < S.n; ++i) order.push_back(i);
+        }
+        for (int i = 0; i < S.n; ++i) {
+          const int e = nat[order[i]];
+          S.es[(size_t)s * S.n + i] = e;
+          if (inv[k][e] != -1) return fail(c, HPS_ECUDA, "internal: element side on two subdomain boundaries");
+          inv[k][e] = i;
+        }
+      }
+  }
+  // ---- levels: pairs, destination maps, checks ----
+  size_t x_elems = 0;
+  int max_pm = 0, max_p2m = 0, max_pairs = 0;
+  for (int l = 1; l <= L_exact; ++l) {
+    Level& Lv = c->levels[l];
+    const Stage& P0 = c->stages[l - 1];
+    const Stage& P1 = c->stages[l];
+    Lv.dir = (l % 2 == 1) ? 0 : 1;
+    Lv.n = P0.n;
+    Lv.m = Lv.dir == 0 ? P0.b * q : P0.a * q;
+    Lv.p = Lv.n - Lv.m;
+    Lv.npairs = P1.nsub;
+    if (2 * Lv.p != P1.n) return fail(c, HPS_ECUDA, "internal: merged boundary length");
+    Lv.i1.resize(Lv.npairs);
+    Lv.i2.resize(Lv.npairs);
+    std::vector<int> dst((size_t)Lv.npairs * 2 * Lv.p), up((size_t)P1.nsub * P1.n, -1);
+    for (int sy = 0; sy < P1.gy; ++sy)
+      for (int sx = 0; sx < P1.gx; ++sx) {
+        const int P = sx + P1.gx * sy;
+        int s1, s2;
+        if (Lv.dir == 0) {
+          s1 = 2 * sx + P0.gx * sy;
+          s2 = 2 * sx + 1 + P0.gx * sy;
+        } else {
+          s1 = sx + P0.gx * (2 * sy);
+          s2 = sx + P0.gx * (2 * sy + 1);
+        }
+        Lv.i1[P] = s1;
+        Lv.i2[P] = s2;
+        for (int i = 0; i < Lv.m; ++i) {
+          const int a1 = P0.es[(size_t)s1 * P0.n + i], a2 = P0.es[(size_t)s2 * P0.n + i];
+          if (c->es_nb[a1] != a2) return fail(c, HPS_ECUDA, "internal: interface nodes do not match");
+        }
+        std::vector<char> seen(2 * Lv.p, 0);
+        for (int i = 0; i < 2 * Lv.p; ++i) {
+          const int child = i < Lv.p ? s1 : s2;
+          const int ci = Lv.m + (i < Lv.p ? i : i - Lv.p);
+          const int e = P0.es[(size_t)child * P0.n + ci];
+          const int d = inv[l][e];
+          if (d < 0 || P1.es[(size_t)P * P1.n + d] != e || seen[d])
+            return fail(c, HPS_ECUDA, "internal: merge destination map");
+          seen[d] = 1;
+          dst[(size_t)P * 2 * Lv.p + i] = d;
+          up[(size_t)P * P1.n + d] = child * P0.n + ci;
+        }
+      }
+    Lv.d_dst = dev_upload(c, dst);
+    Lv.d_up = dev_upload(c, up);
+    if (!Lv.d_dst || !Lv.d_up) return fail(c, HPS_ENOMEM, "merge maps");
+    x_elems = std::max(x_elems, (size_t)Lv.npairs * Lv.m * 2 * Lv.p);
+    max_pm = std::max(max_pm, Lv.npairs * Lv.m);
+    max_p2m = std::max(max_p2m, Lv.npairs * 2 * Lv.m);
+    max_pairs = std::max(max_pairs, Lv.npairs);
+  }
+  // ---- descriptors ----
+  for (int l = 1; l <= L_exact; ++l) {
+    Level& Lv = c->levels[l];
+    const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
+    std::vector<GemmDesc> md((size_t)N_MROLE * NP), sd((size_t)N_SROLE * NP);
+    for (int P = 0; P < NP; ++P) {
+      const int r1 = Lv.i1[P] * n, r2 = Lv.i2[P] * n;  // child row offsets in T / stage vectors
+      const int w = P * m, x = P * m, t = P * 2 * p;
+      const int dm1 = P * 2 * p, dm2 = P * 2 * p + p;  // dst map offsets for E1, E2
+      md[MS * NP + P] = D(r2, 0, r1, 0, w, 0, w, 0, m, m, m);
+      md[MR * NP + P] = D(r2, 0, r1, m, 0, 0, x, 0, m, p, m);
+      md[MX1A * NP + P] = D(w, m, x, 0, 0, 0, x, 0, m, p, m);
+      md[MX1B * NP + P] = D(w, m, r2, m, 0, 0, x, p, m, p, m);
+      md[MX2A * NP + P] = D(r1, 0, x, 0, r1, m, x, 0, m, p, m);
+      md[MX2B * NP + P] = D(r1, 0, x, p, 0, 0, x, p, m, p, m);
+      md[MOA * NP + P] = D(r1 + m, 0, x, 0, r1 + m, m, t, 0, p, p, m, dm1, dm1);
+      md[MOB * NP + P] = D(r1 + m, 0, x, p, 0, 0, t, 0, p, p, m, dm1, dm2);
+      md[MOC * NP + P] = D(r2 + m, 0, x, 0, 0, 0, t, 0, p, p, m, dm2, dm1);
+      md[MOD * NP + P] = D(r2 + m, 0, x, p, r2 + m, m, t, 0, p, p, m, dm2, dm2);
+      // sweeps (vector rows; n = -1 -> number of right-hand sides)
+      const int tm = P * m, t2 = P * 2 * m, mr = P * 2 * p;  // tmp rows, tmp2/zt rows, merged rows
+      sd[UP1 * NP + P] = D(r2, 0, r1, 0, r2, 0, tm, 0, m, -1, m);
+      sd[UP2 * NP + P] = D(w, m, tm, 0, 0, 0, t2, 0, m, -1, m);
+      sd[UP3 * NP + P] = D(r1, 0, t2, 0, r1, 0, t2 + m, 0, m, -1, m);
+      sd[UP4 * NP + P] = D(r1 + m, 0, t2, 0, r1 + m, 0, mr, 0, p, -1, m, dm1, -1);
+      sd[UP5 * NP + P] = D(r2 + m, 0, t2 + m, 0, r2 + m, 0, mr, 0, p, -1, m, dm2, -1);
+      sd[DN1 * NP + P] = D(r2, m, r2 + m, 0, r2, 0, t2, 0, m, -1, p);
+      sd[DN2 * NP + P] = D(r1, m, r1 + m, 0, r1, 0, t2 + m, 0, m, -1, p);
+      sd[DN3 * NP + P] = D(r2, 0, t2 + m, 0, t2, 0, tm, 0, m, -1, m);
+      sd[DN4 * NP + P] = D(w, m, tm, 0, 0, 0, r1, 0, m, -1, m);
+      sd[DN5 * NP + P] = D(r1, 0, r1, 0, t2 + m, 0, r2, 0, m, -1, m);
+    }
+    Lv.d_mdesc = dev_upload(c, md);
+    Lv.d_sdesc = dev_upload(c, sd);
+    if (!Lv.d_mdesc || !Lv.d_sdesc) return fail(c, HPS_ENOMEM, "descriptors");
+  }
+  // ---- allocations ----
+  for (int k = 0; k <= L_exact; ++k) {
+    Stage& S = c->stages[k];
+    S.T = dev_alloc(c, sizeof(C) * (size_t)S.nsub * S.n * S.n);
+    if (!S.T) return fail(c, HPS_ENOMEM, "stage maps");
+    if (k == 0 || k == L_exact) {
+      S.d_es = dev_upload(c, S.es);
+      if (!S.d_es) return fail(c, HPS_ENOMEM, "stage index");
+    }
+  }
+  for (int l = 1; l <= L_exact; ++l) {
+    Level& Lv = c->levels[l];
+    Lv.W = dev_alloc(c, sizeof(C) * (size_t)Lv.npairs * Lv.m * 2 * Lv.m);
+    if (!Lv.W) return fail(c, HPS_ENOMEM, "interface inverses");
+  }
+  if (L_exact > 0) {
+    c->ws_X1 = dev_alloc(c, sizeof(C) * x_elems);
+    c->ws_X2 = dev_alloc(c, sizeof(C) * x_elems);
+    c->d_piv = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)max_pairs * GJ_NB));
+    c->d_lu = dev_alloc(c, sizeof(C) * (size_t)max_pairs * GJ_NB * GJ_NB);
+    if (!c->ws_X1 || !c->ws_X2 || !c->d_piv || !c->d_lu) return fail(c, HPS_ENOMEM, "merge workspace");
+    c->ws_X_elems = x_elems;
+  }
+  // ---- stage 0 maps from the FP64 leaf maps ----
+  {
+    const Stage& S0 = c->stages[0];
+    std::vector<int> map0((size_t)S0.nsub * S0.n);
+    for (int e = 0; e < S0.nsub; ++e)
+      for (int i = 0; i < S0.n; ++i) map0[(size_t)e * S0.n + i] = S0.es[(size_t)e * S0.n + i] - e * c->nb;
+    int* dmap = dev_upload(c, map0);
+    if (!dmap) return fail(c, HPS_ENOMEM, "stage-0 map");
+    HPS_CK(c, (permute_blocks<double, R>(static_cast<C*>(S0.T), c->d_T, dmap, S0.nsub, S0.n, c->stream)));
+    HPS_CK(c, cudaStreamSynchronize(c->stream));
+    dev_free(c, dmap);
+  }
+  // ---- merges ----
+  HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  for (int l = 1; l <= L_exact; ++l) {
+    Level& Lv = c->levels[l];
+    const Stage& P0 = c->stages[l - 1];
+    const Stage& P1 = c->stages[l];
+    const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
+    const GemmDesc* md = Lv.d_mdesc;
+    const void* T0 = P0.T;
+    HPS_CK(c, eye2<R>(static_cast<C*>(Lv.W), m, NP, c->stream));
+    HPS_CK(c, gemm<R>(c, md + MS * NP, NP, T0, n, T0, n, Lv.W, 2 * m, Lv.W, 2 * m, -1.0, nullptr, m, m, m));
+    HPS_CK(c, gj_invert<R>(static_cast<C*>(Lv.W), m, NP, c->d_piv, static_cast<C*>(c->d_lu), c->d_flag, c->stream));
+    HPS_CK(c, gemm<R>(c, md + MR * NP, NP, T0, n, T0, n, nullptr, 0, c->ws_X2, 2 * p, -1.0, nullptr, m, p, p));
+    HPS_CK(c, gemm<R>(c, md + MX1A * NP, NP, Lv.W, 2 * m, c->ws_X2, 2 * p, nullptr, 0, c->ws_X1, 2 * p, 1.0, nullptr, m,
+                      p, p));
+    HPS_CK(c, gemm<R>(c, md + MX1B * NP, NP, Lv.W, 2 * m, T0, n, nullptr, 0, c->ws_X1, 2 * p, 1.0, nullptr, m, p, p));
+    HPS_CK(c, gemm<R>(c, md + MX2A * NP, NP, T0, n, c->ws_X1, 2 * p, T0, n, c->ws_X2, 2 * p, -1.0, nullptr, m, p, p));
+    HPS_CK(c, gemm<R>(c, md + MX2B * NP, NP, T0, n, c->ws_X1, 2 * p, nullptr, 0, c->ws_X2, 2 * p, -1.0, nullptr, m, p,
+                      p));
+    void* Tn = P1.T;
+    HPS_CK(c, gemm<R>(c, md + MOA * NP, NP, T0, n, c->ws_X1, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
+    HPS_CK(c, gemm<R>(c, md + MOB * NP, NP, T0, n, c->ws_X1, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
+    HPS_CK(c, gemm<R>(c, md + MOC * NP, NP, T0, n, c->ws_X2, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
+    HPS_CK(c, gemm<R>(c, md + MOD * NP, NP, T0, n, c->ws_X2, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
+  }
+  // ---- coarse level ----
+  {
+    const Stage& Sc = c->stages[L_exact];
+    Coarse& cc = c->coarse;
+    int lo, hi;
+    for (int sd = 0; sd < 4; ++sd) {
+      side_range(Sc.a, Sc.b, q, sd, lo, hi);
+      cc.off[sd] = lo;
+      cc.off[sd + 1] = hi;
+    }
+    std::vector<int> mask(Sc.nsub), cnb((size_t)Sc.nsub * Sc.n, -1), upos, ucnb;
+    for (int sy = 0; sy < Sc.gy; ++sy)
+      for (int sx = 0; sx < Sc.gx; ++sx) {
+        const int s = sx + Sc.gx * sy;
+        mask[s] = (sx > 0 ? 1 : 0) | (sx < Sc.gx - 1 ? 2 : 0) | (sy > 0 ? 4 : 0) | (sy < Sc.gy - 1 ? 8 : 0);
+      }
+    std::vector<int> owner(c->n_es, -1);
+    for (int s = 0; s < Sc.nsub; ++s)
+      for (int i = 0; i < Sc.n; ++i) owner[Sc.es[(size_t)s * Sc.n + i]] = s;
+    for (int s = 0; s < Sc.nsub; ++s)
+      for (int i = 0; i < Sc.n; ++i) {
+        const size_t r = (size_t)s * Sc.n + i;
+        const int en = c->es_nb[Sc.es[r]];
+        if (en < 0) continue;
+        const int so = owner[en];
+        const int d = inv[L_exact][en];
+        if (so < 0 || so == s || d < 0) return fail(c, HPS_ECUDA, "internal: coarse neighbour map");
+        cnb[r] = so * Sc.n + d;
+        upos.push_back((int)r);
+      }
+    cc.n_int = (int)upos.size();
+    for (int u = 0; u < cc.n_int; ++u) ucnb.push_back(cnb[upos[u]]);
+    cc.d_mask = dev_upload(c, mask);
+    cc.d_cnb = dev_upload(c, cnb);
+    cc.d_upos = dev_upload(c, upos);
+    cc.d_ucnb = dev_upload(c, ucnb);
+    if (!cc.d_mask || !cc.d_cnb || !cc.d_upos || !cc.d_ucnb) return fail(c, HPS_ENOMEM, "coarse maps");
+    cc.exact = exact != 0;
+    if (cc.exact && cc.n_int > 0) {
+      const int ni = cc.n_int;
+      cc.Winv = dev_alloc(c, sizeof(C) * (size_t)ni * 2 * ni);
+      if (!cc.Winv) return fail(c, HPS_ENOMEM, "coarse inverse");
+      // dense M_c = I + Pi T_c on the interior positions, then [M_c | I] -> [. | M_c^{-1}]
+      std::vector<int> compact((size_t)Sc.nsub * Sc.n, -1);
+      for (int u = 0; u < ni; ++u) compact[upos[u]] = u;
+      // host assembly from a host copy of T_c (small by construction of the exact mode)
+      std::vector<C> Th((size_t)Sc.nsub * Sc.n * Sc.n);
+      HPS_CK(c, cudaStreamSynchronize(c->stream));
+      HPS_CK(c, cudaMemcpy(Th.data(), Sc.T, sizeof(C) * Th.size(), cudaMemcpyDeviceToHost));
+      std::vector<C> Wh((size_t)ni * 2 * ni);
+      for (auto& z : Wh) z = mk<R>(R(0), R(0));
+      for (int u = 0; u < ni; ++u) {
+        Wh[(size_t)u * 2 * ni + u] = mk<R>(R(1), R(0));
+        Wh[(size_t)u * 2 * ni + ni + u] = mk<R>(R(1), R(0));
+        const int across = ucnb[u];
+        const int so = across / Sc.n, io = across % Sc.n;
+        for (int j = 0; j < Sc.n; ++j) {
+          const int v = compact[(size_t)so * Sc.n + j];
+          if (v < 0) continue;
+          const C t = Th[((size_t)so * Sc.n + io) * Sc.n + j];
+          C& dst = Wh[(size_t)u * 2 * ni + v];
+          dst.x += t.x;
+          dst.y += t.y;
+        }
+      }
+      HPS_CK(c, cudaMemcpy(cc.Winv, Wh.data(), sizeof(C) * Wh.size(), cudaMemcpyHostToDevice));
+      std::vector<GemmDesc> dd(1, D(0, ni, 0, 0, 0, 0, 0, 0, ni, -1, ni));
+      cc.d_desc = dev_upload(c, dd);
+      if (!cc.d_desc) return fail(c, HPS_ENOMEM, "coarse descriptor");
+      int* piv = static_cast<int*>(dev_alloc(c, sizeof(int) * GJ_NB));
+      void* lu = dev_alloc(c, sizeof(C) * GJ_NB * GJ_NB);
+      if (!piv || !lu) return fail(c, HPS_ENOMEM, "coarse workspace");
+      HPS_CK(c, gj_invert<R>(static_cast<C*>(cc.Winv), ni, 1, piv, static_cast<C*>(lu), c->d_flag, c->stream));
+      HPS_CK(c, cudaStreamSynchronize(c->stream));
+      dev_free(c, piv);
+      dev_free(c, lu);
+    }
+  }
+  int flag = 0;
+  HPS_CK(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HPS_CK(c, cudaStreamSynchronize(c->stream));
+  if (flag) return fail(c, HPS_ENUMERIC, "zero pivot in an interface or coarse inversion");
+  c->have_tree = true;
+  return HPS_OK;
+}
+
+}  // namespace
+
+int build_tree(hps_ctx* c, int L_exact, int exact_coarse) {
+  free_tree(c);
+  int rc = c->precision == HPS_FP64 ? build_tree_t<double>(c, L_exact, exact_coarse)
+                                    : build_tree_t<float>(c, L_exact, exact_coarse);
+  if (rc != HPS_OK) {
+    cudaStreamSynchronize(c->stream);
+    free_tree(c);
+  }
+  return rc;
+}
+
+int ensure_sweep_buffers(hps_ctx* c, int nrhs) {
+  if (nrhs <= c->nrhs_cap) return HPS_OK;
+  const size_t cs = csize(c->precision);
+  for (auto& S : c->stages) {
+    dev_free(c, S.vec);
+    S.vec = dev_alloc(c, cs * (size_t)S.nsub * S.n * nrhs);
+    if (!S.vec) return fail(c, HPS_ENOMEM, "sweep vectors");
+  }
+  size_t pm = 1, p2m = 1;
+  for (int l = 1; l <= c->L_exact; ++l) {
+    pm = std::max(pm, (size_t)c->levels[l].npairs * c->levels[l].m);
+    p2m = std::max(p2m, (size_t)c->levels[l].npairs * 2 * c->levels[l].m);
+  }
+  dev_free(c, c->sw_tmp);
+  dev_free(c, c->sw_tmp2);
+  dev_free(c, c->sw_zt);
+  c->sw_tmp = dev_alloc(c, cs * pm * nrhs);
+  c->sw_tmp2 = dev_alloc(c, cs * p2m * nrhs);
+  c->sw_zt = dev_alloc(c, cs * p2m * nrhs);
+  if (!c->sw_tmp || !c->sw_tmp2 || !c->sw_zt) return fail(c, HPS_ENOMEM, "sweep temporaries");
+  c->nrhs_cap = nrhs;
+  return HPS_OK;
+}
+
+namespace {
+
+template <typename R>
+int ensure_cg(hps_ctx* c, int k, int nrhs) {
+  if (k <= c->cg_k && nrhs <= c->cg_nrhs) return HPS_OK;
+  k = std::max(k, c->cg_k);
+  nrhs = std::max(nrhs, c->cg_nrhs);
+  const Stage& Sc = c->stages[c->L_exact];
+  const size_t rows = (size_t)Sc.nsub * Sc.n;
+  const size_t cs = sizeof(c_t<R>);
+  void** bufs[] = {&c->cg_V, &c->cg_w, &c->cg_W, &c->cg_H, &c->cg_h1, &c->cg_h2, &c->cg_nrm,
+                   &c->cg_y, &c->cg_g, &c->cg_s, &c->cg_part, &c->cg_beta, &c->cg_floor, &c->cg_c};
+  for (void** b : bufs) {
+    dev_free(c, *b);
+    *b = nullptr;
+  }
+  c->cg_V = dev_alloc(c, cs * (k + 1) * rows * nrhs);
+  c->cg_w = dev_alloc(c, cs * rows * nrhs);
+  c->cg_W = dev_alloc(c, cs * rows * nrhs);
+  c->cg_H = dev_alloc(c, cs * (size_t)nrhs * (k + 1) * k);
+  c->cg_h1 = dev_alloc(c, cs * (size_t)(k + 1) * nrhs);
+  c->cg_h2 = dev_alloc(c, cs * (size_t)(k + 1) * nrhs);
+  c->cg_nrm = dev_alloc(c, cs * nrhs);
+  c->cg_y = dev_alloc(c, cs * (size_t)k * nrhs);
+  c->cg_g = dev_alloc(c, cs * (size_t)(k + 1) * nrhs);
+  c->cg_s = dev_alloc(c, cs * (size_t)k * nrhs);
+  c->cg_part = dev_alloc(c, cs * (size_t)bdot_blocks((long long)rows) * (k + 1) * nrhs);
+  c->cg_beta = dev_alloc(c, sizeof(R) * nrhs);
+  c->cg_floor = dev_alloc(c, sizeof(R) * nrhs);
+  c->cg_c = dev_alloc(c, sizeof(R) * (size_t)k * nrhs);
+  for (void** b : bufs)
+    if (!*b) return fail(c, HPS_ENOMEM, "coarse GMRES workspace");
+  c->cg_k = k;
+  c->cg_nrhs = nrhs;
+  return HPS_OK;
+}
+
+template <typename R>
+int coarse_solve(hps_ctx* c, int nrhs, int k) {
+  using C = c_t<R>;
+  const Stage& Sc = c->stages[c->L_exact];
+  const Coarse& cc = c->coarse;
+  const long long rows = (long long)Sc.nsub * Sc.n;
+  C* Vc = static_cast<C*>(Sc.vec);
+  cudaStream_t st = c->stream;
+  if (cc.n_int == 0 || (!cc.exact && k <= 0)) {
+    HPS_CK(c, zero<R>(Vc, rows * nrhs, st));
+    return HPS_OK;
+  }
+  if (cc.exact) {
+    if (nrhs > c->ex_nrhs) {
+      dev_free(c, c->ex_r);
+      dev_free(c, c->ex_e);
+      c->ex_r = dev_alloc(c, sizeof(C) * (size_t)cc.n_int * nrhs);
+      c->ex_e = dev_alloc(c, sizeof(C) * (size_t)cc.n_int * nrhs);
+      if (!c->ex_r || !c->ex_e) return fail(c, HPS_ENOMEM, "exact coarse scratch");
+      c->ex_nrhs = nrhs;
+    }
+    HPS_CK(c, (gather_rows<R, R>(static_cast<C*>(c->ex_r), Vc, cc.d_ucnb, cc.n_int, nrhs, st)));
+    HPS_CK(c, gemm<R>(c, cc.d_desc, 1, cc.Winv, 2LL * cc.n_int, c->ex_r, nrhs, nullptr, 0, c->ex_e, nrhs, 1.0, nullptr,
+                      cc.n_int, nrhs, nrhs));
+    HPS_CK(c, zero<R>(Vc, rows * nrhs, st));
+    HPS_CK(c, (scatter_rows<R, R>(Vc, static_cast<C*>(c->ex_e), cc.d_upos, cc.n_int, nrhs, st)));
+    return HPS_OK;
+  }
+  int rc = ensure_cg<R>(c, k, nrhs);
+  if (rc != HPS_OK) return rc;
+  C* V = static_cast<C*>(c->cg_V);
+  C* w = static_cast<C*>(c->cg_w);
+  C* W = static_cast<C*>(c->cg_W);
+  C* h1 = static_cast<C*>(c->cg_h1);
+  C* h2 = static_cast<C*>(c->cg_h2);
+  C* nrm = static_cast<C*>(c->cg_nrm);
+  C* part = static_cast<C*>(c->cg_part);
+  R* beta = static_cast<R*>(c->cg_beta);
+  R* floor = static_cast<R*>(c->cg_floor);
+  const long long vs = rows * nrhs;
+  const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+  // r_c = Pi rho_c (incoming coordinates of the coarse unknowns)
+  HPS_CK(c, swap_add<R>(w, nullptr, Vc, cc.d_cnb, rows, nrhs, st));
+  HPS_CK(c, bdot<R>(w, 0, 1, w, rows, nrhs, part, nrm, 0, st));
+  HPS_CK(c, beta_floor<R>(beta, floor, nrm, tol, nrhs, st));
+  HPS_CK(c, bscale<R>(V, w, nrm, nullptr, rows, nrhs, st));
+  for (int j = 0; j < k; ++j) {
+    C* Vj = V + j * vs;
+    HPS_CK(c, coarse_apply<R>(W, static_cast<const C*>(Sc.T), Vj, cc.d_mask, cc.off, Sc.nsub, Sc.n, nrhs, st));
+    HPS_CK(c, swap_add<R>(w, Vj, W, cc.d_cnb, rows, nrhs, st));
+    HPS_CK(c, bdot<R>(V, vs, j + 1, w, rows, nrhs, part, h1, 0, st));
+    HPS_CK(c, (bupdate<R, R>(w, V, vs, j + 1, h1, rows, nrhs, R(-1), st)));
+    HPS_CK(c, bdot<R>(V, vs, j + 1, w, rows, nrhs, part, h2, 0, st));
+    HPS_CK(c, (bupdate<R, R>(w, V, vs, j + 1, h2, rows, nrhs, R(-1), st)));
+    HPS_CK(c, bdot<R>(w, 0, 1, w, rows, nrhs, part, nrm, 0, st));
+    HPS_CK(c, hstore<R>(static_cast<C*>(c->cg_H), h1, h2, nrm, j, k, nrhs, st));
+    HPS_CK(c, bscale<R>(V + (j + 1) * vs, w, nrm, floor, rows, nrhs, st));
+  }
+  HPS_CK(c, lsq<R>(static_cast<C*>(c->cg_H), beta, floor, static_cast<C*>(c->cg_y), static_cast<C*>(c->cg_g),
+                   static_cast<R*>(c->cg_c), static_cast<C*>(c->cg_s), k, nrhs, st));
+  HPS_CK(c, zero<R>(Vc, rows * nrhs, st));
+  HPS_CK(c, (bupdate<R, R>(Vc, V, vs, k, static_cast<C*>(c->cg_y), rows, nrhs, R(1), st)));
+  return HPS_OK;
+}
+
+}  // namespace
+
+template <typename R>
+int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) {
+  using C = c_t<R>;
+  int rc = ensure_sweep_buffers(c, nrhs);
+  if (rc != HPS_OK) return rc;
+  cudaStream_t st = c->stream;
+  const Stage& S0 = c->stages[0];
+  HPS_CK(c, (gather_rows<double, R>(static_cast<C*>(S0.vec), rho_es, S0.d_es, (long long)S0.nsub * S0.n, nrhs, st)));
+  for (int l = 1; l <= c->L_exact; ++l) {
+    const Level& Lv = c->levels[l];
+    const Stage& P0 = c->stages[l - 1];
+    const Stage& P1 = c->stages[l];
+    const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
+    const GemmDesc* sd = Lv.d_sdesc;
+    const void* T0 = P0.T;
+    void* v0 = P0.vec;
+    HPS_CK(c, gemm<R>(c, sd + UP1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + UP2 * NP, NP, Lv.W, 2 * m, c->sw_tmp, nrhs, nullptr, 0, c->sw_zt, nrhs, 1.0, nullptr, m,
+                      nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + UP3 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, c->sw_zt, nrhs, -1.0, nullptr, m, nrhs,
+                      nrhs));
+    HPS_CK(c, gemm<R>(c, sd + UP4 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, P1.vec, nrhs, -1.0, Lv.d_dst, p, nrhs,
+                      nrhs));
+    HPS_CK(c, gemm<R>(c, sd + UP5 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, P1.vec, nrhs, -1.0, Lv.d_dst, p, nrhs,
+                      nrhs));
+  }
+  rc = coarse_solve<R>(c, nrhs, k);
+  if (rc != HPS_OK) return rc;
+  for (int l = c->L_exact; l >= 1; --l) {
+    const Level& Lv = c->levels[l];
+    const Stage& P0 = c->stages[l - 1];
+    const Stage& P1 = c->stages[l];
+    const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
+    const GemmDesc* sd = Lv.d_sdesc;
+    const void* T0 = P0.T;
+    void* v0 = P0.vec;
+    HPS_CK(c, (scatter_rows<R, R>(static_cast<C*>(v0), static_cast<const C*>(P1.vec), Lv.d_up,
+                                  (long long)P1.nsub * P1.n, nrhs, st)));
+    HPS_CK(c, gemm<R>(c, sd + DN1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + DN2 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + DN3 * NP, NP, T0, n, c->sw_tmp2, nrhs, c->sw_tmp2, nrhs, c->sw_tmp, nrhs, -1.0, nullptr,
+                      m, nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + DN4 * NP, NP, Lv.W, 2 * m, c->sw_tmp, nrhs, nullptr, 0, v0, nrhs, 1.0, nullptr, m, nrhs,
+                      nrhs));
+    HPS_CK(c, gemm<R>(c, sd + DN5 * NP, NP, T0, n, v0, nrhs, c->sw_tmp2, nrhs, v0, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+  }
+  HPS_CK(c, (scatter_rows<R, double>(z_es, static_cast<const C*>(S0.vec), S0.d_es, (long long)S0.nsub * S0.n, nrhs,
+                                     st)));
+  return HPS_OK;
+}
+
+template int mg_apply<double>(hps_ctx*, const double2*, double2*, int, int);
+template int mg_apply<float>(hps_ctx*, const double2*, double2*, int, int);
+
+}  // namespace hps
+
+namespace hps {
+void subdomain_natural(const hps_ctx* c, int stage, int sub, std::vector<int>& out) {
+  const Stage& S = c->stages[stage];
+  natural_es(c, sub % S.gx, sub / S.gx, S.a, S.b, out);
+}
+}  // namespace hps

@@ -1,0 +1,516 @@
+// Skeleton-level kernels (section 3.2): the FP64 matvec with M = I + Pi T in
+// element-side layout, RHS assembly from boundary data, layout gathers and
+// scatters (with precision conversion), the coarse-level operator of the
+// multigrid hierarchy (section 4.3), and block-vector Krylov primitives.
+//
+// Layouts.  A block vector holds `nrhs` columns, stored row-major
+// [rows][nrhs] (right-hand side fastest).  Element-side ("ES") rows are
+// p = (e*4 + side)*q + k.  Residual-like vectors are kept in "outgoing"
+// coordinates rho_p = r_{pi(p)} (the equation owned by the outgoing relation
+// on side p) and solution-like vectors in "incoming" coordinates, so that
+// the outer matvec reads  (Pi M g)_p = g_{nb(p)} + (T_e g_e)_p  per element.
+#include "common.cuh"
+#include "skel.cuh"
+
+namespace hps {
+
+namespace {
+constexpr int NT = 256;
+
+inline int nblocks(long long work, int per = NT, int cap = 1 << 20) {
+  long long b = (work + per - 1) / per;
+  if (b < 1) b = 1;
+  return (int)(b > cap ? cap : b);
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Outer matvec:  y_p = [ x_{nb(p)} + sum_b T_e[a][b] x_{e,b} ]  (nb(p) >= 0), 0 otherwise;
+// with c0 != null: y = c0 - that  (residual form).
+// One block per element, x_e staged in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) es_matvec_kernel(const double2* __restrict__ T, const int* __restrict__ nbr,
+                                                       const double2* __restrict__ x, const double2* __restrict__ c0,
+                                                       double2* __restrict__ y, int E, int nb, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* xs = reinterpret_cast<double2*>(smem_raw);  // [nb][nrhs]
+  for (int e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();
+    const long long base = (long long)e * nb;
+    for (int l = threadIdx.x; l < nb * nrhs; l += NT) xs[l] = x[base * nrhs + l];
+    __syncthreads();
+    const double2* Te = T + (long long)e * nb * nb;
+    for (int l = threadIdx.x; l < nb * nrhs; l += NT) {
+      const int a = l / nrhs, r = l % nrhs;
+      const long long p = base + a;
+      const int q = nbr[p];
+      double2 out = make_double2(0.0, 0.0);
+      if (q >= 0) {
+        double2 acc = x[(long long)q * nrhs + r];
+        const double2* Tr = Te + (long long)a * nb;
+        for (int b = 0; b < nb; ++b) cfma(acc, Tr[b], xs[b * nrhs + r]);
+        out = acc;
+        if (c0) out = csub(c0[p * nrhs + r], acc);
+      } else if (c0) {
+        out = make_double2(0.0, 0.0);
+      }
+      y[p * nrhs + r] = out;
+    }
+  }
+}
+
+cudaError_t es_matvec(const double2* T, const int* nbr, const double2* x, const double2* c0, double2* y, int E,
+                      int nb, int nrhs, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(double2) * (size_t)nb * nrhs;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(es_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  es_matvec_kernel<<<grid, NT, smem, s>>>(T, nbr, x, c0, y, E, nb, nrhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// RHS in outgoing coordinates: rho_p = -sum_{b on the boundary} T_e[a][b] t_{bdry(e,b)}
+// for interior p (nb(p) >= 0), 0 otherwise.  t is [n_bdry][nrhs].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) es_rhs_kernel(const double2* __restrict__ T, const int* __restrict__ nbr,
+                                                    const int* __restrict__ bdry, const double2* __restrict__ t,
+                                                    double2* __restrict__ rho, int E, int nb, int nrhs) {
+  for (int e = blockIdx.x; e < E; e += gridDim.x) {
+    const long long base = (long long)e * nb;
+    const double2* Te = T + (long long)e * nb * nb;
+    for (int l = threadIdx.x; l < nb * nrhs; l += NT) {
+      const int a = l / nrhs, r = l % nrhs;
+      const long long p = base + a;
+      double2 acc = make_double2(0.0, 0.0);
+      if (nbr[p] >= 0) {
+        for (int b = 0; b < nb; ++b) {
+          const int bi = bdry[base + b];
+          if (bi >= 0) cfma(acc, Te[(long long)a * nb + b], t[(long long)bi * nrhs + r]);
+        }
+      }
+      rho[p * nrhs + r] = make_double2(-acc.x, -acc.y);
+    }
+  }
+}
+
+cudaError_t es_rhs(const double2* T, const int* nbr, const int* bdry, const double2* t, double2* rho, int E, int nb,
+                   int nrhs, int grid, cudaStream_t s) {
+  es_rhs_kernel<<<grid, NT, 0, s>>>(T, nbr, bdry, t, rho, E, nb, nrhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Layout changes.
+// ---------------------------------------------------------------------------
+template <typename RS, typename RD>
+__global__ void gather_rows_kernel(c_t<RD>* __restrict__ dst, const c_t<RS>* __restrict__ src, const int* __restrict__ map,
+                                   long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map[row];
+    dst[l] = m >= 0 ? cvt<RD, RS>(src[(long long)m * nrhs + r]) : czero<RD>();
+  }
+}
+
+template <typename RS, typename RD>
+__global__ void scatter_rows_kernel(c_t<RD>* __restrict__ dst, const c_t<RS>* __restrict__ src, const int* __restrict__ map,
+                                    long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map[row];
+    if (m >= 0) dst[(long long)m * nrhs + r] = cvt<RD, RS>(src[l]);
+  }
+}
+
+template <typename RS, typename RD>
+cudaError_t gather_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  gather_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  return cudaGetLastError();
+}
+template <typename RS, typename RD>
+cudaError_t scatter_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  scatter_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  return cudaGetLastError();
+}
+
+// user [nrhs][n] <-> rows [rows][nrhs] through map (row -> index in n, -1 = none)
+__global__ void user_to_rows_kernel(double2* __restrict__ dst, const double2* __restrict__ src, const int* __restrict__ map,
+                                    long long rows, int nrhs, long long n) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map ? map[row] : (int)row;
+    dst[l] = m >= 0 ? src[(long long)r * n + m] : make_double2(0.0, 0.0);
+  }
+}
+__global__ void rows_to_user_kernel(double2* __restrict__ dst, const double2* __restrict__ src, const int* __restrict__ map,
+                                    long long rows, int nrhs, long long n) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map ? map[row] : (int)row;
+    if (m >= 0) dst[(long long)r * n + m] = src[l];
+  }
+}
+cudaError_t user_to_rows(double2* dst, const double2* src, const int* map, long long rows, int nrhs, long long n,
+                         cudaStream_t s) {
+  user_to_rows_kernel<<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs, n);
+  return cudaGetLastError();
+}
+cudaError_t rows_to_user(double2* dst, const double2* src, const int* map, long long rows, int nrhs, long long n,
+                         cudaStream_t s) {
+  rows_to_user_kernel<<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs, n);
+  return cudaGetLastError();
+}
+
+// dst[s][i][j] = src[s][map[s*n+i]][map[s*n+j]] (n x n blocks), with conversion.
+template <typename RS, typename RD>
+__global__ void permute_blocks_kernel(c_t<RD>* __restrict__ dst, const c_t<RS>* __restrict__ src, const int* __restrict__ map,
+                                      int nsub, int n) {
+  const long long tot = (long long)nsub * n * n;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long s = l / ((long long)n * n);
+    const int rem = (int)(l % ((long long)n * n));
+    const int i = rem / n, j = rem % n;
+    const int si = map[s * n + i], sj = map[s * n + j];
+    dst[l] = cvt<RD, RS>(src[(s * n + si) * (long long)n + sj]);
+  }
+}
+template <typename RS, typename RD>
+cudaError_t permute_blocks(c_t<RD>* dst, const c_t<RS>* src, const int* map, int nsub, int n, cudaStream_t s) {
+  permute_blocks_kernel<RS, RD><<<nblocks((long long)nsub * n * n, NT, 16384), NT, 0, s>>>(dst, src, map, nsub, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coarse level.  W_s = T_s g_s restricted to interior sides (side bit set in
+// mask[s]); sides are the contiguous ranges [off[0],off[1]) .. [off[3],off[4]).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(NT) coarse_apply_kernel(c_t<R>* __restrict__ W, const c_t<R>* __restrict__ T,
+                                                          const c_t<R>* __restrict__ g, const int* __restrict__ mask,
+                                                          int4 off03, int off4, int n, int nrhs, int rows_per_block) {
+  const int s = blockIdx.y;
+  const int msk = mask[s];
+  const int off[5] = {off03.x, off03.y, off03.z, off03.w, off4};
+  const int r0 = blockIdx.x * rows_per_block;
+  const c_t<R>* Ts = T + (long long)s * n * n;
+  const c_t<R>* gs = g + (long long)s * n * nrhs;
+  for (int l = threadIdx.x; l < rows_per_block * nrhs; l += NT) {
+    const int i = r0 + l / nrhs, r = l % nrhs;
+    if (i >= n) continue;
+    int side_i = 0;
+    while (side_i < 3 && i >= off[side_i + 1]) ++side_i;
+    c_t<R> acc = czero<R>();
+    if ((msk >> side_i) & 1) {
+      const c_t<R>* Tr = Ts + (long long)i * n;
+      for (int sd = 0; sd < 4; ++sd) {
+        if (!((msk >> sd) & 1)) continue;
+        for (int j = off[sd]; j < off[sd + 1]; ++j) cfma(acc, Tr[j], gs[(long long)j * nrhs + r]);
+      }
+    }
+    W[((long long)s * n + i) * nrhs + r] = acc;
+  }
+}
+
+template <typename R>
+cudaError_t coarse_apply(c_t<R>* W, const c_t<R>* T, const c_t<R>* g, const int* mask, const int* off, int nsub, int n,
+                         int nrhs, cudaStream_t s) {
+  const int rpb = NT / nrhs > 0 ? (NT / nrhs) : 1;
+  dim3 grid((n + rpb - 1) / rpb, nsub);
+  coarse_apply_kernel<R><<<grid, NT, 0, s>>>(W, T, g, mask, make_int4(off[0], off[1], off[2], off[3]), off[4], n, nrhs,
+                                             rpb);
+  return cudaGetLastError();
+}
+
+// out_p = nb(p) >= 0 ? (a ? a_p : 0) + b_{nb(p)} : 0
+template <typename R>
+__global__ void swap_add_kernel(c_t<R>* __restrict__ out, const c_t<R>* __restrict__ a, const c_t<R>* __restrict__ b,
+                                const int* __restrict__ nbr, long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = nbr[row];
+    c_t<R> v = czero<R>();
+    if (m >= 0) {
+      v = b[(long long)m * nrhs + r];
+      if (a) v = cadd(v, a[l]);
+    }
+    out[l] = v;
+  }
+}
+template <typename R>
+cudaError_t swap_add(c_t<R>* out, const c_t<R>* a, const c_t<R>* b, const int* nbr, long long rows, int nrhs,
+                     cudaStream_t s) {
+  swap_add_kernel<R><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(out, a, b, nbr, rows, nrhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Block-vector Krylov primitives.  V holds nvec vectors of `rows` rows, vector
+// i at V + i*vstride.  Reductions are two-pass and deterministic.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(NT) bdot_partial_kernel(const c_t<R>* __restrict__ V, long long vstride, int nvec,
+                                                          const c_t<R>* __restrict__ w, long long rows, int nrhs,
+                                                          int rpad, c_t<R>* __restrict__ partial, long long chunk) {
+  __shared__ c_t<R> red[NT];
+  const int r = threadIdx.x % rpad, lrow = threadIdx.x / rpad, rper = NT / rpad;
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < rows ? lo + chunk : rows;
+  for (int i = 0; i < nvec; ++i) {
+    c_t<R> acc = czero<R>();
+    if (r < nrhs) {
+      const c_t<R>* Vi = V + i * vstride;
+      for (long long row = lo + lrow; row < hi; row += rper)
+        cfma_conj(acc, Vi[row * nrhs + r], w[row * nrhs + r]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s2 = rper / 2; s2 > 0; s2 >>= 1) {
+      if (lrow < s2) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + s2 * rpad]);
+      __syncthreads();
+    }
+    if (lrow == 0 && r < nrhs) partial[((long long)blockIdx.x * nvec + i) * nrhs + r] = red[r];
+    __syncthreads();
+  }
+}
+
+template <typename R>
+__global__ void bdot_final_kernel(const c_t<R>* __restrict__ partial, int nblk, int nvec, int nrhs,
+                                  c_t<R>* __restrict__ out, int accumulate) {
+  const int l = blockIdx.x * NT + threadIdx.x;
+  if (l >= nvec * nrhs) return;
+  c_t<R> acc = czero<R>();
+  for (int b = 0; b < nblk; ++b) acc = cadd(acc, partial[(long long)b * nvec * nrhs + l]);
+  out[l] = accumulate ? cadd(out[l], acc) : acc;
+}
+
+int bdot_blocks(long long rows) {
+  long long b = (rows + 511) / 512;
+  if (b < 1) b = 1;
+  return (int)(b > 512 ? 512 : b);
+}
+
+template <typename R>
+cudaError_t bdot(const c_t<R>* V, long long vstride, int nvec, const c_t<R>* w, long long rows, int nrhs,
+                 c_t<R>* partial, c_t<R>* out, int accumulate, cudaStream_t s) {
+  if (nrhs > NT || nvec <= 0) return cudaErrorInvalidValue;
+  int rpad = 1;
+  while (rpad < nrhs) rpad <<= 1;
+  const int nblk = bdot_blocks(rows);
+  const long long chunk = (rows + nblk - 1) / nblk;
+  bdot_partial_kernel<R><<<nblk, NT, 0, s>>>(V, vstride, nvec, w, rows, nrhs, rpad, partial, chunk);
+  bdot_final_kernel<R><<<(nvec * nrhs + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nvec, nrhs, out, accumulate);
+  return cudaGetLastError();
+}
+
+// w += sign * sum_i V_i h_i   (h: [nvec][nrhs])
+template <typename R, typename RH>
+__global__ void bupdate_kernel(c_t<R>* __restrict__ w, const c_t<R>* __restrict__ V, long long vstride, int nvec,
+                               const c_t<RH>* __restrict__ h, long long rows, int nrhs, R sign) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int r = (int)(l % nrhs);
+    c_t<R> acc = czero<R>();
+    for (int i = 0; i < nvec; ++i) cfma(acc, V[i * vstride + l], cvt<R, RH>(h[i * nrhs + r]));
+    w[l] = cadd(w[l], cscale(acc, sign));
+  }
+}
+template <typename R, typename RH>
+cudaError_t bupdate(c_t<R>* w, const c_t<R>* V, long long vstride, int nvec, const c_t<RH>* h, long long rows, int nrhs,
+                    R sign, cudaStream_t s) {
+  if (nvec <= 0) return cudaSuccess;
+  bupdate_kernel<R, RH><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(w, V, vstride, nvec, h, rows, nrhs, sign);
+  return cudaGetLastError();
+}
+
+// out = w / nrm[r] where nrm[r] = sqrt(re dots[r]) > floor[r] (floor may be null), else 0;
+// also stores nrm into nrm_out when non-null.
+template <typename R>
+__global__ void bscale_kernel(c_t<R>* __restrict__ out, const c_t<R>* __restrict__ w, const c_t<R>* __restrict__ dots,
+                              const R* __restrict__ floor, long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int r = (int)(l % nrhs);
+    const R nrm = sqrt(dots[r].x > R(0) ? dots[r].x : R(0));
+    const bool ok = nrm > (floor ? floor[r] : R(0));
+    out[l] = ok ? cscale(w[l], R(1) / nrm) : czero<R>();
+  }
+}
+template <typename R>
+cudaError_t bscale(c_t<R>* out, const c_t<R>* w, const c_t<R>* dots, const R* floor, long long rows, int nrhs,
+                   cudaStream_t s) {
+  bscale_kernel<R><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(out, w, dots, floor, rows, nrhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coarse GMRES bookkeeping on the device (one thread per right-hand side).
+// ---------------------------------------------------------------------------
+// H[r][i][j] (ldh = k+1 rows, column j): store column j = h1 + h2 (i <= j) and
+// the subdiagonal sqrt(re nrm2); beta[r] from the first norm.
+template <typename R>
+__global__ void hstore_kernel(c_t<R>* __restrict__ H, const c_t<R>* __restrict__ h1, const c_t<R>* __restrict__ h2,
+                              const c_t<R>* __restrict__ nrm2, int j, int k, int nrhs) {
+  const int r = blockIdx.x * NT + threadIdx.x;
+  if (r >= nrhs) return;
+  c_t<R>* Hr = H + (long long)r * (k + 1) * k;
+  for (int i = 0; i <= j; ++i) Hr[i * k + j] = cadd(h1[i * nrhs + r], h2[i * nrhs + r]);
+  const R nn = nrm2[r].x > R(0) ? sqrt(nrm2[r].x) : R(0);
+  Hr[(j + 1) * k + j] = mk<R>(nn, R(0));
+}
+template <typename R>
+cudaError_t hstore(c_t<R>* H, const c_t<R>* h1, const c_t<R>* h2, const c_t<R>* nrm2, int j, int k, int nrhs,
+                   cudaStream_t s) {
+  hstore_kernel<R><<<(nrhs + NT - 1) / NT, NT, 0, s>>>(H, h1, h2, nrm2, j, k, nrhs);
+  return cudaGetLastError();
+}
+
+// beta[r] = sqrt(re nrm2[r]); floor[r] = tol * beta[r]
+template <typename R>
+__global__ void beta_kernel(R* __restrict__ beta, R* __restrict__ floor, const c_t<R>* __restrict__ nrm2, R tol, int nrhs) {
+  const int r = blockIdx.x * NT + threadIdx.x;
+  if (r >= nrhs) return;
+  const R b = nrm2[r].x > R(0) ? sqrt(nrm2[r].x) : R(0);
+  beta[r] = b;
+  floor[r] = tol * b;
+}
+template <typename R>
+cudaError_t beta_floor(R* beta, R* floor, const c_t<R>* nrm2, R tol, int nrhs, cudaStream_t s) {
+  beta_kernel<R><<<(nrhs + NT - 1) / NT, NT, 0, s>>>(beta, floor, nrm2, tol, nrhs);
+  return cudaGetLastError();
+}
+
+// Least squares min || beta e1 - Hbar y || by complex Givens rotations
+//   G = [[c, s], [-conj(s), c]],  c = |a| / nu,  s = (a / |a|) (b / nu),  nu = sqrt(|a|^2 + b^2),
+// which maps (a, b) (b real >= 0, the Arnoldi subdiagonal) to (a nu / |a|, 0).
+// Stops after the first column whose subdiagonal is <= floor[r] (happy breakdown).
+// H: [nrhs][k+1][k]; y: [k][nrhs]; workspaces g [nrhs][k+1], cs [nrhs][k], sn [nrhs][k].
+template <typename R>
+__global__ void lsq_kernel(c_t<R>* __restrict__ H, const R* __restrict__ beta, const R* __restrict__ floor,
+                           c_t<R>* __restrict__ y, c_t<R>* __restrict__ gws, R* __restrict__ cws,
+                           c_t<R>* __restrict__ sws, int k, int nrhs) {
+  const int r = blockIdx.x * NT + threadIdx.x;
+  if (r >= nrhs) return;
+  c_t<R>* Hr = H + (long long)r * (k + 1) * k;
+  c_t<R>* g = gws + (long long)r * (k + 1);
+  R* cr = cws + (long long)r * k;
+  c_t<R>* sr = sws + (long long)r * k;
+  for (int i = 0; i <= k; ++i) g[i] = czero<R>();
+  g[0] = mk<R>(beta[r], R(0));
+  int steps = k;
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < j; ++i) {
+      const c_t<R> a = Hr[i * k + j], b = Hr[(i + 1) * k + j];
+      Hr[i * k + j] = cadd(cscale(a, cr[i]), cmul(sr[i], b));
+      Hr[(i + 1) * k + j] = csub(cscale(b, cr[i]), cmul(mk<R>(sr[i].x, -sr[i].y), a));
+    }
+    const c_t<R> a = Hr[j * k + j];
+    const R b = Hr[(j + 1) * k + j].x;
+    const R aa = sqrt(a.x * a.x + a.y * a.y);
+    R c;
+    c_t<R> sn;
+    if (b == R(0)) {
+      c = R(1);
+      sn = czero<R>();
+    } else if (aa == R(0)) {
+      c = R(0);
+      sn = mk<R>(R(1), R(0));
+    } else {
+      const R nu = sqrt(aa * aa + b * b);
+      c = aa / nu;
+      sn = mk<R>(a.x / aa * (b / nu), a.y / aa * (b / nu));
+    }
+    cr[j] = c;
+    sr[j] = sn;
+    Hr[j * k + j] = cadd(cscale(a, c), cscale(sn, b));
+    Hr[(j + 1) * k + j] = czero<R>();
+    const c_t<R> gj = g[j];
+    g[j] = cscale(gj, c);
+    g[j + 1] = cmul(mk<R>(-sn.x, sn.y), gj);  // -conj(s) g_j
+    if (b <= floor[r]) {
+      steps = j + 1;
+      break;
+    }
+  }
+  for (int j = steps - 1; j >= 0; --j) {
+    c_t<R> v = g[j];
+    for (int i = j + 1; i < steps; ++i) v = csub(v, cmul(Hr[j * k + i], y[i * nrhs + r]));
+    y[j * nrhs + r] = cmul(v, cinv(Hr[j * k + j]));
+  }
+  for (int j = steps; j < k; ++j) y[j * nrhs + r] = czero<R>();
+}
+template <typename R>
+cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws, R* cws, c_t<R>* sws, int k,
+                int nrhs, cudaStream_t s) {
+  lsq_kernel<R><<<(nrhs + NT - 1) / NT, NT, 0, s>>>(H, beta, floor, y, gws, cws, sws, k, nrhs);
+  return cudaGetLastError();
+}
+
+// fill
+template <typename R>
+__global__ void zero_kernel(c_t<R>* __restrict__ x, long long n) {
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT) x[l] = czero<R>();
+}
+template <typename R>
+cudaError_t zero(c_t<R>* x, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  zero_kernel<R><<<nblocks(n, NT, 8192), NT, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+// W = [I | I] for nmat matrices of m rows (leading dimension 2m)
+template <typename R>
+__global__ void eye2_kernel(c_t<R>* __restrict__ W, int m, int nmat) {
+  const long long tot = (long long)nmat * m * 2 * m;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int rem = (int)(l % (2LL * m * m));
+    const int i = rem / (2 * m), j = rem % (2 * m);
+    W[l] = mk<R>((j == i || j == i + m) ? R(1) : R(0), R(0));
+  }
+}
+template <typename R>
+cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s) {
+  eye2_kernel<R><<<nblocks((long long)nmat * m * 2 * m, NT, 16384), NT, 0, s>>>(W, m, nmat);
+  return cudaGetLastError();
+}
+
+#define HPS_INST_R(R)                                                                                                   \
+  template cudaError_t coarse_apply<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const int*, const int*, int, int, int,   \
+                                       cudaStream_t);                                                                   \
+  template cudaError_t swap_add<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const int*, long long, int, cudaStream_t);   \
+  template cudaError_t bdot<R>(const c_t<R>*, long long, int, const c_t<R>*, long long, int, c_t<R>*, c_t<R>*, int,     \
+                               cudaStream_t);                                                                           \
+  template cudaError_t bscale<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const R*, long long, int, cudaStream_t);       \
+  template cudaError_t hstore<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const c_t<R>*, int, int, int, cudaStream_t);  \
+  template cudaError_t beta_floor<R>(R*, R*, const c_t<R>*, R, int, cudaStream_t);                                      \
+  template cudaError_t lsq<R>(c_t<R>*, const R*, const R*, c_t<R>*, c_t<R>*, R*, c_t<R>*, int, int,        \
+                              cudaStream_t);                  \
+  template cudaError_t zero<R>(c_t<R>*, long long, cudaStream_t);                                                       \
+  template cudaError_t eye2<R>(c_t<R>*, int, int, cudaStream_t);
+
+HPS_INST_R(double)
+HPS_INST_R(float)
+
+template cudaError_t bupdate<double, double>(double2*, const double2*, long long, int, const double2*, long long, int,
+                                             double, cudaStream_t);
+template cudaError_t bupdate<float, float>(float2*, const float2*, long long, int, const float2*, long long, int, float,
+                                           cudaStream_t);
+template cudaError_t gather_rows<double, double>(double2*, const double2*, const int*, long long, int, cudaStream_t);
+template cudaError_t gather_rows<double, float>(float2*, const double2*, const int*, long long, int, cudaStream_t);
+template cudaError_t gather_rows<float, float>(float2*, const float2*, const int*, long long, int, cudaStream_t);
+template cudaError_t scatter_rows<double, double>(double2*, const double2*, const int*, long long, int, cudaStream_t);
+template cudaError_t scatter_rows<float, double>(double2*, const float2*, const int*, long long, int, cudaStream_t);
+template cudaError_t scatter_rows<float, float>(float2*, const float2*, const int*, long long, int, cudaStream_t);
+template cudaError_t permute_blocks<double, double>(double2*, const double2*, const int*, int, int, cudaStream_t);
+template cudaError_t permute_blocks<double, float>(float2*, const double2*, const int*, int, int, cudaStream_t);
+
+}  // namespace hps

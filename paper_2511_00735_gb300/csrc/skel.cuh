@@ -1,0 +1,73 @@
+// Declarations of the leaf, skeleton, layout and Krylov kernel launchers.
+#pragma once
+
+#include "common.cuh"
+
+namespace hps {
+
+// leaf.cu
+struct LeafParams {
+  int N, q, ni, nb, E, cw;
+  double h, eta;
+  const double* c;    // [E][(N+1)^2]  c = kappa^2 (1 - b) at the element nodes
+  const double* Dh;   // [(N+1)^2] reference differentiation matrix on [-1, 1]
+  const double* Kh;   // [(N+1)^2] reference stiffness D^T W D
+  const double* wh;   // [N+1] reference GLL weights
+  double* Ascr;       // [gridDim.x][nb][nb] per-CTA scratch for A
+  double2* T;         // [E][nb][nb] output, side order l, r, b, t
+  int* flag;          // set to e+1 when a Cholesky pivot is not positive
+};
+size_t leaf_smem_bytes(int N, int cw);
+cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s);
+
+// skel.cu -- FP64 element-side operators
+cudaError_t es_matvec(const double2* T, const int* nbr, const double2* x, const double2* c0, double2* y, int E,
+                      int nb, int nrhs, int grid, cudaStream_t s);
+cudaError_t es_rhs(const double2* T, const int* nbr, const int* bdry, const double2* t, double2* rho, int E, int nb,
+                   int nrhs, int grid, cudaStream_t s);
+
+// layout changes (RS -> RD conversion)
+template <typename RS, typename RD>
+cudaError_t gather_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s);
+template <typename RS, typename RD>
+cudaError_t scatter_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s);
+cudaError_t user_to_rows(double2* dst, const double2* src, const int* map, long long rows, int nrhs, long long n,
+                         cudaStream_t s);
+cudaError_t rows_to_user(double2* dst, const double2* src, const int* map, long long rows, int nrhs, long long n,
+                         cudaStream_t s);
+template <typename RS, typename RD>
+cudaError_t permute_blocks(c_t<RD>* dst, const c_t<RS>* src, const int* map, int nsub, int n, cudaStream_t s);
+
+// coarse level
+template <typename R>
+cudaError_t coarse_apply(c_t<R>* W, const c_t<R>* T, const c_t<R>* g, const int* mask, const int* off, int nsub, int n,
+                         int nrhs, cudaStream_t s);
+template <typename R>
+cudaError_t swap_add(c_t<R>* out, const c_t<R>* a, const c_t<R>* b, const int* nbr, long long rows, int nrhs,
+                     cudaStream_t s);
+
+// block-vector Krylov primitives
+int bdot_blocks(long long rows);
+template <typename R>
+cudaError_t bdot(const c_t<R>* V, long long vstride, int nvec, const c_t<R>* w, long long rows, int nrhs,
+                 c_t<R>* partial, c_t<R>* out, int accumulate, cudaStream_t s);
+template <typename R, typename RH>
+cudaError_t bupdate(c_t<R>* w, const c_t<R>* V, long long vstride, int nvec, const c_t<RH>* h, long long rows, int nrhs,
+                    R sign, cudaStream_t s);
+template <typename R>
+cudaError_t bscale(c_t<R>* out, const c_t<R>* w, const c_t<R>* dots, const R* floor, long long rows, int nrhs,
+                   cudaStream_t s);
+template <typename R>
+cudaError_t hstore(c_t<R>* H, const c_t<R>* h1, const c_t<R>* h2, const c_t<R>* nrm2, int j, int k, int nrhs,
+                   cudaStream_t s);
+template <typename R>
+cudaError_t beta_floor(R* beta, R* floor, const c_t<R>* nrm2, R tol, int nrhs, cudaStream_t s);
+template <typename R>
+cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws, R* cws, c_t<R>* sws, int k,
+                int nrhs, cudaStream_t s);
+template <typename R>
+cudaError_t zero(c_t<R>* x, long long n, cudaStream_t s);
+template <typename R>
+cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s);
+
+}  // namespace hps

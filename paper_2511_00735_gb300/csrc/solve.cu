@@ -1,0 +1,377 @@
+// C ABI, second half: merge levels, skeleton RHS / matvec / preconditioner in
+// the skeleton ("face") order, and the FP64 flexible GMRES (section 4.3).
+//
+// FGMRES runs on the element-side layout with residual-like vectors (the
+// Arnoldi basis V) in outgoing coordinates rho = Pi r and solution-like
+// vectors (Z, x) in incoming coordinates.  Pi is a permutation, so every inner
+// product and norm equals the one of the skeleton-order vectors and the
+// iterates are those of FGMRES on M g = RHS.  Classical Gram-Schmidt with one
+// re-orthogonalisation pass; Givens rotations and the convergence test on the
+// host (one small device-to-host copy per iteration).
+#include <algorithm>
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "ctx.h"
+#include "skel.cuh"
+
+namespace hps {
+
+void subdomain_natural(const hps_ctx* c, int stage, int sub, std::vector<int>& out);
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_pv(hps_ctx* c, int nrhs) {
+  if (nrhs <= c->pv_nrhs) return HPS_OK;
+  dev_free(c, c->pv_in);
+  dev_free(c, c->pv_out);
+  const size_t rows = std::max<long long>(c->n_es, c->n_bdry);
+  c->pv_in = static_cast<double2*>(dev_alloc(c, sizeof(double2) * rows * nrhs));
+  c->pv_out = static_cast<double2*>(dev_alloc(c, sizeof(double2) * rows * nrhs));
+  if (!c->pv_in || !c->pv_out) return fail(c, HPS_ENOMEM, "staging vectors");
+  c->pv_nrhs = nrhs;
+  return HPS_OK;
+}
+
+int ensure_fg(hps_ctx* c, int restart, int nrhs) {
+  if (restart <= c->fg_restart && nrhs <= c->fg_nrhs) return HPS_OK;
+  restart = std::max(restart, c->fg_restart);
+  nrhs = std::max(nrhs, c->fg_nrhs);
+  dev_free(c, c->fg_V); dev_free(c, c->fg_Z); dev_free(c, c->fg_x); dev_free(c, c->fg_w);
+  dev_free(c, c->fg_rhs); dev_free(c, c->fg_t); dev_free(c, c->fg_h); dev_free(c, c->fg_part);
+  dev_free(c, c->fg_y); dev_free(c, c->fg_floor);
+  if (c->pin_h) cudaFreeHost(c->pin_h);
+  if (c->pin_y) cudaFreeHost(c->pin_y);
+  if (c->pin_floor) cudaFreeHost(c->pin_floor);
+  c->pin_h = c->pin_y = nullptr;
+  c->pin_floor = nullptr;
+  const size_t vs = (size_t)c->n_es * nrhs;
+  c->fg_V = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * (restart + 1)));
+  c->fg_Z = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * restart));
+  c->fg_x = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
+  c->fg_w = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
+  c->fg_rhs = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
+  c->fg_t = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->n_bdry * nrhs));
+  const size_t hsz = (size_t)(2 * (restart + 1) + 1) * nrhs;
+  c->fg_h = static_cast<double2*>(dev_alloc(c, sizeof(double2) * hsz));
+  c->fg_part = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)bdot_blocks(c->n_es) * (restart + 1) * nrhs));
+  c->fg_y = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)restart * nrhs));
+  c->fg_floor = static_cast<double*>(dev_alloc(c, sizeof(double) * nrhs));
+  if (!c->fg_V || !c->fg_Z || !c->fg_x || !c->fg_w || !c->fg_rhs || !c->fg_t || !c->fg_h || !c->fg_part || !c->fg_y ||
+      !c->fg_floor)
+    return fail(c, HPS_ENOMEM, "FGMRES workspace");
+  if (cudaMallocHost(&c->pin_h, sizeof(double2) * hsz) != cudaSuccess ||
+      cudaMallocHost(&c->pin_y, sizeof(double2) * (size_t)restart * nrhs) != cudaSuccess ||
+      cudaMallocHost(&c->pin_floor, sizeof(double) * nrhs) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HPS_ENOMEM, "pinned host workspace");
+  }
+  c->fg_restart = restart;
+  c->fg_nrhs = nrhs;
+  return HPS_OK;
+}
+
+int precond(hps_ctx* c, const double2* v, double2* z, int nrhs, int k) {
+  if (k < 0) {
+    HPS_CK(c, swap_add<double>(z, nullptr, v, c->d_es_nb, c->n_es, nrhs, c->stream));
+    return HPS_OK;
+  }
+  return c->precision == HPS_FP64 ? mg_apply<double>(c, v, z, nrhs, k) : mg_apply<float>(c, v, z, nrhs, k);
+}
+
+using cd = std::complex<double>;
+
+}  // namespace
+}  // namespace hps
+
+using namespace hps;
+
+#define CHECK_CTX(c)                                                   \
+  do {                                                                 \
+    if (!(c)) return HPS_EINVAL;                                       \
+    cudaError_t e0_ = cudaSetDevice((c)->device);                      \
+    if (e0_ != cudaSuccess) return cuda_fail(c, e0_, "cudaSetDevice"); \
+  } while (0)
+
+extern "C" {
+
+int hps_merge_levels(hps_ctx* c, int L_exact, int exact_coarse) {
+  CHECK_CTX(c);
+  if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
+  if (L_exact < 0 || L_exact > c->L) return fail(c, HPS_EINVAL, "0 <= L_exact <= L");
+  return build_tree(c, L_exact, exact_coarse);
+}
+
+int hps_stage_T(hps_ctx* c, int stage, int sub, void* T_host) {
+  CHECK_CTX(c);
+  if (!c->have_tree) return fail(c, HPS_ENOTBUILT, "hps_merge_levels first");
+  if (stage < 0 || stage > c->L_exact || !T_host) return fail(c, HPS_EINVAL, "stage");
+  const Stage& S = c->stages[stage];
+  if (sub < 0 || sub >= S.nsub) return fail(c, HPS_EINVAL, "subdomain");
+  const int n = S.n;
+  std::vector<double2> out((size_t)n * n);
+  HPS_CK(c, cudaStreamSynchronize(c->stream));
+  if (c->precision == HPS_FP64) {
+    HPS_CK(c, cudaMemcpy(out.data(), static_cast<double2*>(S.T) + (size_t)sub * n * n, sizeof(double2) * n * n,
+                         cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float2> tmp((size_t)n * n);
+    HPS_CK(c, cudaMemcpy(tmp.data(), static_cast<float2*>(S.T) + (size_t)sub * n * n, sizeof(float2) * n * n,
+                         cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < tmp.size(); ++i) out[i] = make_double2(tmp[i].x, tmp[i].y);
+  }
+  std::vector<int> nat;
+  subdomain_natural(c, stage, sub, nat);
+  std::vector<int> pos(n);
+  for (int i = 0; i < n; ++i) {
+    const int e = S.es[(size_t)sub * n + i];
+    pos[i] = -1;
+    for (int j = 0; j < n; ++j)
+      if (nat[j] == e) pos[i] = j;
+    if (pos[i] < 0) return fail(c, HPS_ECUDA, "internal: stage order");
+  }
+  double2* dst = static_cast<double2*>(T_host);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) dst[(size_t)pos[i] * n + pos[j]] = out[(size_t)i * n + j];
+  return HPS_OK;
+}
+
+int hps_rhs(hps_ctx* c, const void* t, void* rhs, int nrhs) {
+  CHECK_CTX(c);
+  if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
+  if (!t || !rhs || nrhs < 1 || nrhs > 64) return fail(c, HPS_EINVAL, "pointers, 1 <= nrhs <= 64");
+  int rc = ensure_pv(c, nrhs);
+  if (rc) return rc;
+  HPS_CK(c, user_to_rows(c->pv_in, static_cast<const double2*>(t), nullptr, c->n_bdry, nrhs, c->n_bdry, c->stream));
+  HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->pv_in, c->pv_out, c->E, c->nb, nrhs,
+                   std::min(c->E, 8 * c->num_sms), c->stream));
+  HPS_CK(c, rows_to_user(static_cast<double2*>(rhs), c->pv_out, c->d_es_out, c->n_es, nrhs, c->n_skel, c->stream));
+  return HPS_OK;
+}
+
+int hps_skel_matvec(hps_ctx* c, const void* x, void* y, int nrhs) {
+  CHECK_CTX(c);
+  if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
+  if (!x || !y || nrhs < 1 || nrhs > 64) return fail(c, HPS_EINVAL, "pointers, 1 <= nrhs <= 64");
+  int rc = ensure_pv(c, nrhs);
+  if (rc) return rc;
+  HPS_CK(c, user_to_rows(c->pv_in, static_cast<const double2*>(x), c->d_es_in, c->n_es, nrhs, c->n_skel, c->stream));
+  HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->pv_in, nullptr, c->pv_out, c->E, c->nb, nrhs,
+                      std::min(c->E, 8 * c->num_sms), c->stream));
+  HPS_CK(c, rows_to_user(static_cast<double2*>(y), c->pv_out, c->d_es_out, c->n_es, nrhs, c->n_skel, c->stream));
+  return HPS_OK;
+}
+
+int hps_precond_apply(hps_ctx* c, const void* r, void* z, int nrhs, int inner_iters) {
+  CHECK_CTX(c);
+  if (!c->have_tree) return fail(c, HPS_ENOTBUILT, "hps_merge_levels first");
+  if (!r || !z || nrhs < 1 || nrhs > 64 || inner_iters < 0 || inner_iters > 60)
+    return fail(c, HPS_EINVAL, "pointers, 1 <= nrhs <= 64, 0 <= inner_iters <= 60");
+  int rc = ensure_pv(c, nrhs);
+  if (rc) return rc;
+  HPS_CK(c, user_to_rows(c->pv_in, static_cast<const double2*>(r), c->d_es_out, c->n_es, nrhs, c->n_skel, c->stream));
+  rc = precond(c, c->pv_in, c->pv_out, nrhs, inner_iters);
+  if (rc) return rc;
+  HPS_CK(c, rows_to_user(static_cast<double2*>(z), c->pv_out, c->d_es_in, c->n_es, nrhs, c->n_skel, c->stream));
+  return HPS_OK;
+}
+
+int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double tol, int inner_iters, int restart,
+                    int max_outer, void* g_out, hps_info* info) {
+  CHECK_CTX(c);
+  if (s) return fail(c, HPS_EUNSUPPORTED, "sources s != 0 are not handled by this build (pass NULL)");
+  if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
+  if (inner_iters >= 0 && !c->have_tree) return fail(c, HPS_ENOTBUILT, "hps_merge_levels first (or inner_iters < 0)");
+  if (!t || !g_out || nrhs < 1 || nrhs > 64 || !(tol > 0) || restart < 1 || restart > 200 || max_outer < 1 ||
+      inner_iters > 60)
+    return fail(c, HPS_EINVAL, "pointers, 1<=nrhs<=64, tol>0, 1<=restart<=200, max_outer>=1, inner_iters<=60");
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = ensure_fg(c, restart, nrhs);
+  if (rc) return rc;
+  rc = ensure_pv(c, nrhs);
+  if (rc) return rc;
+  cudaStream_t st = c->stream;
+  const long long n = c->n_es;
+  const long long vs = n * nrhs;
+  const int grid = std::min(c->E, 8 * c->num_sms);
+  // boundary data -> [n_bdry][nrhs]
+  const double2* t_dev = static_cast<const double2*>(t);
+  if (!is_device_ptr(t)) {
+    HPS_CK(c, cudaMemcpyAsync(c->pv_in, t, sizeof(double2) * (size_t)c->n_bdry * nrhs, cudaMemcpyHostToDevice, st));
+    t_dev = c->pv_in;
+  }
+  HPS_CK(c, user_to_rows(c->fg_t, t_dev, nullptr, c->n_bdry, nrhs, c->n_bdry, st));
+  HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->fg_t, c->fg_rhs, c->E, c->nb, nrhs, grid, st));
+  double2* hbuf = c->fg_h;
+  HPS_CK(c, bdot<double>(c->fg_rhs, 0, 1, c->fg_rhs, n, nrhs, c->fg_part, hbuf, 0, st));
+  HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+  HPS_CK(c, cudaStreamSynchronize(st));
+  const auto t1 = std::chrono::steady_clock::now();
+  std::vector<double> bnorm(nrhs);
+  for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(std::max(0.0, c->pin_h[r].x));
+  HPS_CK(c, zero<double>(c->fg_x, vs, st));
+  std::vector<int> its(nrhs, 0);
+  std::vector<char> done(nrhs, 0);
+  std::vector<cd> H((size_t)(restart + 1) * restart * nrhs), g((size_t)(restart + 1) * nrhs);
+  std::vector<double> cs((size_t)restart * nrhs);
+  std::vector<cd> sn((size_t)restart * nrhs);
+  std::vector<int> steps(nrhs);
+  std::vector<double> res(nrhs, 0.0);
+  int outer_total = 0;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // explicit residual w = rhs - Pi M x
+    HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
+    HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
+    HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+    HPS_CK(c, cudaStreamSynchronize(st));
+    bool all = true;
+    std::vector<char> active(nrhs, 0);
+    for (int r = 0; r < nrhs; ++r) {
+      const double beta = std::sqrt(std::max(0.0, c->pin_h[r].x));
+      res[r] = bnorm[r] > 0 ? beta / bnorm[r] : 0.0;
+      done[r] = res[r] <= tol;
+      active[r] = !done[r];
+      all = all && done[r];
+      for (int i = 0; i <= restart; ++i) g[(size_t)r * (restart + 1) + i] = 0.0;
+      g[(size_t)r * (restart + 1)] = beta;
+      steps[r] = 0;
+      c->pin_floor[r] = active[r] ? 0.0 : DBL_MAX;
+    }
+    if (all) break;
+    HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    HPS_CK(c, bscale<double>(c->fg_V, c->fg_w, hbuf, c->fg_floor, n, nrhs, st));
+    int jdone = 0;
+    for (int j = 0; j < restart; ++j) {
+      double2* Vj = c->fg_V + (size_t)j * vs;
+      double2* Zj = c->fg_Z + (size_t)j * vs;
+      rc = precond(c, Vj, Zj, nrhs, inner_iters);
+      if (rc) return rc;
+      HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, Zj, nullptr, c->fg_w, c->E, c->nb, nrhs, grid, st));
+      double2* h1 = hbuf;
+      double2* h2 = hbuf + (size_t)(restart + 1) * nrhs;
+      double2* nr = hbuf + (size_t)2 * (restart + 1) * nrhs;
+      HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h1, 0, st));
+      HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h1, n, nrhs, -1.0, st)));
+      HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h2, 0, st));
+      HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h2, n, nrhs, -1.0, st)));
+      HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, nr, 0, st));
+      HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * (size_t)(2 * (restart + 1) + 1) * nrhs,
+                                cudaMemcpyDeviceToHost, st));
+      HPS_CK(c, cudaStreamSynchronize(st));
+      jdone = j + 1;
+      bool any = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!active[r]) continue;
+        cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+        for (int i = 0; i <= j; ++i) {
+          const double2 a = c->pin_h[(size_t)i * nrhs + r];
+          const double2 b = c->pin_h[(size_t)(restart + 1) * nrhs + (size_t)i * nrhs + r];
+          Hr[(size_t)i * restart + j] = cd(a.x + b.x, a.y + b.y);
+        }
+        const double hn = std::sqrt(std::max(0.0, c->pin_h[(size_t)2 * (restart + 1) * nrhs + r].x));
+        double* csr = &cs[(size_t)r * restart];
+        cd* snr = &sn[(size_t)r * restart];
+        cd* gr = &g[(size_t)r * (restart + 1)];
+        for (int i = 0; i < j; ++i) {
+          const cd a = Hr[(size_t)i * restart + j], b = Hr[(size_t)(i + 1) * restart + j];
+          Hr[(size_t)i * restart + j] = csr[i] * a + snr[i] * b;
+          Hr[(size_t)(i + 1) * restart + j] = csr[i] * b - std::conj(snr[i]) * a;
+        }
+        const cd a = Hr[(size_t)j * restart + j];
+        const double aa = std::abs(a);
+        double cc;
+        cd ss;
+        if (hn == 0.0) { cc = 1.0; ss = 0.0; }
+        else if (aa == 0.0) { cc = 0.0; ss = 1.0; }
+        else {
+          const double nu = std::hypot(aa, hn);
+          cc = aa / nu;
+          ss = (a / aa) * (hn / nu);
+        }
+        csr[j] = cc;
+        snr[j] = ss;
+        Hr[(size_t)j * restart + j] = cc * a + ss * hn;
+        const cd gj = gr[j];
+        gr[j] = cc * gj;
+        gr[j + 1] = -std::conj(ss) * gj;
+        its[r] += 1;
+        steps[r] = j + 1;
+        res[r] = bnorm[r] > 0 ? std::abs(gr[j + 1]) / bnorm[r] : 0.0;
+        if (res[r] <= tol || hn <= 1e-300) active[r] = 0;
+        else any = true;
+      }
+      ++outer_total;
+      if (!any) break;
+      if (j + 1 < restart) {
+        for (int r = 0; r < nrhs; ++r) c->pin_floor[r] = active[r] ? 0.0 : DBL_MAX;
+        HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+        HPS_CK(c, bscale<double>(c->fg_V + (size_t)(j + 1) * vs, c->fg_w, nr, c->fg_floor, n, nrhs, st));
+      }
+    }
+    // y = R^{-1} g per right-hand side, then x += Z y
+    for (int r = 0; r < nrhs; ++r) {
+      const cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+      const cd* gr = &g[(size_t)r * (restart + 1)];
+      std::vector<cd> y(jdone, 0.0);
+      for (int i = steps[r] - 1; i >= 0; --i) {
+        cd v = gr[i];
+        for (int l = i + 1; l < steps[r]; ++l) v -= Hr[(size_t)i * restart + l] * y[l];
+        const cd d = Hr[(size_t)i * restart + i];
+        y[i] = std::abs(d) > 0 ? v / d : 0.0;
+      }
+      for (int i = 0; i < jdone; ++i) c->pin_y[(size_t)i * nrhs + r] = make_double2(y[i].real(), y[i].imag());
+    }
+    HPS_CK(c, cudaMemcpyAsync(c->fg_y, c->pin_y, sizeof(double2) * (size_t)jdone * nrhs, cudaMemcpyHostToDevice, st));
+    HPS_CK(c, (bupdate<double, double>(c->fg_x, c->fg_Z, vs, jdone, c->fg_y, n, nrhs, 1.0, st)));
+  }
+  // explicit FP64 residual
+  HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
+  HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
+  HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+  // solution in skeleton order
+  double2* gdev = static_cast<double2*>(g_out);
+  const bool host_out = !is_device_ptr(g_out);
+  if (host_out) gdev = c->pv_out;
+  HPS_CK(c, rows_to_user(gdev, c->fg_x, c->d_es_in, n, nrhs, c->n_skel, st));
+  if (host_out)
+    HPS_CK(c, cudaMemcpyAsync(g_out, gdev, sizeof(double2) * (size_t)c->n_skel * nrhs, cudaMemcpyDeviceToHost, st));
+  HPS_CK(c, cudaStreamSynchronize(st));
+  int nconv = 0, maxit = 0;
+  double maxres = 0.0;
+  for (int r = 0; r < nrhs; ++r) {
+    res[r] = bnorm[r] > 0 ? std::sqrt(std::max(0.0, c->pin_h[r].x)) / bnorm[r] : 0.0;
+    nconv += res[r] <= tol;
+    maxit = std::max(maxit, its[r]);
+    maxres = std::max(maxres, res[r]);
+  }
+  const auto t2 = std::chrono::steady_clock::now();
+  if (info) {
+    info->outer_iterations = maxit;
+    info->converged = nconv;
+    info->max_rel_residual = maxres;
+    if (info->iterations)
+      for (int r = 0; r < nrhs; ++r) info->iterations[r] = its[r];
+    if (info->rel_residual)
+      for (int r = 0; r < nrhs; ++r) info->rel_residual[r] = res[r];
+    info->ms_rhs = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    info->ms_solve = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  }
+  (void)outer_total;
+  if (nconv < nrhs) return fail(c, HPS_ENOTCONV, "FGMRES stopped before the tolerance");
+  return HPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+"""The C-ABI library loads and exports every entry point include/hps.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2511_00735_gb300 import build as B
+from paper_2511_00735_gb300 import hps as H
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def libpath():
+    srcs = [os.path.join(B.CSRC, f) for f in os.listdir(B.CSRC)]
+    if not os.path.exists(B.LIB) or max(os.path.getmtime(s) for s in srcs) > os.path.getmtime(B.LIB):
+        B.build()
+    return B.LIB
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "hps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hps_[A-Za-z_]+)\s*\(", txt)) - {"hps_alloc_fn", "hps_free_fn"})
+
+
+def test_header_declares_the_binding_surface():
+    assert declared() == sorted(H.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_without_device(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.hps_strerror.restype = ctypes.c_char_p
+    assert lib.hps_strerror(0) == b"ok"
+    assert b"unsupported" in lib.hps_strerror(-8) or b"not supported" in lib.hps_strerror(-8)
+
+
+def test_null_context_is_rejected(libpath):
+    lib = ctypes.CDLL(libpath)
+    assert lib.hps_mesh(None, 4, 4, 8) == -1
+    assert lib.hps_destroy(None) == 0

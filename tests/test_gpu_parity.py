@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every case is seeded and small enough for the oracle; tolerances follow from
+FP64 rounding of the operations involved (relative l2 errors).  Index maps are
+compared bit for bit.  The last test runs the 64x64, N = 16 workload and checks
+sampled leaves against the oracle plus the explicit FP64 residual.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.hps import MergeTree
+from oracle.leaf import leaf_itI
+from oracle.problem import OracleProblem, coefficient
+from oracle.skeleton import Mesh, apply_M, assemble_M
+from paper_2511_00735_gb300 import hps as H
+from paper_2511_00735_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    s = H.Solver(0)
+    yield s
+    s.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def host(x):
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+# ---------------------------------------------------------------- index maps
+@pytest.mark.parametrize("nx,N", [(2, 3), (4, 6), (8, 4)])
+def test_index_maps_bit_exact(solver, nx, N):
+    solver.mesh(nx, N)
+    sin, sout, bd = solver.index_maps()
+    m = Mesh(nx, nx, N)
+    q = N - 1
+    e_in, e_out, e_bd = [], [], []
+    for e in range(m.E):
+        for s in range(4):
+            for k in range(q):
+                ui, uo, bi = m.unknown_in[e, s], m.unknown_out(e, s), m.bdry_in[e, s]
+                e_in.append(ui + k if ui >= 0 else -1)
+                e_out.append(uo + k if uo >= 0 else -1)
+                e_bd.append(bi + k if bi >= 0 else -1)
+    assert np.array_equal(sin, np.array(e_in)) and np.array_equal(sout, np.array(e_out))
+    assert np.array_equal(bd, np.array(e_bd))
+    X, Y = solver.node_coords()
+    Xo, Yo = m.all_node_xy()
+    np.testing.assert_allclose(X, Xo, atol=1e-15)
+    np.testing.assert_allclose(Y, Yo, atol=1e-15)
+    bx, by, bnx, bny = solver.boundary_points()
+    ox, oy, onx, ony = m.boundary_points()
+    np.testing.assert_allclose(np.stack([bx, by, bnx, bny]), np.stack([ox, oy, onx, ony]), atol=1e-15)
+
+
+# ---------------------------------------------------------------- leaves
+@pytest.mark.parametrize("nx,N,kappa", [(2, 4, 5.0), (4, 8, 10.0), (4, 16, 40.0), (8, 12, 30.0)])
+def test_leaf_maps(solver, nx, N, kappa):
+    prob = inputs.single_bump(nx, N, kappa, 1, seed=7)
+    H.setup(solver, prob)
+    Tg = solver.leaf_T(0, nx * nx)
+    mesh = Mesh(nx, nx, N)
+    c = coefficient(mesh, kappa, prob.bumps)
+    for e in range(mesh.E):
+        To = leaf_itI(N, mesh.h, c[e], kappa)["T"]
+        assert rel(Tg[e], To) < 1e-11, e
+
+
+def test_paper_bump_leaf_and_unsupported(solver):
+    prob = inputs.Problem(nx=8, N=8, kappa=150.0, eta=150.0, bumps=[inputs.PAPER_BUMP], thetas=[0.1])
+    with pytest.raises(H.HPSError) as ei:
+        H.setup(solver, prob)
+    assert ei.value.status == -8
+
+
+# ---------------------------------------------------------------- skeleton operators
+@pytest.fixture(scope="module")
+def cfg_small():
+    prob = inputs.single_bump(4, 8, 12.0, 3, seed=11, L_exact=2)
+    return prob, OracleProblem(prob)
+
+
+def test_rhs_and_matvec(solver, cfg_small):
+    prob, op = cfg_small
+    t = H.setup(solver, prob)
+    rhs = host(solver.rhs(dev(t)))
+    for k in range(prob.nrhs):
+        assert rel(rhs[k], op.rhs[k]) < 1e-12
+    x = np.random.default_rng(0).standard_normal((3, op.mesh.n_skel)) * (1 - 0.7j)
+    y = host(solver.matvec(dev(x)))
+    yo = apply_M(op.mesh, op.Ts, x.T).T
+    assert rel(y, yo) < 1e-12
+
+
+# ---------------------------------------------------------------- merges
+@pytest.mark.parametrize("nx,N", [(2, 6), (4, 8), (8, 4)])
+def test_stage_maps(solver, nx, N):
+    prob = inputs.single_bump(nx, N, 10.0, 1, seed=5)
+    H.setup(solver, prob)
+    op = OracleProblem(prob)
+    L = op.mesh.L
+    solver.merge_levels(L)
+    tree = MergeTree(op.mesh, op.Ts, None, L)
+    for k in range(L + 1):
+        for sub in range(len(tree.stages[k])):
+            Tg = solver.stage_T(k, sub)
+            assert rel(Tg, tree.stages[k][sub].T) < 1e-10, (k, sub)
+
+
+@pytest.mark.parametrize("L_exact", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("coarse", ["gmres", "exact"])
+def test_precond_apply(solver, cfg_small, L_exact, coarse):
+    prob, op = cfg_small
+    H.setup(solver, prob)
+    solver.merge_levels(L_exact, exact_coarse=(coarse == "exact"))
+    tree = MergeTree(op.mesh, op.Ts, None, L_exact)
+    r = np.random.default_rng(L_exact).standard_normal((2, op.mesh.n_skel)) * (0.3 + 1j)
+    z = host(solver.precond_apply(dev(r), inner_iters=3))
+    for k in range(2):
+        zo = tree.mg(r[k], coarse, 3)
+        assert rel(z[k], zo) < 1e-10, (L_exact, coarse, k)
+
+
+def test_precond_exact_is_inverse(solver, cfg_small):
+    prob, op = cfg_small
+    H.setup(solver, prob)
+    solver.merge_levels(op.mesh.L)
+    r = np.random.default_rng(3).standard_normal((1, op.mesh.n_skel)) + 0j
+    z = host(solver.precond_apply(dev(r)))
+    assert rel(z[0], np.linalg.solve(assemble_M(op.mesh, op.Ts), r[0])) < 1e-11
+
+
+# ---------------------------------------------------------------- solves
+def test_solve_4x4_fp64(solver):
+    prob = inputs.small_4x4(0)
+    op = OracleProblem(prob)
+    g_ref = np.linalg.solve(assemble_M(op.mesh, op.Ts), op.rhs[0])
+    t = H.setup(solver, prob)
+    solver.merge_levels(prob.L_exact)
+    g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=prob.inner_iters)
+    assert info["max_rel_residual"] <= 1e-10
+    assert rel(g[0], g_ref) < 1e-9
+    _, oinfo = op.solve_fgmres(L_exact=prob.L_exact, inner_iters=prob.inner_iters, tol=1e-10)
+    assert abs(info["outer_iterations"] - oinfo[0]["iterations"]) <= 1
+    # direct HPS: all merges but the last, exact coarse -> one iteration
+    solver.merge_levels(op.mesh.L - 1, exact_coarse=True)
+    g2, info2 = solver.gmres_solve(t, tol=1e-10, inner_iters=0)
+    assert info2["outer_iterations"] == 1 and rel(g2[0], g_ref) < 1e-10
+
+
+def test_solve_unpreconditioned_and_multi_rhs(solver, cfg_small):
+    prob, op = cfg_small
+    t = H.setup(solver, prob)
+    g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=-1, restart=30, max_outer=40)
+    M = assemble_M(op.mesh, op.Ts)
+    for k in range(prob.nrhs):
+        assert rel(g[k], np.linalg.solve(M, op.rhs[k])) < 1e-8
+    assert info["max_rel_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [H.HPS_FP64, H.HPS_MIXED])
+def test_solve_8x8_device_buffers(solver, precision):
+    prob = inputs.single_bump(8, 12, 30.0, 4, seed=21, L_exact=4)
+    op = OracleProblem(prob)
+    M = assemble_M(op.mesh, op.Ts)
+    t = H.setup(solver, prob, precision)
+    solver.merge_levels(prob.L_exact)
+    g, info = solver.gmres_solve(dev(t), tol=1e-10, inner_iters=5)
+    g = host(g)
+    assert info["max_rel_residual"] <= 1e-10
+    for k in range(prob.nrhs):
+        gr = np.linalg.solve(M, op.rhs[k])
+        assert rel(g[k], gr) < 1e-8
+        assert np.linalg.norm(op.rhs[k] - M @ g[k]) / np.linalg.norm(op.rhs[k]) < 1e-9
+
+
+def test_bad_arguments(solver):
+    with pytest.raises(H.HPSError):
+        solver.mesh(6, 8)
+    with pytest.raises(H.HPSError):
+        solver.mesh(4, 17)
+    solver.mesh(4, 8)
+    with pytest.raises(H.HPSError):
+        solver.build_leaves()          # no coefficient yet
+    with pytest.raises(H.HPSError):
+        solver.merge_levels(1)
+
+
+# ---------------------------------------------------------------- full size
+def test_64x64_N16_sampled(solver):
+    prob = inputs.fp64_64x64(seed=1, nrhs=4)
+    t = H.setup(solver, prob, H.HPS_FP64)
+    mesh = Mesh(64, 64, 16)
+    c = coefficient(mesh, prob.kappa, prob.bumps)
+    rng = np.random.default_rng(0)
+    for e in [0, 63, 4095, 2080] + list(rng.integers(0, 4096, 6)):
+        To = leaf_itI(16, mesh.h, c[e], prob.kappa)["T"]
+        assert rel(solver.leaf_T(int(e), 1)[0], To) < 1e-11, e
+    solver.merge_levels(prob.L_exact)
+    g, info = solver.gmres_solve(dev(t), tol=1e-10, inner_iters=prob.inner_iters)
+    assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10
+    rhs = solver.rhs(dev(t))
+    r = host(rhs) - host(solver.matvec(g))
+    assert np.max(np.linalg.norm(r, axis=1) / np.linalg.norm(host(rhs), axis=1)) <= 1.01e-10
