@@ -190,6 +190,32 @@ int hps_gmres_solve(hps_ctx* ctx, const void* t, const void* s, int nrhs, double
                     int inner_iters, int restart, int max_outer, void* g_out,
                     hps_info* info);
 
+/* Profiling phases of hps_profile_read. */
+enum {
+  HPS_PH_LEAF = 0,   /* hps_build_leaves: the leaf kernel alone                     */
+  HPS_PH_MERGE,      /* hps_merge_levels                                            */
+  HPS_PH_RHS,        /* RHS assembly inside hps_gmres_solve                         */
+  HPS_PH_MATVEC,     /* FP64 skeleton matvec inside hps_gmres_solve (one kernel each) */
+  HPS_PH_PRECOND,    /* MG(M) applications inside hps_gmres_solve                   */
+  HPS_PH_ORTHO,      /* Gram-Schmidt inside hps_gmres_solve                         */
+  HPS_PH_OTHER,      /* final residual and output                                   */
+  HPS_NPHASE
+};
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts); a cheap host-side counter, no device synchronisation. */
+long long hps_kernel_launches(void);
+
+/* enable != 0: clear the per-phase counters and start bracketing the phases
+ * above with CUDA events on the context's stream; enable == 0: stop.
+ * Profiling adds two event records per phase instance and no synchronisation. */
+int hps_profile(hps_ctx* ctx, int enable);
+
+/* Device milliseconds, kernel launches and phase instances accumulated since
+ * the last hps_profile(ctx, 1), per phase; host arrays [HPS_NPHASE], any may be
+ * NULL.  Synchronises the context's stream. */
+int hps_profile_read(hps_ctx* ctx, double* ms, long long* launches, long long* calls);
+
 #ifdef __cplusplus
 }
 #endif

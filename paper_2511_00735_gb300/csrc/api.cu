@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -14,6 +15,62 @@
 
 namespace hps {
 
+static std::atomic<long long> g_launches{0};
+static thread_local long long* tl_phase_launch = nullptr;
+
+void note_launch(int n) {
+  g_launches += n;
+  if (tl_phase_launch) *tl_phase_launch += n;
+}
+
+static cudaEvent_t get_event(hps_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+PhaseScope::PhaseScope(hps_ctx* ctx, int phase) : c(ctx), ph(phase), prev(tl_phase_launch) {
+  tl_phase_launch = &c->prof_launch[ph];
+  c->prof_calls[ph] += 1;
+  if (c->prof) {
+    a = get_event(c);
+    if (a) cudaEventRecord(a, c->stream);
+  }
+}
+
+PhaseScope::~PhaseScope() {
+  tl_phase_launch = prev;
+  if (c->prof && a) {
+    cudaEvent_t b = get_event(c);
+    if (b) {
+      cudaEventRecord(b, c->stream);
+      c->prof_ev.push_back({ph, {a, b}});
+    } else {
+      c->ev_pool.push_back(a);
+    }
+  }
+}
+
+static void prof_collect(hps_ctx* c) {
+  if (c->prof_ev.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& pe : c->prof_ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) c->prof_ms[pe.first] += ms;
+    else cudaGetLastError();
+    c->ev_pool.push_back(pe.second.first);
+    c->ev_pool.push_back(pe.second.second);
+  }
+  c->prof_ev.clear();
+}
 
 int fail(hps_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -255,6 +312,11 @@ int hps_destroy(hps_ctx* c) {
   free_solver(c);
   while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
   cudaFree(c->d_flag);
+  for (auto& pe : c->prof_ev) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return HPS_OK;
 }
@@ -485,7 +547,10 @@ int hps_build_leaves(hps_ctx* c, int precision) {
   p.c = c->d_c; p.Dh = c->d_Dref; p.Kh = c->d_Kref; p.wh = c->d_wref;
   p.Ascr = Ascr; p.T = c->d_T; p.flag = c->d_flag;
   HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-  HPS_CK(c, launch_leaf(p, grid, c->stream));
+  {
+    PhaseScope ps(c, HPS_PH_LEAF);
+    HPS_CK(c, launch_leaf(p, grid, c->stream));
+  }
   int flag = 0;
   HPS_CK(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HPS_CK(c, cudaStreamSynchronize(c->stream));
@@ -503,6 +568,33 @@ int hps_leaf_T(hps_ctx* c, int e0, int count, void* T_host) {
   HPS_CK(c, cudaStreamSynchronize(c->stream));
   HPS_CK(c, cudaMemcpy(T_host, c->d_T + (size_t)e0 * c->nb * c->nb, sizeof(double2) * (size_t)count * c->nb * c->nb,
                        cudaMemcpyDeviceToHost));
+  return HPS_OK;
+}
+
+long long hps_kernel_launches(void) { return hps::g_launches.load(); }
+
+int hps_profile(hps_ctx* c, int enable) {
+  CHECK_CTX(c);
+  prof_collect(c);
+  if (enable) {
+    for (int i = 0; i < HPS_NPHASE; ++i) {
+      c->prof_ms[i] = 0.0;
+      c->prof_launch[i] = 0;
+      c->prof_calls[i] = 0;
+    }
+  }
+  c->prof = enable != 0;
+  return HPS_OK;
+}
+
+int hps_profile_read(hps_ctx* c, double* ms, long long* launches, long long* calls) {
+  CHECK_CTX(c);
+  prof_collect(c);
+  for (int i = 0; i < HPS_NPHASE; ++i) {
+    if (ms) ms[i] = c->prof_ms[i];
+    if (launches) launches[i] = c->prof_launch[i];
+    if (calls) calls[i] = c->prof_calls[i];
+  }
   return HPS_OK;
 }
 

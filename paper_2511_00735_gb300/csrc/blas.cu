@@ -94,6 +94,7 @@ cudaError_t launch_cfg(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s)
   dim3 grid((nmax + BN - 1) / BN, (mmax + BM - 1) / BM, a.nbatch < 65535 ? a.nbatch : 65535);
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
   cgemm_kernel<R, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(a);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -281,6 +282,7 @@ cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, in
     for (int b0 = 0; b0 < nmat; b0 += 65535) {
       const int nb = nmat - b0 < 65535 ? nmat - b0 : 65535;
       gj_small_kernel<R><<<nb, NT, small_bytes, s>>>(W + (long long)b0 * m * 2 * m, m, flag);
+      note_launch();
     }
     return cudaGetLastError();
   }
@@ -294,13 +296,16 @@ cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, in
   for (int k0 = 0; k0 < m; k0 += nbw) {
     const int kb = m - k0 < nbw ? m - k0 : nbw;
     gj_panel_kernel<R><<<nmat, NT, panel_bytes, s>>>(W, m, k0, kb, piv_ws, lu_ws, flag);
+    note_launch();
     dim3 ga((2 * m - k0 + NT - 1) / NT, nmat);
     gj_apply_kernel<R><<<ga, NT, 0, s>>>(W, m, k0, kb, piv_ws, lu_ws);
+    note_launch();
     const int mrows = k0 > m - k0 - kb ? k0 : m - k0 - kb;
     const int ncols = 2 * m - k0 - kb;
     if (mrows > 0 && ncols > 0) {
       dim3 gu((ncols + 63) / 64, (mrows + 63) / 64, nmat * 2);
       gj_update_kernel<R, 64, 64, 8, 4, 4><<<gu, NT, 0, s>>>(W, m, k0, kb);
+      note_launch();
     }
   }
   return cudaGetLastError();

@@ -7,6 +7,9 @@
 
 namespace hps {
 
+// Counts one kernel launch (total and per profiling phase of the calling context).
+void note_launch(int n = 1);
+
 template <typename R> struct cplx;
 template <> struct cplx<double> { using T = double2; };
 template <> struct cplx<float> { using T = float2; };

@@ -125,6 +125,14 @@ struct hps_ctx {
   double* pin_floor = nullptr;
   double2 *pv_in = nullptr, *pv_out = nullptr;  // precond_apply/matvec ES staging
   int pv_nrhs = 0;
+
+  // profiling (hps_profile): CUDA events per phase on the context's stream
+  bool prof = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[HPS_NPHASE] = {0};
+  long long prof_launch[HPS_NPHASE] = {0};
+  long long prof_calls[HPS_NPHASE] = {0};
 };
 
 namespace hps {
@@ -143,6 +151,19 @@ int build_tree(hps_ctx* c, int L_exact, int exact_coarse);
 template <typename R>
 int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int inner_iters);
 
+}  // namespace hps
+
+namespace hps {
+// Attributes kernel launches to a phase and, when profiling is on, brackets the
+// phase with CUDA events on the context's stream.
+struct PhaseScope {
+  hps_ctx* c;
+  int ph;
+  cudaEvent_t a = nullptr;
+  long long* prev;
+  PhaseScope(hps_ctx* ctx, int phase);
+  ~PhaseScope();
+};
 }  // namespace hps
 
 #define HPS_CK(ctx, call)                                   \

@@ -217,6 +217,7 @@ cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
   cudaError_t err = cudaFuncSetAttribute(leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   leaf_kernel<<<grid, 256, smem, s>>>(p);
+  note_launch();
   return cudaGetLastError();
 }
 

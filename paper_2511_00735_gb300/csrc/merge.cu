@@ -380,6 +380,7 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
 
 int build_tree(hps_ctx* c, int L_exact, int exact_coarse) {
   free_tree(c);
+  PhaseScope ps(c, HPS_PH_MERGE);
   int rc = c->precision == HPS_FP64 ? build_tree_t<double>(c, L_exact, exact_coarse)
                                     : build_tree_t<float>(c, L_exact, exact_coarse);
   if (rc != HPS_OK) {

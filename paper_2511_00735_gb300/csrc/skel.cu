@@ -64,6 +64,7 @@ cudaError_t es_matvec(const double2* T, const int* nbr, const double2* x, const 
   const size_t smem = sizeof(double2) * (size_t)nb * nrhs;
   if (smem > 48 * 1024) cudaFuncSetAttribute(es_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   es_matvec_kernel<<<grid, NT, smem, s>>>(T, nbr, x, c0, y, E, nb, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(NT) es_rhs_kernel(const double2* __restrict__ 
 cudaError_t es_rhs(const double2* T, const int* nbr, const int* bdry, const double2* t, double2* rho, int E, int nb,
                    int nrhs, int grid, cudaStream_t s) {
   es_rhs_kernel<<<grid, NT, 0, s>>>(T, nbr, bdry, t, rho, E, nb, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -129,12 +131,14 @@ template <typename RS, typename RD>
 cudaError_t gather_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   gather_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 template <typename RS, typename RD>
 cudaError_t scatter_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   scatter_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -162,11 +166,13 @@ __global__ void rows_to_user_kernel(double2* __restrict__ dst, const double2* __
 cudaError_t user_to_rows(double2* dst, const double2* src, const int* map, long long rows, int nrhs, long long n,
                          cudaStream_t s) {
   user_to_rows_kernel<<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs, n);
+  note_launch();
   return cudaGetLastError();
 }
 cudaError_t rows_to_user(double2* dst, const double2* src, const int* map, long long rows, int nrhs, long long n,
                          cudaStream_t s) {
   rows_to_user_kernel<<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -186,6 +192,7 @@ __global__ void permute_blocks_kernel(c_t<RD>* __restrict__ dst, const c_t<RS>* 
 template <typename RS, typename RD>
 cudaError_t permute_blocks(c_t<RD>* dst, const c_t<RS>* src, const int* map, int nsub, int n, cudaStream_t s) {
   permute_blocks_kernel<RS, RD><<<nblocks((long long)nsub * n * n, NT, 16384), NT, 0, s>>>(dst, src, map, nsub, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -227,6 +234,7 @@ cudaError_t coarse_apply(c_t<R>* W, const c_t<R>* T, const c_t<R>* g, const int*
   dim3 grid((n + rpb - 1) / rpb, nsub);
   coarse_apply_kernel<R><<<grid, NT, 0, s>>>(W, T, g, mask, make_int4(off[0], off[1], off[2], off[3]), off[4], n, nrhs,
                                              rpb);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -251,6 +259,7 @@ template <typename R>
 cudaError_t swap_add(c_t<R>* out, const c_t<R>* a, const c_t<R>* b, const int* nbr, long long rows, int nrhs,
                      cudaStream_t s) {
   swap_add_kernel<R><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(out, a, b, nbr, rows, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -308,7 +317,9 @@ cudaError_t bdot(const c_t<R>* V, long long vstride, int nvec, const c_t<R>* w, 
   const int nblk = bdot_blocks(rows);
   const long long chunk = (rows + nblk - 1) / nblk;
   bdot_partial_kernel<R><<<nblk, NT, 0, s>>>(V, vstride, nvec, w, rows, nrhs, rpad, partial, chunk);
+  note_launch();
   bdot_final_kernel<R><<<(nvec * nrhs + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nvec, nrhs, out, accumulate);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -329,6 +340,7 @@ cudaError_t bupdate(c_t<R>* w, const c_t<R>* V, long long vstride, int nvec, con
                     R sign, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
   bupdate_kernel<R, RH><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(w, V, vstride, nvec, h, rows, nrhs, sign);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -349,6 +361,7 @@ template <typename R>
 cudaError_t bscale(c_t<R>* out, const c_t<R>* w, const c_t<R>* dots, const R* floor, long long rows, int nrhs,
                    cudaStream_t s) {
   bscale_kernel<R><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(out, w, dots, floor, rows, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -371,6 +384,7 @@ template <typename R>
 cudaError_t hstore(c_t<R>* H, const c_t<R>* h1, const c_t<R>* h2, const c_t<R>* nrm2, int j, int k, int nrhs,
                    cudaStream_t s) {
   hstore_kernel<R><<<(nrhs + NT - 1) / NT, NT, 0, s>>>(H, h1, h2, nrm2, j, k, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -386,6 +400,7 @@ __global__ void beta_kernel(R* __restrict__ beta, R* __restrict__ floor, const c
 template <typename R>
 cudaError_t beta_floor(R* beta, R* floor, const c_t<R>* nrm2, R tol, int nrhs, cudaStream_t s) {
   beta_kernel<R><<<(nrhs + NT - 1) / NT, NT, 0, s>>>(beta, floor, nrm2, tol, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -452,6 +467,7 @@ template <typename R>
 cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws, R* cws, c_t<R>* sws, int k,
                 int nrhs, cudaStream_t s) {
   lsq_kernel<R><<<(nrhs + NT - 1) / NT, NT, 0, s>>>(H, beta, floor, y, gws, cws, sws, k, nrhs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -464,6 +480,7 @@ template <typename R>
 cudaError_t zero(c_t<R>* x, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   zero_kernel<R><<<nblocks(n, NT, 8192), NT, 0, s>>>(x, n);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -480,6 +497,7 @@ __global__ void eye2_kernel(c_t<R>* __restrict__ W, int m, int nmat) {
 template <typename R>
 cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s) {
   eye2_kernel<R><<<nblocks((long long)nmat * m * 2 * m, NT, 16384), NT, 0, s>>>(W, m, nmat);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -85,6 +85,7 @@ int ensure_fg(hps_ctx* c, int restart, int nrhs) {
 }
 
 int precond(hps_ctx* c, const double2* v, double2* z, int nrhs, int k) {
+  PhaseScope ps(c, HPS_PH_PRECOND);
   if (k < 0) {
     HPS_CK(c, swap_add<double>(z, nullptr, v, c->d_es_nb, c->n_es, nrhs, c->stream));
     return HPS_OK;
@@ -213,8 +214,11 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     HPS_CK(c, cudaMemcpyAsync(c->pv_in, t, sizeof(double2) * (size_t)c->n_bdry * nrhs, cudaMemcpyHostToDevice, st));
     t_dev = c->pv_in;
   }
-  HPS_CK(c, user_to_rows(c->fg_t, t_dev, nullptr, c->n_bdry, nrhs, c->n_bdry, st));
-  HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->fg_t, c->fg_rhs, c->E, c->nb, nrhs, grid, st));
+  {
+    PhaseScope ps(c, HPS_PH_RHS);
+    HPS_CK(c, user_to_rows(c->fg_t, t_dev, nullptr, c->n_bdry, nrhs, c->n_bdry, st));
+    HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->fg_t, c->fg_rhs, c->E, c->nb, nrhs, grid, st));
+  }
   double2* hbuf = c->fg_h;
   HPS_CK(c, bdot<double>(c->fg_rhs, 0, 1, c->fg_rhs, n, nrhs, c->fg_part, hbuf, 0, st));
   HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -233,7 +237,10 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   int outer_total = 0;
   for (int outer = 0; outer < max_outer; ++outer) {
     // explicit residual w = rhs - Pi M x
-    HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
+    {
+      PhaseScope ps(c, HPS_PH_MATVEC);
+      HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
+    }
     HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
     HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
     HPS_CK(c, cudaStreamSynchronize(st));
@@ -259,15 +266,21 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
       double2* Zj = c->fg_Z + (size_t)j * vs;
       rc = precond(c, Vj, Zj, nrhs, inner_iters);
       if (rc) return rc;
-      HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, Zj, nullptr, c->fg_w, c->E, c->nb, nrhs, grid, st));
+      {
+        PhaseScope ps(c, HPS_PH_MATVEC);
+        HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, Zj, nullptr, c->fg_w, c->E, c->nb, nrhs, grid, st));
+      }
       double2* h1 = hbuf;
       double2* h2 = hbuf + (size_t)(restart + 1) * nrhs;
       double2* nr = hbuf + (size_t)2 * (restart + 1) * nrhs;
-      HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h1, 0, st));
-      HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h1, n, nrhs, -1.0, st)));
-      HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h2, 0, st));
-      HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h2, n, nrhs, -1.0, st)));
-      HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, nr, 0, st));
+      {
+        PhaseScope ps(c, HPS_PH_ORTHO);
+        HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h1, 0, st));
+        HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h1, n, nrhs, -1.0, st)));
+        HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h2, 0, st));
+        HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h2, n, nrhs, -1.0, st)));
+        HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, nr, 0, st));
+      }
       HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * (size_t)(2 * (restart + 1) + 1) * nrhs,
                                 cudaMemcpyDeviceToHost, st));
       HPS_CK(c, cudaStreamSynchronize(st));
@@ -338,6 +351,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     HPS_CK(c, (bupdate<double, double>(c->fg_x, c->fg_Z, vs, jdone, c->fg_y, n, nrhs, 1.0, st)));
   }
   // explicit FP64 residual
+  PhaseScope ps_other(c, HPS_PH_OTHER);
   HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
   HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
   HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));

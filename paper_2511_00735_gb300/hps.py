@@ -27,7 +27,9 @@ _STATUS = {0: "HPS_OK", -1: "HPS_EINVAL", -2: "HPS_ENOMEM", -3: "HPS_ENOTBUILT",
 EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "hps_strerror", "hps_mesh",
            "hps_sizes", "hps_node_coords", "hps_boundary_points", "hps_index_maps", "hps_set_coeff",
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
-           "hps_precond_apply", "hps_gmres_solve"]
+           "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read"]
+
+PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
 
 class HPSError(RuntimeError):
@@ -77,6 +79,9 @@ def load_library(path: str = LIB_PATH):
         "hps_skel_matvec": (i, [vp, vp, vp, i]),
         "hps_precond_apply": (i, [vp, vp, vp, i, i]),
         "hps_gmres_solve": (i, [vp, vp, vp, i, d, i, i, i, vp, C.POINTER(HPSInfo)]),
+        "hps_kernel_launches": (ll, []),
+        "hps_profile": (i, [vp, i]),
+        "hps_profile_read": (i, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -223,6 +228,19 @@ class Solver:
         self._check(self.lib.hps_stage_T(self.h, stage, sub, _ptr(out)))
         return out
 
+    # -- profiling -------------------------------------------------------------
+    def profile(self, enable: bool = True):
+        self._check(self.lib.hps_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """{phase: (device ms, kernel launches, phase instances)} since profile(True)."""
+        n = len(PHASES)
+        ms = np.zeros(n)
+        la = np.zeros(n, dtype=np.int64)
+        ca = np.zeros(n, dtype=np.int64)
+        self._check(self.lib.hps_profile_read(self.h, _ptr(ms), _ptr(la), _ptr(ca)))
+        return {ph: (float(ms[i]), int(la[i]), int(ca[i])) for i, ph in enumerate(PHASES)}
+
     # -- skeleton operators (device tensors [nrhs][n]) ------------------------
     def rhs(self, t):
         nrhs = t.shape[0]
@@ -261,6 +279,11 @@ class Solver:
              "max_rel_residual": info.max_rel_residual, "iterations": list(its), "rel_residual": list(res),
              "ms_rhs": info.ms_rhs, "ms_solve": info.ms_solve}
         return out, d
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libhps in this process so far."""
+    return int(load_library().hps_kernel_launches())
 
 
 def exported_symbols(path: str = LIB_PATH):

@@ -69,7 +69,7 @@ def test_index_maps_bit_exact(solver, nx, N):
 
 
 # ---------------------------------------------------------------- leaves
-@pytest.mark.parametrize("nx,N,kappa", [(2, 4, 5.0), (4, 8, 10.0), (4, 16, 40.0), (8, 12, 30.0)])
+@pytest.mark.parametrize("nx,N,kappa", [(2, 4, 5.0), (4, 8, 10.0), (4, 16, 15.0), (8, 12, 30.0)])
 def test_leaf_maps(solver, nx, N, kappa):
     prob = inputs.single_bump(nx, N, kappa, 1, seed=7)
     H.setup(solver, prob)
