@@ -236,8 +236,6 @@ def oracle_estimate(prob, iterations: int, leaf_sample: int = 48):
     per level); one FP64 skeleton matvec and one V-cycle's per-pair sweep
     operations plus the coarse GMRES steps for one right-hand side (scaled by the
     FGMRES iteration count and the number of right-hand sides)."""
-    import threadpoolctl
-
     from oracle.hps import Sub, merge_pair
     from oracle.krylov import gmres_fixed
     from oracle.leaf import leaf_itI
@@ -302,10 +300,20 @@ def oracle_estimate(prob, iterations: int, leaf_sample: int = 48):
     t_mv = time.perf_counter() - t5
     per_rhs = iterations * (t_mv + t_sweep + t_coarse)
     total = t_leaf + t_merge + prob.nrhs * per_rhs
-    info = threadpoolctl.threadpool_info()
-    cores = max([p.get("num_threads", 1) for p in info] + [1])
+    cores = blas_threads()
     return {"seconds_per_step": total, "t_leaf": t_leaf, "t_merge": t_merge, "t_solve_per_rhs": per_rhs,
             "cores": cores, "measured_s": time.perf_counter() - t0}
+
+
+def blas_threads() -> int:
+    """Threads numpy's BLAS uses (threadpoolctl when installed, else the visible cores)."""
+    try:
+        import threadpoolctl
+
+        info = threadpoolctl.threadpool_info()
+        return max([p.get("num_threads", 1) for p in info] + [1])
+    except ImportError:
+        return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
 def cpu_baseline_entry(prob, iterations):

@@ -12,8 +12,10 @@
 //
 // L~_ii is real and symmetric; it is positive definite when
 // c < lambda_min(K(x)M + M(x)K, M(x)M) on the interior (the host checks this
-// with a rigorous bound before launching), so Z comes from a real Cholesky
-// factorisation in shared memory (packed lower triangle, 203 KB at N = 16).
+// with a rigorous bound before launching), so Z comes from a real L D L^T
+// (square-root-free Cholesky) factorisation in shared memory (packed unit lower
+// triangle with d on the diagonal, 203 KB at N = 16): every update of the
+// factorisation and of the two triangular solves is a single FP64 FMA.
 // The 4q x 4q complex P is inverted by Gauss-Jordan with partial pivoting.
 //
 // One persistent CTA per SM (the factor needs almost all of the 227 KB of
@@ -72,8 +74,8 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
       Lp[l] = v;
     }
     __syncthreads();
-    // ---- right-looking Cholesky, column scaling deferred by one step ----
-    double prev_rs = 0.0;
+    // ---- right-looking L D L^T (unit lower U, diagonal d), column scaling deferred one step ----
+    double prev_inv = 0.0;
     for (int k = 0; k < ni; ++k) {
       for (int i = k + tid; i < ni; i += nth) colk[i] = Lp[pk(i, k)];
       __syncthreads();
@@ -84,18 +86,16 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
       }
       const double inv = 1.0 / dk;
       if (k > 0)
-        for (int i = k - 1 + tid; i < ni; i += nth) Lp[pk(i, k - 1)] *= prev_rs;
+        for (int i = k + tid; i < ni; i += nth) Lp[pk(i, k - 1)] *= prev_inv;  // U(i, k-1), diagonal keeps d
       const int warp = tid / 32, lane = tid % 32, nw = nth / 32;
       for (int i = k + 1 + warp; i < ni; i += nw) {
         const double f = colk[i] * inv;
         double* row = Lp + pk(i, 0);
         for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= f * colk[j];
       }
-      prev_rs = 1.0 / sqrt(dk);
+      prev_inv = inv;
       __syncthreads();
     }
-    if (tid == 0) Lp[pk(ni - 1, ni - 1)] *= prev_rs;
-    __syncthreads();
 
     // ---- Z = L~_ii^{-1} L~_iG by chunks of cw columns, A = Dn_GG - Dn_Gi Z ----
     for (int g0 = 0; g0 < nb; g0 += cw) {
@@ -116,37 +116,31 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
         Bc[I * cw + cc] = v;
       }
       __syncthreads();
-      // forward: L y = b (diagonal division deferred)
+      // forward: U y = b (unit lower), one FMA per update
       for (int k = 0; k < ni - 1; ++k) {
-        const double inv = 1.0 / Lp[pk(k, k)];
         const int cnt = (ni - k - 1) * w;
         for (int l = tid; l < cnt; l += nth) {
           const int i = k + 1 + l / w, cc = l % w;
-          Bc[i * cw + cc] -= Lp[pk(i, k)] * (Bc[k * cw + cc] * inv);
+          Bc[i * cw + cc] -= Lp[pk(i, k)] * Bc[k * cw + cc];
         }
         __syncthreads();
       }
+      // diagonal: z = D^{-1} y
       for (int l = tid; l < ni * w; l += nth) {
         const int i = l / w, cc = l % w;
         Bc[i * cw + cc] /= Lp[pk(i, i)];
       }
       __syncthreads();
-      // backward: L^T x = y
+      // backward: U^T x = z
       for (int k = ni - 1; k > 0; --k) {
-        const double inv = 1.0 / Lp[pk(k, k)];
         const double* row = Lp + pk(k, 0);
         const int cnt = k * w;
         for (int l = tid; l < cnt; l += nth) {
           const int i = l / w, cc = l % w;
-          Bc[i * cw + cc] -= row[i] * (Bc[k * cw + cc] * inv);
+          Bc[i * cw + cc] -= row[i] * Bc[k * cw + cc];
         }
         __syncthreads();
       }
-      for (int l = tid; l < ni * w; l += nth) {
-        const int i = l / w, cc = l % w;
-        Bc[i * cw + cc] /= Lp[pk(i, i)];
-      }
-      __syncthreads();
       // A(:, chunk): Dn rows l(j): -D[0,i'] on (i',j); r(j): D[N,i']; b(i): -D[0,j'] on (i,j'); t(i): D[N,j']
       for (int l = tid; l < nb * w; l += nth) {
         const int g = l / w, cc = l % w, gc = g0 + cc;

@@ -108,9 +108,9 @@ def test_rhs_and_matvec(solver, cfg_small):
 
 
 # ---------------------------------------------------------------- merges
-@pytest.mark.parametrize("nx,N", [(2, 6), (4, 8), (8, 4)])
-def test_stage_maps(solver, nx, N):
-    prob = inputs.single_bump(nx, N, 10.0, 1, seed=5)
+@pytest.mark.parametrize("nx,N,kappa", [(2, 6, 6.0), (4, 8, 10.0), (8, 4, 10.0)])
+def test_stage_maps(solver, nx, N, kappa):
+    prob = inputs.single_bump(nx, N, kappa, 1, seed=5)
     H.setup(solver, prob)
     op = OracleProblem(prob)
     L = op.mesh.L
