@@ -150,9 +150,10 @@ void free_tree(hps_ctx* c) {
   }
   c->stages.clear();
   c->levels.clear();
-  FREE(c->coarse.d_mask); FREE(c->coarse.d_cnb); FREE(c->coarse.d_upos); FREE(c->coarse.d_ucnb);
+  FREE(c->coarse.d_cdesc); FREE(c->coarse.d_cnb); FREE(c->coarse.d_upos); FREE(c->coarse.d_ucnb);
   FREE(c->coarse.Winv); FREE(c->coarse.d_desc);
   c->coarse = Coarse();
+  FREE(c->gemm_ws); c->gemm_ws_elems = 0;
   FREE(c->ws_X1); FREE(c->ws_X2); FREE(c->d_piv); FREE(c->d_lu);
   FREE(c->sw_tmp); FREE(c->sw_tmp2); FREE(c->sw_zt);
   FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);

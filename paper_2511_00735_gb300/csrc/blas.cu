@@ -13,15 +13,19 @@ namespace {
 
 constexpr int NT = 256;
 
+// One BM x BN tile of C over k in [kb, ke).  part >= 0: store the raw partial sum
+// into the split-K workspace slot `part` instead of applying the epilogue.
 template <typename R, int BM, int BN, int BK, int TM, int TN>
-__device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& d, int tm, int tn) {
+__device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& d, int tm, int tn, int kb = 0,
+                                          int ke = 1 << 30, int part = -1, int batch = 0, int mmax = 0,
+                                          int nmax = 0) {
   using C = c_t<R>;
   constexpr int TY = BM / TM, TX = BN / TN;
   static_assert(TY * TX == NT, "tile shape must use 256 threads");
   __shared__ C As[BK][BM];
   __shared__ C Bs[BK][BN];
   const int n = d.n < 0 ? a.n_launch : d.n;
-  const int m = d.m, k = d.k;
+  const int m = d.m, k = d.k < ke ? d.k : ke;
   const int row0 = tm * BM, col0 = tn * BN;
   if (row0 >= m || col0 >= n) return;  // uniform over the block
   const int tid = threadIdx.x;
@@ -33,7 +37,7 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& 
     for (int j = 0; j < TN; ++j) acc[i][j] = czero<R>();
   const C* Ab = a.A + (long long)d.a_r * a.lda + d.a_c;
   const C* Bb = a.B + (long long)d.b_r * a.ldb + d.b_c;
-  for (int k0 = 0; k0 < k; k0 += BK) {
+  for (int k0 = kb; k0 < k; k0 += BK) {
     for (int l = tid; l < BM * BK; l += NT) {
       const int i = l / BK, kk = l % BK;
       const int gi = row0 + i, gk = k0 + kk;
@@ -58,6 +62,20 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& 
         for (int j = 0; j < TN; ++j) cfma(acc[i][j], av[i], bv[j]);
     }
     __syncthreads();
+  }
+  if (part >= 0) {
+    C* W = a.ws + (((long long)part * a.nbatch + batch) * mmax) * nmax;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int gi = row0 + ty + i * TY;
+      if (gi >= m) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int gj = col0 + tx + j * TX;
+        if (gj < n) W[(long long)gi * nmax + gj] = acc[i][j];
+      }
+    }
+    return;
   }
   const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
   const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
@@ -89,11 +107,65 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(GemmArgs<R> a) {
   }
 }
 
+// Split-K: blockIdx.z = batch + nbatch * split; each split covers kc consecutive k.
 template <typename R, int BM, int BN, int BK, int TM, int TN>
-cudaError_t launch_cfg(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s) {
-  dim3 grid((nmax + BN - 1) / BN, (mmax + BM - 1) / BM, a.nbatch < 65535 ? a.nbatch : 65535);
-  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
-  cgemm_kernel<R, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(a);
+__global__ void __launch_bounds__(NT) cgemm_split_kernel(GemmArgs<R> a, int ksplit, int kc, int mmax, int nmax) {
+  const int b = blockIdx.z % a.nbatch, sp = blockIdx.z / a.nbatch;
+  const GemmDesc d = a.desc[b];
+  gemm_tile<R, BM, BN, BK, TM, TN>(a, d, blockIdx.y, blockIdx.x, sp * kc, (sp + 1) * kc, sp, b, mmax, nmax);
+}
+
+// Sum the split-K partials (fixed order) and apply the epilogue of gemm_tile.
+template <typename R>
+__global__ void __launch_bounds__(NT) splitk_reduce_kernel(GemmArgs<R> a, int ksplit, int mmax, int nmax) {
+  using C = c_t<R>;
+  const int b = blockIdx.y;
+  const GemmDesc d = a.desc[b];
+  const int n = d.n < 0 ? a.n_launch : d.n;
+  const int m = d.m;
+  const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
+  const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
+  for (int l = blockIdx.x * NT + threadIdx.x; l < m * n; l += gridDim.x * NT) {
+    const int i = l / n, j = l % n;
+    C acc = czero<R>();
+    for (int sp = 0; sp < ksplit; ++sp)
+      acc = cadd(acc, a.ws[(((long long)sp * a.nbatch + b) * mmax + i) * nmax + j]);
+    C v = cmul(a.alpha, acc);
+    if (a.C0) v = cadd(v, cmul(a.beta, a.C0[(long long)(d.c0_r + i) * a.ldc0 + d.c0_c + j]));
+    a.C[((long long)d.c_r + (rmap ? rmap[i] : i)) * a.ldc + d.c_c + (cmap ? cmap[j] : j)] = v;
+  }
+}
+
+template <typename R, int BM, int BN, int BK, int TM, int TN>
+cudaError_t launch_cfg(const GemmArgs<R>& a, int mmax, int nmax, int kmax, cudaStream_t s) {
+  const int gx = (nmax + BN - 1) / BN, gy = (mmax + BM - 1) / BM;
+  if (gx == 0 || gy == 0 || a.nbatch == 0) return cudaSuccess;
+  const long long blocks = (long long)gx * gy * a.nbatch;
+  int ksplit = 1;
+  if (kmax >= 4 * BK && a.ws && blocks < 2LL * a.num_sms) {
+    ksplit = (int)((2LL * a.num_sms + blocks - 1) / blocks);
+    ksplit = ksplit < kmax / (2 * BK) ? ksplit : kmax / (2 * BK);
+    ksplit = ksplit < 16 ? ksplit : 16;
+    while (ksplit > 1 && ((long long)ksplit * a.nbatch > 65535 ||
+                          (long long)ksplit * a.nbatch * mmax * nmax > a.ws_elems))
+      --ksplit;
+  }
+  if (ksplit <= 1) {
+    dim3 grid(gx, gy, a.nbatch < 65535 ? a.nbatch : 65535);
+    cgemm_kernel<R, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+  }
+  int kc = (kmax + ksplit - 1) / ksplit;
+  kc = (kc + BK - 1) / BK * BK;
+  ksplit = (kmax + kc - 1) / kc;
+  dim3 grid(gx, gy, a.nbatch * ksplit);
+  cgemm_split_kernel<R, BM, BN, BK, TM, TN><<<grid, NT, 0, s>>>(a, ksplit, kc, mmax, nmax);
+  note_launch();
+  int rb = (mmax * nmax + NT - 1) / NT;
+  rb = rb < 64 ? rb : 64;
+  dim3 rgrid(rb, a.nbatch);
+  splitk_reduce_kernel<R><<<rgrid, NT, 0, s>>>(a, ksplit, mmax, nmax);
   note_launch();
   return cudaGetLastError();
 }
@@ -264,12 +336,19 @@ void set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 template <typename R>
-cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s) {
+cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
-  if (nmax <= 16) return launch_cfg<R, 64, 16, 16, 4, 1>(a, mmax, nmax, s);
-  if (nmax <= 32) return launch_cfg<R, 64, 32, 8, 4, 2>(a, mmax, nmax, s);
-  if (mmax <= 32) return launch_cfg<R, 32, 32, 8, 2, 2>(a, mmax, nmax, s);
-  return launch_cfg<R, 64, 64, 8, 4, 4>(a, mmax, nmax, s);
+  if (nmax <= 16) {
+    if (mmax <= 16) return launch_cfg<R, 16, 16, 16, 1, 1>(a, mmax, nmax, kmax, s);
+    if (mmax <= 32) return launch_cfg<R, 32, 16, 16, 2, 1>(a, mmax, nmax, kmax, s);
+    return launch_cfg<R, 64, 16, 16, 4, 1>(a, mmax, nmax, kmax, s);
+  }
+  if (nmax <= 32) {
+    if (mmax <= 32) return launch_cfg<R, 32, 32, 8, 2, 2>(a, mmax, nmax, kmax, s);
+    return launch_cfg<R, 64, 32, 8, 4, 2>(a, mmax, nmax, kmax, s);
+  }
+  if (mmax <= 32) return launch_cfg<R, 32, 32, 8, 2, 2>(a, mmax, nmax, kmax, s);
+  return launch_cfg<R, 64, 64, 8, 4, 4>(a, mmax, nmax, kmax, s);
 }
 
 template <typename R>
@@ -311,8 +390,8 @@ cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, in
   return cudaGetLastError();
 }
 
-template cudaError_t launch_gemm<double>(const GemmArgs<double>&, int, int, cudaStream_t);
-template cudaError_t launch_gemm<float>(const GemmArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_gemm<double>(const GemmArgs<double>&, int, int, cudaStream_t, int);
+template cudaError_t launch_gemm<float>(const GemmArgs<float>&, int, int, cudaStream_t, int);
 template cudaError_t gj_invert<double>(double2*, int, int, int*, double2*, int*, cudaStream_t);
 template cudaError_t gj_invert<float>(float2*, int, int, int*, float2*, int*, cudaStream_t);
 

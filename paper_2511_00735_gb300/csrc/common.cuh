@@ -92,10 +92,15 @@ template <typename R> struct GemmArgs {
   int nbatch;
   const int* maps;       // device
   int n_launch;          // value of n for descriptors with n < 0
+  // split-K workspace (optional): partial products [split][batch][mmax][nmax]
+  c_t<R>* ws = nullptr;
+  long long ws_elems = 0;
+  int num_sms = 148;
 };
 
+// kmax > 0 enables splitting K across blocks when the grid would not fill the GPU.
 template <typename R>
-cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s);
+cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax = 0);
 
 // Gauss-Jordan inversion of nmat augmented matrices W = [S | I] (m x 2m, row-major,
 // matrix b at W + b*m*2m).  Partial pivoting; on exit W(:, m:2m) = S^{-1}.

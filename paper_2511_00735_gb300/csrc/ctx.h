@@ -39,8 +39,8 @@ struct Level {               // merge l: stage l-1 -> stage l
 
 struct Coarse {
   int n_int = 0;             // interior (unknown) positions over all coarse subdomains
-  int* d_mask = nullptr;     // [nsub] interior-side bits
-  int off[5] = {0, 0, 0, 0, 0};
+  int max_int = 0;           // largest interior count of one coarse subdomain
+  GemmDesc* d_cdesc = nullptr;  // [nsub] T_int,int g_int GEMM per coarse subdomain
   int* d_cnb = nullptr;      // [nsub*n] stage row across the face (-1 on the physical boundary)
   int* d_upos = nullptr;     // [n_int] stage row of unknown u
   int* d_ucnb = nullptr;     // [n_int] stage row across from unknown u
@@ -98,6 +98,8 @@ struct hps_ctx {
   std::vector<hps::Level> levels;  // levels[l] for l = 1..L_exact (levels[0] unused)
   hps::Coarse coarse;
   int nrhs_cap = 0;                // sweep buffers sized for this many columns
+  void* gemm_ws = nullptr;         // split-K partial products
+  size_t gemm_ws_elems = 0;
   void* ws_X1 = nullptr;           // merge workspaces
   void* ws_X2 = nullptr;
   size_t ws_X_elems = 0;

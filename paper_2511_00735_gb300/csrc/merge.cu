@@ -65,7 +65,7 @@ size_t csize(int prec) { return prec == HPS_FP64 ? sizeof(double2) : sizeof(floa
 template <typename R>
 cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long lda, const void* B, long long ldb,
                  const void* C0, long long ldc0, void* C, long long ldc, double alpha, const int* maps, int mmax,
-                 int nmax, int n_launch) {
+                 int nmax, int n_launch, int kmax = 0) {
   GemmArgs<R> a;
   a.A = static_cast<const c_t<R>*>(A);
   a.B = static_cast<const c_t<R>*>(B);
@@ -81,7 +81,10 @@ cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long
   a.nbatch = nb;
   a.maps = maps;
   a.n_launch = n_launch;
-  return launch_gemm<R>(a, mmax, nmax, c->stream);
+  a.ws = static_cast<c_t<R>*>(c->gemm_ws);
+  a.ws_elems = (long long)c->gemm_ws_elems;
+  a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
+  return launch_gemm<R>(a, mmax, nmax, c->stream, kmax);
 }
 
 GemmDesc D(int a_r, int a_c, int b_r, int b_c, int c0_r, int c0_c, int c_r, int c_c, int m, int n, int k, int rmap = -1,
@@ -130,7 +133,15 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
             for (int i = lo; i < hi; ++i) order.push_back(i);
           }
         } else {
-          for (int i = 0; i < S.n; ++i) order.push_back(i);
+          // coarse level: interior sides first (l, r, b, t order among them), then the physical ones
+          const bool inner[4] = {sx > 0, sx < S.gx - 1, sy > 0, sy < S.gy - 1};
+          for (int pass = 0; pass < 2; ++pass)
+            for (int sd = 0; sd < 4; ++sd) {
+              if (inner[sd] != (pass == 0)) continue;
+              int lo, hi;
+              side_range(S.a, S.b, q, sd, lo, hi);
+              for (int i = lo; i < hi; ++i) order.push_back(i);
+            }
         }
         for (int i = 0; i < S.n; ++i) {
           const int e = nat[order[i]];
@@ -253,6 +264,9 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     if (!c->ws_X1 || !c->ws_X2 || !c->d_piv || !c->d_lu) return fail(c, HPS_ENOMEM, "merge workspace");
     c->ws_X_elems = x_elems;
   }
+  c->gemm_ws_elems = (size_t)1 << 22;  // split-K partials
+  c->gemm_ws = dev_alloc(c, sizeof(C) * c->gemm_ws_elems);
+  if (!c->gemm_ws) return fail(c, HPS_ENOMEM, "split-K workspace");
   // ---- stage 0 maps from the FP64 leaf maps ----
   {
     const Stage& S0 = c->stages[0];
@@ -275,37 +289,36 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     const GemmDesc* md = Lv.d_mdesc;
     const void* T0 = P0.T;
     HPS_CK(c, eye2<R>(static_cast<C*>(Lv.W), m, NP, c->stream));
-    HPS_CK(c, gemm<R>(c, md + MS * NP, NP, T0, n, T0, n, Lv.W, 2 * m, Lv.W, 2 * m, -1.0, nullptr, m, m, m));
+    HPS_CK(c, gemm<R>(c, md + MS * NP, NP, T0, n, T0, n, Lv.W, 2 * m, Lv.W, 2 * m, -1.0, nullptr, m, m, m, m));
     HPS_CK(c, gj_invert<R>(static_cast<C*>(Lv.W), m, NP, c->d_piv, static_cast<C*>(c->d_lu), c->d_flag, c->stream));
-    HPS_CK(c, gemm<R>(c, md + MR * NP, NP, T0, n, T0, n, nullptr, 0, c->ws_X2, 2 * p, -1.0, nullptr, m, p, p));
+    HPS_CK(c, gemm<R>(c, md + MR * NP, NP, T0, n, T0, n, nullptr, 0, c->ws_X2, 2 * p, -1.0, nullptr, m, p, p, m));
     HPS_CK(c, gemm<R>(c, md + MX1A * NP, NP, Lv.W, 2 * m, c->ws_X2, 2 * p, nullptr, 0, c->ws_X1, 2 * p, 1.0, nullptr, m,
-                      p, p));
-    HPS_CK(c, gemm<R>(c, md + MX1B * NP, NP, Lv.W, 2 * m, T0, n, nullptr, 0, c->ws_X1, 2 * p, 1.0, nullptr, m, p, p));
-    HPS_CK(c, gemm<R>(c, md + MX2A * NP, NP, T0, n, c->ws_X1, 2 * p, T0, n, c->ws_X2, 2 * p, -1.0, nullptr, m, p, p));
+                      p, p, m));
+    HPS_CK(c, gemm<R>(c, md + MX1B * NP, NP, Lv.W, 2 * m, T0, n, nullptr, 0, c->ws_X1, 2 * p, 1.0, nullptr, m, p, p, m));
+    HPS_CK(c, gemm<R>(c, md + MX2A * NP, NP, T0, n, c->ws_X1, 2 * p, T0, n, c->ws_X2, 2 * p, -1.0, nullptr, m, p, p, m));
     HPS_CK(c, gemm<R>(c, md + MX2B * NP, NP, T0, n, c->ws_X1, 2 * p, nullptr, 0, c->ws_X2, 2 * p, -1.0, nullptr, m, p,
-                      p));
+                      p, m));
     void* Tn = P1.T;
-    HPS_CK(c, gemm<R>(c, md + MOA * NP, NP, T0, n, c->ws_X1, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
-    HPS_CK(c, gemm<R>(c, md + MOB * NP, NP, T0, n, c->ws_X1, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
-    HPS_CK(c, gemm<R>(c, md + MOC * NP, NP, T0, n, c->ws_X2, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
-    HPS_CK(c, gemm<R>(c, md + MOD * NP, NP, T0, n, c->ws_X2, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p));
+    HPS_CK(c, gemm<R>(c, md + MOA * NP, NP, T0, n, c->ws_X1, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
+    HPS_CK(c, gemm<R>(c, md + MOB * NP, NP, T0, n, c->ws_X1, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
+    HPS_CK(c, gemm<R>(c, md + MOC * NP, NP, T0, n, c->ws_X2, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
+    HPS_CK(c, gemm<R>(c, md + MOD * NP, NP, T0, n, c->ws_X2, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
   }
   // ---- coarse level ----
   {
     const Stage& Sc = c->stages[L_exact];
     Coarse& cc = c->coarse;
-    int lo, hi;
-    for (int sd = 0; sd < 4; ++sd) {
-      side_range(Sc.a, Sc.b, q, sd, lo, hi);
-      cc.off[sd] = lo;
-      cc.off[sd + 1] = hi;
-    }
-    std::vector<int> mask(Sc.nsub), cnb((size_t)Sc.nsub * Sc.n, -1), upos, ucnb;
+    std::vector<int> cnb((size_t)Sc.nsub * Sc.n, -1), upos, ucnb;
+    std::vector<GemmDesc> cdesc(Sc.nsub);
+    int max_int = 0;
     for (int sy = 0; sy < Sc.gy; ++sy)
       for (int sx = 0; sx < Sc.gx; ++sx) {
         const int s = sx + Sc.gx * sy;
-        mask[s] = (sx > 0 ? 1 : 0) | (sx < Sc.gx - 1 ? 2 : 0) | (sy > 0 ? 4 : 0) | (sy < Sc.gy - 1 ? 8 : 0);
+        const int ni = ((sx > 0) + (sx < Sc.gx - 1)) * Sc.b * q + ((sy > 0) + (sy < Sc.gy - 1)) * Sc.a * q;
+        cdesc[s] = D(s * Sc.n, 0, s * Sc.n, 0, 0, 0, s * Sc.n, 0, ni, -1, ni);
+        max_int = std::max(max_int, ni);
       }
+    cc.max_int = max_int;
     std::vector<int> owner(c->n_es, -1);
     for (int s = 0; s < Sc.nsub; ++s)
       for (int i = 0; i < Sc.n; ++i) owner[Sc.es[(size_t)s * Sc.n + i]] = s;
@@ -318,15 +331,16 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
         const int d = inv[L_exact][en];
         if (so < 0 || so == s || d < 0) return fail(c, HPS_ECUDA, "internal: coarse neighbour map");
         cnb[r] = so * Sc.n + d;
+        if (i >= cdesc[s].m) return fail(c, HPS_ECUDA, "internal: coarse interior order");
         upos.push_back((int)r);
       }
     cc.n_int = (int)upos.size();
     for (int u = 0; u < cc.n_int; ++u) ucnb.push_back(cnb[upos[u]]);
-    cc.d_mask = dev_upload(c, mask);
+    cc.d_cdesc = dev_upload(c, cdesc);
     cc.d_cnb = dev_upload(c, cnb);
     cc.d_upos = dev_upload(c, upos);
     cc.d_ucnb = dev_upload(c, ucnb);
-    if (!cc.d_mask || !cc.d_cnb || !cc.d_upos || !cc.d_ucnb) return fail(c, HPS_ENOMEM, "coarse maps");
+    if (!cc.d_cdesc || !cc.d_cnb || !cc.d_upos || !cc.d_ucnb) return fail(c, HPS_ENOMEM, "coarse maps");
     cc.exact = exact != 0;
     if (cc.exact && cc.n_int > 0) {
       const int ni = cc.n_int;
@@ -499,7 +513,8 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
   HPS_CK(c, bscale<R>(V, w, nrm, nullptr, rows, nrhs, st));
   for (int j = 0; j < k; ++j) {
     C* Vj = V + j * vs;
-    HPS_CK(c, coarse_apply<R>(W, static_cast<const C*>(Sc.T), Vj, cc.d_mask, cc.off, Sc.nsub, Sc.n, nrhs, st));
+    HPS_CK(c, gemm<R>(c, cc.d_cdesc, Sc.nsub, Sc.T, Sc.n, Vj, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int, nrhs,
+                      nrhs, cc.max_int));
     HPS_CK(c, swap_add<R>(w, Vj, W, cc.d_cnb, rows, nrhs, st));
     HPS_CK(c, bdot<R>(V, vs, j + 1, w, rows, nrhs, part, h1, 0, st));
     HPS_CK(c, (bupdate<R, R>(w, V, vs, j + 1, h1, rows, nrhs, R(-1), st)));
@@ -534,15 +549,15 @@ int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) 
     const GemmDesc* sd = Lv.d_sdesc;
     const void* T0 = P0.T;
     void* v0 = P0.vec;
-    HPS_CK(c, gemm<R>(c, sd + UP1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + UP1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp, nrhs, -1.0, nullptr, m, nrhs, nrhs, m));
     HPS_CK(c, gemm<R>(c, sd + UP2 * NP, NP, Lv.W, 2 * m, c->sw_tmp, nrhs, nullptr, 0, c->sw_zt, nrhs, 1.0, nullptr, m,
-                      nrhs, nrhs));
+                      nrhs, nrhs, m));
     HPS_CK(c, gemm<R>(c, sd + UP3 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, c->sw_zt, nrhs, -1.0, nullptr, m, nrhs,
-                      nrhs));
+                      nrhs, m));
     HPS_CK(c, gemm<R>(c, sd + UP4 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, P1.vec, nrhs, -1.0, Lv.d_dst, p, nrhs,
-                      nrhs));
+                      nrhs, m));
     HPS_CK(c, gemm<R>(c, sd + UP5 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, P1.vec, nrhs, -1.0, Lv.d_dst, p, nrhs,
-                      nrhs));
+                      nrhs, m));
   }
   rc = coarse_solve<R>(c, nrhs, k);
   if (rc != HPS_OK) return rc;
@@ -556,13 +571,13 @@ int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) 
     void* v0 = P0.vec;
     HPS_CK(c, (scatter_rows<R, R>(static_cast<C*>(v0), static_cast<const C*>(P1.vec), Lv.d_up,
                                   (long long)P1.nsub * P1.n, nrhs, st)));
-    HPS_CK(c, gemm<R>(c, sd + DN1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs));
-    HPS_CK(c, gemm<R>(c, sd + DN2 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+    HPS_CK(c, gemm<R>(c, sd + DN1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs, p));
+    HPS_CK(c, gemm<R>(c, sd + DN2 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs, p));
     HPS_CK(c, gemm<R>(c, sd + DN3 * NP, NP, T0, n, c->sw_tmp2, nrhs, c->sw_tmp2, nrhs, c->sw_tmp, nrhs, -1.0, nullptr,
-                      m, nrhs, nrhs));
+                      m, nrhs, nrhs, m));
     HPS_CK(c, gemm<R>(c, sd + DN4 * NP, NP, Lv.W, 2 * m, c->sw_tmp, nrhs, nullptr, 0, v0, nrhs, 1.0, nullptr, m, nrhs,
-                      nrhs));
-    HPS_CK(c, gemm<R>(c, sd + DN5 * NP, NP, T0, n, v0, nrhs, c->sw_tmp2, nrhs, v0, nrhs, -1.0, nullptr, m, nrhs, nrhs));
+                      nrhs, m));
+    HPS_CK(c, gemm<R>(c, sd + DN5 * NP, NP, T0, n, v0, nrhs, c->sw_tmp2, nrhs, v0, nrhs, -1.0, nullptr, m, nrhs, nrhs, m));
   }
   HPS_CK(c, (scatter_rows<R, double>(z_es, static_cast<const C*>(S0.vec), S0.d_es, (long long)S0.nsub * S0.n, nrhs,
                                      st)));

@@ -197,47 +197,8 @@ cudaError_t permute_blocks(c_t<RD>* dst, const c_t<RS>* src, const int* map, int
 }
 
 // ---------------------------------------------------------------------------
-// Coarse level.  W_s = T_s g_s restricted to interior sides (side bit set in
-// mask[s]); sides are the contiguous ranges [off[0],off[1]) .. [off[3],off[4]).
+// Coarse level (the T_c g products run as batched GEMMs on interior-first storage).
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(NT) coarse_apply_kernel(c_t<R>* __restrict__ W, const c_t<R>* __restrict__ T,
-                                                          const c_t<R>* __restrict__ g, const int* __restrict__ mask,
-                                                          int4 off03, int off4, int n, int nrhs, int rows_per_block) {
-  const int s = blockIdx.y;
-  const int msk = mask[s];
-  const int off[5] = {off03.x, off03.y, off03.z, off03.w, off4};
-  const int r0 = blockIdx.x * rows_per_block;
-  const c_t<R>* Ts = T + (long long)s * n * n;
-  const c_t<R>* gs = g + (long long)s * n * nrhs;
-  for (int l = threadIdx.x; l < rows_per_block * nrhs; l += NT) {
-    const int i = r0 + l / nrhs, r = l % nrhs;
-    if (i >= n) continue;
-    int side_i = 0;
-    while (side_i < 3 && i >= off[side_i + 1]) ++side_i;
-    c_t<R> acc = czero<R>();
-    if ((msk >> side_i) & 1) {
-      const c_t<R>* Tr = Ts + (long long)i * n;
-      for (int sd = 0; sd < 4; ++sd) {
-        if (!((msk >> sd) & 1)) continue;
-        for (int j = off[sd]; j < off[sd + 1]; ++j) cfma(acc, Tr[j], gs[(long long)j * nrhs + r]);
-      }
-    }
-    W[((long long)s * n + i) * nrhs + r] = acc;
-  }
-}
-
-template <typename R>
-cudaError_t coarse_apply(c_t<R>* W, const c_t<R>* T, const c_t<R>* g, const int* mask, const int* off, int nsub, int n,
-                         int nrhs, cudaStream_t s) {
-  const int rpb = NT / nrhs > 0 ? (NT / nrhs) : 1;
-  dim3 grid((n + rpb - 1) / rpb, nsub);
-  coarse_apply_kernel<R><<<grid, NT, 0, s>>>(W, T, g, mask, make_int4(off[0], off[1], off[2], off[3]), off[4], n, nrhs,
-                                             rpb);
-  note_launch();
-  return cudaGetLastError();
-}
-
 // out_p = nb(p) >= 0 ? (a ? a_p : 0) + b_{nb(p)} : 0
 template <typename R>
 __global__ void swap_add_kernel(c_t<R>* __restrict__ out, const c_t<R>* __restrict__ a, const c_t<R>* __restrict__ b,
@@ -295,11 +256,17 @@ __global__ void __launch_bounds__(NT) bdot_partial_kernel(const c_t<R>* __restri
 template <typename R>
 __global__ void bdot_final_kernel(const c_t<R>* __restrict__ partial, int nblk, int nvec, int nrhs,
                                   c_t<R>* __restrict__ out, int accumulate) {
-  const int l = blockIdx.x * NT + threadIdx.x;
-  if (l >= nvec * nrhs) return;
+  // one warp per output: lanes stride over the block partials, fixed-order butterfly sum
+  const int warp = (blockIdx.x * NT + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (warp >= nvec * nrhs) return;
   c_t<R> acc = czero<R>();
-  for (int b = 0; b < nblk; ++b) acc = cadd(acc, partial[(long long)b * nvec * nrhs + l]);
-  out[l] = accumulate ? cadd(out[l], acc) : acc;
+  for (int b = lane; b < nblk; b += 32) acc = cadd(acc, partial[(long long)b * nvec * nrhs + warp]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if (lane == 0) out[warp] = accumulate ? cadd(out[warp], acc) : acc;
 }
 
 int bdot_blocks(long long rows) {
@@ -318,7 +285,7 @@ cudaError_t bdot(const c_t<R>* V, long long vstride, int nvec, const c_t<R>* w, 
   const long long chunk = (rows + nblk - 1) / nblk;
   bdot_partial_kernel<R><<<nblk, NT, 0, s>>>(V, vstride, nvec, w, rows, nrhs, rpad, partial, chunk);
   note_launch();
-  bdot_final_kernel<R><<<(nvec * nrhs + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nvec, nrhs, out, accumulate);
+  bdot_final_kernel<R><<<(nvec * nrhs * 32 + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nvec, nrhs, out, accumulate);
   note_launch();
   return cudaGetLastError();
 }
@@ -349,13 +316,15 @@ cudaError_t bupdate(c_t<R>* w, const c_t<R>* V, long long vstride, int nvec, con
 template <typename R>
 __global__ void bscale_kernel(c_t<R>* __restrict__ out, const c_t<R>* __restrict__ w, const c_t<R>* __restrict__ dots,
                               const R* __restrict__ floor, long long rows, int nrhs) {
-  const long long tot = rows * nrhs;
-  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
-    const int r = (int)(l % nrhs);
+  __shared__ R inv[NT];
+  for (int r = threadIdx.x; r < nrhs; r += NT) {
     const R nrm = sqrt(dots[r].x > R(0) ? dots[r].x : R(0));
-    const bool ok = nrm > (floor ? floor[r] : R(0));
-    out[l] = ok ? cscale(w[l], R(1) / nrm) : czero<R>();
+    inv[r] = nrm > (floor ? floor[r] : R(0)) ? R(1) / nrm : R(0);
   }
+  __syncthreads();
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT)
+    out[l] = cscale(w[l], inv[(int)(l % nrhs)]);
 }
 template <typename R>
 cudaError_t bscale(c_t<R>* out, const c_t<R>* w, const c_t<R>* dots, const R* floor, long long rows, int nrhs,
@@ -502,8 +471,6 @@ cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s) {
 }
 
 #define HPS_INST_R(R)                                                                                                   \
-  template cudaError_t coarse_apply<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const int*, const int*, int, int, int,   \
-                                       cudaStream_t);                                                                   \
   template cudaError_t swap_add<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const int*, long long, int, cudaStream_t);   \
   template cudaError_t bdot<R>(const c_t<R>*, long long, int, const c_t<R>*, long long, int, c_t<R>*, c_t<R>*, int,     \
                                cudaStream_t);                                                                           \

@@ -40,9 +40,6 @@ cudaError_t permute_blocks(c_t<RD>* dst, const c_t<RS>* src, const int* map, int
 
 // coarse level
 template <typename R>
-cudaError_t coarse_apply(c_t<R>* W, const c_t<R>* T, const c_t<R>* g, const int* mask, const int* off, int nsub, int n,
-                         int nrhs, cudaStream_t s);
-template <typename R>
 cudaError_t swap_add(c_t<R>* out, const c_t<R>* a, const c_t<R>* b, const int* nbr, long long rows, int nrhs,
                      cudaStream_t s);
 
