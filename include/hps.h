@@ -216,6 +216,31 @@ int hps_profile(hps_ctx* ctx, int enable);
  * NULL.  Synchronises the context's stream. */
 int hps_profile_read(hps_ctx* ctx, double* ms, long long* launches, long long* calls);
 
+/* Leaf ItI maps without any device allocation (no counterpart in the paper:
+ * a deployment variant of hps_build_leaves).  For callers that cannot
+ * allocate device memory while they run, e.g. a process whose device memory
+ * all belongs to its own pool, or a loop that must not call cudaMalloc /
+ * cudaFree because those calls can synchronise the device.
+ *
+ *   device, stream  where to run (stream: a cudaStream_t, NULL = legacy default)
+ *   N               GLL order, 2 <= N <= 16 (larger orders exceed the static
+ *                   workspace: HPS_EINVAL)
+ *   h, eta          element width and impedance parameter
+ *   c               device [E][(N+1)^2]: c = kappa^2 (1 - b) at the element
+ *                   nodes (node order of hps_node_coords)
+ *   T               device output [E][4(N-1)][4(N-1)] complex128, side order
+ *                   l, r, b, t (the same maps hps_build_leaves keeps)
+ *
+ * All workspace lives in one file-scope device array of about 4.6 MB that
+ * every GPU which loads the library holds until the process exits.  Its
+ * device address is looked up on the first call on each device, with that
+ * device current.  Every call shares the array: calls whose work overlaps on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  The call synchronises `stream` once to read the breakdown flag:
+ * HPS_ENUMERIC when an interior operator is not positive definite. */
+int hps_leaf_maps_noalloc(int device, void* stream, int N, double h, double eta, const double* c, int E,
+                          void* T);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ _STATUS = {0: "HPS_OK", -1: "HPS_EINVAL", -2: "HPS_ENOMEM", -3: "HPS_ENOTBUILT",
 EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "hps_strerror", "hps_mesh",
            "hps_sizes", "hps_node_coords", "hps_boundary_points", "hps_index_maps", "hps_set_coeff",
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
-           "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read"]
+           "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
+           "hps_leaf_maps_noalloc"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "hps_kernel_launches": (ll, []),
         "hps_profile": (i, [vp, i]),
         "hps_profile_read": (i, [vp, vp, vp, vp]),
+        "hps_leaf_maps_noalloc": (i, [i, vp, i, d, d, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
