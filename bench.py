@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "64x64 elements, N=16 GLL, kappa=100, 1 seeded bump, 16 plane-wave RHS, L_exact=10, 5 coarse GMRES steps"
 FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (nominal, vector = tensor rate)
+# dram read + write bytes of one leaf_kernel launch at 64x64, N=16 from the committed ncu capture
+# (profiles/leaf_kernel_64x64_N16.md); must be reset to None whenever leaf.cu changes.
+LEAF_TRAFFIC_BYTES = 191.9e6
 
 
 def load_peaks():
@@ -396,7 +399,8 @@ def main():
         cand.append((leaf_ms, {"kernel": "leaf_kernel (leaf ItI maps, FP64)", "bound": "alu",
                                "achieved": fl / (per / 1e3) / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
                                "unit": "TFLOP/s", "frac": fl / (per / 1e3) / FP64_PEAK_NOMINAL,
-                               "traffic": None, "flops_per_launch": fl, "ms_per_launch": per,
+                               "traffic": LEAF_TRAFFIC_BYTES if prob.nx == 64 and N == 16 else None,
+                               "flops_per_launch": fl, "ms_per_launch": per,
                                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)"}))
     if mv_calls:
         per = mv_ms / mv_calls
