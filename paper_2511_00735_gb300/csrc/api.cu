@@ -146,7 +146,8 @@ void free_tree(hps_ctx* c) {
     FREE(s.d_es); FREE(s.T); FREE(s.vec);
   }
   for (auto& l : c->levels) {
-    FREE(l.d_dst); FREE(l.d_up); FREE(l.W); FREE(l.d_mdesc); FREE(l.d_sdesc);
+    FREE(l.d_dst); FREE(l.d_up); FREE(l.W); FREE(l.U); FREE(l.Dm); FREE(l.d_xmap); FREE(l.d_mdesc);
+    FREE(l.d_sdesc);
   }
   c->stages.clear();
   c->levels.clear();
@@ -155,7 +156,7 @@ void free_tree(hps_ctx* c) {
   c->coarse = Coarse();
   FREE(c->gemm_ws); c->gemm_ws_elems = 0;
   FREE(c->ws_X1); FREE(c->ws_X2); FREE(c->d_piv); FREE(c->d_lu);
-  FREE(c->sw_tmp); FREE(c->sw_tmp2); FREE(c->sw_zt);
+  FREE(c->sw_x); FREE(c->ws_G); FREE(c->d_eye);
   FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);
   FREE(c->cg_nrm); FREE(c->cg_y); FREE(c->cg_g); FREE(c->cg_s); FREE(c->cg_part);
   FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c);

@@ -36,7 +36,6 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& 
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = czero<R>();
   const C* Ab = a.A + (long long)d.a_r * a.lda + d.a_c;
-  const C* Bb = a.B + (long long)d.b_r * a.ldb + d.b_c;
   for (int k0 = kb; k0 < k; k0 += BK) {
     for (int l = tid; l < BM * BK; l += NT) {
       const int i = l / BK, kk = l % BK;
@@ -46,7 +45,8 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& 
     for (int l = tid; l < BK * BN; l += NT) {
       const int kk = l / BN, j = l % BN;
       const int gk = k0 + kk, gj = col0 + j;
-      Bs[kk][j] = (gk < k && gj < n) ? Bb[(long long)gk * a.ldb + gj] : czero<R>();
+      const long long br = (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+      Bs[kk][j] = (gk < k && gj < n) ? a.B[br * a.ldb + d.b_c + gj] : czero<R>();
     }
     __syncthreads();
 #pragma unroll
@@ -90,7 +90,8 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<R>& a, const GemmDesc& 
       if (gj >= n) continue;
       C v = cmul(a.alpha, acc[i][j]);
       if (a.C0) {
-        const C c0 = a.C0[(long long)(d.c0_r + gi) * a.ldc0 + d.c0_c + gj];
+        const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+        const C c0 = a.C0[cr * a.ldc0 + d.c0_c + gj];
         v = cadd(v, cmul(a.beta, c0));
       }
       const long long ocol = (long long)d.c_c + (cmap ? cmap[gj] : gj);
@@ -131,7 +132,10 @@ __global__ void __launch_bounds__(NT) splitk_reduce_kernel(GemmArgs<R> a, int ks
     for (int sp = 0; sp < ksplit; ++sp)
       acc = cadd(acc, a.ws[(((long long)sp * a.nbatch + b) * mmax + i) * nmax + j]);
     C v = cmul(a.alpha, acc);
-    if (a.C0) v = cadd(v, cmul(a.beta, a.C0[(long long)(d.c0_r + i) * a.ldc0 + d.c0_c + j]));
+    if (a.C0) {
+      const long long cr = (d.mc2 > 0 && i >= d.mc2) ? (long long)d.c0_r2 + (i - d.mc2) : (long long)d.c0_r + i;
+      v = cadd(v, cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + j]));
+    }
     a.C[((long long)d.c_r + (rmap ? rmap[i] : i)) * a.ldc + d.c_c + (cmap ? cmap[j] : j)] = v;
   }
 }
@@ -315,6 +319,7 @@ __global__ void __launch_bounds__(NT) gj_update_kernel(c_t<R>* W, int m, int k0,
   d.c0_r = d.c_r = base + r0;
   d.c0_c = d.c_c = k0 + kb;
   d.rmap = d.cmap = -1;
+  d.b_r2 = d.kb2 = d.c0_r2 = d.mc2 = 0;
   GemmArgs<R> a;
   a.A = a.B = a.C0 = W;
   a.C = W;

@@ -75,10 +75,14 @@ __host__ __device__ __forceinline__ c_t<D> cvt(c_t<S> a) {
 // matrices are row-major complex.  rmap / cmap >= 0 give offsets into the
 // launch's map array: row i of C is written to row c_r + map[rmap + i], column
 // j to c_c + map[cmap + j].  n < 0 means "the launch's n" (number of RHS).
+// Two-segment operands: when kb2 > 0, rows k >= kb2 of B come from row
+// b_r2 + (k - kb2); when mc2 > 0, rows i >= mc2 of C0 come from row
+// c0_r2 + (i - mc2) (used to read two merge children as one operand).
 struct GemmDesc {
   int a_r, a_c, b_r, b_c, c0_r, c0_c, c_r, c_c;
   int m, n, k;
   int rmap, cmap;
+  int b_r2, kb2, c0_r2, mc2;
 };
 
 template <typename R> struct GemmArgs {

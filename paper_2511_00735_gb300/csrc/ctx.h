@@ -13,8 +13,12 @@
 namespace hps {
 
 // Merge-level GEMM roles (see merge.cu for the formulas).
-enum MergeRole { MS = 0, MR, MX1A, MX1B, MX2A, MX2B, MOA, MOB, MOC, MOD, N_MROLE };
-enum SweepRole { UP1 = 0, UP2, UP3, UP4, UP5, DN1, DN2, DN3, DN4, DN5, N_SROLE };
+enum MergeRole {
+  MS = 0, MR, MX1A, MX1B, MX2A, MX2B, MOA, MOB, MOC, MOD,  // merged map T_pair
+  PG1A, PG1B, PG2A, PG2B, PU1, PU2, PD1, PD2, PD3, PD4,     // sweep operators U, D
+  N_MROLE
+};
+enum SweepRole { SUP = 0, SDN, N_SROLE };
 
 struct Stage {
   int a = 0, b = 0;          // element block size of each subdomain
@@ -33,6 +37,9 @@ struct Level {               // merge l: stage l-1 -> stage l
   int* d_dst = nullptr;      // [npairs][2p] storage position in the merged subdomain of [E1; E2]
   int* d_up = nullptr;       // [npairs * 2p] merged row -> child row (down-sweep copy)
   void* W = nullptr;         // [npairs][m][2m]: [S | I] -> [. | S^{-1}]
+  void* U = nullptr;         // [npairs][2p][2m] restriction: rho'_E = rho_E - U f
+  void* Dm = nullptr;        // [npairs][2m][2n] prolongation: x = Dm [child1 ; child2]
+  int* d_xmap = nullptr;     // [npairs * 2m] row of x -> child row (interface rows)
   GemmDesc* d_mdesc = nullptr;  // [N_MROLE][npairs]
   GemmDesc* d_sdesc = nullptr;  // [N_SROLE][npairs]
 };
@@ -105,9 +112,10 @@ struct hps_ctx {
   size_t ws_X_elems = 0;
   int* d_piv = nullptr;
   void* d_lu = nullptr;
-  void* sw_tmp = nullptr;          // sweep temporaries [max npairs*m][nrhs], [max npairs*2m][nrhs]
-  void* sw_tmp2 = nullptr;
-  void* sw_zt = nullptr;
+  void* sw_x = nullptr;            // down-sweep interface solution [max npairs*2m][nrhs]
+  void* ws_G = nullptr;            // merge workspace: G = A^{-1} in [f1 | f2] column order
+  void* d_eye = nullptr;           // identity of the largest interface size
+  int eye_ld = 0;
   // coarse GMRES
   int cg_k = 0, cg_nrhs = 0;
   void *cg_V = nullptr, *cg_w = nullptr, *cg_W = nullptr, *cg_H = nullptr, *cg_h1 = nullptr, *cg_h2 = nullptr;

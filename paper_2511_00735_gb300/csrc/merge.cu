@@ -92,6 +92,13 @@ GemmDesc D(int a_r, int a_c, int b_r, int b_c, int c0_r, int c0_c, int c_r, int 
   GemmDesc d;
   d.a_r = a_r; d.a_c = a_c; d.b_r = b_r; d.b_c = b_c; d.c0_r = c0_r; d.c0_c = c0_c; d.c_r = c_r; d.c_c = c_c;
   d.m = m; d.n = n; d.k = k; d.rmap = rmap; d.cmap = cmap;
+  d.b_r2 = d.kb2 = d.c0_r2 = d.mc2 = 0;
+  return d;
+}
+
+// with two-segment B (rows k >= kb2 from b_r2 + k - kb2) and C0 (rows i >= mc2 from c0_r2 + i - mc2)
+GemmDesc D2(GemmDesc d, int b_r2, int kb2, int c0_r2, int mc2) {
+  d.b_r2 = b_r2; d.kb2 = kb2; d.c0_r2 = c0_r2; d.mc2 = mc2;
   return d;
 }
 
@@ -224,18 +231,32 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
       md[MOB * NP + P] = D(r1 + m, 0, x, p, 0, 0, t, 0, p, p, m, dm1, dm2);
       md[MOC * NP + P] = D(r2 + m, 0, x, 0, 0, 0, t, 0, p, p, m, dm2, dm1);
       md[MOD * NP + P] = D(r2 + m, 0, x, p, r2 + m, m, t, 0, p, p, m, dm2, dm2);
+      // sweep operators: G = A^{-1} with columns [f1 | f2] (rows g..g+2m of the G workspace),
+      // U = [T1_Ea G1 ; T2_Eb G2] (restriction), Dm = [G_f2 | -G_f2 T1_aE1 | G_f1 | -G_f1 T2_bE2]
+      const int g = P * 2 * m, u = P * 2 * p, dd = P * 2 * m;
+      md[PG1A * NP + P] = D(0, 0, 0, 0, w, m, g, 0, m, m, 0);          // G1[:, f1] = S^{-1}
+      md[PG1B * NP + P] = D(w, m, r2, 0, 0, 0, g, m, m, m, m);         // G1[:, f2] = -S^{-1} T2_bb
+      md[PG2A * NP + P] = D(r1, 0, g, 0, 0, 0, g + m, 0, m, m, m);     // G2[:, f1] = -T1_aa G1[:, f1]
+      md[PG2B * NP + P] = D(r1, 0, g, m, 0, 0, g + m, m, m, m, m);     // G2[:, f2] = I - T1_aa G1[:, f2]
+      md[PU1 * NP + P] = D(r1 + m, 0, g, 0, 0, 0, u, 0, p, 2 * m, m);  // U[E1] = T1_Ea G1
+      md[PU2 * NP + P] = D(r2 + m, 0, g + m, 0, 0, 0, u + p, 0, p, 2 * m, m);  // U[E2] = T2_Eb G2
+      md[PD1 * NP + P] = D(0, 0, 0, 0, g, m, dd, 0, 2 * m, m, 0);      // Dm[:, f2] = G[:, f2]
+      md[PD2 * NP + P] = D(g, m, r1, m, 0, 0, dd, m, 2 * m, p, m);     // Dm[:, e1] = -G[:, f2] T1_aE1
+      md[PD3 * NP + P] = D(0, 0, 0, 0, g, 0, dd, n, 2 * m, m, 0);      // Dm[:, f1] = G[:, f1]
+      md[PD4 * NP + P] = D(g, 0, r2, m, 0, 0, dd, n + m, 2 * m, p, m); // Dm[:, e2] = -G[:, f1] T2_bE2
       // sweeps (vector rows; n = -1 -> number of right-hand sides)
-      const int tm = P * m, t2 = P * 2 * m, mr = P * 2 * p;  // tmp rows, tmp2/zt rows, merged rows
-      sd[UP1 * NP + P] = D(r2, 0, r1, 0, r2, 0, tm, 0, m, -1, m);
-      sd[UP2 * NP + P] = D(w, m, tm, 0, 0, 0, t2, 0, m, -1, m);
-      sd[UP3 * NP + P] = D(r1, 0, t2, 0, r1, 0, t2 + m, 0, m, -1, m);
-      sd[UP4 * NP + P] = D(r1 + m, 0, t2, 0, r1 + m, 0, mr, 0, p, -1, m, dm1, -1);
-      sd[UP5 * NP + P] = D(r2 + m, 0, t2 + m, 0, r2 + m, 0, mr, 0, p, -1, m, dm2, -1);
-      sd[DN1 * NP + P] = D(r2, m, r2 + m, 0, r2, 0, t2, 0, m, -1, p);
-      sd[DN2 * NP + P] = D(r1, m, r1 + m, 0, r1, 0, t2 + m, 0, m, -1, p);
-      sd[DN3 * NP + P] = D(r2, 0, t2 + m, 0, t2, 0, tm, 0, m, -1, m);
-      sd[DN4 * NP + P] = D(w, m, tm, 0, 0, 0, r1, 0, m, -1, m);
-      sd[DN5 * NP + P] = D(r1, 0, r1, 0, t2 + m, 0, r2, 0, m, -1, m);
+      // up:   rho'_[E1;E2] = rho_[E1;E2] - U [f1; f2],  f1 = child2 rows 0..m, f2 = child1 rows 0..m
+      sd[SUP * NP + P] = D2(D(u, 0, r2, 0, r1 + m, 0, u, 0, 2 * p, -1, 2 * m, dm1, -1), r1, m, r2 + m, p);
+      // down: x = Dm [child1 rows 0..n ; child2 rows 0..n]  (into the x workspace)
+      sd[SDN * NP + P] = D2(D(dd, 0, r1, 0, 0, 0, g, 0, 2 * m, -1, 2 * n), r2, n, 0, 0);
+    }
+    {
+      std::vector<int> xmap((size_t)NP * 2 * m);
+      for (int P = 0; P < NP; ++P)
+        for (int i = 0; i < 2 * m; ++i)
+          xmap[(size_t)P * 2 * m + i] = i < m ? Lv.i1[P] * n + i : Lv.i2[P] * n + (i - m);
+      Lv.d_xmap = dev_upload(c, xmap);
+      if (!Lv.d_xmap) return fail(c, HPS_ENOMEM, "interface map");
     }
     Lv.d_mdesc = dev_upload(c, md);
     Lv.d_sdesc = dev_upload(c, sd);
@@ -254,7 +275,9 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
   for (int l = 1; l <= L_exact; ++l) {
     Level& Lv = c->levels[l];
     Lv.W = dev_alloc(c, sizeof(C) * (size_t)Lv.npairs * Lv.m * 2 * Lv.m);
-    if (!Lv.W) return fail(c, HPS_ENOMEM, "interface inverses");
+    Lv.U = dev_alloc(c, sizeof(C) * (size_t)Lv.npairs * 2 * Lv.p * 2 * Lv.m);
+    Lv.Dm = dev_alloc(c, sizeof(C) * (size_t)Lv.npairs * 2 * Lv.m * 2 * Lv.n);
+    if (!Lv.W || !Lv.U || !Lv.Dm) return fail(c, HPS_ENOMEM, "interface inverses and sweep operators");
   }
   if (L_exact > 0) {
     c->ws_X1 = dev_alloc(c, sizeof(C) * x_elems);
@@ -263,6 +286,21 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     c->d_lu = dev_alloc(c, sizeof(C) * (size_t)max_pairs * GJ_NB * GJ_NB);
     if (!c->ws_X1 || !c->ws_X2 || !c->d_piv || !c->d_lu) return fail(c, HPS_ENOMEM, "merge workspace");
     c->ws_X_elems = x_elems;
+  }
+  {
+    size_t g_elems = 1;
+    int mmax = 1;
+    for (int l = 1; l <= L_exact; ++l) {
+      g_elems = std::max(g_elems, (size_t)c->levels[l].npairs * 4 * c->levels[l].m * c->levels[l].m);
+      mmax = std::max(mmax, c->levels[l].m);
+    }
+    c->ws_G = dev_alloc(c, sizeof(C) * g_elems);
+    std::vector<C> eye((size_t)mmax * mmax, mk<R>(R(0), R(0)));
+    for (int i = 0; i < mmax; ++i) eye[(size_t)i * mmax + i] = mk<R>(R(1), R(0));
+    c->d_eye = dev_alloc(c, sizeof(C) * eye.size());
+    if (!c->ws_G || !c->d_eye) return fail(c, HPS_ENOMEM, "sweep-operator workspace");
+    HPS_CK(c, cudaMemcpy(c->d_eye, eye.data(), sizeof(C) * eye.size(), cudaMemcpyHostToDevice));
+    c->eye_ld = mmax;
   }
   c->gemm_ws_elems = (size_t)1 << 22;  // split-K partials
   c->gemm_ws = dev_alloc(c, sizeof(C) * c->gemm_ws_elems);
@@ -303,6 +341,19 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     HPS_CK(c, gemm<R>(c, md + MOB * NP, NP, T0, n, c->ws_X1, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
     HPS_CK(c, gemm<R>(c, md + MOC * NP, NP, T0, n, c->ws_X2, 2 * p, nullptr, 0, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
     HPS_CK(c, gemm<R>(c, md + MOD * NP, NP, T0, n, c->ws_X2, 2 * p, T0, n, Tn, 2 * p, -1.0, Lv.d_dst, p, p, p, m));
+    // sweep operators
+    void* G = c->ws_G;
+    HPS_CK(c, gemm<R>(c, md + PG1A * NP, NP, nullptr, 0, nullptr, 0, Lv.W, 2 * m, G, 2 * m, 1.0, nullptr, m, m, m));
+    HPS_CK(c, gemm<R>(c, md + PG1B * NP, NP, Lv.W, 2 * m, T0, n, nullptr, 0, G, 2 * m, -1.0, nullptr, m, m, m, m));
+    HPS_CK(c, gemm<R>(c, md + PG2A * NP, NP, T0, n, G, 2 * m, nullptr, 0, G, 2 * m, -1.0, nullptr, m, m, m, m));
+    HPS_CK(c, gemm<R>(c, md + PG2B * NP, NP, T0, n, G, 2 * m, c->d_eye, c->eye_ld, G, 2 * m, -1.0, nullptr, m, m, m,
+                      m));
+    HPS_CK(c, gemm<R>(c, md + PU1 * NP, 2 * NP, T0, n, G, 2 * m, nullptr, 0, Lv.U, 2 * m, 1.0, nullptr, p, 2 * m,
+                      2 * m, m));
+    HPS_CK(c, gemm<R>(c, md + PD1 * NP, NP, nullptr, 0, nullptr, 0, G, 2 * m, Lv.Dm, 2 * n, 1.0, nullptr, 2 * m, m, m));
+    HPS_CK(c, gemm<R>(c, md + PD3 * NP, NP, nullptr, 0, nullptr, 0, G, 2 * m, Lv.Dm, 2 * n, 1.0, nullptr, 2 * m, m, m));
+    HPS_CK(c, gemm<R>(c, md + PD2 * NP, NP, G, 2 * m, T0, n, nullptr, 0, Lv.Dm, 2 * n, -1.0, nullptr, 2 * m, p, p, m));
+    HPS_CK(c, gemm<R>(c, md + PD4 * NP, NP, G, 2 * m, T0, n, nullptr, 0, Lv.Dm, 2 * n, -1.0, nullptr, 2 * m, p, p, m));
   }
   // ---- coarse level ----
   {
@@ -417,13 +468,10 @@ int ensure_sweep_buffers(hps_ctx* c, int nrhs) {
     pm = std::max(pm, (size_t)c->levels[l].npairs * c->levels[l].m);
     p2m = std::max(p2m, (size_t)c->levels[l].npairs * 2 * c->levels[l].m);
   }
-  dev_free(c, c->sw_tmp);
-  dev_free(c, c->sw_tmp2);
-  dev_free(c, c->sw_zt);
-  c->sw_tmp = dev_alloc(c, cs * pm * nrhs);
-  c->sw_tmp2 = dev_alloc(c, cs * p2m * nrhs);
-  c->sw_zt = dev_alloc(c, cs * p2m * nrhs);
-  if (!c->sw_tmp || !c->sw_tmp2 || !c->sw_zt) return fail(c, HPS_ENOMEM, "sweep temporaries");
+  (void)pm;
+  dev_free(c, c->sw_x);
+  c->sw_x = dev_alloc(c, cs * p2m * nrhs);
+  if (!c->sw_x) return fail(c, HPS_ENOMEM, "sweep temporaries");
   c->nrhs_cap = nrhs;
   return HPS_OK;
 }
@@ -541,43 +589,28 @@ int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) 
   cudaStream_t st = c->stream;
   const Stage& S0 = c->stages[0];
   HPS_CK(c, (gather_rows<double, R>(static_cast<C*>(S0.vec), rho_es, S0.d_es, (long long)S0.nsub * S0.n, nrhs, st)));
+  // up-sweep: rho'_E = rho_E - U f (one GEMM per level)
   for (int l = 1; l <= c->L_exact; ++l) {
     const Level& Lv = c->levels[l];
     const Stage& P0 = c->stages[l - 1];
     const Stage& P1 = c->stages[l];
-    const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
-    const GemmDesc* sd = Lv.d_sdesc;
-    const void* T0 = P0.T;
-    void* v0 = P0.vec;
-    HPS_CK(c, gemm<R>(c, sd + UP1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp, nrhs, -1.0, nullptr, m, nrhs, nrhs, m));
-    HPS_CK(c, gemm<R>(c, sd + UP2 * NP, NP, Lv.W, 2 * m, c->sw_tmp, nrhs, nullptr, 0, c->sw_zt, nrhs, 1.0, nullptr, m,
-                      nrhs, nrhs, m));
-    HPS_CK(c, gemm<R>(c, sd + UP3 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, c->sw_zt, nrhs, -1.0, nullptr, m, nrhs,
-                      nrhs, m));
-    HPS_CK(c, gemm<R>(c, sd + UP4 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, P1.vec, nrhs, -1.0, Lv.d_dst, p, nrhs,
-                      nrhs, m));
-    HPS_CK(c, gemm<R>(c, sd + UP5 * NP, NP, T0, n, c->sw_zt, nrhs, v0, nrhs, P1.vec, nrhs, -1.0, Lv.d_dst, p, nrhs,
-                      nrhs, m));
+    const int m = Lv.m, p = Lv.p, NP = Lv.npairs;
+    HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
+                      Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
   }
   rc = coarse_solve<R>(c, nrhs, k);
   if (rc != HPS_OK) return rc;
+  // down-sweep: children's outer rows from the merged solution, x = Dm [child1; child2], x into the interface rows
   for (int l = c->L_exact; l >= 1; --l) {
     const Level& Lv = c->levels[l];
     const Stage& P0 = c->stages[l - 1];
     const Stage& P1 = c->stages[l];
-    const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
-    const GemmDesc* sd = Lv.d_sdesc;
-    const void* T0 = P0.T;
-    void* v0 = P0.vec;
-    HPS_CK(c, (scatter_rows<R, R>(static_cast<C*>(v0), static_cast<const C*>(P1.vec), Lv.d_up,
-                                  (long long)P1.nsub * P1.n, nrhs, st)));
-    HPS_CK(c, gemm<R>(c, sd + DN1 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs, p));
-    HPS_CK(c, gemm<R>(c, sd + DN2 * NP, NP, T0, n, v0, nrhs, v0, nrhs, c->sw_tmp2, nrhs, -1.0, nullptr, m, nrhs, nrhs, p));
-    HPS_CK(c, gemm<R>(c, sd + DN3 * NP, NP, T0, n, c->sw_tmp2, nrhs, c->sw_tmp2, nrhs, c->sw_tmp, nrhs, -1.0, nullptr,
-                      m, nrhs, nrhs, m));
-    HPS_CK(c, gemm<R>(c, sd + DN4 * NP, NP, Lv.W, 2 * m, c->sw_tmp, nrhs, nullptr, 0, v0, nrhs, 1.0, nullptr, m, nrhs,
-                      nrhs, m));
-    HPS_CK(c, gemm<R>(c, sd + DN5 * NP, NP, T0, n, v0, nrhs, c->sw_tmp2, nrhs, v0, nrhs, -1.0, nullptr, m, nrhs, nrhs, m));
+    const int n = Lv.n, m = Lv.m, NP = Lv.npairs;
+    C* v0 = static_cast<C*>(P0.vec);
+    HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(P1.vec), Lv.d_up, (long long)P1.nsub * P1.n, nrhs, st)));
+    HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
+                      2 * m, nrhs, nrhs, 2 * n));
+    HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(c->sw_x), Lv.d_xmap, (long long)NP * 2 * m, nrhs, st)));
   }
   HPS_CK(c, (scatter_rows<R, double>(z_es, static_cast<const C*>(S0.vec), S0.d_es, (long long)S0.nsub * S0.n, nrhs,
                                      st)));
