@@ -338,11 +338,114 @@ void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+
+// ---------------------------------------------------------------------------
+// Skinny GEMM for n <= NC columns (block vectors of right-hand sides): A is
+// streamed once with coalesced loads (lanes split k), B is staged in padded
+// shared memory by k-chunks, each warp accumulates RW rows x NC columns and
+// reduces across its lanes at the end.  Same descriptors and epilogue as
+// gemm_tile (two-segment B / C0, row and column maps).
+// ---------------------------------------------------------------------------
+template <typename R, int NC, int RW>
+__global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
+  using C = c_t<R>;
+  constexpr int KC = 128;          // k-chunk staged in shared memory
+  constexpr int LDB = NC + 1;      // padding against bank conflicts
+  constexpr int RB = (NT / 32) * RW;
+  __shared__ C Bs[KC * LDB];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int b = blockIdx.z; b < a.nbatch; b += gridDim.z) {
+    const GemmDesc d = a.desc[b];
+    const int n = d.n < 0 ? a.n_launch : d.n;
+    const int m = d.m, k = d.k;
+    const int row0 = blockIdx.x * RB;
+    if (row0 >= m) continue;  // uniform over the block
+    C acc[RW][NC];
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[r][c] = czero<R>();
+    int rows[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) rows[r] = row0 + warp * RW + r;
+    for (int k0 = 0; k0 < k; k0 += KC) {
+      __syncthreads();
+      for (int l = threadIdx.x; l < KC * NC; l += NT) {
+        const int kk = l / NC, j = l % NC;
+        const int gk = k0 + kk;
+        C v = czero<R>();
+        if (gk < k && j < n) {
+          const long long br = (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+          v = a.B[br * a.ldb + d.b_c + j];
+        }
+        Bs[kk * LDB + j] = v;
+      }
+      __syncthreads();
+      const int kend = k - k0 < KC ? k - k0 : KC;
+      for (int kk = lane; kk < kend; kk += 32) {
+        C av[RW];
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+          av[r] = rows[r] < m ? a.A[(long long)(d.a_r + rows[r]) * a.lda + d.a_c + k0 + kk] : czero<R>();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const C bv = Bs[kk * LDB + c];
+#pragma unroll
+          for (int r = 0; r < RW; ++r) cfma(acc[r][c], av[r], bv);
+        }
+      }
+    }
+    // reduce across lanes; lane c ends up owning column c of each row
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          acc[r][c].x += __shfl_xor_sync(0xffffffffu, acc[r][c].x, off);
+          acc[r][c].y += __shfl_xor_sync(0xffffffffu, acc[r][c].y, off);
+        }
+    const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
+    const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const int gi = rows[r];
+      if (gi >= m) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (c % 32 != lane || c >= n) continue;
+        C v = cmul(a.alpha, acc[r][c]);
+        if (a.C0) {
+          const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+          v = cadd(v, cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + c]));
+        }
+        const long long orow = (long long)d.c_r + (rmap ? rmap[gi] : gi);
+        a.C[orow * a.ldc + d.c_c + (cmap ? cmap[c] : c)] = v;
+      }
+    }
+  }
+}
+
+template <typename R, int NC, int RW>
+cudaError_t launch_skinny(const GemmArgs<R>& a, int mmax, cudaStream_t s) {
+  constexpr int RB = (NT / 32) * RW;
+  dim3 grid((mmax + RB - 1) / RB, 1, a.nbatch < 65535 ? a.nbatch : 65535);
+  skinny_kernel<R, NC, RW><<<grid, NT, 0, s>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename R>
 cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
+  // block-vector products (few columns, long k): stream A once
+  if (kmax >= 32) {
+    if (nmax <= 8) return launch_skinny<R, 8, 4>(a, mmax, s);
+    if (nmax <= 16) return launch_skinny<R, 16, 2>(a, mmax, s);
+    if (nmax <= 32) return launch_skinny<R, 32, 1>(a, mmax, s);
+  }
   if (nmax <= 16) {
     if (mmax <= 16) return launch_cfg<R, 16, 16, 16, 1, 1>(a, mmax, nmax, kmax, s);
     if (mmax <= 32) return launch_cfg<R, 32, 16, 16, 2, 1>(a, mmax, nmax, kmax, s);

@@ -270,7 +270,7 @@ __global__ void bdot_final_kernel(const c_t<R>* __restrict__ partial, int nblk, 
 }
 
 int bdot_blocks(long long rows) {
-  long long b = (rows + 511) / 512;
+  long long b = (rows + 63) / 64;
   if (b < 1) b = 1;
   return (int)(b > 512 ? 512 : b);
 }
