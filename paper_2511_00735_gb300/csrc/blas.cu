@@ -346,10 +346,10 @@ void set_smem(K kernel, size_t bytes) {
 // reduces across its lanes at the end.  Same descriptors and epilogue as
 // gemm_tile (two-segment B / C0, row and column maps).
 // ---------------------------------------------------------------------------
-template <typename R, int NC, int RW>
+template <typename R, int NC, int RW, int KU>
 __global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
   using C = c_t<R>;
-  constexpr int KC = 128;          // k-chunk staged in shared memory
+  constexpr int KC = 32 * KU;      // k-chunk: every lane holds KU values of A per row
   constexpr int LDB = NC + 1;      // padding against bank conflicts
   constexpr int RB = (NT / 32) * RW;
   __shared__ C Bs[KC * LDB];
@@ -365,10 +365,23 @@ __global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
     for (int r = 0; r < RW; ++r)
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[r][c] = czero<R>();
-    int rows[RW];
+    const C* arow[RW];
+    bool rok[RW];
 #pragma unroll
-    for (int r = 0; r < RW; ++r) rows[r] = row0 + warp * RW + r;
+    for (int r = 0; r < RW; ++r) {
+      const int gi = row0 + warp * RW + r;
+      rok[r] = gi < m;
+      arow[r] = a.A + (long long)(d.a_r + (rok[r] ? gi : 0)) * a.lda + d.a_c;
+    }
     for (int k0 = 0; k0 < k; k0 += KC) {
+      // issue this lane's loads of A first (KU x RW independent loads in flight)
+      C av[RW][KU];
+#pragma unroll
+      for (int t = 0; t < KU; ++t) {
+        const int gk = k0 + lane + 32 * t;
+#pragma unroll
+        for (int r = 0; r < RW; ++r) av[r][t] = (rok[r] && gk < k) ? arow[r][gk] : czero<R>();
+      }
       __syncthreads();
       for (int l = threadIdx.x; l < KC * NC; l += NT) {
         const int kk = l / NC, j = l % NC;
@@ -381,17 +394,14 @@ __global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
         Bs[kk * LDB + j] = v;
       }
       __syncthreads();
-      const int kend = k - k0 < KC ? k - k0 : KC;
-      for (int kk = lane; kk < kend; kk += 32) {
-        C av[RW];
 #pragma unroll
-        for (int r = 0; r < RW; ++r)
-          av[r] = rows[r] < m ? a.A[(long long)(d.a_r + rows[r]) * a.lda + d.a_c + k0 + kk] : czero<R>();
+      for (int t = 0; t < KU; ++t) {
+        const int kk = lane + 32 * t;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const C bv = Bs[kk * LDB + c];
 #pragma unroll
-          for (int r = 0; r < RW; ++r) cfma(acc[r][c], av[r], bv);
+          for (int r = 0; r < RW; ++r) cfma(acc[r][c], av[r][t], bv);
         }
       }
     }
@@ -409,8 +419,8 @@ __global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
     const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
-      const int gi = rows[r];
-      if (gi >= m) continue;
+      const int gi = row0 + warp * RW + r;
+      if (!rok[r]) continue;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c % 32 != lane || c >= n) continue;
@@ -426,11 +436,11 @@ __global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
   }
 }
 
-template <typename R, int NC, int RW>
+template <typename R, int NC, int RW, int KU>
 cudaError_t launch_skinny(const GemmArgs<R>& a, int mmax, cudaStream_t s) {
   constexpr int RB = (NT / 32) * RW;
   dim3 grid((mmax + RB - 1) / RB, 1, a.nbatch < 65535 ? a.nbatch : 65535);
-  skinny_kernel<R, NC, RW><<<grid, NT, 0, s>>>(a);
+  skinny_kernel<R, NC, RW, KU><<<grid, NT, 0, s>>>(a);
   note_launch();
   return cudaGetLastError();
 }
@@ -441,10 +451,15 @@ template <typename R>
 cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
   // block-vector products (few columns, long k): stream A once
-  if (kmax >= 32) {
-    if (nmax <= 8) return launch_skinny<R, 8, 4>(a, mmax, s);
-    if (nmax <= 16) return launch_skinny<R, 16, 2>(a, mmax, s);
-    if (nmax <= 32) return launch_skinny<R, 32, 1>(a, mmax, s);
+  if (kmax >= 128) {
+    if (sizeof(R) == 4) {
+      if (nmax <= 8) return launch_skinny<R, 8, 4, 8>(a, mmax, s);
+      if (nmax <= 16) return launch_skinny<R, 16, 2, 8>(a, mmax, s);
+      if (nmax <= 32) return launch_skinny<R, 32, 1, 8>(a, mmax, s);
+    } else {
+      if (nmax <= 8) return launch_skinny<R, 8, 2, 4>(a, mmax, s);
+      if (nmax <= 16) return launch_skinny<R, 16, 1, 4>(a, mmax, s);
+    }
   }
   if (nmax <= 16) {
     if (mmax <= 16) return launch_cfg<R, 16, 16, 16, 1, 1>(a, mmax, nmax, kmax, s);
