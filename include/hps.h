@@ -144,9 +144,12 @@ int hps_set_coeff(hps_ctx* ctx, double kappa, double eta, const double* b);
  * result kept on the device in side order l, r, b, t.  `precision` selects the
  * precision of the merge tree built later (HPS_FP64 or HPS_MIXED); the leaf
  * maps themselves are FP64 in both (the outer matvec needs them).
- * HPS_EUNSUPPORTED if an element's interior operator is not provably
- * positive definite (kappa^2 (1-b) too large for the element size): this build
- * eliminates the interior nodes by a real Cholesky factorisation. */
+ * Elements whose interior operator is provably positive definite
+ * (kappa^2 (1-b) (h/2)^2 below the smallest interior Dirichlet eigenvalue of
+ * the reference element, with a 2% margin) eliminate the interior by a real
+ * L D L^T factorisation; the others (near or past an interior resonance) use
+ * a pivoted complex elimination of the edge rows first.  HPS_ENUMERIC if an
+ * element system is singular. */
 int hps_build_leaves(hps_ctx* ctx, int precision);
 
 /* Host copy of leaf maps e0 .. e0+count-1: [count][4q][4q] complex128, row-major. */

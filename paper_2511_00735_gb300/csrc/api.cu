@@ -529,35 +529,63 @@ int hps_build_leaves(hps_ctx* c, int precision) {
   CHECK_CTX(c);
   if (!c->have_coeff) return fail(c, HPS_ENOTBUILT, "hps_set_coeff first");
   if (precision != HPS_FP64 && precision != HPS_MIXED) return fail(c, HPS_EINVAL, "precision");
-  // positive-definiteness of the interior operator (leaf.cu): max c (h/2)^2 < 2 mu_min
-  const double cmax = *std::max_element(c->c_host.begin(), c->c_host.end());
-  const double bound = 2.0 * c->mu_min / (0.25 * c->h * c->h);
-  if (cmax >= 0.98 * bound)
-    return fail(c, HPS_EUNSUPPORTED,
-                "kappa^2 (1 - b) = " + std::to_string(cmax) + " reaches the interior Dirichlet bound " +
-                    std::to_string(bound) + " of these elements; this build eliminates the interior by Cholesky");
+  // Route per element: the Cholesky route where the interior operator is provably positive
+  // definite (max c (h/2)^2 < 0.98 * 2 mu_min), the pivoted robust route elsewhere (leaf.cu).
+  const int n1 = c->N + 1;
+  const double bound = 0.98 * 2.0 * c->mu_min / (0.25 * c->h * c->h);
+  std::vector<int> good, bad;
+  for (int e = 0; e < c->E; ++e) {
+    double cm = -1e300;
+    for (int l = 0; l < n1 * n1; ++l) cm = std::max(cm, c->c_host[(size_t)e * n1 * n1 + l]);
+    (cm < bound ? good : bad).push_back(e);
+  }
   cudaStreamSynchronize(c->stream);
   free_tree(c);
   if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
   if (!c->d_T) return fail(c, HPS_ENOMEM, "leaf maps");
-  const int grid = std::min(c->E, std::max(1, c->num_sms));
-  double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
-  if (!Ascr) return fail(c, HPS_ENOMEM, "leaf scratch");
   LeafParams p;
   p.N = c->N; p.q = c->q; p.ni = c->q * c->q; p.nb = c->nb; p.E = c->E; p.cw = 8;
   p.h = c->h; p.eta = c->eta;
   p.c = c->d_c; p.Dh = c->d_Dref; p.Kh = c->d_Kref; p.wh = c->d_wref;
-  p.Ascr = Ascr; p.T = c->d_T; p.flag = c->d_flag;
+  p.T = c->d_T; p.flag = c->d_flag;
   HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-  {
+  std::vector<void*> scratch;
+  if (!good.empty()) {
+    const int grid = std::min((int)good.size(), std::max(1, c->num_sms));
+    double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
+    int* d_good = good.size() == (size_t)c->E ? nullptr : dev_upload(c, good);
+    if (!Ascr || (good.size() != (size_t)c->E && !d_good)) return fail(c, HPS_ENOMEM, "leaf scratch");
+    scratch.push_back(Ascr);
+    if (d_good) scratch.push_back(d_good);
+    p.Ascr = Ascr;
+    p.elems = d_good;
+    p.count = (int)good.size();
     PhaseScope ps(c, HPS_PH_LEAF);
     HPS_CK(c, launch_leaf(p, grid, c->stream));
+  }
+  if (!bad.empty()) {
+    const size_t per = sizeof(double2) * (size_t)p.ni * (p.ni + p.nb);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(bad.size(), ((size_t)512 << 20) / per));
+    double2* W = static_cast<double2*>(dev_alloc(c, per * chunk));
+    int* piv = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)chunk * GJ_NB));
+    double2* lu = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)chunk * GJ_NB * GJ_NB));
+    int* d_bad = dev_upload(c, bad);
+    if (!W || !piv || !lu || !d_bad) return fail(c, HPS_ENOMEM, "robust leaf workspace");
+    scratch.insert(scratch.end(), {W, piv, lu, d_bad});
+    PhaseScope ps(c, HPS_PH_LEAF);
+    for (size_t b0 = 0; b0 < bad.size(); b0 += chunk) {
+      const int nch = (int)std::min<size_t>(chunk, bad.size() - b0);
+      HPS_CK(c, robust_assemble(p, d_bad + b0, nch, W, c->stream));
+      HPS_CK(c, gj_solve<double>(W, p.ni, p.ni + p.nb, nch, piv, lu, c->d_flag, c->stream));
+      HPS_CK(c, robust_finish(p, d_bad + b0, nch, W, c->stream));
+    }
   }
   int flag = 0;
   HPS_CK(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HPS_CK(c, cudaStreamSynchronize(c->stream));
-  dev_free(c, Ascr);
-  if (flag) return fail(c, HPS_ENUMERIC, "non-positive Cholesky pivot in element " + std::to_string(flag - 1));
+  for (void* s : scratch) dev_free(c, s);
+  if (flag) return fail(c, HPS_ENUMERIC, "singular element system (zero pivot or non-positive Cholesky pivot)");
+  c->n_robust = (int)bad.size();
   c->precision = precision;
   c->have_leaves = true;
   return HPS_OK;

@@ -179,29 +179,28 @@ cudaError_t launch_cfg(const GemmArgs<R>& a, int mmax, int nmax, int kmax, cudaS
 // ---------------------------------------------------------------------------
 
 template <typename R>
-__global__ void __launch_bounds__(NT) gj_small_kernel(c_t<R>* W, int m, int* flag) {
+__global__ void __launch_bounds__(NT) gj_small_kernel(c_t<R>* W, int m, int ld, int* flag) {
   using C = c_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* S = reinterpret_cast<C*>(smem_raw);
-  const int ld = 2 * m;
   C* Wg = W + (long long)blockIdx.x * m * ld;
   for (int l = threadIdx.x; l < m * ld; l += NT) S[l] = Wg[l];
   __syncthreads();
   gj_smem<R>(S, m, ld, ld, flag);
-  for (int l = threadIdx.x; l < m * m; l += NT) {
-    const int i = l / m, j = m + l % m;
+  const int w = ld - m;
+  for (int l = threadIdx.x; l < m * w; l += NT) {
+    const int i = l / w, j = m + l % w;
     Wg[i * ld + j] = S[i * ld + j];
   }
 }
 
 // Pivot search and LU of the (m-k0) x kb column slab of one matrix.
 template <typename R>
-__global__ void __launch_bounds__(NT) gj_panel_kernel(c_t<R>* W, int m, int k0, int kb, int* piv,
+__global__ void __launch_bounds__(NT) gj_panel_kernel(c_t<R>* W, int m, int ld, int k0, int kb, int* piv,
                                                       c_t<R>* lu, int* flag) {
   using C = c_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* S = reinterpret_cast<C*>(smem_raw);  // [mr][kb]
-  const int ld = 2 * m;
   const int mr = m - k0;
   const C* Wg = W + (long long)blockIdx.x * m * ld;
   for (int l = threadIdx.x; l < mr * kb; l += NT) {
@@ -247,13 +246,12 @@ __global__ void __launch_bounds__(NT) gj_panel_kernel(c_t<R>* W, int m, int k0, 
 
 // Row swaps of one column block and the pivot rows' solve P = (L11 U11)^{-1} W(k0:k0+kb, j).
 template <typename R>
-__global__ void __launch_bounds__(NT) gj_apply_kernel(c_t<R>* W, int m, int k0, int kb, const int* piv,
+__global__ void __launch_bounds__(NT) gj_apply_kernel(c_t<R>* W, int m, int ld, int k0, int kb, const int* piv,
                                                       const c_t<R>* lu) {
   using C = c_t<R>;
   __shared__ C sL[GJ_NB * GJ_NB];
   __shared__ int sp[GJ_NB];
   const int mat = blockIdx.y;
-  const int ld = 2 * m;
   for (int l = threadIdx.x; l < GJ_NB * GJ_NB; l += NT) sL[l] = lu[(long long)mat * GJ_NB * GJ_NB + l];
   if (threadIdx.x < GJ_NB) sp[threadIdx.x] = piv[mat * GJ_NB + threadIdx.x];
   __syncthreads();
@@ -304,13 +302,13 @@ __global__ void __launch_bounds__(NT) gj_apply_kernel(c_t<R>* W, int m, int k0, 
 
 // Rank-kb elimination of every non-pivot row: W(i, j) -= W(i, k0:k0+kb) P(:, j), j >= k0+kb.
 template <typename R, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(NT) gj_update_kernel(c_t<R>* W, int m, int k0, int kb) {
+__global__ void __launch_bounds__(NT) gj_update_kernel(c_t<R>* W, int m, int ld, int k0, int kb) {
   const int mat = blockIdx.z / 2, part = blockIdx.z % 2;
   GemmDesc d;
   const int base = mat * m;
   const int r0 = part == 0 ? 0 : k0 + kb;
   d.m = part == 0 ? k0 : m - k0 - kb;
-  d.n = 2 * m - k0 - kb;
+  d.n = ld - k0 - kb;
   d.k = kb;
   d.a_r = base + r0;
   d.a_c = k0;
@@ -323,7 +321,7 @@ __global__ void __launch_bounds__(NT) gj_update_kernel(c_t<R>* W, int m, int k0,
   GemmArgs<R> a;
   a.A = a.B = a.C0 = W;
   a.C = W;
-  a.lda = a.ldb = a.ldc0 = a.ldc = 2 * m;
+  a.lda = a.ldb = a.ldc0 = a.ldc = ld;
   a.alpha = mk<R>(R(-1), R(0));
   a.beta = mk<R>(R(1), R(0));
   a.desc = nullptr;
@@ -476,15 +474,15 @@ cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s
 }
 
 template <typename R>
-cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag, cudaStream_t s) {
+cudaError_t gj_solve(c_t<R>* W, int m, int ld, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag, cudaStream_t s) {
   using C = c_t<R>;
-  if (m <= 0 || nmat <= 0) return cudaSuccess;
-  const size_t small_bytes = (size_t)m * 2 * m * sizeof(C);
+  if (m <= 0 || nmat <= 0 || ld <= m) return cudaSuccess;
+  const size_t small_bytes = (size_t)m * ld * sizeof(C);
   if (small_bytes <= 160 * 1024) {
     set_smem(gj_small_kernel<R>, small_bytes);
     for (int b0 = 0; b0 < nmat; b0 += 65535) {
       const int nb = nmat - b0 < 65535 ? nmat - b0 : 65535;
-      gj_small_kernel<R><<<nb, NT, small_bytes, s>>>(W + (long long)b0 * m * 2 * m, m, flag);
+      gj_small_kernel<R><<<nb, NT, small_bytes, s>>>(W + (long long)b0 * m * ld, m, ld, flag);
       note_launch();
     }
     return cudaGetLastError();
@@ -498,25 +496,32 @@ cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, in
   set_smem(gj_panel_kernel<R>, panel_bytes);
   for (int k0 = 0; k0 < m; k0 += nbw) {
     const int kb = m - k0 < nbw ? m - k0 : nbw;
-    gj_panel_kernel<R><<<nmat, NT, panel_bytes, s>>>(W, m, k0, kb, piv_ws, lu_ws, flag);
+    gj_panel_kernel<R><<<nmat, NT, panel_bytes, s>>>(W, m, ld, k0, kb, piv_ws, lu_ws, flag);
     note_launch();
-    dim3 ga((2 * m - k0 + NT - 1) / NT, nmat);
-    gj_apply_kernel<R><<<ga, NT, 0, s>>>(W, m, k0, kb, piv_ws, lu_ws);
+    dim3 ga((ld - k0 + NT - 1) / NT, nmat);
+    gj_apply_kernel<R><<<ga, NT, 0, s>>>(W, m, ld, k0, kb, piv_ws, lu_ws);
     note_launch();
     const int mrows = k0 > m - k0 - kb ? k0 : m - k0 - kb;
-    const int ncols = 2 * m - k0 - kb;
+    const int ncols = ld - k0 - kb;
     if (mrows > 0 && ncols > 0) {
       dim3 gu((ncols + 63) / 64, (mrows + 63) / 64, nmat * 2);
-      gj_update_kernel<R, 64, 64, 8, 4, 4><<<gu, NT, 0, s>>>(W, m, k0, kb);
+      gj_update_kernel<R, 64, 64, 8, 4, 4><<<gu, NT, 0, s>>>(W, m, ld, k0, kb);
       note_launch();
     }
   }
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag, cudaStream_t s) {
+  return gj_solve<R>(W, m, 2 * m, nmat, piv_ws, lu_ws, flag, s);
+}
+
 template cudaError_t launch_gemm<double>(const GemmArgs<double>&, int, int, cudaStream_t, int);
 template cudaError_t launch_gemm<float>(const GemmArgs<float>&, int, int, cudaStream_t, int);
 template cudaError_t gj_invert<double>(double2*, int, int, int*, double2*, int*, cudaStream_t);
 template cudaError_t gj_invert<float>(float2*, int, int, int*, float2*, int*, cudaStream_t);
+template cudaError_t gj_solve<double>(double2*, int, int, int, int*, double2*, int*, cudaStream_t);
+template cudaError_t gj_solve<float>(float2*, int, int, int, int*, float2*, int*, cudaStream_t);
 
 }  // namespace hps

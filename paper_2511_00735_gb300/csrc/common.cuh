@@ -114,5 +114,8 @@ constexpr int GJ_NB = 16;
 template <typename R>
 cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag,
                       cudaStream_t s);
+// General form: W = [S | B] (m x ld, ld > m) -> right part S^{-1} B (same pivoting).
+template <typename R>
+cudaError_t gj_solve(c_t<R>* W, int m, int ld, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag, cudaStream_t s);
 
 }  // namespace hps

@@ -96,6 +96,7 @@ struct hps_ctx {
   bool have_leaves = false;
   int precision = HPS_FP64;
   double2* d_T = nullptr;      // [E][nb][nb] FP64, side order l, r, b, t
+  int n_robust = 0;            // elements built by the pivoted route
   int* d_flag = nullptr;
 
   // tree

@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
   }
   for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
 
-  for (int e = blockIdx.x; e < p.E; e += gridDim.x) {
+  const int nel = p.elems ? p.count : p.E;
+  for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
+    const int e = p.elems ? p.elems[ei] : ei;
     __syncthreads();
     for (int l = tid; l < n1 * n1; l += nth) sc[l] = p.c[(long long)e * n1 * n1 + l];
     __syncthreads();
@@ -198,6 +200,149 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
 }
 
 }  // namespace
+
+
+// ---------------------------------------------------------------------------
+// Robust route (any element the impedance problem is solvable on).  The edge
+// rows I_i = Dn + i eta couple each node only to the opposite node of its line,
+// so L_GG is block diagonal with one 2x2 block per line,
+//     Mb = [[-D00 + i eta, -D0N], [DN0, DNN + i eta]]   (order: left/bottom, right/top),
+// the same for every line and always invertible.  Eliminating the edge nodes
+// first leaves the complex interior Schur complement
+//     S_i = L~_ii - R Dn_Gi,   R = L~_iG L_GG^{-1},
+// with Y_i = -S_i^{-1} R (pivoted Gauss-Jordan on [S_i | -R]) and
+//     Y_G = L_GG^{-1} (I - Dn_Gi Y_i),  T = I - 2 i eta Y_G.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Minv2 {
+  double2 a, b, c, d;  // inverse of Mb, row-major
+};
+
+__device__ __forceinline__ Minv2 mb_inverse(const double* Dp, int N, double eta) {
+  const int n1 = N + 1;
+  const double2 m00 = make_double2(-Dp[0], eta), m01 = make_double2(-Dp[N], 0.0);
+  const double2 m10 = make_double2(Dp[N * n1], 0.0), m11 = make_double2(Dp[N * n1 + N], eta);
+  const double2 det = csub(cmul(m00, m11), cmul(m01, m10));
+  const double2 id = cinv(det);
+  Minv2 r;
+  r.a = cmul(m11, id);
+  r.b = cmul(make_double2(-m01.x, -m01.y), id);
+  r.c = cmul(make_double2(-m10.x, -m10.y), id);
+  r.d = cmul(m00, id);
+  return r;
+}
+
+__global__ void robust_assemble_kernel(LeafParams p, const int* __restrict__ elems, int count,
+                                       double2* __restrict__ W) {
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1, ld = ni + nb;
+  const double dsc = 2.0 / p.h, h2 = 0.25 * p.h * p.h;
+  __shared__ double sD[17 * 17];
+  for (int l = threadIdx.x; l < n1 * n1; l += blockDim.x) sD[l] = dsc * p.Dh[l];
+  __syncthreads();
+  const Minv2 mi = mb_inverse(sD, N, p.eta);
+  const long long tot = (long long)count * ni * ld;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(l / ((long long)ni * ld));
+    const int rem = (int)(l % ((long long)ni * ld));
+    const int I = rem / ld, col = rem % ld;
+    const int e = elems[b];
+    const int ti = I / q + 1, tj = I % q + 1;
+    // R entries of row I on its two lines (x-pair of line tj, y-pair of line ti)
+    const double a0 = p.Kh[ti * n1 + 0] * p.wh[tj], aN = p.Kh[ti * n1 + N] * p.wh[tj];
+    const double c0 = p.wh[ti] * p.Kh[tj * n1 + 0], cN = p.wh[ti] * p.Kh[tj * n1 + N];
+    const double2 Rl = cadd(cscale(mi.a, a0), cscale(mi.c, aN)), Rr = cadd(cscale(mi.b, a0), cscale(mi.d, aN));
+    const double2 Rb = cadd(cscale(mi.a, c0), cscale(mi.c, cN)), Rt = cadd(cscale(mi.b, c0), cscale(mi.d, cN));
+    double2 v = make_double2(0.0, 0.0);
+    if (col < ni) {
+      const int ui = col / q + 1, uj = col % q + 1;
+      double lt = 0.0;
+      if (tj == uj) lt += p.Kh[ti * n1 + ui] * p.wh[tj];
+      if (ti == ui) lt += p.wh[ti] * p.Kh[tj * n1 + uj];
+      if (I == col) lt -= p.c[(long long)e * n1 * n1 + ti * n1 + tj] * h2 * p.wh[ti] * p.wh[tj];
+      v.x = lt;
+      if (tj == uj) v = csub(v, cadd(cscale(Rl, -sD[0 * n1 + ui]), cscale(Rr, sD[N * n1 + ui])));
+      if (ti == ui) v = csub(v, cadd(cscale(Rb, -sD[0 * n1 + uj]), cscale(Rt, sD[N * n1 + uj])));
+    } else {
+      const int g = col - ni, side = g / q, s = g % q + 1;
+      // -R[I][g]
+      if (side == 0 && s == tj) v = Rl;
+      else if (side == 1 && s == tj) v = Rr;
+      else if (side == 2 && s == ti) v = Rb;
+      else if (side == 3 && s == ti) v = Rt;
+      v = make_double2(-v.x, -v.y);
+    }
+    W[(long long)b * ni * ld + (long long)I * ld + col] = v;
+  }
+}
+
+__global__ void robust_finish_kernel(LeafParams p, const int* __restrict__ elems, int count,
+                                     const double2* __restrict__ W) {
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1, ld = ni + nb;
+  const double dsc = 2.0 / p.h;
+  __shared__ double sD[17 * 17];
+  for (int l = threadIdx.x; l < n1 * n1; l += blockDim.x) sD[l] = dsc * p.Dh[l];
+  __syncthreads();
+  const Minv2 mi = mb_inverse(sD, N, p.eta);
+  const long long tot = (long long)count * 2 * q * nb;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(l / (2LL * q * nb));
+    const int rem = (int)(l % (2LL * q * nb));
+    const int line = rem / nb, col = rem % nb;
+    const double2* Y = W + (long long)b * ni * ld + ni;  // Y_i[J][col] at Y[J * ld + col]
+    double2 z0, z1;  // Z on the line's first node (l or b) and second node (r or t)
+    int g0, g1;
+    if (line < q) {  // x-pair: l_j, r_j with j = line + 1; interior nodes (ui, j)
+      const int j = line + 1;
+      g0 = j - 1;
+      g1 = q + j - 1;
+      z0 = make_double2(g0 == col ? 1.0 : 0.0, 0.0);
+      z1 = make_double2(g1 == col ? 1.0 : 0.0, 0.0);
+      for (int ui = 1; ui <= q; ++ui) {
+        const double2 y = Y[(long long)((ui - 1) * q + (j - 1)) * ld + col];
+        z0 = cadd(z0, cscale(y, sD[0 * n1 + ui]));
+        z1 = csub(z1, cscale(y, sD[N * n1 + ui]));
+      }
+    } else {  // y-pair: b_i, t_i with i = line - q + 1; interior nodes (i, uj)
+      const int i = line - q + 1;
+      g0 = 2 * q + i - 1;
+      g1 = 3 * q + i - 1;
+      z0 = make_double2(g0 == col ? 1.0 : 0.0, 0.0);
+      z1 = make_double2(g1 == col ? 1.0 : 0.0, 0.0);
+      for (int uj = 1; uj <= q; ++uj) {
+        const double2 y = Y[(long long)((i - 1) * q + (uj - 1)) * ld + col];
+        z0 = cadd(z0, cscale(y, sD[0 * n1 + uj]));
+        z1 = csub(z1, cscale(y, sD[N * n1 + uj]));
+      }
+    }
+    const double2 y0 = cadd(cmul(mi.a, z0), cmul(mi.b, z1));
+    const double2 y1 = cadd(cmul(mi.c, z0), cmul(mi.d, z1));
+    double2* To = p.T + (long long)elems[b] * nb * nb;
+    // T = I - 2 i eta Y_G:  -2 i eta (x + i y) = 2 eta y - 2 i eta x
+    To[(long long)g0 * nb + col] = make_double2((g0 == col ? 1.0 : 0.0) + 2.0 * p.eta * y0.y, -2.0 * p.eta * y0.x);
+    To[(long long)g1 * nb + col] = make_double2((g1 == col ? 1.0 : 0.0) + 2.0 * p.eta * y1.y, -2.0 * p.eta * y1.x);
+  }
+}
+
+}  // namespace
+
+cudaError_t robust_assemble(const LeafParams& p, const int* elems, int count, double2* W, cudaStream_t s) {
+  const long long tot = (long long)count * p.ni * (p.ni + p.nb);
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 16384) blocks = 16384;
+  robust_assemble_kernel<<<(int)blocks, 256, 0, s>>>(p, elems, count, W);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t robust_finish(const LeafParams& p, const int* elems, int count, const double2* W, cudaStream_t s) {
+  const long long tot = (long long)count * 2 * p.q * p.nb;
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 16384) blocks = 16384;
+  robust_finish_kernel<<<(int)blocks, 256, 0, s>>>(p, elems, count, W);
+  note_launch();
+  return cudaGetLastError();
+}
 
 size_t leaf_smem_bytes(int N, int cw) {
   const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;

@@ -16,9 +16,16 @@ struct LeafParams {
   double* Ascr;       // [gridDim.x][nb][nb] per-CTA scratch for A
   double2* T;         // [E][nb][nb] output, side order l, r, b, t
   int* flag;          // set to e+1 when a Cholesky pivot is not positive
+  const int* elems = nullptr;  // optional list of the elements to build (count entries); null: 0..E-1
+  int count = 0;
 };
 size_t leaf_smem_bytes(int N, int cw);
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s);
+// Robust route for elements whose interior block is not positive definite:
+// W[b] = [S_i | -R] (n_i x (n_i + nb)) for elems[b], then (after W's right part
+// holds Y_i = S_i^{-1}(-R)) the leaf map of elems[b] into p.T.
+cudaError_t robust_assemble(const LeafParams& p, const int* elems, int count, double2* W, cudaStream_t s);
+cudaError_t robust_finish(const LeafParams& p, const int* elems, int count, const double2* W, cudaStream_t s);
 
 // skel.cu -- FP64 element-side operators
 cudaError_t es_matvec(const double2* T, const int* nbr, const double2* x, const double2* c0, double2* y, int E,

@@ -81,11 +81,23 @@ def test_leaf_maps(solver, nx, N, kappa):
         assert rel(Tg[e], To) < 1e-11, e
 
 
-def test_paper_bump_leaf_and_unsupported(solver):
-    prob = inputs.Problem(nx=8, N=8, kappa=150.0, eta=150.0, bumps=[inputs.PAPER_BUMP], thetas=[0.1])
-    with pytest.raises(H.HPSError) as ei:
-        H.setup(solver, prob)
-    assert ei.value.status == -8
+@pytest.mark.parametrize("nx,N,kappa", [(8, 8, 150.0), (8, 8, 36.0), (4, 12, 60.0)])
+def test_leaf_maps_robust_route(solver, nx, N, kappa):
+    # kappa^2 (1 - b) (h/2)^2 past the interior Dirichlet bound: the pivoted route (all
+    # elements at kappa = 150; only those away from the bump at kappa = 36)
+    prob = inputs.Problem(nx=nx, N=N, kappa=kappa, eta=kappa, bumps=[inputs.PAPER_BUMP], thetas=[0.1, 2.0],
+                          L_exact=2)
+    t = H.setup(solver, prob)
+    op = OracleProblem(prob)
+    Tg = solver.leaf_T(0, nx * nx)
+    for e in range(nx * nx):
+        assert rel(Tg[e], op.Ts[e]) < 1e-10, e
+    M = assemble_M(op.mesh, op.Ts)
+    solver.merge_levels(prob.L_exact)
+    g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=5, max_outer=40)
+    for k in range(prob.nrhs):
+        assert rel(g[k], np.linalg.solve(M, op.rhs[k])) < 1e-7
+    assert info["max_rel_residual"] <= 1e-10
 
 
 # ---------------------------------------------------------------- skeleton operators
