@@ -152,6 +152,15 @@ int hps_set_coeff(hps_ctx* ctx, double kappa, double eta, const double* b);
  * element system is singular. */
 int hps_build_leaves(hps_ctx* ctx, int precision);
 
+/* hps_build_leaves for n contexts at once (section 3.1): the elements of all
+ * contexts on the Cholesky route are built by one kernel launch per GLL order
+ * (one CTA per SM striding over a per-element list of coefficient pointer,
+ * output pointer, h and eta), the others by the pivoted route.  Every context
+ * needs hps_set_coeff; all must live on one device.  Work is enqueued on the
+ * stream of ctxs[0] and the call returns after it completes, so every
+ * context's maps are ready on return.  Errors are reported on ctxs[0]. */
+int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision);
+
 /* Host copy of leaf maps e0 .. e0+count-1: [count][4q][4q] complex128, row-major. */
 int hps_leaf_T(hps_ctx* ctx, int e0, int count, void* T_host);
 

@@ -628,4 +628,105 @@ int hps_profile_read(hps_ctx* c, double* ms, long long* launches, long long* cal
   return HPS_OK;
 }
 
+int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
+  if (!ctxs || n < 1) return HPS_EINVAL;
+  hps_ctx* c0 = ctxs[0];
+  CHECK_CTX(c0);
+  if (precision != HPS_FP64 && precision != HPS_MIXED) return fail(c0, HPS_EINVAL, "precision");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || ctxs[i]->device != c0->device) return fail(c0, HPS_EINVAL, "contexts on one device required");
+    if (!ctxs[i]->have_coeff) return fail(c0, HPS_ENOTBUILT, "hps_set_coeff on every context first");
+  }
+  // classify every element of every context; group the Cholesky-route ones by GLL order
+  std::vector<LeafElem> groups[17];
+  std::vector<std::vector<int>> bad(n);
+  for (int i = 0; i < n; ++i) {
+    hps_ctx* c = ctxs[i];
+    cudaStreamSynchronize(c->stream);
+    free_tree(c);
+    if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
+    if (!c->d_T) return fail(c0, HPS_ENOMEM, "leaf maps");
+    const int n1 = c->N + 1;
+    const double bound = 0.98 * 2.0 * c->mu_min / (0.25 * c->h * c->h);
+    for (int e = 0; e < c->E; ++e) {
+      double cm = -1e300;
+      for (int l = 0; l < n1 * n1; ++l) cm = std::max(cm, c->c_host[(size_t)e * n1 * n1 + l]);
+      if (cm < bound) {
+        LeafElem d;
+        d.c = c->d_c + (size_t)e * n1 * n1;
+        d.T = c->d_T + (size_t)e * c->nb * c->nb;
+        d.h = c->h;
+        d.eta = c->eta;
+        groups[c->N].push_back(d);
+      } else {
+        bad[i].push_back(e);
+      }
+    }
+  }
+  HPS_CK(c0, cudaMemsetAsync(c0->d_flag, 0, sizeof(int), c0->stream));
+  std::vector<void*> scratch;
+  int flag = 0;
+  {
+    PhaseScope ps(c0, HPS_PH_LEAF);
+    for (int N = 2; N <= 16; ++N) {
+      if (groups[N].empty()) continue;
+      // reference tables of order N from any context with that order
+      hps_ctx* cn = nullptr;
+      for (int i = 0; i < n && !cn; ++i)
+        if (ctxs[i]->N == N) cn = ctxs[i];
+      const int nb = 4 * (N - 1);
+      const int count = (int)groups[N].size();
+      const int grid = std::min(count, std::max(1, c0->num_sms));
+      LeafElem* d_ed = static_cast<LeafElem*>(dev_alloc(c0, sizeof(LeafElem) * groups[N].size()));
+      double* Ascr = static_cast<double*>(dev_alloc(c0, sizeof(double) * (size_t)grid * nb * nb));
+      if (!d_ed || !Ascr) return fail(c0, HPS_ENOMEM, "batched leaf workspace");
+      scratch.push_back(d_ed);
+      scratch.push_back(Ascr);
+      HPS_CK(c0, cudaMemcpyAsync(d_ed, groups[N].data(), sizeof(LeafElem) * groups[N].size(), cudaMemcpyHostToDevice,
+                                 c0->stream));
+      LeafParams p;
+      p.N = N; p.q = N - 1; p.ni = (N - 1) * (N - 1); p.nb = nb; p.E = count; p.cw = 8;
+      p.h = 1.0; p.eta = 1.0; p.c = nullptr; p.T = nullptr;
+      p.Dh = cn->d_Dref; p.Kh = cn->d_Kref; p.wh = cn->d_wref;
+      p.Ascr = Ascr; p.flag = c0->d_flag;
+      p.ed = d_ed; p.count = count;
+      HPS_CK(c0, launch_leaf(p, grid, c0->stream));
+    }
+    for (int i = 0; i < n; ++i) {
+      if (bad[i].empty()) continue;
+      hps_ctx* c = ctxs[i];
+      LeafParams p;
+      p.N = c->N; p.q = c->q; p.ni = c->q * c->q; p.nb = c->nb; p.E = c->E; p.cw = 8;
+      p.h = c->h; p.eta = c->eta;
+      p.c = c->d_c; p.Dh = c->d_Dref; p.Kh = c->d_Kref; p.wh = c->d_wref;
+      p.T = c->d_T; p.flag = c0->d_flag;
+      const size_t per = sizeof(double2) * (size_t)p.ni * (p.ni + p.nb);
+      const int chunk = (int)std::max<size_t>(1, std::min<size_t>(bad[i].size(), ((size_t)512 << 20) / per));
+      double2* W = static_cast<double2*>(dev_alloc(c0, per * chunk));
+      int* piv = static_cast<int*>(dev_alloc(c0, sizeof(int) * (size_t)chunk * GJ_NB));
+      double2* lu = static_cast<double2*>(dev_alloc(c0, sizeof(double2) * (size_t)chunk * GJ_NB * GJ_NB));
+      int* d_bad = static_cast<int*>(dev_alloc(c0, sizeof(int) * bad[i].size()));
+      if (!W || !piv || !lu || !d_bad) return fail(c0, HPS_ENOMEM, "robust leaf workspace");
+      scratch.insert(scratch.end(), {W, piv, lu, d_bad});
+      HPS_CK(c0, cudaMemcpyAsync(d_bad, bad[i].data(), sizeof(int) * bad[i].size(), cudaMemcpyHostToDevice, c0->stream));
+      for (size_t b0 = 0; b0 < bad[i].size(); b0 += chunk) {
+        const int nch = (int)std::min<size_t>(chunk, bad[i].size() - b0);
+        HPS_CK(c0, robust_assemble(p, d_bad + b0, nch, W, c0->stream));
+        HPS_CK(c0, gj_solve<double>(W, p.ni, p.ni + p.nb, nch, piv, lu, c0->d_flag, c0->stream));
+        HPS_CK(c0, robust_finish(p, d_bad + b0, nch, W, c0->stream));
+      }
+    }
+  }
+  HPS_CK(c0, cudaMemcpyAsync(&flag, c0->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c0->stream));
+  HPS_CK(c0, cudaStreamSynchronize(c0->stream));
+  for (void* s : scratch) dev_free(c0, s);
+  if (flag) return fail(c0, HPS_ENUMERIC, "singular element system in the batch");
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->n_robust = (int)bad[i].size();
+    ctxs[i]->precision = precision;
+    ctxs[i]->have_leaves = true;
+  }
+  return HPS_OK;
+}
+
 }  // extern "C"

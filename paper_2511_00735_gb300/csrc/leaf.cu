@@ -44,21 +44,25 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
   double* sw = sK + n1 * n1;                          // [n1] reference weights
   double* sc = sw + n1;                               // [n1*n1] c of this element
   const int tid = threadIdx.x, nth = blockDim.x;
-  const double h2 = 0.25 * p.h * p.h;                 // (h/2)^2
-  const double dsc = 2.0 / p.h;
   double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
 
-  for (int l = tid; l < n1 * n1; l += nth) {
-    sD[l] = dsc * p.Dh[l];
-    sK[l] = p.Kh[l];
-  }
+  for (int l = tid; l < n1 * n1; l += nth) sK[l] = p.Kh[l];
   for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
 
-  const int nel = p.elems ? p.count : p.E;
+  const int nel = (p.elems || p.ed) ? p.count : p.E;
   for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
     const int e = p.elems ? p.elems[ei] : ei;
+    const double h = p.ed ? p.ed[ei].h : p.h;
+    const double eta = p.ed ? p.ed[ei].eta : p.eta;
+    const double* ce = p.ed ? p.ed[ei].c : p.c + (long long)e * n1 * n1;
+    double2* To = p.ed ? p.ed[ei].T : p.T + (long long)e * nb * nb;
+    const double h2 = 0.25 * h * h;  // (h/2)^2
+    const double dsc = 2.0 / h;
     __syncthreads();
-    for (int l = tid; l < n1 * n1; l += nth) sc[l] = p.c[(long long)e * n1 * n1 + l];
+    for (int l = tid; l < n1 * n1; l += nth) {
+      sc[l] = ce[l];
+      sD[l] = dsc * p.Dh[l];
+    }
     __syncthreads();
     // ---- assemble L~_ii: interior node I = (i-1) q + (j-1), i, j in 1..q ----
     // L~[(i,j),(i',j')] = K^[i,i'] w^_j d_jj' + w^_i K^[j,j'] d_ii' - c_ij (h/2)^2 w^_i w^_j d_IJ
@@ -83,7 +87,7 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
       __syncthreads();
       double dk = colk[k];
       if (!(dk > 0.0)) {
-        if (tid == 0) atomicCAS(p.flag, 0, e + 1);
+        if (tid == 0) atomicCAS(p.flag, 0, ei + 1);
         dk = 1.0;
       }
       const double inv = 1.0 / dk;
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
       double2 v = make_double2(0.0, 0.0);
       if (j < nb) {
         v.x = A[g * nb + j];
-        if (j == g) v.y = p.eta;
+        if (j == g) v.y = eta;
       } else if (j - nb == g) {
         v.x = 1.0;
       }
@@ -190,11 +194,10 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
     }
     __syncthreads();
     gj_smem<double>(W, nb, ld, ld, nullptr);
-    double2* To = p.T + (long long)e * nb * nb;
     for (int l = tid; l < nb * nb; l += nth) {
       const int g = l / nb, j = l % nb;
       const double2 y = W[g * ld + nb + j];
-      To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * p.eta * y.y, -2.0 * p.eta * y.x);
+      To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
     }
   }
 }

@@ -6,6 +6,12 @@
 namespace hps {
 
 // leaf.cu
+// One element of a multi-problem leaf launch.
+struct LeafElem {
+  const double* c;  // (N+1)^2 coefficient samples of this element
+  double2* T;       // 4q x 4q output map
+  double h, eta;    // element width and impedance parameter of its problem
+};
 struct LeafParams {
   int N, q, ni, nb, E, cw;
   double h, eta;
@@ -18,6 +24,8 @@ struct LeafParams {
   int* flag;          // set to e+1 when a Cholesky pivot is not positive
   const int* elems = nullptr;  // optional list of the elements to build (count entries); null: 0..E-1
   int count = 0;
+  const LeafElem* ed = nullptr;  // optional per-element descriptors (count entries, several problems);
+                                 // then c, T, h, eta above are ignored
 };
 size_t leaf_smem_bytes(int N, int cw);
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s);

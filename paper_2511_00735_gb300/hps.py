@@ -28,7 +28,7 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_sizes", "hps_node_coords", "hps_boundary_points", "hps_index_maps", "hps_set_coeff",
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
-           "hps_leaf_maps_noalloc"]
+           "hps_leaf_maps_noalloc", "hps_build_leaves_batch"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "hps_profile": (i, [vp, i]),
         "hps_profile_read": (i, [vp, vp, vp, vp]),
         "hps_leaf_maps_noalloc": (i, [i, vp, i, d, d, vp, i, vp]),
+        "hps_build_leaves_batch": (i, [C.POINTER(vp), i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -128,8 +129,11 @@ class Solver:
             dev = torch.device("cuda", device)
 
             def _alloc(nbytes, user):
+                # allocate on this context's stream whatever thread calls, so the caching
+                # allocator only reuses the block in that stream's order
                 try:
-                    t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+                    with torch.cuda.stream(self.stream):
+                        t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
                 except RuntimeError:
                     return None
                 p = t.data_ptr()
@@ -281,6 +285,15 @@ class Solver:
              "max_rel_residual": info.max_rel_residual, "iterations": list(its), "rel_residual": list(res),
              "ms_rhs": info.ms_rhs, "ms_solve": info.ms_solve}
         return out, d
+
+
+def build_leaves_batch(solvers, precision: int = HPS_FP64):
+    """hps_build_leaves for several Solver contexts at once (one leaf launch per GLL order)."""
+    lib = load_library()
+    arr = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    st = lib.hps_build_leaves_batch(arr, len(solvers), precision)
+    if st != HPS_OK:
+        raise HPSError(st, (lib.hps_last_error(solvers[0].h) or b"").decode())
 
 
 def kernel_launches() -> int:
