@@ -86,6 +86,7 @@ class Server:
         self.stop = False
         self.completed = []
         self.peak_bytes = 0
+        self.evictions = 0
         self.workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
         for w in self.workers:
             w.start()
@@ -141,6 +142,7 @@ class Server:
                     victim = min(idle, key=lambda x: x.last_used)
                     victim.solver.close()
                     del self.trees[victim.key]
+                    self.evictions += 1
                 stream = self.torch.cuda.Stream(self.device)
                 t = _Tree(r.key, H.Solver(self.device, stream=stream), stream)
                 t.reserved = need
