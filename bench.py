@@ -330,6 +330,49 @@ def cpu_baseline_entry(prob, iterations):
                          "solve_per_rhs": est["t_solve_per_rhs"]}}
 
 
+# ---------------------------------------------------------------------------- batching / serving
+def run_systems(args):
+    from paper_2511_00735_gb300 import hps as H
+
+    prec = H.HPS_MIXED if args.precision == "mixed" else H.HPS_FP64
+    clocks = ClockSampler(0)
+    l0 = None
+    if args.workload == "batch":
+        from paper_2511_00735_gb300 import batch as B
+
+        count = args.count or 512
+        B.run_mix(min(count, 16), seed=99, slots=args.slots, precision=prec)  # warm-up (other seeds)
+        clocks.start()
+        l0 = H.kernel_launches()
+        r = B.run_mix(count, seed=3, slots=args.slots, precision=prec)
+        line = {"metric": "Helmholtz solves/s at rel-residual 1e-10, batching mix", "value": r["solves_per_s"],
+                "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32" if prec else "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{count} problems: grids U{{8,16,32,64}}^2, N U{{8,12,16}}, kappa U[20,150], "
+                                       "1 bump, 1-8 RHS", "slots": args.slots, "precision": args.precision},
+                **r}
+    else:
+        from paper_2511_00735_gb300 import serve as S
+
+        count = args.count or 2000
+        reqs = S.poisson_stream(count, args.rate)
+        srv = S.Server(0, workers=args.slots, precision=prec, hbm_cap=150e9)
+        clocks.start()
+        l0 = H.kernel_launches()
+        r = S.run_stream(reqs, srv)
+        srv.close()
+        line = {"metric": "Helmholtz solves/s and p50/p99 latency at rel-residual 1e-10, serving stream",
+                "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+                "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
+                "config": {"workload": f"{count} Poisson arrivals at {args.rate}/s: 90% batching-mix trees, "
+                                       "10% 128x128 N=16 kappa=200 trees, 1-64 RHS per request, 150 GB cap",
+                           "workers": args.slots, "precision": args.precision},
+                **r}
+    line["gpu_launches"] = H.kernel_launches() - l0
+    line["clocks"] = clocks.stop()
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -342,7 +385,14 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--workload", default="scattering64", choices=["scattering64", "batch", "serve"],
+                    help="scattering64: the timed step above; batch: the 512-problem mix; serve: a Poisson stream")
+    ap.add_argument("--count", type=int, default=0, help="problems (batch) or requests (serve)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
+    ap.add_argument("--slots", type=int, default=8, help="batch slots / serve workers")
     args = ap.parse_args()
+    if args.workload != "scattering64":
+        return run_systems(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

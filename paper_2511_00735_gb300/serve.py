@@ -129,8 +129,11 @@ class Server:
             if t is not None and t.busy:
                 continue
             batch, nrhs = [], 0
+            # right-hand sides per solve: at most max_rhs, and a Krylov workspace of about 16 GB
+            per_rhs = (2 * self.restart + 4) * r.prob.nx * r.prob.nx * 4 * (r.prob.N - 1) * 16
+            cap_rhs = max(r.prob.nrhs, min(self.max_rhs, int(16e9 // per_rhs)))
             for r2 in list(self.pending):
-                if r2.key == r.key and nrhs + r2.prob.nrhs <= self.max_rhs:
+                if r2.key == r.key and nrhs + r2.prob.nrhs <= cap_rhs:
                     batch.append(r2)
                     nrhs += r2.prob.nrhs
             if t is None:
