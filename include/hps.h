@@ -161,6 +161,11 @@ int hps_build_leaves(hps_ctx* ctx, int precision);
  * context's maps are ready on return.  Errors are reported on ctxs[0]. */
 int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision);
 
+/* Free the per-solve workspaces (FGMRES basis, sweep and coarse vectors,
+ * staging) and keep the leaf maps and the merge tree; the next solve
+ * allocates them again.  Synchronises the context's stream. */
+int hps_release_workspace(hps_ctx* ctx);
+
 /* Host copy of leaf maps e0 .. e0+count-1: [count][4q][4q] complex128, row-major. */
 int hps_leaf_T(hps_ctx* ctx, int e0, int count, void* T_host);
 

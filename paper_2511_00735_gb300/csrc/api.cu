@@ -729,4 +729,19 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
   return HPS_OK;
 }
 
+int hps_release_workspace(hps_ctx* c) {
+  CHECK_CTX(c);
+  HPS_CK(c, cudaStreamSynchronize(c->stream));
+  free_solver(c);
+  for (auto& s : c->stages) FREE(s.vec);
+  FREE(c->sw_x);
+  FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);
+  FREE(c->cg_nrm); FREE(c->cg_y); FREE(c->cg_g); FREE(c->cg_s); FREE(c->cg_part);
+  FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c);
+  FREE(c->ex_r); FREE(c->ex_e);
+  c->nrhs_cap = 0;
+  c->cg_k = c->cg_nrhs = c->ex_nrhs = 0;
+  return HPS_OK;
+}
+
 }  // extern "C"

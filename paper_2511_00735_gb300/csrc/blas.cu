@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(NT) gj_update_kernel(c_t<R>* W, int m, int ld,
 
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 48 * 1024) smem_optin(kernel);
 }
 
 

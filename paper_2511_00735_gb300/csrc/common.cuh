@@ -10,6 +10,16 @@ namespace hps {
 // Counts one kernel launch (total and per profiling phase of the calling context).
 void note_launch(int n = 1);
 
+// Raise a kernel's dynamic shared-memory limit once to the device's opt-in maximum
+// (a per-launch value would race between host threads launching different sizes).
+template <typename K>
+inline void smem_optin(K kernel) {
+  int dev = 0, mx = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
 template <typename R> struct cplx;
 template <> struct cplx<double> { using T = double2; };
 template <> struct cplx<float> { using T = float2; };

@@ -356,8 +356,7 @@ size_t leaf_smem_bytes(int N, int cw) {
 
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
   const size_t smem = leaf_smem_bytes(p.N, p.cw);
-  cudaError_t err = cudaFuncSetAttribute(leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
+  smem_optin(leaf_kernel);
   leaf_kernel<<<grid, 256, smem, s>>>(p);
   note_launch();
   return cudaGetLastError();

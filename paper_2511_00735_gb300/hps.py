@@ -28,7 +28,7 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_sizes", "hps_node_coords", "hps_boundary_points", "hps_index_maps", "hps_set_coeff",
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
-           "hps_leaf_maps_noalloc", "hps_build_leaves_batch"]
+           "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
         "hps_profile_read": (i, [vp, vp, vp, vp]),
         "hps_leaf_maps_noalloc": (i, [i, vp, i, d, d, vp, i, vp]),
         "hps_build_leaves_batch": (i, [C.POINTER(vp), i, i]),
+        "hps_release_workspace": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,6 +187,10 @@ class Solver:
 
     def bytes_held(self) -> int:
         return self.sizes()[3]
+
+    def release_workspace(self):
+        """Free the per-solve buffers, keep the leaf maps and the merge tree."""
+        self._check(self.lib.hps_release_workspace(self.h))
 
     def node_coords(self):
         n = self.E * (self.N + 1) ** 2

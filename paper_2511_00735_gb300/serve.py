@@ -48,14 +48,23 @@ class Request:
 
 def tree_bytes_estimate(nx: int, N: int, nrhs: int, precision: int, restart: int = 60) -> int:
     """Device bytes of one context: leaf maps, merge tree and sweep operators, FGMRES workspace."""
+    return tree_only_bytes(nx, N, precision) + krylov_bytes(nx, N, nrhs, restart)
+
+
+def tree_only_bytes(nx: int, N: int, precision: int) -> int:
+    """Leaf maps (FP64), stage maps, interface inverses and sweep operators (upper estimate)."""
     q = N - 1
     E = nx * nx
     leaf = E * (4 * q) ** 2 * 16
     cs = 16 if precision == H.HPS_FP64 else 8
     L = 2 * int(round(math.log2(nx)))
-    tree = int(2.5 * L * E * (4 * q) ** 2 * cs)
-    krylov = (2 * restart + 4) * E * 4 * q * nrhs * 16
-    return leaf + tree + krylov + (64 << 20)
+    return leaf + int(3.0 * L * E * (4 * q) ** 2 * cs) + (64 << 20)
+
+
+def krylov_bytes(nx: int, N: int, nrhs: int, restart: int = 60) -> int:
+    """Per-solve workspace: FGMRES basis V and Z, sweep vectors of every stage, staging."""
+    rows = nx * nx * 4 * (N - 1)
+    return (2 * restart + 8) * rows * nrhs * 16 + 4 * rows * nrhs * 16 + (32 << 20)
 
 
 class _Tree:
@@ -66,7 +75,7 @@ class _Tree:
         self.busy = False
         self.last_used = time.perf_counter()
         self.ready = False
-        self.reserved = 0
+        self.tree_bytes = 0
 
 
 class Server:
@@ -87,6 +96,9 @@ class Server:
         self.completed = []
         self.peak_bytes = 0
         self.evictions = 0
+        self.inflight = 0  # bytes reserved by running jobs
+        torch.cuda.empty_cache()
+        self.base = torch.cuda.memory_reserved(device)  # held by the process before the server started
         self.workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
         for w in self.workers:
             w.start()
@@ -116,8 +128,10 @@ class Server:
 
     # ---- internals ---------------------------------------------------------
     def _held(self) -> int:
-        # ready trees: what their context holds; trees being built: their admission estimate
-        return sum(t.solver.bytes_held() if t.ready else t.reserved for t in self.trees.values())
+        """Device bytes in use: built trees (measured after their build) plus what running jobs reserved;
+        never less than what torch's allocator holds."""
+        model = sum(t.tree_bytes for t in self.trees.values() if t.ready) + self.inflight
+        return max(model, self.torch.cuda.memory_reserved(self.device) - self.base)
 
     def _pick(self):
         """Under the lock: choose the next job (tree, requests) or None."""
@@ -136,20 +150,29 @@ class Server:
                 if r2.key == r.key and nrhs + r2.prob.nrhs <= cap_rhs:
                     batch.append(r2)
                     nrhs += r2.prob.nrhs
+            need = krylov_bytes(r.prob.nx, r.prob.N, nrhs, self.restart)
             if t is None:
-                need = tree_bytes_estimate(r.prob.nx, r.prob.N, nrhs, self.precision, self.restart)
-                while self._held() + need > self.hbm_cap:
-                    idle = [x for x in self.trees.values() if not x.busy and x.ready]
-                    if not idle:
-                        return None  # wait for memory
+                need += tree_only_bytes(r.prob.nx, r.prob.N, self.precision)
+            while self._held() + need > self.hbm_cap:
+                idle = [x for x in self.trees.values() if not x.busy and x.ready and x is not t]
+                if idle:
                     victim = min(idle, key=lambda x: x.last_used)
                     victim.solver.close()
                     del self.trees[victim.key]
                     self.evictions += 1
+                    continue
+                model = sum(x.tree_bytes for x in self.trees.values() if x.ready) + self.inflight
+                if self.torch.cuda.memory_reserved(self.device) - self.base > model + need:
+                    self.torch.cuda.empty_cache()  # return cached blocks, then re-check
+                    if self._held() + need <= self.hbm_cap:
+                        break
+                return None  # wait for running jobs to release memory
+            if t is None:
                 stream = self.torch.cuda.Stream(self.device)
                 t = _Tree(r.key, H.Solver(self.device, stream=stream), stream)
-                t.reserved = need
                 self.trees[r.key] = t
+            t.job_bytes = need
+            self.inflight += need
             t.busy = True
             for r2 in batch:
                 self.pending.remove(r2)
@@ -178,6 +201,8 @@ class Server:
                         self.completed.append(r)
             finally:
                 with self.lock:
+                    self.inflight -= tree.job_bytes
+                    tree.job_bytes = 0
                     tree.busy = False
                     tree.last_used = time.perf_counter()
                     self.peak_bytes = max(self.peak_bytes, self._held())
@@ -195,6 +220,7 @@ class Server:
                 s.merge_levels(prob.L_exact)
                 bx, by, bnx, bny = s.boundary_points()
                 tree.bdry = (bx, by, bnx, bny)
+                tree.tree_bytes = s.bytes_held()
                 tree.ready = True
             bx, by, bnx, bny = tree.bdry
             thetas = [th for r in batch for th in r.prob.thetas]
@@ -202,6 +228,7 @@ class Server:
                                                for th in thetas]))
             g, info = s.gmres_solve(t, tol=self.tol, inner_iters=prob.inner_iters, restart=self.restart,
                                     max_outer=self.max_outer, raise_on_notconv=False)
+            s.release_workspace()
         now = time.perf_counter() - self.t_origin
         k = 0
         with self.lock:
@@ -235,7 +262,7 @@ def poisson_stream(count: int, rate: float, seed: int = 5, big_fraction: float =
     return reqs
 
 
-def run_stream(reqs, server: Server, time_scale: float = 1.0):
+def run_stream(reqs, server: Server, time_scale: float = 1.0, timeout: float = 3600.0):
     """Replay the arrivals (arrival times multiplied by time_scale) and wait for every result."""
     t0 = time.perf_counter()
     server.t_origin = t0
@@ -245,7 +272,7 @@ def run_stream(reqs, server: Server, time_scale: float = 1.0):
         if delay > 0:
             time.sleep(delay)
         server.submit(r)
-    done = server.drain(len(reqs))
+    done = server.drain(len(reqs), timeout)
     makespan = time.perf_counter() - t0
     lat = np.array([r.done - r.arrival for r in done])
     solves = sum(r.prob.nrhs for r in done)

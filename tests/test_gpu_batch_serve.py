@@ -78,7 +78,7 @@ def test_serve_same_alone_and_in_mix(gpu):
                            inner_iters=b.inner_iters, name=b.name)
         reqs.append(S.Request(i, p, t))
     srv = S.Server(0, workers=3, precision=H.HPS_MIXED, hbm_cap=40e9)
-    stats = S.run_stream(reqs, srv)
+    stats = S.run_stream(reqs, srv, timeout=300)
     srv.close()
     assert stats["requests"] == 24 and stats["max_rel_residual"] <= 1e-10
     assert stats["mean_batch"] > 1.0  # requests for a busy tree joined its next solve
@@ -92,9 +92,9 @@ def test_admission_cap_evicts_idle_trees(gpu):
     bases = [inputs.single_bump(8, 8, 20.0 + 5 * i, 1, seed=50 + i) for i in range(5)]
     reqs = [S.Request(i, b, 0.001 * i) for i, b in enumerate(bases)]
     one = S.tree_bytes_estimate(8, 8, 1, H.HPS_MIXED)
-    cap = 2.5 * one
+    cap = 2.5 * one  # about two trees with their solve workspaces
     srv = S.Server(0, workers=1, precision=H.HPS_MIXED, hbm_cap=cap)
-    stats = S.run_stream(reqs, srv)
+    stats = S.run_stream(reqs, srv, timeout=300)
     live, ev = len(srv.trees), srv.evictions
     srv.close()
     assert stats["requests"] == 5 and stats["max_rel_residual"] <= 1e-10
