@@ -17,7 +17,10 @@ inline void smem_optin(K kernel) {
   int dev = 0, mx = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) mx -= (int)fa.sharedSizeBytes;  // minus static smem
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaGetLastError();
 }
 
 template <typename R> struct cplx;
