@@ -354,7 +354,7 @@ def run_systems(args):
     else:
         from paper_2511_00735_gb300 import serve as S
 
-        count = args.count or 2000
+        count = args.count or 200
         reqs = S.poisson_stream(count, args.rate)
         srv = S.Server(0, workers=args.slots, precision=prec, hbm_cap=150e9)
         clocks.start()

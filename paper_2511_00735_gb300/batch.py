@@ -104,6 +104,9 @@ def run_mix(count: int = 512, seed: int = 3, slots: int = 8, precision: int = H.
     br.close()
     nsolves = sum(p.nrhs for p in probs)
     conv = sum(info["converged"] for _, info in res)
-    return {"problems": count, "solves": nsolves, "seconds": dt, "solves_per_s": nsolves / dt,
-            "converged": conv, "max_rel_residual": max(info["max_rel_residual"] for _, info in res),
+    conv_res = [r for _, info in res for r in info["rel_residual"] if r <= 1e-10]
+    stalled = [(p.nx, p.N, round(p.kappa, 1)) for p, (_, info) in zip(probs, res) if info["converged"] < p.nrhs]
+    return {"problems": count, "solves": nsolves, "converged_solves": conv, "seconds": dt,
+            "solves_per_s": conv / dt, "max_rel_residual_converged": max(conv_res) if conv_res else None,
+            "not_converged_problems": stalled,
             "max_iterations": max(info["outer_iterations"] for _, info in res)}

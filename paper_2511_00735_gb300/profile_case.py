@@ -27,11 +27,15 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--multi", action="store_true", help="the 128x128 kappa=200 eight-bump problem")
     a = ap.parse_args()
     prec = H.HPS_MIXED if a.precision == "mixed" else H.HPS_FP64
     kappa = 100.0 * a.nx / 64.0
     L = 2 * int(round(np.log2(a.nx)))
-    prob = inputs.single_bump(a.nx, 16, kappa, a.nrhs, seed=1, L_exact=max(L - 2, 0))
+    if a.multi:
+        prob = inputs.mixed_128x128(seed=2, nrhs=a.nrhs)
+    else:
+        prob = inputs.single_bump(a.nx, 16, kappa, a.nrhs, seed=1, L_exact=max(L - 2, 0))
     s = H.Solver(0)
     t = H.setup(s, prob, prec, build=False)
     td = torch.from_numpy(t).cuda()
@@ -56,8 +60,11 @@ def main():
                 s.precond_apply(r, prob.inner_iters)
         else:
             s.merge_levels(prob.L_exact)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             _, info = s.gmres_solve(td, tol=1e-10, inner_iters=prob.inner_iters)
-            print("iterations", info["outer_iterations"], "residual", info["max_rel_residual"])
+            print("iterations", info["outer_iterations"], "residual", info["max_rel_residual"],
+                  f"solve {time.perf_counter() - t1:.3f} s, bytes held {s.bytes_held() / 1e9:.1f} GB")
     torch.cuda.synchronize()
     print(f"{a.phase} x{a.repeat} on {a.nx}x{a.nx}: {time.perf_counter() - t0:.3f} s")
     s.close()
