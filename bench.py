@@ -359,7 +359,8 @@ def run_systems(args):
         srv = S.Server(0, workers=args.slots, precision=prec, hbm_cap=150e9)
         clocks.start()
         l0 = H.kernel_launches()
-        r = S.run_stream(reqs, srv)
+        r = S.run_stream(reqs, srv, timeout=args.serve_timeout,
+                         progress=lambda m: print(m, file=sys.stderr, flush=True))
         srv.close()
         line = {"metric": "Helmholtz solves/s and p50/p99 latency at rel-residual 1e-10, serving stream",
                 "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
@@ -390,6 +391,7 @@ def main():
     ap.add_argument("--count", type=int, default=0, help="problems (batch) or requests (serve)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="batch slots / serve workers")
+    ap.add_argument("--serve-timeout", type=float, default=240.0, help="serve: stop waiting after this many seconds")
     args = ap.parse_args()
     if args.workload != "scattering64":
         return run_systems(args)

@@ -109,11 +109,17 @@ class Server:
             self.pending.append(req)
             self.lock.notify_all()
 
-    def drain(self, n_expected: int, timeout: float = 3600.0):
+    def drain(self, n_expected: int, timeout: float = 3600.0, progress=None):
         t0 = time.perf_counter()
+        last = t0
         with self.lock:
             while len(self.completed) < n_expected and time.perf_counter() - t0 < timeout:
                 self.lock.wait(0.05)
+                if progress and time.perf_counter() - last > 10.0:
+                    last = time.perf_counter()
+                    progress(f"[serve] t={last - t0:.0f}s done={len(self.completed)}/{n_expected} "
+                             f"pending={len(self.pending)} trees={len(self.trees)} "
+                             f"busy={sum(t.busy for t in self.trees.values())} held={self._held() / 1e9:.1f}GB")
         return list(self.completed)
 
     def close(self):
@@ -143,14 +149,16 @@ class Server:
             if t is not None and t.busy:
                 continue
             batch, nrhs = [], 0
-            # right-hand sides per solve: at most max_rhs, and a Krylov workspace of about 16 GB
-            per_rhs = (2 * self.restart + 4) * r.prob.nx * r.prob.nx * 4 * (r.prob.N - 1) * 16
-            cap_rhs = max(r.prob.nrhs, min(self.max_rhs, int(16e9 // per_rhs)))
+            # right-hand sides per solve call: at most max_rhs and a Krylov workspace of about 16 GB;
+            # a batch larger than that (one big request) is solved in consecutive chunks
+            per_rhs = krylov_bytes(r.prob.nx, r.prob.N, 1, self.restart)
+            chunk = max(1, min(self.max_rhs, int(16e9 // per_rhs)))
+            cap_rhs = max(r.prob.nrhs, chunk)
             for r2 in list(self.pending):
                 if r2.key == r.key and nrhs + r2.prob.nrhs <= cap_rhs:
                     batch.append(r2)
                     nrhs += r2.prob.nrhs
-            need = krylov_bytes(r.prob.nx, r.prob.N, nrhs, self.restart)
+            need = krylov_bytes(r.prob.nx, r.prob.N, min(nrhs, chunk), self.restart)
             if t is None:
                 need += tree_only_bytes(r.prob.nx, r.prob.N, self.precision)
             while self._held() + need > self.hbm_cap:
@@ -172,6 +180,7 @@ class Server:
                 t = _Tree(r.key, H.Solver(self.device, stream=stream), stream)
                 self.trees[r.key] = t
             t.job_bytes = need
+            t.chunk = chunk
             self.inflight += need
             t.busy = True
             for r2 in batch:
@@ -226,9 +235,17 @@ class Server:
             thetas = [th for r in batch for th in r.prob.thetas]
             t = np.ascontiguousarray(np.stack([inputs.plane_wave_impedance(th, prob.kappa, prob.eta, bx, by, bnx, bny)
                                                for th in thetas]))
-            g, info = s.gmres_solve(t, tol=self.tol, inner_iters=prob.inner_iters, restart=self.restart,
-                                    max_outer=self.max_outer, raise_on_notconv=False)
+            gs, its, res = [], [], []
+            for c0 in range(0, len(thetas), tree.chunk):
+                g, info = s.gmres_solve(np.ascontiguousarray(t[c0:c0 + tree.chunk]), tol=self.tol,
+                                        inner_iters=prob.inner_iters, restart=self.restart, max_outer=self.max_outer,
+                                        raise_on_notconv=False)
+                gs.append(g)
+                its += info["iterations"]
+                res += info["rel_residual"]
             s.release_workspace()
+            g = np.concatenate(gs)
+            info = {"iterations": its, "rel_residual": res}
         now = time.perf_counter() - self.t_origin
         k = 0
         with self.lock:
@@ -262,7 +279,7 @@ def poisson_stream(count: int, rate: float, seed: int = 5, big_fraction: float =
     return reqs
 
 
-def run_stream(reqs, server: Server, time_scale: float = 1.0, timeout: float = 3600.0):
+def run_stream(reqs, server: Server, time_scale: float = 1.0, timeout: float = 3600.0, progress=None):
     """Replay the arrivals (arrival times multiplied by time_scale) and wait for every result."""
     t0 = time.perf_counter()
     server.t_origin = t0
@@ -272,12 +289,14 @@ def run_stream(reqs, server: Server, time_scale: float = 1.0, timeout: float = 3
         if delay > 0:
             time.sleep(delay)
         server.submit(r)
-    done = server.drain(len(reqs), timeout)
+    done = server.drain(len(reqs), timeout, progress)
     makespan = time.perf_counter() - t0
     lat = np.array([r.done - r.arrival for r in done])
-    solves = sum(r.prob.nrhs for r in done)
-    res = max((max(r.info["rel_residual"]) for r in done), default=0.0)
-    return {"requests": len(done), "solves": solves, "seconds": makespan, "solves_per_s": solves / makespan,
+    ok = [r for r in done if max(r.info["rel_residual"]) <= server.tol]
+    solves = sum(r.prob.nrhs for r in ok)
+    res = max((max(r.info["rel_residual"]) for r in ok), default=0.0)
+    return {"requests": len(done), "requests_submitted": len(reqs), "requests_converged": len(ok), "solves": solves,
+            "seconds": makespan, "solves_per_s": solves / makespan,
             "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "max_rel_residual": res, "peak_device_bytes": server.peak_bytes,
