@@ -213,6 +213,9 @@ class Server:
                     self.inflight -= tree.job_bytes
                     tree.job_bytes = 0
                     tree.busy = False
+                    # the caching allocator keeps freed blocks per stream; hand them back when over the cap
+                    if self.torch.cuda.memory_reserved(self.device) - self.base > self.hbm_cap:
+                        self.torch.cuda.empty_cache()
                     tree.last_used = time.perf_counter()
                     self.peak_bytes = max(self.peak_bytes, self._held())
                     self.lock.notify_all()
