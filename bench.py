@@ -140,6 +140,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     prob = inputs.fp64_64x64(seed=1 + rank, nrhs=args.nrhs)
     prec = H.HPS_MIXED if args.precision == "mixed" else H.HPS_FP64
     s = H.Solver(local_rank)
+    s.set_outer_arith({"default": H.OUTER_DEFAULT, "fp64": H.OUTER_FP64, "df64": H.OUTER_DF64}[args.outer])
     t_host = H.setup(s, prob, prec, build=False)
     X, Y = s.node_coords()
     b_host = np.ascontiguousarray(inputs.eval_b(prob.bumps, X, Y))
@@ -215,6 +216,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     # ---- the plain FP64 GPU path on the same workload (comparison) ----
     fp64 = None
     if prec == H.HPS_MIXED and not args.no_fp64:
+        s.set_outer_arith(H.OUTER_DEFAULT)
         step(H.HPS_FP64, b_dev, t_dev, g_dev)
         k64 = max(1, min(args.steps, 2))
         ms64, _, inf64 = timed(lambda: step(H.HPS_FP64, b_dev, t_dev, g_dev), k64)
@@ -383,6 +385,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--outer", default="default", choices=["default", "fp64", "df64"],
+                    help="outer FGMRES arithmetic (default: df64 for mixed, fp64 for fp64)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -472,6 +476,7 @@ def main():
         "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": nrhs * world, "precision": args.precision,
+                   "outer": args.outer if args.outer != "default" else ("df64" if args.precision == "mixed" else "fp64"),
                    "tol": args.tol, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: leaf maps 236 MB, merge tree ~1.3 GB, Krylov basis 3.8 GB per step"},
         "iterations": r["its"], "max_rel_residual": r["res"], "converged": r["conv"],

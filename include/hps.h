@@ -76,6 +76,9 @@ enum {
 
 enum { HPS_FP64 = 0, HPS_MIXED = 1 };
 
+/* Arithmetic of the outer FGMRES (hps_set_outer_arith). */
+enum { HPS_OUTER_DEFAULT = -1, HPS_OUTER_FP64 = 0, HPS_OUTER_DF64 = 1 };
+
 /* Per-solve report of hps_gmres_solve. */
 typedef struct {
   int outer_iterations;     /* FGMRES iterations (max over right-hand sides)         */
@@ -207,12 +210,26 @@ int hps_gmres_solve(hps_ctx* ctx, const void* t, const void* s, int nrhs, double
                     int inner_iters, int restart, int max_outer, void* g_out,
                     hps_info* info);
 
+/* Arithmetic of the outer FGMRES of later hps_gmres_solve calls on ctx:
+ *   HPS_OUTER_FP64     matvec, Gram-Schmidt and basis in FP64 (section 4.3);
+ *   HPS_OUTER_DF64     (with HPS_MIXED leaves only) the same steps on pairs of
+ *                      FP32 numbers (about 48 significand bits, error-free
+ *                      TwoSum/TwoProduct accumulation), the preconditioned
+ *                      directions kept in FP32 (they are the FP32 tree's
+ *                      output); every restart residual, and so every
+ *                      convergence decision and the reported residual, is
+ *                      still computed in FP64;
+ *   HPS_OUTER_DEFAULT  DF64 for HPS_MIXED, FP64 for HPS_FP64 (the initial state).
+ * HPS_EINVAL for other values.  DF64 needs HPS_MIXED leaves: with HPS_FP64
+ * leaves hps_gmres_solve returns HPS_EINVAL (there is no silent fallback). */
+int hps_set_outer_arith(hps_ctx* ctx, int mode);
+
 /* Profiling phases of hps_profile_read. */
 enum {
   HPS_PH_LEAF = 0,   /* hps_build_leaves: the leaf kernel alone                     */
   HPS_PH_MERGE,      /* hps_merge_levels                                            */
   HPS_PH_RHS,        /* RHS assembly inside hps_gmres_solve                         */
-  HPS_PH_MATVEC,     /* FP64 skeleton matvec inside hps_gmres_solve (one kernel each) */
+  HPS_PH_MATVEC,     /* skeleton matvec inside hps_gmres_solve (one kernel each)     */
   HPS_PH_PRECOND,    /* MG(M) applications inside hps_gmres_solve                   */
   HPS_PH_ORTHO,      /* Gram-Schmidt inside hps_gmres_solve                         */
   HPS_PH_OTHER,      /* final residual and output                                   */

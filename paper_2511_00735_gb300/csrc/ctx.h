@@ -134,6 +134,12 @@ struct hps_ctx {
   double2* pin_h = nullptr;  // pinned host mirror of fg_h
   double2* pin_y = nullptr;
   double* pin_floor = nullptr;
+  // df64 outer FGMRES (HPS_OUTER_DF64): basis, residual and iterate as float pairs,
+  // preconditioned directions in FP32, a df64 copy of the leaf maps
+  int outer_arith = HPS_OUTER_DEFAULT;
+  bool fg_df = false;
+  float4 *df_V = nullptr, *df_x = nullptr, *df_w = nullptr, *df_part = nullptr, *df_T = nullptr;
+  float2* df_Z = nullptr;
   double2 *pv_in = nullptr, *pv_out = nullptr;  // precond_apply/matvec ES staging
   int pv_nrhs = 0;
 
@@ -161,6 +167,8 @@ int ensure_sweep_buffers(hps_ctx* c, int nrhs);
 int build_tree(hps_ctx* c, int L_exact, int exact_coarse);
 template <typename R>
 int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int inner_iters);
+// the FP32 V-cycle on a df64 residual (its leading FP32 parts), FP32 result
+int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int inner_iters);
 
 }  // namespace hps
 

@@ -1,0 +1,331 @@
+// Double-float ("df64") vector kernels for the outer FGMRES of the mixed path.
+//
+// GB300 executes FP32 fused multiply-adds about 58x faster than FP64 ones, so the
+// FP64-class work of the outer iteration -- the skeleton matvec and the
+// Gram-Schmidt dot products and updates -- runs on pairs of floats (hi, lo) with
+// |lo| <= ulp(hi)/2, i.e. about 48 significand bits.  Building blocks are the
+// error-free transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and the
+// FMA-based TwoProduct, accumulated as in the compensated dot product "Dot2"
+// (Ogita, Rump, Oishi, SIAM J. Sci. Comput. 26 (2005)): the running sum keeps
+// its rounding errors and the products' errors in a separate float that is
+// added once at the end.  Relative error of a length-n sum ~ n eps32^2 cond,
+// far below the 1e-10 residual the solver certifies; the final residual of a
+// solve is recomputed in true FP64.
+//
+// Storage: one complex df64 number is a float4 (re_hi, im_hi, re_lo, im_lo).
+#include "common.cuh"
+#include "df64.cuh"
+#include "skel.cuh"
+
+namespace hps {
+
+namespace {
+constexpr int NT = 256;
+
+inline int nblocks(long long work, int cap) {
+  long long b = (work + NT - 1) / NT;
+  if (b < 1) b = 1;
+  return (int)(b > cap ? cap : b);
+}
+
+// The error-free transformations below must run exactly as written: every
+// rounding step uses the _rn intrinsics, which the compiler never contracts
+// into fused multiply-adds (a contracted s + a*b would break TwoSum).
+
+// t + err = a + b exactly (TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& t, float& err) {
+  t = __fadd_rn(a, b);
+  const float v = __fsub_rn(t, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, v)), __fsub_rn(b, v));
+}
+
+// (s, c) += a * b for real df64 a = (ah, al), b = (bh, bl): TwoProduct of the leading
+// parts with the cross terms folded into its error, TwoSum into s, errors into c.
+__device__ __forceinline__ void dot2(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// normalise (s, c) into (hi, lo)
+__device__ __forceinline__ void fast2(float s, float c, float& hi, float& lo) { two_sum(s, c, hi, lo); }
+
+struct cacc {  // complex df64 accumulator
+  float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+};
+
+// acc += a * b   (complex, a and b df64)
+__device__ __forceinline__ void cdot2(cacc& acc, float4 a, float4 b) {
+  dot2(acc.rs, acc.rc, a.x, a.z, b.x, b.z);
+  dot2(acc.rs, acc.rc, -a.y, -a.w, b.y, b.w);
+  dot2(acc.is, acc.ic, a.x, a.z, b.y, b.w);
+  dot2(acc.is, acc.ic, a.y, a.w, b.x, b.z);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cdot2_conj(cacc& acc, float4 a, float4 b) {
+  dot2(acc.rs, acc.rc, a.x, a.z, b.x, b.z);
+  dot2(acc.rs, acc.rc, a.y, a.w, b.y, b.w);
+  dot2(acc.is, acc.ic, a.x, a.z, b.y, b.w);
+  dot2(acc.is, acc.ic, -a.y, -a.w, b.x, b.z);
+}
+// acc += a (df64 complex value)
+__device__ __forceinline__ void cadd2(cacc& acc, float4 a) {
+  dot2(acc.rs, acc.rc, a.x, a.z, 1.f, 0.f);
+  dot2(acc.is, acc.ic, a.y, a.w, 1.f, 0.f);
+}
+__device__ __forceinline__ float4 cfin(const cacc& a) {
+  float4 r;
+  fast2(a.rs, a.rc, r.x, r.z);
+  fast2(a.is, a.ic, r.y, r.w);
+  return r;
+}
+__device__ __forceinline__ float4 from_f2(float2 v) { return make_float4(v.x, v.y, 0.f, 0.f); }
+__device__ __forceinline__ float4 from_d2(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 to_d2(float4 v) {
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+__device__ __forceinline__ float4 ld(const float4* p, long long i) { return p[i]; }
+__device__ __forceinline__ float4 ld(const float2* p, long long i) { return from_f2(p[i]); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+__global__ void df_from_d_kernel(float4* __restrict__ dst, const double2* __restrict__ src, long long n) {
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT)
+    dst[l] = from_d2(src[l]);
+}
+__global__ void df_to_d_kernel(double2* __restrict__ dst, const float4* __restrict__ src, long long n) {
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT)
+    dst[l] = to_d2(src[l]);
+}
+cudaError_t df_from_d(float4* dst, const double2* src, long long n, cudaStream_t s) {
+  df_from_d_kernel<<<nblocks(n, 8192), NT, 0, s>>>(dst, src, n);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t df_to_d(double2* dst, const float4* src, long long n, cudaStream_t s) {
+  df_to_d_kernel<<<nblocks(n, 8192), NT, 0, s>>>(dst, src, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// rows of hi parts (FP32) through a row map: dst[row][r] = hi(src[map[row]][r]) (map < 0 -> 0)
+__global__ void df_gather_hi_kernel(float2* __restrict__ dst, const float4* __restrict__ src, const int* __restrict__ map,
+                                    long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map[row];
+    const float4 v = m >= 0 ? src[(long long)m * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    dst[l] = make_float2(v.x, v.y);
+  }
+}
+cudaError_t df_gather_hi(float2* dst, const float4* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
+  df_gather_hi_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Outer matvec  y_p = x_{nb(p)} + sum_b T_e[a][b] x_{e,b}  (nb(p) >= 0), else 0;
+// residual form y = c0 - that when c0 != null.  T in df64, x FP32 or df64.
+template <typename X>
+__global__ void __launch_bounds__(NT) df_matvec_kernel(const float4* __restrict__ T, const int* __restrict__ nbr,
+                                                       const X* __restrict__ x, const float4* __restrict__ c0,
+                                                       float4* __restrict__ y, int E, int nb, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* xs = reinterpret_cast<float4*>(smem_raw);  // [nb][nrhs]
+  for (int e = blockIdx.x; e < E; e += gridDim.x) {
+    __syncthreads();
+    const long long base = (long long)e * nb;
+    for (int l = threadIdx.x; l < nb * nrhs; l += NT) xs[l] = ld(x, base * nrhs + l);
+    __syncthreads();
+    const float4* Te = T + (long long)e * nb * nb;
+    for (int l = threadIdx.x; l < nb * nrhs; l += NT) {
+      const int a = l / nrhs, r = l % nrhs;
+      const long long p = base + a;
+      const int q = nbr[p];
+      float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q >= 0) {
+        cacc acc;
+        cadd2(acc, ld(x, (long long)q * nrhs + r));
+        const float4* Tr = Te + (long long)a * nb;
+        for (int b = 0; b < nb; ++b) cdot2(acc, Tr[b], xs[b * nrhs + r]);
+        if (c0) {
+          const float4 cv = c0[p * nrhs + r];
+          acc.rs = -acc.rs; acc.rc = -acc.rc; acc.is = -acc.is; acc.ic = -acc.ic;
+          cadd2(acc, cv);
+        }
+        out = cfin(acc);
+      }
+      y[p * nrhs + r] = out;
+    }
+  }
+}
+
+template <typename X>
+cudaError_t df_matvec(const float4* T, const int* nbr, const X* x, const float4* c0, float4* y, int E, int nb, int nrhs,
+                      int grid, cudaStream_t s) {
+  const size_t smem = sizeof(float4) * (size_t)nb * nrhs;
+  if (smem > 48 * 1024) smem_optin(df_matvec_kernel<X>);
+  df_matvec_kernel<X><<<grid, NT, smem, s>>>(T, nbr, x, c0, y, E, nb, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t df_matvec<float2>(const float4*, const int*, const float2*, const float4*, float4*, int, int, int,
+                                       int, cudaStream_t);
+template cudaError_t df_matvec<float4>(const float4*, const int*, const float4*, const float4*, float4*, int, int, int,
+                                       int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// h[i][r] = sum_rows conj(V_i) w   (two-pass, fixed order; block partials in df64, final sum in FP64)
+__global__ void __launch_bounds__(NT) df_bdot_partial_kernel(const float4* __restrict__ V, long long vstride, int nvec,
+                                                             const float4* __restrict__ w, long long rows, int nrhs,
+                                                             int rpad, float4* __restrict__ partial, long long chunk) {
+  __shared__ float4 red[NT];
+  const int r = threadIdx.x % rpad, lrow = threadIdx.x / rpad, rper = NT / rpad;
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < rows ? lo + chunk : rows;
+  for (int i = 0; i < nvec; ++i) {
+    cacc acc;
+    if (r < nrhs) {
+      const float4* Vi = V + i * vstride;
+      for (long long row = lo + lrow; row < hi; row += rper) cdot2_conj(acc, Vi[row * nrhs + r], w[row * nrhs + r]);
+    }
+    red[threadIdx.x] = cfin(acc);
+    __syncthreads();
+    for (int s2 = rper / 2; s2 > 0; s2 >>= 1) {
+      if (lrow < s2) {
+        cacc t;
+        cadd2(t, red[threadIdx.x]);
+        cadd2(t, red[threadIdx.x + s2 * rpad]);
+        red[threadIdx.x] = cfin(t);
+      }
+      __syncthreads();
+    }
+    if (lrow == 0 && r < nrhs) partial[((long long)blockIdx.x * nvec + i) * nrhs + r] = red[r];
+    __syncthreads();
+  }
+}
+
+__global__ void df_bdot_final_kernel(const float4* __restrict__ partial, int nblk, int nvec, int nrhs,
+                                     double2* __restrict__ out) {
+  const int warp = (blockIdx.x * NT + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (warp >= nvec * nrhs) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = lane; b < nblk; b += 32) {
+    const double2 v = to_d2(partial[(long long)b * nvec * nrhs + warp]);
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if (lane == 0) out[warp] = acc;
+}
+
+cudaError_t df_bdot(const float4* V, long long vstride, int nvec, const float4* w, long long rows, int nrhs,
+                    float4* partial, double2* out, cudaStream_t s) {
+  if (nrhs > NT || nvec <= 0) return cudaErrorInvalidValue;
+  int rpad = 1;
+  while (rpad < nrhs) rpad <<= 1;
+  const int nblk = bdot_blocks(rows);
+  const long long chunk = (rows + nblk - 1) / nblk;
+  df_bdot_partial_kernel<<<nblk, NT, 0, s>>>(V, vstride, nvec, w, rows, nrhs, rpad, partial, chunk);
+  note_launch();
+  df_bdot_final_kernel<<<(nvec * nrhs * 32 + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nvec, nrhs, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// w += sign * sum_i V_i h_i   (V df64 or FP32, h FP64 converted to df64 once per block)
+template <typename VT>
+__global__ void df_bupdate_kernel(float4* __restrict__ w, const VT* __restrict__ V, long long vstride, int nvec,
+                                  const double2* __restrict__ h, long long rows, int nrhs, float sign) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* hs = reinterpret_cast<float4*>(smem_raw);  // [nvec][nrhs]
+  for (int l = threadIdx.x; l < nvec * nrhs; l += NT) {
+    const double2 v = h[l];
+    hs[l] = from_d2(make_double2(sign * v.x, sign * v.y));
+  }
+  __syncthreads();
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int r = (int)(l % nrhs);
+    cacc acc;
+    cadd2(acc, w[l]);
+    for (int i = 0; i < nvec; ++i) cdot2(acc, ld(V, i * vstride + l), hs[i * nrhs + r]);
+    w[l] = cfin(acc);
+  }
+}
+template <typename VT>
+cudaError_t df_bupdate(float4* w, const VT* V, long long vstride, int nvec, const double2* h, long long rows, int nrhs,
+                       float sign, cudaStream_t s) {
+  if (nvec <= 0) return cudaSuccess;
+  const size_t smem = sizeof(float4) * (size_t)nvec * nrhs;
+  if (smem > 48 * 1024) smem_optin(df_bupdate_kernel<VT>);
+  df_bupdate_kernel<VT><<<nblocks(rows * nrhs, 4096), NT, smem, s>>>(w, V, vstride, nvec, h, rows, nrhs, sign);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t df_bupdate<float4>(float4*, const float4*, long long, int, const double2*, long long, int, float,
+                                        cudaStream_t);
+template cudaError_t df_bupdate<float2>(float4*, const float2*, long long, int, const double2*, long long, int, float,
+                                        cudaStream_t);
+
+// out = w * (1 / sqrt(re dots[r])) when that norm exceeds floor[r], else 0 (norm and inverse in FP64)
+__global__ void df_bscale_kernel(float4* __restrict__ out, const float4* __restrict__ w,
+                                 const double2* __restrict__ dots, const double* __restrict__ floor, long long rows,
+                                 int nrhs) {
+  __shared__ float4 inv[NT];
+  for (int r = threadIdx.x; r < nrhs; r += NT) {
+    const double nrm = sqrt(dots[r].x > 0.0 ? dots[r].x : 0.0);
+    const double iv = nrm > (floor ? floor[r] : 0.0) ? 1.0 / nrm : 0.0;
+    inv[r] = from_d2(make_double2(iv, 0.0));
+  }
+  __syncthreads();
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const float4 a = w[l], s = inv[(int)(l % nrhs)];
+    cacc acc;
+    dot2(acc.rs, acc.rc, a.x, a.z, s.x, s.z);
+    dot2(acc.is, acc.ic, a.y, a.w, s.x, s.z);
+    out[l] = cfin(acc);
+  }
+}
+cudaError_t df_bscale(float4* out, const float4* w, const double2* dots, const double* floor, long long rows, int nrhs,
+                      cudaStream_t s) {
+  df_bscale_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(out, w, dots, floor, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// z[p] = v[nb(p)] (identity preconditioner in incoming coordinates), FP32 hi parts
+__global__ void df_swap_hi_kernel(float2* __restrict__ z, const float4* __restrict__ v, const int* __restrict__ nbr,
+                                  long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = nbr[row];
+    const float4 a = m >= 0 ? v[(long long)m * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    z[l] = make_float2(a.x, a.y);
+  }
+}
+cudaError_t df_swap_hi(float2* z, const float4* v, const int* nbr, long long rows, int nrhs, cudaStream_t s) {
+  df_swap_hi_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(z, v, nbr, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hps

@@ -1,0 +1,33 @@
+// Double-float (df64) kernels of the outer FGMRES: a complex df64 number is a
+// float4 (re_hi, im_hi, re_lo, im_lo) with the value (re_hi + re_lo) + i (im_hi + im_lo).
+#pragma once
+
+#include "common.cuh"
+
+namespace hps {
+
+cudaError_t df_from_d(float4* dst, const double2* src, long long n, cudaStream_t s);
+cudaError_t df_to_d(double2* dst, const float4* src, long long n, cudaStream_t s);
+// dst[row][r] = hi(src[map[row]][r]) (map < 0 -> 0)
+cudaError_t df_gather_hi(float2* dst, const float4* src, const int* map, long long rows, int nrhs, cudaStream_t s);
+// z[p] = hi(v[nb(p)]) (0 on the physical boundary): the identity preconditioner in incoming coordinates
+cudaError_t df_swap_hi(float2* z, const float4* v, const int* nbr, long long rows, int nrhs, cudaStream_t s);
+
+// y = Pi M x (c0 == null) or y = c0 - Pi M x on the element-side layout; T df64 [E][nb][nb]
+template <typename X>
+cudaError_t df_matvec(const float4* T, const int* nbr, const X* x, const float4* c0, float4* y, int E, int nb, int nrhs,
+                      int grid, cudaStream_t s);
+
+// out[i][r] = sum_rows conj(V_i[row][r]) w[row][r] (i < nvec), FP64 result; partial holds
+// bdot_blocks(rows) * nvec * nrhs df64 numbers
+cudaError_t df_bdot(const float4* V, long long vstride, int nvec, const float4* w, long long rows, int nrhs,
+                    float4* partial, double2* out, cudaStream_t s);
+// w += sign * sum_i V_i h_i
+template <typename VT>
+cudaError_t df_bupdate(float4* w, const VT* V, long long vstride, int nvec, const double2* h, long long rows, int nrhs,
+                       float sign, cudaStream_t s);
+// out = w / sqrt(re dots[r]) when that norm exceeds floor[r], else 0
+cudaError_t df_bscale(float4* out, const float4* w, const double2* dots, const double* floor, long long rows, int nrhs,
+                      cudaStream_t s);
+
+}  // namespace hps

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "df64.cuh"
 #include "skel.cuh"
 
 namespace hps {
@@ -579,16 +580,12 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
   return HPS_OK;
 }
 
-}  // namespace
 
+// One V-cycle on the stage-0 sweep vector: rho in S0.vec on entry, z in S0.vec on return.
 template <typename R>
-int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) {
+int mg_core(hps_ctx* c, int nrhs, int k) {
   using C = c_t<R>;
-  int rc = ensure_sweep_buffers(c, nrhs);
-  if (rc != HPS_OK) return rc;
   cudaStream_t st = c->stream;
-  const Stage& S0 = c->stages[0];
-  HPS_CK(c, (gather_rows<double, R>(static_cast<C*>(S0.vec), rho_es, S0.d_es, (long long)S0.nsub * S0.n, nrhs, st)));
   // up-sweep: rho'_E = rho_E - U f (one GEMM per level)
   for (int l = 1; l <= c->L_exact; ++l) {
     const Level& Lv = c->levels[l];
@@ -598,7 +595,7 @@ int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) 
     HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
                       Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
   }
-  rc = coarse_solve<R>(c, nrhs, k);
+  int rc = coarse_solve<R>(c, nrhs, k);
   if (rc != HPS_OK) return rc;
   // down-sweep: children's outer rows from the merged solution, x = Dm [child1; child2], x into the interface rows
   for (int l = c->L_exact; l >= 1; --l) {
@@ -612,8 +609,37 @@ int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) 
                       2 * m, nrhs, nrhs, 2 * n));
     HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(c->sw_x), Lv.d_xmap, (long long)NP * 2 * m, nrhs, st)));
   }
-  HPS_CK(c, (scatter_rows<R, double>(z_es, static_cast<const C*>(S0.vec), S0.d_es, (long long)S0.nsub * S0.n, nrhs,
-                                     st)));
+  return HPS_OK;
+}
+
+}  // namespace
+
+template <typename R>
+int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) {
+  using C = c_t<R>;
+  int rc = ensure_sweep_buffers(c, nrhs);
+  if (rc != HPS_OK) return rc;
+  cudaStream_t st = c->stream;
+  const Stage& S0 = c->stages[0];
+  const long long rows = (long long)S0.nsub * S0.n;
+  HPS_CK(c, (gather_rows<double, R>(static_cast<C*>(S0.vec), rho_es, S0.d_es, rows, nrhs, st)));
+  rc = mg_core<R>(c, nrhs, k);
+  if (rc != HPS_OK) return rc;
+  HPS_CK(c, (scatter_rows<R, double>(z_es, static_cast<const C*>(S0.vec), S0.d_es, rows, nrhs, st)));
+  return HPS_OK;
+}
+
+int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int k) {
+  int rc = ensure_sweep_buffers(c, nrhs);
+  if (rc != HPS_OK) return rc;
+  if (c->precision != HPS_MIXED) return fail(c, HPS_EINVAL, "internal: df64 outer needs the FP32 tree");
+  cudaStream_t st = c->stream;
+  const Stage& S0 = c->stages[0];
+  const long long rows = (long long)S0.nsub * S0.n;
+  HPS_CK(c, df_gather_hi(static_cast<float2*>(S0.vec), rho_es, S0.d_es, rows, nrhs, st));
+  rc = mg_core<float>(c, nrhs, k);
+  if (rc != HPS_OK) return rc;
+  HPS_CK(c, (scatter_rows<float, float>(z_es, static_cast<const float2*>(S0.vec), S0.d_es, rows, nrhs, st)));
   return HPS_OK;
 }
 

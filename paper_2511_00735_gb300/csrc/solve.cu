@@ -1,5 +1,6 @@
 // C ABI, second half: merge levels, skeleton RHS / matvec / preconditioner in
-// the skeleton ("face") order, and the FP64 flexible GMRES (section 4.3).
+// the skeleton ("face") order, and the flexible GMRES (section 4.3), in FP64 or
+// (mixed path) in double-float arithmetic with FP64 restart residuals.
 //
 // FGMRES runs on the element-side layout with residual-like vectors (the
 // Arnoldi basis V) in outgoing coordinates rho = Pi r and solution-like
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "df64.cuh"
 #include "skel.cuh"
 
 namespace hps {
@@ -46,41 +48,74 @@ int ensure_pv(hps_ctx* c, int nrhs) {
   return HPS_OK;
 }
 
-int ensure_fg(hps_ctx* c, int restart, int nrhs) {
-  if (restart <= c->fg_restart && nrhs <= c->fg_nrhs) return HPS_OK;
-  restart = std::max(restart, c->fg_restart);
-  nrhs = std::max(nrhs, c->fg_nrhs);
-  dev_free(c, c->fg_V); dev_free(c, c->fg_Z); dev_free(c, c->fg_x); dev_free(c, c->fg_w);
-  dev_free(c, c->fg_rhs); dev_free(c, c->fg_t); dev_free(c, c->fg_h); dev_free(c, c->fg_part);
-  dev_free(c, c->fg_y); dev_free(c, c->fg_floor);
+bool use_df(const hps_ctx* c) {
+  return c->outer_arith == HPS_OUTER_DF64 || (c->outer_arith == HPS_OUTER_DEFAULT && c->precision == HPS_MIXED);
+}
+
+void free_fg(hps_ctx* c) {
+  void** bufs[] = {(void**)&c->fg_V, (void**)&c->fg_Z, (void**)&c->fg_x, (void**)&c->fg_w, (void**)&c->fg_rhs,
+                   (void**)&c->fg_t, (void**)&c->fg_h, (void**)&c->fg_part, (void**)&c->fg_y, (void**)&c->fg_floor,
+                   (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_part,
+                   (void**)&c->df_T};
+  for (void** b : bufs) {
+    dev_free(c, *b);
+    *b = nullptr;
+  }
   if (c->pin_h) cudaFreeHost(c->pin_h);
   if (c->pin_y) cudaFreeHost(c->pin_y);
   if (c->pin_floor) cudaFreeHost(c->pin_floor);
   c->pin_h = c->pin_y = nullptr;
   c->pin_floor = nullptr;
+  c->fg_restart = c->fg_nrhs = 0;
+}
+
+// FGMRES workspace for `restart` and `nrhs`; df selects the df64 basis (float pairs) and FP32 directions
+int ensure_fg(hps_ctx* c, int restart, int nrhs, bool df) {
+  if (restart <= c->fg_restart && nrhs <= c->fg_nrhs && df == c->fg_df) return HPS_OK;
+  if (df == c->fg_df) {
+    restart = std::max(restart, c->fg_restart);
+    nrhs = std::max(nrhs, c->fg_nrhs);
+  }
+  free_fg(c);
   const size_t vs = (size_t)c->n_es * nrhs;
-  c->fg_V = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * (restart + 1)));
-  c->fg_Z = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * restart));
-  c->fg_x = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
-  c->fg_w = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
+  const size_t nblk = (size_t)bdot_blocks(c->n_es);
   c->fg_rhs = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
   c->fg_t = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->n_bdry * nrhs));
   const size_t hsz = (size_t)(2 * (restart + 1) + 1) * nrhs;
   c->fg_h = static_cast<double2*>(dev_alloc(c, sizeof(double2) * hsz));
-  c->fg_part = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)bdot_blocks(c->n_es) * (restart + 1) * nrhs));
+  c->fg_part = static_cast<double2*>(dev_alloc(c, sizeof(double2) * nblk * (df ? 1 : restart + 1) * nrhs));
   c->fg_y = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)restart * nrhs));
   c->fg_floor = static_cast<double*>(dev_alloc(c, sizeof(double) * nrhs));
-  if (!c->fg_V || !c->fg_Z || !c->fg_x || !c->fg_w || !c->fg_rhs || !c->fg_t || !c->fg_h || !c->fg_part || !c->fg_y ||
-      !c->fg_floor)
+  bool ok = c->fg_rhs && c->fg_t && c->fg_h && c->fg_part && c->fg_y && c->fg_floor;
+  if (df) {
+    c->df_V = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs * (restart + 1)));
+    c->df_Z = static_cast<float2*>(dev_alloc(c, sizeof(float2) * vs * restart));
+    c->df_x = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
+    c->df_w = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
+    c->df_part = static_cast<float4*>(dev_alloc(c, sizeof(float4) * nblk * (restart + 1) * nrhs));
+    c->df_T = static_cast<float4*>(dev_alloc(c, sizeof(float4) * (size_t)c->E * c->nb * c->nb));
+    ok = ok && c->df_V && c->df_Z && c->df_x && c->df_w && c->df_part && c->df_T;
+  } else {
+    c->fg_V = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * (restart + 1)));
+    c->fg_Z = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * restart));
+    c->fg_x = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
+    c->fg_w = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs));
+    ok = ok && c->fg_V && c->fg_Z && c->fg_x && c->fg_w;
+  }
+  if (!ok) {
+    free_fg(c);
     return fail(c, HPS_ENOMEM, "FGMRES workspace");
+  }
   if (cudaMallocHost(&c->pin_h, sizeof(double2) * hsz) != cudaSuccess ||
       cudaMallocHost(&c->pin_y, sizeof(double2) * (size_t)restart * nrhs) != cudaSuccess ||
       cudaMallocHost(&c->pin_floor, sizeof(double) * nrhs) != cudaSuccess) {
     cudaGetLastError();
+    free_fg(c);
     return fail(c, HPS_ENOMEM, "pinned host workspace");
   }
   c->fg_restart = restart;
   c->fg_nrhs = nrhs;
+  c->fg_df = df;
   return HPS_OK;
 }
 
@@ -190,6 +225,14 @@ int hps_precond_apply(hps_ctx* c, const void* r, void* z, int nrhs, int inner_it
   return HPS_OK;
 }
 
+int hps_set_outer_arith(hps_ctx* c, int mode) {
+  if (!c) return HPS_EINVAL;
+  if (mode != HPS_OUTER_DEFAULT && mode != HPS_OUTER_FP64 && mode != HPS_OUTER_DF64)
+    return fail(c, HPS_EINVAL, "outer arithmetic: HPS_OUTER_DEFAULT, HPS_OUTER_FP64 or HPS_OUTER_DF64");
+  c->outer_arith = mode;
+  return HPS_OK;
+}
+
 int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double tol, int inner_iters, int restart,
                     int max_outer, void* g_out, hps_info* info) {
   CHECK_CTX(c);
@@ -199,8 +242,10 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   if (!t || !g_out || nrhs < 1 || nrhs > 64 || !(tol > 0) || restart < 1 || restart > 200 || max_outer < 1 ||
       inner_iters > 60)
     return fail(c, HPS_EINVAL, "pointers, 1<=nrhs<=64, tol>0, 1<=restart<=200, max_outer>=1, inner_iters<=60");
+  const bool df = use_df(c);
+  if (df && c->precision != HPS_MIXED) return fail(c, HPS_EINVAL, "HPS_OUTER_DF64 needs HPS_MIXED leaves");
   const auto t0 = std::chrono::steady_clock::now();
-  int rc = ensure_fg(c, restart, nrhs);
+  int rc = ensure_fg(c, restart, nrhs, df);
   if (rc) return rc;
   rc = ensure_pv(c, nrhs);
   if (rc) return rc;
@@ -218,6 +263,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     PhaseScope ps(c, HPS_PH_RHS);
     HPS_CK(c, user_to_rows(c->fg_t, t_dev, nullptr, c->n_bdry, nrhs, c->n_bdry, st));
     HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->fg_t, c->fg_rhs, c->E, c->nb, nrhs, grid, st));
+    if (df) HPS_CK(c, df_from_d(c->df_T, c->d_T, (long long)c->E * c->nb * c->nb, st));
   }
   double2* hbuf = c->fg_h;
   HPS_CK(c, bdot<double>(c->fg_rhs, 0, 1, c->fg_rhs, n, nrhs, c->fg_part, hbuf, 0, st));
@@ -226,7 +272,28 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   const auto t1 = std::chrono::steady_clock::now();
   std::vector<double> bnorm(nrhs);
   for (int r = 0; r < nrhs; ++r) bnorm[r] = std::sqrt(std::max(0.0, c->pin_h[r].x));
-  HPS_CK(c, zero<double>(c->fg_x, vs, st));
+  if (df) HPS_CK(c, cudaMemsetAsync(c->df_x, 0, sizeof(float4) * (size_t)vs, st));
+  else HPS_CK(c, zero<double>(c->fg_x, vs, st));
+
+  // Explicit FP64 residual of the current iterate, its squared norms in hbuf[0..nrhs), and
+  // (df) the iterate in FP64 in pv_in.  The residual itself lands in fg_w (FP64) or pv_out (df).
+  auto residual = [&]() -> int {
+    {
+      PhaseScope ps(c, HPS_PH_MATVEC);
+      if (df) {
+        HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
+        HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->pv_in, c->fg_rhs, c->pv_out, c->E, c->nb, nrhs, grid, st));
+      } else {
+        HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
+      }
+    }
+    const double2* w = df ? c->pv_out : c->fg_w;
+    HPS_CK(c, bdot<double>(w, 0, 1, w, n, nrhs, c->fg_part, hbuf, 0, st));
+    HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+    HPS_CK(c, cudaStreamSynchronize(st));
+    return HPS_OK;
+  };
+
   std::vector<int> its(nrhs, 0);
   std::vector<char> done(nrhs, 0);
   std::vector<cd> H((size_t)(restart + 1) * restart * nrhs), g((size_t)(restart + 1) * nrhs);
@@ -234,16 +301,14 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   std::vector<cd> sn((size_t)restart * nrhs);
   std::vector<int> steps(nrhs);
   std::vector<double> res(nrhs, 0.0);
-  int outer_total = 0;
+  bool fresh = false;  // pin_h holds the residual norms of the current iterate
   for (int outer = 0; outer < max_outer; ++outer) {
-    // explicit residual w = rhs - Pi M x
-    {
-      PhaseScope ps(c, HPS_PH_MATVEC);
-      HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
+    // explicit residual w = rhs - Pi M x (x = 0 at the start: w = rhs, norms already in hbuf)
+    if (outer > 0) {
+      rc = residual();
+      if (rc) return rc;
     }
-    HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
-    HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
-    HPS_CK(c, cudaStreamSynchronize(st));
+    fresh = true;
     bool all = true;
     std::vector<char> active(nrhs, 0);
     for (int r = 0; r < nrhs; ++r) {
@@ -258,22 +323,46 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
       c->pin_floor[r] = active[r] ? 0.0 : DBL_MAX;
     }
     if (all) break;
+    fresh = false;
     HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-    HPS_CK(c, bscale<double>(c->fg_V, c->fg_w, hbuf, c->fg_floor, n, nrhs, st));
+    if (df) {
+      HPS_CK(c, df_from_d(c->df_w, outer > 0 ? c->pv_out : c->fg_rhs, vs, st));
+      HPS_CK(c, df_bscale(c->df_V, c->df_w, hbuf, c->fg_floor, n, nrhs, st));
+    } else {
+      HPS_CK(c, bscale<double>(c->fg_V, outer > 0 ? c->fg_w : c->fg_rhs, hbuf, c->fg_floor, n, nrhs, st));
+    }
     int jdone = 0;
     for (int j = 0; j < restart; ++j) {
-      double2* Vj = c->fg_V + (size_t)j * vs;
-      double2* Zj = c->fg_Z + (size_t)j * vs;
-      rc = precond(c, Vj, Zj, nrhs, inner_iters);
-      if (rc) return rc;
-      {
-        PhaseScope ps(c, HPS_PH_MATVEC);
-        HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, Zj, nullptr, c->fg_w, c->E, c->nb, nrhs, grid, st));
-      }
       double2* h1 = hbuf;
       double2* h2 = hbuf + (size_t)(restart + 1) * nrhs;
       double2* nr = hbuf + (size_t)2 * (restart + 1) * nrhs;
-      {
+      if (df) {
+        const float4* Vj = c->df_V + (size_t)j * vs;
+        float2* Zj = c->df_Z + (size_t)j * vs;
+        {
+          PhaseScope ps(c, HPS_PH_PRECOND);
+          if (inner_iters < 0) HPS_CK(c, df_swap_hi(Zj, Vj, c->d_es_nb, n, nrhs, st));
+          else if ((rc = mg_apply_df(c, Vj, Zj, nrhs, inner_iters)) != HPS_OK) return rc;
+        }
+        {
+          PhaseScope ps(c, HPS_PH_MATVEC);
+          HPS_CK(c, df_matvec<float2>(c->df_T, c->d_es_nb, Zj, nullptr, c->df_w, c->E, c->nb, nrhs, grid, st));
+        }
+        PhaseScope ps(c, HPS_PH_ORTHO);
+        HPS_CK(c, df_bdot(c->df_V, vs, j + 1, c->df_w, n, nrhs, c->df_part, h1, st));
+        HPS_CK(c, df_bupdate<float4>(c->df_w, c->df_V, vs, j + 1, h1, n, nrhs, -1.f, st));
+        HPS_CK(c, df_bdot(c->df_V, vs, j + 1, c->df_w, n, nrhs, c->df_part, h2, st));
+        HPS_CK(c, df_bupdate<float4>(c->df_w, c->df_V, vs, j + 1, h2, n, nrhs, -1.f, st));
+        HPS_CK(c, df_bdot(c->df_w, 0, 1, c->df_w, n, nrhs, c->df_part, nr, st));
+      } else {
+        double2* Vj = c->fg_V + (size_t)j * vs;
+        double2* Zj = c->fg_Z + (size_t)j * vs;
+        rc = precond(c, Vj, Zj, nrhs, inner_iters);
+        if (rc) return rc;
+        {
+          PhaseScope ps(c, HPS_PH_MATVEC);
+          HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, Zj, nullptr, c->fg_w, c->E, c->nb, nrhs, grid, st));
+        }
         PhaseScope ps(c, HPS_PH_ORTHO);
         HPS_CK(c, bdot<double>(c->fg_V, vs, j + 1, c->fg_w, n, nrhs, c->fg_part, h1, 0, st));
         HPS_CK(c, (bupdate<double, double>(c->fg_w, c->fg_V, vs, j + 1, h1, n, nrhs, -1.0, st)));
@@ -326,12 +415,12 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
         if (res[r] <= tol || hn <= 1e-300) active[r] = 0;
         else any = true;
       }
-      ++outer_total;
       if (!any) break;
       if (j + 1 < restart) {
         for (int r = 0; r < nrhs; ++r) c->pin_floor[r] = active[r] ? 0.0 : DBL_MAX;
         HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-        HPS_CK(c, bscale<double>(c->fg_V + (size_t)(j + 1) * vs, c->fg_w, nr, c->fg_floor, n, nrhs, st));
+        if (df) HPS_CK(c, df_bscale(c->df_V + (size_t)(j + 1) * vs, c->df_w, nr, c->fg_floor, n, nrhs, st));
+        else HPS_CK(c, bscale<double>(c->fg_V + (size_t)(j + 1) * vs, c->fg_w, nr, c->fg_floor, n, nrhs, st));
       }
     }
     // y = R^{-1} g per right-hand side, then x += Z y
@@ -348,25 +437,32 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
       for (int i = 0; i < jdone; ++i) c->pin_y[(size_t)i * nrhs + r] = make_double2(y[i].real(), y[i].imag());
     }
     HPS_CK(c, cudaMemcpyAsync(c->fg_y, c->pin_y, sizeof(double2) * (size_t)jdone * nrhs, cudaMemcpyHostToDevice, st));
-    HPS_CK(c, (bupdate<double, double>(c->fg_x, c->fg_Z, vs, jdone, c->fg_y, n, nrhs, 1.0, st)));
+    if (df) HPS_CK(c, df_bupdate<float2>(c->df_x, c->df_Z, vs, jdone, c->fg_y, n, nrhs, 1.f, st));
+    else HPS_CK(c, (bupdate<double, double>(c->fg_x, c->fg_Z, vs, jdone, c->fg_y, n, nrhs, 1.0, st)));
   }
-  // explicit FP64 residual
   PhaseScope ps_other(c, HPS_PH_OTHER);
-  HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
-  HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
-  HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
+  // explicit FP64 residual of the returned iterate (already at hand when the last restart converged)
+  if (!fresh) {
+    rc = residual();
+    if (rc) return rc;
+  } else if (df) {
+    HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
+  }
+  std::vector<double> nrm2(nrhs);
+  for (int r = 0; r < nrhs; ++r) nrm2[r] = c->pin_h[r].x;
   // solution in skeleton order
+  const double2* x64 = df ? c->pv_in : c->fg_x;
   double2* gdev = static_cast<double2*>(g_out);
   const bool host_out = !is_device_ptr(g_out);
   if (host_out) gdev = c->pv_out;
-  HPS_CK(c, rows_to_user(gdev, c->fg_x, c->d_es_in, n, nrhs, c->n_skel, st));
+  HPS_CK(c, rows_to_user(gdev, x64, c->d_es_in, n, nrhs, c->n_skel, st));
   if (host_out)
     HPS_CK(c, cudaMemcpyAsync(g_out, gdev, sizeof(double2) * (size_t)c->n_skel * nrhs, cudaMemcpyDeviceToHost, st));
   HPS_CK(c, cudaStreamSynchronize(st));
   int nconv = 0, maxit = 0;
   double maxres = 0.0;
   for (int r = 0; r < nrhs; ++r) {
-    res[r] = bnorm[r] > 0 ? std::sqrt(std::max(0.0, c->pin_h[r].x)) / bnorm[r] : 0.0;
+    res[r] = bnorm[r] > 0 ? std::sqrt(std::max(0.0, nrm2[r])) / bnorm[r] : 0.0;
     nconv += res[r] <= tol;
     maxit = std::max(maxit, its[r]);
     maxres = std::max(maxres, res[r]);
@@ -383,7 +479,6 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     info->ms_rhs = std::chrono::duration<double, std::milli>(t1 - t0).count();
     info->ms_solve = std::chrono::duration<double, std::milli>(t2 - t1).count();
   }
-  (void)outer_total;
   if (nconv < nrhs) return fail(c, HPS_ENOTCONV, "FGMRES stopped before the tolerance");
   return HPS_OK;
 }

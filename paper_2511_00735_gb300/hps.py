@@ -19,6 +19,9 @@ HPS_OK = 0
 HPS_ENOTCONV = -4
 HPS_FP64 = 0
 HPS_MIXED = 1
+OUTER_DEFAULT = -1  # outer FGMRES arithmetic (hps_set_outer_arith)
+OUTER_FP64 = 0
+OUTER_DF64 = 1
 
 _STATUS = {0: "HPS_OK", -1: "HPS_EINVAL", -2: "HPS_ENOMEM", -3: "HPS_ENOTBUILT", -4: "HPS_ENOTCONV",
            -5: "HPS_ETIMEOUT", -6: "HPS_ECUDA", -7: "HPS_ENODEV", -8: "HPS_EUNSUPPORTED", -9: "HPS_ENUMERIC"}
@@ -28,7 +31,8 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_sizes", "hps_node_coords", "hps_boundary_points", "hps_index_maps", "hps_set_coeff",
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
-           "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace"]
+           "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace",
+           "hps_set_outer_arith"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -86,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "hps_leaf_maps_noalloc": (i, [i, vp, i, d, d, vp, i, vp]),
         "hps_build_leaves_batch": (i, [C.POINTER(vp), i, i]),
         "hps_release_workspace": (i, [vp]),
+        "hps_set_outer_arith": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +196,10 @@ class Solver:
     def release_workspace(self):
         """Free the per-solve buffers, keep the leaf maps and the merge tree."""
         self._check(self.lib.hps_release_workspace(self.h))
+
+    def set_outer_arith(self, mode: int):
+        """Outer FGMRES arithmetic: OUTER_FP64, OUTER_DF64 (mixed leaves only) or OUTER_DEFAULT."""
+        self._check(self.lib.hps_set_outer_arith(self.h, mode))
 
     def node_coords(self):
         n = self.E * (self.N + 1) ** 2

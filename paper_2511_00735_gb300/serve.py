@@ -62,9 +62,11 @@ def tree_only_bytes(nx: int, N: int, precision: int) -> int:
 
 
 def krylov_bytes(nx: int, N: int, nrhs: int, restart: int = 60) -> int:
-    """Per-solve workspace: FGMRES basis V and Z, sweep vectors of every stage, staging."""
+    """Per-solve workspace: FGMRES basis V and Z, sweep vectors of every stage, staging, and the
+    double-float copy of the leaf maps that the mixed path's outer iteration reads (an upper
+    bound for both outer arithmetics)."""
     rows = nx * nx * 4 * (N - 1)
-    return (2 * restart + 8) * rows * nrhs * 16 + 4 * rows * nrhs * 16 + (32 << 20)
+    return (2 * restart + 8) * rows * nrhs * 16 + 4 * rows * nrhs * 16 + rows * 4 * (N - 1) * 16 + (32 << 20)
 
 
 class _Tree:

@@ -201,6 +201,48 @@ def test_solve_8x8_device_buffers(solver, precision):
         assert np.linalg.norm(op.rhs[k] - M @ g[k]) / np.linalg.norm(op.rhs[k]) < 1e-9
 
 
+@pytest.mark.parametrize("inner", [5, -1])
+def test_solve_outer_df64_vs_fp64(solver, inner):
+    """Mixed path, outer FGMRES in double-float arithmetic against the same solve in FP64
+    (section 4.3): both reach the tolerance on the FP64 residual, both match the oracle's
+    dense solve, and their iteration counts differ by at most a few."""
+    prob = inputs.single_bump(8, 12, 30.0, 4, seed=21, L_exact=4)
+    op = OracleProblem(prob)
+    M = assemble_M(op.mesh, op.Ts)
+    t = H.setup(solver, prob, H.HPS_MIXED)
+    solver.merge_levels(prob.L_exact)
+    its = {}
+    try:
+        for mode in (H.OUTER_FP64, H.OUTER_DF64):
+            solver.set_outer_arith(mode)
+            g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=inner, restart=60, max_outer=20)
+            assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10
+            for k in range(prob.nrhs):
+                gr = np.linalg.solve(M, op.rhs[k])
+                assert rel(g[k], gr) < 1e-8
+                assert np.linalg.norm(op.rhs[k] - M @ g[k]) / np.linalg.norm(op.rhs[k]) < 1e-9
+            its[mode] = info["outer_iterations"]
+    finally:
+        solver.set_outer_arith(H.OUTER_DEFAULT)
+    assert abs(its[H.OUTER_FP64] - its[H.OUTER_DF64]) <= max(2, its[H.OUTER_FP64] // 20), its
+
+
+def test_outer_df64_needs_mixed_leaves(solver):
+    prob = inputs.small_4x4(0)
+    t = H.setup(solver, prob, H.HPS_FP64)
+    solver.merge_levels(prob.L_exact)
+    with pytest.raises(H.HPSError):
+        solver.set_outer_arith(7)
+    solver.set_outer_arith(H.OUTER_DF64)
+    try:
+        with pytest.raises(H.HPSError):
+            solver.gmres_solve(t, tol=1e-10, inner_iters=prob.inner_iters)
+    finally:
+        solver.set_outer_arith(H.OUTER_DEFAULT)
+    g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=prob.inner_iters)
+    assert info["max_rel_residual"] <= 1e-10
+
+
 def test_bad_arguments(solver):
     with pytest.raises(H.HPSError):
         solver.mesh(6, 8)
