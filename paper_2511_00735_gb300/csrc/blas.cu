@@ -338,108 +338,192 @@ void set_smem(K kernel, size_t bytes) {
 
 
 // ---------------------------------------------------------------------------
-// Skinny GEMM for n <= NC columns (block vectors of right-hand sides): A is
-// streamed once with coalesced loads (lanes split k), B is staged in padded
-// shared memory by k-chunks, each warp accumulates RW rows x NC columns and
-// reduces across its lanes at the end.  Same descriptors and epilogue as
-// gemm_tile (two-segment B / C0, row and column maps).
+// Block-vector GEMM (n <= 16 columns per block, the right-hand sides of the
+// multigrid sweeps and of the coarse solve).  One thread owns RPT output rows
+// and all 16 columns of each in registers: per k it reads one A value per row
+// from a padded shared-memory tile (conflict-free) and the 16 B values of
+// that k by broadcast, i.e. 16 x RPT complex FMAs per RPT + 8 (FP32) shared
+// loads.  The A and B tiles of the next k-chunk stream in with cp.async while
+// the current one is multiplied (two buffers), so the global loads need no
+// registers and overlap the arithmetic.  Same descriptors and epilogue as
+// gemm_tile (two-segment B / C0, row and column maps); blockIdx.y selects a
+// 16-column slice, blockIdx.z = batch + nbatch * split for split-K (partials
+// in the workspace, reduced in fixed order by splitk_reduce_kernel).
 // ---------------------------------------------------------------------------
-template <typename R, int NC, int RW, int KU>
-__global__ void __launch_bounds__(NT) skinny_kernel(GemmArgs<R> a) {
+constexpr int RG_NT = 128, RG_NC = 16, RG_KC = 16;
+
+template <typename R, int RPT>
+constexpr size_t rowgemm_smem() {
+  return 2 * sizeof(c_t<R>) * ((size_t)RG_NT * RPT * (RG_KC + 1) + (size_t)RG_KC * RG_NC);
+}
+
+// asynchronous global -> shared copy of one complex value; zero-filled when !pred
+template <typename C>
+__device__ __forceinline__ void cp_async_c(C* dst, const C* src, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  const int nbytes = pred ? (int)sizeof(C) : 0;
+  if (sizeof(C) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(nbytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// the 16 B values of one k (a 16-column row of the B tile, 16-byte aligned)
+template <typename C>
+__device__ __forceinline__ void load_brow(const C* src, C (&bv)[RG_NC]) {
+  if constexpr (sizeof(C) == 8) {
+#pragma unroll
+    for (int q = 0; q < RG_NC / 2; ++q) {
+      const float4 t = reinterpret_cast<const float4*>(src)[q];
+      bv[2 * q] = make_float2(t.x, t.y);
+      bv[2 * q + 1] = make_float2(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < RG_NC; ++j) bv[j] = src[j];
+  }
+}
+
+template <typename R, int RPT>
+__global__ void __launch_bounds__(RG_NT) rowgemm_kernel(GemmArgs<R> a, int ksplit, int kc, int mmax, int nmax) {
   using C = c_t<R>;
-  constexpr int KC = 32 * KU;      // k-chunk: every lane holds KU values of A per row
-  constexpr int LDB = NC + 1;      // padding against bank conflicts
-  constexpr int RB = (NT / 32) * RW;
-  __shared__ C Bs[KC * LDB];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int b = blockIdx.z; b < a.nbatch; b += gridDim.z) {
-    const GemmDesc d = a.desc[b];
-    const int n = d.n < 0 ? a.n_launch : d.n;
-    const int m = d.m, k = d.k;
-    const int row0 = blockIdx.x * RB;
-    if (row0 >= m) continue;  // uniform over the block
-    C acc[RW][NC];
-#pragma unroll
-    for (int r = 0; r < RW; ++r)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) acc[r][c] = czero<R>();
-    const C* arow[RW];
-    bool rok[RW];
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const int gi = row0 + warp * RW + r;
-      rok[r] = gi < m;
-      arow[r] = a.A + (long long)(d.a_r + (rok[r] ? gi : 0)) * a.lda + d.a_c;
+  constexpr int BM = RG_NT * RPT, LDA = RG_KC + 1;
+  constexpr int ASZ = BM * LDA, BSZ = RG_KC * RG_NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Bs = reinterpret_cast<C*>(smem_raw);  // [2][KC][16] (first: 16-byte aligned rows)
+  C* As = Bs + 2 * BSZ;                    // [2][BM][LDA]
+  const int b = blockIdx.z % a.nbatch, sp = blockIdx.z / a.nbatch;
+  const GemmDesc d = a.desc[b];
+  const int n = d.n < 0 ? a.n_launch : d.n;
+  const int m = d.m;
+  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * RG_NC;
+  if (row0 >= m || col0 >= n) return;  // uniform over the block
+  const int kb = ksplit > 1 ? sp * kc : 0;
+  const int ke = ksplit > 1 ? min(d.k, kb + kc) : d.k;
+  const int tid = threadIdx.x;
+  const C* Ab = a.A + (long long)d.a_r * a.lda + d.a_c;
+  // issue the copies of chunk [k0, k0 + KC) into buffer `buf`
+  auto load = [&](int k0, int buf) {
+    C* Ad = As + buf * ASZ;
+    C* Bd = Bs + buf * BSZ;
+#pragma unroll 4
+    for (int l = tid; l < BM * RG_KC; l += RG_NT) {
+      const int i = l / RG_KC, kk = l % RG_KC;
+      const int gi = row0 + i, gk = k0 + kk;
+      const bool ok = gi < m && gk < ke;
+      cp_async_c(Ad + i * LDA + kk, ok ? Ab + (long long)gi * a.lda + gk : Ab, ok);
     }
-    for (int k0 = 0; k0 < k; k0 += KC) {
-      // issue this lane's loads of A first (KU x RW independent loads in flight)
-      C av[RW][KU];
+    for (int l = tid; l < BSZ; l += RG_NT) {
+      const int kk = l / RG_NC, j = l % RG_NC;
+      const int gk = k0 + kk, gj = col0 + j;
+      const bool ok = gk < ke && gj < n;
+      const long long br = (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+      cp_async_c(Bd + l, ok ? a.B + br * a.ldb + d.b_c + gj : a.B, ok);
+    }
+    cp_async_commit();
+  };
+  C acc[RPT][RG_NC];
 #pragma unroll
-      for (int t = 0; t < KU; ++t) {
-        const int gk = k0 + lane + 32 * t;
+  for (int i = 0; i < RPT; ++i)
 #pragma unroll
-        for (int r = 0; r < RW; ++r) av[r][t] = (rok[r] && gk < k) ? arow[r][gk] : czero<R>();
-      }
-      __syncthreads();
-      for (int l = threadIdx.x; l < KC * NC; l += NT) {
-        const int kk = l / NC, j = l % NC;
-        const int gk = k0 + kk;
-        C v = czero<R>();
-        if (gk < k && j < n) {
-          const long long br = (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
-          v = a.B[br * a.ldb + d.b_c + j];
-        }
-        Bs[kk * LDB + j] = v;
-      }
-      __syncthreads();
+    for (int j = 0; j < RG_NC; ++j) acc[i][j] = czero<R>();
+  if (kb < ke) load(kb, 0);
+  int buf = 0;
+  for (int k0 = kb; k0 < ke; k0 += RG_KC, buf ^= 1) {
+    if (k0 + RG_KC < ke) {
+      load(k0 + RG_KC, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const C* Ac = As + buf * ASZ;
+    const C* Bc = Bs + buf * BSZ;
+#pragma unroll 4
+    for (int kk = 0; kk < RG_KC; ++kk) {
+      C bv[RG_NC];
+      load_brow(Bc + kk * RG_NC, bv);
 #pragma unroll
-      for (int t = 0; t < KU; ++t) {
-        const int kk = lane + 32 * t;
+      for (int i = 0; i < RPT; ++i) {
+        const C av = Ac[(tid + i * RG_NT) * LDA + kk];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const C bv = Bs[kk * LDB + c];
-#pragma unroll
-          for (int r = 0; r < RW; ++r) cfma(acc[r][c], av[r][t], bv);
-        }
+        for (int j = 0; j < RG_NC; ++j) cfma(acc[i][j], av, bv[j]);
       }
     }
-    // reduce across lanes; lane c ends up owning column c of each row
+    __syncthreads();  // buffer `buf` is refilled two chunks later
+  }
+  if (ksplit > 1) {
+    C* W = a.ws + (((long long)sp * a.nbatch + b) * mmax) * nmax;
 #pragma unroll
-    for (int r = 0; r < RW; ++r)
+    for (int i = 0; i < RPT; ++i) {
+      const int gi = row0 + tid + i * RG_NT;
+      if (gi >= m) continue;
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          acc[r][c].x += __shfl_xor_sync(0xffffffffu, acc[r][c].x, off);
-          acc[r][c].y += __shfl_xor_sync(0xffffffffu, acc[r][c].y, off);
-        }
-    const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
-    const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
-#pragma unroll
-    for (int r = 0; r < RW; ++r) {
-      const int gi = row0 + warp * RW + r;
-      if (!rok[r]) continue;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        if (c % 32 != lane || c >= n) continue;
-        C v = cmul(a.alpha, acc[r][c]);
-        if (a.C0) {
-          const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
-          v = cadd(v, cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + c]));
-        }
-        const long long orow = (long long)d.c_r + (rmap ? rmap[gi] : gi);
-        a.C[orow * a.ldc + d.c_c + (cmap ? cmap[c] : c)] = v;
+      for (int j = 0; j < RG_NC; ++j) {
+        const int gj = col0 + j;
+        if (gj < n) W[(long long)gi * nmax + gj] = acc[i][j];
       }
+    }
+    return;
+  }
+  const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
+  const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int gi = row0 + tid + i * RG_NT;
+    if (gi >= m) continue;
+    const long long orow = (long long)d.c_r + (rmap ? rmap[gi] : gi);
+    const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+#pragma unroll
+    for (int j = 0; j < RG_NC; ++j) {
+      const int gj = col0 + j;
+      if (gj >= n) continue;
+      C v = cmul(a.alpha, acc[i][j]);
+      if (a.C0) v = cadd(v, cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj]));
+      a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = v;
     }
   }
 }
 
-template <typename R, int NC, int RW, int KU>
-cudaError_t launch_skinny(const GemmArgs<R>& a, int mmax, cudaStream_t s) {
-  constexpr int RB = (NT / 32) * RW;
-  dim3 grid((mmax + RB - 1) / RB, 1, a.nbatch < 65535 ? a.nbatch : 65535);
-  skinny_kernel<R, NC, RW, KU><<<grid, NT, 0, s>>>(a);
+template <typename R, int RPT>
+cudaError_t launch_rowgemm(const GemmArgs<R>& a, int mmax, int nmax, int kmax, cudaStream_t s) {
+  constexpr int BM = RG_NT * RPT;
+  constexpr size_t smem = rowgemm_smem<R, RPT>();
+  if (smem > 48 * 1024) smem_optin(rowgemm_kernel<R, RPT>);
+  const int gx = (mmax + BM - 1) / BM, gy = (nmax + RG_NC - 1) / RG_NC;
+  const long long blocks = (long long)gx * gy * a.nbatch;
+  // resident blocks per SM from the shared-memory footprint; split K until the GPU is covered
+  const long long per_sm = (long long)(227 * 1024 / (smem + 1024));
+  const long long target = (per_sm > 0 ? per_sm : 1) * a.num_sms;
+  int ksplit = 1;
+  if (kmax >= 4 * RG_KC && a.ws && blocks < target) {
+    ksplit = (int)((target + blocks - 1) / blocks);
+    ksplit = ksplit < kmax / (2 * RG_KC) ? ksplit : kmax / (2 * RG_KC);
+    ksplit = ksplit < 32 ? ksplit : 32;
+    while (ksplit > 1 && ((long long)ksplit * a.nbatch > 65535 ||
+                          (long long)ksplit * a.nbatch * mmax * nmax > a.ws_elems))
+      --ksplit;
+  }
+  int kc = kmax;
+  if (ksplit > 1) {
+    kc = (kmax + ksplit - 1) / ksplit;
+    kc = (kc + RG_KC - 1) / RG_KC * RG_KC;
+    ksplit = (kmax + kc - 1) / kc;
+  }
+  if ((long long)a.nbatch * ksplit > 65535) return cudaErrorInvalidValue;
+  dim3 grid(gx, gy, a.nbatch * ksplit);
+  rowgemm_kernel<R, RPT><<<grid, RG_NT, smem, s>>>(a, ksplit, kc, mmax, nmax);
   note_launch();
+  if (ksplit > 1) {
+    int rb = (mmax * nmax + NT - 1) / NT;
+    rb = rb < 64 ? rb : 64;
+    dim3 rgrid(rb, a.nbatch);
+    splitk_reduce_kernel<R><<<rgrid, NT, 0, s>>>(a, ksplit, mmax, nmax);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -448,17 +532,10 @@ cudaError_t launch_skinny(const GemmArgs<R>& a, int mmax, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
-  // block-vector products (few columns): the skinny kernel streams A once; measured slower than
-  // the tiled kernels for every sweep shape of the 64x64 workload, so it is kept off by default.
-  if (kmax >= (1 << 30)) {
-    if (sizeof(R) == 4) {
-      if (nmax <= 8) return launch_skinny<R, 8, 4, 8>(a, mmax, s);
-      if (nmax <= 16) return launch_skinny<R, 16, 2, 8>(a, mmax, s);
-      if (nmax <= 32) return launch_skinny<R, 32, 1, 8>(a, mmax, s);
-    } else {
-      if (nmax <= 8) return launch_skinny<R, 8, 2, 4>(a, mmax, s);
-      if (nmax <= 16) return launch_skinny<R, 16, 1, 4>(a, mmax, s);
-    }
+  // block-vector products (the sweeps' and the coarse solve's right-hand sides)
+  if (nmax <= 16 && kmax > 0 && mmax > 32) {
+    if (sizeof(R) == 4 && mmax > RG_NT) return launch_rowgemm<R, 2>(a, mmax, nmax, kmax, s);
+    return launch_rowgemm<R, 1>(a, mmax, nmax, kmax, s);
   }
   if (nmax <= 16) {
     if (mmax <= 16) return launch_cfg<R, 16, 16, 16, 1, 1>(a, mmax, nmax, kmax, s);

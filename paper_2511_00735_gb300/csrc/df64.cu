@@ -188,32 +188,43 @@ template cudaError_t df_matvec<float4>(const float4*, const int*, const float4*,
 
 // ---------------------------------------------------------------------------
 // h[i][r] = sum_rows conj(V_i) w   (two-pass, fixed order; block partials in df64, final sum in FP64)
+// Vectors in groups of DG per block (blockIdx.y = group): w is read once per group.
+constexpr int DG = 8;
 __global__ void __launch_bounds__(NT) df_bdot_partial_kernel(const float4* __restrict__ V, long long vstride, int nvec,
                                                              const float4* __restrict__ w, long long rows, int nrhs,
                                                              int rpad, float4* __restrict__ partial, long long chunk) {
-  __shared__ float4 red[NT];
+  __shared__ float4 red[DG][NT];
   const int r = threadIdx.x % rpad, lrow = threadIdx.x / rpad, rper = NT / rpad;
+  const int i0 = blockIdx.y * DG, ng = min(DG, nvec - i0);
   const long long lo = blockIdx.x * chunk, hi = lo + chunk < rows ? lo + chunk : rows;
-  for (int i = 0; i < nvec; ++i) {
-    cacc acc;
-    if (r < nrhs) {
-      const float4* Vi = V + i * vstride;
-      for (long long row = lo + lrow; row < hi; row += rper) cdot2_conj(acc, Vi[row * nrhs + r], w[row * nrhs + r]);
+  cacc acc[DG];
+  if (r < nrhs) {
+    for (long long row = lo + lrow; row < hi; row += rper) {
+      const long long l = row * nrhs + r;
+      const float4 wv = w[l];
+#pragma unroll
+      for (int g = 0; g < DG; ++g)
+        if (g < ng) cdot2_conj(acc[g], V[(i0 + g) * vstride + l], wv);
     }
-    red[threadIdx.x] = cfin(acc);
-    __syncthreads();
-    for (int s2 = rper / 2; s2 > 0; s2 >>= 1) {
-      if (lrow < s2) {
+  }
+#pragma unroll
+  for (int g = 0; g < DG; ++g) red[g][threadIdx.x] = cfin(acc[g]);
+  __syncthreads();
+  for (int s2 = rper / 2; s2 > 0; s2 >>= 1) {
+    if (lrow < s2) {
+#pragma unroll
+      for (int g = 0; g < DG; ++g) {
+        if (g >= ng) break;
         cacc t;
-        cadd2(t, red[threadIdx.x]);
-        cadd2(t, red[threadIdx.x + s2 * rpad]);
-        red[threadIdx.x] = cfin(t);
+        cadd2(t, red[g][threadIdx.x]);
+        cadd2(t, red[g][threadIdx.x + s2 * rpad]);
+        red[g][threadIdx.x] = cfin(t);
       }
-      __syncthreads();
     }
-    if (lrow == 0 && r < nrhs) partial[((long long)blockIdx.x * nvec + i) * nrhs + r] = red[r];
     __syncthreads();
   }
+  if (lrow == 0 && r < nrhs)
+    for (int g = 0; g < ng; ++g) partial[((long long)blockIdx.x * nvec + i0 + g) * nrhs + r] = red[g][r];
 }
 
 __global__ void df_bdot_final_kernel(const float4* __restrict__ partial, int nblk, int nvec, int nrhs,
@@ -241,7 +252,8 @@ cudaError_t df_bdot(const float4* V, long long vstride, int nvec, const float4* 
   while (rpad < nrhs) rpad <<= 1;
   const int nblk = bdot_blocks(rows);
   const long long chunk = (rows + nblk - 1) / nblk;
-  df_bdot_partial_kernel<<<nblk, NT, 0, s>>>(V, vstride, nvec, w, rows, nrhs, rpad, partial, chunk);
+  df_bdot_partial_kernel<<<dim3(nblk, (nvec + DG - 1) / DG), NT, 0, s>>>(V, vstride, nvec, w, rows, nrhs, rpad,
+                                                                         partial, chunk);
   note_launch();
   df_bdot_final_kernel<<<(nvec * nrhs * 32 + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nvec, nrhs, out);
   note_launch();
