@@ -554,9 +554,12 @@ int hps_build_leaves(hps_ctx* c, int precision) {
   if (!good.empty()) {
     const int grid = std::min((int)good.size(), std::max(1, c->num_sms));
     double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
+    double* Zscr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * p.ni * c->nb));
     int* d_good = good.size() == (size_t)c->E ? nullptr : dev_upload(c, good);
-    if (!Ascr || (good.size() != (size_t)c->E && !d_good)) return fail(c, HPS_ENOMEM, "leaf scratch");
+    if (!Ascr || !Zscr || (good.size() != (size_t)c->E && !d_good)) return fail(c, HPS_ENOMEM, "leaf scratch");
     scratch.push_back(Ascr);
+    scratch.push_back(Zscr);
+    p.Zscr = Zscr;
     if (d_good) scratch.push_back(d_good);
     p.Ascr = Ascr;
     p.elems = d_good;
@@ -680,16 +683,18 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
       const int grid = std::min(count, std::max(1, c0->num_sms));
       LeafElem* d_ed = static_cast<LeafElem*>(dev_alloc(c0, sizeof(LeafElem) * groups[N].size()));
       double* Ascr = static_cast<double*>(dev_alloc(c0, sizeof(double) * (size_t)grid * nb * nb));
-      if (!d_ed || !Ascr) return fail(c0, HPS_ENOMEM, "batched leaf workspace");
+      double* Zscr = static_cast<double*>(dev_alloc(c0, sizeof(double) * (size_t)grid * (N - 1) * (N - 1) * nb));
+      if (!d_ed || !Ascr || !Zscr) return fail(c0, HPS_ENOMEM, "batched leaf workspace");
       scratch.push_back(d_ed);
       scratch.push_back(Ascr);
+      scratch.push_back(Zscr);
       HPS_CK(c0, cudaMemcpyAsync(d_ed, groups[N].data(), sizeof(LeafElem) * groups[N].size(), cudaMemcpyHostToDevice,
                                  c0->stream));
       LeafParams p;
       p.N = N; p.q = N - 1; p.ni = (N - 1) * (N - 1); p.nb = nb; p.E = count; p.cw = 8;
       p.h = 1.0; p.eta = 1.0; p.c = nullptr; p.T = nullptr;
       p.Dh = cn->d_Dref; p.Kh = cn->d_Kref; p.wh = cn->d_wref;
-      p.Ascr = Ascr; p.flag = c0->d_flag;
+      p.Ascr = Ascr; p.Zscr = Zscr; p.flag = c0->d_flag;
       p.ed = d_ed; p.count = count;
       HPS_CK(c0, launch_leaf(p, grid, c0->stream));
     }

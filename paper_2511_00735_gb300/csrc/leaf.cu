@@ -20,6 +20,8 @@
 //
 // One persistent CTA per SM (the factor needs almost all of the 227 KB of
 // shared memory); CTAs stride over the elements.
+#include <algorithm>
+
 #include "common.cuh"
 #include "dense.cuh"
 #include "skel.cuh"
@@ -202,6 +204,259 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same maps with the interior solve in FP32 plus FP64 iterative refinement.
+//
+// On the Cholesky route L~_ii is symmetric positive definite and well
+// conditioned (GLL weak form: condition number about 150-200 at N = 16 for the
+// coefficients the host admits), so an FP32 L D L^T factor is a good
+// approximate inverse: with Z_0 = 0 and
+//     R_k = L~_iG - L~_ii Z_k   (FP64),   Z_{k+1} = Z_k + (L D L^T)^{-1} R_k   (FP32 solve)
+// every step gains about -log10(cond * eps_32) = 5 digits, and Z converges to
+// the FP64 solution (classical mixed-precision iterative refinement).  The
+// residual costs only 2 q^3 + q^2 FP64 FMAs per column because L~_ii is a sum
+// of Kronecker products plus a diagonal:
+//     (L~ Z)_(i,j) = w_j sum_i' K[i,i'] Z_(i',j) + w_i sum_j' K[j,j'] Z_(i,j') - c_ij (h/2)^2 w_i w_j Z_(i,j),
+// against ni^2 for a dense FP64 solve.  The FP32 factor lives packed in shared
+// memory (half the FP64 size), the 4q right-hand sides are solved together,
+// each column by four lanes of one warp (no block barriers inside the
+// triangular solves), and the FP64 iterate Z stays in a per-CTA global
+// workspace.  The refinement stops once the predicted next correction is
+// below 1e-14 of Z (ratio of the last two corrections); the element is flagged
+// if that takes more than IR_MAX steps.  A, P = A + i eta I and the FP64
+// Gauss-Jordan inverse are as in leaf_kernel.
+// ---------------------------------------------------------------------------
+constexpr int IR_MAX = 10;
+
+__host__ __device__ inline int ir_ldy(int nb) { return (nb + 23) / 32 * 32 + 8; }  // = 8 mod 32: no bank conflicts
+__host__ __device__ inline int ir_npk_pad(int ni) { return (ni * (ni + 1) / 2 + 3) / 4 * 4; }
+
+// block-wide max of a non-negative value (all threads get the result)
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x / 32); ++w) r = fmax(r, red[w]);
+  return r;
+}
+
+__global__ void __launch_bounds__(256, 1) leaf_ir_kernel(LeafParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
+  const int npk = ni * (ni + 1) / 2, ldy = ir_ldy(nb);
+  float* Lp = reinterpret_cast<float*>(smem_raw);     // packed FP32 factor: unit lower U, d on the diagonal
+  float* Y = Lp + ir_npk_pad(ni);                      // [ni][ldy] right-hand sides / corrections, FP32
+  const size_t reg0 = max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ldy * 4, (size_t)nb * 2 * nb * 16);
+  double* sD = reinterpret_cast<double*>(smem_raw + (reg0 + 15) / 16 * 16);  // [n1*n1] physical D
+  double* sK = sD + n1 * n1;                           // [n1*n1] reference K
+  double* sw = sK + n1 * n1;                           // [n1] reference weights
+  double* sc = sw + n1;                                // [n1*n1] c of this element
+  double* red = sc + n1 * n1;                          // [8] reductions
+  const int tid = threadIdx.x, nth = blockDim.x;
+  double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
+  double* Z = p.Zscr + (long long)blockIdx.x * ni * nb;
+
+  for (int l = tid; l < n1 * n1; l += nth) sK[l] = p.Kh[l];
+  for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
+
+  const int nel = (p.elems || p.ed) ? p.count : p.E;
+  for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
+    const int e = p.elems ? p.elems[ei] : ei;
+    const double h = p.ed ? p.ed[ei].h : p.h;
+    const double eta = p.ed ? p.ed[ei].eta : p.eta;
+    const double* ce = p.ed ? p.ed[ei].c : p.c + (long long)e * n1 * n1;
+    double2* To = p.ed ? p.ed[ei].T : p.T + (long long)e * nb * nb;
+    const double h2 = 0.25 * h * h;
+    const double dsc = 2.0 / h;
+    __syncthreads();
+    for (int l = tid; l < n1 * n1; l += nth) {
+      sc[l] = ce[l];
+      sD[l] = dsc * p.Dh[l];
+    }
+    __syncthreads();
+    // ---- assemble L~_ii (FP32, packed lower triangle) ----
+    for (int l = tid; l < npk; l += nth) {
+      int r = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+      while (r * (r + 1) / 2 > l) --r;
+      while ((r + 1) * (r + 2) / 2 <= l) ++r;
+      const int cc = l - r * (r + 1) / 2;
+      const int i = r / q + 1, j = r % q + 1, i2 = cc / q + 1, j2 = cc % q + 1;
+      double v = 0.0;
+      if (j == j2) v += sK[i * n1 + i2] * sw[j];
+      if (i == i2) v += sw[i] * sK[j * n1 + j2];
+      if (r == cc) v -= sc[i * n1 + j] * h2 * sw[i] * sw[j];
+      Lp[l] = (float)v;
+    }
+    __syncthreads();
+    // ---- FP32 right-looking L D L^T (column k kept in Y's space while it is updated) ----
+    {
+      float* colk = Y;
+      float prev_inv = 0.f;
+      for (int k = 0; k < ni; ++k) {
+        for (int i = k + tid; i < ni; i += nth) colk[i] = Lp[pk(i, k)];
+        __syncthreads();
+        float dk = colk[k];
+        if (!(dk > 0.f)) {
+          if (tid == 0) atomicCAS(p.flag, 0, ei + 1);
+          dk = 1.f;
+        }
+        const float inv = 1.f / dk;
+        if (k > 0)
+          for (int i = k + tid; i < ni; i += nth) Lp[pk(i, k - 1)] *= prev_inv;
+        const int warp = tid / 32, lane = tid % 32, nw = nth / 32;
+        for (int i = k + 1 + warp; i < ni; i += nw) {
+          const float f = colk[i] * inv;
+          float* row = Lp + pk(i, 0);
+          for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= f * colk[j];
+        }
+        prev_inv = inv;
+        __syncthreads();
+      }
+    }
+    // ---- refinement: Z <- Z + (L D L^T)^{-1} (L~_iG - L~_ii Z) ----
+    const int part = tid % 4;  // four lanes per right-hand side column
+    const bool cact = tid / 4 < nb;
+    const int col = cact ? tid / 4 : 0;  // idle lanes read column 0 and write nothing
+    double rel_prev = 1.0;
+    bool done = false;
+    for (int it = 0; it < IR_MAX && !done; ++it) {
+      // residual (FP64), rounded into Y
+      for (int l = tid; l < ni * nb; l += nth) {
+        const int I = l / nb, g = l % nb;
+        const int i = I / q + 1, j = I % q + 1;
+        const int side = g / q, s = g % q + 1;
+        double bv = 0.0;
+        if (side == 0 && j == s) bv = sK[i * n1 + 0] * sw[s];
+        else if (side == 1 && j == s) bv = sK[i * n1 + N] * sw[s];
+        else if (side == 2 && i == s) bv = sw[s] * sK[j * n1 + 0];
+        else if (side == 3 && i == s) bv = sw[s] * sK[j * n1 + N];
+        if (it > 0) {
+          double s1 = 0.0, s2 = 0.0;
+          for (int t = 1; t <= q; ++t) {
+            s1 += sK[i * n1 + t] * Z[(long long)((t - 1) * q + (j - 1)) * nb + g];
+            s2 += sK[j * n1 + t] * Z[(long long)((i - 1) * q + (t - 1)) * nb + g];
+          }
+          bv -= sw[j] * s1 + sw[i] * s2 - sc[i * n1 + j] * h2 * sw[i] * sw[j] * Z[(long long)I * nb + g];
+        }
+        Y[I * ldy + g] = (float)bv;
+      }
+      __syncthreads();
+      // forward: U y = r (unit lower), four lanes per column, warp-synchronous
+      for (int i = 1; i < ni; ++i) {
+        float a0 = 0.f, a1 = 0.f;
+        const float* Ui = Lp + pk(i, 0);
+        int k = part;
+        for (; k + 4 < i; k += 8) {
+          a0 += Ui[k] * Y[k * ldy + col];
+          a1 += Ui[k + 4] * Y[(k + 4) * ldy + col];
+        }
+        if (k < i) a0 += Ui[k] * Y[k * ldy + col];
+        float sum = a0 + a1;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (cact && part == 0) Y[i * ldy + col] -= sum;
+        __syncwarp();
+      }
+      // diagonal
+      if (cact)
+        for (int i = part; i < ni; i += 4) Y[i * ldy + col] /= Lp[pk(i, i)];
+      __syncwarp();
+      // backward: U^T x = z
+      for (int i = ni - 2; i >= 0; --i) {
+        float a0 = 0.f, a1 = 0.f;
+        int k = i + 1 + part;
+        for (; k + 4 < ni; k += 8) {
+          a0 += Lp[pk(k, i)] * Y[k * ldy + col];
+          a1 += Lp[pk(k + 4, i)] * Y[(k + 4) * ldy + col];
+        }
+        if (k < ni) a0 += Lp[pk(k, i)] * Y[k * ldy + col];
+        float sum = a0 + a1;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (cact && part == 0) Y[i * ldy + col] -= sum;
+        __syncwarp();
+      }
+      __syncthreads();
+      // Z += correction (FP64), sizes for the stopping test
+      double md = 0.0, mz = 0.0;
+      for (int l = tid; l < ni * nb; l += nth) {
+        const int I = l / nb, g = l % nb;
+        const double d = (double)Y[I * ldy + g];
+        const double z = (it == 0 ? 0.0 : Z[l]) + d;
+        Z[l] = z;
+        md = fmax(md, fabs(d));
+        mz = fmax(mz, fabs(z));
+      }
+      md = block_max(md, red);
+      mz = block_max(mz, red);
+      const double rel = mz > 0.0 ? md / mz : 0.0;
+      if (it > 0) {
+        const double rho = fmax(rel / rel_prev, 1e-6);
+        done = rel * rho <= 1e-14;
+      }
+      if (!(rel == rel)) done = false;
+      rel_prev = rel > 0.0 ? rel : 1e-300;
+      if (rel == 0.0) done = true;
+      if (!done && it == IR_MAX - 1 && tid == 0) atomicCAS(p.flag, 0, ei + 1);
+      __syncthreads();
+    }
+
+    // ---- A = Dn_GG - Dn_Gi Z (FP64) ----
+    for (int l = tid; l < nb * nb; l += nth) {
+      const int g = l / nb, gc = l % nb;
+      const int side = g / q, s = g % q + 1;
+      double acc = 0.0;
+      for (int t = 1; t <= q; ++t) {
+        int I;
+        double dcoef;
+        if (side == 0) { I = (t - 1) * q + (s - 1); dcoef = -sD[0 * n1 + t]; }
+        else if (side == 1) { I = (t - 1) * q + (s - 1); dcoef = sD[N * n1 + t]; }
+        else if (side == 2) { I = (s - 1) * q + (t - 1); dcoef = -sD[0 * n1 + t]; }
+        else { I = (s - 1) * q + (t - 1); dcoef = sD[N * n1 + t]; }
+        acc += dcoef * Z[(long long)I * nb + gc];
+      }
+      const int sidec = gc / q, sc2 = gc % q + 1;
+      double dgg = 0.0;
+      if (sc2 == s) {
+        const bool xside = side < 2, xsidec = sidec < 2;
+        if (xside == xsidec) {
+          const int rowN = (side == 0 || side == 2) ? 0 : N;
+          const int colN = (sidec == 0 || sidec == 2) ? 0 : N;
+          const double sg = (side == 0 || side == 2) ? -1.0 : 1.0;
+          dgg = sg * sD[rowN * n1 + colN];
+        }
+      }
+      A[g * nb + gc] = dgg - acc;
+    }
+    __syncthreads();
+    // ---- P = A + i eta I, Gauss-Jordan [P | I] -> P^{-1}, T = I - 2 i eta P^{-1} ----
+    double2* W = reinterpret_cast<double2*>(smem_raw);
+    const int ld = 2 * nb;
+    for (int l = tid; l < nb * ld; l += nth) {
+      const int g = l / ld, j = l % ld;
+      double2 v = make_double2(0.0, 0.0);
+      if (j < nb) {
+        v.x = A[g * nb + j];
+        if (j == g) v.y = eta;
+      } else if (j - nb == g) {
+        v.x = 1.0;
+      }
+      W[l] = v;
+    }
+    __syncthreads();
+    gj_smem<double>(W, nb, ld, ld, nullptr);
+    for (int l = tid; l < nb * nb; l += nth) {
+      const int g = l / nb, j = l % nb;
+      const double2 y = W[g * ld + nb + j];
+      To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
+    }
+  }
+}
+
 }  // namespace
 
 
@@ -354,10 +609,20 @@ size_t leaf_smem_bytes(int N, int cw) {
   return sizeof(double) * ((r1 > r2 ? r1 : r2) + 3 * n1 * n1 + n1);
 }
 
+size_t leaf_ir_smem_bytes(int N) {
+  const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
+  const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
+  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 8);
+}
+
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
-  const size_t smem = leaf_smem_bytes(p.N, p.cw);
-  smem_optin(leaf_kernel);
-  leaf_kernel<<<grid, 256, smem, s>>>(p);
+  if (p.Zscr) {
+    smem_optin(leaf_ir_kernel);
+    leaf_ir_kernel<<<grid, 256, leaf_ir_smem_bytes(p.N), s>>>(p);
+  } else {
+    smem_optin(leaf_kernel);
+    leaf_kernel<<<grid, 256, leaf_smem_bytes(p.N, p.cw), s>>>(p);
+  }
   note_launch();
   return cudaGetLastError();
 }
