@@ -233,8 +233,7 @@ __global__ void __launch_bounds__(NT) gj_panel_kernel(c_t<R>* W, int m, int ld, 
         const int i = c + 1 + l / w, j = c + 1 + l % w;
         C v = S[i * kb + j];
         const C f = S[i * kb + c], u = S[c * kb + j];
-        v.x -= f.x * u.x - f.y * u.y;
-        v.y -= f.x * u.y + f.y * u.x;
+        cfms(v, f, u);
         S[i * kb + j] = v;
       }
     }
@@ -276,8 +275,7 @@ __global__ void __launch_bounds__(NT) gj_apply_kernel(c_t<R>* W, int m, int ld, 
     for (int cc = 0; cc < c; ++cc) {
       if (c < kb) {
         const C f = sL[c * GJ_NB + cc];
-        y[c].x -= f.x * y[cc].x - f.y * y[cc].y;
-        y[c].y -= f.x * y[cc].y + f.y * y[cc].x;
+        cfms(y[c], f, y[cc]);
       }
     }
   }
@@ -288,8 +286,7 @@ __global__ void __launch_bounds__(NT) gj_apply_kernel(c_t<R>* W, int m, int ld, 
       for (int cc = c + 1; cc < GJ_NB; ++cc) {
         if (cc < kb) {
           const C f = sL[c * GJ_NB + cc];
-          y[c].x -= f.x * y[cc].x - f.y * y[cc].y;
-          y[c].y -= f.x * y[cc].y + f.y * y[cc].x;
+          cfms(y[c], f, y[cc]);
         }
       }
       y[c] = cmul(y[c], cinv(sL[c * GJ_NB + c]));

@@ -54,6 +54,13 @@ template <typename T> __host__ __device__ __forceinline__ void cfma(T& acc, T a,
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
 }
+// acc -= a * b (four FMAs)
+template <typename T> __host__ __device__ __forceinline__ void cfms(T& acc, T a, T b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
 // acc += conj(a) * b
 template <typename T> __host__ __device__ __forceinline__ void cfma_conj(T& acc, T a, T b) {
   acc.x = fma(a.x, b.x, acc.x);

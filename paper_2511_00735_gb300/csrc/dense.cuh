@@ -24,15 +24,16 @@ __device__ __forceinline__ void warp_argmax(V& v, int& i) {
 }
 
 // Block-wide argmax over rows [lo, hi) of cabs1(S[row * ld + col]).  All threads
-// must call it; returns the winning row in every thread.
+// must call it (any block size up to 1024); returns the winning row in every thread.
 template <typename R>
 __device__ int block_argmax_col(const c_t<R>* S, int ld, int col, int lo, int hi) {
-  __shared__ R s_v[DNT / 32];
-  __shared__ int s_i[DNT / 32];
+  __shared__ R s_v[32];
+  __shared__ int s_i[32];
   __shared__ int s_res;
+  const int nw = (int)(blockDim.x / 32);
   R best = R(-1);
   int bi = -1;
-  for (int r = lo + (int)threadIdx.x; r < hi; r += DNT) {
+  for (int r = lo + (int)threadIdx.x; r < hi; r += (int)blockDim.x) {
     const R v = cabs1(S[(long long)r * ld + col]);
     if (v > best) {
       best = v;
@@ -47,8 +48,8 @@ __device__ int block_argmax_col(const c_t<R>* S, int ld, int col, int lo, int hi
   }
   __syncthreads();
   if (w == 0) {
-    best = lane < DNT / 32 ? s_v[lane] : R(-1);
-    bi = lane < DNT / 32 ? s_i[lane] : -1;
+    best = lane < nw ? s_v[lane] : R(-1);
+    bi = lane < nw ? s_i[lane] : -1;
     warp_argmax(best, bi);
     if (lane == 0) s_res = bi;
   }
@@ -87,8 +88,7 @@ __device__ void gj_smem(c_t<R>* W, int n, int ld, int ncols, int* flag) {
       const C f = W[i * ld + k];
       C v = W[i * ld + j];
       const C pk = W[k * ld + j];
-      v.x -= f.x * pk.x - f.y * pk.y;
-      v.y -= f.x * pk.y + f.y * pk.x;
+      cfms(v, f, pk);
       W[i * ld + j] = v;
     }
     __syncthreads();

@@ -218,17 +218,20 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
 // of Kronecker products plus a diagonal:
 //     (L~ Z)_(i,j) = w_j sum_i' K[i,i'] Z_(i',j) + w_i sum_j' K[j,j'] Z_(i,j') - c_ij (h/2)^2 w_i w_j Z_(i,j),
 // against ni^2 for a dense FP64 solve.  The FP32 factor lives packed in shared
-// memory (half the FP64 size), the 4q right-hand sides are solved together,
-// each column by four lanes of one warp (no block barriers inside the
-// triangular solves), and the FP64 iterate Z stays in a per-CTA global
-// workspace.  The refinement stops once the predicted next correction is
+// memory (half the FP64 size) and the 4q right-hand sides are solved together
+// by row blocks: a block-wide GEMM update from the solved rows, then a short
+// triangle per column in registers.  The FP64 iterate Z stays in a per-CTA
+// global workspace.  The refinement stops once the predicted next correction is
 // below 1e-14 of Z (ratio of the last two corrections); the element is flagged
 // if that takes more than IR_MAX steps.  A, P = A + i eta I and the FP64
 // Gauss-Jordan inverse are as in leaf_kernel.
 // ---------------------------------------------------------------------------
 constexpr int IR_MAX = 10;
+constexpr int TB = 32;     // row block of the triangular solves
+constexpr int PB = 16;     // panel width of the FP32 L D L^T
+constexpr int IR_NT = 512;  // threads per CTA
 
-__host__ __device__ inline int ir_ldy(int nb) { return (nb + 23) / 32 * 32 + 8; }  // = 8 mod 32: no bank conflicts
+__host__ __device__ inline int ir_ldy(int nb) { return (nb + 3) / 4 * 4 + 4; }  // 16-byte rows, staggered banks
 __host__ __device__ inline int ir_npk_pad(int ni) { return (ni * (ni + 1) / 2 + 3) / 4 * 4; }
 
 // block-wide max of a non-negative value (all threads get the result)
@@ -244,10 +247,10 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(256, 1) leaf_ir_kernel(LeafParams p) {
+__global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
-  const int npk = ni * (ni + 1) / 2, ldy = ir_ldy(nb);
+  const int ldy = ir_ldy(nb);
   float* Lp = reinterpret_cast<float*>(smem_raw);     // packed FP32 factor: unit lower U, d on the diagonal
   float* Y = Lp + ir_npk_pad(ni);                      // [ni][ldy] right-hand sides / corrections, FP32
   const size_t reg0 = max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ldy * 4, (size_t)nb * 2 * nb * 16);
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(256, 1) leaf_ir_kernel(LeafParams p) {
   double* sK = sD + n1 * n1;                           // [n1*n1] reference K
   double* sw = sK + n1 * n1;                           // [n1] reference weights
   double* sc = sw + n1;                                // [n1*n1] c of this element
-  double* red = sc + n1 * n1;                          // [8] reductions
+  double* red = sc + n1 * n1;                          // [IR_NT / 32] reductions
   const int tid = threadIdx.x, nth = blockDim.x;
   double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
   double* Z = p.Zscr + (long long)blockIdx.x * ni * nb;
@@ -278,49 +281,95 @@ __global__ void __launch_bounds__(256, 1) leaf_ir_kernel(LeafParams p) {
       sD[l] = dsc * p.Dh[l];
     }
     __syncthreads();
-    // ---- assemble L~_ii (FP32, packed lower triangle) ----
-    for (int l = tid; l < npk; l += nth) {
-      int r = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
-      while (r * (r + 1) / 2 > l) --r;
-      while ((r + 1) * (r + 2) / 2 <= l) ++r;
-      const int cc = l - r * (r + 1) / 2;
-      const int i = r / q + 1, j = r % q + 1, i2 = cc / q + 1, j2 = cc % q + 1;
-      double v = 0.0;
-      if (j == j2) v += sK[i * n1 + i2] * sw[j];
-      if (i == i2) v += sw[i] * sK[j * n1 + j2];
-      if (r == cc) v -= sc[i * n1 + j] * h2 * sw[i] * sw[j];
-      Lp[l] = (float)v;
+    // ---- assemble L~_ii (FP32, packed lower triangle), one warp per row ----
+    {
+      const int warp = tid / 32, lane = tid % 32, nw = nth / 32;
+      for (int r = warp; r < ni; r += nw) {
+        const int i = r / q + 1, j = r % q + 1;
+        float* row = Lp + pk(r, 0);
+        for (int cc = lane; cc <= r; cc += 32) {
+          const int i2 = cc / q + 1, j2 = cc % q + 1;
+          double v = 0.0;
+          if (j == j2) v += sK[i * n1 + i2] * sw[j];
+          if (i == i2) v += sw[i] * sK[j * n1 + j2];
+          if (r == cc) v -= sc[i * n1 + j] * h2 * sw[i] * sw[j];
+          row[cc] = (float)v;
+        }
+      }
     }
     __syncthreads();
-    // ---- FP32 right-looking L D L^T (column k kept in Y's space while it is updated) ----
+    // ---- FP32 blocked right-looking L D L^T: panels of PB columns are factored column by
+    //      column, then the trailing matrix takes one rank-PB update, register-tiled 4 x 4
+    //      from k-major copies of the panel (scaled L and L D) ----
     {
-      float* colk = Y;
-      float prev_inv = 0.f;
-      for (int k = 0; k < ni; ++k) {
-        for (int i = k + tid; i < ni; i += nth) colk[i] = Lp[pk(i, k)];
-        __syncthreads();
-        float dk = colk[k];
-        if (!(dk > 0.f)) {
-          if (tid == 0) atomicCAS(p.flag, 0, ei + 1);
-          dk = 1.f;
+      const int mpad = (ni + 3) / 4 * 4;
+      float* Ps = Y;                 // [PB][mpad] panel rows below it: L (unit lower, scaled)
+      float* Pd = Ps + PB * mpad;    // [PB][mpad] the same times d
+      float* colk = Pd + PB * mpad;  // [ni]
+      for (int p0 = 0; p0 < ni; p0 += PB) {
+        const int pe = min(p0 + PB, ni);
+        for (int l = tid; l < 2 * PB * mpad; l += nth) Ps[l] = 0.f;  // padding rows and columns stay 0
+        for (int k = p0; k < pe; ++k) {
+          for (int i = k + tid; i < ni; i += nth) colk[i] = Lp[pk(i, k)];
+          __syncthreads();
+          float dk = colk[k];
+          if (!(dk > 0.f)) {
+            if (tid == 0) atomicCAS(p.flag, 0, ei + 1);
+            dk = 1.f;
+          }
+          const float inv = 1.f / dk;
+          for (int i = k + 1 + tid; i < ni; i += nth) {
+            float* row = Lp + pk(i, 0);
+            const float f = colk[i] * inv;
+            const int je = min(i, pe - 1);
+            for (int j = k + 1; j <= je; ++j) row[j] -= f * colk[j];
+            row[k] = f;  // U(i, k)
+            if (i >= pe) {
+              Ps[(k - p0) * mpad + (i - pe)] = f;
+              Pd[(k - p0) * mpad + (i - pe)] = colk[i];
+            }
+          }
+          __syncthreads();
         }
-        const float inv = 1.f / dk;
-        if (k > 0)
-          for (int i = k + tid; i < ni; i += nth) Lp[pk(i, k - 1)] *= prev_inv;
-        const int warp = tid / 32, lane = tid % 32, nw = nth / 32;
-        for (int i = k + 1 + warp; i < ni; i += nw) {
-          const float f = colk[i] * inv;
-          float* row = Lp + pk(i, 0);
-          for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= f * colk[j];
+        const int m = ni - pe;
+        if (m <= 0) continue;
+        const int nt = (m + 3) / 4, ntiles = nt * (nt + 1) / 2;
+        for (int tt = tid; tt < ntiles; tt += nth) {
+          int ti = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
+          while (ti * (ti + 1) / 2 > tt) --ti;
+          while ((ti + 1) * (ti + 2) / 2 <= tt) ++ti;
+          const int tj = tt - ti * (ti + 1) / 2;
+          float acc[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+          for (int kk = 0; kk < PB; ++kk) {
+            const float4 a4 = *reinterpret_cast<const float4*>(Ps + kk * mpad + 4 * ti);
+            const float4 b4 = *reinterpret_cast<const float4*>(Pd + kk * mpad + 4 * tj);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = pe + 4 * ti + u;
+            if (i >= ni) continue;
+            float* row = Lp + pk(i, 0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int j = pe + 4 * tj + v;
+              if (j <= i) row[j] -= acc[u][v];
+            }
+          }
         }
-        prev_inv = inv;
         __syncthreads();
       }
     }
     // ---- refinement: Z <- Z + (L D L^T)^{-1} (L~_iG - L~_ii Z) ----
-    const int part = tid % 4;  // four lanes per right-hand side column
-    const bool cact = tid / 4 < nb;
-    const int col = cact ? tid / 4 : 0;  // idle lanes read column 0 and write nothing
     double rel_prev = 1.0;
     bool done = false;
     for (int it = 0; it < IR_MAX && !done; ++it) {
@@ -345,40 +394,93 @@ __global__ void __launch_bounds__(256, 1) leaf_ir_kernel(LeafParams p) {
         Y[I * ldy + g] = (float)bv;
       }
       __syncthreads();
-      // forward: U y = r (unit lower), four lanes per column, warp-synchronous
-      for (int i = 1; i < ni; ++i) {
-        float a0 = 0.f, a1 = 0.f;
-        const float* Ui = Lp + pk(i, 0);
-        int k = part;
-        for (; k + 4 < i; k += 8) {
-          a0 += Ui[k] * Y[k * ldy + col];
-          a1 += Ui[k + 4] * Y[(k + 4) * ldy + col];
+      // forward U y = r, diagonal, backward U^T x = z, by row blocks of TB: the rows above
+      // (below) a block enter through one block-wide GEMM update (thread: one row x four
+      // columns), then one lane per column finishes the TB x TB triangle in registers
+      {
+        const int gr = tid / 16, gq = tid % 16;  // GEMM-update row and column quad
+        const bool gact = 4 * gq < nb;
+        for (int r0 = 0; r0 < ni; r0 += TB) {
+          const int nr = min(TB, ni - r0);
+          if (r0 > 0 && gact && gr < nr) {
+            const float* Ur = Lp + pk(r0 + gr, 0);
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+            for (int k = 0; k < r0; ++k) {
+              const float u = Ur[k];
+              const float4 y = *reinterpret_cast<const float4*>(Y + k * ldy + 4 * gq);
+              acc.x += u * y.x; acc.y += u * y.y; acc.z += u * y.z; acc.w += u * y.w;
+            }
+            float4* yo = reinterpret_cast<float4*>(Y + (r0 + gr) * ldy + 4 * gq);
+            float4 v = *yo;
+            v.x -= acc.x; v.y -= acc.y; v.z -= acc.z; v.w -= acc.w;
+            *yo = v;
+          }
+          __syncthreads();
+          if (tid < nb) {
+            float yb[TB];
+#pragma unroll
+            for (int t = 0; t < TB; ++t) yb[t] = t < nr ? Y[(r0 + t) * ldy + tid] : 0.f;
+#pragma unroll
+            for (int t = 1; t < TB; ++t) {
+              if (t < nr) {
+                const float* Ut = Lp + pk(r0 + t, r0);
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int u = 0; u < t; u += 2) {
+                  s0 += Ut[u] * yb[u];
+                  if (u + 1 < t) s1 += Ut[u + 1] * yb[u + 1];
+                }
+                yb[t] -= s0 + s1;
+              }
+            }
+#pragma unroll
+            for (int t = 0; t < TB; ++t)
+              if (t < nr) Y[(r0 + t) * ldy + tid] = yb[t];
+          }
+          __syncthreads();
         }
-        if (k < i) a0 += Ui[k] * Y[k * ldy + col];
-        float sum = a0 + a1;
-        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-        if (cact && part == 0) Y[i * ldy + col] -= sum;
-        __syncwarp();
-      }
-      // diagonal
-      if (cact)
-        for (int i = part; i < ni; i += 4) Y[i * ldy + col] /= Lp[pk(i, i)];
-      __syncwarp();
-      // backward: U^T x = z
-      for (int i = ni - 2; i >= 0; --i) {
-        float a0 = 0.f, a1 = 0.f;
-        int k = i + 1 + part;
-        for (; k + 4 < ni; k += 8) {
-          a0 += Lp[pk(k, i)] * Y[k * ldy + col];
-          a1 += Lp[pk(k + 4, i)] * Y[(k + 4) * ldy + col];
+        for (int l = tid; l < ni * nb; l += nth) {  // z = D^{-1} y
+          const int I = l / nb;
+          Y[I * ldy + l % nb] /= Lp[pk(I, I)];
         }
-        if (k < ni) a0 += Lp[pk(k, i)] * Y[k * ldy + col];
-        float sum = a0 + a1;
-        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-        if (cact && part == 0) Y[i * ldy + col] -= sum;
-        __syncwarp();
+        __syncthreads();
+        for (int r1 = ni; r1 > 0; r1 -= TB) {
+          const int r0 = max(0, r1 - TB), nr = r1 - r0;
+          if (r1 < ni && gact && gr < nr) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+            for (int k = r1; k < ni; ++k) {
+              const float u = Lp[pk(k, r0 + gr)];
+              const float4 x = *reinterpret_cast<const float4*>(Y + k * ldy + 4 * gq);
+              acc.x += u * x.x; acc.y += u * x.y; acc.z += u * x.z; acc.w += u * x.w;
+            }
+            float4* xo = reinterpret_cast<float4*>(Y + (r0 + gr) * ldy + 4 * gq);
+            float4 v = *xo;
+            v.x -= acc.x; v.y -= acc.y; v.z -= acc.z; v.w -= acc.w;
+            *xo = v;
+          }
+          __syncthreads();
+          if (tid < nb) {
+            float xb[TB];
+#pragma unroll
+            for (int t = 0; t < TB; ++t) xb[t] = t < nr ? Y[(r0 + t) * ldy + tid] : 0.f;
+#pragma unroll
+            for (int t = TB - 2; t >= 0; --t) {
+              float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+              for (int u = t + 1; u < TB; u += 2) {
+                if (u < nr) s0 += Lp[pk(r0 + u, r0 + t)] * xb[u];
+                if (u + 1 < TB && u + 1 < nr) s1 += Lp[pk(r0 + u + 1, r0 + t)] * xb[u + 1];
+              }
+              xb[t] -= s0 + s1;
+            }
+#pragma unroll
+            for (int t = 0; t < TB; ++t)
+              if (t < nr) Y[(r0 + t) * ldy + tid] = xb[t];
+          }
+          __syncthreads();
+        }
       }
       __syncthreads();
       // Z += correction (FP64), sizes for the stopping test
@@ -433,26 +535,68 @@ __global__ void __launch_bounds__(256, 1) leaf_ir_kernel(LeafParams p) {
       A[g * nb + gc] = dgg - acc;
     }
     __syncthreads();
-    // ---- P = A + i eta I, Gauss-Jordan [P | I] -> P^{-1}, T = I - 2 i eta P^{-1} ----
-    double2* W = reinterpret_cast<double2*>(smem_raw);
-    const int ld = 2 * nb;
-    for (int l = tid; l < nb * ld; l += nth) {
-      const int g = l / ld, j = l % ld;
-      double2 v = make_double2(0.0, 0.0);
-      if (j < nb) {
-        v.x = A[g * nb + j];
-        if (j == g) v.y = eta;
-      } else if (j - nb == g) {
-        v.x = 1.0;
+    // ---- P = A + i eta I, in-place Gauss-Jordan with partial pivoting -> P^{-1} (FP64),
+    //      T = I - 2 i eta P^{-1} ----
+    {
+      double2* W = reinterpret_cast<double2*>(smem_raw);  // [nb][nb], reuses the factor's space
+      double2* colk = W + nb * nb;                         // [nb]
+      int* perm = reinterpret_cast<int*>(colk + nb);       // [nb]
+      for (int l = tid; l < nb * nb; l += nth) {
+        const int g = l / nb, j = l % nb;
+        W[l] = make_double2(A[l], g == j ? eta : 0.0);
       }
-      W[l] = v;
-    }
-    __syncthreads();
-    gj_smem<double>(W, nb, ld, ld, nullptr);
-    for (int l = tid; l < nb * nb; l += nth) {
-      const int g = l / nb, j = l % nb;
-      const double2 y = W[g * ld + nb + j];
-      To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
+      __syncthreads();
+      const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
+      for (int k = 0; k < nb; ++k) {
+        const int pr = block_argmax_col<double>(W, nb, k, k, nb);
+        const int pv = pr >= 0 ? pr : k;
+        if (tid == 0) {
+          perm[k] = pv;
+          if (pr < 0) atomicCAS(p.flag, 0, ei + 1);
+        }
+        if (pv != k)
+          for (int j = tid; j < nb; j += nth) {
+            const double2 t = W[k * nb + j];
+            W[k * nb + j] = W[pv * nb + j];
+            W[pv * nb + j] = t;
+          }
+        __syncthreads();
+        const double2 piv = W[k * nb + k];
+        if (tid == 0 && piv.x == 0.0 && piv.y == 0.0) atomicCAS(p.flag, 0, ei + 1);
+        const double2 inv = cinv(piv);
+        for (int i = tid; i < nb; i += nth) colk[i] = W[i * nb + k];
+        __syncthreads();
+        // pivot row: W[k][j] = (j == k ? 1 : W[k][j]) / piv
+        for (int j = tid; j < nb; j += nth) W[k * nb + j] = cmul(j == k ? make_double2(1.0, 0.0) : W[k * nb + j], inv);
+        __syncthreads();
+        if (jc < nb) {
+          const double2 rk = W[k * nb + jc];
+          for (int i = rg; i < nb; i += nrg) {
+            if (i == k) continue;
+            const double2 f = colk[i];
+            double2 v = jc == k ? make_double2(0.0, 0.0) : W[i * nb + jc];
+            cfms(v, f, rk);
+            W[i * nb + jc] = v;
+          }
+        }
+        __syncthreads();
+      }
+      // undo the row interchanges as column interchanges, last first
+      for (int k = nb - 1; k >= 0; --k) {
+        const int pv = perm[k];
+        if (pv != k)
+          for (int i = tid; i < nb; i += nth) {
+            const double2 t = W[i * nb + k];
+            W[i * nb + k] = W[i * nb + pv];
+            W[i * nb + pv] = t;
+          }
+        __syncthreads();
+      }
+      for (int l = tid; l < nb * nb; l += nth) {
+        const int g = l / nb, j = l % nb;
+        const double2 y = W[l];
+        To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
+      }
     }
   }
 }
@@ -612,13 +756,13 @@ size_t leaf_smem_bytes(int N, int cw) {
 size_t leaf_ir_smem_bytes(int N) {
   const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
   const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
-  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 8);
+  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + IR_NT / 32);
 }
 
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
   if (p.Zscr) {
     smem_optin(leaf_ir_kernel);
-    leaf_ir_kernel<<<grid, 256, leaf_ir_smem_bytes(p.N), s>>>(p);
+    leaf_ir_kernel<<<grid, IR_NT, leaf_ir_smem_bytes(p.N), s>>>(p);
   } else {
     smem_optin(leaf_kernel);
     leaf_kernel<<<grid, 256, leaf_smem_bytes(p.N, p.cw), s>>>(p);
