@@ -247,6 +247,36 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return r;
 }
 
+// Block-wide pivot search over rows [lo, hi) of column col (largest |re| + |im|, ties to
+// the lower row); scratch: 2 * (blockDim / 32) doubles.  Two barriers; every thread gets
+// the row.  The caller separates consecutive calls by a barrier.
+__device__ int ir_argmax_col(const double2* W, int ld, int col, int lo, int hi, double* scratch) {
+  double best = -1.0;
+  int bi = -1;
+  for (int r = lo + (int)threadIdx.x; r < hi; r += (int)blockDim.x) {
+    const double2 w = W[r * ld + col];
+    const double v = fabs(w.x) + fabs(w.y);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
+  }
+  warp_argmax(best, bi);
+  const int nw = (int)(blockDim.x / 32), w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int* si = reinterpret_cast<int*>(scratch + nw);
+  if (lane == 0) {
+    scratch[w] = best;
+    si[w] = bi;
+  }
+  __syncthreads();
+  double b2 = lane < nw ? scratch[lane] : -1.0;
+  int i2 = lane < nw ? si[lane] : -1;
+  warp_argmax(b2, i2);  // every warp reduces the per-warp winners itself
+  i2 = __shfl_sync(0xffffffffu, i2, 0);
+  __syncthreads();
+  return i2 >= 0 ? i2 : lo;
+}
+
 __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
@@ -258,7 +288,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   double* sK = sD + n1 * n1;                           // [n1*n1] reference K
   double* sw = sK + n1 * n1;                           // [n1] reference weights
   double* sc = sw + n1;                                // [n1*n1] c of this element
-  double* red = sc + n1 * n1;                          // [IR_NT / 32] reductions
+  double* red = sc + n1 * n1;                          // [2 * IR_NT / 32] reductions
   const int tid = threadIdx.x, nth = blockDim.x;
   double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
   double* Z = p.Zscr + (long long)blockIdx.x * ni * nb;
@@ -539,8 +569,10 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
     //      T = I - 2 i eta P^{-1} ----
     {
       double2* W = reinterpret_cast<double2*>(smem_raw);  // [nb][nb], reuses the factor's space
-      double2* colk = W + nb * nb;                         // [nb]
-      int* perm = reinterpret_cast<int*>(colk + nb);       // [nb]
+      double2* colk = W + nb * nb;                         // [nb] column k after the interchange
+      double2* rowk = colk + nb;                           // [nb] scaled pivot row
+      double2* s_inv = rowk + nb;                          // [1]
+      int* perm = reinterpret_cast<int*>(s_inv + 1);       // [nb] pivot rows, then the column order
       for (int l = tid; l < nb * nb; l += nth) {
         const int g = l / nb, j = l % nb;
         W[l] = make_double2(A[l], g == j ? eta : 0.0);
@@ -548,53 +580,55 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       __syncthreads();
       const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
       for (int k = 0; k < nb; ++k) {
-        const int pr = block_argmax_col<double>(W, nb, k, k, nb);
-        const int pv = pr >= 0 ? pr : k;
-        if (tid == 0) {
-          perm[k] = pv;
-          if (pr < 0) atomicCAS(p.flag, 0, ei + 1);
-        }
-        if (pv != k)
-          for (int j = tid; j < nb; j += nth) {
-            const double2 t = W[k * nb + j];
-            W[k * nb + j] = W[pv * nb + j];
-            W[pv * nb + j] = t;
+        const int pv = ir_argmax_col(W, nb, k, k, nb, red);
+        // interchange rows k and pv; the thread of column k also inverts the pivot
+        for (int j = tid; j < nb; j += nth) {
+          const double2 a = W[k * nb + j], b = W[pv * nb + j];
+          W[k * nb + j] = b;
+          W[pv * nb + j] = a;
+          if (j == k) {
+            if (b.x == 0.0 && b.y == 0.0) atomicCAS(p.flag, 0, ei + 1);
+            *s_inv = cinv(b);
+            perm[k] = pv;
           }
+        }
         __syncthreads();
-        const double2 piv = W[k * nb + k];
-        if (tid == 0 && piv.x == 0.0 && piv.y == 0.0) atomicCAS(p.flag, 0, ei + 1);
-        const double2 inv = cinv(piv);
+        const double2 inv = *s_inv;
         for (int i = tid; i < nb; i += nth) colk[i] = W[i * nb + k];
-        __syncthreads();
-        // pivot row: W[k][j] = (j == k ? 1 : W[k][j]) / piv
-        for (int j = tid; j < nb; j += nth) W[k * nb + j] = cmul(j == k ? make_double2(1.0, 0.0) : W[k * nb + j], inv);
+        for (int j = tid; j < nb; j += nth) rowk[j] = cmul(j == k ? make_double2(1.0, 0.0) : W[k * nb + j], inv);
         __syncthreads();
         if (jc < nb) {
-          const double2 rk = W[k * nb + jc];
+          const double2 rk = rowk[jc];
+#pragma unroll 2
           for (int i = rg; i < nb; i += nrg) {
-            if (i == k) continue;
-            const double2 f = colk[i];
-            double2 v = jc == k ? make_double2(0.0, 0.0) : W[i * nb + jc];
-            cfms(v, f, rk);
-            W[i * nb + jc] = v;
+            if (i == k) {
+              W[i * nb + jc] = rk;
+            } else {
+              const double2 f = colk[i];
+              double2 v = jc == k ? make_double2(0.0, 0.0) : W[i * nb + jc];
+              cfms(v, f, rk);
+              W[i * nb + jc] = v;
+            }
           }
         }
         __syncthreads();
       }
-      // undo the row interchanges as column interchanges, last first
-      for (int k = nb - 1; k >= 0; --k) {
-        const int pv = perm[k];
-        if (pv != k)
-          for (int i = tid; i < nb; i += nth) {
-            const double2 t = W[i * nb + k];
-            W[i * nb + k] = W[i * nb + pv];
-            W[i * nb + pv] = t;
-          }
-        __syncthreads();
+      // the row interchanges, undone last first as column interchanges, compose to one column order
+      if (tid == 0) {
+        int* sig = perm + nb;  // [nb]
+        for (int c = 0; c < nb; ++c) sig[c] = c;
+        for (int k = nb - 1; k >= 0; --k) {
+          const int pk2 = perm[k];
+          const int t = sig[k];
+          sig[k] = sig[pk2];
+          sig[pk2] = t;
+        }
       }
+      __syncthreads();
+      const int* sig = perm + nb;
       for (int l = tid; l < nb * nb; l += nth) {
         const int g = l / nb, j = l % nb;
-        const double2 y = W[l];
+        const double2 y = W[g * nb + sig[j]];
         To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
       }
     }
@@ -756,7 +790,7 @@ size_t leaf_smem_bytes(int N, int cw) {
 size_t leaf_ir_smem_bytes(int N) {
   const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
   const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
-  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + IR_NT / 32);
+  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 2 * (IR_NT / 32));
 }
 
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
