@@ -32,9 +32,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "64x64 elements, N=16 GLL, kappa=100, 1 seeded bump, 16 plane-wave RHS, L_exact=10, 5 coarse GMRES steps"
 FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (nominal, vector = tensor rate)
-# dram read + write bytes of one leaf_kernel launch at 64x64, N=16 from the committed ncu capture
-# (profiles/leaf_kernel_64x64_N16.md); must be reset to None whenever leaf.cu changes.
-LEAF_TRAFFIC_BYTES = 191.9e6
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# dram read + write bytes of one leaf_ir_kernel launch at 64x64, N=16 from the committed ncu capture
+# (profiles/leaf_ir_kernel_64x64_N16.md); None until captured and whenever leaf.cu changes.
+LEAF_TRAFFIC_BYTES = None
 
 
 def load_peaks():
@@ -99,17 +100,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- FLOP models
-def leaf_flops(N: int) -> float:
-    """FP64 flops the leaf kernel executes per element (Cholesky of the interior block,
-    two triangular solves with 4q right-hand sides, A = Dn_GG - Dn_Gi Z, complex Gauss-Jordan)."""
+def leaf_flops(N: int, residuals: int = 2) -> tuple:
+    """Executed flops of the leaf kernel per element: (FP64, FP32).
+
+    FP32: L D L^T of the n_i x n_i interior block (n_i^3/6 FMAs) and residuals + 1 pairs of
+    triangular solves with 4q right-hand sides (n_i^2 * 4q FMAs each).  FP64: `residuals`
+    Kronecker-structured residuals (n_i * 4q * (2q + 4) FMAs each), A = Dn_GG - Dn_Gi Z
+    ((4q)^2 q FMAs) and the in-place complex Gauss-Jordan inverse of P ((4q)^3 complex FMAs,
+    four real FMAs each)."""
     q = N - 1
     ni, nb = q * q, 4 * q
-    chol = sum((ni - k - 1) * (ni - k) // 2 for k in range(ni))
-    fwd = sum((ni - k - 1) * nb for k in range(ni - 1))
-    bwd = sum(k * nb for k in range(1, ni))
-    a = nb * nb * q
-    gj_cma = sum((nb - 1) * (2 * nb - k - 1) for k in range(nb))
-    return 2.0 * (chol + fwd + bwd + a) + 8.0 * gj_cma
+    fp64 = 2.0 * (residuals * ni * nb * (2 * q + 4) + nb * nb * q + 4 * nb ** 3)
+    fp32 = 2.0 * (ni ** 3 / 6.0 + (residuals + 1) * ni * ni * nb)
+    return fp64, fp32
 
 
 def leaf_flops_paper(N: int) -> float:
@@ -224,7 +227,8 @@ def run_gpu(args, rank, world, local_rank, dist):
                 "iterations": max(i["outer_iterations"] for i in inf64),
                 "max_rel_residual": max(i["max_rel_residual"] for i in inf64)}
     s.close()
-    return dict(prob=prob, ms=ms, wall_ms=wall_ms, value=value, its=its, res=res, conv=conv, prof=prof,
+    return dict(outer=args.outer if args.outer != "default" else ("df64" if prec == H.HPS_MIXED else "fp64"),
+                prob=prob, ms=ms, wall_ms=wall_ms, value=value, its=its, res=res, conv=conv, prof=prof,
                 launches=launches, clk=clk, e2e_ms=e2e_ms, e2e_wall=e2e_wall, h2d=h2d, d2h=d2h,
                 warm_ms=warm_ms, fp64=fp64)
 
@@ -451,14 +455,23 @@ def main():
     cand = []
     if leaf_calls:
         per = leaf_ms / leaf_calls
-        fl = leaf_flops(N) * E
-        cand.append((leaf_ms, {"kernel": "leaf_kernel (leaf ItI maps, FP64)", "bound": "alu",
-                               "achieved": fl / (per / 1e3) / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                               "unit": "TFLOP/s", "frac": fl / (per / 1e3) / FP64_PEAK_NOMINAL,
+        f64, f32 = leaf_flops(N)
+        f64 *= E
+        f32 *= E
+        lit = leaf_flops_paper(N) * E
+        cand.append((leaf_ms, {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, FP64 refinement and inverse)",
+                               "bound": "alu", "achieved": f64 / (per / 1e3) / 1e12,
+                               "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
+                               "frac": f64 / (per / 1e3) / FP64_PEAK_NOMINAL,
                                "traffic": LEAF_TRAFFIC_BYTES if prob.nx == 64 and N == 16 else None,
-                               "flops_per_launch": fl, "ms_per_launch": per,
-                               "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)"}))
-    if mv_calls:
+                               "flops_per_launch": f64, "ms_per_launch": per,
+                               "fp32_flops_per_launch": f32,
+                               "fp32_frac": f32 / (per / 1e3) / FP32_PEAK_NOMINAL,
+                               "paper_literal_flops_per_launch": lit,
+                               "paper_literal_rate_tflops": lit / (per / 1e3) / 1e12,
+                               "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s), the pipe the FP64 part binds; "
+                                              "FP32 nominal 80.5 TFLOP/s for fp32_frac"}))
+    if mv_calls and r.get("outer") == "fp64":
         per = mv_ms / mv_calls
         fl = matvec_flops(E, N, nrhs)
         cand.append((mv_ms, {"kernel": "es_matvec_kernel (skeleton matvec, FP64)", "bound": "alu",

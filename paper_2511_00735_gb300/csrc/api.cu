@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "ctx.h"
@@ -142,6 +143,19 @@ void free_solver(hps_ctx* c) {
   c->fg_restart = c->fg_nrhs = c->pv_nrhs = 0;
 }
 
+// The captured V-cycle graph, its stream and events; the handles are reset, so a later
+// solve captures again.
+void free_graph(hps_ctx* c) {
+  if (c->mg_exec) cudaGraphExecDestroy(c->mg_exec);
+  if (c->gs) cudaStreamDestroy(c->gs);
+  if (c->gs_in) cudaEventDestroy(c->gs_in);
+  if (c->gs_out) cudaEventDestroy(c->gs_out);
+  c->mg_exec = nullptr;
+  c->gs = nullptr;
+  c->gs_in = c->gs_out = nullptr;
+  c->mg_gen = -1;
+}
+
 void free_tree(hps_ctx* c) {
   for (auto& s : c->stages) {
     FREE(s.d_es); FREE(s.T); FREE(s.vec);
@@ -166,6 +180,7 @@ void free_tree(hps_ctx* c) {
   c->nrhs_cap = 0;
   c->cg_k = c->cg_nrhs = c->ex_nrhs = 0;
   c->have_tree = false;
+  ++c->vc_gen;
 }
 
 // ---------------------------------------------------------------------------
@@ -261,6 +276,25 @@ using namespace hps;
     if (e0_ != cudaSuccess) return cuda_fail(c, e0_, "cudaSetDevice"); \
   } while (0)
 
+namespace hps {
+void optin_all_once() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  optin_leaf();
+  optin_blas();
+  optin_df64();
+  optin_skel();
+  done[dev] = true;
+}
+}  // namespace hps
+
 extern "C" {
 
 const char* hps_strerror(int s) {
@@ -294,6 +328,7 @@ int hps_create(hps_ctx** out, int device, void* stream) {
     cudaGetLastError();
     return HPS_ENODEV;
   }
+  optin_all_once();
   hps_ctx* c = new hps_ctx();
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
@@ -313,7 +348,9 @@ int hps_destroy(hps_ctx* c) {
   cudaStreamSynchronize(c->stream);
   free_tree(c);
   free_solver(c);
+  free_graph(c);
   while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
+  c->mg_ptr = nullptr;  // freed with every other allocation
   cudaFree(c->d_flag);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
@@ -342,7 +379,9 @@ int hps_mesh(hps_ctx* c, int nx, int ny, int N) {
   cudaStreamSynchronize(c->stream);
   free_tree(c);
   free_solver(c);
+  free_graph(c);
   while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
+  c->mg_ptr = nullptr;  // freed with every other allocation
   c->d_es_nb = c->d_es_in = c->d_es_out = c->d_es_bdry = c->d_bdry_rows = nullptr;
   c->d_Dref = c->d_Kref = c->d_wref = nullptr;
   c->d_c = nullptr;
@@ -747,6 +786,7 @@ int hps_release_workspace(hps_ctx* c) {
   FREE(c->ex_r); FREE(c->ex_e);
   c->nrhs_cap = 0;
   c->cg_k = c->cg_nrhs = c->ex_nrhs = 0;
+  ++c->vc_gen;
   return HPS_OK;
 }
 

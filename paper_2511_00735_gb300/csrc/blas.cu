@@ -328,10 +328,6 @@ __global__ void __launch_bounds__(NT) gj_update_kernel(c_t<R>* W, int m, int ld,
   gemm_tile<R, BM, BN, BK, TM, TN>(a, d, blockIdx.y, blockIdx.x);
 }
 
-template <typename K>
-void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) smem_optin(kernel);
-}
 
 
 // ---------------------------------------------------------------------------
@@ -489,7 +485,6 @@ template <typename R, int RPT>
 cudaError_t launch_rowgemm(const GemmArgs<R>& a, int mmax, int nmax, int kmax, cudaStream_t s) {
   constexpr int BM = RG_NT * RPT;
   constexpr size_t smem = rowgemm_smem<R, RPT>();
-  if (smem > 48 * 1024) smem_optin(rowgemm_kernel<R, RPT>);
   const int gx = (mmax + BM - 1) / BM, gy = (nmax + RG_NC - 1) / RG_NC;
   const long long blocks = (long long)gx * gy * a.nbatch;
   // resident blocks per SM from the shared-memory footprint; split K until the GPU is covered
@@ -553,7 +548,6 @@ cudaError_t gj_solve(c_t<R>* W, int m, int ld, int nmat, int* piv_ws, c_t<R>* lu
   if (m <= 0 || nmat <= 0 || ld <= m) return cudaSuccess;
   const size_t small_bytes = (size_t)m * ld * sizeof(C);
   if (small_bytes <= 160 * 1024) {
-    set_smem(gj_small_kernel<R>, small_bytes);
     for (int b0 = 0; b0 < nmat; b0 += 65535) {
       const int nb = nmat - b0 < 65535 ? nmat - b0 : 65535;
       gj_small_kernel<R><<<nb, NT, small_bytes, s>>>(W + (long long)b0 * m * ld, m, ld, flag);
@@ -567,7 +561,6 @@ cudaError_t gj_solve(c_t<R>* W, int m, int ld, int nmat, int* piv_ws, c_t<R>* lu
   while (nbw > 1 && (size_t)m * nbw * sizeof(C) > 200 * 1024) --nbw;
   const size_t panel_bytes = (size_t)m * nbw * sizeof(C);
   if (panel_bytes > 200 * 1024) return cudaErrorInvalidValue;
-  set_smem(gj_panel_kernel<R>, panel_bytes);
   for (int k0 = 0; k0 < m; k0 += nbw) {
     const int kb = m - k0 < nbw ? m - k0 : nbw;
     gj_panel_kernel<R><<<nmat, NT, panel_bytes, s>>>(W, m, ld, k0, kb, piv_ws, lu_ws, flag);
@@ -589,6 +582,16 @@ cudaError_t gj_solve(c_t<R>* W, int m, int ld, int nmat, int* piv_ws, c_t<R>* lu
 template <typename R>
 cudaError_t gj_invert(c_t<R>* W, int m, int nmat, int* piv_ws, c_t<R>* lu_ws, int* flag, cudaStream_t s) {
   return gj_solve<R>(W, m, 2 * m, nmat, piv_ws, lu_ws, flag, s);
+}
+
+void optin_blas() {
+  smem_optin(rowgemm_kernel<float, 1>);
+  smem_optin(rowgemm_kernel<float, 2>);
+  smem_optin(rowgemm_kernel<double, 1>);
+  smem_optin(gj_small_kernel<float>);
+  smem_optin(gj_small_kernel<double>);
+  smem_optin(gj_panel_kernel<float>);
+  smem_optin(gj_panel_kernel<double>);
 }
 
 template cudaError_t launch_gemm<double>(const GemmArgs<double>&, int, int, cudaStream_t, int);

@@ -23,6 +23,15 @@ inline void smem_optin(K kernel) {
   cudaGetLastError();
 }
 
+// Raise the dynamic shared-memory limit of every kernel that needs more than 48 KB, once
+// per device (called by hps_create and hps_leaf_maps_noalloc with the device current), so
+// that no launch path calls cudaFuncSetAttribute while other host threads launch or capture.
+void optin_all_once();
+void optin_leaf();
+void optin_blas();
+void optin_df64();
+void optin_skel();
+
 template <typename R> struct cplx;
 template <> struct cplx<double> { using T = double2; };
 template <> struct cplx<float> { using T = float2; };

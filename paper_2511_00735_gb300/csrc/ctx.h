@@ -125,6 +125,16 @@ struct hps_ctx {
   // exact coarse scratch
   void *ex_r = nullptr, *ex_e = nullptr;
   int ex_nrhs = 0;
+  // the mixed path's V-cycle as a CUDA graph (captured once per nrhs, coarse steps and buffer
+  // generation); the graph reads its input and output pointers from mg_ptr
+  long long vc_gen = 0;            // bumped whenever a V-cycle buffer is (re)allocated or freed
+  cudaGraphExec_t mg_exec = nullptr;
+  int mg_nrhs = 0, mg_k = 0;
+  long long mg_gen = -1, mg_count = 0;  // buffer generation and kernel count of the captured graph
+  bool mg_nograph = false;         // capture failed once: launch directly
+  cudaStream_t gs = nullptr;       // capture / replay stream of the graph
+  cudaEvent_t gs_in = nullptr, gs_out = nullptr;
+  void** mg_ptr = nullptr;         // device [2]: rho (float4*), z (float2*)
 
   // FP64 solver workspaces
   int fg_restart = 0, fg_nrhs = 0;
@@ -161,6 +171,7 @@ void dev_free(hps_ctx* c, void* p);
 template <typename T> T* dev_upload(hps_ctx* c, const std::vector<T>& v);
 void free_tree(hps_ctx* c);
 void free_solver(hps_ctx* c);
+void free_graph(hps_ctx* c);
 int ensure_sweep_buffers(hps_ctx* c, int nrhs);
 
 // tree operations (merge.cu)

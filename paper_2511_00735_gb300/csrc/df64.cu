@@ -135,6 +135,55 @@ cudaError_t df_gather_hi(float2* dst, const float4* src, const int* map, long lo
   return cudaGetLastError();
 }
 
+// the same with the source pointer read from device memory (graph-replayable with a new source)
+__global__ void df_gather_hi_ind_kernel(float2* __restrict__ dst, const float4* const* __restrict__ srcp,
+                                        const int* __restrict__ map, long long rows, int nrhs) {
+  const float4* src = *srcp;
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map[row];
+    const float4 v = m >= 0 ? src[(long long)m * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    dst[l] = make_float2(v.x, v.y);
+  }
+}
+cudaError_t df_gather_hi_ind(float2* dst, const float4* const* srcp, const int* map, long long rows, int nrhs,
+                             cudaStream_t s) {
+  df_gather_hi_ind_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(dst, srcp, map, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void set_pointers_kernel(void** dst, const void* a, void* b) {
+  dst[0] = const_cast<void*>(a);
+  dst[1] = b;
+}
+cudaError_t set_pointers(void** dst, const void* a, void* b, cudaStream_t s) {
+  set_pointers_kernel<<<1, 1, 0, s>>>(dst, a, b);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// dst[map[row]][r] = src[row][r] (map < 0: skipped) with dst read from device memory
+__global__ void scatter_f2_ind_kernel(float2* const* __restrict__ dstp, const float2* __restrict__ src,
+                                      const int* __restrict__ map, long long rows, int nrhs) {
+  float2* dst = *dstp;
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const long long row = l / nrhs;
+    const int r = (int)(l % nrhs);
+    const int m = map[row];
+    if (m >= 0) dst[(long long)m * nrhs + r] = src[l];
+  }
+}
+cudaError_t scatter_f2_ind(float2* const* dstp, const float2* src, const int* map, long long rows, int nrhs,
+                           cudaStream_t s) {
+  scatter_f2_ind_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(dstp, src, map, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Outer matvec  y_p = x_{nb(p)} + sum_b T_e[a][b] x_{e,b}  (nb(p) >= 0), else 0;
 // residual form y = c0 - that when c0 != null.  T in df64, x FP32 or df64.
@@ -176,7 +225,6 @@ template <typename X>
 cudaError_t df_matvec(const float4* T, const int* nbr, const X* x, const float4* c0, float4* y, int E, int nb, int nrhs,
                       int grid, cudaStream_t s) {
   const size_t smem = sizeof(float4) * (size_t)nb * nrhs;
-  if (smem > 48 * 1024) smem_optin(df_matvec_kernel<X>);
   df_matvec_kernel<X><<<grid, NT, smem, s>>>(T, nbr, x, c0, y, E, nb, nrhs);
   note_launch();
   return cudaGetLastError();
@@ -285,7 +333,6 @@ cudaError_t df_bupdate(float4* w, const VT* V, long long vstride, int nvec, cons
                        float sign, cudaStream_t s) {
   if (nvec <= 0) return cudaSuccess;
   const size_t smem = sizeof(float4) * (size_t)nvec * nrhs;
-  if (smem > 48 * 1024) smem_optin(df_bupdate_kernel<VT>);
   df_bupdate_kernel<VT><<<nblocks(rows * nrhs, 4096), NT, smem, s>>>(w, V, vstride, nvec, h, rows, nrhs, sign);
   note_launch();
   return cudaGetLastError();
@@ -338,6 +385,13 @@ cudaError_t df_swap_hi(float2* z, const float4* v, const int* nbr, long long row
   df_swap_hi_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(z, v, nbr, rows, nrhs);
   note_launch();
   return cudaGetLastError();
+}
+
+void optin_df64() {
+  smem_optin(df_matvec_kernel<float2>);
+  smem_optin(df_matvec_kernel<float4>);
+  smem_optin(df_bupdate_kernel<float4>);
+  smem_optin(df_bupdate_kernel<float2>);
 }
 
 }  // namespace hps

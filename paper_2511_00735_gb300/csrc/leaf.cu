@@ -787,6 +787,11 @@ size_t leaf_smem_bytes(int N, int cw) {
   return sizeof(double) * ((r1 > r2 ? r1 : r2) + 3 * n1 * n1 + n1);
 }
 
+void optin_leaf() {
+  smem_optin(leaf_ir_kernel);
+  smem_optin(leaf_kernel);
+}
+
 size_t leaf_ir_smem_bytes(int N) {
   const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
   const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
@@ -794,13 +799,8 @@ size_t leaf_ir_smem_bytes(int N) {
 }
 
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
-  if (p.Zscr) {
-    smem_optin(leaf_ir_kernel);
-    leaf_ir_kernel<<<grid, IR_NT, leaf_ir_smem_bytes(p.N), s>>>(p);
-  } else {
-    smem_optin(leaf_kernel);
-    leaf_kernel<<<grid, 256, leaf_smem_bytes(p.N, p.cw), s>>>(p);
-  }
+  if (p.Zscr) leaf_ir_kernel<<<grid, IR_NT, leaf_ir_smem_bytes(p.N), s>>>(p);
+  else leaf_kernel<<<grid, 256, leaf_smem_bytes(p.N, p.cw), s>>>(p);
   note_launch();
   return cudaGetLastError();
 }

@@ -28,6 +28,7 @@
 // GMRES steps from zero (or by a dense inverse).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -474,6 +475,7 @@ int ensure_sweep_buffers(hps_ctx* c, int nrhs) {
   c->sw_x = dev_alloc(c, cs * p2m * nrhs);
   if (!c->sw_x) return fail(c, HPS_ENOMEM, "sweep temporaries");
   c->nrhs_cap = nrhs;
+  ++c->vc_gen;
   return HPS_OK;
 }
 
@@ -510,7 +512,23 @@ int ensure_cg(hps_ctx* c, int k, int nrhs) {
   for (void** b : bufs)
     if (!*b) return fail(c, HPS_ENOMEM, "coarse GMRES workspace");
   c->cg_k = k;
+  ++c->vc_gen;
   c->cg_nrhs = nrhs;
+  return HPS_OK;
+}
+
+template <typename R>
+int ensure_ex(hps_ctx* c, int nrhs) {
+  using C = c_t<R>;
+  if (nrhs <= c->ex_nrhs) return HPS_OK;
+  const Coarse& cc = c->coarse;
+  dev_free(c, c->ex_r);
+  dev_free(c, c->ex_e);
+  c->ex_r = dev_alloc(c, sizeof(C) * (size_t)std::max(cc.n_int, 1) * nrhs);
+  c->ex_e = dev_alloc(c, sizeof(C) * (size_t)std::max(cc.n_int, 1) * nrhs);
+  ++c->vc_gen;
+  if (!c->ex_r || !c->ex_e) return fail(c, HPS_ENOMEM, "exact coarse scratch");
+  c->ex_nrhs = nrhs;
   return HPS_OK;
 }
 
@@ -527,14 +545,8 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
     return HPS_OK;
   }
   if (cc.exact) {
-    if (nrhs > c->ex_nrhs) {
-      dev_free(c, c->ex_r);
-      dev_free(c, c->ex_e);
-      c->ex_r = dev_alloc(c, sizeof(C) * (size_t)cc.n_int * nrhs);
-      c->ex_e = dev_alloc(c, sizeof(C) * (size_t)cc.n_int * nrhs);
-      if (!c->ex_r || !c->ex_e) return fail(c, HPS_ENOMEM, "exact coarse scratch");
-      c->ex_nrhs = nrhs;
-    }
+    int rc0 = ensure_ex<R>(c, nrhs);
+    if (rc0 != HPS_OK) return rc0;
     HPS_CK(c, (gather_rows<R, R>(static_cast<C*>(c->ex_r), Vc, cc.d_ucnb, cc.n_int, nrhs, st)));
     HPS_CK(c, gemm<R>(c, cc.d_desc, 1, cc.Winv, 2LL * cc.n_int, c->ex_r, nrhs, nullptr, 0, c->ex_e, nrhs, 1.0, nullptr,
                       cc.n_int, nrhs, nrhs));
@@ -633,13 +645,80 @@ int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int k)
   int rc = ensure_sweep_buffers(c, nrhs);
   if (rc != HPS_OK) return rc;
   if (c->precision != HPS_MIXED) return fail(c, HPS_EINVAL, "internal: df64 outer needs the FP32 tree");
+  // every buffer the V-cycle touches exists before a capture
+  if (c->coarse.exact) rc = ensure_ex<float>(c, nrhs);
+  else if (c->coarse.n_int > 0 && k > 0) rc = ensure_cg<float>(c, k, nrhs);
+  if (rc != HPS_OK) return rc;
   cudaStream_t st = c->stream;
+  if (!c->mg_ptr) {
+    c->mg_ptr = static_cast<void**>(dev_alloc(c, 2 * sizeof(void*)));
+    if (!c->mg_ptr) return fail(c, HPS_ENOMEM, "V-cycle pointer block");
+  }
+  // this call's vectors go to the device by kernel arguments, stream-ordered before the graph
+  HPS_CK(c, set_pointers(c->mg_ptr, rho_es, z_es, st));
   const Stage& S0 = c->stages[0];
   const long long rows = (long long)S0.nsub * S0.n;
-  HPS_CK(c, df_gather_hi(static_cast<float2*>(S0.vec), rho_es, S0.d_es, rows, nrhs, st));
-  rc = mg_core<float>(c, nrhs, k);
-  if (rc != HPS_OK) return rc;
-  HPS_CK(c, (scatter_rows<float, float>(z_es, static_cast<const float2*>(S0.vec), S0.d_es, rows, nrhs, st)));
+  auto body = [&]() -> int {  // launches on c->stream (the capture stream while capturing)
+    HPS_CK(c, df_gather_hi_ind(static_cast<float2*>(S0.vec), reinterpret_cast<const float4* const*>(c->mg_ptr),
+                               S0.d_es, rows, nrhs, c->stream));
+    int r2 = mg_core<float>(c, nrhs, k);
+    if (r2 != HPS_OK) return r2;
+    HPS_CK(c, scatter_f2_ind(reinterpret_cast<float2* const*>(c->mg_ptr) + 1, static_cast<const float2*>(S0.vec),
+                             S0.d_es, rows, nrhs, c->stream));
+    return HPS_OK;
+  };
+  if (c->mg_nograph) return body();
+  // the graph runs on the context's own capture stream, ordered after and before the caller's
+  // stream by events (the caller's stream may be the legacy default stream, which cannot capture)
+  if (!c->gs) {
+    if (cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gs_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->gs_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      c->mg_nograph = true;
+      return body();
+    }
+  }
+  HPS_CK(c, cudaEventRecord(c->gs_in, st));
+  HPS_CK(c, cudaStreamWaitEvent(c->gs, c->gs_in, 0));
+  if (!(c->mg_exec && c->mg_nrhs == nrhs && c->mg_k == k && c->mg_gen == c->vc_gen)) {
+    if (c->mg_exec) cudaGraphExecDestroy(c->mg_exec);
+    c->mg_exec = nullptr;
+    // one capture at a time in the process (contexts of several host threads)
+    static std::mutex capture_mu;
+    std::lock_guard<std::mutex> lk(capture_mu);
+    const long long l0 = hps_kernel_launches();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      c->mg_nograph = true;
+      return body();
+    }
+    c->stream = c->gs;  // every launch of the V-cycle goes to the capture stream
+    const int rb = body();
+    c->stream = st;
+    const cudaError_t ec = cudaStreamEndCapture(c->gs, &graph);
+    const long long captured = hps_kernel_launches() - l0;
+    note_launch(-(int)captured);  // recorded into the graph, not run: counted per replay
+    cudaError_t ei = cudaErrorUnknown;
+    if (rb == HPS_OK && ec == cudaSuccess && graph) ei = cudaGraphInstantiate(&c->mg_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      // no graph on this context from now on: the same launches run directly
+      cudaGetLastError();
+      c->mg_exec = nullptr;
+      c->mg_nograph = true;
+      return body();
+    }
+    c->mg_nrhs = nrhs;
+    c->mg_k = k;
+    c->mg_gen = c->vc_gen;
+    c->mg_count = captured;
+  }
+  HPS_CK(c, cudaGraphLaunch(c->mg_exec, c->gs));
+  HPS_CK(c, cudaEventRecord(c->gs_out, c->gs));
+  HPS_CK(c, cudaStreamWaitEvent(st, c->gs_out, 0));
+  note_launch((int)c->mg_count);
   return HPS_OK;
 }
 

@@ -110,6 +110,7 @@ extern "C" int hps_leaf_maps_noalloc(int device, void* stream, int N, double h, 
     cudaGetLastError();
     return HPS_ECUDA;
   }
+  optin_all_once();
   double* base = nullptr;
   int rc = scratch_on(device, &base);
   if (rc != HPS_OK) return rc;

@@ -62,11 +62,12 @@ __global__ void __launch_bounds__(NT) es_matvec_kernel(const double2* __restrict
 cudaError_t es_matvec(const double2* T, const int* nbr, const double2* x, const double2* c0, double2* y, int E,
                       int nb, int nrhs, int grid, cudaStream_t s) {
   const size_t smem = sizeof(double2) * (size_t)nb * nrhs;
-  if (smem > 48 * 1024) smem_optin(es_matvec_kernel);
   es_matvec_kernel<<<grid, NT, smem, s>>>(T, nbr, x, c0, y, E, nb, nrhs);
   note_launch();
   return cudaGetLastError();
 }
+
+void optin_skel() { smem_optin(es_matvec_kernel); }
 
 // ---------------------------------------------------------------------------
 // RHS in outgoing coordinates: rho_p = -sum_{b on the boundary} T_e[a][b] t_{bdry(e,b)}
