@@ -291,6 +291,7 @@ void optin_all_once() {
   optin_blas();
   optin_df64();
   optin_skel();
+  optin_tc();
   done[dev] = true;
 }
 }  // namespace hps
@@ -333,11 +334,15 @@ int hps_create(hps_ctx** out, int device, void* stream) {
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_gemm_err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->d_flag);
+  cudaFree(c->d_gemm_err);
     delete c;
     return HPS_ENOMEM;
   }
   cudaMemset(c->d_flag, 0, sizeof(int));
+  cudaMemset(c->d_gemm_err, 0, sizeof(int));
   *out = c;
   return HPS_OK;
 }

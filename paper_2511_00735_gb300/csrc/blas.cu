@@ -524,6 +524,11 @@ cudaError_t launch_rowgemm(const GemmArgs<R>& a, int mmax, int nmax, int kmax, c
 template <typename R>
 cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
+  // large FP32 products (the merges of the upper levels): tensor cores, 3xTF32
+  if constexpr (sizeof(R) == 4) {
+    if (a.err && mmax >= 64 && nmax >= 64 && kmax >= 64 && a.nbatch <= 65535)
+      return launch_tc_gemm(a, mmax, nmax, a.err, s);
+  }
   // block-vector products (the sweeps' and the coarse solve's right-hand sides)
   if (nmax <= 16 && kmax > 0 && mmax > 32) {
     if (sizeof(R) == 4 && mmax > RG_NT) return launch_rowgemm<R, 2>(a, mmax, nmax, kmax, s);

@@ -129,7 +129,13 @@ template <typename R> struct GemmArgs {
   c_t<R>* ws = nullptr;
   long long ws_elems = 0;
   int num_sms = 148;
+  int* err = nullptr;    // device flag for the tensor-core path's bounded waits; null: SIMT only
 };
+
+// FP32 complex GEMM on the tensor cores (tc.cu): batched like launch_gemm, for tiles of
+// 128 rows x 64 complex columns; *err is set when a bounded wait gives up.
+cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int* err, cudaStream_t s);
+void optin_tc();
 
 // kmax > 0 enables splitting K across blocks when the grid would not fill the GPU.
 template <typename R>

@@ -98,6 +98,8 @@ struct hps_ctx {
   double2* d_T = nullptr;      // [E][nb][nb] FP64, side order l, r, b, t
   int n_robust = 0;            // elements built by the pivoted route
   int* d_flag = nullptr;
+  int* d_gemm_err = nullptr;   // set by a tensor-core GEMM whose bounded wait gave up
+  bool in_build = false;       // inside hps_merge_levels: FP32 GEMMs may take the tensor cores
 
   // tree
   bool have_tree = false;

@@ -148,7 +148,17 @@ int hps_merge_levels(hps_ctx* c, int L_exact, int exact_coarse) {
   CHECK_CTX(c);
   if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
   if (L_exact < 0 || L_exact > c->L) return fail(c, HPS_EINVAL, "0 <= L_exact <= L");
-  return build_tree(c, L_exact, exact_coarse);
+  int rc = build_tree(c, L_exact, exact_coarse);
+  if (rc != HPS_OK) return rc;
+  int gerr = 0;
+  HPS_CK(c, cudaMemcpyAsync(&gerr, c->d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HPS_CK(c, cudaStreamSynchronize(c->stream));
+  if (gerr) {
+    cudaMemsetAsync(c->d_gemm_err, 0, sizeof(int), c->stream);
+    free_tree(c);
+    return fail(c, HPS_ETIMEOUT, "a tensor-core GEMM of the merges timed out waiting for its MMAs");
+  }
+  return HPS_OK;
 }
 
 int hps_stage_T(hps_ctx* c, int stage, int sub, void* T_host) {

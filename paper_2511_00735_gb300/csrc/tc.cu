@@ -1,0 +1,267 @@
+// Batched complex FP32 GEMM on the fifth-generation tensor cores (tcgen05) for the
+// merge levels (section 4.1: S = I - T_bb T_aa, X1, X2, T_pair = D - C A^{-1} B and the
+// sweep operators are all batched complex GEMMs with scatter epilogues).
+//
+// Complex product as one real product.  With A stored interleaved (re, im) it already is
+// the real matrix [m][2k]; B (k x n complex) is expanded while it is staged into
+//     B'[2k][2n] = [[Re b, Im b], [-Im b, Re b]]   per complex entry,
+// so that A_real B' = C interleaved: C[i][2j] = sum_k Re a Re b - Im a Im b and
+// C[i][2j+1] = sum_k Re a Im b + Im a Re b.
+//
+// FP32 accuracy from TF32 inputs (3xTF32): every operand x is split x = hi + lo with
+// hi = tf32(x), lo = tf32(x - hi); the tile product accumulates hi*hi + hi*lo + lo*hi in
+// FP32 in tensor memory (the dropped lo*lo term is below 2^-22 relative).
+//
+// One CTA (128 threads) computes a 128-row x 64-complex-column tile: all threads split one
+// k-chunk (8 complex) of A and B into shared memory in the canonical no-swizzle K-major
+// layout (8-row x 16-byte core matrices), one thread issues the 6 tcgen05.mma (M = 128,
+// N = 128 real, K = 8) of the chunk and commits them to the chunk's mbarrier; two stages,
+// and each thread fetches the next chunk's values into registers before the current one
+// is multiplied.  Three CTAs fit on an SM (97 KB of shared memory, 384 TMEM columns).
+// The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
+// i.e. output rows) and applies the same descriptor epilogue as the SIMT GEMM
+// (alpha, beta * C0 with a two-segment C0, row and column maps).  Every mbarrier wait is
+// bounded; a wait that gives up sets *err and the tile is left unwritten.
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace hps {
+namespace {
+
+constexpr int TC_NT = 128;
+constexpr int TC_M = 128;              // output rows per CTA = TMEM lanes
+constexpr int TC_NC = 64;              // complex output columns per CTA
+constexpr int TC_NR = 2 * TC_NC;       // real columns = MMA N
+constexpr int TC_KC = 8;               // complex k per chunk
+constexpr int TC_KR = 2 * TC_KC;       // real k per chunk = 2 MMA k-steps of 8
+constexpr int A_PER = TC_M * TC_KC / TC_NT;   // complex A values each thread stages per chunk
+constexpr int B_PER = TC_KC * TC_NC / TC_NT;  // complex B values each thread stages per chunk
+constexpr uint32_t LBO = 128;          // bytes between core matrices along k
+constexpr uint32_t SBO = (TC_KR / 4) * 128;  // bytes between 8-row groups
+constexpr int A_TILE = TC_M * TC_KR;   // floats in one A tile (8 KB)
+constexpr int B_TILE = TC_NR * TC_KR;  // floats in one B' tile (8 KB)
+constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;  // hi and lo of A and B': 32 KB
+constexpr long long WAIT_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (r, k) in a tile: core matrix (r/8, k/4), row r%8, column k%4
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+  return (uint32_t)(r >> 3) * SBO + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16 + (uint32_t)(k & 3) * 4;
+}
+
+// shared-memory matrix descriptor: start >> 4, leading (k) and stride (row group) byte
+// offsets >> 4, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, N, M
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_NR >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < WAIT_LIMIT && !done; ++it)
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+  asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
+                   tmem),
+               "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const GemmDesc d = a.desc[blockIdx.z];
+  const int n = d.n < 0 ? a.n_launch : d.n, m = d.m, kk = d.k;
+  const int row0 = blockIdx.y * TC_M, col0 = blockIdx.x * TC_NC;
+  if (row0 >= m || col0 >= n) return;  // uniform over the block, before any tensor-memory use
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "n"(TC_NR)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  const float2* Ab = a.A + (long long)d.a_r * a.lda + d.a_c;
+  const int nk = (kk + TC_KC - 1) / TC_KC;
+  // the next chunk's operands are fetched into registers one iteration ahead
+  float2 ra[A_PER], rb[B_PER];
+  auto fetch = [&](int kt) {
+    const int k0 = kt * TC_KC;
+#pragma unroll
+    for (int u = 0; u < A_PER; ++u) {
+      const int l = tid + u * TC_NT, r = l / TC_KC, kc = l % TC_KC;
+      const int gi = row0 + r, gk = k0 + kc;
+      ra[u] = (gi < m && gk < kk) ? Ab[(long long)gi * a.lda + gk] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < B_PER; ++u) {
+      const int l = tid + u * TC_NT, kc = l / TC_NC, nc = l % TC_NC;
+      const int gk = k0 + kc, gj = col0 + nc;
+      float2 v = make_float2(0.f, 0.f);
+      if (gk < kk && gj < n) {
+        const long long br = (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+        v = a.B[br * a.ldb + d.b_c + gj];
+      }
+      rb[u] = v;
+    }
+  };
+  bool ok = true;
+  if (nk > 0) fetch(0);
+  for (int kt = 0; kt < nk && ok; ++kt) {
+    const int s = kt & 1;
+    if (kt >= 2 && !mbar_wait(smem_u32(&mbar[s]), ((kt >> 1) - 1) & 1)) {
+      s_fail = 1;  // every thread sees the same timeout: the loop ends uniformly below
+    }
+    __syncthreads();
+    if (s_fail) {
+      ok = false;
+      break;
+    }
+    float* Ah = base + s * STAGE;
+    float* Al = Ah + A_TILE;
+    float* Bh = Al + A_TILE;
+    float* Bl = Bh + B_TILE;
+    // A: 128 rows x TC_KC complex, (re, im) -> real columns 2kc, 2kc+1 of the row
+#pragma unroll
+    for (int u = 0; u < A_PER; ++u) {
+      const int l = tid + u * TC_NT, r = l / TC_KC, kc = l % TC_KC;
+      uint2 h, lo;
+      split_tf32(ra[u].x, h.x, lo.x);
+      split_tf32(ra[u].y, h.y, lo.y);
+      const uint32_t off = core_off(r, 2 * kc) / 4;
+      *reinterpret_cast<uint2*>(Ah + off) = h;
+      *reinterpret_cast<uint2*>(Al + off) = lo;
+    }
+    // B': complex (kc, nc) -> real column 2nc gets (Re b, -Im b), column 2nc+1 gets (Im b, Re b)
+    // at real k = 2kc, 2kc+1
+#pragma unroll
+    for (int u = 0; u < B_PER; ++u) {
+      const int l = tid + u * TC_NT, kc = l / TC_NC, nc = l % TC_NC;
+      const float2 v = rb[u];
+      uint2 h0, l0, h1, l1;
+      split_tf32(v.x, h0.x, l0.x);
+      split_tf32(-v.y, h0.y, l0.y);
+      split_tf32(v.y, h1.x, l1.x);
+      h1.y = h0.x;
+      l1.y = l0.x;
+      const uint32_t o0 = core_off(2 * nc, 2 * kc) / 4, o1 = core_off(2 * nc + 1, 2 * kc) / 4;
+      *reinterpret_cast<uint2*>(Bh + o0) = h0;
+      *reinterpret_cast<uint2*>(Bl + o0) = l0;
+      *reinterpret_cast<uint2*>(Bh + o1) = h1;
+      *reinterpret_cast<uint2*>(Bl + o1) = l1;
+    }
+    if (kt + 1 < nk) fetch(kt + 1);  // in flight while this chunk is multiplied
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+#pragma unroll
+      for (int ks = 0; ks < TC_KR / 8; ++ks) {
+        const uint32_t step = ks * 2 * LBO;  // two core matrices = 8 real k
+        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bh + step), (kt > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bl + step), 1u);
+        mma_tf32(tmem, smem_desc(al + step), smem_desc(bh + step), 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[s]))
+                   : "memory");
+    }
+  }
+  if (ok && nk > 0 && !mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) s_fail = 1;
+  __syncthreads();
+  ok = ok && !s_fail;  // uniform over the block (tcgen05.ld is warp-collective)
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // let the MMAs already issued finish before the tensor memory is released
+    if (nk > 0) mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const int row = 32 * warp + lane, gi = row0 + row;
+  const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
+  const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
+  const long long orow = gi < m ? (long long)d.c_r + (rmap ? rmap[gi] : gi) : 0;
+  const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_NR; c0 += 16) {
+      uint32_t v[16];
+      if (nk > 0) {
+        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
+      }
+      if (gi < m) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int gj = col0 + c0 / 2 + j;
+          if (gj >= n) continue;
+          float2 o = cmul(a.alpha, make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+          if (a.C0) o = cadd(o, cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj]));
+          a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = o;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_NR) : "memory");
+}
+
+}  // namespace
+
+size_t tc_gemm_smem() { return (size_t)2 * STAGE * sizeof(float) + 1024; }
+
+cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int* err, cudaStream_t s) {
+  if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
+  if (a.nbatch > 65535) return cudaErrorInvalidValue;
+  dim3 grid((nmax + TC_NC - 1) / TC_NC, (mmax + TC_M - 1) / TC_M, a.nbatch);
+  tc_gemm_kernel<<<grid, TC_NT, tc_gemm_smem(), s>>>(a, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+void optin_tc() { smem_optin(tc_gemm_kernel); }
+
+}  // namespace hps

@@ -243,6 +243,24 @@ def test_outer_df64_needs_mixed_leaves(solver):
     assert info["max_rel_residual"] <= 1e-10
 
 
+def test_merges_mixed_tensor_cores(solver):
+    """Mixed-precision merge tree (FP32; the top merge of a 16x16, N=8 mesh runs its GEMMs on
+    the tensor cores, 3xTF32) against the FP64 tree and the oracle (section 4.1)."""
+    prob = inputs.single_bump(16, 8, 20.0, 1, seed=9)
+    L = 8
+    H.setup(solver, prob, H.HPS_FP64)
+    solver.merge_levels(L)
+    top = [(k, sub) for k in (L - 1, L) for sub in range(2 ** (L - k))]
+    ref = {ks: solver.stage_T(*ks) for ks in top}
+    H.setup(solver, prob, H.HPS_MIXED)
+    solver.merge_levels(L)
+    for ks in top:
+        assert rel(solver.stage_T(*ks), ref[ks]) < 2e-5, ks
+    op = OracleProblem(prob)
+    tree = MergeTree(op.mesh, op.Ts, None, L)
+    assert rel(solver.stage_T(L, 0), tree.stages[L][0].T) < 2e-5
+
+
 def test_bad_arguments(solver):
     with pytest.raises(H.HPSError):
         solver.mesh(6, 8)
