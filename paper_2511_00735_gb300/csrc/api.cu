@@ -156,19 +156,14 @@ void free_graph(hps_ctx* c) {
   c->mg_gen = -1;
 }
 
-void free_tree(hps_ctx* c) {
+void free_numeric(hps_ctx* c) {
   for (auto& s : c->stages) {
-    FREE(s.d_es); FREE(s.T); FREE(s.vec);
+    FREE(s.T); FREE(s.vec);
   }
   for (auto& l : c->levels) {
-    FREE(l.d_dst); FREE(l.d_up); FREE(l.W); FREE(l.U); FREE(l.Dm); FREE(l.d_xmap); FREE(l.d_mdesc);
-    FREE(l.d_sdesc);
+    FREE(l.W); FREE(l.U); FREE(l.Dm);
   }
-  c->stages.clear();
-  c->levels.clear();
-  FREE(c->coarse.d_cdesc); FREE(c->coarse.d_cnb); FREE(c->coarse.d_upos); FREE(c->coarse.d_ucnb);
   FREE(c->coarse.Winv); FREE(c->coarse.d_desc);
-  c->coarse = Coarse();
   FREE(c->gemm_ws); c->gemm_ws_elems = 0;
   FREE(c->ws_X1); FREE(c->ws_X2); FREE(c->d_piv); FREE(c->d_lu);
   FREE(c->sw_x); FREE(c->ws_G); FREE(c->d_eye);
@@ -181,6 +176,20 @@ void free_tree(hps_ctx* c) {
   c->cg_k = c->cg_nrhs = c->ex_nrhs = 0;
   c->have_tree = false;
   ++c->vc_gen;
+}
+
+void free_tree(hps_ctx* c) {
+  free_numeric(c);
+  for (auto& s : c->stages) FREE(s.d_es);
+  for (auto& l : c->levels) {
+    FREE(l.d_dst); FREE(l.d_up); FREE(l.d_xmap); FREE(l.d_mdesc); FREE(l.d_sdesc);
+  }
+  c->stages.clear();
+  c->levels.clear();
+  FREE(c->coarse.d_cdesc); FREE(c->coarse.d_cnb); FREE(c->coarse.d_upos); FREE(c->coarse.d_ucnb);
+  c->coarse = Coarse();
+  FREE(c->plan_map0);
+  c->plan_L = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -558,7 +567,7 @@ int hps_set_coeff(hps_ctx* c, double kappa, double eta, const double* b) {
     c->c_host[i] = kappa * kappa * (1.0 - bh[i]);
   }
   cudaStreamSynchronize(c->stream);
-  free_tree(c);
+  free_numeric(c);
   if (c->d_c) FREE(c->d_c);
   if (c->d_T) FREE(c->d_T);
   c->have_leaves = false;
@@ -585,7 +594,7 @@ int hps_build_leaves(hps_ctx* c, int precision) {
     (cm < bound ? good : bad).push_back(e);
   }
   cudaStreamSynchronize(c->stream);
-  free_tree(c);
+  free_numeric(c);
   if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
   if (!c->d_T) return fail(c, HPS_ENOMEM, "leaf maps");
   LeafParams p;
@@ -691,7 +700,7 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
   for (int i = 0; i < n; ++i) {
     hps_ctx* c = ctxs[i];
     cudaStreamSynchronize(c->stream);
-    free_tree(c);
+    free_numeric(c);
     if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
     if (!c->d_T) return fail(c0, HPS_ENOMEM, "leaf maps");
     const int n1 = c->N + 1;

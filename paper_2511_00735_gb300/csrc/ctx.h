@@ -54,6 +54,7 @@ struct Coarse {
   void* Winv = nullptr;      // exact coarse: [n_int][2 n_int] -> right half = M_c^{-1}
   GemmDesc* d_desc = nullptr;  // exact coarse: the one GEMM descriptor
   bool exact = false;
+  std::vector<int> upos_h, ucnb_h;  // host copies of d_upos, d_ucnb (exact coarse assembly)
 };
 
 struct Alloc {
@@ -101,9 +102,15 @@ struct hps_ctx {
   int* d_gemm_err = nullptr;   // set by a tensor-core GEMM whose bounded wait gave up
   bool in_build = false;       // inside hps_merge_levels: FP32 GEMMs may take the tensor cores
 
-  // tree
+  // tree.  The plan (stage orders, merge maps, GEMM descriptors, coarse maps: everything that
+  // depends on the mesh and L_exact only) survives new coefficients and leaves; the numeric
+  // part (maps T, inverses, sweep operators, workspaces) is rebuilt by every hps_merge_levels.
   bool have_tree = false;
   int L_exact = 0;
+  int plan_L = -1;                 // L_exact of the cached plan, -1: none
+  size_t plan_x_elems = 0;
+  int plan_max_pairs = 0;
+  int* plan_map0 = nullptr;        // stage-0 positions within each element's map
   std::vector<hps::Stage> stages;
   std::vector<hps::Level> levels;  // levels[l] for l = 1..L_exact (levels[0] unused)
   hps::Coarse coarse;
@@ -171,7 +178,8 @@ int cuda_fail(hps_ctx* c, cudaError_t e, const char* what);
 void* dev_alloc(hps_ctx* c, size_t bytes);
 void dev_free(hps_ctx* c, void* p);
 template <typename T> T* dev_upload(hps_ctx* c, const std::vector<T>& v);
-void free_tree(hps_ctx* c);
+void free_tree(hps_ctx* c);     // numeric part and plan
+void free_numeric(hps_ctx* c);  // numeric part only (the plan stays)
 void free_solver(hps_ctx* c);
 void free_graph(hps_ctx* c);
 int ensure_sweep_buffers(hps_ctx* c, int nrhs);

@@ -109,11 +109,14 @@ template <typename R>
 int build_tree_t(hps_ctx* c, int L_exact, int exact) {
   using C = c_t<R>;
   const int q = c->q;
+  const bool plan = c->plan_L != L_exact;  // build the mesh-dependent plan, or reuse the cached one
   c->L_exact = L_exact;
+  std::vector<std::vector<int>> inv;
+  std::vector<int> nat;
+  if (plan) {
   c->stages.assign(L_exact + 1, Stage());
   c->levels.assign(L_exact + 1, Level());
-  std::vector<std::vector<int>> inv(L_exact + 1);
-  std::vector<int> nat;
+  inv.assign(L_exact + 1, std::vector<int>());
   // ---- stage geometry and storage orders ----
   for (int k = 0; k <= L_exact; ++k) {
     Stage& S = c->stages[k];
@@ -215,6 +218,8 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     max_p2m = std::max(max_p2m, Lv.npairs * 2 * Lv.m);
     max_pairs = std::max(max_pairs, Lv.npairs);
   }
+  c->plan_x_elems = x_elems;
+  c->plan_max_pairs = max_pairs;
   // ---- descriptors ----
   for (int l = 1; l <= L_exact; ++l) {
     Level& Lv = c->levels[l];
@@ -265,12 +270,13 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     Lv.d_sdesc = dev_upload(c, sd);
     if (!Lv.d_mdesc || !Lv.d_sdesc) return fail(c, HPS_ENOMEM, "descriptors");
   }
+  }  // plan
   // ---- allocations ----
   for (int k = 0; k <= L_exact; ++k) {
     Stage& S = c->stages[k];
     S.T = dev_alloc(c, sizeof(C) * (size_t)S.nsub * S.n * S.n);
     if (!S.T) return fail(c, HPS_ENOMEM, "stage maps");
-    if (k == 0 || k == L_exact) {
+    if (plan && (k == 0 || k == L_exact)) {
       S.d_es = dev_upload(c, S.es);
       if (!S.d_es) return fail(c, HPS_ENOMEM, "stage index");
     }
@@ -283,6 +289,8 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     if (!Lv.W || !Lv.U || !Lv.Dm) return fail(c, HPS_ENOMEM, "interface inverses and sweep operators");
   }
   if (L_exact > 0) {
+    const size_t x_elems = c->plan_x_elems;
+    const int max_pairs = c->plan_max_pairs;
     c->ws_X1 = dev_alloc(c, sizeof(C) * x_elems);
     c->ws_X2 = dev_alloc(c, sizeof(C) * x_elems);
     c->d_piv = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)max_pairs * GJ_NB));
@@ -311,14 +319,14 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
   // ---- stage 0 maps from the FP64 leaf maps ----
   {
     const Stage& S0 = c->stages[0];
-    std::vector<int> map0((size_t)S0.nsub * S0.n);
-    for (int e = 0; e < S0.nsub; ++e)
-      for (int i = 0; i < S0.n; ++i) map0[(size_t)e * S0.n + i] = S0.es[(size_t)e * S0.n + i] - e * c->nb;
-    int* dmap = dev_upload(c, map0);
-    if (!dmap) return fail(c, HPS_ENOMEM, "stage-0 map");
-    HPS_CK(c, (permute_blocks<double, R>(static_cast<C*>(S0.T), c->d_T, dmap, S0.nsub, S0.n, c->stream)));
-    HPS_CK(c, cudaStreamSynchronize(c->stream));
-    dev_free(c, dmap);
+    if (plan) {
+      std::vector<int> map0((size_t)S0.nsub * S0.n);
+      for (int e = 0; e < S0.nsub; ++e)
+        for (int i = 0; i < S0.n; ++i) map0[(size_t)e * S0.n + i] = S0.es[(size_t)e * S0.n + i] - e * c->nb;
+      c->plan_map0 = dev_upload(c, map0);
+      if (!c->plan_map0) return fail(c, HPS_ENOMEM, "stage-0 map");
+    }
+    HPS_CK(c, (permute_blocks<double, R>(static_cast<C*>(S0.T), c->d_T, c->plan_map0, S0.nsub, S0.n, c->stream)));
   }
   // ---- merges ----
   HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
@@ -362,6 +370,7 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
   {
     const Stage& Sc = c->stages[L_exact];
     Coarse& cc = c->coarse;
+    if (plan) {
     std::vector<int> cnb((size_t)Sc.nsub * Sc.n, -1), upos, ucnb;
     std::vector<GemmDesc> cdesc(Sc.nsub);
     int max_int = 0;
@@ -395,7 +404,12 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     cc.d_upos = dev_upload(c, upos);
     cc.d_ucnb = dev_upload(c, ucnb);
     if (!cc.d_cdesc || !cc.d_cnb || !cc.d_upos || !cc.d_ucnb) return fail(c, HPS_ENOMEM, "coarse maps");
+    cc.upos_h = upos;
+    cc.ucnb_h = ucnb;
+    }  // plan
     cc.exact = exact != 0;
+    const std::vector<int>& upos = cc.upos_h;
+    const std::vector<int>& ucnb = cc.ucnb_h;
     if (cc.exact && cc.n_int > 0) {
       const int ni = cc.n_int;
       cc.Winv = dev_alloc(c, sizeof(C) * (size_t)ni * 2 * ni);
@@ -440,6 +454,7 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
   HPS_CK(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HPS_CK(c, cudaStreamSynchronize(c->stream));
   if (flag) return fail(c, HPS_ENUMERIC, "zero pivot in an interface or coarse inversion");
+  c->plan_L = L_exact;
   c->have_tree = true;
   return HPS_OK;
 }
@@ -447,7 +462,8 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
 }  // namespace
 
 int build_tree(hps_ctx* c, int L_exact, int exact_coarse) {
-  free_tree(c);
+  if (c->plan_L == L_exact) free_numeric(c);  // same mesh and depth: keep the plan
+  else free_tree(c);
   PhaseScope ps(c, HPS_PH_MERGE);
   c->in_build = true;
   int rc = c->precision == HPS_FP64 ? build_tree_t<double>(c, L_exact, exact_coarse)
