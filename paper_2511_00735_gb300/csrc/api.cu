@@ -135,11 +135,12 @@ void free_solver(hps_ctx* c) {
   FREE(c->fg_V); FREE(c->fg_Z); FREE(c->fg_x); FREE(c->fg_w); FREE(c->fg_rhs); FREE(c->fg_t);
   FREE(c->fg_h); FREE(c->fg_part); FREE(c->fg_y); FREE(c->fg_floor);
   FREE(c->pv_in); FREE(c->pv_out);
-  FREE(c->df_V); FREE(c->df_x); FREE(c->df_w); FREE(c->df_part); FREE(c->df_T); FREE(c->df_Z);
+  FREE(c->df_V); FREE(c->df_x); FREE(c->df_w); FREE(c->df_part); FREE(c->df_T); FREE(c->df_Z); FREE(c->df_coef);
   if (c->pin_h) cudaFreeHost(c->pin_h);
   if (c->pin_y) cudaFreeHost(c->pin_y);
   if (c->pin_floor) cudaFreeHost(c->pin_floor);
-  c->pin_h = nullptr; c->pin_y = nullptr; c->pin_floor = nullptr;
+  if (c->pin_coef) cudaFreeHost(c->pin_coef);
+  c->pin_h = nullptr; c->pin_y = nullptr; c->pin_floor = nullptr; c->pin_coef = nullptr;
   c->fg_restart = c->fg_nrhs = c->pv_nrhs = 0;
 }
 

@@ -158,6 +158,8 @@ struct hps_ctx {
   int outer_arith = HPS_OUTER_DEFAULT;
   bool fg_df = false;
   float4 *df_V = nullptr, *df_x = nullptr, *df_w = nullptr, *df_part = nullptr, *df_T = nullptr;
+  float4* df_coef = nullptr;       // Gram-Schmidt update coefficients [2 restart + 3][nrhs]
+  float4* pin_coef = nullptr;      // pinned host mirror of df_coef
   float2* df_Z = nullptr;
   double2 *pv_in = nullptr, *pv_out = nullptr;  // precond_apply/matvec ES staging
   int pv_nrhs = 0;

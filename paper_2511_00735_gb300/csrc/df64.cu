@@ -308,6 +308,138 @@ cudaError_t df_bdot(const float4* V, long long vstride, int nvec, const float4* 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Two-pass Gram-Schmidt step (one reduction, one update per Arnoldi step).
+//
+// df_dots2: D[2i] = sum conj(X_i) y0, D[2i+1] = sum conj(X_i) y1 (i < nvec, X_i = V + i*vstride)
+// and D[2 nvec] = sum conj(y1) y1, over rows, per right-hand side, FP64 result [2 nvec + 1][nrhs].
+// Groups of DG2 vectors per block (blockIdx.y); y0 and y1 are read once per group.
+constexpr int DG2 = 8, NT2 = 128;
+__global__ void __launch_bounds__(NT2, 3) df_dots2_partial_kernel(const float4* __restrict__ V, long long vstride,
+                                                               int nvec, const float4* __restrict__ y0,
+                                                               const float4* __restrict__ y1, long long rows,
+                                                               int nrhs, int rpad, float4* __restrict__ partial,
+                                                               long long chunk) {
+  __shared__ float4 red[2 * DG2 + 1][NT2];
+  const int r = threadIdx.x % rpad, lrow = threadIdx.x / rpad, rper = NT2 / rpad;
+  const int i0 = blockIdx.y * DG2, ng = min(DG2, nvec - i0);
+  const bool extra = blockIdx.y == 0;
+  const int nout = 2 * nvec + 1;
+  const long long lo = blockIdx.x * chunk, hi = lo + chunk < rows ? lo + chunk : rows;
+  cacc a0[DG2], a1[DG2], ee;
+  if (r < nrhs) {
+    // the next row's values are loaded while the current row is accumulated
+    float4 u0, u1, x[DG2], nu0, nu1, nx[DG2];
+    auto load = [&](long long row, float4& v0, float4& v1, float4 (&xv)[DG2]) {
+      const long long l = row * nrhs + r;
+      v0 = y0[l];
+      v1 = y1[l];
+#pragma unroll
+      for (int g = 0; g < DG2; ++g)
+        if (g < ng) xv[g] = V[(i0 + g) * vstride + l];
+    };
+    long long row = lo + lrow;
+    if (row < hi) load(row, u0, u1, x);
+    for (; row < hi; row += rper) {
+      const long long nrow = row + rper;
+      if (nrow < hi) load(nrow, nu0, nu1, nx);
+      if (extra) cdot2_conj(ee, u1, u1);
+#pragma unroll
+      for (int g = 0; g < DG2; ++g) {
+        if (g < ng) {
+          cdot2_conj(a0[g], x[g], u0);
+          cdot2_conj(a1[g], x[g], u1);
+        }
+      }
+      u0 = nu0;
+      u1 = nu1;
+#pragma unroll
+      for (int g = 0; g < DG2; ++g) x[g] = nx[g];
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < DG2; ++g) {
+    red[2 * g][threadIdx.x] = cfin(a0[g]);
+    red[2 * g + 1][threadIdx.x] = cfin(a1[g]);
+  }
+  red[2 * DG2][threadIdx.x] = cfin(ee);
+  __syncthreads();
+  for (int s2 = rper / 2; s2 > 0; s2 >>= 1) {
+    if (lrow < s2) {
+      for (int k = 0; k < 2 * DG2 + 1; ++k) {
+        if (k < 2 * DG2 && k / 2 >= ng) continue;
+        if (k == 2 * DG2 && !extra) continue;
+        cacc t;
+        cadd2(t, red[k][threadIdx.x]);
+        cadd2(t, red[k][threadIdx.x + s2 * rpad]);
+        red[k][threadIdx.x] = cfin(t);
+      }
+    }
+    __syncthreads();
+  }
+  if (lrow == 0 && r < nrhs) {
+    float4* P = partial + (long long)blockIdx.x * nout * nrhs;
+    for (int g = 0; g < ng; ++g) {
+      P[(2 * (i0 + g)) * nrhs + r] = red[2 * g][r];
+      P[(2 * (i0 + g) + 1) * nrhs + r] = red[2 * g + 1][r];
+    }
+    if (extra) P[(2 * nvec) * nrhs + r] = red[2 * DG2][r];
+  }
+}
+
+int df_dots2_blocks(long long rows) { return bdot_blocks(rows); }
+
+cudaError_t df_dots2(const float4* V, long long vstride, int nvec, const float4* y0, const float4* y1, long long rows,
+                     int nrhs, float4* partial, double2* out, cudaStream_t s) {
+  if (nrhs > NT2 / 2 || nvec <= 0) return cudaErrorInvalidValue;
+  int rpad = 1;
+  while (rpad < nrhs) rpad <<= 1;
+  const int nblk = df_dots2_blocks(rows);
+  const long long chunk = (rows + nblk - 1) / nblk;
+  df_dots2_partial_kernel<<<dim3(nblk, (nvec + DG2 - 1) / DG2), NT2, 0, s>>>(V, vstride, nvec, y0, y1, rows, nrhs,
+                                                                             rpad, partial, chunk);
+  note_launch();
+  const int nout = 2 * nvec + 1;
+  df_bdot_final_kernel<<<(nout * nrhs * 32 + NT - 1) / NT, NT, 0, s>>>(partial, nblk, nout, nrhs, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// df_update2: out_v = sv vt + sum_{i<nvec} ca_i V_i  and  out_w = sw w + svw vt + sum_{i<nvec} cb_i V_i,
+// coefficients df64 in global memory [2 nvec + 3][nrhs]: ca (nvec rows), cb (nvec rows), sv, sw, svw.
+// out_v may be vt itself (each element is read before it is written, by the same thread).
+__global__ void df_update2_kernel(const float4* __restrict__ V, long long vstride, int nvec, const float4* vt,
+                                  const float4* __restrict__ w, const float4* __restrict__ coef, float4* out_v,
+                                  float4* __restrict__ out_w, long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  const float4* ca = coef;
+  const float4* cb = coef + (long long)nvec * nrhs;
+  const float4* sc = coef + 2LL * nvec * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int r = (int)(l % nrhs);
+    const float4 x = vt[l], y = w[l];
+    cacc av, aw;
+    cdot2(av, __ldg(sc + r), x);
+    cdot2(aw, __ldg(sc + nrhs + r), y);
+    cdot2(aw, __ldg(sc + 2 * nrhs + r), x);
+    for (int i = 0; i < nvec; ++i) {
+      const float4 v = V[i * vstride + l];
+      cdot2(av, __ldg(ca + (long long)i * nrhs + r), v);
+      cdot2(aw, __ldg(cb + (long long)i * nrhs + r), v);
+    }
+    out_v[l] = cfin(av);
+    out_w[l] = cfin(aw);
+  }
+}
+
+cudaError_t df_update2(const float4* V, long long vstride, int nvec, const float4* vt, const float4* w,
+                       const float4* coef, float4* out_v, float4* out_w, long long rows, int nrhs, cudaStream_t s) {
+  df_update2_kernel<<<nblocks(rows * nrhs, 4096), NT, 0, s>>>(V, vstride, nvec, vt, w, coef, out_v, out_w, rows,
+                                                             nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // w += sign * sum_i V_i h_i   (V df64 or FP32, h FP64 converted to df64 once per block)
 template <typename VT>
 __global__ void df_bupdate_kernel(float4* __restrict__ w, const VT* __restrict__ V, long long vstride, int nvec,

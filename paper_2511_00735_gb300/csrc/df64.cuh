@@ -31,6 +31,16 @@ cudaError_t df_matvec(const float4* T, const int* nbr, const X* x, const float4*
 // bdot_blocks(rows) * nvec * nrhs df64 numbers
 cudaError_t df_bdot(const float4* V, long long vstride, int nvec, const float4* w, long long rows, int nrhs,
                     float4* partial, double2* out, cudaStream_t s);
+// one pass over V_0..V_{nvec-1}: out[2i] = sum conj(V_i) y0, out[2i+1] = sum conj(V_i) y1,
+// out[2 nvec] = sum conj(y1) y1; FP64 [2 nvec + 1][nrhs]; partial holds
+// df_dots2_blocks(rows) * (2 nvec + 1) * nrhs df64 numbers
+int df_dots2_blocks(long long rows);
+cudaError_t df_dots2(const float4* V, long long vstride, int nvec, const float4* y0, const float4* y1, long long rows,
+                     int nrhs, float4* partial, double2* out, cudaStream_t s);
+// one pass over V_0..V_{nvec-1}: out_v = sv vt + sum ca_i V_i, out_w = sw w + svw vt + sum cb_i V_i
+// (coef: df64 [2 nvec + 3][nrhs] = ca rows, cb rows, sv, sw, svw); out_v may equal vt
+cudaError_t df_update2(const float4* V, long long vstride, int nvec, const float4* vt, const float4* w,
+                       const float4* coef, float4* out_v, float4* out_w, long long rows, int nrhs, cudaStream_t s);
 // w += sign * sum_i V_i h_i
 template <typename VT>
 cudaError_t df_bupdate(float4* w, const VT* V, long long vstride, int nvec, const double2* h, long long rows, int nrhs,

@@ -56,7 +56,7 @@ void free_fg(hps_ctx* c) {
   void** bufs[] = {(void**)&c->fg_V, (void**)&c->fg_Z, (void**)&c->fg_x, (void**)&c->fg_w, (void**)&c->fg_rhs,
                    (void**)&c->fg_t, (void**)&c->fg_h, (void**)&c->fg_part, (void**)&c->fg_y, (void**)&c->fg_floor,
                    (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_part,
-                   (void**)&c->df_T};
+                   (void**)&c->df_T, (void**)&c->df_coef};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -64,8 +64,10 @@ void free_fg(hps_ctx* c) {
   if (c->pin_h) cudaFreeHost(c->pin_h);
   if (c->pin_y) cudaFreeHost(c->pin_y);
   if (c->pin_floor) cudaFreeHost(c->pin_floor);
+  if (c->pin_coef) cudaFreeHost(c->pin_coef);
   c->pin_h = c->pin_y = nullptr;
   c->pin_floor = nullptr;
+  c->pin_coef = nullptr;
   c->fg_restart = c->fg_nrhs = 0;
 }
 
@@ -92,9 +94,10 @@ int ensure_fg(hps_ctx* c, int restart, int nrhs, bool df) {
     c->df_Z = static_cast<float2*>(dev_alloc(c, sizeof(float2) * vs * restart));
     c->df_x = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
     c->df_w = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
-    c->df_part = static_cast<float4*>(dev_alloc(c, sizeof(float4) * nblk * (restart + 1) * nrhs));
+    c->df_part = static_cast<float4*>(dev_alloc(c, sizeof(float4) * nblk * (2 * (restart + 1) + 1) * nrhs));
     c->df_T = static_cast<float4*>(dev_alloc(c, sizeof(float4) * (size_t)c->E * c->nb * c->nb));
-    ok = ok && c->df_V && c->df_Z && c->df_x && c->df_w && c->df_part && c->df_T;
+    c->df_coef = static_cast<float4*>(dev_alloc(c, sizeof(float4) * (size_t)(2 * restart + 3) * nrhs));
+    ok = ok && c->df_V && c->df_Z && c->df_x && c->df_w && c->df_part && c->df_T && c->df_coef;
   } else {
     c->fg_V = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * (restart + 1)));
     c->fg_Z = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * restart));
@@ -108,7 +111,8 @@ int ensure_fg(hps_ctx* c, int restart, int nrhs, bool df) {
   }
   if (cudaMallocHost(&c->pin_h, sizeof(double2) * hsz) != cudaSuccess ||
       cudaMallocHost(&c->pin_y, sizeof(double2) * (size_t)restart * nrhs) != cudaSuccess ||
-      cudaMallocHost(&c->pin_floor, sizeof(double) * nrhs) != cudaSuccess) {
+      cudaMallocHost(&c->pin_floor, sizeof(double) * nrhs) != cudaSuccess ||
+      (df && cudaMallocHost(&c->pin_coef, sizeof(float4) * (size_t)(2 * restart + 3) * nrhs) != cudaSuccess)) {
     cudaGetLastError();
     free_fg(c);
     return fail(c, HPS_ENOMEM, "pinned host workspace");
@@ -312,6 +316,212 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   std::vector<int> steps(nrhs);
   std::vector<double> res(nrhs, 0.0);
   bool fresh = false;  // pin_h holds the residual norms of the current iterate
+  // Givens rotation of column col of right-hand side r (entries 0..col set, hn = H[col+1][col])
+  auto rotate = [&](int r, int col, double hn) {
+    cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+    double* csr = &cs[(size_t)r * restart];
+    cd* snr = &sn[(size_t)r * restart];
+    cd* gr = &g[(size_t)r * (restart + 1)];
+    for (int i = 0; i < col; ++i) {
+      const cd a = Hr[(size_t)i * restart + col], b = Hr[(size_t)(i + 1) * restart + col];
+      Hr[(size_t)i * restart + col] = csr[i] * a + snr[i] * b;
+      Hr[(size_t)(i + 1) * restart + col] = csr[i] * b - std::conj(snr[i]) * a;
+    }
+    const cd a = Hr[(size_t)col * restart + col];
+    const double aa = std::abs(a);
+    double cc;
+    cd ss;
+    if (hn == 0.0) { cc = 1.0; ss = 0.0; }
+    else if (aa == 0.0) { cc = 0.0; ss = 1.0; }
+    else {
+      const double nu = std::hypot(aa, hn);
+      cc = aa / nu;
+      ss = (a / aa) * (hn / nu);
+    }
+    csr[col] = cc;
+    snr[col] = ss;
+    Hr[(size_t)col * restart + col] = cc * a + ss * hn;
+    const cd gj = gr[col];
+    gr[col] = cc * gj;
+    gr[col + 1] = -std::conj(ss) * gj;
+  };
+  // host double -> double-float (re_hi, im_hi, re_lo, im_lo)
+  auto to_df = [](cd v) {
+    const float rh = (float)v.real(), ih = (float)v.imag();
+    return make_float4(rh, ih, (float)(v.real() - (double)rh), (float)(v.imag() - (double)ih));
+  };
+  if (df) {
+    // Two-pass Gram-Schmidt with the re-orthogonalisation lagged by one step.  Slot j of V
+    // holds the tentative vector vt_j (once orthogonalised, normalised by an estimate) until
+    // step j's reduction gives a = V_j^H vt_j, d = |vt_j|^2, b = V_j^H w_j, c = vt_j^H w_j,
+    // e = |w_j|^2 in one pass; then v_j = (vt_j - V_j a) / rho with rho^2 = d - |a|^2 closes
+    // column j-1 (H[:, j-1] += nu_{j-1} a, H[j][j-1] = nu_{j-1} rho), column j is
+    // [b ; (c - a^H b) / rho], and one update pass writes v_j and
+    // vt_{j+1} = (w_j - V_j b - h_jj v_j) / nu_j, nu_j^2 estimated as e - |b|^2 - |h_jj|^2.
+    // z_j is the preconditioned tentative vector (flexible GMRES allows any direction); the
+    // Arnoldi relation M Z = V H holds with the orthonormal final basis.
+    std::vector<cd> htent((size_t)(restart + 1) * nrhs);
+    std::vector<double> nu_prev(nrhs, 0.0), bet(nrhs, 0.0);
+    for (int outer = 0; outer < max_outer; ++outer) {
+      if (outer > 0) {
+        rc = residual();
+        if (rc) return rc;
+      }
+      fresh = true;
+      bool all = true;
+      std::vector<char> active(nrhs, 0);
+      for (int r = 0; r < nrhs; ++r) {
+        bet[r] = std::sqrt(std::max(0.0, c->pin_h[r].x));
+        res[r] = bnorm[r] > 0 ? bet[r] / bnorm[r] : 0.0;
+        done[r] = res[r] <= tol;
+        active[r] = !done[r];
+        all = all && done[r];
+        for (int i = 0; i <= restart; ++i) g[(size_t)r * (restart + 1) + i] = 0.0;
+        steps[r] = 0;
+        c->pin_floor[r] = active[r] ? 0.0 : DBL_MAX;
+      }
+      if (all) break;
+      fresh = false;
+      HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+      HPS_CK(c, df_from_d(c->df_w, outer > 0 ? c->pv_out : c->fg_rhs, vs, st));
+      HPS_CK(c, df_bscale(c->df_V, c->df_w, hbuf, c->fg_floor, n, nrhs, st));
+      bool any = true;
+      for (int j = 0; j < restart && any; ++j) {
+        float4* Vt = c->df_V + (size_t)j * vs;
+        float2* Zj = c->df_Z + (size_t)j * vs;
+        {
+          PhaseScope ps(c, HPS_PH_PRECOND);
+          if (inner_iters < 0) HPS_CK(c, df_swap_hi(Zj, Vt, c->d_es_nb, n, nrhs, st));
+          else if ((rc = mg_apply_df(c, Vt, Zj, nrhs, inner_iters)) != HPS_OK) return rc;
+        }
+        {
+          PhaseScope ps(c, HPS_PH_MATVEC);
+          HPS_CK(c, df_matvec<float2>(c->df_T, c->d_es_nb, Zj, nullptr, c->df_w, c->E, c->nb, nrhs, grid, st));
+        }
+        {
+          PhaseScope ps(c, HPS_PH_ORTHO);
+          HPS_CK(c, df_dots2(c->df_V, vs, j + 1, Vt, c->df_w, n, nrhs, c->df_part, hbuf, st));
+        }
+        HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * (size_t)(2 * (j + 1) + 1) * nrhs,
+                                  cudaMemcpyDeviceToHost, st));
+        HPS_CK(c, cudaStreamSynchronize(st));
+        any = false;
+        const int rows_coef = 2 * j + 3;
+        for (int r = 0; r < nrhs; ++r) {
+          auto D = [&](int k) { const double2 v = c->pin_h[(size_t)k * nrhs + r]; return cd(v.x, v.y); };
+          auto set_zero = [&]() {
+            for (int k = 0; k < rows_coef; ++k) c->pin_coef[(size_t)k * nrhs + r] = make_float4(0.f, 0.f, 0.f, 0.f);
+          };
+          if (!active[r]) {
+            set_zero();
+            continue;
+          }
+          cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+          cd* ht = &htent[(size_t)r * (restart + 1)];
+          double sa = 0.0;
+          for (int i = 0; i < j; ++i) sa += std::norm(D(2 * i));
+          const double rho = std::sqrt(std::max(0.0, D(2 * j).real() - sa));
+          if (j > 0) {  // close column j - 1
+            for (int i = 0; i < j; ++i) Hr[(size_t)i * restart + (j - 1)] = ht[i] + nu_prev[r] * D(2 * i);
+            const double hn = nu_prev[r] * rho;
+            rotate(r, j - 1, hn);
+            its[r] += 1;
+            steps[r] = j;
+            res[r] = bnorm[r] > 0 ? std::abs(g[(size_t)r * (restart + 1) + j]) / bnorm[r] : 0.0;
+            if (res[r] <= tol || hn <= 1e-300) {
+              active[r] = 0;
+              set_zero();
+              continue;
+            }
+          } else {
+            g[(size_t)r * (restart + 1)] = bet[r] * rho;  // r0 = beta vt_0 = beta rho v_0
+          }
+          if (!(rho > 0.0)) {
+            active[r] = 0;
+            set_zero();
+            continue;
+          }
+          cd ab = 0.0;
+          double sb = 0.0;
+          for (int i = 0; i < j; ++i) {
+            ab += std::conj(D(2 * i)) * D(2 * i + 1);
+            sb += std::norm(D(2 * i + 1));
+            ht[i] = D(2 * i + 1);
+          }
+          const cd hjj = (D(2 * j + 1) - ab) / rho;
+          ht[j] = hjj;
+          const cd gam = hjj / rho;
+          const double e = D(2 * (j + 1)).real();
+          const double q = e - sb - std::norm(hjj);
+          const double nu = std::sqrt(std::max(q, 1e-28 * e));
+          if (!(nu > 0.0)) {
+            active[r] = 0;
+            set_zero();
+            continue;
+          }
+          for (int i = 0; i < j; ++i) {
+            c->pin_coef[(size_t)i * nrhs + r] = to_df(-D(2 * i) / rho);
+            c->pin_coef[(size_t)(j + i) * nrhs + r] = to_df(-(D(2 * i + 1) - gam * D(2 * i)) / nu);
+          }
+          c->pin_coef[(size_t)(2 * j) * nrhs + r] = to_df(cd(1.0 / rho, 0.0));
+          c->pin_coef[(size_t)(2 * j + 1) * nrhs + r] = to_df(cd(1.0 / nu, 0.0));
+          c->pin_coef[(size_t)(2 * j + 2) * nrhs + r] = to_df(-gam / nu);
+          nu_prev[r] = nu;
+          any = true;
+        }
+        if (!any) break;
+        HPS_CK(c, cudaMemcpyAsync(c->df_coef, c->pin_coef, sizeof(float4) * (size_t)rows_coef * nrhs,
+                                  cudaMemcpyHostToDevice, st));
+        PhaseScope ps(c, HPS_PH_ORTHO);
+        HPS_CK(c, df_update2(c->df_V, vs, j, Vt, c->df_w, c->df_coef, Vt, c->df_V + (size_t)(j + 1) * vs, n, nrhs,
+                             st));
+      }
+      // the last step's column is still open for the right-hand sides that kept going: close it
+      bool open = false;
+      for (int r = 0; r < nrhs; ++r) open = open || active[r];
+      if (open) {
+        const float4* Vl = c->df_V + (size_t)restart * vs;
+        {
+          PhaseScope ps(c, HPS_PH_ORTHO);
+          HPS_CK(c, df_dots2(c->df_V, vs, restart + 1, Vl, Vl, n, nrhs, c->df_part, hbuf, st));
+        }
+        HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * (size_t)(2 * (restart + 1) + 1) * nrhs,
+                                  cudaMemcpyDeviceToHost, st));
+        HPS_CK(c, cudaStreamSynchronize(st));
+        for (int r = 0; r < nrhs; ++r) {
+          if (!active[r]) continue;
+          auto D = [&](int k) { const double2 v = c->pin_h[(size_t)k * nrhs + r]; return cd(v.x, v.y); };
+          cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+          const cd* ht = &htent[(size_t)r * (restart + 1)];
+          double sa = 0.0;
+          for (int i = 0; i < restart; ++i) sa += std::norm(D(2 * i));
+          const double rho = std::sqrt(std::max(0.0, D(2 * restart).real() - sa));
+          for (int i = 0; i < restart; ++i) Hr[(size_t)i * restart + (restart - 1)] = ht[i] + nu_prev[r] * D(2 * i);
+          rotate(r, restart - 1, nu_prev[r] * rho);
+          its[r] += 1;
+          steps[r] = restart;
+          res[r] = bnorm[r] > 0 ? std::abs(g[(size_t)r * (restart + 1) + restart]) / bnorm[r] : 0.0;
+        }
+      }
+      int jdone = 0;
+      for (int r = 0; r < nrhs; ++r) jdone = std::max(jdone, steps[r]);
+      if (jdone == 0) continue;
+      for (int r = 0; r < nrhs; ++r) {
+        const cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+        const cd* gr = &g[(size_t)r * (restart + 1)];
+        std::vector<cd> y(jdone, 0.0);
+        for (int i = steps[r] - 1; i >= 0; --i) {
+          cd v = gr[i];
+          for (int l = i + 1; l < steps[r]; ++l) v -= Hr[(size_t)i * restart + l] * y[l];
+          const cd d = Hr[(size_t)i * restart + i];
+          y[i] = std::abs(d) > 0 ? v / d : 0.0;
+        }
+        for (int i = 0; i < jdone; ++i) c->pin_y[(size_t)i * nrhs + r] = make_double2(y[i].real(), y[i].imag());
+      }
+      HPS_CK(c, cudaMemcpyAsync(c->fg_y, c->pin_y, sizeof(double2) * (size_t)jdone * nrhs, cudaMemcpyHostToDevice, st));
+      HPS_CK(c, df_bupdate<float2>(c->df_x, c->df_Z, vs, jdone, c->fg_y, n, nrhs, 1.f, st));
+    }
+  } else
   for (int outer = 0; outer < max_outer; ++outer) {
     // explicit residual w = rhs - Pi M x (x = 0 at the start: w = rhs, norms already in hbuf)
     if (outer > 0) {
