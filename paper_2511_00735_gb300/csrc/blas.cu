@@ -524,10 +524,11 @@ cudaError_t launch_rowgemm(const GemmArgs<R>& a, int mmax, int nmax, int kmax, c
 template <typename R>
 cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s, int kmax) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
-  // large FP32 products (the merges of the upper levels): tensor cores, 3xTF32
+  // FP32 products on the tensor cores (3xTF32): the merges of the upper levels and the
+  // block-vector products of the sweeps and the coarse solve with long rows
   if constexpr (sizeof(R) == 4) {
-    if (a.err && mmax >= 64 && nmax >= 64 && kmax >= 64 && a.nbatch <= 65535)
-      return launch_tc_gemm(a, mmax, nmax, a.err, s);
+    if (a.err && mmax >= 64 && kmax >= 64 && (nmax >= 64 || (nmax <= 16 && kmax >= 64)) && a.nbatch <= 65535)
+      return launch_tc_gemm(a, mmax, nmax, kmax, a.err, s);
   }
   // block-vector products (the sweeps' and the coarse solve's right-hand sides)
   if (nmax <= 16 && kmax > 0 && mmax > 32) {
@@ -597,6 +598,14 @@ void optin_blas() {
   smem_optin(gj_small_kernel<double>);
   smem_optin(gj_panel_kernel<float>);
   smem_optin(gj_panel_kernel<double>);
+}
+
+cudaError_t splitk_reduce(const GemmArgs<float>& a, int ksplit, int mmax, int nmax, cudaStream_t s) {
+  int rb = (mmax * nmax + NT - 1) / NT;
+  rb = rb < 64 ? rb : 64;
+  splitk_reduce_kernel<float><<<dim3(rb, a.nbatch), NT, 0, s>>>(a, ksplit, mmax, nmax);
+  note_launch();
+  return cudaGetLastError();
 }
 
 template cudaError_t launch_gemm<double>(const GemmArgs<double>&, int, int, cudaStream_t, int);

@@ -134,7 +134,9 @@ template <typename R> struct GemmArgs {
 
 // FP32 complex GEMM on the tensor cores (tc.cu): batched like launch_gemm, for tiles of
 // 128 rows x 64 complex columns; *err is set when a bounded wait gives up.
-cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int* err, cudaStream_t s);
+cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s);
+// Fixed-order sum of ksplit partial tiles from a.ws with the descriptor epilogue (blas.cu).
+cudaError_t splitk_reduce(const GemmArgs<float>& a, int ksplit, int mmax, int nmax, cudaStream_t s);
 void optin_tc();
 
 // kmax > 0 enables splitting K across blocks when the grid would not fill the GPU.

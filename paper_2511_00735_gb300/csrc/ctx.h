@@ -100,7 +100,6 @@ struct hps_ctx {
   int n_robust = 0;            // elements built by the pivoted route
   int* d_flag = nullptr;
   int* d_gemm_err = nullptr;   // set by a tensor-core GEMM whose bounded wait gave up
-  bool in_build = false;       // inside hps_merge_levels: FP32 GEMMs may take the tensor cores
 
   // tree.  The plan (stage orders, merge maps, GEMM descriptors, coarse maps: everything that
   // depends on the mesh and L_exact only) survives new coefficients and leaves; the numeric

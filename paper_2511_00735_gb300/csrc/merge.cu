@@ -86,7 +86,7 @@ cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long
   a.ws = static_cast<c_t<R>*>(c->gemm_ws);
   a.ws_elems = (long long)c->gemm_ws_elems;
   a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
-  a.err = c->in_build ? c->d_gemm_err : nullptr;  // tensor cores for the merges only
+  a.err = c->d_gemm_err;  // FP32 GEMMs may take the tensor cores (their waits report through it)
   return launch_gemm<R>(a, mmax, nmax, c->stream, kmax);
 }
 
@@ -465,10 +465,8 @@ int build_tree(hps_ctx* c, int L_exact, int exact_coarse) {
   if (c->plan_L == L_exact) free_numeric(c);  // same mesh and depth: keep the plan
   else free_tree(c);
   PhaseScope ps(c, HPS_PH_MERGE);
-  c->in_build = true;
   int rc = c->precision == HPS_FP64 ? build_tree_t<double>(c, L_exact, exact_coarse)
                                     : build_tree_t<float>(c, L_exact, exact_coarse);
-  c->in_build = false;
   if (rc != HPS_OK) {
     cudaStreamSynchronize(c->stream);
     free_tree(c);

@@ -678,7 +678,13 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   HPS_CK(c, rows_to_user(gdev, x64, c->d_es_in, n, nrhs, c->n_skel, st));
   if (host_out)
     HPS_CK(c, cudaMemcpyAsync(g_out, gdev, sizeof(double2) * (size_t)c->n_skel * nrhs, cudaMemcpyDeviceToHost, st));
+  int gerr = 0;
+  HPS_CK(c, cudaMemcpyAsync(&gerr, c->d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   HPS_CK(c, cudaStreamSynchronize(st));
+  if (gerr) {
+    cudaMemsetAsync(c->d_gemm_err, 0, sizeof(int), st);
+    return fail(c, HPS_ETIMEOUT, "a tensor-core GEMM of the preconditioner timed out waiting for its MMAs");
+  }
   int nconv = 0, maxit = 0;
   double maxres = 0.0;
   for (int r = 0; r < nrhs; ++r) {

@@ -31,17 +31,23 @@ namespace {
 
 constexpr int TC_NT = 128;
 constexpr int TC_M = 128;              // output rows per CTA = TMEM lanes
-constexpr int TC_NC = 64;              // complex output columns per CTA
-constexpr int TC_NR = 2 * TC_NC;       // real columns = MMA N
 constexpr int TC_KC = 8;               // complex k per chunk
 constexpr int TC_KR = 2 * TC_KC;       // real k per chunk = 2 MMA k-steps of 8
 constexpr int A_PER = TC_M * TC_KC / TC_NT;   // complex A values each thread stages per chunk
-constexpr int B_PER = TC_KC * TC_NC / TC_NT;  // complex B values each thread stages per chunk
 constexpr uint32_t LBO = 128;          // bytes between core matrices along k
 constexpr uint32_t SBO = (TC_KR / 4) * 128;  // bytes between 8-row groups
 constexpr int A_TILE = TC_M * TC_KR;   // floats in one A tile (8 KB)
-constexpr int B_TILE = TC_NR * TC_KR;  // floats in one B' tile (8 KB)
-constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;  // hi and lo of A and B': 32 KB
+// per column tile NC (complex columns per CTA): MMA N = 2 NC real columns
+template <int NC> struct TcTile {
+  static constexpr int NR = 2 * NC;
+  static constexpr int B_PER = TC_KC * NC / TC_NT;  // complex B values each thread stages per chunk
+  static constexpr int B_TILE = NR * TC_KR;         // floats in one B' tile
+  static constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;  // hi and lo of A and B'
+  static constexpr int TCOLS = NR < 32 ? 32 : NR;   // tensor-memory columns (power of two >= 32)
+  // instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, N, M
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+};
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -57,10 +63,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
          ((uint64_t)1 << 46);
 }
-
-// instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, N, M
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_NR >> 3) << 17) |
-                           ((uint32_t)(TC_M >> 4) << 24);
 
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
@@ -78,23 +80,32 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return done != 0;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
   asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
                    tmem),
-               "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+               "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
                : "memory");
 }
 
-__global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, int* err) {
+// blockIdx.z = batch + nbatch * split; with ksplit > 1 each split covers kc complex k and stores
+// its raw tile in the split-K workspace (reduced in fixed order by splitk_reduce)
+template <int NC>
+__global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, int* err, int ksplit, int kc, int mmax,
+                                                           int nmax) {
+  using TT = TcTile<NC>;
+  constexpr int NR = TT::NR, B_PER = TT::B_PER, B_TILE = TT::B_TILE, STAGE = TT::STAGE;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const GemmDesc d = a.desc[blockIdx.z];
-  const int n = d.n < 0 ? a.n_launch : d.n, m = d.m, kk = d.k;
-  const int row0 = blockIdx.y * TC_M, col0 = blockIdx.x * TC_NC;
+  const int bb = blockIdx.z % a.nbatch, sp = blockIdx.z / a.nbatch;
+  const GemmDesc d = a.desc[bb];
+  const int n = d.n < 0 ? a.n_launch : d.n, m = d.m;
+  const int kb = ksplit > 1 ? sp * kc : 0;
+  const int kk = ksplit > 1 ? min(d.k, kb + kc) : d.k;  // this split covers complex k in [kb, kk)
+  const int row0 = blockIdx.y * TC_M, col0 = blockIdx.x * NC;
   if (row0 >= m || col0 >= n) return;  // uniform over the block, before any tensor-memory use
   if (tid == 0) {
     s_fail = 0;
@@ -104,7 +115,7 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "n"(TC_NR)
+                 "n"(TT::TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -114,11 +125,11 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
   const uint32_t tmem = tmem_base;
 
   const float2* Ab = a.A + (long long)d.a_r * a.lda + d.a_c;
-  const int nk = (kk + TC_KC - 1) / TC_KC;
+  const int nk = kk > kb ? (kk - kb + TC_KC - 1) / TC_KC : 0;
   // the next chunk's operands are fetched into registers one iteration ahead
   float2 ra[A_PER], rb[B_PER];
   auto fetch = [&](int kt) {
-    const int k0 = kt * TC_KC;
+    const int k0 = kb + kt * TC_KC;
 #pragma unroll
     for (int u = 0; u < A_PER; ++u) {
       const int l = tid + u * TC_NT, r = l / TC_KC, kc = l % TC_KC;
@@ -127,7 +138,7 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
     }
 #pragma unroll
     for (int u = 0; u < B_PER; ++u) {
-      const int l = tid + u * TC_NT, kc = l / TC_NC, nc = l % TC_NC;
+      const int l = tid + u * TC_NT, kc = l / NC, nc = l % NC;
       const int gk = k0 + kc, gj = col0 + nc;
       float2 v = make_float2(0.f, 0.f);
       if (gk < kk && gj < n) {
@@ -168,7 +179,7 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
     // at real k = 2kc, 2kc+1
 #pragma unroll
     for (int u = 0; u < B_PER; ++u) {
-      const int l = tid + u * TC_NT, kc = l / TC_NC, nc = l % TC_NC;
+      const int l = tid + u * TC_NT, kc = l / NC, nc = l % NC;
       const float2 v = rb[u];
       uint2 h0, l0, h1, l1;
       split_tf32(v.x, h0.x, l0.x);
@@ -191,9 +202,9 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
 #pragma unroll
       for (int ks = 0; ks < TC_KR / 8; ++ks) {
         const uint32_t step = ks * 2 * LBO;  // two core matrices = 8 real k
-        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bh + step), (kt > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bl + step), 1u);
-        mma_tf32(tmem, smem_desc(al + step), smem_desc(bh + step), 1u);
+        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bh + step), TT::IDESC, (kt > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bl + step), TT::IDESC, 1u);
+        mma_tf32(tmem, smem_desc(al + step), smem_desc(bh + step), TT::IDESC, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&mbar[s]))
@@ -216,8 +227,9 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
   const long long orow = gi < m ? (long long)d.c_r + (rmap ? rmap[gi] : gi) : 0;
   const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
   if (ok) {
+    float2* W = ksplit > 1 ? a.ws + (((long long)sp * a.nbatch + bb) * mmax) * nmax : nullptr;
 #pragma unroll 1
-    for (int c0 = 0; c0 < TC_NR; c0 += 16) {
+    for (int c0 = 0; c0 < NR; c0 += 16) {
       uint32_t v[16];
       if (nk > 0) {
         const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
@@ -236,7 +248,12 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
         for (int j = 0; j < 8; ++j) {
           const int gj = col0 + c0 / 2 + j;
           if (gj >= n) continue;
-          float2 o = cmul(a.alpha, make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+          const float2 acc = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+          if (W) {
+            W[(long long)gi * nmax + gj] = acc;
+            continue;
+          }
+          float2 o = cmul(a.alpha, acc);
           if (a.C0) o = cadd(o, cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj]));
           a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = o;
         }
@@ -246,22 +263,53 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_NR) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TT::TCOLS) : "memory");
+}
+
+template <int NC>
+constexpr size_t tc_gemm_smem() { return (size_t)2 * TcTile<NC>::STAGE * sizeof(float) + 1024; }
+
+template <int NC>
+cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+  const int gx = (nmax + NC - 1) / NC, gy = (mmax + TC_M - 1) / TC_M;
+  const long long blocks = (long long)gx * gy * a.nbatch;
+  // split K until about three CTAs per SM are busy (a CTA streams its k range serially)
+  const long long target = 3LL * a.num_sms;
+  int ksplit = 1;
+  if (kmax >= 8 * TC_KC && a.ws && blocks < target) {
+    ksplit = (int)((target + blocks - 1) / blocks);
+    ksplit = ksplit < kmax / (4 * TC_KC) ? ksplit : kmax / (4 * TC_KC);
+    ksplit = ksplit < 16 ? ksplit : 16;
+    while (ksplit > 1 && ((long long)ksplit * a.nbatch > 65535 ||
+                          (long long)ksplit * a.nbatch * mmax * nmax > a.ws_elems))
+      --ksplit;
+  }
+  int kc = kmax;
+  if (ksplit > 1) {
+    kc = (kmax + ksplit - 1) / ksplit;
+    kc = (kc + TC_KC - 1) / TC_KC * TC_KC;
+    ksplit = (kmax + kc - 1) / kc;
+  }
+  if ((long long)a.nbatch * ksplit > 65535) return cudaErrorInvalidValue;
+  dim3 grid(gx, gy, a.nbatch * ksplit);
+  tc_gemm_kernel<NC><<<grid, TC_NT, tc_gemm_smem<NC>(), s>>>(a, err, ksplit, kc, mmax, nmax);
+  note_launch();
+  if (ksplit > 1) return splitk_reduce(a, ksplit, mmax, nmax, s);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t tc_gemm_smem() { return (size_t)2 * STAGE * sizeof(float) + 1024; }
-
-cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int* err, cudaStream_t s) {
+cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
-  dim3 grid((nmax + TC_NC - 1) / TC_NC, (mmax + TC_M - 1) / TC_M, a.nbatch);
-  tc_gemm_kernel<<<grid, TC_NT, tc_gemm_smem(), s>>>(a, err);
-  note_launch();
-  return cudaGetLastError();
+  if (nmax <= 16) return launch_tc<16>(a, mmax, nmax, kmax, err, s);
+  return launch_tc<64>(a, mmax, nmax, kmax, err, s);
 }
 
-void optin_tc() { smem_optin(tc_gemm_kernel); }
+void optin_tc() {
+  smem_optin(tc_gemm_kernel<16>);
+  smem_optin(tc_gemm_kernel<64>);
+}
 
 }  // namespace hps
