@@ -64,6 +64,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          ((uint64_t)1 << 46);
 }
 
+// Staging order of the A tile: element e covers core matrix e / 16 (row group, k group) and
+// position e % 16 in it (row (e % 16) / 2, complex k (e % 2)), so that the 8-byte stores of a
+// warp fill two whole core matrices (conflict-free) while its loads still read whole 32-byte
+// sectors (8 rows x 4 complex).
+__device__ __forceinline__ void a_elem(int e, int& r, int& kc) {
+  constexpr int KG = TC_KC / 2;  // k groups (2 complex each) per chunk
+  const int cm = e >> 4, w = e & 15;
+  r = (cm / KG) * 8 + (w >> 1);
+  kc = (cm % KG) * 2 + (w & 1);
+}
+
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
   const float r = x - __uint_as_float(hi);
@@ -132,7 +143,8 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
     const int k0 = kb + kt * TC_KC;
 #pragma unroll
     for (int u = 0; u < A_PER; ++u) {
-      const int l = tid + u * TC_NT, r = l / TC_KC, kc = l % TC_KC;
+      int r, kc;
+      a_elem(tid + u * TC_NT, r, kc);
       const int gi = row0 + r, gk = k0 + kc;
       ra[u] = (gi < m && gk < kk) ? Ab[(long long)gi * a.lda + gk] : make_float2(0.f, 0.f);
     }
@@ -167,7 +179,8 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
     // A: 128 rows x TC_KC complex, (re, im) -> real columns 2kc, 2kc+1 of the row
 #pragma unroll
     for (int u = 0; u < A_PER; ++u) {
-      const int l = tid + u * TC_NT, r = l / TC_KC, kc = l % TC_KC;
+      int r, kc;
+      a_elem(tid + u * TC_NT, r, kc);
       uint2 h, lo;
       split_tf32(ra[u].x, h.x, lo.x);
       split_tf32(ra[u].y, h.y, lo.y);
