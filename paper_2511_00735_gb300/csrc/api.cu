@@ -170,7 +170,7 @@ void free_numeric(hps_ctx* c) {
   FREE(c->sw_x); FREE(c->ws_G); FREE(c->d_eye);
   FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);
   FREE(c->cg_nrm); FREE(c->cg_y); FREE(c->cg_g); FREE(c->cg_s); FREE(c->cg_part);
-  FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c);
+  FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c); FREE(c->cg_inv); FREE(c->cg_cnt);
   FREE(c->ex_r); FREE(c->ex_e);
   c->ws_X_elems = 0;
   c->nrhs_cap = 0;
@@ -797,7 +797,7 @@ int hps_release_workspace(hps_ctx* c) {
   FREE(c->sw_x);
   FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);
   FREE(c->cg_nrm); FREE(c->cg_y); FREE(c->cg_g); FREE(c->cg_s); FREE(c->cg_part);
-  FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c);
+  FREE(c->cg_beta); FREE(c->cg_floor); FREE(c->cg_c); FREE(c->cg_inv); FREE(c->cg_cnt);
   FREE(c->ex_r); FREE(c->ex_e);
   c->nrhs_cap = 0;
   c->cg_k = c->cg_nrhs = c->ex_nrhs = 0;

@@ -129,7 +129,7 @@ struct hps_ctx {
   int cg_k = 0, cg_nrhs = 0;
   void *cg_V = nullptr, *cg_w = nullptr, *cg_W = nullptr, *cg_H = nullptr, *cg_h1 = nullptr, *cg_h2 = nullptr;
   void *cg_nrm = nullptr, *cg_y = nullptr, *cg_g = nullptr, *cg_s = nullptr, *cg_part = nullptr;
-  void *cg_beta = nullptr, *cg_floor = nullptr, *cg_c = nullptr;
+  void *cg_beta = nullptr, *cg_floor = nullptr, *cg_c = nullptr, *cg_inv = nullptr, *cg_cnt = nullptr;
   // exact coarse scratch
   void *ex_r = nullptr, *ex_e = nullptr;
   int ex_nrhs = 0;

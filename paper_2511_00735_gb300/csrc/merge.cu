@@ -507,7 +507,8 @@ int ensure_cg(hps_ctx* c, int k, int nrhs) {
   const size_t rows = (size_t)Sc.nsub * Sc.n;
   const size_t cs = sizeof(c_t<R>);
   void** bufs[] = {&c->cg_V, &c->cg_w, &c->cg_W, &c->cg_H, &c->cg_h1, &c->cg_h2, &c->cg_nrm,
-                   &c->cg_y, &c->cg_g, &c->cg_s, &c->cg_part, &c->cg_beta, &c->cg_floor, &c->cg_c};
+                   &c->cg_y, &c->cg_g, &c->cg_s, &c->cg_part, &c->cg_beta, &c->cg_floor, &c->cg_c,
+                   &c->cg_inv, &c->cg_cnt};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -522,12 +523,18 @@ int ensure_cg(hps_ctx* c, int k, int nrhs) {
   c->cg_y = dev_alloc(c, cs * (size_t)k * nrhs);
   c->cg_g = dev_alloc(c, cs * (size_t)(k + 1) * nrhs);
   c->cg_s = dev_alloc(c, cs * (size_t)k * nrhs);
-  c->cg_part = dev_alloc(c, cs * (size_t)bdot_blocks((long long)rows) * (k + 1) * nrhs);
+  const int fb = cg_pass_blocks((long long)rows, nrhs);
+  const size_t np = std::max((size_t)bdot_blocks((long long)rows), (size_t)fb + cg_groups(fb));
+  c->cg_part = dev_alloc(c, cs * np * (k + 1) * nrhs);
   c->cg_beta = dev_alloc(c, sizeof(R) * nrhs);
   c->cg_floor = dev_alloc(c, sizeof(R) * nrhs);
   c->cg_c = dev_alloc(c, sizeof(R) * (size_t)k * nrhs);
+  c->cg_inv = dev_alloc(c, sizeof(R) * nrhs);
+  const size_t ncnt = 1 + (size_t)cg_groups(fb);
+  c->cg_cnt = dev_alloc(c, sizeof(unsigned) * ncnt);
   for (void** b : bufs)
     if (!*b) return fail(c, HPS_ENOMEM, "coarse GMRES workspace");
+  if (cudaMemsetAsync(c->cg_cnt, 0, sizeof(unsigned) * ncnt, c->stream) != cudaSuccess) return fail(c, HPS_ECUDA, "coarse GMRES counter");
   c->cg_k = k;
   ++c->vc_gen;
   c->cg_nrhs = nrhs;
@@ -584,6 +591,42 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
   R* floor = static_cast<R*>(c->cg_floor);
   const long long vs = rows * nrhs;
   const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+  if (cg_pass_fits<R>(k, nrhs)) {
+    // fused passes: start, then per step the operator product of the unnormalised w and
+    // three passes (apply + first projection, second projection, norm + Hessenberg column)
+    CgPass<R> p;
+    p.V = V;
+    p.vs = vs;
+    p.w = w;
+    p.W = W;
+    p.g = Vc;
+    p.nb = cc.d_cnb;
+    p.rows = rows;
+    p.nrhs = nrhs;
+    p.k = k;
+    p.part = part;
+    p.cnt = static_cast<unsigned*>(c->cg_cnt);
+    p.h1 = h1;
+    p.h2 = h2;
+    p.H = static_cast<C*>(c->cg_H);
+    p.beta = beta;
+    p.floor = floor;
+    p.inv = static_cast<R*>(c->cg_inv);
+    p.tol = tol;
+    HPS_CK(c, cg_pass<R>(CG_START, p, st));
+    for (int j = 0; j < k; ++j) {
+      p.j = j;
+      HPS_CK(c, gemm<R>(c, cc.d_cdesc, Sc.nsub, Sc.T, Sc.n, w, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int,
+                        nrhs, nrhs, cc.max_int));
+      HPS_CK(c, cg_pass<R>(CG_APPLY, p, st));
+      HPS_CK(c, cg_pass<R>(CG_PROJECT, p, st));
+      HPS_CK(c, cg_pass<R>(CG_CLOSE, p, st));
+    }
+    HPS_CK(c, lsq<R>(static_cast<C*>(c->cg_H), beta, floor, static_cast<C*>(c->cg_y), static_cast<C*>(c->cg_g),
+                     static_cast<R*>(c->cg_c), static_cast<C*>(c->cg_s), k, nrhs, st));
+    HPS_CK(c, bcombine<R>(Vc, V, vs, k, static_cast<C*>(c->cg_y), rows, nrhs, st));
+    return HPS_OK;
+  }
   // r_c = Pi rho_c (incoming coordinates of the coarse unknowns)
   HPS_CK(c, swap_add<R>(w, nullptr, Vc, cc.d_cnb, rows, nrhs, st));
   HPS_CK(c, bdot<R>(w, 0, 1, w, rows, nrhs, part, nrm, 0, st));

@@ -441,6 +441,195 @@ cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Fused coarse-GMRES passes.  One thread per (row, right-hand side): thread (lrow, r) of a
+// block takes row lo + lrow of the block's rper rows; every load of a pass is independent of
+// the others (one memory round trip).  Block partials are reduced in two levels by the last
+// block to arrive: the last block of each group of CG_GROUP blocks sums the group's partials
+// in block order, the last group reducer sums the group sums in group order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int CG_GROUP = 16;
+
+int cg_pass_blocks(long long rows, int nrhs) {
+  int rpad = 1;
+  while (rpad < nrhs) rpad <<= 1;
+  const long long rper = NT / rpad;
+  const long long b = (rows + rper - 1) / rper;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(NT) cg_pass_kernel(CgPass<R> p, int rpad) {
+  using C = c_t<R>;
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  C* red = reinterpret_cast<C*>(cg_smem);  // [nvec][NT / 32][rpad]
+  __shared__ int is_last;
+  const int r = threadIdx.x % rpad, lrow = threadIdx.x / rpad, rper = NT / rpad;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long row = (long long)blockIdx.x * rper + lrow;
+  const int nvec = (MODE == CG_START || MODE == CG_CLOSE) ? 1 : p.j + 1;  // dot products per column
+  const int nupd = (MODE == CG_PROJECT || MODE == CG_CLOSE) ? p.j + 1 : 0;
+  C acc[CG_KMAX];
+#pragma unroll
+  for (int i = 0; i < CG_KMAX; ++i) acc[i] = czero<R>();
+  if (r < p.nrhs && row < p.rows) {
+    const long long l = row * p.nrhs + r;
+    C x, vj = czero<R>();
+    if (MODE == CG_START) {
+      const int m = p.nb[row];
+      x = m >= 0 ? p.g[(long long)m * p.nrhs + r] : czero<R>();
+    } else if (MODE == CG_APPLY) {
+      const R sc = p.inv[r];
+      const C wl = p.w[l];
+      const int m = p.nb[row];
+      vj = cscale(wl, sc);
+      x = m >= 0 ? cscale(cadd(wl, p.W[(long long)m * p.nrhs + r]), sc) : czero<R>();
+      p.V[p.j * p.vs + l] = vj;
+    } else {
+      const C* hin = MODE == CG_PROJECT ? p.h1 : p.h2;
+      C v[CG_KMAX], h[CG_KMAX];
+#pragma unroll
+      for (int i = 0; i < CG_KMAX; ++i)
+        if (i < nupd) {
+          v[i] = p.V[i * p.vs + l];
+          h[i] = hin[i * p.nrhs + r];
+        }
+      x = p.w[l];
+#pragma unroll
+      for (int i = 0; i < CG_KMAX; ++i)
+        if (i < nupd) cfms(x, v[i], h[i]);
+      if (MODE == CG_PROJECT) {
+#pragma unroll
+        for (int i = 0; i < CG_KMAX; ++i)
+          if (i < nvec) cfma_conj(acc[i], v[i], x);
+      }
+    }
+    p.w[l] = x;
+    if (MODE == CG_START || MODE == CG_CLOSE) {
+      cfma_conj(acc[0], x, x);
+    } else if (MODE == CG_APPLY) {
+#pragma unroll
+      for (int i = 0; i < CG_KMAX; ++i)
+        if (i < nvec) cfma_conj(acc[i], i == p.j ? vj : p.V[i * p.vs + l], x);
+    }
+  }
+  // block partials: lanes of one r within a warp by shuffles, then the warps in order
+#pragma unroll
+  for (int i = 0; i < CG_KMAX; ++i) {
+    if (i >= nvec) break;
+    C a = acc[i];
+    for (int off = rpad; off < 32; off <<= 1) {
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+    }
+    if (lane < rpad) red[(i * (NT / 32) + warp) * rpad + lane] = a;
+  }
+  __syncthreads();
+  const int nout = nvec * p.nrhs;
+  const int nwr = (NT / 32) < (rper * rpad + 31) / 32 ? (NT / 32) : (rper * rpad + 31) / 32;  // warps holding rows
+  for (int o = threadIdx.x; o < nout; o += NT) {
+    const int i = o / p.nrhs, q = o % p.nrhs;
+    C a = czero<R>();
+    for (int w2 = 0; w2 < nwr; ++w2) a = cadd(a, red[(i * (NT / 32) + w2) * rpad + q]);
+    p.part[(long long)blockIdx.x * nout + o] = a;
+  }
+  // level 1: the last block of this group sums the group's partials
+  const int grp = blockIdx.x / CG_GROUP, ngrp = (gridDim.x + CG_GROUP - 1) / CG_GROUP;
+  const int b0 = grp * CG_GROUP, b1 = min((int)gridDim.x, b0 + CG_GROUP);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(p.cnt + 1 + grp, 1u) == (unsigned)(b1 - b0 - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  C* gsum = p.part + (long long)gridDim.x * nout;
+  for (int o = threadIdx.x; o < nout; o += NT) {
+    C a = czero<R>();
+    for (int b = b0; b < b1; ++b) a = cadd(a, __ldcg(&p.part[(long long)b * nout + o]));
+    gsum[(long long)grp * nout + o] = a;
+  }
+  if (threadIdx.x == 0) p.cnt[1 + grp] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(p.cnt, 1u) == (unsigned)(ngrp - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // level 2: the last group reducer sums the groups and finishes the pass
+  C* fin = red;  // nout <= CG_KMAX * rpad fits in the partial buffer
+  for (int o = threadIdx.x; o < nout; o += NT) {
+    C a = czero<R>();
+    for (int g2 = 0; g2 < ngrp; ++g2) a = cadd(a, __ldcg(&gsum[(long long)g2 * nout + o]));
+    if (MODE == CG_APPLY) p.h1[o] = a;
+    else if (MODE == CG_PROJECT) p.h2[o] = a;
+    fin[o] = a;
+  }
+  __syncthreads();
+  if (MODE == CG_START) {
+    for (int q = threadIdx.x; q < p.nrhs; q += NT) {
+      const R b = fin[q].x > R(0) ? sqrt(fin[q].x) : R(0);
+      p.beta[q] = b;
+      p.floor[q] = p.tol * b;
+      p.inv[q] = b > R(0) ? R(1) / b : R(0);
+    }
+  } else if (MODE == CG_CLOSE) {
+    for (int q = threadIdx.x; q < p.nrhs; q += NT) {
+      C* Hr = p.H + (long long)q * (p.k + 1) * p.k;
+      for (int i = 0; i <= p.j; ++i) Hr[i * p.k + p.j] = cadd(p.h1[i * p.nrhs + q], p.h2[i * p.nrhs + q]);
+      const R nn = fin[q].x > R(0) ? sqrt(fin[q].x) : R(0);
+      Hr[(p.j + 1) * p.k + p.j] = mk<R>(nn, R(0));
+      p.inv[q] = nn > p.floor[q] ? R(1) / nn : R(0);
+    }
+  }
+  if (threadIdx.x == 0) p.cnt[0] = 0u;  // ready for the next pass
+}
+
+template <typename R>
+bool cg_pass_fits(int k, int nrhs) {
+  int rpad = 1;
+  while (rpad < nrhs) rpad <<= 1;
+  return nrhs > 0 && rpad <= 32 && k + 1 <= CG_KMAX &&
+         (size_t)CG_KMAX * (NT / 32) * rpad * sizeof(c_t<R>) <= 48 * 1024;
+}
+
+template <typename R>
+cudaError_t cg_pass(int mode, const CgPass<R>& p, cudaStream_t s) {
+  if (!cg_pass_fits<R>(p.k, p.nrhs) || p.j > p.k || (mode == CG_CLOSE && p.j >= p.k)) return cudaErrorInvalidValue;
+  int rpad = 1;
+  while (rpad < p.nrhs) rpad <<= 1;
+  const int nblk = cg_pass_blocks(p.rows, p.nrhs);
+  const int nvec = (mode == CG_START || mode == CG_CLOSE) ? 1 : p.j + 1;
+  const size_t smem = (size_t)nvec * (NT / 32) * rpad * sizeof(c_t<R>);
+  switch (mode) {
+    case CG_START: cg_pass_kernel<R, CG_START><<<nblk, NT, smem, s>>>(p, rpad); break;
+    case CG_APPLY: cg_pass_kernel<R, CG_APPLY><<<nblk, NT, smem, s>>>(p, rpad); break;
+    case CG_PROJECT: cg_pass_kernel<R, CG_PROJECT><<<nblk, NT, smem, s>>>(p, rpad); break;
+    case CG_CLOSE: cg_pass_kernel<R, CG_CLOSE><<<nblk, NT, smem, s>>>(p, rpad); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void bcombine_kernel(c_t<R>* __restrict__ x, const c_t<R>* __restrict__ V, long long vstride, int nvec,
+                                const c_t<R>* __restrict__ y, long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int r = (int)(l % nrhs);
+    c_t<R> acc = czero<R>();
+    for (int i = 0; i < nvec; ++i) cfma(acc, V[i * vstride + l], y[i * nrhs + r]);
+    x[l] = acc;
+  }
+}
+template <typename R>
+cudaError_t bcombine(c_t<R>* x, const c_t<R>* V, long long vstride, int nvec, const c_t<R>* y, long long rows, int nrhs,
+                     cudaStream_t s) {
+  bcombine_kernel<R><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(x, V, vstride, nvec, y, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // fill
 template <typename R>
 __global__ void zero_kernel(c_t<R>* __restrict__ x, long long n) {
@@ -481,6 +670,9 @@ cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s) {
   template cudaError_t lsq<R>(c_t<R>*, const R*, const R*, c_t<R>*, c_t<R>*, R*, c_t<R>*, int, int,        \
                               cudaStream_t);                  \
   template cudaError_t zero<R>(c_t<R>*, long long, cudaStream_t);                                                       \
+  template cudaError_t cg_pass<R>(int, const CgPass<R>&, cudaStream_t);                                                 \
+  template bool cg_pass_fits<R>(int, int);                                                                               \
+  template cudaError_t bcombine<R>(c_t<R>*, const c_t<R>*, long long, int, const c_t<R>*, long long, int, cudaStream_t); \
   template cudaError_t eye2<R>(c_t<R>*, int, int, cudaStream_t);
 
 HPS_INST_R(double)

@@ -82,6 +82,43 @@ cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws
                 int nrhs, cudaStream_t s);
 template <typename R>
 cudaError_t zero(c_t<R>* x, long long n, cudaStream_t s);
+
+// Fused passes of the coarse GMRES (Arnoldi with two classical Gram-Schmidt passes); each is
+// one launch whose last block reduces the block partials in fixed order (deterministic) and
+// finishes the step.  w is the working vector, V the basis [k+1][rows][nrhs], W the coarse
+// operator product of the unnormalised w, inv the per-column scale of the pending vector.
+//   CG_START:   w_p = g_nb(p) (0 on the physical boundary); beta = ||w||, floor = tol beta, inv = 1 / beta
+//   CG_APPLY:   V_j = inv w; w_p = inv (w_p + W_nb(p)); h1 = V_{0..j}^H w
+//   CG_PROJECT: w -= V_{0..j} h1; h2 = V_{0..j}^H w
+//   CG_CLOSE:   w -= V_{0..j} h2; H[:, j] = h1 + h2, H[j+1][j] = ||w||, inv = 1 / ||w|| above floor, else 0
+enum { CG_START = 0, CG_APPLY = 1, CG_PROJECT = 2, CG_CLOSE = 3 };
+constexpr int CG_KMAX = 16;  // largest j + 1 of the fused passes
+template <typename R>
+struct CgPass {
+  c_t<R>* V = nullptr;
+  long long vs = 0;            // vector stride of V
+  c_t<R>* w = nullptr;
+  const c_t<R>* W = nullptr;   // CG_APPLY: operator product (stage rows)
+  const c_t<R>* g = nullptr;   // CG_START: coarse stage vector
+  const int* nb = nullptr;     // stage row across the face (-1 on the physical boundary)
+  long long rows = 0;
+  int nrhs = 0, j = 0, k = 0;
+  c_t<R>* part = nullptr;      // (cg_pass_blocks + its groups) * (j + 1) * nrhs
+  unsigned* cnt = nullptr;     // 1 + groups counters, zero between launches
+  c_t<R>*h1 = nullptr, *h2 = nullptr, *H = nullptr;
+  R *beta = nullptr, *floor = nullptr, *inv = nullptr;
+  R tol = 0;
+};
+int cg_pass_blocks(long long rows, int nrhs);
+constexpr int cg_groups(int blocks) { return (blocks + 15) / 16; }
+template <typename R>
+bool cg_pass_fits(int k, int nrhs);
+template <typename R>
+cudaError_t cg_pass(int mode, const CgPass<R>& p, cudaStream_t s);
+// x = sum_{i < nvec} V_i y_i (overwrites x)
+template <typename R>
+cudaError_t bcombine(c_t<R>* x, const c_t<R>* V, long long vstride, int nvec, const c_t<R>* y, long long rows, int nrhs,
+                     cudaStream_t s);
 template <typename R>
 cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s);
 
