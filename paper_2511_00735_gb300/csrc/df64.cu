@@ -15,6 +15,7 @@
 // Storage: one complex df64 number is a float4 (re_hi, im_hi, re_lo, im_lo).
 #include "common.cuh"
 #include "df64.cuh"
+#include "dfops.cuh"
 #include "skel.cuh"
 
 namespace hps {
@@ -28,32 +29,9 @@ inline int nblocks(long long work, int cap) {
   return (int)(b > cap ? cap : b);
 }
 
-// The error-free transformations below must run exactly as written: every
-// rounding step uses the _rn intrinsics, which the compiler never contracts
-// into fused multiply-adds (a contracted s + a*b would break TwoSum).
-
-// t + err = a + b exactly (TwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float& t, float& err) {
-  t = __fadd_rn(a, b);
-  const float v = __fsub_rn(t, a);
-  err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, v)), __fsub_rn(b, v));
-}
-
-// (s, c) += a * b for real df64 a = (ah, al), b = (bh, bl): TwoProduct of the leading
-// parts with the cross terms folded into its error, TwoSum into s, errors into c.
-__device__ __forceinline__ void dot2(float& s, float& c, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = __fmaf_rn(ah, bh, -p);
-  e = __fmaf_rn(ah, bl, e);
-  e = __fmaf_rn(al, bh, e);
-  float t, err;
-  two_sum(s, p, t, err);
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, e));
-}
-
-// normalise (s, c) into (hi, lo)
-__device__ __forceinline__ void fast2(float s, float c, float& hi, float& lo) { two_sum(s, c, hi, lo); }
+using dfops::dot2;
+using dfops::fast2;
+using dfops::two_sum;
 
 struct cacc {  // complex df64 accumulator
   float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
@@ -85,13 +63,8 @@ __device__ __forceinline__ float4 cfin(const cacc& a) {
   return r;
 }
 __device__ __forceinline__ float4 from_f2(float2 v) { return make_float4(v.x, v.y, 0.f, 0.f); }
-__device__ __forceinline__ float4 from_d2(double2 v) {
-  const float rh = (float)v.x, ih = (float)v.y;
-  return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
-}
-__device__ __forceinline__ double2 to_d2(float4 v) {
-  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
-}
+using dfops::from_d2;
+using dfops::to_d2;
 __device__ __forceinline__ float4 ld(const float4* p, long long i) { return p[i]; }
 __device__ __forceinline__ float4 ld(const float2* p, long long i) { return from_f2(p[i]); }
 

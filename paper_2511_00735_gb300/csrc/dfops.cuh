@@ -1,0 +1,60 @@
+// Double-float (df64) error-free transformations shared by the kernels that carry values as
+// unevaluated sums of two FP32 numbers (hi + lo, about 48 significant bits): the Arnoldi
+// kernels of the outer FGMRES and the leaf's Gauss-Jordan inverse.  A complex df64 value is
+// a float4 (re_hi, im_hi, re_lo, im_lo).
+//
+// Every rounding step uses the _rn intrinsics, which the compiler never contracts into fused
+// multiply-adds (a contracted s + a*b would break TwoSum).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hps {
+namespace dfops {
+
+// t + err = a + b exactly (TwoSum, Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& t, float& err) {
+  t = __fadd_rn(a, b);
+  const float v = __fsub_rn(t, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, v)), __fsub_rn(b, v));
+}
+
+// (s, c) += a * b for real df64 a = (ah, al), b = (bh, bl): TwoProduct of the leading
+// parts (FMA) with the cross terms folded into its error, TwoSum into s, errors into c.
+__device__ __forceinline__ void dot2(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// normalise (s, c) into (hi, lo)
+__device__ __forceinline__ void fast2(float s, float c, float& hi, float& lo) { two_sum(s, c, hi, lo); }
+
+// complex df64 v - f r
+__device__ __forceinline__ float4 cfms(float4 v, float4 f, float4 r) {
+  float sr = v.x, cr = v.z, si = v.y, ci = v.w;
+  dot2(sr, cr, -f.x, -f.z, r.x, r.z);  // - Re f Re r
+  dot2(sr, cr, f.y, f.w, r.y, r.w);    // + Im f Im r
+  dot2(si, ci, -f.x, -f.z, r.y, r.w);  // - Re f Im r
+  dot2(si, ci, -f.y, -f.w, r.x, r.z);  // - Im f Re r
+  float4 o;
+  fast2(sr, cr, o.x, o.z);
+  fast2(si, ci, o.y, o.w);
+  return o;
+}
+
+__device__ __forceinline__ float4 from_d2(double2 v) {
+  const float rh = (float)v.x, ih = (float)v.y;
+  return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 to_d2(float4 v) {
+  return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+
+}  // namespace dfops
+}  // namespace hps

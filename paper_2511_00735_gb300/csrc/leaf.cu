@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "dfops.cuh"
 #include "skel.cuh"
 
 namespace hps {
@@ -256,6 +257,34 @@ __device__ int ir_argmax_col(const double2* W, int ld, int col, int lo, int hi, 
   for (int r = lo + (int)threadIdx.x; r < hi; r += (int)blockDim.x) {
     const double2 w = W[r * ld + col];
     const double v = fabs(w.x) + fabs(w.y);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
+  }
+  warp_argmax(best, bi);
+  const int nw = (int)(blockDim.x / 32), w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int* si = reinterpret_cast<int*>(scratch + nw);
+  if (lane == 0) {
+    scratch[w] = best;
+    si[w] = bi;
+  }
+  __syncthreads();
+  double b2 = lane < nw ? scratch[lane] : -1.0;
+  int i2 = lane < nw ? si[lane] : -1;
+  warp_argmax(b2, i2);  // every warp reduces the per-warp winners itself
+  i2 = __shfl_sync(0xffffffffu, i2, 0);
+  __syncthreads();
+  return i2 >= 0 ? i2 : lo;
+}
+
+// ir_argmax_col on a complex df64 matrix: the leading parts decide the pivot.
+__device__ int ir_argmax_col_df(const float4* W, int ld, int col, int lo, int hi, double* scratch) {
+  double best = -1.0;
+  int bi = -1;
+  for (int r = lo + (int)threadIdx.x; r < hi; r += (int)blockDim.x) {
+    const float4 w = W[r * ld + col];
+    const double v = (double)fabsf(w.x) + (double)fabsf(w.y);
     if (v > best) {
       best = v;
       bi = r;
@@ -565,49 +594,50 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       A[g * nb + gc] = dgg - acc;
     }
     __syncthreads();
-    // ---- P = A + i eta I, in-place Gauss-Jordan with partial pivoting -> P^{-1} (FP64),
-    //      T = I - 2 i eta P^{-1} ----
+    // ---- P = A + i eta I, in-place Gauss-Jordan with partial pivoting -> P^{-1} in double-float
+    //      (pairs of FP32, about 48 bits: the rank-1 updates run on the FP32 pipes; pivots and
+    //      the scaled pivot row in FP64), T = I - 2 i eta P^{-1} ----
     {
-      double2* W = reinterpret_cast<double2*>(smem_raw);  // [nb][nb], reuses the factor's space
-      double2* colk = W + nb * nb;                         // [nb] column k after the interchange
-      double2* rowk = colk + nb;                           // [nb] scaled pivot row
-      double2* s_inv = rowk + nb;                          // [1]
-      int* perm = reinterpret_cast<int*>(s_inv + 1);       // [nb] pivot rows, then the column order
+      float4* W = reinterpret_cast<float4*>(smem_raw);  // [nb][nb] complex df64, reuses the factor's space
+      float4* colk = W + nb * nb;                        // [nb] column k after the interchange
+      float4* rowk = colk + nb;                          // [nb] scaled pivot row
+      double2* s_inv = reinterpret_cast<double2*>(rowk + nb);  // [1]
+      int* perm = reinterpret_cast<int*>(s_inv + 1);     // [nb] pivot rows, then the column order
       for (int l = tid; l < nb * nb; l += nth) {
         const int g = l / nb, j = l % nb;
-        W[l] = make_double2(A[l], g == j ? eta : 0.0);
+        W[l] = dfops::from_d2(make_double2(A[l], g == j ? eta : 0.0));
       }
       __syncthreads();
       const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
       for (int k = 0; k < nb; ++k) {
-        const int pv = ir_argmax_col(W, nb, k, k, nb, red);
-        // interchange rows k and pv; the thread of column k also inverts the pivot
+        const int pv = ir_argmax_col_df(W, nb, k, k, nb, red);
+        // interchange rows k and pv; the thread of column k also inverts the pivot (FP64)
         for (int j = tid; j < nb; j += nth) {
-          const double2 a = W[k * nb + j], b = W[pv * nb + j];
+          const float4 a = W[k * nb + j], b = W[pv * nb + j];
           W[k * nb + j] = b;
           W[pv * nb + j] = a;
           if (j == k) {
-            if (b.x == 0.0 && b.y == 0.0) atomicCAS(p.flag, 0, ei + 1);
-            *s_inv = cinv(b);
+            const double2 bd = dfops::to_d2(b);
+            if (bd.x == 0.0 && bd.y == 0.0) atomicCAS(p.flag, 0, ei + 1);
+            *s_inv = cinv(bd);
             perm[k] = pv;
           }
         }
         __syncthreads();
         const double2 inv = *s_inv;
         for (int i = tid; i < nb; i += nth) colk[i] = W[i * nb + k];
-        for (int j = tid; j < nb; j += nth) rowk[j] = cmul(j == k ? make_double2(1.0, 0.0) : W[k * nb + j], inv);
+        for (int j = tid; j < nb; j += nth)
+          rowk[j] = dfops::from_d2(cmul(j == k ? make_double2(1.0, 0.0) : dfops::to_d2(W[k * nb + j]), inv));
         __syncthreads();
         if (jc < nb) {
-          const double2 rk = rowk[jc];
+          const float4 rk = rowk[jc];
 #pragma unroll 2
           for (int i = rg; i < nb; i += nrg) {
             if (i == k) {
               W[i * nb + jc] = rk;
             } else {
-              const double2 f = colk[i];
-              double2 v = jc == k ? make_double2(0.0, 0.0) : W[i * nb + jc];
-              cfms(v, f, rk);
-              W[i * nb + jc] = v;
+              const float4 v = jc == k ? make_float4(0.f, 0.f, 0.f, 0.f) : W[i * nb + jc];
+              W[i * nb + jc] = dfops::cfms(v, colk[i], rk);
             }
           }
         }
@@ -628,7 +658,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       const int* sig = perm + nb;
       for (int l = tid; l < nb * nb; l += nth) {
         const int g = l / nb, j = l % nb;
-        const double2 y = W[g * nb + sig[j]];
+        const double2 y = dfops::to_d2(W[g * nb + sig[j]]);
         To[l] = make_double2((g == j ? 1.0 : 0.0) + 2.0 * eta * y.y, -2.0 * eta * y.x);
       }
     }
