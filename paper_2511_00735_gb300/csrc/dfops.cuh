@@ -48,6 +48,42 @@ __device__ __forceinline__ float4 cfms(float4 v, float4 f, float4 r) {
   return o;
 }
 
+// complex df64 a b
+__device__ __forceinline__ float4 cmul(float4 a, float4 b) {
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+  dot2(sr, cr, a.x, a.z, b.x, b.z);
+  dot2(sr, cr, -a.y, -a.w, b.y, b.w);
+  dot2(si, ci, a.x, a.z, b.y, b.w);
+  dot2(si, ci, a.y, a.w, b.x, b.z);
+  float4 o;
+  fast2(sr, cr, o.x, o.z);
+  fast2(si, ci, o.y, o.w);
+  return o;
+}
+
+// complex df64 1 / a = conj(a) / |a|^2: |a|^2 in df64, its reciprocal from the FP32 one by a
+// Newton step in df64 (r = r0 + r0 (1 - d r0)), then conj(a) r
+__device__ __forceinline__ float4 cinv(float4 a) {
+  float ds = 0.f, dc = 0.f;
+  dot2(ds, dc, a.x, a.z, a.x, a.z);
+  dot2(ds, dc, a.y, a.w, a.y, a.w);
+  float dh, dl;
+  fast2(ds, dc, dh, dl);
+  const float r0 = __frcp_rn(dh);
+  float es = 1.f, ec = 0.f;
+  dot2(es, ec, -dh, -dl, r0, 0.f);  // 1 - d r0, about 2^-24
+  const float e = __fadd_rn(es, ec);
+  float rh, rl;
+  two_sum(r0, __fmul_rn(r0, e), rh, rl);
+  float4 o;
+  float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+  dot2(s1, c1, a.x, a.z, rh, rl);
+  dot2(s2, c2, -a.y, -a.w, rh, rl);
+  fast2(s1, c1, o.x, o.z);
+  fast2(s2, c2, o.y, o.w);
+  return o;
+}
+
 __device__ __forceinline__ float4 from_d2(double2 v) {
   const float rh = (float)v.x, ih = (float)v.y;
   return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));

@@ -278,34 +278,6 @@ __device__ int ir_argmax_col(const double2* W, int ld, int col, int lo, int hi, 
   return i2 >= 0 ? i2 : lo;
 }
 
-// ir_argmax_col on a complex df64 matrix: the leading parts decide the pivot.
-__device__ int ir_argmax_col_df(const float4* W, int ld, int col, int lo, int hi, double* scratch) {
-  double best = -1.0;
-  int bi = -1;
-  for (int r = lo + (int)threadIdx.x; r < hi; r += (int)blockDim.x) {
-    const float4 w = W[r * ld + col];
-    const double v = (double)fabsf(w.x) + (double)fabsf(w.y);
-    if (v > best) {
-      best = v;
-      bi = r;
-    }
-  }
-  warp_argmax(best, bi);
-  const int nw = (int)(blockDim.x / 32), w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  int* si = reinterpret_cast<int*>(scratch + nw);
-  if (lane == 0) {
-    scratch[w] = best;
-    si[w] = bi;
-  }
-  __syncthreads();
-  double b2 = lane < nw ? scratch[lane] : -1.0;
-  int i2 = lane < nw ? si[lane] : -1;
-  warp_argmax(b2, i2);  // every warp reduces the per-warp winners itself
-  i2 = __shfl_sync(0xffffffffu, i2, 0);
-  __syncthreads();
-  return i2 >= 0 ? i2 : lo;
-}
-
 __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
@@ -318,12 +290,27 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   double* sw = sK + n1 * n1;                           // [n1] reference weights
   double* sc = sw + n1;                                // [n1*n1] c of this element
   double* red = sc + n1 * n1;                          // [2 * IR_NT / 32] reductions
+  float2* sKd = reinterpret_cast<float2*>(red + 2 * (IR_NT / 32));  // [n1*n1] K in double-float
+  float2* swd = sKd + n1 * n1;                         // [n1] weights in double-float
+  float2* cwd = swd + n1;                              // [n1*n1] c h^2/4 w_i w_j of this element, double-float
+  float2* sDe = cwd + n1 * n1;                         // [2][n1] rows 0 and N of D in double-float
   const int tid = threadIdx.x, nth = blockDim.x;
   double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
-  double* Z = p.Zscr + (long long)blockIdx.x * ni * nb;
+  // the refinement's iterate Z in double-float (the FP64 scratch holds the pairs)
+  float2* Zd = reinterpret_cast<float2*>(p.Zscr + (long long)blockIdx.x * ni * nb);
+  auto to_df = [](double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  };
 
-  for (int l = tid; l < n1 * n1; l += nth) sK[l] = p.Kh[l];
-  for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
+  for (int l = tid; l < n1 * n1; l += nth) {
+    sK[l] = p.Kh[l];
+    sKd[l] = to_df(p.Kh[l]);
+  }
+  for (int l = tid; l < n1; l += nth) {
+    sw[l] = p.wh[l];
+    swd[l] = to_df(p.wh[l]);
+  }
 
   const int nel = (p.elems || p.ed) ? p.count : p.E;
   for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
@@ -338,6 +325,10 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
     for (int l = tid; l < n1 * n1; l += nth) {
       sc[l] = ce[l];
       sD[l] = dsc * p.Dh[l];
+      const int i = l / n1, j = l % n1;
+      cwd[l] = to_df(ce[l] * h2 * p.wh[i] * p.wh[j]);
+      if (i == 0) sDe[j] = to_df(dsc * p.Dh[l]);
+      if (i == N) sDe[n1 + j] = to_df(dsc * p.Dh[l]);
     }
     __syncthreads();
     // ---- assemble L~_ii (FP32, packed lower triangle), one warp per row ----
@@ -432,7 +423,8 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
     double rel_prev = 1.0;
     bool done = false;
     for (int it = 0; it < IR_MAX && !done; ++it) {
-      // residual (FP64), rounded into Y
+      // residual in double-float (error-free products, TwoSum accumulation: about 48 bits on the
+      // FP32 pipes), rounded into Y
       for (int l = tid; l < ni * nb; l += nth) {
         const int I = l / nb, g = l % nb;
         const int i = I / q + 1, j = I % q + 1;
@@ -442,15 +434,29 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         else if (side == 1 && j == s) bv = sK[i * n1 + N] * sw[s];
         else if (side == 2 && i == s) bv = sw[s] * sK[j * n1 + 0];
         else if (side == 3 && i == s) bv = sw[s] * sK[j * n1 + N];
-        if (it > 0) {
-          double s1 = 0.0, s2 = 0.0;
-          for (int t = 1; t <= q; ++t) {
-            s1 += sK[i * n1 + t] * Z[(long long)((t - 1) * q + (j - 1)) * nb + g];
-            s2 += sK[j * n1 + t] * Z[(long long)((i - 1) * q + (t - 1)) * nb + g];
-          }
-          bv -= sw[j] * s1 + sw[i] * s2 - sc[i * n1 + j] * h2 * sw[i] * sw[j] * Z[(long long)I * nb + g];
+        float rs, rc;
+        {
+          const float2 b2 = to_df(bv);
+          rs = b2.x;
+          rc = b2.y;
         }
-        Y[I * ldy + g] = (float)bv;
+        if (it > 0) {
+          float s1s = 0.f, s1c = 0.f, s2s = 0.f, s2c = 0.f;
+          for (int t = 1; t <= q; ++t) {
+            const float2 ka = sKd[i * n1 + t], za = Zd[(long long)((t - 1) * q + (j - 1)) * nb + g];
+            dfops::dot2(s1s, s1c, ka.x, ka.y, za.x, za.y);
+            const float2 kb = sKd[j * n1 + t], zb = Zd[(long long)((i - 1) * q + (t - 1)) * nb + g];
+            dfops::dot2(s2s, s2c, kb.x, kb.y, zb.x, zb.y);
+          }
+          float s1h, s1l, s2h, s2l;
+          dfops::fast2(s1s, s1c, s1h, s1l);
+          dfops::fast2(s2s, s2c, s2h, s2l);
+          const float2 wj = swd[j], wi = swd[i], cw = cwd[i * n1 + j], zi = Zd[(long long)I * nb + g];
+          dfops::dot2(rs, rc, -wj.x, -wj.y, s1h, s1l);
+          dfops::dot2(rs, rc, -wi.x, -wi.y, s2h, s2l);
+          dfops::dot2(rs, rc, cw.x, cw.y, zi.x, zi.y);
+        }
+        Y[I * ldy + g] = __fadd_rn(rs, rc);
       }
       __syncthreads();
       // forward U y = r, diagonal, backward U^T x = z, by row blocks of TB: the rows above
@@ -542,15 +548,19 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         }
       }
       __syncthreads();
-      // Z += correction (FP64), sizes for the stopping test
+      // Z += correction (double-float), sizes for the stopping test
       double md = 0.0, mz = 0.0;
       for (int l = tid; l < ni * nb; l += nth) {
         const int I = l / nb, g = l % nb;
-        const double d = (double)Y[I * ldy + g];
-        const double z = (it == 0 ? 0.0 : Z[l]) + d;
-        Z[l] = z;
-        md = fmax(md, fabs(d));
-        mz = fmax(mz, fabs(z));
+        const float d = Y[I * ldy + g];
+        const float2 z = it == 0 ? make_float2(0.f, 0.f) : Zd[l];
+        float t, e;
+        dfops::two_sum(z.x, d, t, e);
+        float2 zn;
+        dfops::fast2(t, __fadd_rn(z.y, e), zn.x, zn.y);
+        Zd[l] = zn;
+        md = fmax(md, (double)fabsf(d));
+        mz = fmax(mz, (double)fabsf(zn.x));
       }
       md = block_max(md, red);
       mz = block_max(mz, red);
@@ -566,20 +576,22 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       __syncthreads();
     }
 
-    // ---- A = Dn_GG - Dn_Gi Z (FP64) ----
+    // ---- A = Dn_GG - Dn_Gi Z (products accumulated in double-float, A in FP64) ----
     for (int l = tid; l < nb * nb; l += nth) {
       const int g = l / nb, gc = l % nb;
       const int side = g / q, s = g % q + 1;
-      double acc = 0.0;
+      float as = 0.f, ac = 0.f;
       for (int t = 1; t <= q; ++t) {
         int I;
-        double dcoef;
-        if (side == 0) { I = (t - 1) * q + (s - 1); dcoef = -sD[0 * n1 + t]; }
-        else if (side == 1) { I = (t - 1) * q + (s - 1); dcoef = sD[N * n1 + t]; }
-        else if (side == 2) { I = (s - 1) * q + (t - 1); dcoef = -sD[0 * n1 + t]; }
-        else { I = (s - 1) * q + (t - 1); dcoef = sD[N * n1 + t]; }
-        acc += dcoef * Z[(long long)I * nb + gc];
+        float2 dcoef;
+        if (side == 0) { I = (t - 1) * q + (s - 1); dcoef = sDe[t]; dcoef.x = -dcoef.x; dcoef.y = -dcoef.y; }
+        else if (side == 1) { I = (t - 1) * q + (s - 1); dcoef = sDe[n1 + t]; }
+        else if (side == 2) { I = (s - 1) * q + (t - 1); dcoef = sDe[t]; dcoef.x = -dcoef.x; dcoef.y = -dcoef.y; }
+        else { I = (s - 1) * q + (t - 1); dcoef = sDe[n1 + t]; }
+        const float2 z = Zd[(long long)I * nb + gc];
+        dfops::dot2(as, ac, dcoef.x, dcoef.y, z.x, z.y);
       }
+      const double acc = (double)as + (double)ac;
       const int sidec = gc / q, sc2 = gc % q + 1;
       double dgg = 0.0;
       if (sc2 == s) {
@@ -595,50 +607,80 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
     }
     __syncthreads();
     // ---- P = A + i eta I, in-place Gauss-Jordan with partial pivoting -> P^{-1} in double-float
-    //      (pairs of FP32, about 48 bits: the rank-1 updates run on the FP32 pipes; pivots and
-    //      the scaled pivot row in FP64), T = I - 2 i eta P^{-1} ----
+    //      (pairs of FP32, about 48 bits, on the FP32 pipes), T = I - 2 i eta P^{-1} ----
     {
       float4* W = reinterpret_cast<float4*>(smem_raw);  // [nb][nb] complex df64, reuses the factor's space
       float4* colk = W + nb * nb;                        // [nb] column k after the interchange
       float4* rowk = colk + nb;                          // [nb] scaled pivot row
-      double2* s_inv = reinterpret_cast<double2*>(rowk + nb);  // [1]
-      int* perm = reinterpret_cast<int*>(s_inv + 1);     // [nb] pivot rows, then the column order
+      float4* rowo = rowk + nb;                          // [nb] row k before the interchange (becomes row pv)
+      double* cval = reinterpret_cast<double*>(rowo + nb);  // [IR_NT / 64] pivot candidates of the next column
+      int* crow = reinterpret_cast<int*>(cval + IR_NT / 64);
+      int* perm = crow + IR_NT / 64;                     // [nb] pivot rows, then the column order
+      const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
       for (int l = tid; l < nb * nb; l += nth) {
         const int g = l / nb, j = l % nb;
         W[l] = dfops::from_d2(make_double2(A[l], g == j ? eta : 0.0));
       }
       __syncthreads();
-      const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
+      // the pivot of column k is searched while column k is updated at step k - 1: the
+      // thread of column k in each row group keeps its largest |re| + |im| (leading parts)
+      if (jc == 0) {
+        double best = -1.0;
+        int bi = -1;
+        for (int i = rg; i < nb; i += nrg) {
+          const float4 w = W[i * nb];
+          const double v = (double)fabsf(w.x) + (double)fabsf(w.y);
+          if (v > best) { best = v; bi = i; }
+        }
+        cval[rg] = best;
+        crow[rg] = bi;
+      }
+      __syncthreads();
       for (int k = 0; k < nb; ++k) {
-        const int pv = ir_argmax_col_df(W, nb, k, k, nb, red);
-        // interchange rows k and pv; the thread of column k also inverts the pivot (FP64)
-        for (int j = tid; j < nb; j += nth) {
-          const float4 a = W[k * nb + j], b = W[pv * nb + j];
-          W[k * nb + j] = b;
-          W[pv * nb + j] = a;
-          if (j == k) {
-            const double2 bd = dfops::to_d2(b);
-            if (bd.x == 0.0 && bd.y == 0.0) atomicCAS(p.flag, 0, ei + 1);
-            *s_inv = cinv(bd);
+        int pv = -1;
+        double pb = -1.0;
+        for (int c = 0; c < nrg; ++c) {  // largest candidate, ties to the lower row
+          const double v = cval[c];
+          const int r = crow[c];
+          if (r >= 0 && (v > pb || (v == pb && r < pv))) { pb = v; pv = r; }
+        }
+        if (pv < 0) pv = k;
+        // interchange rows k and pv logically: pivot row, column k and the old row k are staged
+        if (tid < nb) {
+          const int j = tid;
+          const float4 piv = W[pv * nb + k];
+          const float4 inv = dfops::cinv(piv);
+          rowo[j] = W[k * nb + j];
+          rowk[j] = j == k ? inv : dfops::cmul(W[pv * nb + j], inv);
+          colk[j] = j == k ? piv : (j == pv ? W[k * nb + k] : W[j * nb + k]);
+          if (j == 0) {
+            if (piv.x == 0.f && piv.y == 0.f) atomicCAS(p.flag, 0, ei + 1);
             perm[k] = pv;
           }
         }
         __syncthreads();
-        const double2 inv = *s_inv;
-        for (int i = tid; i < nb; i += nth) colk[i] = W[i * nb + k];
-        for (int j = tid; j < nb; j += nth)
-          rowk[j] = dfops::from_d2(cmul(j == k ? make_double2(1.0, 0.0) : dfops::to_d2(W[k * nb + j]), inv));
-        __syncthreads();
         if (jc < nb) {
           const float4 rk = rowk[jc];
+          const bool cand = jc == k + 1;
+          double best = -1.0;
+          int bi = -1;
 #pragma unroll 2
           for (int i = rg; i < nb; i += nrg) {
             if (i == k) {
               W[i * nb + jc] = rk;
             } else {
-              const float4 v = jc == k ? make_float4(0.f, 0.f, 0.f, 0.f) : W[i * nb + jc];
-              W[i * nb + jc] = dfops::cfms(v, colk[i], rk);
+              const float4 src = i == pv ? rowo[jc] : W[i * nb + jc];
+              const float4 v = dfops::cfms(jc == k ? make_float4(0.f, 0.f, 0.f, 0.f) : src, colk[i], rk);
+              W[i * nb + jc] = v;
+              if (cand && i > k) {
+                const double m = (double)fabsf(v.x) + (double)fabsf(v.y);
+                if (m > best) { best = m; bi = i; }
+              }
             }
+          }
+          if (cand) {
+            cval[rg] = best;
+            crow[rg] = bi;
           }
         }
         __syncthreads();
@@ -825,7 +867,8 @@ void optin_leaf() {
 size_t leaf_ir_smem_bytes(int N) {
   const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
   const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
-  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 2 * (IR_NT / 32));
+  return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 2 * (IR_NT / 32)) +
+         sizeof(float2) * (2 * n1 * n1 + 3 * n1);
 }
 
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {
