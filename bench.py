@@ -100,19 +100,21 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- FLOP models
-def leaf_flops(N: int, residuals: int = 2) -> tuple:
-    """Executed flops of the leaf kernel per element: (FP64, FP32).
+def leaf_flops(N: int, residuals: int = 2) -> float:
+    """Executed FP32-pipe flops of the leaf kernel per element (an FMA counts 2).
 
-    FP32: L D L^T of the n_i x n_i interior block (n_i^3/6 FMAs) and residuals + 1 pairs of
-    triangular solves with 4q right-hand sides (n_i^2 * 4q FMAs each).  FP64: `residuals`
-    Kronecker-structured residuals (n_i * 4q * (2q + 4) FMAs each), A = Dn_GG - Dn_Gi Z
-    ((4q)^2 q FMAs) and the in-place complex Gauss-Jordan inverse of P ((4q)^3 complex FMAs,
-    four real FMAs each)."""
+    FP32 arithmetic: L D L^T of the n_i x n_i interior block (n_i^3/6 FMAs) and residuals + 1
+    pairs of triangular solves with 4q right-hand sides (n_i^2 * 4q FMAs each).  Double-float
+    arithmetic (pairs of FP32) counted as the FP32 operations it executes: one real product
+    accumulated by the error-free dot2 is 1 MUL + 3 FMA + 8 ADD = 15 flops, a normalisation 6:
+    `residuals` Kronecker-structured residuals (n_i * 4q outputs of 2q + 3 products and two
+    normalisations), A = Dn_GG - Dn_Gi Z ((4q)^2 q products) and the complex Gauss-Jordan
+    inverse of P ((4q)^3 complex multiply-subtracts of 4 products and 2 normalisations)."""
     q = N - 1
     ni, nb = q * q, 4 * q
-    fp64 = 2.0 * (residuals * ni * nb * (2 * q + 4) + nb * nb * q + 4 * nb ** 3)
     fp32 = 2.0 * (ni ** 3 / 6.0 + (residuals + 1) * ni * ni * nb)
-    return fp64, fp32
+    df = residuals * ni * nb * ((2 * q + 3) * 15 + 12) + nb * nb * q * 15 + nb ** 3 * (4 * 15 + 2 * 6)
+    return fp32 + df
 
 
 def leaf_flops_paper(N: int) -> float:
@@ -455,22 +457,20 @@ def main():
     cand = []
     if leaf_calls:
         per = leaf_ms / leaf_calls
-        f64, f32 = leaf_flops(N)
-        f64 *= E
-        f32 *= E
+        f32 = leaf_flops(N) * E
         lit = leaf_flops_paper(N) * E
-        cand.append((leaf_ms, {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, FP64 refinement and inverse)",
-                               "bound": "alu", "achieved": f64 / (per / 1e3) / 1e12,
-                               "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                               "frac": f64 / (per / 1e3) / FP64_PEAK_NOMINAL,
-                               "traffic": LEAF_TRAFFIC_BYTES if prob.nx == 64 and N == 16 else None,
-                               "flops_per_launch": f64, "ms_per_launch": per,
-                               "fp32_flops_per_launch": f32,
-                               "fp32_frac": f32 / (per / 1e3) / FP32_PEAK_NOMINAL,
+        cand.append((leaf_ms, {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, double-float refinement "
+                                         "and inverse)",
+                               "bound": "alu", "achieved": f32 / (per / 1e3) / 1e12,
+                               "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
+                               "frac": f32 / (per / 1e3) / FP32_PEAK_NOMINAL,
+                               "traffic": None,
+                               "flops_per_launch": f32, "ms_per_launch": per,
                                "paper_literal_flops_per_launch": lit,
                                "paper_literal_rate_tflops": lit / (per / 1e3) / 1e12,
-                               "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s), the pipe the FP64 part binds; "
-                                              "FP32 nominal 80.5 TFLOP/s for fp32_frac"}))
+                               "peak_source": "FP32 pipes from unit counts and clock: 152 SMs x 128 lanes x "
+                                              "2 (FMA) x 2.07 GHz = 80.5 TFLOP/s (double-float counted as the "
+                                              "FP32 operations it executes)"}))
     if mv_calls and r.get("outer") == "fp64":
         per = mv_ms / mv_calls
         fl = matvec_flops(E, N, nrhs)

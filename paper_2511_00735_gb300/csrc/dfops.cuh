@@ -61,15 +61,16 @@ __device__ __forceinline__ float4 cmul(float4 a, float4 b) {
   return o;
 }
 
-// complex df64 1 / a = conj(a) / |a|^2: |a|^2 in df64, its reciprocal from the FP32 one by a
-// Newton step in df64 (r = r0 + r0 (1 - d r0)), then conj(a) r
+// complex df64 1 / a = conj(a) / |a|^2: |a|^2 in df64, its reciprocal from an approximate FP32
+// one by a Newton step in df64 (r = r0 + r0 (1 - d r0)), then conj(a) r
 __device__ __forceinline__ float4 cinv(float4 a) {
   float ds = 0.f, dc = 0.f;
   dot2(ds, dc, a.x, a.z, a.x, a.z);
   dot2(ds, dc, a.y, a.w, a.y, a.w);
   float dh, dl;
   fast2(ds, dc, dh, dl);
-  const float r0 = __frcp_rn(dh);
+  float r0;  // approximate reciprocal: the Newton step below supplies the remaining bits
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dh));
   float es = 1.f, ec = 0.f;
   dot2(es, ec, -dh, -dl, r0, 0.f);  // 1 - d r0, about 2^-24
   const float e = __fadd_rn(es, ec);

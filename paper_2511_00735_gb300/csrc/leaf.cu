@@ -613,7 +613,8 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       float4* colk = W + nb * nb;                        // [nb] column k after the interchange
       float4* rowk = colk + nb;                          // [nb] scaled pivot row
       float4* rowo = rowk + nb;                          // [nb] row k before the interchange (becomes row pv)
-      double* cval = reinterpret_cast<double*>(rowo + nb);  // [IR_NT / 64] pivot candidates of the next column
+      float4* coln = rowo + nb;                          // [nb] column k as left by step k - 1 (contiguous)
+      double* cval = reinterpret_cast<double*>(coln + nb);  // [IR_NT / 64] pivot candidates of the next column
       int* crow = reinterpret_cast<int*>(cval + IR_NT / 64);
       int* perm = crow + IR_NT / 64;                     // [nb] pivot rows, then the column order
       const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
@@ -629,6 +630,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         int bi = -1;
         for (int i = rg; i < nb; i += nrg) {
           const float4 w = W[i * nb];
+          coln[i] = w;
           const double v = (double)fabsf(w.x) + (double)fabsf(w.y);
           if (v > best) { best = v; bi = i; }
         }
@@ -648,11 +650,11 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         // interchange rows k and pv logically: pivot row, column k and the old row k are staged
         if (tid < nb) {
           const int j = tid;
-          const float4 piv = W[pv * nb + k];
+          const float4 piv = coln[pv];
           const float4 inv = dfops::cinv(piv);
           rowo[j] = W[k * nb + j];
           rowk[j] = j == k ? inv : dfops::cmul(W[pv * nb + j], inv);
-          colk[j] = j == k ? piv : (j == pv ? W[k * nb + k] : W[j * nb + k]);
+          colk[j] = j == k ? piv : (j == pv ? coln[k] : coln[j]);
           if (j == 0) {
             if (piv.x == 0.f && piv.y == 0.f) atomicCAS(p.flag, 0, ei + 1);
             perm[k] = pv;
@@ -668,13 +670,17 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
           for (int i = rg; i < nb; i += nrg) {
             if (i == k) {
               W[i * nb + jc] = rk;
+              if (cand) coln[i] = rk;
             } else {
               const float4 src = i == pv ? rowo[jc] : W[i * nb + jc];
               const float4 v = dfops::cfms(jc == k ? make_float4(0.f, 0.f, 0.f, 0.f) : src, colk[i], rk);
               W[i * nb + jc] = v;
-              if (cand && i > k) {
-                const double m = (double)fabsf(v.x) + (double)fabsf(v.y);
-                if (m > best) { best = m; bi = i; }
+              if (cand) {
+                coln[i] = v;
+                if (i > k) {
+                  const double m = (double)fabsf(v.x) + (double)fabsf(v.y);
+                  if (m > best) { best = m; bi = i; }
+                }
               }
             }
           }
