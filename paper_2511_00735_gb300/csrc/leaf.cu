@@ -339,11 +339,13 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         float* row = Lp + pk(r, 0);
         for (int cc = lane; cc <= r; cc += 32) {
           const int i2 = cc / q + 1, j2 = cc % q + 1;
-          double v = 0.0;
-          if (j == j2) v += sK[i * n1 + i2] * sw[j];
-          if (i == i2) v += sw[i] * sK[j * n1 + j2];
-          if (r == cc) v -= sc[i * n1 + j] * h2 * sw[i] * sw[j];
-          row[cc] = (float)v;
+          // FP32 (leading parts): the factor only preconditions the refinement, whose
+          // residual uses the double-float operator
+          float v = 0.f;
+          if (j == j2) v += sKd[i * n1 + i2].x * swd[j].x;
+          if (i == i2) v += swd[i].x * sKd[j * n1 + j2].x;
+          if (r == cc) v -= cwd[i * n1 + j].x;
+          row[cc] = v;
         }
       }
     }
@@ -429,16 +431,15 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         const int I = l / nb, g = l % nb;
         const int i = I / q + 1, j = I % q + 1;
         const int side = g / q, s = g % q + 1;
-        double bv = 0.0;
-        if (side == 0 && j == s) bv = sK[i * n1 + 0] * sw[s];
-        else if (side == 1 && j == s) bv = sK[i * n1 + N] * sw[s];
-        else if (side == 2 && i == s) bv = sw[s] * sK[j * n1 + 0];
-        else if (side == 3 && i == s) bv = sw[s] * sK[j * n1 + N];
-        float rs, rc;
+        float rs = 0.f, rc = 0.f;  // boundary coupling K_b w_s, then minus L~_ii Z
         {
-          const float2 b2 = to_df(bv);
-          rs = b2.x;
-          rc = b2.y;
+          float2 kb = make_float2(0.f, 0.f);
+          if (side == 0 && j == s) kb = sKd[i * n1 + 0];
+          else if (side == 1 && j == s) kb = sKd[i * n1 + N];
+          else if (side == 2 && i == s) kb = sKd[j * n1 + 0];
+          else if (side == 3 && i == s) kb = sKd[j * n1 + N];
+          const float2 ws = swd[s];
+          dfops::dot2(rs, rc, kb.x, kb.y, ws.x, ws.y);
         }
         if (it > 0) {
           float s1s = 0.f, s1c = 0.f, s2s = 0.f, s2c = 0.f;
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       }
       __syncthreads();
       // Z += correction (double-float), sizes for the stopping test
-      double md = 0.0, mz = 0.0;
+      float mdf = 0.f, mzf = 0.f;
       for (int l = tid; l < ni * nb; l += nth) {
         const int I = l / nb, g = l % nb;
         const float d = Y[I * ldy + g];
@@ -559,11 +560,11 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         float2 zn;
         dfops::fast2(t, __fadd_rn(z.y, e), zn.x, zn.y);
         Zd[l] = zn;
-        md = fmax(md, (double)fabsf(d));
-        mz = fmax(mz, (double)fabsf(zn.x));
+        mdf = fmaxf(mdf, fabsf(d));
+        mzf = fmaxf(mzf, fabsf(zn.x));
       }
-      md = block_max(md, red);
-      mz = block_max(mz, red);
+      const double md = block_max((double)mdf, red);
+      const double mz = block_max((double)mzf, red);
       const double rel = mz > 0.0 ? md / mz : 0.0;
       if (it > 0) {
         const double rho = fmax(rel / rel_prev, 1e-6);
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       float4* rowk = colk + nb;                          // [nb] scaled pivot row
       float4* rowo = rowk + nb;                          // [nb] row k before the interchange (becomes row pv)
       float4* coln = rowo + nb;                          // [nb] column k as left by step k - 1 (contiguous)
-      double* cval = reinterpret_cast<double*>(coln + nb);  // [IR_NT / 64] pivot candidates of the next column
+      float* cval = reinterpret_cast<float*>(coln + nb);  // [IR_NT / 64] pivot candidates of the next column
       int* crow = reinterpret_cast<int*>(cval + IR_NT / 64);
       int* perm = crow + IR_NT / 64;                     // [nb] pivot rows, then the column order
       const int jc = tid % 64, rg = tid / 64, nrg = nth / 64;  // column and row group of this thread
@@ -626,12 +627,12 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       // the pivot of column k is searched while column k is updated at step k - 1: the
       // thread of column k in each row group keeps its largest |re| + |im| (leading parts)
       if (jc == 0) {
-        double best = -1.0;
+        float best = -1.f;
         int bi = -1;
         for (int i = rg; i < nb; i += nrg) {
           const float4 w = W[i * nb];
           coln[i] = w;
-          const double v = (double)fabsf(w.x) + (double)fabsf(w.y);
+          const float v = fabsf(w.x) + fabsf(w.y);
           if (v > best) { best = v; bi = i; }
         }
         cval[rg] = best;
@@ -640,9 +641,9 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       __syncthreads();
       for (int k = 0; k < nb; ++k) {
         int pv = -1;
-        double pb = -1.0;
+        float pb = -1.f;
         for (int c = 0; c < nrg; ++c) {  // largest candidate, ties to the lower row
-          const double v = cval[c];
+          const float v = cval[c];
           const int r = crow[c];
           if (r >= 0 && (v > pb || (v == pb && r < pv))) { pb = v; pv = r; }
         }
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         if (jc < nb) {
           const float4 rk = rowk[jc];
           const bool cand = jc == k + 1;
-          double best = -1.0;
+          float best = -1.f;
           int bi = -1;
 #pragma unroll 2
           for (int i = rg; i < nb; i += nrg) {
@@ -678,7 +679,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
               if (cand) {
                 coln[i] = v;
                 if (i > k) {
-                  const double m = (double)fabsf(v.x) + (double)fabsf(v.y);
+                  const float m = fabsf(v.x) + fabsf(v.y);
                   if (m > best) { best = m; bi = i; }
                 }
               }
