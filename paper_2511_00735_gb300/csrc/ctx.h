@@ -156,7 +156,7 @@ struct hps_ctx {
   // preconditioned directions in FP32, a df64 copy of the leaf maps
   int outer_arith = HPS_OUTER_DEFAULT;
   bool fg_df = false;
-  float4 *df_V = nullptr, *df_x = nullptr, *df_w = nullptr, *df_part = nullptr, *df_T = nullptr;
+  float4 *df_V = nullptr, *df_x = nullptr, *df_w = nullptr, *df_rhs = nullptr, *df_part = nullptr, *df_T = nullptr;
   float4* df_coef = nullptr;       // Gram-Schmidt update coefficients [2 restart + 3][nrhs]
   float4* pin_coef = nullptr;      // pinned host mirror of df_coef
   float2* df_Z = nullptr;

@@ -55,7 +55,7 @@ bool use_df(const hps_ctx* c) {
 void free_fg(hps_ctx* c) {
   void** bufs[] = {(void**)&c->fg_V, (void**)&c->fg_Z, (void**)&c->fg_x, (void**)&c->fg_w, (void**)&c->fg_rhs,
                    (void**)&c->fg_t, (void**)&c->fg_h, (void**)&c->fg_part, (void**)&c->fg_y, (void**)&c->fg_floor,
-                   (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_part,
+                   (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_rhs, (void**)&c->df_part,
                    (void**)&c->df_T, (void**)&c->df_coef};
   for (void** b : bufs) {
     dev_free(c, *b);
@@ -94,10 +94,11 @@ int ensure_fg(hps_ctx* c, int restart, int nrhs, bool df) {
     c->df_Z = static_cast<float2*>(dev_alloc(c, sizeof(float2) * vs * restart));
     c->df_x = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
     c->df_w = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
+    c->df_rhs = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
     c->df_part = static_cast<float4*>(dev_alloc(c, sizeof(float4) * nblk * (2 * (restart + 1) + 1) * nrhs));
     c->df_T = static_cast<float4*>(dev_alloc(c, sizeof(float4) * (size_t)c->E * c->nb * c->nb));
     c->df_coef = static_cast<float4*>(dev_alloc(c, sizeof(float4) * (size_t)(2 * restart + 3) * nrhs));
-    ok = ok && c->df_V && c->df_Z && c->df_x && c->df_w && c->df_part && c->df_T && c->df_coef;
+    ok = ok && c->df_V && c->df_Z && c->df_x && c->df_w && c->df_rhs && c->df_part && c->df_T && c->df_coef;
   } else {
     c->fg_V = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * (restart + 1)));
     c->fg_Z = static_cast<double2*>(dev_alloc(c, sizeof(double2) * vs * restart));
@@ -279,6 +280,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->fg_t, c->fg_rhs, c->E, c->nb, nrhs, grid, st));
     if (df) HPS_CK(c, df_from_d(c->df_T, c->d_T, (long long)c->E * c->nb * c->nb, st));
   }
+  if (df) HPS_CK(c, df_from_d(c->df_rhs, c->fg_rhs, vs, st));
   double2* hbuf = c->fg_h;
   HPS_CK(c, bdot<double>(c->fg_rhs, 0, 1, c->fg_rhs, n, nrhs, c->fg_part, hbuf, 0, st));
   HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -289,20 +291,20 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   if (df) HPS_CK(c, cudaMemsetAsync(c->df_x, 0, sizeof(float4) * (size_t)vs, st));
   else HPS_CK(c, zero<double>(c->fg_x, vs, st));
 
-  // Explicit FP64 residual of the current iterate, its squared norms in hbuf[0..nrhs), and
-  // (df) the iterate in FP64 in pv_in.  The residual itself lands in fg_w (FP64) or pv_out (df).
+  // Explicit residual of the current iterate and its squared norms in hbuf[0..nrhs): FP64 in
+  // fg_w, or (df) double-float in df_w (products error-free, sums by TwoSum: about 48 bits,
+  // the residual's norm to ~1e-5 relative at a 1e-10 relative residual).
   auto residual = [&]() -> int {
     {
       PhaseScope ps(c, HPS_PH_MATVEC);
       if (df) {
-        HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
-        HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->pv_in, c->fg_rhs, c->pv_out, c->E, c->nb, nrhs, grid, st));
+        HPS_CK(c, df_matvec<float4>(c->df_T, c->d_es_nb, c->df_x, c->df_rhs, c->df_w, c->E, c->nb, nrhs, grid, st));
       } else {
         HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
       }
     }
-    const double2* w = df ? c->pv_out : c->fg_w;
-    HPS_CK(c, bdot<double>(w, 0, 1, w, n, nrhs, c->fg_part, hbuf, 0, st));
+    if (df) HPS_CK(c, df_bdot(c->df_w, 0, 1, c->df_w, n, nrhs, c->df_part, hbuf, st));
+    else HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
     HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
     HPS_CK(c, cudaStreamSynchronize(st));
     return HPS_OK;
@@ -383,7 +385,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
       if (all) break;
       fresh = false;
       HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-      HPS_CK(c, df_from_d(c->df_w, outer > 0 ? c->pv_out : c->fg_rhs, vs, st));
+      if (outer == 0) HPS_CK(c, cudaMemcpyAsync(c->df_w, c->df_rhs, sizeof(float4) * vs, cudaMemcpyDeviceToDevice, st));
       HPS_CK(c, df_bscale(c->df_V, c->df_w, hbuf, c->fg_floor, n, nrhs, st));
       bool any = true;
       for (int j = 0; j < restart && any; ++j) {
@@ -546,7 +548,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     fresh = false;
     HPS_CK(c, cudaMemcpyAsync(c->fg_floor, c->pin_floor, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
     if (df) {
-      HPS_CK(c, df_from_d(c->df_w, outer > 0 ? c->pv_out : c->fg_rhs, vs, st));
+      if (outer == 0) HPS_CK(c, cudaMemcpyAsync(c->df_w, c->df_rhs, sizeof(float4) * vs, cudaMemcpyDeviceToDevice, st));
       HPS_CK(c, df_bscale(c->df_V, c->df_w, hbuf, c->fg_floor, n, nrhs, st));
     } else {
       HPS_CK(c, bscale<double>(c->fg_V, outer > 0 ? c->fg_w : c->fg_rhs, hbuf, c->fg_floor, n, nrhs, st));
@@ -661,13 +663,12 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     else HPS_CK(c, (bupdate<double, double>(c->fg_x, c->fg_Z, vs, jdone, c->fg_y, n, nrhs, 1.0, st)));
   }
   PhaseScope ps_other(c, HPS_PH_OTHER);
-  // explicit FP64 residual of the returned iterate (already at hand when the last restart converged)
+  // explicit residual of the returned iterate (already at hand when the last restart converged)
   if (!fresh) {
     rc = residual();
     if (rc) return rc;
-  } else if (df) {
-    HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
   }
+  if (df) HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
   std::vector<double> nrm2(nrhs);
   for (int r = 0; r < nrhs; ++r) nrm2[r] = c->pin_h[r].x;
   // solution in skeleton order
