@@ -79,11 +79,15 @@ __global__ void __launch_bounds__(NT) es_rhs_kernel(const double2* __restrict__ 
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
     const long long base = (long long)e * nb;
     const double2* Te = T + (long long)e * nb * nb;
+    // elements without a side on the physical boundary contribute nothing (most of them)
+    int mine = 0;
+    for (int b = threadIdx.x; b < nb; b += NT) mine |= bdry[base + b] >= 0;
+    const bool touches = __syncthreads_or(mine) != 0;
     for (int l = threadIdx.x; l < nb * nrhs; l += NT) {
       const int a = l / nrhs, r = l % nrhs;
       const long long p = base + a;
       double2 acc = make_double2(0.0, 0.0);
-      if (nbr[p] >= 0) {
+      if (touches && nbr[p] >= 0) {
         for (int b = 0; b < nb; ++b) {
           const int bi = bdry[base + b];
           if (bi >= 0) cfma(acc, Te[(long long)a * nb + b], t[(long long)bi * nrhs + r]);
