@@ -101,15 +101,20 @@ void* dev_alloc(hps_ctx* c, size_t bytes) {
   return p;
 }
 
+// Frees an allocation of this context; a pointer the context does not hold (already
+// released, e.g. by hps_mesh's release of everything) is ignored, never freed twice.
 void dev_free(hps_ctx* c, void* p) {
   if (!p) return;
+  bool held = false;
   for (size_t i = 0; i < c->allocs.size(); ++i) {
     if (c->allocs[i].p == p) {
       c->bytes_held -= c->allocs[i].bytes;
       c->allocs.erase(c->allocs.begin() + i);
+      held = true;
       break;
     }
   }
+  if (!held) return;
   if (c->free_fn) c->free_fn(p, c->alloc_user);
   else cudaFree(p);
 }
@@ -132,16 +137,9 @@ template GemmDesc* dev_upload<GemmDesc>(hps_ctx*, const std::vector<GemmDesc>&);
   } while (0)
 
 void free_solver(hps_ctx* c) {
-  FREE(c->fg_V); FREE(c->fg_Z); FREE(c->fg_x); FREE(c->fg_w); FREE(c->fg_rhs); FREE(c->fg_t);
-  FREE(c->fg_h); FREE(c->fg_part); FREE(c->fg_y); FREE(c->fg_floor);
+  free_fg(c);  // the FGMRES workspace (FP64 and double-float buffers, pinned mirrors)
   FREE(c->pv_in); FREE(c->pv_out);
-  FREE(c->df_V); FREE(c->df_x); FREE(c->df_w); FREE(c->df_part); FREE(c->df_T); FREE(c->df_Z); FREE(c->df_coef);
-  if (c->pin_h) cudaFreeHost(c->pin_h);
-  if (c->pin_y) cudaFreeHost(c->pin_y);
-  if (c->pin_floor) cudaFreeHost(c->pin_floor);
-  if (c->pin_coef) cudaFreeHost(c->pin_coef);
-  c->pin_h = nullptr; c->pin_y = nullptr; c->pin_floor = nullptr; c->pin_coef = nullptr;
-  c->fg_restart = c->fg_nrhs = c->pv_nrhs = 0;
+  c->pv_nrhs = 0;
 }
 
 // The captured V-cycle graph, its stream and events; the handles are reset, so a later

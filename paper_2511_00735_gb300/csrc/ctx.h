@@ -130,6 +130,8 @@ struct hps_ctx {
   void *cg_V = nullptr, *cg_w = nullptr, *cg_W = nullptr, *cg_H = nullptr, *cg_h1 = nullptr, *cg_h2 = nullptr;
   void *cg_nrm = nullptr, *cg_y = nullptr, *cg_g = nullptr, *cg_s = nullptr, *cg_part = nullptr;
   void *cg_beta = nullptr, *cg_floor = nullptr, *cg_c = nullptr, *cg_inv = nullptr, *cg_cnt = nullptr;
+  long long cg_part_cap = 0;  // elements of cg_part
+  int cg_cnt_cap = 0;         // counters in cg_cnt
   // exact coarse scratch
   void *ex_r = nullptr, *ex_e = nullptr;
   int ex_nrhs = 0;
@@ -182,6 +184,7 @@ template <typename T> T* dev_upload(hps_ctx* c, const std::vector<T>& v);
 void free_tree(hps_ctx* c);     // numeric part and plan
 void free_numeric(hps_ctx* c);  // numeric part only (the plan stays)
 void free_solver(hps_ctx* c);
+void free_fg(hps_ctx* c);  // FGMRES workspace (solve.cu)
 void free_graph(hps_ctx* c);
 int ensure_sweep_buffers(hps_ctx* c, int nrhs);
 

@@ -526,12 +526,14 @@ int ensure_cg(hps_ctx* c, int k, int nrhs) {
   const int fb = cg_pass_blocks((long long)rows, nrhs);
   const size_t np = std::max((size_t)bdot_blocks((long long)rows), (size_t)fb + cg_groups(fb));
   c->cg_part = dev_alloc(c, cs * np * (k + 1) * nrhs);
+  c->cg_part_cap = (long long)np * (k + 1) * nrhs;
   c->cg_beta = dev_alloc(c, sizeof(R) * nrhs);
   c->cg_floor = dev_alloc(c, sizeof(R) * nrhs);
   c->cg_c = dev_alloc(c, sizeof(R) * (size_t)k * nrhs);
   c->cg_inv = dev_alloc(c, sizeof(R) * nrhs);
   const size_t ncnt = 1 + (size_t)cg_groups(fb);
   c->cg_cnt = dev_alloc(c, sizeof(unsigned) * ncnt);
+  c->cg_cnt_cap = (int)ncnt;
   for (void** b : bufs)
     if (!*b) return fail(c, HPS_ENOMEM, "coarse GMRES workspace");
   if (cudaMemsetAsync(c->cg_cnt, 0, sizeof(unsigned) * ncnt, c->stream) != cudaSuccess) return fail(c, HPS_ECUDA, "coarse GMRES counter");
@@ -606,6 +608,8 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
     p.k = k;
     p.part = part;
     p.cnt = static_cast<unsigned*>(c->cg_cnt);
+    p.part_cap = c->cg_part_cap;
+    p.cnt_cap = c->cg_cnt_cap;
     p.h1 = h1;
     p.h2 = h2;
     p.H = static_cast<C*>(c->cg_H);

@@ -481,13 +481,13 @@ __global__ void __launch_bounds__(NT) cg_pass_kernel(CgPass<R> p, int rpad) {
     C x, vj = czero<R>();
     if (MODE == CG_START) {
       const int m = p.nb[row];
-      x = m >= 0 ? p.g[(long long)m * p.nrhs + r] : czero<R>();
+      x = (m >= 0 && m < p.rows) ? p.g[(long long)m * p.nrhs + r] : czero<R>();
     } else if (MODE == CG_APPLY) {
       const R sc = p.inv[r];
       const C wl = p.w[l];
       const int m = p.nb[row];
       vj = cscale(wl, sc);
-      x = m >= 0 ? cscale(cadd(wl, p.W[(long long)m * p.nrhs + r]), sc) : czero<R>();
+      x = (m >= 0 && m < p.rows) ? cscale(cadd(wl, p.W[(long long)m * p.nrhs + r]), sc) : czero<R>();
       p.V[p.j * p.vs + l] = vj;
     } else {
       const C* hin = MODE == CG_PROJECT ? p.h1 : p.h2;
@@ -603,6 +603,8 @@ cudaError_t cg_pass(int mode, const CgPass<R>& p, cudaStream_t s) {
   while (rpad < p.nrhs) rpad <<= 1;
   const int nblk = cg_pass_blocks(p.rows, p.nrhs);
   const int nvec = (mode == CG_START || mode == CG_CLOSE) ? 1 : p.j + 1;
+  if ((long long)(nblk + cg_groups(nblk)) * nvec * p.nrhs > p.part_cap || 1 + cg_groups(nblk) > p.cnt_cap)
+    return cudaErrorInvalidValue;
   const size_t smem = (size_t)nvec * (NT / 32) * rpad * sizeof(c_t<R>);
   switch (mode) {
     case CG_START: cg_pass_kernel<R, CG_START><<<nblk, NT, smem, s>>>(p, rpad); break;

@@ -105,6 +105,8 @@ struct CgPass {
   int nrhs = 0, j = 0, k = 0;
   c_t<R>* part = nullptr;      // (cg_pass_blocks + its groups) * (j + 1) * nrhs
   unsigned* cnt = nullptr;     // 1 + groups counters, zero between launches
+  long long part_cap = 0;      // elements of part and of cnt (checked before every launch)
+  int cnt_cap = 0;
   c_t<R>*h1 = nullptr, *h2 = nullptr, *H = nullptr;
   R *beta = nullptr, *floor = nullptr, *inv = nullptr;
   R tol = 0;

@@ -23,6 +23,26 @@
 
 namespace hps {
 
+void free_fg(hps_ctx* c) {
+  void** bufs[] = {(void**)&c->fg_V, (void**)&c->fg_Z, (void**)&c->fg_x, (void**)&c->fg_w, (void**)&c->fg_rhs,
+                   (void**)&c->fg_t, (void**)&c->fg_h, (void**)&c->fg_part, (void**)&c->fg_y, (void**)&c->fg_floor,
+                   (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_rhs, (void**)&c->df_part,
+                   (void**)&c->df_T, (void**)&c->df_coef};
+  for (void** b : bufs) {
+    dev_free(c, *b);
+    *b = nullptr;
+  }
+  if (c->pin_h) cudaFreeHost(c->pin_h);
+  if (c->pin_y) cudaFreeHost(c->pin_y);
+  if (c->pin_floor) cudaFreeHost(c->pin_floor);
+  if (c->pin_coef) cudaFreeHost(c->pin_coef);
+  c->pin_h = c->pin_y = nullptr;
+  c->pin_floor = nullptr;
+  c->pin_coef = nullptr;
+  c->fg_restart = c->fg_nrhs = 0;
+}
+
+
 void subdomain_natural(const hps_ctx* c, int stage, int sub, std::vector<int>& out);
 
 namespace {
@@ -52,24 +72,6 @@ bool use_df(const hps_ctx* c) {
   return c->outer_arith == HPS_OUTER_DF64 || (c->outer_arith == HPS_OUTER_DEFAULT && c->precision == HPS_MIXED);
 }
 
-void free_fg(hps_ctx* c) {
-  void** bufs[] = {(void**)&c->fg_V, (void**)&c->fg_Z, (void**)&c->fg_x, (void**)&c->fg_w, (void**)&c->fg_rhs,
-                   (void**)&c->fg_t, (void**)&c->fg_h, (void**)&c->fg_part, (void**)&c->fg_y, (void**)&c->fg_floor,
-                   (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_rhs, (void**)&c->df_part,
-                   (void**)&c->df_T, (void**)&c->df_coef};
-  for (void** b : bufs) {
-    dev_free(c, *b);
-    *b = nullptr;
-  }
-  if (c->pin_h) cudaFreeHost(c->pin_h);
-  if (c->pin_y) cudaFreeHost(c->pin_y);
-  if (c->pin_floor) cudaFreeHost(c->pin_floor);
-  if (c->pin_coef) cudaFreeHost(c->pin_coef);
-  c->pin_h = c->pin_y = nullptr;
-  c->pin_floor = nullptr;
-  c->pin_coef = nullptr;
-  c->fg_restart = c->fg_nrhs = 0;
-}
 
 // FGMRES workspace for `restart` and `nrhs`; df selects the df64 basis (float pairs) and FP32 directions
 int ensure_fg(hps_ctx* c, int restart, int nrhs, bool df) {
