@@ -567,8 +567,11 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
       const double mz = block_max((double)mzf, red);
       const double rel = mz > 0.0 ? md / mz : 0.0;
       if (it > 0) {
+        // converged when the predicted next correction is below 1e-14 of Z, or when the
+        // corrections have stopped contracting at the double-float residual's floor
+        // (about cond(L~_ii) 2^-48: elements near the positive-definite bound reach it first)
         const double rho = fmax(rel / rel_prev, 1e-6);
-        done = rel * rho <= 1e-14;
+        done = rel * rho <= 1e-14 || (it >= 2 && rho >= 0.25 && rel <= 1e-10);
       }
       if (!(rel == rel)) done = false;
       rel_prev = rel > 0.0 ? rel : 1e-300;
