@@ -287,6 +287,10 @@ cudaError_t df_bdot(const float4* V, long long vstride, int nvec, const float4* 
 // df_dots2: D[2i] = sum conj(X_i) y0, D[2i+1] = sum conj(X_i) y1 (i < nvec, X_i = V + i*vstride)
 // and D[2 nvec] = sum conj(y1) y1, over rows, per right-hand side, FP64 result [2 nvec + 1][nrhs].
 // Groups of DG2 vectors per block (blockIdx.y); y0 and y1 are read once per group.
+// The y0 products (the tentative vector: the second Gram-Schmidt pass and its norm) are
+// accumulated in double-float; the y1 products (the new Krylov vector: first-pass
+// coefficients and its norm, whose errors the next step's second pass removes) in FP32 on the
+// leading parts.
 constexpr int DG2 = 8, NT2 = 128;
 __global__ void __launch_bounds__(NT2, 3) df_dots2_partial_kernel(const float4* __restrict__ V, long long vstride,
                                                                int nvec, const float4* __restrict__ y0,
@@ -299,7 +303,11 @@ __global__ void __launch_bounds__(NT2, 3) df_dots2_partial_kernel(const float4* 
   const bool extra = blockIdx.y == 0;
   const int nout = 2 * nvec + 1;
   const long long lo = blockIdx.x * chunk, hi = lo + chunk < rows ? lo + chunk : rows;
-  cacc a0[DG2], a1[DG2], ee;
+  cacc a0[DG2];
+  float2 a1[DG2];
+  float ee = 0.f;
+#pragma unroll
+  for (int g = 0; g < DG2; ++g) a1[g] = make_float2(0.f, 0.f);
   if (r < nrhs) {
     // the next row's values are loaded while the current row is accumulated
     float4 u0, u1, x[DG2], nu0, nu1, nx[DG2];
@@ -316,12 +324,13 @@ __global__ void __launch_bounds__(NT2, 3) df_dots2_partial_kernel(const float4* 
     for (; row < hi; row += rper) {
       const long long nrow = row + rper;
       if (nrow < hi) load(nrow, nu0, nu1, nx);
-      if (extra) cdot2_conj(ee, u1, u1);
+      if (extra) ee = fmaf(u1.x, u1.x, fmaf(u1.y, u1.y, ee));
 #pragma unroll
       for (int g = 0; g < DG2; ++g) {
         if (g < ng) {
           cdot2_conj(a0[g], x[g], u0);
-          cdot2_conj(a1[g], x[g], u1);
+          a1[g].x = fmaf(x[g].x, u1.x, fmaf(x[g].y, u1.y, a1[g].x));  // conj(x) u1, leading parts
+          a1[g].y = fmaf(x[g].x, u1.y, fmaf(-x[g].y, u1.x, a1[g].y));
         }
       }
       u0 = nu0;
@@ -333,9 +342,9 @@ __global__ void __launch_bounds__(NT2, 3) df_dots2_partial_kernel(const float4* 
 #pragma unroll
   for (int g = 0; g < DG2; ++g) {
     red[2 * g][threadIdx.x] = cfin(a0[g]);
-    red[2 * g + 1][threadIdx.x] = cfin(a1[g]);
+    red[2 * g + 1][threadIdx.x] = make_float4(a1[g].x, a1[g].y, 0.f, 0.f);
   }
-  red[2 * DG2][threadIdx.x] = cfin(ee);
+  red[2 * DG2][threadIdx.x] = make_float4(ee, 0.f, 0.f, 0.f);
   __syncthreads();
   for (int s2 = rper / 2; s2 > 0; s2 >>= 1) {
     if (lrow < s2) {
