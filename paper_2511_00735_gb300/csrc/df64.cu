@@ -44,6 +44,13 @@ __device__ __forceinline__ void cdot2(cacc& acc, float4 a, float4 b) {
   dot2(acc.is, acc.ic, a.x, a.z, b.y, b.w);
   dot2(acc.is, acc.ic, a.y, a.w, b.x, b.z);
 }
+// acc += a * b   (complex, a df64, b FP32)
+__device__ __forceinline__ void cdot2f(cacc& acc, float4 a, float2 b) {
+  dfops::dot2f(acc.rs, acc.rc, a.x, a.z, b.x);
+  dfops::dot2f(acc.rs, acc.rc, -a.y, -a.w, b.y);
+  dfops::dot2f(acc.is, acc.ic, a.x, a.z, b.y);
+  dfops::dot2f(acc.is, acc.ic, a.y, a.w, b.x);
+}
 // acc += conj(a) * b
 __device__ __forceinline__ void cdot2_conj(cacc& acc, float4 a, float4 b) {
   dot2(acc.rs, acc.rc, a.x, a.z, b.x, b.z);
@@ -165,11 +172,11 @@ __global__ void __launch_bounds__(NT) df_matvec_kernel(const float4* __restrict_
                                                        const X* __restrict__ x, const float4* __restrict__ c0,
                                                        float4* __restrict__ y, int E, int nb, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* xs = reinterpret_cast<float4*>(smem_raw);  // [nb][nrhs]
+  X* xs = reinterpret_cast<X*>(smem_raw);  // [nb][nrhs] this element's x (FP32 or df64 as given)
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
     __syncthreads();
     const long long base = (long long)e * nb;
-    for (int l = threadIdx.x; l < nb * nrhs; l += NT) xs[l] = ld(x, base * nrhs + l);
+    for (int l = threadIdx.x; l < nb * nrhs; l += NT) xs[l] = x[base * nrhs + l];
     __syncthreads();
     const float4* Te = T + (long long)e * nb * nb;
     for (int l = threadIdx.x; l < nb * nrhs; l += NT) {
@@ -178,10 +185,25 @@ __global__ void __launch_bounds__(NT) df_matvec_kernel(const float4* __restrict_
       const int q = nbr[p];
       float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
       if (q >= 0) {
-        cacc acc;
+        // two accumulators (even and odd b) halve the dependency chain through TwoSum
+        cacc acc, acc2;
         cadd2(acc, ld(x, (long long)q * nrhs + r));
         const float4* Tr = Te + (long long)a * nb;
-        for (int b = 0; b < nb; ++b) cdot2(acc, Tr[b], xs[b * nrhs + r]);
+        int b = 0;
+        for (; b + 1 < nb; b += 2) {
+          if constexpr (sizeof(X) == sizeof(float2)) {  // x FP32: no lo products
+            cdot2f(acc, Tr[b], xs[b * nrhs + r]);
+            cdot2f(acc2, Tr[b + 1], xs[(b + 1) * nrhs + r]);
+          } else {
+            cdot2(acc, Tr[b], xs[b * nrhs + r]);
+            cdot2(acc2, Tr[b + 1], xs[(b + 1) * nrhs + r]);
+          }
+        }
+        if (b < nb) {
+          if constexpr (sizeof(X) == sizeof(float2)) cdot2f(acc, Tr[b], xs[b * nrhs + r]);
+          else cdot2(acc, Tr[b], xs[b * nrhs + r]);
+        }
+        cadd2(acc, cfin(acc2));
         if (c0) {
           const float4 cv = c0[p * nrhs + r];
           acc.rs = -acc.rs; acc.rc = -acc.rc; acc.is = -acc.is; acc.ic = -acc.ic;
@@ -197,7 +219,7 @@ __global__ void __launch_bounds__(NT) df_matvec_kernel(const float4* __restrict_
 template <typename X>
 cudaError_t df_matvec(const float4* T, const int* nbr, const X* x, const float4* c0, float4* y, int E, int nb, int nrhs,
                       int grid, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * (size_t)nb * nrhs;
+  const size_t smem = sizeof(X) * (size_t)nb * nrhs;
   df_matvec_kernel<X><<<grid, NT, smem, s>>>(T, nbr, x, c0, y, E, nb, nrhs);
   note_launch();
   return cudaGetLastError();

@@ -32,6 +32,17 @@ __device__ __forceinline__ void dot2(float& s, float& c, float ah, float al, flo
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
+// (s, c) += a * b for df64 a = (ah, al) and FP32 b
+__device__ __forceinline__ void dot2f(float& s, float& c, float ah, float al, float b) {
+  const float p = __fmul_rn(ah, b);
+  float e = __fmaf_rn(ah, b, -p);
+  e = __fmaf_rn(al, b, e);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
 // normalise (s, c) into (hi, lo)
 __device__ __forceinline__ void fast2(float s, float c, float& hi, float& lo) { two_sum(s, c, hi, lo); }
 
