@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
 // Gauss-Jordan inverse are as in leaf_kernel.
 // ---------------------------------------------------------------------------
 constexpr int IR_MAX = 10;
-constexpr int TB = 32;     // row block of the triangular solves
+constexpr int TB = 16;     // row block of the triangular solves
 constexpr int PB = 16;     // panel width of the FP32 L D L^T
 constexpr int IR_NT = 512;  // threads per CTA
 
