@@ -35,7 +35,7 @@ FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (nominal, vector = tensor rate)
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # dram read + write bytes of one leaf_ir_kernel launch at 64x64, N=16 from the committed ncu capture
 # (profiles/leaf_ir_kernel_64x64_N16.md); None until captured and whenever leaf.cu changes.
-LEAF_TRAFFIC_BYTES = 210.6e6
+LEAF_TRAFFIC_BYTES = 209.3e6  # ncu: dram read + write of one leaf_ir_kernel launch, 64x64, N=16
 
 
 def load_peaks():
@@ -464,7 +464,8 @@ def main():
                                "bound": "alu", "achieved": f32 / (per / 1e3) / 1e12,
                                "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                                "frac": f32 / (per / 1e3) / FP32_PEAK_NOMINAL,
-                               "traffic": None,
+                               "traffic": LEAF_TRAFFIC_BYTES if prob.nx == 64 and N == 16 else None,
+                               "traffic_unit": "bytes per launch (ncu dram read + write)",
                                "flops_per_launch": f32, "ms_per_launch": per,
                                "paper_literal_flops_per_launch": lit,
                                "paper_literal_rate_tflops": lit / (per / 1e3) / 1e12,
