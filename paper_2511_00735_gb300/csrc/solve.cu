@@ -390,9 +390,47 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
       if (outer == 0) HPS_CK(c, cudaMemcpyAsync(c->df_w, c->df_rhs, sizeof(float4) * vs, cudaMemcpyDeviceToDevice, st));
       HPS_CK(c, df_bscale(c->df_V, c->df_w, hbuf, c->fg_floor, n, nrhs, st));
       bool any = true;
+      // When every active right-hand side is predicted to converge as column j-1 closes, step
+      // j first closes it from the second-pass reduction alone, without preconditioning vt_j;
+      // closed[r] marks a column already closed that way if the prediction fails.
+      bool pred_close = false;
+      std::vector<char> closed(nrhs, 0);
       for (int j = 0; j < restart && any; ++j) {
         float4* Vt = c->df_V + (size_t)j * vs;
         float2* Zj = c->df_Z + (size_t)j * vs;
+        if (pred_close) {
+          pred_close = false;
+          {
+            PhaseScope ps(c, HPS_PH_ORTHO);
+            HPS_CK(c, df_dots2(c->df_V, vs, j + 1, Vt, Vt, n, nrhs, c->df_part, hbuf, st));
+          }
+          HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * (size_t)(2 * (j + 1) + 1) * nrhs,
+                                    cudaMemcpyDeviceToHost, st));
+          HPS_CK(c, cudaStreamSynchronize(st));
+          bool all_conv = true;
+          for (int r = 0; r < nrhs; ++r) {
+            if (!active[r]) continue;
+            auto D = [&](int k) { const double2 v = c->pin_h[(size_t)k * nrhs + r]; return cd(v.x, v.y); };
+            cd* Hr = &H[(size_t)r * (restart + 1) * restart];
+            const cd* ht = &htent[(size_t)r * (restart + 1)];
+            double sa = 0.0;
+            for (int i = 0; i < j; ++i) sa += std::norm(D(2 * i));
+            const double rho = std::sqrt(std::max(0.0, D(2 * j).real() - sa));
+            for (int i = 0; i < j; ++i) Hr[(size_t)i * restart + (j - 1)] = ht[i] + nu_prev[r] * D(2 * i);
+            const double hn = nu_prev[r] * rho;
+            rotate(r, j - 1, hn);
+            its[r] += 1;
+            steps[r] = j;
+            res[r] = bnorm[r] > 0 ? std::abs(g[(size_t)r * (restart + 1) + j]) / bnorm[r] : 0.0;
+            closed[r] = 1;
+            if (res[r] <= tol || hn <= 1e-300) active[r] = 0;
+            else all_conv = false;
+          }
+          if (all_conv) {
+            any = false;
+            break;
+          }
+        }
         {
           PhaseScope ps(c, HPS_PH_PRECOND);
           if (inner_iters < 0) HPS_CK(c, df_swap_hi(Zj, Vt, c->d_es_nb, n, nrhs, st));
@@ -410,6 +448,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
                                   cudaMemcpyDeviceToHost, st));
         HPS_CK(c, cudaStreamSynchronize(st));
         any = false;
+        bool pred_ok = true;
         const int rows_coef = 2 * j + 3;
         for (int r = 0; r < nrhs; ++r) {
           auto D = [&](int k) { const double2 v = c->pin_h[(size_t)k * nrhs + r]; return cd(v.x, v.y); };
@@ -425,7 +464,9 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
           double sa = 0.0;
           for (int i = 0; i < j; ++i) sa += std::norm(D(2 * i));
           const double rho = std::sqrt(std::max(0.0, D(2 * j).real() - sa));
-          if (j > 0) {  // close column j - 1
+          if (j > 0 && closed[r]) {
+            closed[r] = 0;  // closed at the start of this step (a prediction that failed)
+          } else if (j > 0) {  // close column j - 1
             for (int i = 0; i < j; ++i) Hr[(size_t)i * restart + (j - 1)] = ht[i] + nu_prev[r] * D(2 * i);
             const double hn = nu_prev[r] * rho;
             rotate(r, j - 1, hn);
@@ -472,8 +513,20 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
           c->pin_coef[(size_t)(2 * j + 2) * nrhs + r] = to_df(-gam / nu);
           nu_prev[r] = nu;
           any = true;
+          // predicted residual once column j closes: the tentative column through the rotations
+          // so far, subdiagonal nu (the second pass changes both by about the first pass's error)
+          {
+            const double* csr = &cs[(size_t)r * restart];
+            const cd* snr = &sn[(size_t)r * restart];
+            cd a = ht[0];
+            for (int i = 0; i < j; ++i) a = csr[i] * ht[i + 1] - std::conj(snr[i]) * a;
+            const double gmag = std::abs(g[(size_t)r * (restart + 1) + j]);
+            const double pres = bnorm[r] > 0 ? gmag * nu / std::hypot(std::abs(a), nu) / bnorm[r] : 0.0;
+            pred_ok = pred_ok && pres <= 0.999 * tol;
+          }
         }
         if (!any) break;
+        pred_close = pred_ok;
         HPS_CK(c, cudaMemcpyAsync(c->df_coef, c->pin_coef, sizeof(float4) * (size_t)rows_coef * nrhs,
                                   cudaMemcpyHostToDevice, st));
         PhaseScope ps(c, HPS_PH_ORTHO);
