@@ -606,7 +606,7 @@ int hps_build_leaves(hps_ctx* c, int precision) {
   if (!good.empty()) {
     const int grid = std::min((int)good.size(), std::max(1, c->num_sms));
     double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
-    double* Zscr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * p.ni * c->nb));
+    double* Zscr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * 2 * p.ni * c->nb));
     int* d_good = good.size() == (size_t)c->E ? nullptr : dev_upload(c, good);
     if (!Ascr || !Zscr || (good.size() != (size_t)c->E && !d_good)) return fail(c, HPS_ENOMEM, "leaf scratch");
     scratch.push_back(Ascr);
@@ -735,7 +735,7 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
       const int grid = std::min(count, std::max(1, c0->num_sms));
       LeafElem* d_ed = static_cast<LeafElem*>(dev_alloc(c0, sizeof(LeafElem) * groups[N].size()));
       double* Ascr = static_cast<double*>(dev_alloc(c0, sizeof(double) * (size_t)grid * nb * nb));
-      double* Zscr = static_cast<double*>(dev_alloc(c0, sizeof(double) * (size_t)grid * (N - 1) * (N - 1) * nb));
+      double* Zscr = static_cast<double*>(dev_alloc(c0, sizeof(double) * (size_t)grid * 2 * (N - 1) * (N - 1) * nb));
       if (!d_ed || !Ascr || !Zscr) return fail(c0, HPS_ENOMEM, "batched leaf workspace");
       scratch.push_back(d_ed);
       scratch.push_back(Ascr);

@@ -297,7 +297,8 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   const int tid = threadIdx.x, nth = blockDim.x;
   double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
   // the refinement's iterate Z in double-float (the FP64 scratch holds the pairs)
-  float2* Zd = reinterpret_cast<float2*>(p.Zscr + (long long)blockIdx.x * ni * nb);
+  float2* Zd = reinterpret_cast<float2*>(p.Zscr + (long long)blockIdx.x * 2 * ni * nb);
+  float2* S1 = Zd + (long long)ni * nb;  // [ni][nb] first Kronecker sum of the residual, double-float
   auto to_df = [](double v) {
     const float h = (float)v;
     return make_float2(h, (float)(v - (double)h));
@@ -426,38 +427,75 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
     bool done = false;
     for (int it = 0; it < IR_MAX && !done; ++it) {
       // residual in double-float (error-free products, TwoSum accumulation: about 48 bits on the
-      // FP32 pipes), rounded into Y
-      for (int l = tid; l < ni * nb; l += nth) {
-        const int I = l / nb, g = l % nb;
-        const int i = I / q + 1, j = I % q + 1;
-        const int side = g / q, s = g % q + 1;
-        float rs = 0.f, rc = 0.f;  // boundary coupling K_b w_s, then minus L~_ii Z
-        {
-          float2 kb = make_float2(0.f, 0.f);
-          if (side == 0 && j == s) kb = sKd[i * n1 + 0];
-          else if (side == 1 && j == s) kb = sKd[i * n1 + N];
-          else if (side == 2 && i == s) kb = sKd[j * n1 + 0];
-          else if (side == 3 && i == s) kb = sKd[j * n1 + N];
-          const float2 ws = swd[s];
-          dfops::dot2(rs, rc, kb.x, kb.y, ws.x, ws.y);
-        }
-        if (it > 0) {
-          float s1s = 0.f, s1c = 0.f, s2s = 0.f, s2c = 0.f;
-          for (int t = 1; t <= q; ++t) {
-            const float2 ka = sKd[i * n1 + t], za = Zd[(long long)((t - 1) * q + (j - 1)) * nb + g];
-            dfops::dot2(s1s, s1c, ka.x, ka.y, za.x, za.y);
-            const float2 kb = sKd[j * n1 + t], zb = Zd[(long long)((i - 1) * q + (t - 1)) * nb + g];
-            dfops::dot2(s2s, s2c, kb.x, kb.y, zb.x, zb.y);
+      // FP32 pipes), rounded into Y:
+      //   r(i,j,g) = K_b w_s - w_j sum_t K[i][t] Z(t,j,g) - w_i sum_t K[j][t] Z(i,t,g) + c_ij Z(i,j,g).
+      // The first sum runs over one column (j, g) of Z, the second over one row (i, g): a thread
+      // keeps that line of Z in registers and forms all q sums from it; the first sums go
+      // through global scratch (S1) to the thread of the matching row.
+      constexpr int QMAX = 15;  // q <= 15 (N <= 16)
+      if (it > 0) {
+        for (int l = tid; l < q * nb; l += nth) {
+          const int j = l / nb + 1, g = l % nb;
+          float2 zc[QMAX];
+#pragma unroll
+          for (int t = 0; t < QMAX; ++t)
+            if (t < q) zc[t] = Zd[(long long)(t * q + (j - 1)) * nb + g];
+          for (int i = 1; i <= q; ++i) {
+            float ss = 0.f, sc2 = 0.f;
+#pragma unroll
+            for (int t = 0; t < QMAX; ++t)
+              if (t < q) {
+                const float2 ka = sKd[i * n1 + t + 1];
+                dfops::dot2(ss, sc2, ka.x, ka.y, zc[t].x, zc[t].y);
+              }
+            float2 o;
+            dfops::fast2(ss, sc2, o.x, o.y);
+            S1[(long long)((i - 1) * q + (j - 1)) * nb + g] = o;
           }
-          float s1h, s1l, s2h, s2l;
-          dfops::fast2(s1s, s1c, s1h, s1l);
-          dfops::fast2(s2s, s2c, s2h, s2l);
-          const float2 wj = swd[j], wi = swd[i], cw = cwd[i * n1 + j], zi = Zd[(long long)I * nb + g];
-          dfops::dot2(rs, rc, -wj.x, -wj.y, s1h, s1l);
-          dfops::dot2(rs, rc, -wi.x, -wi.y, s2h, s2l);
-          dfops::dot2(rs, rc, cw.x, cw.y, zi.x, zi.y);
         }
-        Y[I * ldy + g] = __fadd_rn(rs, rc);
+        __syncthreads();
+      }
+      for (int l = tid; l < q * nb; l += nth) {
+        const int i = l / nb + 1, g = l % nb;
+        const int side = g / q, s = g % q + 1;
+        float2 zr[QMAX];
+        if (it > 0) {
+#pragma unroll
+          for (int t = 0; t < QMAX; ++t)
+            if (t < q) zr[t] = Zd[(long long)((i - 1) * q + t) * nb + g];
+        }
+        for (int j = 1; j <= q; ++j) {
+          const int I = (i - 1) * q + (j - 1);
+          float rs = 0.f, rc = 0.f;  // boundary coupling K_b w_s, then minus L~_ii Z
+          {
+            float2 kb = make_float2(0.f, 0.f);
+            if (side == 0 && j == s) kb = sKd[i * n1 + 0];
+            else if (side == 1 && j == s) kb = sKd[i * n1 + N];
+            else if (side == 2 && i == s) kb = sKd[j * n1 + 0];
+            else if (side == 3 && i == s) kb = sKd[j * n1 + N];
+            const float2 ws = swd[s];
+            dfops::dot2(rs, rc, kb.x, kb.y, ws.x, ws.y);
+          }
+          if (it > 0) {
+            float s2s = 0.f, s2c = 0.f;
+            float2 zij = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < QMAX; ++t)
+              if (t < q) {
+                const float2 kb = sKd[j * n1 + t + 1];
+                dfops::dot2(s2s, s2c, kb.x, kb.y, zr[t].x, zr[t].y);
+                if (t == j - 1) zij = zr[t];
+              }
+            float s2h, s2l;
+            dfops::fast2(s2s, s2c, s2h, s2l);
+            const float2 s1 = S1[(long long)I * nb + g];
+            const float2 wj = swd[j], wi = swd[i], cw = cwd[i * n1 + j];
+            dfops::dot2(rs, rc, -wj.x, -wj.y, s1.x, s1.y);
+            dfops::dot2(rs, rc, -wi.x, -wi.y, s2h, s2l);
+            dfops::dot2(rs, rc, cw.x, cw.y, zij.x, zij.y);
+          }
+          Y[I * ldy + g] = __fadd_rn(rs, rc);
+        }
       }
       __syncthreads();
       // forward U y = r, diagonal, backward U^T x = z, by row blocks of TB: the rows above

@@ -26,8 +26,9 @@ struct LeafParams {
   int count = 0;
   const LeafElem* ed = nullptr;  // optional per-element descriptors (count entries, several problems);
                                  // then c, T, h, eta above are ignored
-  double* Zscr = nullptr;        // [gridDim.x][ni][nb] per-CTA FP64 workspace: selects the refined
-                                 // FP32 factorisation (leaf_ir_smem_bytes); null: the FP64 one
+  double* Zscr = nullptr;        // [gridDim.x][2][ni][nb] per-CTA workspace (the double-float iterate Z
+                                 // and the residual's first Kronecker sums): selects the refined FP32
+                                 // factorisation (leaf_ir_smem_bytes); null: the FP64 one
 };
 size_t leaf_ir_smem_bytes(int N);
 size_t leaf_smem_bytes(int N, int cw);
