@@ -35,7 +35,7 @@ FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (nominal, vector = tensor rate)
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # dram read + write bytes of one leaf_ir_kernel launch at 64x64, N=16 from the committed ncu capture
 # (profiles/leaf_ir_kernel_64x64_N16.md); None until captured and whenever leaf.cu changes.
-LEAF_TRAFFIC_BYTES = 209.3e6  # ncu: dram read + write of one leaf_ir_kernel launch, 64x64, N=16
+LEAF_TRAFFIC_BYTES = 225.0e6  # ncu: dram read + write of one leaf_ir_kernel launch, 64x64, N=16
 
 
 def load_peaks():
