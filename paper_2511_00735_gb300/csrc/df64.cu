@@ -409,7 +409,8 @@ cudaError_t df_dots2(const float4* V, long long vstride, int nvec, const float4*
   return cudaGetLastError();
 }
 
-// df_update2: out_v = sv vt + sum_{i<nvec} ca_i V_i  and  out_w = sw w + svw vt + sum_{i<nvec} cb_i V_i,
+// df_update2: out_v = sv vt + sum_{i<nvec} ca_i V_i  and  out_w = sw w + svw vt + sum_{i<nvec} cb_i V_i
+// (the ca products in FP32: they are second-pass corrections of the first pass's error size),
 // coefficients df64 in global memory [2 nvec + 3][nrhs]: ca (nvec rows), cb (nvec rows), sv, sw, svw.
 // out_v may be vt itself (each element is read before it is written, by the same thread).
 __global__ void df_update2_kernel(const float4* __restrict__ V, long long vstride, int nvec, const float4* vt,
@@ -426,11 +427,17 @@ __global__ void df_update2_kernel(const float4* __restrict__ V, long long vstrid
     cdot2(av, __ldg(sc + r), x);
     cdot2(aw, __ldg(sc + nrhs + r), y);
     cdot2(aw, __ldg(sc + 2 * nrhs + r), x);
+    // the second-pass coefficients ca are of the size of the first pass's error, so their
+    // products need only FP32 (leading parts): the sum enters the double-float result once
+    float2 pv = make_float2(0.f, 0.f);
     for (int i = 0; i < nvec; ++i) {
       const float4 v = V[i * vstride + l];
-      cdot2(av, __ldg(ca + (long long)i * nrhs + r), v);
+      const float4 a = __ldg(ca + (long long)i * nrhs + r);
+      pv.x = fmaf(a.x, v.x, fmaf(-a.y, v.y, pv.x));
+      pv.y = fmaf(a.x, v.y, fmaf(a.y, v.x, pv.y));
       cdot2(aw, __ldg(cb + (long long)i * nrhs + r), v);
     }
+    cadd2(av, make_float4(pv.x, pv.y, 0.f, 0.f));
     out_v[l] = cfin(av);
     out_w[l] = cfin(aw);
   }
