@@ -116,21 +116,38 @@ cudaError_t df_gather_hi(float2* dst, const float4* src, const int* map, long lo
 }
 
 // the same with the source pointer read from device memory (graph-replayable with a new source)
+// Gathers and scatters take GU elements per thread per pass (indices, then loads, then stores,
+// each GU independent), so a thread has GU dependent map -> data chains in flight.
+constexpr int GU = 4;
+
 __global__ void df_gather_hi_ind_kernel(float2* __restrict__ dst, const float4* const* __restrict__ srcp,
                                         const int* __restrict__ map, long long rows, int nrhs) {
-  const float4* src = *srcp;
-  const long long tot = rows * nrhs;
-  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
-    const long long row = l / nrhs;
-    const int r = (int)(l % nrhs);
-    const int m = map[row];
-    const float4 v = m >= 0 ? src[(long long)m * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-    dst[l] = make_float2(v.x, v.y);
+  // the leading FP32 pair of each double-float complex (8-byte loads)
+  const float2* src = reinterpret_cast<const float2*>(*srcp);
+  const long long tot = rows * nrhs, stride = (long long)gridDim.x * NT;
+  for (long long l0 = blockIdx.x * (long long)NT + threadIdx.x; l0 < tot; l0 += GU * stride) {
+    int m[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      m[u] = l < tot ? map[l / nrhs] : -1;
+    }
+    float2 v[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      v[u] = m[u] >= 0 ? src[2 * ((long long)m[u] * nrhs + l % nrhs)] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      if (l < tot) dst[l] = v[u];
+    }
   }
 }
 cudaError_t df_gather_hi_ind(float2* dst, const float4* const* srcp, const int* map, long long rows, int nrhs,
                              cudaStream_t s) {
-  df_gather_hi_ind_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(dst, srcp, map, rows, nrhs);
+  df_gather_hi_ind_kernel<<<nblocks((rows * nrhs + GU - 1) / GU, 8192), NT, 0, s>>>(dst, srcp, map, rows, nrhs);
   note_launch();
   return cudaGetLastError();
 }
@@ -149,17 +166,26 @@ cudaError_t set_pointers(void** dst, const void* a, void* b, cudaStream_t s) {
 __global__ void scatter_f2_ind_kernel(float2* const* __restrict__ dstp, const float2* __restrict__ src,
                                       const int* __restrict__ map, long long rows, int nrhs) {
   float2* dst = *dstp;
-  const long long tot = rows * nrhs;
-  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
-    const long long row = l / nrhs;
-    const int r = (int)(l % nrhs);
-    const int m = map[row];
-    if (m >= 0) dst[(long long)m * nrhs + r] = src[l];
+  const long long tot = rows * nrhs, stride = (long long)gridDim.x * NT;
+  for (long long l0 = blockIdx.x * (long long)NT + threadIdx.x; l0 < tot; l0 += GU * stride) {
+    int m[GU];
+    float2 v[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      m[u] = l < tot ? map[l / nrhs] : -1;
+      v[u] = l < tot ? src[l] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      if (m[u] >= 0) dst[(long long)m[u] * nrhs + l % nrhs] = v[u];
+    }
   }
 }
 cudaError_t scatter_f2_ind(float2* const* dstp, const float2* src, const int* map, long long rows, int nrhs,
                            cudaStream_t s) {
-  scatter_f2_ind_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(dstp, src, map, rows, nrhs);
+  scatter_f2_ind_kernel<<<nblocks((rows * nrhs + GU - 1) / GU, 8192), NT, 0, s>>>(dstp, src, map, rows, nrhs);
   note_launch();
   return cudaGetLastError();
 }

@@ -108,41 +108,67 @@ cudaError_t es_rhs(const double2* T, const int* nbr, const int* bdry, const doub
 // ---------------------------------------------------------------------------
 // Layout changes.
 // ---------------------------------------------------------------------------
+// Gathers and scatters take GU elements per thread per pass (indices, then loads, then stores,
+// each GU independent), so a thread has GU dependent map -> data chains in flight.
+constexpr int GU = 4;
+
 template <typename RS, typename RD>
 __global__ void gather_rows_kernel(c_t<RD>* __restrict__ dst, const c_t<RS>* __restrict__ src, const int* __restrict__ map,
                                    long long rows, int nrhs) {
-  const long long tot = rows * nrhs;
-  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
-    const long long row = l / nrhs;
-    const int r = (int)(l % nrhs);
-    const int m = map[row];
-    dst[l] = m >= 0 ? cvt<RD, RS>(src[(long long)m * nrhs + r]) : czero<RD>();
+  const long long tot = rows * nrhs, stride = (long long)gridDim.x * NT;
+  for (long long l0 = blockIdx.x * (long long)NT + threadIdx.x; l0 < tot; l0 += GU * stride) {
+    int m[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      m[u] = l < tot ? map[l / nrhs] : -1;
+    }
+    c_t<RD> v[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      v[u] = m[u] >= 0 ? cvt<RD, RS>(src[(long long)m[u] * nrhs + l % nrhs]) : czero<RD>();
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      if (l < tot) dst[l] = v[u];
+    }
   }
 }
 
 template <typename RS, typename RD>
 __global__ void scatter_rows_kernel(c_t<RD>* __restrict__ dst, const c_t<RS>* __restrict__ src, const int* __restrict__ map,
                                     long long rows, int nrhs) {
-  const long long tot = rows * nrhs;
-  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
-    const long long row = l / nrhs;
-    const int r = (int)(l % nrhs);
-    const int m = map[row];
-    if (m >= 0) dst[(long long)m * nrhs + r] = cvt<RD, RS>(src[l]);
+  const long long tot = rows * nrhs, stride = (long long)gridDim.x * NT;
+  for (long long l0 = blockIdx.x * (long long)NT + threadIdx.x; l0 < tot; l0 += GU * stride) {
+    int m[GU];
+    c_t<RS> v[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      m[u] = l < tot ? map[l / nrhs] : -1;
+      v[u] = l < tot ? src[l] : czero<RS>();
+    }
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const long long l = l0 + u * stride;
+      if (m[u] >= 0) dst[(long long)m[u] * nrhs + l % nrhs] = cvt<RD, RS>(v[u]);
+    }
   }
 }
 
 template <typename RS, typename RD>
 cudaError_t gather_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  gather_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  gather_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT * GU, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
   note_launch();
   return cudaGetLastError();
 }
 template <typename RS, typename RD>
 cudaError_t scatter_rows(c_t<RD>* dst, const c_t<RS>* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  scatter_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
+  scatter_rows_kernel<RS, RD><<<nblocks(rows * nrhs, NT * GU, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
   note_launch();
   return cudaGetLastError();
 }
