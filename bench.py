@@ -139,10 +139,11 @@ def run_gpu(args, rank, world, local_rank, dist):
 
     from paper_2511_00735_gb300 import hps as H
     from paper_2511_00735_gb300 import inputs
+    from paper_2511_00735_gb300 import replicas as RP
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    prob = inputs.fp64_64x64(seed=1 + rank, nrhs=args.nrhs)
+    prob = inputs.fp64_64x64(seed=RP.seed_for_rank(rank), nrhs=args.nrhs)
     prec = H.HPS_MIXED if args.precision == "mixed" else H.HPS_FP64
     s = H.Solver(local_rank)
     s.set_outer_arith({"default": H.OUTER_DEFAULT, "fp64": H.OUTER_FP64, "df64": H.OUTER_DF64}[args.outer])
@@ -161,29 +162,10 @@ def run_gpu(args, rank, world, local_rank, dist):
         _, info = s.gmres_solve(t, tol=args.tol, inner_iters=prob.inner_iters, restart=60, max_outer=20, out=out)
         return info
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        v = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        return float(v.item())
-
     def timed(fn, k):
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        w0 = time.perf_counter()
-        e0.record(stream)
-        out = [fn() for _ in range(k)]
-        e1.record(stream)
-        barrier()
-        wall = time.perf_counter() - w0
-        return max_over_ranks(e0.elapsed_time(e1)), max_over_ranks(wall * 1e3), out
+        # barrier + synchronize on both sides, CUDA events on the launching stream, max over ranks
+        return RP.timed(fn, k, RP.CudaEventClock(stream), dist=dist, sync=lambda: torch.cuda.synchronize(dev),
+                        device=dev)
 
     for _ in range(args.warmup):
         step(prec, b_dev, t_dev, g_dev)
@@ -198,7 +180,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     launches = H.kernel_launches() - l0
     clk = clocks.stop()
     nrhs = prob.nrhs
-    value = args.steps * nrhs * world / (ms / 1e3)
+    value = RP.job_throughput(nrhs, args.steps, world, ms)
     its = max(i["outer_iterations"] for i in infos)
     res = max(i["max_rel_residual"] for i in infos)
     conv = min(i["converged"] for i in infos)
