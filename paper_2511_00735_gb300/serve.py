@@ -82,9 +82,13 @@ class _Tree:
 
 class Server:
     def __init__(self, device: int = 0, workers: int = 4, precision: int = H.HPS_MIXED, tol: float = 1e-10,
-                 hbm_cap: float = 150e9, max_rhs: int = 64, restart: int = 60, max_outer: int = 20):
-        import torch
-
+                 hbm_cap: float = 150e9, max_rhs: int = 64, restart: int = 60, max_outer: int = 20,
+                 torch_module=None):
+        # torch_module: the device runtime (torch by default; the host-logic tests pass a stand-in
+        # with the few torch.cuda calls used here)
+        if torch_module is None:
+            import torch as torch_module
+        torch = torch_module
         self.torch = torch
         self.device = device
         self.precision = precision
