@@ -22,9 +22,11 @@ from . import inputs
 
 class BatchRunner:
     def __init__(self, device: int = 0, slots: int = 8, precision: int = H.HPS_MIXED, tol: float = 1e-10,
-                 restart: int = 60, max_outer: int = 20):
-        import torch
-
+                 restart: int = 60, max_outer: int = 20, torch_module=None):
+        # torch_module: the device runtime (torch by default; the host-logic tests pass a stand-in)
+        if torch_module is None:
+            import torch as torch_module
+        torch = torch_module
         self.torch = torch
         self.device = device
         self.precision = precision
