@@ -99,8 +99,10 @@ def test_real_eta_without_i_fails():
 
 @pytest.mark.parametrize("kh", [0.5, 2.5])
 def test_energy_and_unimodular_eigenvalues(kh):
-    # b = 0: the ItI map conserves the edge-weighted energy of plane-wave traces and
-    # its eigenvalues lie on the unit circle up to discretisation error (reading A10)
+    # b = 0: the ItI map conserves the edge-weighted energy of plane-wave traces (to 1e-12 at
+    # N = 16) and its eigenvalues lie on the unit circle up to discretisation error; it is not
+    # unitary as an operator (the edge-weighted singular values spread over [0.75, 1.35]),
+    # reading A10
     N, h = 16, 0.25
     kappa = kh / h
     _, w = gll_rule(N)
@@ -111,7 +113,7 @@ def test_energy_and_unimodular_eigenvalues(kh):
         fin, _ = _traces(N, h, kappa, kappa, th)
         ein = np.sqrt(np.sum(W * abs(fin) ** 2))
         eout = np.sqrt(np.sum(W * abs(T @ fin) ** 2))
-        assert abs(eout / ein - 1) < 1e-10
+        assert abs(eout / ein - 1) < 1e-12
     ev = np.linalg.eigvals(T)
     assert np.all(abs(abs(ev) - 1) < 1e-2)
 
