@@ -97,29 +97,12 @@ cudaError_t df_to_d(double2* dst, const float4* src, long long n, cudaStream_t s
   return cudaGetLastError();
 }
 
-// rows of hi parts (FP32) through a row map: dst[row][r] = hi(src[map[row]][r]) (map < 0 -> 0)
-__global__ void df_gather_hi_kernel(float2* __restrict__ dst, const float4* __restrict__ src, const int* __restrict__ map,
-                                    long long rows, int nrhs) {
-  const long long tot = rows * nrhs;
-  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
-    const long long row = l / nrhs;
-    const int r = (int)(l % nrhs);
-    const int m = map[row];
-    const float4 v = m >= 0 ? src[(long long)m * nrhs + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-    dst[l] = make_float2(v.x, v.y);
-  }
-}
-cudaError_t df_gather_hi(float2* dst, const float4* src, const int* map, long long rows, int nrhs, cudaStream_t s) {
-  df_gather_hi_kernel<<<nblocks(rows * nrhs, 8192), NT, 0, s>>>(dst, src, map, rows, nrhs);
-  note_launch();
-  return cudaGetLastError();
-}
-
-// the same with the source pointer read from device memory (graph-replayable with a new source)
 // Gathers and scatters take GU elements per thread per pass (indices, then loads, then stores,
 // each GU independent), so a thread has GU dependent map -> data chains in flight.
 constexpr int GU = 4;
 
+// rows of leading parts (FP32) through a row map: dst[row][r] = hi(src[map[row]][r]) (map < 0 -> 0),
+// with the source pointer read from device memory (graph-replayable with a new source)
 __global__ void df_gather_hi_ind_kernel(float2* __restrict__ dst, const float4* const* __restrict__ srcp,
                                         const int* __restrict__ map, long long rows, int nrhs) {
   // the leading FP32 pair of each double-float complex (8-byte loads)

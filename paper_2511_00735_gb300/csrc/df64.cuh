@@ -8,13 +8,11 @@ namespace hps {
 
 cudaError_t df_from_d(float4* dst, const double2* src, long long n, cudaStream_t s);
 cudaError_t df_to_d(double2* dst, const float4* src, long long n, cudaStream_t s);
-// dst[row][r] = hi(src[map[row]][r]) (map < 0 -> 0)
-cudaError_t df_gather_hi(float2* dst, const float4* src, const int* map, long long rows, int nrhs, cudaStream_t s);
 // dst[0] = a, dst[1] = b in stream order (one thread)
 cudaError_t set_pointers(void** dst, const void* a, void* b, cudaStream_t s);
-// df_gather_hi with the source pointer read from device memory, and a row scatter
-// dst[map[row]][r] = src[row][r] whose destination pointer is read from device memory
-// (a captured graph replays them with new vectors)
+// a row gather of leading parts dst[row][r] = hi(src[map[row]][r]) (map < 0 -> 0) whose source
+// pointer is read from device memory, and a row scatter dst[map[row]][r] = src[row][r] whose
+// destination pointer is read from device memory (a captured graph replays them with new vectors)
 cudaError_t df_gather_hi_ind(float2* dst, const float4* const* srcp, const int* map, long long rows, int nrhs,
                              cudaStream_t s);
 cudaError_t scatter_f2_ind(float2* const* dstp, const float2* src, const int* map, long long rows, int nrhs,
