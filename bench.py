@@ -321,13 +321,70 @@ def cpu_baseline_entry(prob, iterations):
 
 
 # ---------------------------------------------------------------------------- batching / serving
+def run_table1(args, prec):
+    """Memory-time trade-off of section 5 (Table 1) on the 64x64 workload: for each number of
+    exactly merged levels and each count of coarse GMRES steps, the device bytes held by the
+    tree (PMem), the merge time (Bt), the FGMRES iterations (It) and the solve time (St), plus
+    direct HPS (exact coarse level).  Times are CUDA events on the library's stream."""
+    import torch
+
+    from paper_2511_00735_gb300 import hps as H
+    from paper_2511_00735_gb300 import inputs
+
+    prob = inputs.fp64_64x64(seed=1, nrhs=args.nrhs)
+    s = H.Solver(0)
+    stream = torch.cuda.current_stream(0)
+    t = H.setup(s, prob, prec, build=True)
+    leaf_bytes = s.bytes_held()
+    t_dev = torch.from_numpy(t).to("cuda:0")
+    g_dev = torch.empty((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda:0")
+
+    def ev_ms(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def solve(ci):
+        return s.gmres_solve(t_dev, tol=args.tol, inner_iters=ci, restart=60, max_outer=20, out=g_dev,
+                             raise_on_notconv=False)[1]
+
+    rows = []
+    cases = [(lx, False) for lx in range(1, s.levels, 2)] + [(s.levels - 1, True)]
+    for lx, exact in cases:
+        s.release_workspace()
+        bt, _ = ev_ms(lambda: s.merge_levels(lx, exact_coarse=exact))
+        held = s.bytes_held()
+        for ci in ([0] if exact else [2, 4, 6]):
+            solve(ci)  # first solve of a tree captures the V-cycle graph
+            st, info = ev_ms(lambda: solve(ci))
+            rows.append({"levels": lx + 1, "L_exact": lx, "coarse": "exact" if exact else f"{ci} c.i.",
+                         "pmem_bytes": held - leaf_bytes, "bytes_held_tree": held, "bt_ms": bt,
+                         "it": info["outer_iterations"], "converged": info["converged"], "st_ms": st,
+                         "max_rel_residual": info["max_rel_residual"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    s.close()
+    return {"metric": "memory-time trade-off (section 5, Table 1): PMem, Bt, It, St by levels and coarse steps",
+            "value": None, "unit": None, "n_gpus": 1, "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("L_exact=10, 5 coarse GMRES steps", "L_exact and coarse steps swept"),
+                       "precision": args.precision, "tol": args.tol, "leaf_bytes": leaf_bytes},
+            "rows": rows}
+
+
 def run_systems(args):
     from paper_2511_00735_gb300 import hps as H
 
     prec = H.HPS_MIXED if args.precision == "mixed" else H.HPS_FP64
     clocks = ClockSampler(0)
     l0 = None
-    if args.workload == "batch":
+    if args.workload == "table1":
+        clocks.start()
+        l0 = H.kernel_launches()
+        line = run_table1(args, prec)
+    elif args.workload == "batch":
         from paper_2511_00735_gb300 import batch as B
 
         count = args.count or 512
@@ -378,8 +435,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--workload", default="scattering64", choices=["scattering64", "batch", "serve"],
-                    help="scattering64: the timed step above; batch: the 512-problem mix; serve: a Poisson stream")
+    ap.add_argument("--workload", default="scattering64", choices=["scattering64", "batch", "serve", "table1"],
+                    help="scattering64: the timed step above; batch: the 512-problem mix; serve: a Poisson stream; "
+                         "table1: the memory-time trade-off over exact levels and coarse steps")
     ap.add_argument("--count", type=int, default=0, help="problems (batch) or requests (serve)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="batch slots / serve workers")
