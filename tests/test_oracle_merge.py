@@ -130,3 +130,41 @@ def test_restriction_identity(small):
         Fr[xs] = np.linalg.solve(Ml[np.ix_(xs, xs)], rl[xs])
         res = rl - Ml @ Fr
         assert np.abs(res[xs]).max() < 1e-13 * np.abs(rl).max()
+
+
+def test_transposed_child_map_fails_dense_schur(small, monkeypatch):
+    # planted mistake: a merge that reads its children's maps transposed no longer equals the
+    # block elimination of the assembled M (the pin above would catch it)
+    import oracle.hps as hps_mod
+
+    op, M, lv = small
+    orig = hps_mod.merge_pair
+
+    def transposed(mesh, s1, s2, direction, keep_blocks=True):
+        t1, t2 = s1.T, s2.T
+        s1.T, s2.T = t1.T.copy(), t2.T.copy()
+        try:
+            return orig(mesh, s1, s2, direction, keep_blocks)
+        finally:
+            s1.T, s2.T = t1, t2
+
+    monkeypatch.setattr(hps_mod, "merge_pair", transposed)
+    S, _ = schur_levels(M, lv, 1)[1]
+    tree = hps_mod.MergeTree(op.mesh, op.Ts, None, 1)
+    assert np.linalg.norm(tree.coarse_dense(tree.coarse_index()) - S) / np.linalg.norm(S) > 1e-3
+
+
+def test_transposed_interface_solve_fails_block_inverse(small, monkeypatch):
+    # planted mistake: the sweeps solving with A^T instead of A break MG(M) = M^{-1} for an
+    # exact coarse solve (the block-inverse pin above would catch it)
+    import scipy.linalg as sla
+
+    import oracle.hps as hps_mod
+
+    op, M, lv = small
+    monkeypatch.setattr(hps_mod.MergeRecord, "solveA", lambda self, v: sla.lu_solve(self.lu, v, trans=1))
+    tree = hps_mod.MergeTree(op.mesh, op.Ts, None, 2)
+    r = np.random.default_rng(12).standard_normal(op.mesh.n_skel) + 0j
+    z = tree.mg(r, "exact")
+    zt = np.linalg.solve(M, r)
+    assert np.linalg.norm(z - zt) / np.linalg.norm(zt) > 1e-3
