@@ -28,6 +28,12 @@ Multigrid (section 4.3, block-inverse identity):
     P = [-A^{-1} B ; I],  R = [0 I],  S = D - C A^{-1} B,
 one coarse call per level (V-cycle); the coarse system after L_exact merges is
 solved by a fixed number of unpreconditioned GMRES steps or exactly.
+gamma-cycle (section 4.3, "multiple [coarse calls] define a gamma-cycle";
+reading A17): the coarse correction e for S r_c is made by gamma calls, each
+on the current residual,
+    e_0 = 0,  e_k = e_{k-1} + MG(S) (r_c - S e_{k-1}),  k = 1..gamma,
+at every level, the coarsest included (there MG(S) is the coarse solver);
+gamma = 1 is the V-cycle.
 `mg_dense` applies this formula literally to an assembled M; `MergeTree.mg`
 applies the same operator through the per-pair blocks (pinned to `mg_dense`).
 """
@@ -197,9 +203,34 @@ class MergeTree:
         nc = len(cidx)
         return self.coarse_apply(np.eye(nc, dtype=np.complex128), cidx)
 
+    # ---- the system of any stage: M_{k+1} on the unknowns left after k merges ----
+    def stage_index(self, k: int) -> np.ndarray:
+        idx = np.concatenate([s.inn[s.inn >= 0] for s in self.stages[k]])
+        return np.sort(idx)
+
+    def stage_apply(self, k: int, g):
+        """M_{k+1} g for a full-length skeleton vector g supported on the stage-k unknowns:
+        (M_{k+1} g)_u = g_u + (T_s g_s)_{pi(u)} with the stage-k subdomain maps T_s; the
+        result is full length, zero off the stage-k unknowns."""
+        g = np.asarray(g, dtype=np.complex128)
+        idx = self.stage_index(k)
+        out = np.zeros_like(g)
+        out[idx] = g[idx]
+        for s in self.stages[k]:
+            gs = np.zeros(s.n, dtype=np.complex128)
+            m = s.inn >= 0
+            gs[m] = g[s.inn[m]]
+            w = s.T @ gs
+            mo = s.out >= 0
+            out[s.out[mo]] += w[mo]
+        return out
+
     # ---- the preconditioner ------------------------------------------------
-    def mg(self, r, coarse="gmres", inner_iters=5):
-        """z = MG(M) r through the per-pair blocks (V-cycle, section 4.3)."""
+    def mg(self, r, coarse="gmres", inner_iters=5, gamma=1):
+        """z = MG(M) r through the per-pair blocks (V-cycle, section 4.3; gamma > 1: the
+        gamma-cycle, see mg_gamma)."""
+        if gamma != 1:
+            return self.mg_gamma(r, coarse, inner_iters, gamma)
         r = np.array(r, dtype=np.complex128)
         zs = []
         for lev in range(1, self.L_exact + 1):
@@ -227,6 +258,49 @@ class MergeTree:
                 y[m] = sol[rec.y_inn[m]]
                 sol[rec.x_idx] = z - rec.solveA(rec.B @ y)      # P e
         return sol
+
+    def mg_gamma(self, r, coarse="gmres", inner_iters=5, gamma=2):
+        """z = MG(M) r with gamma coarse calls per level (section 4.3, reading A17): at level l
+        the smoother and restriction of the V-cycle, then e_k = e_{k-1} + MG(M_{l+1})(r_c -
+        M_{l+1} e_{k-1}) for k = 1..gamma (MG of the coarsest system = the coarse solver),
+        then the prolongation."""
+        cidx = self.coarse_index()
+
+        def level(lev, r):
+            # MG of M_lev (its unknowns: those of stage lev-1) applied to r
+            if lev > self.L_exact:
+                sol = np.zeros_like(r)
+                if len(cidx):
+                    rc = r[cidx]
+                    if coarse == "exact":
+                        sol[cidx] = np.linalg.solve(self.coarse_dense(cidx), rc)
+                    else:
+                        sol[cidx] = gmres_fixed(lambda v: self.coarse_apply(v, cidx), rc, inner_iters)
+                return sol
+            r = r.copy()
+            zs = []
+            for rec in self.merges[lev]:
+                z = rec.solveA(r[rec.x_idx])                      # F r on this block
+                Cz = rec.C @ z
+                m = rec.y_out >= 0
+                r[rec.y_out[m]] -= Cz[m]                          # R (I - M F) r
+                zs.append(z)
+            idx = self.stage_index(lev)
+            rc = np.zeros_like(r)
+            rc[idx] = r[idx]
+            e = np.zeros_like(r)
+            for k in range(gamma):
+                res = rc if k == 0 else rc - self.stage_apply(lev, e)
+                e = e + level(lev + 1, res)
+            sol = e
+            for rec, z in zip(self.merges[lev], zs):
+                y = np.zeros(len(rec.y_inn), dtype=np.complex128)
+                m = rec.y_inn >= 0
+                y[m] = sol[rec.y_inn[m]]
+                sol[rec.x_idx] = z - rec.solveA(rec.B @ y)      # P e
+            return sol
+
+        return level(1, np.array(r, dtype=np.complex128))
 
     # ---- direct HPS (all merges, boundary data at the root) ----------------
     def direct_solve(self, t):
@@ -264,9 +338,10 @@ def unknown_levels(mesh: Mesh) -> np.ndarray:
     return lv
 
 
-def mg_dense(M, levels, lev, L_exact, r, coarse="gmres", inner_iters=5):
+def mg_dense(M, levels, lev, L_exact, r, coarse="gmres", inner_iters=5, gamma=1):
     """MG(M) r = F r + P MG(S) R (I - M F) r applied literally to a dense M whose
-    unknowns carry merge levels `levels` (plain definition, small meshes only)."""
+    unknowns carry merge levels `levels` (plain definition, small meshes only);
+    MG(S) r_c is made by gamma calls on the current residual (gamma-cycle)."""
     r = np.asarray(r, dtype=np.complex128)
     if lev > L_exact:
         if len(r) == 0:
@@ -284,7 +359,9 @@ def mg_dense(M, levels, lev, L_exact, r, coarse="gmres", inner_iters=5):
     Fr[xs] = np.linalg.solve(A, r[xs])
     rc = (r - M @ Fr)[rest]
     S = D - C @ np.linalg.solve(A, B)
-    e = mg_dense(S, levels[rest], lev + 1, L_exact, rc, coarse, inner_iters)
+    e = np.zeros(len(rest), dtype=np.complex128)
+    for _ in range(gamma):
+        e = e + mg_dense(S, levels[rest], lev + 1, L_exact, rc - S @ e, coarse, inner_iters, gamma)
     z = Fr.copy()
     z[rest] += e
     z[xs] += -np.linalg.solve(A, B @ e)

@@ -73,14 +73,14 @@ class OracleProblem:
         return [tree.direct_solve(t) for t in self.ts]
 
     def solve_fgmres(self, L_exact=None, inner_iters=None, tol=1e-10, coarse="gmres",
-                     restart=60, max_outer=20, tree=None):
+                     restart=60, max_outer=20, tree=None, gamma=1):
         L_exact = self.prob.L_exact if L_exact is None else L_exact
         inner_iters = self.prob.inner_iters if inner_iters is None else inner_iters
         if tree is None:
             tree = self.tree(L_exact)
         sols, infos = [], []
         for rhs in self.rhs:
-            x, info = fgmres(self.matvec, rhs, lambda v: tree.mg(v, coarse, inner_iters), tol,
+            x, info = fgmres(self.matvec, rhs, lambda v: tree.mg(v, coarse, inner_iters, gamma), tol,
                              restart, max_outer)
             sols.append(x)
             infos.append(info)

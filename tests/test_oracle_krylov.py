@@ -83,3 +83,13 @@ def test_table1_trends(cfg):
     its_c = [op.solve_fgmres(L_exact=1, inner_iters=c, tol=1e-10)[1][0]["iterations"]
              for c in (2, 4, 8)]
     assert all(b <= a for a, b in zip(its_c, its_c[1:])), its_c
+
+
+def test_table1_gamma_trend(cfg):
+    # Table 1, gamma = 2 columns: with the same coarse steps, two coarse calls per level take
+    # no more FGMRES iterations than one (parity unpinned in absolute counts)
+    op = cfg
+    for L_exact, ci in ((1, 2), (2, 2), (2, 3)):
+        it1 = op.solve_fgmres(L_exact=L_exact, inner_iters=ci, tol=1e-10, gamma=1)[1][0]["iterations"]
+        it2 = op.solve_fgmres(L_exact=L_exact, inner_iters=ci, tol=1e-10, gamma=2)[1][0]["iterations"]
+        assert it2 <= it1, (L_exact, ci, it1, it2)

@@ -168,3 +168,62 @@ def test_transposed_interface_solve_fails_block_inverse(small, monkeypatch):
     z = tree.mg(r, "exact")
     zt = np.linalg.solve(M, r)
     assert np.linalg.norm(z - zt) / np.linalg.norm(zt) > 1e-3
+
+
+# ---------------------------------------------------------------- gamma-cycle (section 4.3)
+@pytest.mark.parametrize("L_exact", [1, 2, 3])
+@pytest.mark.parametrize("gamma", [2, 3])
+def test_gamma_cycle_structured_equals_literal_formula(small, L_exact, gamma):
+    # the per-pair recursion against the literal recursion on the assembled M: two independent
+    # statements of e_k = e_{k-1} + MG(S)(r_c - S e_{k-1}) (GMRES coarse solve: nonlinear in r)
+    op, M, lv = small
+    tree = MergeTree(op.mesh, op.Ts, None, L_exact)
+    r = np.random.default_rng(20 + L_exact).standard_normal(op.mesh.n_skel) * (0.4 - 1j)
+    zd = mg_dense(M, lv, 1, L_exact, r, "gmres", 3, gamma)
+    zs = tree.mg(r, "gmres", 3, gamma)
+    assert np.linalg.norm(zs - zd) / np.linalg.norm(zd) < 1e-12
+
+
+@pytest.mark.parametrize("L_exact", [0, 1, 2])
+def test_gamma_one_is_the_v_cycle(small, L_exact):
+    op, M, lv = small
+    tree = MergeTree(op.mesh, op.Ts, None, L_exact)
+    r = np.random.default_rng(30 + L_exact).standard_normal(op.mesh.n_skel) + 0.3j
+    assert np.linalg.norm(tree.mg_gamma(r, "gmres", 4, 1) - tree.mg(r, "gmres", 4)) <= 1e-13 * np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("gamma", [2, 3])
+def test_gamma_cycle_exact_coarse_is_inverse(small, gamma):
+    # with an exact coarse solve every coarse call is exact, the later calls correct nothing,
+    # and the gamma-cycle is M^{-1} like the V-cycle (block-inverse identity)
+    op, M, lv = small
+    tree = MergeTree(op.mesh, op.Ts, None, 2)
+    r = np.random.default_rng(40 + gamma).standard_normal(op.mesh.n_skel) + 0j
+    z = tree.mg(r, "exact", 0, gamma)
+    zt = np.linalg.solve(M, r)
+    assert np.linalg.norm(z - zt) / np.linalg.norm(zt) < 1e-12
+
+
+def test_gamma_cycle_contracts_toward_the_inverse(small):
+    # more coarse calls per level move MG(M) r closer to M^{-1} r for a fixed coarse solver
+    # (each call is one step of a convergent iteration on the coarse-level system)
+    op, M, lv = small
+    tree = MergeTree(op.mesh, op.Ts, None, 2)
+    r = np.random.default_rng(50).standard_normal(op.mesh.n_skel) * (1 + 0.5j)
+    zt = np.linalg.solve(M, r)
+    errs = [np.linalg.norm(tree.mg(r, "gmres", 2, g) - zt) / np.linalg.norm(zt) for g in (1, 2, 4)]
+    assert errs[0] > errs[1] > errs[2], errs
+
+
+def test_gamma_cycle_without_residual_update_fails(small, monkeypatch):
+    # planted mistake: coarse calls that all take the restricted residual r_c (no "- S e")
+    # add up to gamma MG(S) r_c; the structured-vs-literal pin above catches it
+    import oracle.hps as hps_mod
+
+    op, M, lv = small
+    tree = hps_mod.MergeTree(op.mesh, op.Ts, None, 2)
+    monkeypatch.setattr(hps_mod.MergeTree, "stage_apply", lambda self, k, g: np.zeros_like(g))
+    r = np.random.default_rng(60).standard_normal(op.mesh.n_skel) + 0j
+    zd = mg_dense(M, lv, 1, 2, r, "gmres", 3, 2)
+    zs = tree.mg(r, "gmres", 3, 2)
+    assert np.linalg.norm(zs - zd) / np.linalg.norm(zd) > 1e-3
