@@ -1,15 +1,19 @@
 #!/usr/bin/env python
-"""Helmholtz solves/s of HPS-preconditioned FGMRES on one GB300.
+"""Helmholtz solves/s (and per-step p50/p99 latency) of HPS-preconditioned FGMRES on one GB300.
 
-Workload (one step): the 64x64-element, N = 16 GLL, kappa = 100 scattering
-problem with one seeded Gaussian bump and 16 plane-wave right-hand sides:
-coefficient upload, all 4096 leaf ItI maps, 10 levels of exact merges, and
+Workload (one step, default): the 128x128-element, N = 16 GLL, kappa = 200 scattering
+problem with eight seeded Gaussian bumps and 32 plane-wave right-hand sides:
+coefficient upload, all 16384 leaf ItI maps, 12 levels of exact merges, and
 flexible GMRES (restart 60, zero initial guess) preconditioned by the merge-tree
-V-cycle with 5 coarse GMRES steps, to relative residual 1e-10 per right-hand
-side.  A "solve" is one right-hand side reaching that residual.
+V-cycle with 5 coarse GMRES steps, to an FP64 relative residual of 1e-10 per
+right-hand side.  A "solve" is one right-hand side whose returned solution has
+that FP64 residual; only those are counted.  The plain FP64 path is timed on the
+same problem and the mixed solution's difference from it is stated.
+--workload scattering64 runs the 64x64, N = 16, kappa = 100 problem (16 RHS).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...      (the CPU oracle, bounded sample)
+  python bench.py --workload batch|serve|table1|phase ...
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own seeded
 problem (independent replicas, weak scaling, no collective on the data path).
@@ -30,12 +34,27 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "64x64 elements, N=16 GLL, kappa=100, 1 seeded bump, 16 plane-wave RHS, L_exact=10, 5 coarse GMRES steps"
+# the headline metric, the same string in both arms
+METRIC = "Helmholtz solves/s & p50/p99 latency at rel-residual 1e-10, mixed vs FP64"
+WORKLOADS = {
+    "scattering128": ("128x128 elements, N=16 GLL, kappa=200, 8 seeded bumps, 32 plane-wave RHS, L_exact=12, "
+                      "5 coarse GMRES steps", 32, 2),
+    "scattering64": ("64x64 elements, N=16 GLL, kappa=100, 1 seeded bump, 16 plane-wave RHS, L_exact=10, "
+                     "5 coarse GMRES steps", 16, 1),
+}
 FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (nominal, vector = tensor rate)
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-# dram read + write bytes of one leaf_ir_kernel launch at 64x64, N=16 from the committed ncu capture
-# (profiles/leaf_ir_kernel_64x64_N16.md); None until captured and whenever leaf.cu changes.
-LEAF_TRAFFIC_BYTES = 225.0e6  # ncu: dram read + write of one leaf_ir_kernel launch, 64x64, N=16
+# ncu dram read + write of one leaf_ir_kernel launch per element (64x64, N=16 capture, scaled by
+# the elements of a launch); None whenever leaf.cu changed since the capture
+LEAF_TRAFFIC_BYTES_PER_ELEMENT = 225.0e6 / 4096
+
+
+def make_problem(workload: str, seed: int, nrhs: int):
+    from paper_2511_00735_gb300 import inputs
+
+    if workload == "scattering128":
+        return inputs.mixed_128x128(seed=seed, nrhs=nrhs)
+    return inputs.fp64_64x64(seed=seed, nrhs=nrhs)
 
 
 def _finite_or_none(x: float):
@@ -137,6 +156,45 @@ def matvec_bytes(E: int, N: int, nrhs: int) -> float:
     return 16.0 * E * nb * nb + 3 * 16.0 * E * nb * nrhs
 
 
+# ---------------------------------------------------------------------------- V-cycle bytes
+def vcycle_bytes(nx: int, N: int, L_exact: int, nrhs: int, inner_iters: int, elem: int = 8) -> dict:
+    """Algorithmic HBM bytes of one V-cycle application of the FP32 tree (complex: `elem` bytes).
+
+    Operators, each read once: per merge level l the restriction U [2p x 2m] and the
+    prolongation Dm [2m x 2n] of every pair (n = a child's boundary length, m = its interface
+    length, p = n - m), and per coarse GMRES step the interior-interior block of every coarse
+    subdomain's map.  Block vectors: each stage's sweep vector (rows = subdomains x boundary
+    length, nrhs columns) read and written once on the way up and once on the way down, plus
+    the stage-0 entry gather and exit scatter (the caller's vectors read and written once)."""
+    q = N - 1
+    E = nx * nx
+    a = b = 1
+    ops = 0
+    vec_rows = 4 * q * E  # stage 0
+    vec = 0
+    for lev in range(1, L_exact + 1):
+        n = 2 * (a + b) * q
+        m = (b if lev % 2 == 1 else a) * q
+        p = n - m
+        npairs = E >> lev
+        ops += npairs * (2 * p * 2 * m + 2 * m * 2 * n)
+        vec += 2 * 2 * vec_rows  # up: read stage l-1, write stage l; down: the same, reversed
+        if lev % 2 == 1:
+            a *= 2
+        else:
+            b *= 2
+        vec_rows = (E >> lev) * 2 * (a + b) * q
+    gx, gy = nx // a, nx // b
+    coarse = 0
+    for iy in range(gy):
+        for ix in range(gx):
+            ni = q * ((b if ix > 0 else 0) + (b if ix < gx - 1 else 0) + (a if iy > 0 else 0) + (a if iy < gy - 1 else 0))
+            coarse += ni * ni
+    vec += 2 * 2 * 4 * q * E  # entry gather, exit scatter
+    total = elem * (ops + inner_iters * coarse) + elem * nrhs * vec
+    return {"bytes": total, "operator_bytes": elem * (ops + inner_iters * coarse), "vector_bytes": elem * nrhs * vec}
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local_rank, dist):
     import torch
@@ -147,7 +205,8 @@ def run_gpu(args, rank, world, local_rank, dist):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    prob = inputs.fp64_64x64(seed=RP.seed_for_rank(rank), nrhs=args.nrhs)
+    _, _, base_seed = WORKLOADS[args.workload]
+    prob = make_problem(args.workload, RP.seed_for_rank(rank, base=base_seed), args.nrhs)
     prec = H.HPS_MIXED if args.precision == "mixed" else H.HPS_FP64
     s = H.Solver(local_rank)
     s.set_outer_arith({"default": H.OUTER_DEFAULT, "fp64": H.OUTER_FP64, "df64": H.OUTER_DF64}[args.outer])
@@ -163,13 +222,15 @@ def run_gpu(args, rank, world, local_rank, dist):
         s.set_coeff(prob.kappa, b, prob.eta)
         s.build_leaves(precision)
         s.merge_levels(prob.L_exact)
-        _, info = s.gmres_solve(t, tol=args.tol, inner_iters=prob.inner_iters, restart=60, max_outer=20, out=out)
+        _, info = s.gmres_solve(t, tol=args.tol, inner_iters=prob.inner_iters, restart=60, max_outer=20, out=out,
+                                raise_on_notconv=False)
         return info
 
     def timed(fn, k):
         # barrier + synchronize on both sides, CUDA events on the launching stream, max over ranks
-        return RP.timed(fn, k, RP.CudaEventClock(stream), dist=dist, sync=lambda: torch.cuda.synchronize(dev),
-                        device=dev)
+        clock = RP.CudaEventClock(stream)
+        ms, wall, outs = RP.timed(fn, k, clock, dist=dist, sync=lambda: torch.cuda.synchronize(dev), device=dev)
+        return ms, wall, outs, clock.laps_ms()
 
     for _ in range(args.warmup):
         step(prec, b_dev, t_dev, g_dev)
@@ -178,13 +239,14 @@ def run_gpu(args, rank, world, local_rank, dist):
     clocks.start()
     l0 = H.kernel_launches()
     s.profile(True)
-    ms, wall_ms, infos = timed(lambda: step(prec, b_dev, t_dev, g_dev), args.steps)
+    ms, wall_ms, infos, laps = timed(lambda: step(prec, b_dev, t_dev, g_dev), args.steps)
     prof = s.profile_read()
     s.profile(False)
     launches = H.kernel_launches() - l0
     clk = clocks.stop()
     nrhs = prob.nrhs
-    value = RP.job_throughput(nrhs, args.steps, world, ms)
+    conv_total = sum(i["converged"] for i in infos)  # solves whose FP64 residual reached tol
+    value = RP.sum_over_ranks(conv_total, dist, dev) / (ms / 1e3)  # all ranks' solves / slowest rank's time
     its = max(i["outer_iterations"] for i in infos)
     res = max(i["max_rel_residual"] for i in infos)
     conv = min(i["converged"] for i in infos)
@@ -192,7 +254,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     # ---- end to end through the public API with host buffers ----
     g_host = np.empty((nrhs, s.n_skel), dtype=np.complex128)
     step(prec, b_host, t_host, g_host)
-    e2e_ms, e2e_wall, _ = timed(lambda: step(prec, b_host, t_host, g_host), args.steps)
+    e2e_ms, e2e_wall, e2e_infos, _ = timed(lambda: step(prec, b_host, t_host, g_host), args.steps)
+    e2e_conv = RP.sum_over_ranks(sum(i["converged"] for i in e2e_infos), dist, dev)
     h2d = b_host.nbytes + t_host.nbytes
     d2h = g_host.nbytes
 
@@ -201,131 +264,234 @@ def run_gpu(args, rank, world, local_rank, dist):
     s.build_leaves(prec)
     s.merge_levels(prob.L_exact)
     s.gmres_solve(t_dev, tol=args.tol, inner_iters=prob.inner_iters, out=g_dev)
-    warm_ms, _, _ = timed(lambda: s.gmres_solve(t_dev, tol=args.tol, inner_iters=prob.inner_iters, out=g_dev),
-                          args.steps)
+    warm_ms, _, warm_infos, warm_laps = timed(
+        lambda: s.gmres_solve(t_dev, tol=args.tol, inner_iters=prob.inner_iters, out=g_dev,
+                              raise_on_notconv=False)[1], args.steps)
+    warm_conv = RP.sum_over_ranks(sum(i["converged"] for i in warm_infos), dist, dev)
 
     # ---- the plain FP64 GPU path on the same workload (comparison) ----
     fp64 = None
     if prec == H.HPS_MIXED and not args.no_fp64:
         g_mixed = g_dev.clone()  # the mixed solution of this problem (the warm solve above)
         s.set_outer_arith(H.OUTER_DEFAULT)
+        s.release_workspace()
         step(H.HPS_FP64, b_dev, t_dev, g_dev)
-        k64 = max(1, min(args.steps, 2))
-        ms64, _, inf64 = timed(lambda: step(H.HPS_FP64, b_dev, t_dev, g_dev), k64)
+        ms64, _, inf64, _ = timed(lambda: step(H.HPS_FP64, b_dev, t_dev, g_dev), 1)
         # the mixed result against the FP64 path's (itself the oracle's to 1e-10 in the parity tests)
         diff = torch.linalg.vector_norm(g_mixed - g_dev, dim=1) / torch.linalg.vector_norm(g_dev, dim=1)
-        fp64 = {"value": k64 * nrhs * world / (ms64 / 1e3), "ms_per_step": ms64 / k64,
-                "iterations": max(i["outer_iterations"] for i in inf64),
-                "max_rel_residual": max(i["max_rel_residual"] for i in inf64),
-                "mixed_vs_fp64_max_rel_l2": _finite_or_none(float(diff.max().item()))}
+        fp64 = {"value": RP.sum_over_ranks(inf64[0]["converged"], dist, dev) / (ms64 / 1e3), "unit": "solves/s", "ms_per_step": ms64,
+                "steps": 1, "iterations": inf64[0]["outer_iterations"],
+                "max_rel_residual": inf64[0]["max_rel_residual"], "converged": inf64[0]["converged"],
+                "mixed_vs_fp64_max_rel_l2": _finite_or_none(float(diff.max().item())),
+                "note": "max over right-hand sides of ||g_mixed - g_fp64||_2 / ||g_fp64||_2"}
+        s.release_workspace()
     s.close()
     return dict(outer=args.outer if args.outer != "default" else ("df64" if prec == H.HPS_MIXED else "fp64"),
                 prob=prob, ms=ms, wall_ms=wall_ms, value=value, its=its, res=res, conv=conv, prof=prof,
-                launches=launches, clk=clk, e2e_ms=e2e_ms, e2e_wall=e2e_wall, h2d=h2d, d2h=d2h,
-                warm_ms=warm_ms, fp64=fp64)
+                launches=launches, clk=clk, e2e_ms=e2e_ms, e2e_wall=e2e_wall, e2e_conv=e2e_conv, h2d=h2d, d2h=d2h,
+                warm_ms=warm_ms, warm_conv=warm_conv, warm_laps=warm_laps, fp64=fp64, laps=laps)
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-ORACLE_ITERATIONS_DEFAULT = 40  # FGMRES iterations this workload needs (same method on both sides)
+# FGMRES iterations of each workload's seeded problem (the same method on both sides; the GPU
+# arm passes the count its own run took)
+ORACLE_ITERATIONS = {"scattering128": 48, "scattering64": 40}
 
 
-def oracle_estimate(prob, iterations: int, leaf_sample: int = 48):
-    """Time the CPU oracle on a bounded sample of the workload and scale to one step.
+def _best_time(fn, min_s: float = 0.05, reps: int = 3) -> float:
+    """Seconds of one call of fn: the fastest of `reps` batches, each repeated until it lasts
+    `min_s` (short operations are timed many times so host timer noise does not get scaled)."""
+    best = float("inf")
+    for _ in range(reps):
+        n, t = 0, 0.0
+        t0 = time.perf_counter()
+        while n == 0 or t < min_s:
+            fn()
+            n += 1
+            t = time.perf_counter() - t0
+        best = min(best, t / n)
+    return best
 
-    Phases timed: `leaf_sample` leaf ItI maps (scaled to all elements); one pair
-    merge per level 1..L_exact on children of the true sizes (scaled by the pairs
-    per level); one FP64 skeleton matvec and one V-cycle's per-pair sweep
-    operations plus the coarse GMRES steps for one right-hand side (scaled by the
-    FGMRES iteration count and the number of right-hand sides)."""
-    from oracle.hps import Sub, merge_pair
-    from oracle.krylov import gmres_fixed
-    from oracle.leaf import leaf_itI
-    from oracle.problem import coefficient
-    from oracle.skeleton import Mesh, apply_M
 
-    mesh = Mesh(prob.nx, prob.nx, prob.N)
-    c = coefficient(mesh, prob.kappa, prob.bumps)
-    rng = np.random.default_rng(0)
-    t0 = time.perf_counter()
-    els = rng.choice(mesh.E, leaf_sample, replace=False)
-    Ts = {}
-    for e in els:
-        Ts[int(e)] = leaf_itI(prob.N, mesh.h, c[e], prob.eta)["T"]
-    t_leaf = (time.perf_counter() - t0) / leaf_sample * mesh.E
-    # merges and the per-pair sweep work, level by level
-    t_merge = 0.0
-    t_sweep = 0.0
-    q = mesh.q
-    a, b = 1, 1
-    sample_T = next(iter(Ts.values()))
-    for lev in range(1, prob.L_exact + 1):
-        d = "x" if lev % 2 == 1 else "y"
-        s1 = Sub(mesh, 0, 0, a, b)
-        s2 = Sub(mesh, a if d == "x" else 0, b if d == "y" else 0, a, b)
-        for s in (s1, s2):
-            if s.n == sample_T.shape[0]:
-                s.T = sample_T
+class OracleSampler:
+    """The CPU oracle as it stands, timed on bounded samples of one step of a workload and scaled
+    to the whole step.
+
+    Leaves: the 16 elements of a 4x4 block plus `leaf_sample` seeded elsewhere, timed one by one
+    (median, scaled by E).  Merges: every pair merge of levels 1-4 of that block on its real maps
+    (timed, scaled by the pairs of each level); from level 5 up one pair merge per level on
+    children of the true sizes whose maps are drawn at random (the merge's dense LU and products
+    cost the same whatever the values).  Solve, per right-hand side and FGMRES iteration: one
+    FP64 skeleton matvec over all elements, one V-cycle's per-pair sweep operations (timed per
+    level, scaled by its pairs) and the coarse GMRES steps; scaled by the iteration count and the
+    right-hand sides."""
+
+    def __init__(self, workload: str, nrhs: int, iterations: int):
+        from oracle.skeleton import Mesh
+        from paper_2511_00735_gb300 import inputs
+
+        self.prob = make_problem(workload, WORKLOADS[workload][2], nrhs)
+        self.mesh = Mesh(self.prob.nx, self.prob.nx, self.prob.N)
+        self.iterations = iterations
+        self.inputs = inputs
+        self.big_merge_s = {}  # level -> seconds of one pair merge on random children (levels >= 9)
+
+    def c_of(self, e: int):
+        X, Y = self.mesh.node_xy(e)  # c = kappa^2 (1 - b) at the oracle's own nodes of element e
+        return self.prob.kappa ** 2 * (1.0 - self.inputs.eval_b(self.prob.bumps, X, Y))
+
+    def sample(self, seed: int, leaf_sample: int = 8) -> dict:
+        from oracle.hps import Sub, merge_pair
+        from oracle.krylov import gmres_fixed
+        from oracle.leaf import leaf_itI
+        from oracle.skeleton import apply_M
+
+        prob, mesh = self.prob, self.mesh
+        q = mesh.q
+        rng = np.random.default_rng(seed)
+        t_start = time.perf_counter()
+        block = [mesh.elem(ix, iy) for iy in range(4) for ix in range(4)]
+        others = [int(x) for x in rng.choice(mesh.E, leaf_sample, replace=False)]
+        Ts, t_leaves = {}, []
+        for e in block + others:
+            ce = self.c_of(e)
+            t0 = time.perf_counter()
+            T = leaf_itI(prob.N, mesh.h, ce, prob.eta)["T"]
+            t_leaves.append(time.perf_counter() - t0)
+            Ts.setdefault(e, T)
+        t_leaf = float(np.median(t_leaves)) * mesh.E
+        subs = {}
+        for e in block:
+            ix, iy = e % mesh.nx, e // mesh.nx
+            sb = Sub(mesh, ix, iy, 1, 1)
+            sb.T = Ts[e]
+            subs[(ix, iy)] = sb
+        t_merge = t_sweep = 0.0
+        a, b = 1, 1
+        for lev in range(1, prob.L_exact + 1):
+            d = "x" if lev % 2 == 1 else "y"
+            npairs = mesh.E // (2 ** lev)
+            if a * (2 if d == "x" else 1) <= 4 and b * (2 if d == "y" else 1) <= 4:
+                pairs = [(k, (k[0] + a, k[1]) if d == "x" else (k[0], k[1] + b)) for k in subs
+                         if (d == "x" and (k[0] // a) % 2 == 0) or (d == "y" and (k[1] // b) % 2 == 0)]
+            elif lev in self.big_merge_s:
+                # levels >= 9: the merge on random children was timed by the first (warm-up) sample;
+                # its dense LU and products cost the same on every sample.  Its sweep operations are
+                # still timed below, on children of the true sizes.
+                t_merge += self.big_merge_s[lev] * npairs
+                s1 = Sub(mesh, 0, 0, a, b)
+                s2 = Sub(mesh, a if d == "x" else 0, b if d == "y" else 0, a, b)
+                m = (b if d == "x" else a) * q
+                n2 = 2 * (s1.n - m)
+                lu = __import__("scipy.linalg", fromlist=["lu_factor"]).lu_factor(
+                    np.eye(2 * m) + 0.1 * (rng.standard_normal((2 * m, 2 * m)) + 0j))
+                Bm = rng.standard_normal((2 * m, n2)) + 0j
+                Cm = rng.standard_normal((n2, 2 * m)) + 0j
+                r = rng.standard_normal(2 * m) + 0j
+                y = rng.standard_normal(n2) + 0j
+                sla = __import__("scipy.linalg", fromlist=["lu_solve"])
+                t_sweep += _best_time(lambda: (Cm @ sla.lu_solve(lu, r), sla.lu_solve(lu, Bm @ y)), min_s=0.01,
+                                      reps=1) * npairs
+                subs = {}
+                if d == "x":
+                    a *= 2
+                else:
+                    b *= 2
+                continue
             else:
-                Z = rng.standard_normal((s.n, s.n)) + 1j * rng.standard_normal((s.n, s.n))
-                s.T = 0.5 * Z / np.sqrt(s.n)
-        t1 = time.perf_counter()
-        _, rec = merge_pair(mesh, s1, s2, d)
-        t2 = time.perf_counter()
-        npairs = mesh.E // (2 ** lev)
-        t_merge += (t2 - t1) * npairs
-        r = rng.standard_normal(2 * rec.m) + 0j
-        y = rng.standard_normal(len(rec.y_inn)) + 0j
-        t3 = time.perf_counter()
-        z = rec.solveA(r)
-        _ = rec.C @ z
-        _ = z - rec.solveA(rec.B @ y)
-        t_sweep += (time.perf_counter() - t3) * npairs
-        if d == "x":
-            a *= 2
-        else:
-            b *= 2
-    # coarse GMRES on the coarse subdomains (4 blocks of a x b elements)
-    nsub = mesh.E // (a * b)
-    nc = 2 * (a + b) * q
-    Tc = [0.5 * (rng.standard_normal((nc, nc)) + 1j * rng.standard_normal((nc, nc))) / np.sqrt(nc)
-          for _ in range(min(nsub, 4))]
-    v = rng.standard_normal(nc) + 0j
-    t4 = time.perf_counter()
-    gmres_fixed(lambda x: x + Tc[0] @ x, v, prob.inner_iters)
-    t_coarse = (time.perf_counter() - t4) * nsub
-    # one FP64 skeleton matvec (one right-hand side); every element uses a sampled map
-    Tall = [Ts[int(els[e % leaf_sample])] for e in range(mesh.E)]
-    g = rng.standard_normal(mesh.n_skel) + 0j
-    t5 = time.perf_counter()
-    apply_M(mesh, Tall, g)
-    t_mv = time.perf_counter() - t5
-    per_rhs = iterations * (t_mv + t_sweep + t_coarse)
-    total = t_leaf + t_merge + prob.nrhs * per_rhs
-    cores = blas_threads()
-    return {"seconds_per_step": total, "t_leaf": t_leaf, "t_merge": t_merge, "t_solve_per_rhs": per_rhs,
-            "cores": cores, "measured_s": time.perf_counter() - t0}
+                s1 = Sub(mesh, 0, 0, a, b)
+                s2 = Sub(mesh, a if d == "x" else 0, b if d == "y" else 0, a, b)
+                for sb in (s1, s2):
+                    Z = rng.standard_normal((sb.n, sb.n)) + 1j * rng.standard_normal((sb.n, sb.n))
+                    sb.T = 0.5 * Z / np.sqrt(sb.n)
+                subs = {(0, 0): s1, ((a, 0) if d == "x" else (0, b)): s2}
+                pairs = [((0, 0), (a, 0) if d == "x" else (0, b))]
+            new_subs, tm, ts = {}, 0.0, 0.0
+            for k1, k2 in pairs:
+                t1 = time.perf_counter()
+                merged, rec = merge_pair(mesh, subs[k1], subs[k2], d)
+                tm += time.perf_counter() - t1
+                r = rng.standard_normal(2 * rec.m) + 0j
+                y = rng.standard_normal(len(rec.y_inn)) + 0j
+                ts += _best_time(lambda: (rec.C @ rec.solveA(r), rec.solveA(rec.B @ y)), min_s=0.01, reps=1)
+                new_subs[k1] = merged
+            t_merge += tm / len(pairs) * npairs
+            t_sweep += ts / len(pairs) * npairs
+            if lev >= 9:
+                self.big_merge_s[lev] = tm / len(pairs)
+            subs = new_subs
+            if d == "x":
+                a *= 2
+            else:
+                b *= 2
+        nsub = mesh.E // (a * b)
+        nc = 2 * (a + b) * q
+        Tc = 0.5 * (rng.standard_normal((nc, nc)) + 1j * rng.standard_normal((nc, nc))) / np.sqrt(nc)
+        v = rng.standard_normal(nc) + 0j
+        t_coarse = _best_time(lambda: gmres_fixed(lambda x: x + Tc @ x, v, prob.inner_iters), min_s=0.02,
+                              reps=1) * nsub
+        keys = list(Ts)
+        Tall = [Ts[keys[e % len(keys)]] for e in range(mesh.E)]
+        g = rng.standard_normal(mesh.n_skel) + 0j
+        t_mv = _best_time(lambda: apply_M(mesh, Tall, g), min_s=0.0, reps=1)
+        per_rhs = self.iterations * (t_mv + t_sweep + t_coarse)
+        total = t_leaf + t_merge + prob.nrhs * per_rhs
+        return {"seconds_per_step": total, "solves_per_s": prob.nrhs / total, "t_leaf": t_leaf,
+                "t_merge": t_merge, "t_solve_per_rhs": per_rhs, "measured_s": time.perf_counter() - t_start,
+                "leaf_sample": len(t_leaves)}
 
 
-def blas_threads() -> int:
-    """Threads numpy's BLAS uses (threadpoolctl when installed, else the visible cores)."""
-    try:
-        import threadpoolctl
-
-        info = threadpoolctl.threadpool_info()
-        return max([p.get("num_threads", 1) for p in info] + [1])
-    except ImportError:
-        return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+def oracle_samples(workload: str, nrhs: int, iterations: int, samples: int) -> dict:
+    """One warm-up sample and `samples` timed ones of the oracle (seeds 1..samples)."""
+    smp = OracleSampler(workload, nrhs, iterations)
+    smp.sample(0)
+    runs = [smp.sample(k + 1) for k in range(samples)]
+    return {"runs": runs, "nrhs": smp.prob.nrhs}
 
 
-def cpu_baseline_entry(prob, iterations):
-    est = oracle_estimate(prob, iterations)
-    return {"value": prob.nrhs / est["seconds_per_step"], "unit": "solves/s", "cores": est["cores"],
-            "kind": "oracle",
-            "sample": (f"{48} of {prob.nx * prob.nx} leaf maps, one pair merge per level (children of the true sizes), "
-                       f"one matvec + one V-cycle's pair sweeps + {prob.inner_iters} coarse GMRES steps for one RHS "
-                       f"x {iterations} FGMRES iterations x {prob.nrhs} RHS; {est['measured_s']:.1f} s of CPU work"),
-            "phases_s": {"leaves": est["t_leaf"], "merges": est["t_merge"],
-                         "solve_per_rhs": est["t_solve_per_rhs"]}}
+def _oracle_subprocess(workload: str, nrhs: int, iterations: int, threads: int, samples: int) -> dict:
+    """oracle_samples in a fresh interpreter whose BLAS and OpenMP pools have `threads` threads
+    (set before numpy loads), so the timing does not depend on what this process imported."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", workload, "--nrhs", str(nrhs),
+           "--oracle-iterations", str(iterations), "--steps", str(samples)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def cpu_baseline(workload: str, nrhs: int, iterations: int, samples: int = 1) -> dict:
+    """The oracle's solves/s on this host, shared by the GPU arm's cpu_baseline and --impl
+    reference.  Run twice in fresh interpreters: numpy's BLAS on one thread (`samples` timed
+    samples) and on every core (one sample).  On every core the many small dense operations of
+    the lower levels run far slower than on one (thread start-up per call), so the reported
+    value is the faster configuration's median, with the threads it used; both are listed."""
+    cores = host_cores()
+    one = _oracle_subprocess(workload, nrhs, iterations, 1, samples)
+    allc = _oracle_subprocess(workload, nrhs, iterations, cores, 1) if cores > 1 else one
+    v1 = statistics.median(r["solves_per_s"] for r in one["runs"])
+    va = statistics.median(r["solves_per_s"] for r in allc["runs"])
+    best, used, runs = (v1, 1, one["runs"]) if v1 >= va else (va, cores, allc["runs"])
+    r0 = runs[len(runs) // 2]
+    return {"value": best, "unit": "solves/s", "cores": used, "kind": "oracle",
+            "sample": (f"per sample: {r0['leaf_sample']} leaf maps (16 of them a 4x4 block) scaled to all "
+                       f"elements; every pair merge of levels 1-4 of that block on real maps, one pair merge per "
+                       f"higher level on random children of the true sizes, each scaled by the pairs of its "
+                       f"level (levels 9 and up: the merge timed once, in the warm-up sample); one FP64 matvec + one "
+                       f"V-cycle's pair sweeps + the coarse GMRES steps for one RHS "
+                       f"x {iterations} FGMRES iterations x {one['nrhs']} RHS; {len(runs)} sample(s) of about "
+                       f"{r0['measured_s']:.1f} s of CPU work each, median; numpy/LAPACK"),
+            "value_1_thread": v1, "value_all_cores": va, "host_cores": cores, "samples": [r["solves_per_s"] for r in runs],
+            "phases_s": {"leaves": r0["t_leaf"], "merges": r0["t_merge"], "solve_per_rhs": r0["t_solve_per_rhs"]},
+            "extrapolated": True}
 
 
 # ---------------------------------------------------------------------------- batching / serving
@@ -377,7 +543,7 @@ def run_table1(args, prec):
     s.close()
     return {"metric": "memory-time trade-off (section 5, Table 1): PMem, Bt, It, St by levels and coarse steps",
             "value": None, "unit": None, "n_gpus": 1, "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("L_exact=10, 5 coarse GMRES steps", "L_exact and coarse steps swept"),
+            "config": {"workload": WORKLOADS["scattering64"][0].replace("L_exact=10, 5 coarse GMRES steps", "L_exact and coarse steps swept"),
                        "precision": args.precision, "tol": args.tol, "leaf_bytes": leaf_bytes},
             "rows": rows}
 
@@ -429,7 +595,69 @@ def run_systems(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- one phase (profilers)
+def run_phase(args):
+    """One phase of a workload in isolation, for ncu: `leaf` (R leaf builds), `merge` (leaves, then
+    R merge-tree builds), `matvec` (R FP64 skeleton matvecs), `precond` (R preconditioner
+    applications) or `solve` (one full step).  --nx 32 runs the 32x32, N = 16, kappa = 50 problem."""
+    import torch
+
+    from paper_2511_00735_gb300 import hps as H
+    from paper_2511_00735_gb300 import inputs
+
+    prec = H.HPS_MIXED if args.precision == "mixed" else H.HPS_FP64
+    if args.nx in (0, 128):
+        prob = make_problem("scattering128", 2, args.nrhs)
+    elif args.nx == 64:
+        prob = make_problem("scattering64", 1, args.nrhs)
+    else:
+        L = 2 * int(round(np.log2(args.nx)))
+        prob = inputs.single_bump(args.nx, 16, 100.0 * args.nx / 64.0, args.nrhs, seed=1, L_exact=max(L - 2, 0))
+    s = H.Solver(0)
+    t = H.setup(s, prob, prec, build=False)
+    td = torch.from_numpy(t).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = None
+    if args.phase == "leaf":
+        for _ in range(args.repeat):
+            s.build_leaves(prec)
+    else:
+        s.build_leaves(prec)
+        if args.phase == "merge":
+            for _ in range(args.repeat):
+                s.merge_levels(prob.L_exact)
+        elif args.phase == "matvec":
+            x = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
+            for _ in range(args.repeat):
+                s.matvec(x)
+        elif args.phase == "precond":
+            s.merge_levels(prob.L_exact)
+            r = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
+            for _ in range(args.repeat):
+                s.precond_apply(r, prob.inner_iters)
+        else:
+            s.merge_levels(prob.L_exact)
+            _, info = s.gmres_solve(td, tol=args.tol, inner_iters=prob.inner_iters)
+    torch.cuda.synchronize()
+    line = {"phase": args.phase, "workload": prob.name, "repeat": args.repeat,
+            "wall_s": time.perf_counter() - t0, "bytes_held": s.bytes_held()}
+    if info:
+        line.update(iterations=info["outer_iterations"], max_rel_residual=info["max_rel_residual"])
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------- main
+def pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * p / 100.0
+    lo, hi = int(np.floor(k)), int(np.ceil(k))
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,48 +665,66 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides (default: the workload's)")
     ap.add_argument("--outer", default="default", choices=["default", "fp64", "df64"],
                     help="outer FGMRES arithmetic (default: df64 for mixed, fp64 for fp64)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--workload", default="scattering64", choices=["scattering64", "batch", "serve", "table1"],
-                    help="scattering64: the timed step above; batch: the 512-problem mix; serve: a Poisson stream; "
-                         "table1: the memory-time trade-off over exact levels and coarse steps")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64x64 extra line")
+    ap.add_argument("--workload", default="scattering128",
+                    choices=["scattering128", "scattering64", "batch", "serve", "table1", "phase"],
+                    help="scattering128 (default) / scattering64: the timed step above; batch: the 512-problem "
+                         "mix; serve: a Poisson stream; table1: the memory-time trade-off over exact levels and "
+                         "coarse steps; phase: one phase in isolation (for profilers)")
+    ap.add_argument("--phase", default="leaf", choices=["leaf", "merge", "matvec", "precond", "solve"])
+    ap.add_argument("--nx", type=int, default=0, help="phase: element grid (0: 128)")
+    ap.add_argument("--repeat", type=int, default=1, help="phase: repetitions")
     ap.add_argument("--count", type=int, default=0, help="problems (batch) or requests (serve)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="batch slots / serve workers")
     ap.add_argument("--serve-timeout", type=float, default=240.0, help="serve: stop waiting after this many seconds")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-iterations", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.workload != "scattering64":
+    if args.oracle_sample:  # internal: the CPU oracle's bounded samples in a pinned-thread subprocess
+        wl = args.oracle_sample
+        r = oracle_samples(wl, args.nrhs or WORKLOADS[wl][1], args.oracle_iterations or ORACLE_ITERATIONS[wl],
+                           args.steps)
+        print(json.dumps(r), flush=True)
+        return
+    if args.workload == "phase":
+        if not args.nrhs:
+            args.nrhs = 32 if args.nx in (0, 128) else 16
+        return run_phase(args)
+    if args.workload not in WORKLOADS:
         return run_systems(args)
+    desc, default_nrhs, base_seed = WORKLOADS[args.workload]
+    if not args.nrhs:
+        args.nrhs = default_nrhs
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
-    from paper_2511_00735_gb300 import inputs
-
     if args.impl == "reference":
         if rank != 0:
             return
-        prob = inputs.fp64_64x64(seed=1, nrhs=args.nrhs)
-        vals = []
-        for i in range(args.warmup + args.steps):
-            est = oracle_estimate(prob, ORACLE_ITERATIONS_DEFAULT, leaf_sample=16)
-            if i >= args.warmup:
-                vals.append(prob.nrhs / est["seconds_per_step"])
-        v = statistics.median(vals)
-        line = {"metric": "Helmholtz solves/s at rel-residual 1e-10", "value": v, "unit": "solves/s",
+        iters = ORACLE_ITERATIONS[args.workload]
+        base = cpu_baseline(args.workload, args.nrhs, iters, samples=args.steps)
+        v = base["value"]
+        ms_step = 1e3 * args.nrhs / v
+        line = {"metric": METRIC, "value": v, "unit": "solves/s",
                 "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * prob.nrhs / v, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "global_batch": prob.nrhs, "parallelism": "replicas"},
-                "cpu_baseline": {"value": v, "unit": "solves/s", "kind": "oracle", "cores": est["cores"],
-                                 "sample": f"16 leaf maps, one merge per level, one V-cycle's pair sweeps, one matvec "
-                                           f"(one RHS) scaled by {ORACLE_ITERATIONS_DEFAULT} iterations x "
-                                           f"{prob.nrhs} RHS"},
+                "config": {"workload": desc, "global_batch": args.nrhs, "parallelism": "replicas",
+                           "l2": "host run (no GPU)"},
+                "latency_ms": {"p50": ms_step, "p99": ms_step,
+                               "note": "every solve of a step arrives at its start and completes at its end; "
+                                       "extrapolated step time of the sampled oracle"},
+                "extrapolated": True,
+                "cpu_baseline": base,
                 "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -490,6 +736,17 @@ def main():
         tdist.init_process_group("nccl")
         dist = tdist
     r = run_gpu(args, rank, world, local_rank, dist)
+    extra = None
+    if world == 1 and args.workload == "scattering128" and not args.no_extra:
+        ex_args = argparse.Namespace(**vars(args))
+        ex_args.workload, ex_args.nrhs, ex_args.no_fp64 = "scattering64", 16, True
+        ex_args.steps, ex_args.warmup = max(3, min(args.steps, 10)), 3
+        rx = run_gpu(ex_args, rank, world, local_rank, dist)
+        extra = {"workload": WORKLOADS["scattering64"][0], "value": rx["value"], "unit": "solves/s",
+                 "steps": ex_args.steps, "ms_per_step": rx["ms"] / ex_args.steps, "iterations": rx["its"],
+                 "max_rel_residual": rx["res"], "converged_per_step": rx["conv"],
+                 "e2e_value": rx["e2e_conv"] / (rx["e2e_ms"] / 1e3),
+                 "warm_value": rx["warm_conv"] / (rx["warm_ms"] / 1e3)}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -499,64 +756,78 @@ def main():
     nrhs = prob.nrhs
     prof = r["prof"]
     E, N = prob.nx * prob.nx, prob.N
-    # dominant single-kernel phase: the leaf build (one launch per step) or the FP64 matvec (one launch per call)
+    # the dominant single-launch kernel of a step: the leaf build (one launch per step); the V-cycle
+    # (one graph of sweep kernels per application, HBM-bound) is reported beside it
     leaf_ms, leaf_launch, leaf_calls = prof["leaf"]
-    mv_ms, mv_launch, mv_calls = prof["matvec"]
-    cand = []
+    roof = None
     if leaf_calls:
         per = leaf_ms / leaf_calls
-        f32 = leaf_flops(N) * E
         lit = leaf_flops_paper(N) * E
-        cand.append((leaf_ms, {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, double-float refinement "
-                                         "and inverse)",
-                               "bound": "alu", "achieved": f32 / (per / 1e3) / 1e12,
-                               "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                               "frac": f32 / (per / 1e3) / FP32_PEAK_NOMINAL,
-                               "traffic": LEAF_TRAFFIC_BYTES if prob.nx == 64 and N == 16 else None,
-                               "traffic_unit": "bytes per launch (ncu dram read + write)",
-                               "flops_per_launch": f32, "ms_per_launch": per,
-                               "paper_literal_flops_per_launch": lit,
-                               "paper_literal_rate_tflops": lit / (per / 1e3) / 1e12,
-                               "peak_source": "FP32 pipes from unit counts and clock: 152 SMs x 128 lanes x "
-                                              "2 (FMA) x 2.07 GHz = 80.5 TFLOP/s (double-float counted as the "
-                                              "FP32 operations it executes)"}))
-    if mv_calls and r.get("outer") == "fp64":
-        per = mv_ms / mv_calls
-        fl = matvec_flops(E, N, nrhs)
-        cand.append((mv_ms, {"kernel": "es_matvec_kernel (skeleton matvec, FP64)", "bound": "alu",
-                             "achieved": fl / (per / 1e3) / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
-                             "unit": "TFLOP/s", "frac": fl / (per / 1e3) / FP64_PEAK_NOMINAL,
-                             "traffic": None, "flops_per_launch": fl, "ms_per_launch": per,
-                             "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)"}))
-    roof = max(cand, key=lambda x: x[0])[1] if cand else None
+        ex = leaf_flops(N) * E
+        roof = {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, double-float refinement and inverse)",
+                "bound": "alu", "achieved": lit / (per / 1e3) / 1e12, "peak": FP32_PEAK_NOMINAL / 1e12,
+                "unit": "TFLOP/s", "frac": lit / (per / 1e3) / FP32_PEAK_NOMINAL,
+                "traffic": LEAF_TRAFFIC_BYTES_PER_ELEMENT * E if LEAF_TRAFFIC_BYTES_PER_ELEMENT else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write per element x elements)",
+                "algorithmic_flops_per_launch": lit, "ms_per_launch": per,
+                "flops_model": "paper-literal dense complex LU of the (N+1)^2-4 node element matrix with 4q "
+                               "right-hand sides, 8 (n_L^3/3 + n_L^2 n_G) per element",
+                "executed_fp32_pipe_flops_per_launch": ex,
+                "executed_rate_tflops": ex / (per / 1e3) / 1e12,
+                "peak_source": "FP32 pipes from unit counts and clock: 152 SMs x 128 lanes x 2 (FMA) x "
+                               "2.07 GHz = 80.5 TFLOP/s (no FP32 entry in the measured peaks)",
+                "share_of_step": leaf_ms / r["ms"]}
+    pre_ms, _, pre_calls = prof["precond"]
+    vc = None
+    if pre_calls:
+        vb = vcycle_bytes(prob.nx, N, prob.L_exact, nrhs, prob.inner_iters)
+        per = pre_ms / pre_calls
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        vc = {"kernel": "V-cycle (one CUDA graph: sweep GEMMs, coarse GMRES, gathers)", "bound": "hbm",
+              "achieved": vb["bytes"] / (per / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+              "frac": vb["bytes"] / (per / 1e3) / 1e9 / hbm, "traffic": None,
+              "algorithmic_bytes_per_launch": vb["bytes"], "operator_bytes": vb["operator_bytes"],
+              "vector_bytes": vb["vector_bytes"], "ms_per_launch": per, "launches_per_step": pre_calls / args.steps,
+              "share_of_step": pre_ms / r["ms"],
+              "peak_source": "measured" if not peaks.get("fallback") else "fallback 6.8 TB/s"}
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_baseline_entry(prob, r["its"])
+        cpu = cpu_baseline(args.workload, nrhs, r["its"], samples=1)
+    laps = r["laps"]
     line = {
-        "metric": "Helmholtz solves/s at rel-residual 1e-10 (mixed vs FP64)",
+        "metric": METRIC,
         "value": r["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": nrhs * world, "precision": args.precision,
-                   "outer": args.outer if args.outer != "default" else ("df64" if args.precision == "mixed" else "fp64"),
-                   "tol": args.tol, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2: leaf maps 236 MB, merge tree ~1.3 GB, Krylov basis 3.8 GB per step"},
+        "config": {"workload": desc, "global_batch": nrhs * world, "precision": args.precision,
+                   "outer": r["outer"], "tol": args.tol, "parallelism": "replicas" if world > 1 else "single",
+                   "residual": "FP64 (FP64 leaf maps and norms) at every restart and for the returned solution",
+                   "l2": "inputs larger than L2: leaf maps 0.94 GB, merge tree ~6 GB, Krylov basis ~30 GB per step"
+                   if args.workload == "scattering128" else
+                   "inputs larger than L2: leaf maps 236 MB, merge tree ~1.3 GB, Krylov basis 3.8 GB per step"},
+        "latency_ms": {"p50": pct(laps, 50), "p99": pct(laps, 99),
+                       "note": "per-step device time: every solve of a step arrives at its start and completes at "
+                               "its end (Poisson-arrival latencies: --workload serve)"},
         "iterations": r["its"], "max_rel_residual": r["res"], "converged": r["conv"],
-        "e2e": {"value": args.steps * nrhs * world / (r["e2e_ms"] / 1e3), "unit": "solves/s",
+        "e2e": {"value": r["e2e_conv"] / (r["e2e_ms"] / 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
-                "wall_value": args.steps * nrhs * world / (r["e2e_wall"] / 1e3)},
-        "warm": {"value": args.steps * nrhs * world / (r["warm_ms"] / 1e3), "unit": "solves/s",
+                "wall_value": r["e2e_conv"] / (r["e2e_wall"] / 1e3)},
+        "warm": {"value": r["warm_conv"] / (r["warm_ms"] / 1e3), "unit": "solves/s",
+                 "latency_ms": {"p50": pct(r["warm_laps"], 50), "p99": pct(r["warm_laps"], 99)},
                  "note": "cached leaf maps and merge tree, solve phase only"},
         "fp64": r["fp64"],
         "gpu_launches": r["launches"],
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "roofline": roof,
+        "roofline_vcycle": vc,
         "cpu_baseline": cpu,
         "clocks": r["clk"],
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
-                  "fp64_tflops_nominal": FP64_PEAK_NOMINAL / 1e12},
+                  "fp64_tflops_nominal": FP64_PEAK_NOMINAL / 1e12, "fallback": bool(peaks.get("fallback"))},
     }
+    if extra:
+        line["extra_64x64"] = extra
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -83,7 +83,8 @@ enum { HPS_OUTER_DEFAULT = -1, HPS_OUTER_FP64 = 0, HPS_OUTER_DF64 = 1 };
 typedef struct {
   int outer_iterations;     /* FGMRES iterations (max over right-hand sides)         */
   int converged;            /* number of right-hand sides with true residual <= tol  */
-  double max_rel_residual;  /* max over RHS of ||RHS - M g||_2 / ||RHS||_2 (explicit, FP64) */
+  double max_rel_residual;  /* max over RHS of ||RHS - M g||_2 / ||RHS||_2 of the returned g,
+                               formed with the FP64 matvec on both paths */
   int* iterations;          /* optional caller array [nrhs]: iterations per RHS (may be NULL) */
   double* rel_residual;     /* optional caller array [nrhs]: explicit residual per RHS (may be NULL) */
   double ms_rhs;            /* device time of the RHS assembly                        */
@@ -212,13 +213,15 @@ int hps_gmres_solve(hps_ctx* ctx, const void* t, const void* s, int nrhs, double
 
 /* Arithmetic of the outer FGMRES of later hps_gmres_solve calls on ctx:
  *   HPS_OUTER_FP64     matvec, Gram-Schmidt and basis in FP64 (section 4.3);
- *   HPS_OUTER_DF64     (with HPS_MIXED leaves only) the same steps on pairs of
- *                      FP32 numbers (about 48 significand bits, error-free
- *                      TwoSum/TwoProduct accumulation), the preconditioned
- *                      directions kept in FP32 (they are the FP32 tree's
- *                      output); every restart residual, and so every
- *                      convergence decision and the reported residual, is
- *                      still computed in FP64;
+ *   HPS_OUTER_DF64     (with HPS_MIXED leaves only) the Arnoldi steps (matvec,
+ *                      Gram-Schmidt, basis) on pairs of FP32 numbers (about 48
+ *                      significand bits, error-free TwoSum/TwoProduct
+ *                      accumulation), the preconditioned directions kept in
+ *                      FP32 (they are the FP32 tree's output).  Every restart
+ *                      residual and the residual of the returned solution are
+ *                      formed in FP64 (the iterate rounded to FP64, the FP64
+ *                      leaf maps, FP64 norms), so every convergence decision
+ *                      and the reported residual are FP64;
  *   HPS_OUTER_DEFAULT  DF64 for HPS_MIXED, FP64 for HPS_FP64 (the initial state).
  * HPS_EINVAL for other values.  DF64 needs HPS_MIXED leaves: with HPS_FP64
  * leaves hps_gmres_solve returns HPS_EINVAL (there is no silent fallback). */
@@ -268,10 +271,13 @@ int hps_profile_read(hps_ctx* ctx, double* ms, long long* launches, long long* c
  * All workspace lives in one file-scope device array of about 4.6 MB that
  * every GPU which loads the library holds until the process exits.  Its
  * device address is looked up on the first call on each device, with that
- * device current.  Every call shares the array: calls whose work overlaps on
- * the GPU (other streams, other threads) race and must be serialised by the
- * caller.  The call synchronises `stream` once to read the breakdown flag:
- * HPS_ENUMERIC when an interior operator is not positive definite. */
+ * device current; make that first call before any stream capture.  Every call
+ * shares the array: calls whose work overlaps on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  The call synchronises
+ * `stream` once to read the breakdown flag: HPS_ENUMERIC when an interior
+ * operator is not positive definite (this entry has no pivoted fallback), and
+ * T is then undefined for every element.  The caller's current device is the
+ * same on return as on entry. */
 int hps_leaf_maps_noalloc(int device, void* stream, int N, double h, double eta, const double* c, int E,
                           void* T);
 

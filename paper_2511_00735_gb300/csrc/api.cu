@@ -157,8 +157,10 @@ void free_graph(hps_ctx* c) {
 
 void free_numeric(hps_ctx* c) {
   for (auto& s : c->stages) {
-    FREE(s.T); FREE(s.vec);
+    FREE(s.T); FREE(s.vec); FREE(s.gR); FREE(s.gE);
   }
+  FREE(c->gW);
+  c->gamma_nrhs = 0;
   for (auto& l : c->levels) {
     FREE(l.W); FREE(l.U); FREE(l.Dm);
   }
@@ -179,7 +181,9 @@ void free_numeric(hps_ctx* c) {
 
 void free_tree(hps_ctx* c) {
   free_numeric(c);
-  for (auto& s : c->stages) FREE(s.d_es);
+  for (auto& s : c->stages) {
+    FREE(s.d_es); FREE(s.d_nb); FREE(s.d_tdesc);
+  }
   for (auto& l : c->levels) {
     FREE(l.d_dst); FREE(l.d_up); FREE(l.d_xmap); FREE(l.d_mdesc); FREE(l.d_sdesc);
   }
@@ -342,15 +346,20 @@ int hps_create(hps_ctx** out, int device, void* stream) {
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_gemm_err, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&c->d_flag, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_gemm_err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_cerr, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->pin_counts, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->d_flag);
-  cudaFree(c->d_gemm_err);
+    cudaFree(c->d_gemm_err);
+    cudaFree(c->d_cerr);
+    cudaFreeHost(c->pin_counts);
     delete c;
     return HPS_ENOMEM;
   }
   cudaMemset(c->d_flag, 0, sizeof(int));
   cudaMemset(c->d_gemm_err, 0, sizeof(int));
+  cudaMemset(c->d_cerr, 0, sizeof(int));
   *out = c;
   return HPS_OK;
 }
@@ -365,6 +374,9 @@ int hps_destroy(hps_ctx* c) {
   while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
   c->mg_ptr = nullptr;  // freed with every other allocation
   cudaFree(c->d_flag);
+  cudaFree(c->d_gemm_err);
+  cudaFree(c->d_cerr);
+  cudaFreeHost(c->pin_counts);
   for (auto& pe : c->prof_ev) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
@@ -397,7 +409,8 @@ int hps_mesh(hps_ctx* c, int nx, int ny, int N) {
   c->mg_ptr = nullptr;  // freed with every other allocation
   c->d_es_nb = c->d_es_in = c->d_es_out = c->d_es_bdry = c->d_bdry_rows = nullptr;
   c->d_Dref = c->d_Kref = c->d_wref = nullptr;
-  c->d_c = nullptr;
+  c->d_c = c->d_bstage = nullptr;
+  c->d_route = c->d_lists = nullptr;
   c->d_T = nullptr;
   c->have_mesh = c->have_coeff = c->have_leaves = c->have_tree = false;
 
@@ -553,25 +566,27 @@ int hps_set_coeff(hps_ctx* c, double kappa, double eta, const double* b) {
   if (!c->have_mesh) return fail(c, HPS_ENOTBUILT, "hps_mesh first");
   if (!b || !std::isfinite(kappa) || !std::isfinite(eta) || eta == 0.0)
     return fail(c, HPS_EINVAL, "b non-null, finite kappa, finite non-zero eta required");
-  const long long nn = (long long)c->E * (c->N + 1) * (c->N + 1);
-  std::vector<double> bh(nn);
-  if (is_device_ptr(b)) {
-    HPS_CK(c, cudaMemcpy(bh.data(), b, sizeof(double) * nn, cudaMemcpyDeviceToHost));
-  } else {
-    std::memcpy(bh.data(), b, sizeof(double) * nn);
+  const int nn = (c->N + 1) * (c->N + 1);
+  const size_t bytes = sizeof(double) * (size_t)c->E * nn;
+  // the coefficient and route buffers keep their size for the mesh: allocated once, then reused
+  if (!c->d_c) c->d_c = static_cast<double*>(dev_alloc(c, bytes));
+  if (!c->d_route) c->d_route = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)c->E));
+  if (!c->d_lists) c->d_lists = static_cast<int*>(dev_alloc(c, sizeof(int) * (2 * (size_t)c->E + 2)));
+  if (!c->d_c || !c->d_route || !c->d_lists) return fail(c, HPS_ENOMEM, "coefficient");
+  const double* bd = b;
+  if (!is_device_ptr(b)) {
+    if (!c->d_bstage) c->d_bstage = static_cast<double*>(dev_alloc(c, bytes));
+    if (!c->d_bstage) return fail(c, HPS_ENOMEM, "coefficient staging");
+    HPS_CK(c, cudaMemcpyAsync(c->d_bstage, b, bytes, cudaMemcpyHostToDevice, c->stream));
+    bd = c->d_bstage;
   }
-  c->c_host.resize(nn);
-  for (long long i = 0; i < nn; ++i) {
-    if (!std::isfinite(bh[i])) return fail(c, HPS_EINVAL, "non-finite coefficient sample");
-    c->c_host[i] = kappa * kappa * (1.0 - bh[i]);
-  }
-  cudaStreamSynchronize(c->stream);
-  free_numeric(c);
-  if (c->d_c) FREE(c->d_c);
-  if (c->d_T) FREE(c->d_T);
+  // Route per element (leaf.cu): the Cholesky route where the interior operator is provably
+  // positive definite, max c (h/2)^2 < 0.98 * 2 mu_min, the pivoted robust route elsewhere.
+  const double bound = 0.98 * 2.0 * c->mu_min / (0.25 * c->h * c->h);
+  HPS_CK(c, cudaMemsetAsync(c->d_cerr, 0, sizeof(int), c->stream));
+  HPS_CK(c, coeff_route(bd, kappa, c->E, nn, bound, c->d_c, c->d_route, c->d_cerr, 16 * c->num_sms, c->stream));
   c->have_leaves = false;
-  c->d_c = dev_upload(c, c->c_host);
-  if (!c->d_c) return fail(c, HPS_ENOMEM, "coefficient");
+  c->have_tree = false;
   c->kappa = kappa;
   c->eta = eta;
   c->have_coeff = true;
@@ -582,66 +597,81 @@ int hps_build_leaves(hps_ctx* c, int precision) {
   CHECK_CTX(c);
   if (!c->have_coeff) return fail(c, HPS_ENOTBUILT, "hps_set_coeff first");
   if (precision != HPS_FP64 && precision != HPS_MIXED) return fail(c, HPS_EINVAL, "precision");
-  // Route per element: the Cholesky route where the interior operator is provably positive
-  // definite (max c (h/2)^2 < 0.98 * 2 mu_min), the pivoted robust route elsewhere (leaf.cu).
-  const int n1 = c->N + 1;
-  const double bound = 0.98 * 2.0 * c->mu_min / (0.25 * c->h * c->h);
-  std::vector<int> good, bad;
-  for (int e = 0; e < c->E; ++e) {
-    double cm = -1e300;
-    for (int l = 0; l < n1 * n1; ++l) cm = std::max(cm, c->c_host[(size_t)e * n1 * n1 + l]);
-    (cm < bound ? good : bad).push_back(e);
-  }
-  cudaStreamSynchronize(c->stream);
+  cudaStream_t st = c->stream;
+  cudaStreamSynchronize(st);
   free_numeric(c);
   if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
   if (!c->d_T) return fail(c, HPS_ENOMEM, "leaf maps");
+  int* d_good = c->d_lists;
+  int* d_bad = c->d_lists + c->E;
+  int* d_counts = c->d_lists + 2 * (size_t)c->E;
   LeafParams p;
   p.N = c->N; p.q = c->q; p.ni = c->q * c->q; p.nb = c->nb; p.E = c->E; p.cw = 8;
   p.h = c->h; p.eta = c->eta;
   p.c = c->d_c; p.Dh = c->d_Dref; p.Kh = c->d_Kref; p.wh = c->d_wref;
   p.T = c->d_T; p.flag = c->d_flag;
-  HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), st));
+  // the element lists of both routes (from hps_set_coeff's per-element route), their counts to
+  // the host; the positive-definite route's kernel reads its count on the device and runs while
+  // the host waits for the pivoted route's count
+  HPS_CK(c, route_lists(c->d_route, c->E, d_good, d_bad, d_counts, st));
+  HPS_CK(c, cudaMemcpyAsync(c->pin_counts, d_counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  cudaEvent_t ev_counts = nullptr;
+  HPS_CK(c, cudaEventCreateWithFlags(&ev_counts, cudaEventDisableTiming));
+  struct EvGuard {
+    cudaEvent_t e;
+    ~EvGuard() { cudaEventDestroy(e); }
+  } evg{ev_counts};
+  HPS_CK(c, cudaEventRecord(ev_counts, st));
   std::vector<void*> scratch;
-  if (!good.empty()) {
-    const int grid = std::min((int)good.size(), std::max(1, c->num_sms));
+  struct ScratchGuard {
+    hps_ctx* c;
+    std::vector<void*>& v;
+    ~ScratchGuard() {
+      if (!v.empty()) cudaStreamSynchronize(c->stream);
+      for (void* s : v) dev_free(c, s);
+    }
+  } sg{c, scratch};
+  {
+    const int grid = std::min(c->E, std::max(1, c->num_sms));
     double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
     double* Zscr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * 2 * p.ni * c->nb));
-    int* d_good = good.size() == (size_t)c->E ? nullptr : dev_upload(c, good);
-    if (!Ascr || !Zscr || (good.size() != (size_t)c->E && !d_good)) return fail(c, HPS_ENOMEM, "leaf scratch");
-    scratch.push_back(Ascr);
-    scratch.push_back(Zscr);
+    if (Ascr) scratch.push_back(Ascr);
+    if (Zscr) scratch.push_back(Zscr);
+    if (!Ascr || !Zscr) return fail(c, HPS_ENOMEM, "leaf scratch");
     p.Zscr = Zscr;
-    if (d_good) scratch.push_back(d_good);
     p.Ascr = Ascr;
     p.elems = d_good;
-    p.count = (int)good.size();
+    p.count_dev = d_counts;
     PhaseScope ps(c, HPS_PH_LEAF);
-    HPS_CK(c, launch_leaf(p, grid, c->stream));
+    HPS_CK(c, launch_leaf(p, grid, st));
   }
-  if (!bad.empty()) {
+  HPS_CK(c, cudaEventSynchronize(ev_counts));
+  const int n_bad = c->pin_counts[1];
+  if (n_bad > 0) {
     const size_t per = sizeof(double2) * (size_t)p.ni * (p.ni + p.nb);
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(bad.size(), ((size_t)512 << 20) / per));
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_bad, ((size_t)512 << 20) / per));
     double2* W = static_cast<double2*>(dev_alloc(c, per * chunk));
     int* piv = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)chunk * GJ_NB));
     double2* lu = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)chunk * GJ_NB * GJ_NB));
-    int* d_bad = dev_upload(c, bad);
-    if (!W || !piv || !lu || !d_bad) return fail(c, HPS_ENOMEM, "robust leaf workspace");
-    scratch.insert(scratch.end(), {W, piv, lu, d_bad});
+    for (void* q : {(void*)W, (void*)piv, (void*)lu})
+      if (q) scratch.push_back(q);
+    if (!W || !piv || !lu) return fail(c, HPS_ENOMEM, "robust leaf workspace");
     PhaseScope ps(c, HPS_PH_LEAF);
-    for (size_t b0 = 0; b0 < bad.size(); b0 += chunk) {
-      const int nch = (int)std::min<size_t>(chunk, bad.size() - b0);
-      HPS_CK(c, robust_assemble(p, d_bad + b0, nch, W, c->stream));
-      HPS_CK(c, gj_solve<double>(W, p.ni, p.ni + p.nb, nch, piv, lu, c->d_flag, c->stream));
-      HPS_CK(c, robust_finish(p, d_bad + b0, nch, W, c->stream));
+    for (int b0 = 0; b0 < n_bad; b0 += chunk) {
+      const int nch = std::min(chunk, n_bad - b0);
+      HPS_CK(c, robust_assemble(p, d_bad + b0, nch, W, st));
+      HPS_CK(c, gj_solve<double>(W, p.ni, p.ni + p.nb, nch, piv, lu, c->d_flag, st));
+      HPS_CK(c, robust_finish(p, d_bad + b0, nch, W, st));
     }
   }
-  int flag = 0;
-  HPS_CK(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  HPS_CK(c, cudaStreamSynchronize(c->stream));
-  for (void* s : scratch) dev_free(c, s);
-  if (flag) return fail(c, HPS_ENUMERIC, "singular element system (zero pivot or non-positive Cholesky pivot)");
-  c->n_robust = (int)bad.size();
+  int* flags = c->pin_counts;  // the counts were read above; reuse the pinned words for the flags
+  HPS_CK(c, cudaMemcpyAsync(&flags[0], c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HPS_CK(c, cudaMemcpyAsync(&flags[1], c->d_cerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HPS_CK(c, cudaStreamSynchronize(st));
+  if (flags[1]) return fail(c, HPS_EINVAL, "non-finite coefficient sample");
+  if (flags[0]) return fail(c, HPS_ENUMERIC, "singular element system (zero pivot or non-positive Cholesky pivot)");
+  c->n_robust = n_bad;
   c->precision = precision;
   c->have_leaves = true;
   return HPS_OK;
@@ -703,11 +733,15 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
     if (!c->d_T) c->d_T = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)c->E * c->nb * c->nb));
     if (!c->d_T) return fail(c0, HPS_ENOMEM, "leaf maps");
     const int n1 = c->N + 1;
-    const double bound = 0.98 * 2.0 * c->mu_min / (0.25 * c->h * c->h);
+    // the per-element routes and the finiteness flag from hps_set_coeff's kernel
+    std::vector<int> route(c->E);
+    int cerr = 0;
+    HPS_CK(c0, cudaMemcpyAsync(route.data(), c->d_route, sizeof(int) * c->E, cudaMemcpyDeviceToHost, c->stream));
+    HPS_CK(c0, cudaMemcpyAsync(&cerr, c->d_cerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    HPS_CK(c0, cudaStreamSynchronize(c->stream));
+    if (cerr) return fail(c0, HPS_EINVAL, "non-finite coefficient sample in the batch");
     for (int e = 0; e < c->E; ++e) {
-      double cm = -1e300;
-      for (int l = 0; l < n1 * n1; ++l) cm = std::max(cm, c->c_host[(size_t)e * n1 * n1 + l]);
-      if (cm < bound) {
+      if (route[e] == 0) {
         LeafElem d;
         d.c = c->d_c + (size_t)e * n1 * n1;
         d.T = c->d_T + (size_t)e * c->nb * c->nb;
@@ -791,7 +825,11 @@ int hps_release_workspace(hps_ctx* c) {
   CHECK_CTX(c);
   HPS_CK(c, cudaStreamSynchronize(c->stream));
   free_solver(c);
-  for (auto& s : c->stages) FREE(s.vec);
+  for (auto& s : c->stages) {
+    FREE(s.vec); FREE(s.gR); FREE(s.gE);
+  }
+  FREE(c->gW);
+  c->gamma_nrhs = 0;
   FREE(c->sw_x);
   FREE(c->cg_V); FREE(c->cg_w); FREE(c->cg_W); FREE(c->cg_H); FREE(c->cg_h1); FREE(c->cg_h2);
   FREE(c->cg_nrm); FREE(c->cg_y); FREE(c->cg_g); FREE(c->cg_s); FREE(c->cg_part);

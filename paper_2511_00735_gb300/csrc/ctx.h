@@ -28,6 +28,11 @@ struct Stage {
   int* d_es = nullptr;       // device copy (stage 0 and coarse stage)
   void* T = nullptr;         // [nsub][n][n] ItI maps, tree precision
   void* vec = nullptr;       // [nsub * n][nrhs_cap] sweep vector, tree precision
+  // gamma-cycle (stages k >= 1): the stage system M_{k+1} e = e_nb + T e on these rows
+  int* d_nb = nullptr;       // [nsub * n] stage row across the face (-1 on the physical boundary)
+  GemmDesc* d_tdesc = nullptr;  // [nsub] the n x n product T_s e_s of each subdomain
+  void* gR = nullptr;        // [nsub * n][nrhs_cap] restricted residual of the coarse calls
+  void* gE = nullptr;        // [nsub * n][nrhs_cap] accumulated coarse correction
 };
 
 struct Level {               // merge l: stage l-1 -> stage l
@@ -87,11 +92,15 @@ struct hps_ctx {
   double *d_Dref = nullptr, *d_Kref = nullptr, *d_wref = nullptr;
   double mu_min = 0;           // smallest eigenvalue of K_ii w.r.t. W_ii (reference element)
 
-  // coefficient
+  // coefficient (computed on the device by hps_set_coeff, with each element's leaf route)
   bool have_coeff = false;
   double kappa = 0, eta = 0;
-  std::vector<double> c_host;
   double* d_c = nullptr;
+  double* d_bstage = nullptr;  // device copy of host samples b
+  int* d_route = nullptr;      // [E] 0: positive-definite route, 1: pivoted route
+  int* d_lists = nullptr;      // [2E + 2]: elements of each route, then the two counts
+  int* d_cerr = nullptr;       // set by the coefficient kernel on a non-finite sample
+  int* pin_counts = nullptr;   // pinned host mirror of the two route counts
 
   // leaves
   bool have_leaves = false;
@@ -114,6 +123,9 @@ struct hps_ctx {
   std::vector<hps::Level> levels;  // levels[l] for l = 1..L_exact (levels[0] unused)
   hps::Coarse coarse;
   int nrhs_cap = 0;                // sweep buffers sized for this many columns
+  int gamma = 1;                   // coarse calls per level of the preconditioner (1: V-cycle)
+  int gamma_nrhs = 0;              // gamma-cycle buffers (Stage gR, gE, gW) sized for this many columns
+  void* gW = nullptr;              // gamma-cycle product T e of the largest stage
   void* gemm_ws = nullptr;         // split-K partial products
   size_t gemm_ws_elems = 0;
   void* ws_X1 = nullptr;           // merge workspaces
@@ -139,7 +151,7 @@ struct hps_ctx {
   // generation); the graph reads its input and output pointers from mg_ptr
   long long vc_gen = 0;            // bumped whenever a V-cycle buffer is (re)allocated or freed
   cudaGraphExec_t mg_exec = nullptr;
-  int mg_nrhs = 0, mg_k = 0;
+  int mg_nrhs = 0, mg_k = 0, mg_gamma = 1;
   long long mg_gen = -1, mg_count = 0;  // buffer generation and kernel count of the captured graph
   bool mg_nograph = false;         // capture failed once: launch directly
   cudaStream_t gs = nullptr;       // capture / replay stream of the graph

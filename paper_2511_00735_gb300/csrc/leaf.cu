@@ -21,6 +21,7 @@
 // One persistent CTA per SM (the factor needs almost all of the 227 KB of
 // shared memory); CTAs stride over the elements.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "dense.cuh"
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
   for (int l = tid; l < n1 * n1; l += nth) sK[l] = p.Kh[l];
   for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
 
-  const int nel = (p.elems || p.ed) ? p.count : p.E;
+  const int nel = p.count_dev ? *p.count_dev : (p.elems || p.ed) ? p.count : p.E;
   for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
     const int e = p.elems ? p.elems[ei] : ei;
     const double h = p.ed ? p.ed[ei].h : p.h;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
     swd[l] = to_df(p.wh[l]);
   }
 
-  const int nel = (p.elems || p.ed) ? p.count : p.E;
+  const int nel = p.count_dev ? *p.count_dev : (p.elems || p.ed) ? p.count : p.E;
   for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
     const int e = p.elems ? p.elems[ei] : ei;
     const double h = p.ed ? p.ed[ei].h : p.h;
@@ -917,6 +918,100 @@ size_t leaf_ir_smem_bytes(int N) {
   const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
   return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 2 * (IR_NT / 32)) +
          sizeof(float2) * (2 * n1 * n1 + 3 * n1);
+}
+
+namespace {
+
+// One warp per element: c at its nodes, the maximum of c and the finiteness of b by warp
+// reductions.
+__global__ void coeff_route_kernel(const double* __restrict__ b, double k2, int E, int nn, double bound,
+                                   double* __restrict__ c, int* __restrict__ route, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < E; e += gridDim.x * wpb) {
+    const double* be = b + (long long)e * nn;
+    double* ceo = c + (long long)e * nn;
+    double cm = -INFINITY;
+    bool finite = true;
+    for (int l = lane; l < nn; l += 32) {
+      const double bv = be[l];
+      finite = finite && isfinite(bv);
+      const double cv = k2 * (1.0 - bv);
+      ceo[l] = cv;
+      cm = fmax(cm, cv);
+    }
+    for (int o = 16; o > 0; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    const bool all_finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) {
+      route[e] = cm < bound ? 0 : 1;
+      if (!all_finite) atomicExch(err, 1);
+    }
+  }
+}
+
+// Single CTA of 1024 threads: chunk by chunk, ballots give each element's rank within its
+// warp, a scan over the 32 warp totals its rank within the chunk.
+__global__ void __launch_bounds__(1024) route_lists_kernel(const int* __restrict__ route, int E,
+                                                           int* __restrict__ good, int* __restrict__ bad,
+                                                           int* __restrict__ counts) {
+  __shared__ int wg[32], wb[32], tot[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int base_g = 0, base_b = 0;
+  for (int e0 = 0; e0 < E; e0 += 1024) {
+    const int e = e0 + tid;
+    const int r = e < E ? route[e] : -1;
+    const unsigned bg = __ballot_sync(0xffffffffu, r == 0), bb = __ballot_sync(0xffffffffu, r == 1);
+    if (lane == 0) {
+      wg[w] = __popc(bg);
+      wb[w] = __popc(bb);
+    }
+    __syncthreads();
+    if (w == 0) {
+      const int vg = wg[lane], vb = wb[lane];
+      int ig = vg, ib = vb;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int tg = __shfl_up_sync(0xffffffffu, ig, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+          ig += tg;
+          ib += tb;
+        }
+      }
+      wg[lane] = ig - vg;
+      wb[lane] = ib - vb;
+      if (lane == 31) {
+        tot[0] = ig;
+        tot[1] = ib;
+      }
+    }
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+    if (r == 0) good[base_g + wg[w] + __popc(bg & below)] = e;
+    if (r == 1) bad[base_b + wb[w] + __popc(bb & below)] = e;
+    base_g += tot[0];
+    base_b += tot[1];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    counts[0] = base_g;
+    counts[1] = base_b;
+  }
+}
+
+}  // namespace
+
+cudaError_t coeff_route(const double* b, double kappa, int E, int nn, double bound, double* c, int* route, int* err,
+                        int grid, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  grid = std::max(1, std::min(grid, (E + 7) / 8));
+  coeff_route_kernel<<<grid, 256, 0, s>>>(b, kappa * kappa, E, nn, bound, c, route, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t route_lists(const int* route, int E, int* good, int* bad, int* counts, cudaStream_t s) {
+  route_lists_kernel<<<1, 1024, 0, s>>>(route, E, good, bad, counts);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s) {

@@ -92,29 +92,12 @@ int scratch_on(int device, double** out) {
   return HPS_OK;
 }
 
-}  // namespace
-}  // namespace hps
-
-extern "C" int hps_leaf_maps_noalloc(int device, void* stream, int N, double h, double eta, const double* c, int E,
-                                     void* T) {
-  using namespace hps;
-  if (N < 2 || N > NA_MAX_N) return HPS_EINVAL;        // larger orders exceed the static workspace
-  if (E < 1 || !c || !T || !(h > 0.0) || !std::isfinite(eta) || eta == 0.0) return HPS_EINVAL;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
-    cudaGetLastError();
-    return HPS_ENODEV;
-  }
-  if (device < 0 || device >= ndev) return HPS_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) {
-    cudaGetLastError();
-    return HPS_ECUDA;
-  }
+int leaf_maps_noalloc_on(int device, cudaStream_t st, int N, double h, double eta, const double* c, int E,
+                         void* T) {
   optin_all_once();
   double* base = nullptr;
   int rc = scratch_on(device, &base);
   if (rc != HPS_OK) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   const int grid = std::min(E, std::min(NA_MAX_GRID, std::max(1, sms)));
@@ -169,4 +152,37 @@ extern "C" int hps_leaf_maps_noalloc(int device, void* stream, int N, double h, 
     return HPS_ECUDA;
   }
   return hflag ? HPS_ENUMERIC : HPS_OK;
+}
+
+}  // namespace
+}  // namespace hps
+
+// The caller's current device is restored on every return path: this entry takes a bare
+// device index, so it must not leave a multi-device caller on another device.
+extern "C" int hps_leaf_maps_noalloc(int device, void* stream, int N, double h, double eta, const double* c, int E,
+                                     void* T) {
+  using namespace hps;
+  if (N < 2 || N > NA_MAX_N) return HPS_EINVAL;        // larger orders exceed the static workspace
+  if (E < 1 || !c || !T || !(h > 0.0) || !std::isfinite(eta) || eta == 0.0) return HPS_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return HPS_ENODEV;
+  }
+  if (device < 0 || device >= ndev) return HPS_EINVAL;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    prev = -1;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ECUDA;
+  }
+  const int rc = leaf_maps_noalloc_on(device, static_cast<cudaStream_t>(stream), N, h, eta, c, E, T);
+  if (prev >= 0 && prev != device && cudaSetDevice(prev) != cudaSuccess) {
+    cudaGetLastError();
+    return rc != HPS_OK ? rc : HPS_ECUDA;
+  }
+  return rc;
 }

@@ -29,7 +29,17 @@ struct LeafParams {
   double* Zscr = nullptr;        // [gridDim.x][2][ni][nb] per-CTA workspace (the double-float iterate Z
                                  // and the residual's first Kronecker sums): selects the refined FP32
                                  // factorisation (leaf_ir_smem_bytes); null: the FP64 one
+  const int* count_dev = nullptr;  // optional device count of `elems` (read by the kernel; overrides count)
 };
+// c = kappa^2 (1 - b) at every element node (section 2, eq. diffhelm) from the samples b
+// [E][nn], and the leaf route of each element: route[e] = 0 when max over its nodes of c is
+// below `bound` (the interior operator is provably positive definite), 1 otherwise.  A
+// non-finite sample sets *err to 1 (the other outputs are then meaningless).
+cudaError_t coeff_route(const double* b, double kappa, int E, int nn, double bound, double* c, int* route, int* err,
+                        int grid, cudaStream_t s);
+// Stable compaction of the routes: good = the elements with route 0, bad = those with route 1,
+// both in increasing element order; counts[0] = |good|, counts[1] = |bad|.  One CTA.
+cudaError_t route_lists(const int* route, int E, int* good, int* bad, int* counts, cudaStream_t s);
 size_t leaf_ir_smem_bytes(int N);
 size_t leaf_smem_bytes(int N, int cw);
 cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s);

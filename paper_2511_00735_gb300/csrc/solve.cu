@@ -1,6 +1,10 @@
 // C ABI, second half: merge levels, skeleton RHS / matvec / preconditioner in
 // the skeleton ("face") order, and the flexible GMRES (section 4.3), in FP64 or
-// (mixed path) in double-float arithmetic with FP64 restart residuals.
+// (mixed path) with its Arnoldi steps in double-float arithmetic.  On both paths
+// every restart residual and the residual of the returned solution is formed
+// with the FP64 matvec from the FP64 value of the iterate, so every convergence
+// decision and every reported residual is an FP64 residual (FGMRES as iterative
+// refinement, section 4.3).
 //
 // FGMRES runs on the element-side layout with residual-like vectors (the
 // Arnoldi basis V) in outgoing coordinates rho = Pi r and solution-like
@@ -293,20 +297,19 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
   if (df) HPS_CK(c, cudaMemsetAsync(c->df_x, 0, sizeof(float4) * (size_t)vs, st));
   else HPS_CK(c, zero<double>(c->fg_x, vs, st));
 
-  // Explicit residual of the current iterate and its squared norms in hbuf[0..nrhs): FP64 in
-  // fg_w, or (df) double-float in df_w (products error-free, sums by TwoSum: about 48 bits,
-  // the residual's norm to ~1e-5 relative at a 1e-10 relative residual).
+  // Explicit FP64 residual w = RHS - Pi M x of the current iterate and its squared norms in
+  // hbuf[0..nrhs), on both paths.  The double-float path first rounds its iterate to FP64
+  // (pv_in; that FP64 vector is also the one returned), forms the residual with the FP64
+  // leaf maps in pv_out and restarts from it (rounded to double-float in df_w).
   auto residual = [&]() -> int {
+    double2* w64 = df ? c->pv_out : c->fg_w;
     {
       PhaseScope ps(c, HPS_PH_MATVEC);
-      if (df) {
-        HPS_CK(c, df_matvec<float4>(c->df_T, c->d_es_nb, c->df_x, c->df_rhs, c->df_w, c->E, c->nb, nrhs, grid, st));
-      } else {
-        HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, c->fg_x, c->fg_rhs, c->fg_w, c->E, c->nb, nrhs, grid, st));
-      }
+      if (df) HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
+      HPS_CK(c, es_matvec(c->d_T, c->d_es_nb, df ? c->pv_in : c->fg_x, c->fg_rhs, w64, c->E, c->nb, nrhs, grid, st));
     }
-    if (df) HPS_CK(c, df_bdot(c->df_w, 0, 1, c->df_w, n, nrhs, c->df_part, hbuf, st));
-    else HPS_CK(c, bdot<double>(c->fg_w, 0, 1, c->fg_w, n, nrhs, c->fg_part, hbuf, 0, st));
+    HPS_CK(c, bdot<double>(w64, 0, 1, w64, n, nrhs, c->fg_part, hbuf, 0, st));
+    if (df) HPS_CK(c, df_from_d(c->df_w, w64, vs, st));
     HPS_CK(c, cudaMemcpyAsync(c->pin_h, hbuf, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, st));
     HPS_CK(c, cudaStreamSynchronize(st));
     return HPS_OK;
@@ -723,10 +726,9 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     rc = residual();
     if (rc) return rc;
   }
-  if (df) HPS_CK(c, df_to_d(c->pv_in, c->df_x, vs, st));
   std::vector<double> nrm2(nrhs);
   for (int r = 0; r < nrhs; ++r) nrm2[r] = c->pin_h[r].x;
-  // solution in skeleton order
+  // solution in skeleton order (df: the FP64 iterate whose residual was just formed, in pv_in)
   const double2* x64 = df ? c->pv_in : c->fg_x;
   double2* gdev = static_cast<double2*>(g_out);
   const bool host_out = !is_device_ptr(g_out);

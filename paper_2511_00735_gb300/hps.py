@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libhps.so")
 
 HPS_OK = 0
 HPS_ENOTCONV = -4
+HPS_ENUMERIC = -9
 HPS_FP64 = 0
 HPS_MIXED = 1
 OUTER_DEFAULT = -1  # outer FGMRES arithmetic (hps_set_outer_arith)

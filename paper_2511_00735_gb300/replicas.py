@@ -36,11 +36,25 @@ def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     return float(v.item())
 
 
+def sum_over_ranks(x: float, dist=None, device="cpu") -> float:
+    if dist is None:
+        return float(x)
+    import torch
+
+    v = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(v.item())
+
+
 class WallClock:
     """Host timer with the interface of `CudaEventClock` (for CPU ranks and tests)."""
 
     def start(self):
         self.t0 = time.perf_counter()
+        self.marks = [self.t0]
+
+    def lap(self):
+        self.marks.append(time.perf_counter())
 
     def stop(self):
         self.t1 = time.perf_counter()
@@ -48,25 +62,40 @@ class WallClock:
     def elapsed_ms(self) -> float:
         return (self.t1 - self.t0) * 1e3
 
+    def laps_ms(self) -> list:
+        return [(b - a) * 1e3 for a, b in zip(self.marks, self.marks[1:])]
+
 
 class CudaEventClock:
-    """CUDA events recorded on the stream the work is launched on."""
+    """CUDA events recorded on the stream the work is launched on (one more after each step,
+    so the per-step device times are known too)."""
 
     def __init__(self, stream):
         import torch
 
+        self.torch = torch
         self.stream = stream
         self.e0 = torch.cuda.Event(enable_timing=True)
         self.e1 = torch.cuda.Event(enable_timing=True)
+        self.marks = []
 
     def start(self):
         self.e0.record(self.stream)
+        self.marks = [self.e0]
+
+    def lap(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.marks.append(e)
 
     def stop(self):
         self.e1.record(self.stream)
 
     def elapsed_ms(self) -> float:  # valid once the stream has passed e1 (the closing barrier syncs)
         return self.e0.elapsed_time(self.e1)
+
+    def laps_ms(self) -> list:
+        return [a.elapsed_time(b) for a, b in zip(self.marks, self.marks[1:])]
 
 
 def timed(fn, k: int, clock, dist=None, sync=None, device="cpu"):
@@ -77,7 +106,10 @@ def timed(fn, k: int, clock, dist=None, sync=None, device="cpu"):
     barrier(dist, sync)
     w0 = time.perf_counter()
     clock.start()
-    out = [fn() for _ in range(k)]
+    out = []
+    for _ in range(k):
+        out.append(fn())
+        clock.lap()
     clock.stop()
     barrier(dist, sync)
     wall_ms = (time.perf_counter() - w0) * 1e3

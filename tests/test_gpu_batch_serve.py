@@ -5,10 +5,12 @@ overlap the problems' merges and solves on their own streams; the serving loop
 batches requests for a cached tree into one multi-RHS solve.  Tolerances: the
 same arithmetic per right-hand side (1e-12 relative for batches; 1e-8 for
 served requests, whose FGMRES runs with other right-hand sides in lockstep so
-split-K decisions may reorder sums), and every solve at residual <= 1e-10.
+split-K decisions may reorder sums), every solve at residual <= 1e-10, and
+batched and served solutions within 1e-8 of the oracle's dense solve.
 """
 import numpy as np
 import pytest
+import scipy.linalg as sla
 
 torch = pytest.importorskip("torch")
 
@@ -82,10 +84,17 @@ def test_serve_same_alone_and_in_mix(gpu):
     srv.close()
     assert stats["requests"] == 24 and stats["max_rel_residual"] <= 1e-10
     assert stats["mean_batch"] > 1.0  # requests for a busy tree joined its next solve
+    lus = {}
     for r in reqs:
         g1, info1 = B.solve_alone(r.prob, H.HPS_MIXED)
         assert max(info1["rel_residual"]) <= 1e-10
         assert rel(r.g, g1) <= 1e-8, r.rid
+        # every served request against the oracle's dense solve of M g = RHS (one LU per tree)
+        op = OracleProblem(r.prob)
+        if r.prob.name not in lus:
+            lus[r.prob.name] = sla.lu_factor(assemble_M(op.mesh, op.Ts))
+        for k in range(r.prob.nrhs):
+            assert rel(r.g[k], sla.lu_solve(lus[r.prob.name], op.rhs[k])) < 1e-8, (r.rid, k)
 
 
 def test_admission_cap_evicts_idle_trees(gpu):

@@ -288,13 +288,17 @@ def test_64x64_N16_sampled(solver):
     assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10
     rhs = solver.rhs(dev(t))
     r = host(rhs) - host(solver.matvec(g))
-    assert np.max(np.linalg.norm(r, axis=1) / np.linalg.norm(host(rhs), axis=1)) <= 1.01e-10
+    res = np.linalg.norm(r, axis=1) / np.linalg.norm(host(rhs), axis=1)
+    # the reported residual is the FP64 residual of the returned solution (summation order aside)
+    assert np.max(np.abs(res - np.array(info["rel_residual"]))) <= 1e-15
+    assert np.max(res) <= 1e-10 + 1e-15
 
 
 def test_64x64_N16_mixed_residual_in_fp64(solver):
-    """Mixed path at the benchmark's size (FP32 tree and sweeps, double-float outer iteration):
-    the solution's residual recomputed with the FP64 skeleton matvec, a kernel the mixed solve
-    does not use, is at the 1e-10 tolerance (section 4.3: FGMRES as iterative refinement)."""
+    """Mixed path at 64x64 (FP32 tree and sweeps, double-float Arnoldi steps): the residual the
+    solve reports is the FP64 residual of the solution it returns, recomputed here through the
+    FP64 RHS and matvec entry points, and it meets the 1e-10 tolerance with no slack (section
+    4.3: FGMRES as iterative refinement)."""
     prob = inputs.fp64_64x64(seed=1, nrhs=4)
     t = H.setup(solver, prob, H.HPS_MIXED)
     solver.merge_levels(prob.L_exact)
@@ -302,4 +306,7 @@ def test_64x64_N16_mixed_residual_in_fp64(solver):
     assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10
     rhs = solver.rhs(dev(t))
     r = host(rhs) - host(solver.matvec(g))
-    assert np.max(np.linalg.norm(r, axis=1) / np.linalg.norm(host(rhs), axis=1)) <= 1.01e-10
+    res = np.linalg.norm(r, axis=1) / np.linalg.norm(host(rhs), axis=1)
+    # the reported residual is the FP64 residual of the returned solution (summation order aside)
+    assert np.max(np.abs(res - np.array(info["rel_residual"]))) <= 1e-15
+    assert np.max(res) <= 1e-10 + 1e-15
