@@ -134,6 +134,41 @@ def leaf_solution(N: int, h: float, c, eta: float, f_in, btilde=None):
     return np.linalg.solve(L, b)
 
 
+def corner_values(N: int, u):
+    """Corner post-processing (section 3.1: the corners are removed from the discretization and
+    "recalculated later in post-processing").  Reading: the value at a corner is the mean of the
+    two one-sided extrapolations along the element edges that meet there, each the value at the
+    edge's end point of the degree N-2 polynomial through that edge's N-1 non-corner nodes.
+    Exact for fields whose edge restrictions have degree <= N-2; spectrally accurate for smooth
+    fields.  Returns a copy of u (all (N+1)^2 nodes) with the four corners filled."""
+    from .gll import gll_rule
+
+    xi, _ = gll_rule(N)
+    inner = xi[1:N]
+
+    def end_weights(x_end):
+        # Lagrange basis of the interior nodes evaluated at x_end
+        w = np.ones(N - 1)
+        for j in range(N - 1):
+            for k in range(N - 1):
+                if k != j:
+                    w[j] *= (x_end - inner[k]) / (inner[j] - inner[k])
+        return w
+
+    wl, wr = end_weights(-1.0), end_weights(1.0)
+    u = np.array(u, dtype=np.complex128).reshape(-1).copy()
+    q = range(1, N)
+    left = np.array([u[node(N, 0, j)] for j in q])
+    right = np.array([u[node(N, N, j)] for j in q])
+    bottom = np.array([u[node(N, i, 0)] for i in q])
+    top = np.array([u[node(N, i, N)] for i in q])
+    u[node(N, 0, 0)] = 0.5 * (wl @ left + wl @ bottom)
+    u[node(N, 0, N)] = 0.5 * (wr @ left + wl @ top)
+    u[node(N, N, 0)] = 0.5 * (wl @ right + wr @ bottom)
+    u[node(N, N, N)] = 0.5 * (wr @ right + wr @ top)
+    return u
+
+
 def interior_weights(N: int, h: float):
     """w_i w_j at every node (used to form b~ = w_i w_j s, reading A7)."""
     _, w, _, _, _ = element_1d(N, h)

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle.leaf import index_sets, leaf_solution
+from oracle.leaf import corner_values, index_sets, interior_weights, leaf_solution
 from oracle.problem import OracleProblem, coefficient
 from oracle.skeleton import Mesh, apply_M, assemble_M, element_incoming, volume_system
 from paper_2511_00735_gb300 import inputs
@@ -66,6 +66,18 @@ def test_manufactured_solution_b_nonzero():
     assert np.linalg.norm(g - gex) / np.linalg.norm(gex) < 1e-7
     gd = op.solve_direct()[0]
     assert np.linalg.norm(gd - g) / np.linalg.norm(g) < 1e-12
+    # the volume field with the source (b~ = w_i w_j s) and the corners post-processed equals
+    # the plane wave at every node, corners included
+    mesh = op.mesh
+    c = coefficient(mesh, kappa, bumps)
+    w2 = interior_weights(p.N, mesh.h)
+    err = 0.0
+    for e in range(mesh.E):
+        X, Y = mesh.node_xy(e)
+        u = leaf_solution(p.N, mesh.h, c[e], kappa, element_incoming(mesh, g, op.ts[0], e), w2 * source(X, Y))
+        u = corner_values(p.N, u)
+        err = max(err, np.max(np.abs(u - inputs.plane_wave(theta, kappa, X, Y))))
+    assert err < 1e-6, err
 
 
 def test_direct_hps_equals_dense_and_volume_solve():

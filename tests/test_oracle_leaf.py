@@ -141,3 +141,57 @@ def test_manufactured_source_weighting():
     # and the closed impedance relation I_o u = T I_i u + H
     out = leaf_itI(N, h, c, kappa, btilde=btilde)
     np.testing.assert_allclose(out["T"] @ fin + out["H"], fout, atol=1e-7 * np.abs(fout).max())
+
+
+# ---------------------------------------------------------------- corner post-processing
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_corner_values_exact_for_low_degree_edges(N):
+    # edge restrictions of degree <= N-2 are extrapolated exactly (closed form)
+    from oracle.gll import gll_rule
+    from oracle.leaf import corner_values, index_sets, node
+
+    xi, _ = gll_rule(N)
+    X = np.repeat(xi, N + 1)
+    Y = np.tile(xi, N + 1)
+    d = N - 2
+    u = (1 + 0.5j) * X ** d * Y ** (d // 2) - 2.0 * Y ** d + 0.3j * X * Y + 1.0
+    v = u.copy()
+    for k in index_sets(N)["corners"]:
+        v[k] = 99.0
+    w = corner_values(N, v)
+    for i, j in ((0, 0), (0, N), (N, 0), (N, N)):
+        assert abs(w[node(N, i, j)] - u[node(N, i, j)]) < 1e-11
+    assert np.array_equal(np.delete(w, index_sets(N)["corners"]), np.delete(u, index_sets(N)["corners"]))
+
+
+def test_corner_values_of_a_plane_wave_converge_spectrally():
+    from oracle.gll import gll_rule
+    from oracle.leaf import corner_values, index_sets
+
+    errs = []
+    for N in (8, 12, 16):
+        xi, _ = gll_rule(N)
+        X = np.repeat(xi, N + 1)
+        Y = np.tile(xi, N + 1)
+        u = np.exp(1j * 1.2 * (0.6 * X + 0.8 * Y))  # kappa h / 2 = 1.2
+        c = index_sets(N)["corners"]
+        v = u.copy()
+        v[c] = 0.0
+        errs.append(np.max(np.abs(corner_values(N, v)[c] - u[c])))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9, errs
+
+
+def test_corner_values_take_each_edge_to_its_own_end():
+    # u = x + 2y is linear along every edge: each corner must get its own value; an
+    # extrapolation taken to the wrong end of an edge (a swapped weight vector) is off by O(1)
+    from oracle.gll import gll_rule
+    from oracle.leaf import corner_values, node
+
+    N = 8
+    xi, _ = gll_rule(N)
+    X = np.repeat(xi, N + 1)
+    Y = np.tile(xi, N + 1)
+    u = X + 2.0 * Y + 0.0j
+    w = corner_values(N, u)
+    for i, j, val in ((0, 0, -3.0), (0, N, 1.0), (N, 0, -1.0), (N, N, 3.0)):
+        assert abs(w[node(N, i, j)] - val) < 1e-12, (i, j)
