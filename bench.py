@@ -496,16 +496,20 @@ def cpu_baseline(workload: str, nrhs: int, iterations: int, samples: int = 1) ->
 
 # ---------------------------------------------------------------------------- batching / serving
 def run_table1(args, prec):
-    """Memory-time trade-off of section 5 (Table 1) on the 64x64 workload: for each number of
-    exactly merged levels and each count of coarse GMRES steps, the device bytes held by the
-    tree (PMem), the merge time (Bt), the FGMRES iterations (It) and the solve time (St), plus
-    direct HPS (exact coarse level).  Times are CUDA events on the library's stream."""
+    """Memory-time trade-off of section 5 (Table 1) on the 64x64, N = 16, kappa = 100 problem, one
+    right-hand side as in the paper: for #levels = L_exact + 1 = 2..12 the device bytes of the tree
+    beyond the leaf maps (PMem) and the merge time (Bt), and FGMRES iterations (It) and solve time
+    (St) for gamma = 1 with 4, 5, 6 coarse GMRES steps and gamma = 2 with 2, 3, 4 (up to #levels 7,
+    as in the paper), plus direct HPS (exact coarse level) and unpreconditioned GMRES.  Times are
+    CUDA events on the library's stream; each solve runs once untimed first (V-cycle graph
+    capture)."""
     import torch
 
     from paper_2511_00735_gb300 import hps as H
     from paper_2511_00735_gb300 import inputs
 
-    prob = inputs.fp64_64x64(seed=1, nrhs=args.nrhs)
+    nrhs = args.nrhs or 1
+    prob = inputs.fp64_64x64(seed=1, nrhs=nrhs)
     s = H.Solver(0)
     stream = torch.cuda.current_stream(0)
     t = H.setup(s, prob, prec, build=True)
@@ -522,29 +526,47 @@ def run_table1(args, prec):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
-    def solve(ci):
-        return s.gmres_solve(t_dev, tol=args.tol, inner_iters=ci, restart=60, max_outer=20, out=g_dev,
+    def solve(ci, restart=60, max_outer=20):
+        return s.gmres_solve(t_dev, tol=args.tol, inner_iters=ci, restart=restart, max_outer=max_outer, out=g_dev,
                              raise_on_notconv=False)[1]
 
     rows = []
-    cases = [(lx, False) for lx in range(1, s.levels, 2)] + [(s.levels - 1, True)]
+
+    def emit(row):
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+
+    # unpreconditioned FGMRES (PMem 0, Bt 0)
+    solve(-1, 60, 40)
+    st, info = ev_ms(lambda: solve(-1, 60, 40))
+    emit({"levels": 0, "coarse": "none (unpreconditioned)", "gamma": 0, "pmem_bytes": 0, "bt_ms": 0.0,
+          "it": info["outer_iterations"], "converged": info["converged"], "st_ms": st,
+          "max_rel_residual": info["max_rel_residual"]})
+    cases = [(lx, False) for lx in range(1, s.levels)] + [(s.levels - 1, True)]
     for lx, exact in cases:
         s.release_workspace()
+        s.set_gamma(1)
+        s.merge_levels(lx, exact_coarse=exact)  # plan for this depth, then the timed build
         bt, _ = ev_ms(lambda: s.merge_levels(lx, exact_coarse=exact))
         held = s.bytes_held()
-        for ci in ([0] if exact else [2, 4, 6]):
-            solve(ci)  # first solve of a tree captures the V-cycle graph
+        cols = [(1, 0)] if exact else [(1, ci) for ci in (4, 5, 6)] + (
+            [(2, ci) for ci in (2, 3, 4)] if lx + 1 <= 7 else [])
+        for gamma, ci in cols:
+            s.set_gamma(gamma)
+            solve(ci)  # first solve of a configuration captures the V-cycle graph
             st, info = ev_ms(lambda: solve(ci))
-            rows.append({"levels": lx + 1, "L_exact": lx, "coarse": "exact" if exact else f"{ci} c.i.",
-                         "pmem_bytes": held - leaf_bytes, "bytes_held_tree": held, "bt_ms": bt,
-                         "it": info["outer_iterations"], "converged": info["converged"], "st_ms": st,
-                         "max_rel_residual": info["max_rel_residual"]})
-            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            emit({"levels": lx + 1, "L_exact": lx, "coarse": "exact" if exact else f"{ci} c.i.", "gamma": gamma,
+                  "pmem_bytes": held - leaf_bytes, "bytes_held_tree": held, "bt_ms": bt,
+                  "it": info["outer_iterations"], "converged": info["converged"], "st_ms": st,
+                  "max_rel_residual": info["max_rel_residual"]})
+    s.set_gamma(1)
     s.close()
-    return {"metric": "memory-time trade-off (section 5, Table 1): PMem, Bt, It, St by levels and coarse steps",
+    return {"metric": "memory-time trade-off (section 5, Table 1): PMem, Bt, It, St by levels, coarse steps, gamma",
             "value": None, "unit": None, "n_gpus": 1, "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["scattering64"][0].replace("L_exact=10, 5 coarse GMRES steps", "L_exact and coarse steps swept"),
-                       "precision": args.precision, "tol": args.tol, "leaf_bytes": leaf_bytes},
+            "config": {"workload": WORKLOADS["scattering64"][0].replace(
+                "16 plane-wave RHS, L_exact=10, 5 coarse GMRES steps",
+                f"{nrhs} plane-wave RHS, L_exact, coarse steps and gamma swept"),
+                "precision": args.precision, "tol": args.tol, "leaf_bytes": leaf_bytes},
             "rows": rows}
 
 
@@ -619,27 +641,43 @@ def run_phase(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     info = None
+    prof = torch.cuda.profiler  # the repeated phase is bracketed by cudaProfilerStart / Stop
     if args.phase == "leaf":
+        s.build_leaves(prec)
+        torch.cuda.synchronize()
+        prof.start()
         for _ in range(args.repeat):
             s.build_leaves(prec)
     else:
         s.build_leaves(prec)
         if args.phase == "merge":
+            s.merge_levels(prob.L_exact)
+            torch.cuda.synchronize()
+            prof.start()
             for _ in range(args.repeat):
                 s.merge_levels(prob.L_exact)
         elif args.phase == "matvec":
             x = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
+            s.matvec(x)
+            torch.cuda.synchronize()
+            prof.start()
             for _ in range(args.repeat):
                 s.matvec(x)
         elif args.phase == "precond":
             s.merge_levels(prob.L_exact)
             r = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
+            s.precond_apply(r, prob.inner_iters)
+            torch.cuda.synchronize()
+            prof.start()
             for _ in range(args.repeat):
                 s.precond_apply(r, prob.inner_iters)
         else:
             s.merge_levels(prob.L_exact)
+            torch.cuda.synchronize()
+            prof.start()
             _, info = s.gmres_solve(td, tol=args.tol, inner_iters=prob.inner_iters)
     torch.cuda.synchronize()
+    prof.stop()
     line = {"phase": args.phase, "workload": prob.name, "repeat": args.repeat,
             "wall_s": time.perf_counter() - t0, "bytes_held": s.bytes_held()}
     if info:

@@ -203,13 +203,43 @@ int hps_precond_apply(hps_ctx* ctx, const void* r, void* z, int nrhs, int inner_
  * as the preconditioner (inner_iters coarse GMRES steps), until
  * ||RHS - M g||_2 <= tol ||RHS||_2 per right-hand side (section 4.3, 5).
  * inner_iters < 0 runs unpreconditioned FGMRES.  t [nrhs][n_bdry] and
- * g_out [nrhs][n_skel] are complex128, host or device.  s must be NULL (this
- * build takes sources s = 0; HPS_EUNSUPPORTED otherwise).  info may be NULL.
- * HPS_ENOTCONV when a right-hand side did not reach tol (g_out and info are
- * filled). */
+ * g_out [nrhs][n_skel] are complex128, host or device.  s (may be NULL: no
+ * source) holds the source of each right-hand side at every element node,
+ * [nrhs][E][(N+1)^2] complex128 in the node order of hps_node_coords, host or
+ * device; its interior values enter as b~ = w_i w_j s (physical GLL weights)
+ * and the RHS gets the interior contributions H = I_o L^{-1} I(:, iota_i) b~ of
+ * eq. ItIOperator (section 3.1; the RHS of the header's conventions).  info
+ * may be NULL.  HPS_ENOTCONV when a right-hand side did not reach tol (g_out
+ * and info are filled). */
 int hps_gmres_solve(hps_ctx* ctx, const void* t, const void* s, int nrhs, double tol,
                     int inner_iters, int restart, int max_outer, void* g_out,
                     hps_info* info);
+
+/* Element fields u at every node of every element (section 3.1: L u = b with
+ * b(iota_Gamma) = I_i u, b(iota_i) = b~) from the skeleton solution g
+ * [nrhs][n_skel] of hps_gmres_solve, the boundary data t [nrhs][n_bdry] (NULL:
+ * zero) and the sources s [nrhs][E][(N+1)^2] (NULL: none), all complex128, host
+ * or device.  u [nrhs][E][(N+1)^2] complex128, host or device, node order of
+ * hps_node_coords.  The corner nodes, which the discretization leaves out, are
+ * filled afterwards: each is the mean of the two one-sided extrapolations along
+ * the element edges meeting there (the degree N-2 polynomial through an edge's
+ * N-1 other nodes, evaluated at the corner).  Interior solves: positive-definite
+ * elements by conjugate gradients preconditioned by fast diagonalisation of the
+ * constant-coefficient operator (FP32) inside FP64 refinement; the others by the
+ * pivoted route of hps_build_leaves.  Returns when u is written. */
+int hps_volume_solution(hps_ctx* ctx, const void* t, const void* s, const void* g, int nrhs, void* u);
+
+/* Coarse calls per level of the preconditioner of later hps_precond_apply and
+ * hps_gmres_solve calls on ctx (section 4.3: "a single coarse call yields a
+ * V-cycle; multiple ones define a gamma-cycle").  At every merge level the
+ * correction of the next level's system S r_c is made by `gamma` calls of MG,
+ * each on the current residual, e_k = e_{k-1} + MG(S)(r_c - S e_{k-1}); at the
+ * coarsest level MG(S) is the coarse solver (inner_iters GMRES steps or the
+ * exact inverse).  gamma = 1 (the initial state) is the V-cycle; the coarse
+ * solver then runs gamma^L_exact times per application.  1 <= gamma <= 8,
+ * HPS_EINVAL otherwise.  Buffers for gamma > 1 are allocated by the next
+ * application (one extra pair of stage vectors per merged level). */
+int hps_set_gamma(hps_ctx* ctx, int gamma);
 
 /* Arithmetic of the outer FGMRES of later hps_gmres_solve calls on ctx:
  *   HPS_OUTER_FP64     matvec, Gram-Schmidt and basis in FP64 (section 4.3);

@@ -138,6 +138,8 @@ template GemmDesc* dev_upload<GemmDesc>(hps_ctx*, const std::vector<GemmDesc>&);
 
 void free_solver(hps_ctx* c) {
   free_fg(c);  // the FGMRES workspace (FP64 and double-float buffers, pinned mirrors)
+  free_vol(c);
+  free_vol_staging(c);
   FREE(c->pv_in); FREE(c->pv_out);
   c->pv_nrhs = 0;
 }
@@ -275,6 +277,44 @@ static double min_eig_sym(std::vector<double> A, int n) {
   return m;
 }
 
+// Eigen-decomposition A = U diag(lam) U^T of a symmetric n x n matrix by cyclic Jacobi
+// rotations; U's columns are the eigenvectors (row-major U[i * n + k] = component i of vector k).
+static void eig_sym(std::vector<double> A, int n, std::vector<double>& lam, std::vector<double>& U) {
+  U.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) U[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = cs * akp - sn * akq;
+          A[k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = cs * apk - sn * aqk;
+          A[q * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double ukp = U[(size_t)k * n + p], ukq = U[(size_t)k * n + q];
+          U[(size_t)k * n + p] = cs * ukp - sn * ukq;
+          U[(size_t)k * n + q] = sn * ukp + cs * ukq;
+        }
+      }
+  }
+  lam.resize(n);
+  for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+}
+
 static inline int opp_side(int s) { return s ^ 1; }
 
 }  // namespace hps
@@ -304,6 +344,7 @@ void optin_all_once() {
   optin_df64();
   optin_skel();
   optin_tc();
+  optin_volume();
   done[dev] = true;
 }
 }  // namespace hps
@@ -408,7 +449,7 @@ int hps_mesh(hps_ctx* c, int nx, int ny, int N) {
   while (!c->allocs.empty()) dev_free(c, c->allocs.back().p);
   c->mg_ptr = nullptr;  // freed with every other allocation
   c->d_es_nb = c->d_es_in = c->d_es_out = c->d_es_bdry = c->d_bdry_rows = nullptr;
-  c->d_Dref = c->d_Kref = c->d_wref = nullptr;
+  c->d_Dref = c->d_Kref = c->d_wref = c->d_vtab = nullptr;
   c->d_c = c->d_bstage = nullptr;
   c->d_route = c->d_lists = nullptr;
   c->d_T = nullptr;
@@ -487,7 +528,30 @@ int hps_mesh(hps_ctx* c, int nx, int ny, int N) {
   c->d_Dref = dev_upload(c, c->Dref);
   c->d_Kref = dev_upload(c, c->Kref);
   c->d_wref = dev_upload(c, c->wref);
-  if (!c->d_es_nb || !c->d_es_in || !c->d_es_out || !c->d_es_bdry || !c->d_bdry_rows || !c->d_Dref || !c->d_Kref ||
+  {
+    // interior solve and corner tables (volume.cu): S = V^{-1} K_ii V^{-1} = U diag(lam) U^T with
+    // V = diag(w_i^1/2) on the interior nodes, V's diagonal, and the corner extrapolation weights
+    // (Lagrange basis of the interior nodes at -1 and +1)
+    std::vector<double> U, lam;
+    eig_sym(S, q, lam, U);
+    std::vector<double> tab(2 * q * q + 4 * q);
+    std::copy(S.begin(), S.end(), tab.begin());
+    std::copy(U.begin(), U.end(), tab.begin() + q * q);
+    for (int i = 0; i < q; ++i) {
+      tab[2 * q * q + i] = lam[i];
+      tab[2 * q * q + q + i] = std::sqrt(c->wref[i + 1]);
+      double wl = 1.0, wr = 1.0;
+      for (int k = 0; k < q; ++k) {
+        if (k == i) continue;
+        wl *= (-1.0 - c->xi[k + 1]) / (c->xi[i + 1] - c->xi[k + 1]);
+        wr *= (1.0 - c->xi[k + 1]) / (c->xi[i + 1] - c->xi[k + 1]);
+      }
+      tab[2 * q * q + 2 * q + i] = wl;
+      tab[2 * q * q + 3 * q + i] = wr;
+    }
+    c->d_vtab = dev_upload(c, tab);
+  }
+  if (!c->d_vtab || !c->d_es_nb || !c->d_es_in || !c->d_es_out || !c->d_es_bdry || !c->d_bdry_rows || !c->d_Dref || !c->d_Kref ||
       !c->d_wref)
     return fail(c, HPS_ENOMEM, "index maps");
   c->have_mesh = true;

@@ -31,6 +31,7 @@ void optin_leaf();
 void optin_blas();
 void optin_df64();
 void optin_skel();
+void optin_volume();
 
 template <typename R> struct cplx;
 template <> struct cplx<double> { using T = double2; };

@@ -90,6 +90,7 @@ struct hps_ctx {
   int *d_es_nb = nullptr, *d_es_in = nullptr, *d_es_out = nullptr, *d_es_bdry = nullptr;
   int* d_bdry_rows = nullptr;  // [n_bdry] identity helper for boundary transposes
   double *d_Dref = nullptr, *d_Kref = nullptr, *d_wref = nullptr;
+  double* d_vtab = nullptr;    // interior solve and corner tables (volume.cu)
   double mu_min = 0;           // smallest eigenvalue of K_ii w.r.t. W_ii (reference element)
 
   // coefficient (computed on the device by hps_set_coeff, with each element's leaf route)
@@ -175,6 +176,14 @@ struct hps_ctx {
   float4* pin_coef = nullptr;      // pinned host mirror of df_coef
   float2* df_Z = nullptr;
   double2 *pv_in = nullptr, *pv_out = nullptr;  // precond_apply/matvec ES staging
+  // sources and volume solution (volume.cu): [E][nrhs][ni] interior and [E][nrhs][nb] edge arrays
+  int vol_nrhs = 0;
+  double2 *vol_B = nullptr, *vol_V = nullptr, *vol_U = nullptr, *vol_B2 = nullptr;
+  double2 *vol_F = nullptr, *vol_G = nullptr;
+  double2* vol_s = nullptr;    // staged sources
+  size_t vol_s_elems = 0;
+  double2* vol_H = nullptr;    // interior contributions H [n_es][nrhs]
+  size_t vol_H_elems = 0;
   int pv_nrhs = 0;
 
   // profiling (hps_profile): CUDA events per phase on the context's stream
@@ -197,8 +206,15 @@ void free_tree(hps_ctx* c);     // numeric part and plan
 void free_numeric(hps_ctx* c);  // numeric part only (the plan stays)
 void free_solver(hps_ctx* c);
 void free_fg(hps_ctx* c);  // FGMRES workspace (solve.cu)
+void free_vol(hps_ctx* c); // source and volume-solution work arrays (volume.cu)
+void free_vol_staging(hps_ctx* c);  // staged sources and the H buffer (volume.cu)
+// H of every element for sources s (device [nrhs][E][(N+1)^2]) -> H_es [n_es][nrhs] (volume.cu)
+int source_H(hps_ctx* c, const double2* s, int nrhs, double2* H_es);
+int subtract_H(hps_ctx* c, double2* rho, const double2* H_es, int nrhs);
+const double2* stage_in(hps_ctx* c, const void* src, size_t elems, double2** buf, size_t* cap);
 void free_graph(hps_ctx* c);
 int ensure_sweep_buffers(hps_ctx* c, int nrhs);
+int ensure_gamma_buffers(hps_ctx* c, int nrhs);  // gamma-cycle vectors (no-op for gamma = 1)
 
 // tree operations (merge.cu)
 int build_tree(hps_ctx* c, int L_exact, int exact_coarse);

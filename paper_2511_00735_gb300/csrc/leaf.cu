@@ -790,11 +790,46 @@ __device__ __forceinline__ Minv2 mb_inverse(const double* Dp, int N, double eta)
   return r;
 }
 
-__global__ void robust_assemble_kernel(LeafParams p, const int* __restrict__ elems, int count,
-                                       double2* __restrict__ W) {
-  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1, ld = ni + nb;
-  const double dsc = 2.0 / p.h, h2 = 0.25 * p.h * p.h;
-  __shared__ double sD[17 * 17];
+// Entry (I, col) of [S_i | -R] for an element with coefficient samples ce (col < ni: S_i, else -R).
+__device__ __forceinline__ double2 robust_entry(const LeafParams& p, const double* sD, const Minv2& mi,
+                                                const double* ce, int I, int col) {
+  const int N = p.N, q = p.q, ni = p.ni, n1 = N + 1;
+  const double h2 = 0.25 * p.h * p.h;
+  const int ti = I / q + 1, tj = I % q + 1;
+  // R entries of row I on its two lines (x-pair of line tj, y-pair of line ti)
+  const double a0 = p.Kh[ti * n1 + 0] * p.wh[tj], aN = p.Kh[ti * n1 + N] * p.wh[tj];
+  const double c0 = p.wh[ti] * p.Kh[tj * n1 + 0], cN = p.wh[ti] * p.Kh[tj * n1 + N];
+  const double2 Rl = cadd(cscale(mi.a, a0), cscale(mi.c, aN)), Rr = cadd(cscale(mi.b, a0), cscale(mi.d, aN));
+  const double2 Rb = cadd(cscale(mi.a, c0), cscale(mi.c, cN)), Rt = cadd(cscale(mi.b, c0), cscale(mi.d, cN));
+  double2 v = make_double2(0.0, 0.0);
+  if (col < ni) {
+    const int ui = col / q + 1, uj = col % q + 1;
+    double lt = 0.0;
+    if (tj == uj) lt += p.Kh[ti * n1 + ui] * p.wh[tj];
+    if (ti == ui) lt += p.wh[ti] * p.Kh[tj * n1 + uj];
+    if (I == col) lt -= ce[ti * n1 + tj] * h2 * p.wh[ti] * p.wh[tj];
+    v.x = lt;
+    if (tj == uj) v = csub(v, cadd(cscale(Rl, -sD[0 * n1 + ui]), cscale(Rr, sD[N * n1 + ui])));
+    if (ti == ui) v = csub(v, cadd(cscale(Rb, -sD[0 * n1 + uj]), cscale(Rt, sD[N * n1 + uj])));
+  } else {
+    const int g = col - ni, side = g / q, s = g % q + 1;
+    // -R[I][g]
+    if (side == 0 && s == tj) v = Rl;
+    else if (side == 1 && s == tj) v = Rr;
+    else if (side == 2 && s == ti) v = Rb;
+    else if (side == 3 && s == ti) v = Rt;
+    v = make_double2(-v.x, -v.y);
+  }
+  return v;
+}
+
+// W[b] = [S_i | -R | extra columns]: column ni + nb + r of row I is Bx[(e * nrhs + r) * ni + I]
+// (the interior right-hand side of right-hand side r of element e), or 0 when Bx is null.
+__global__ void robust_assemble_kernel(LeafParams p, const int* __restrict__ elems, int count, int extra,
+                                       const double2* __restrict__ Bx, double2* __restrict__ W) {
+  const int N = p.N, ni = p.ni, nb = p.nb, n1 = N + 1, ld = ni + nb + extra;
+  const double dsc = 2.0 / p.h;
+  __shared__ double sD[25 * 25];
   for (int l = threadIdx.x; l < n1 * n1; l += blockDim.x) sD[l] = dsc * p.Dh[l];
   __syncthreads();
   const Minv2 mi = mb_inverse(sD, N, p.eta);
@@ -804,30 +839,12 @@ __global__ void robust_assemble_kernel(LeafParams p, const int* __restrict__ ele
     const int rem = (int)(l % ((long long)ni * ld));
     const int I = rem / ld, col = rem % ld;
     const int e = elems[b];
-    const int ti = I / q + 1, tj = I % q + 1;
-    // R entries of row I on its two lines (x-pair of line tj, y-pair of line ti)
-    const double a0 = p.Kh[ti * n1 + 0] * p.wh[tj], aN = p.Kh[ti * n1 + N] * p.wh[tj];
-    const double c0 = p.wh[ti] * p.Kh[tj * n1 + 0], cN = p.wh[ti] * p.Kh[tj * n1 + N];
-    const double2 Rl = cadd(cscale(mi.a, a0), cscale(mi.c, aN)), Rr = cadd(cscale(mi.b, a0), cscale(mi.d, aN));
-    const double2 Rb = cadd(cscale(mi.a, c0), cscale(mi.c, cN)), Rt = cadd(cscale(mi.b, c0), cscale(mi.d, cN));
-    double2 v = make_double2(0.0, 0.0);
-    if (col < ni) {
-      const int ui = col / q + 1, uj = col % q + 1;
-      double lt = 0.0;
-      if (tj == uj) lt += p.Kh[ti * n1 + ui] * p.wh[tj];
-      if (ti == ui) lt += p.wh[ti] * p.Kh[tj * n1 + uj];
-      if (I == col) lt -= p.c[(long long)e * n1 * n1 + ti * n1 + tj] * h2 * p.wh[ti] * p.wh[tj];
-      v.x = lt;
-      if (tj == uj) v = csub(v, cadd(cscale(Rl, -sD[0 * n1 + ui]), cscale(Rr, sD[N * n1 + ui])));
-      if (ti == ui) v = csub(v, cadd(cscale(Rb, -sD[0 * n1 + uj]), cscale(Rt, sD[N * n1 + uj])));
+    double2 v;
+    if (col < ni + nb) {
+      v = robust_entry(p, sD, mi, p.c + (long long)e * n1 * n1, I, col);
     } else {
-      const int g = col - ni, side = g / q, s = g % q + 1;
-      // -R[I][g]
-      if (side == 0 && s == tj) v = Rl;
-      else if (side == 1 && s == tj) v = Rr;
-      else if (side == 2 && s == ti) v = Rb;
-      else if (side == 3 && s == ti) v = Rt;
-      v = make_double2(-v.x, -v.y);
+      const int r = col - ni - nb;
+      v = Bx ? Bx[((long long)e * extra + r) * ni + I] : make_double2(0.0, 0.0);
     }
     W[(long long)b * ni * ld + (long long)I * ld + col] = v;
   }
@@ -837,7 +854,7 @@ __global__ void robust_finish_kernel(LeafParams p, const int* __restrict__ elems
                                      const double2* __restrict__ W) {
   const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1, ld = ni + nb;
   const double dsc = 2.0 / p.h;
-  __shared__ double sD[17 * 17];
+  __shared__ double sD[25 * 25];
   for (int l = threadIdx.x; l < n1 * n1; l += blockDim.x) sD[l] = dsc * p.Dh[l];
   __syncthreads();
   const Minv2 mi = mb_inverse(sD, N, p.eta);
@@ -881,13 +898,108 @@ __global__ void robust_finish_kernel(LeafParams p, const int* __restrict__ elems
   }
 }
 
+// Element fields of the pivoted route after Gauss-Jordan on [S_i | -R | b~_0 .. b~_{nrhs-1}]
+// (right part = [Y_i | S_i^{-1} b~_r]): u_i = Y_i f_r + S_i^{-1} b~_r for incoming data f_r
+// (F[(e * nrhs + r) * nb + g], null = 0), then per edge line u_G = Mb^{-1} (f - Dn_Gi u_i).
+__global__ void robust_field_interior_kernel(LeafParams p, const int* __restrict__ elems, int count, int nrhs,
+                                             const double2* __restrict__ W, const double2* __restrict__ F,
+                                             double2* __restrict__ Ui) {
+  const int ni = p.ni, nb = p.nb, ld = ni + nb + nrhs;
+  const long long tot = (long long)count * nrhs * ni;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(l / ((long long)nrhs * ni));
+    const int rem = (int)(l % ((long long)nrhs * ni));
+    const int r = rem / ni, I = rem % ni;
+    const int e = elems[b];
+    const double2* row = W + (long long)b * ni * ld + (long long)I * ld;
+    double2 u = row[ni + nb + r];
+    if (F) {
+      const double2* f = F + ((long long)e * nrhs + r) * nb;
+      for (int g = 0; g < nb; ++g) cfma(u, row[ni + g], f[g]);
+    }
+    Ui[((long long)e * nrhs + r) * ni + I] = u;
+  }
+}
+
+// u_G on the edge nodes from u_i (Ui) and f (F, null = 0); written to UG[(e * nrhs + r) * nb + g], or,
+// when H is given, the interior contribution H = I_o u = -2 i eta u_G (f = 0) to
+// H[(e * nb + g) * nrhs + r].
+__global__ void robust_field_edges_kernel(LeafParams p, const int* __restrict__ elems, int count, int nrhs,
+                                          const double2* __restrict__ Ui, const double2* __restrict__ F,
+                                          double2* __restrict__ UG, double2* __restrict__ H) {
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
+  const double dsc = 2.0 / p.h;
+  __shared__ double sD[25 * 25];
+  for (int l = threadIdx.x; l < n1 * n1; l += blockDim.x) sD[l] = dsc * p.Dh[l];
+  __syncthreads();
+  const Minv2 mi = mb_inverse(sD, N, p.eta);
+  const long long tot = (long long)count * nrhs * 2 * q;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(l / ((long long)nrhs * 2 * q));
+    const int rem = (int)(l % ((long long)nrhs * 2 * q));
+    const int r = rem / (2 * q), line = rem % (2 * q);
+    const int e = elems[b];
+    const double2* u = Ui + ((long long)e * nrhs + r) * ni;
+    const double2* f = F ? F + ((long long)e * nrhs + r) * nb : nullptr;
+    int g0, g1;
+    double2 z0 = make_double2(0.0, 0.0), z1 = make_double2(0.0, 0.0);
+    if (line < q) {  // x-pair l_j, r_j; interior nodes (ui, j)
+      const int j = line + 1;
+      g0 = j - 1;
+      g1 = q + j - 1;
+      for (int ui = 1; ui <= q; ++ui) {
+        const double2 y = u[(ui - 1) * q + (j - 1)];
+        z0 = cadd(z0, cscale(y, sD[0 * n1 + ui]));
+        z1 = csub(z1, cscale(y, sD[N * n1 + ui]));
+      }
+    } else {  // y-pair b_i, t_i; interior nodes (i, uj)
+      const int i = line - q + 1;
+      g0 = 2 * q + i - 1;
+      g1 = 3 * q + i - 1;
+      for (int uj = 1; uj <= q; ++uj) {
+        const double2 y = u[(i - 1) * q + (uj - 1)];
+        z0 = cadd(z0, cscale(y, sD[0 * n1 + uj]));
+        z1 = csub(z1, cscale(y, sD[N * n1 + uj]));
+      }
+    }
+    if (f) {
+      z0 = cadd(z0, f[g0]);
+      z1 = cadd(z1, f[g1]);
+    }
+    const double2 y0 = cadd(cmul(mi.a, z0), cmul(mi.b, z1));
+    const double2 y1 = cadd(cmul(mi.c, z0), cmul(mi.d, z1));
+    if (H) {  // -2 i eta (x + i y) = 2 eta y - 2 i eta x
+      H[((long long)e * nb + g0) * nrhs + r] = make_double2(2.0 * p.eta * y0.y, -2.0 * p.eta * y0.x);
+      H[((long long)e * nb + g1) * nrhs + r] = make_double2(2.0 * p.eta * y1.y, -2.0 * p.eta * y1.x);
+    } else {
+      UG[((long long)e * nrhs + r) * nb + g0] = y0;
+      UG[((long long)e * nrhs + r) * nb + g1] = y1;
+    }
+  }
+}
+
 }  // namespace
 
-cudaError_t robust_assemble(const LeafParams& p, const int* elems, int count, double2* W, cudaStream_t s) {
-  const long long tot = (long long)count * p.ni * (p.ni + p.nb);
+cudaError_t robust_field(const LeafParams& p, const int* elems, int count, int nrhs, const double2* W,
+                         const double2* F, double2* Ui, double2* UG, double2* H, cudaStream_t s) {
+  long long blocks = ((long long)count * nrhs * p.ni + 255) / 256;
+  if (blocks > 16384) blocks = 16384;
+  if (blocks < 1) return cudaSuccess;
+  robust_field_interior_kernel<<<(int)blocks, 256, 0, s>>>(p, elems, count, nrhs, W, F, Ui);
+  note_launch();
+  blocks = ((long long)count * nrhs * 2 * p.q + 255) / 256;
+  if (blocks > 16384) blocks = 16384;
+  robust_field_edges_kernel<<<(int)blocks, 256, 0, s>>>(p, elems, count, nrhs, Ui, F, UG, H);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t robust_assemble(const LeafParams& p, const int* elems, int count, double2* W, cudaStream_t s,
+                            int extra, const double2* Bx) {
+  const long long tot = (long long)count * p.ni * (p.ni + p.nb + extra);
   long long blocks = (tot + 255) / 256;
   if (blocks > 16384) blocks = 16384;
-  robust_assemble_kernel<<<(int)blocks, 256, 0, s>>>(p, elems, count, W);
+  robust_assemble_kernel<<<(int)blocks, 256, 0, s>>>(p, elems, count, extra, Bx, W);
   note_launch();
   return cudaGetLastError();
 }

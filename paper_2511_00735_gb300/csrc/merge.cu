@@ -406,6 +406,28 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     if (!cc.d_cdesc || !cc.d_cnb || !cc.d_upos || !cc.d_ucnb) return fail(c, HPS_ENOMEM, "coarse maps");
     cc.upos_h = upos;
     cc.ucnb_h = ucnb;
+    // gamma-cycle: the system of every stage k >= 1 (row across the face, one n x n product
+    // per subdomain)
+    for (int k = 1; k <= L_exact; ++k) {
+      Stage& Sk = c->stages[k];
+      std::vector<int> own(c->n_es, -1), nbk((size_t)Sk.nsub * Sk.n, -1);
+      for (int s = 0; s < Sk.nsub; ++s)
+        for (int i = 0; i < Sk.n; ++i) own[Sk.es[(size_t)s * Sk.n + i]] = s;
+      std::vector<GemmDesc> td(Sk.nsub);
+      for (int s = 0; s < Sk.nsub; ++s) {
+        td[s] = D(s * Sk.n, 0, s * Sk.n, 0, 0, 0, s * Sk.n, 0, Sk.n, -1, Sk.n);
+        for (int i = 0; i < Sk.n; ++i) {
+          const int en = c->es_nb[Sk.es[(size_t)s * Sk.n + i]];
+          if (en < 0) continue;
+          const int so = own[en], d = inv[k][en];
+          if (so < 0 || so == s || d < 0) return fail(c, HPS_ECUDA, "internal: stage neighbour map");
+          nbk[(size_t)s * Sk.n + i] = so * Sk.n + d;
+        }
+      }
+      Sk.d_nb = dev_upload(c, nbk);
+      Sk.d_tdesc = dev_upload(c, td);
+      if (!Sk.d_nb || !Sk.d_tdesc) return fail(c, HPS_ENOMEM, "stage maps for the gamma-cycle");
+    }
     }  // plan
     cc.exact = exact != 0;
     const std::vector<int>& upos = cc.upos_h;
@@ -492,6 +514,28 @@ int ensure_sweep_buffers(hps_ctx* c, int nrhs) {
   c->sw_x = dev_alloc(c, cs * p2m * nrhs);
   if (!c->sw_x) return fail(c, HPS_ENOMEM, "sweep temporaries");
   c->nrhs_cap = nrhs;
+  ++c->vc_gen;
+  return HPS_OK;
+}
+
+int ensure_gamma_buffers(hps_ctx* c, int nrhs) {
+  if (c->gamma <= 1 || nrhs <= c->gamma_nrhs) return HPS_OK;
+  const size_t cs = csize(c->precision);
+  size_t wmax = 1;
+  for (int k = 1; k <= c->L_exact; ++k) {
+    Stage& S = c->stages[k];
+    const size_t el = (size_t)S.nsub * S.n * nrhs;
+    dev_free(c, S.gR);
+    dev_free(c, S.gE);
+    S.gR = dev_alloc(c, cs * el);
+    S.gE = dev_alloc(c, cs * el);
+    if (!S.gR || !S.gE) return fail(c, HPS_ENOMEM, "gamma-cycle vectors");
+    wmax = std::max(wmax, el);
+  }
+  dev_free(c, c->gW);
+  c->gW = dev_alloc(c, cs * wmax);
+  if (!c->gW) return fail(c, HPS_ENOMEM, "gamma-cycle product");
+  c->gamma_nrhs = nrhs;
   ++c->vc_gen;
   return HPS_OK;
 }
@@ -657,35 +701,56 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
 }
 
 
-// One V-cycle on the stage-0 sweep vector: rho in S0.vec on entry, z in S0.vec on return.
+// MG of the stage-l system (section 4.3): the residual in P_l.vec on entry (outgoing
+// coordinates), the correction in P_l.vec on return (incoming coordinates).  Below the coarse
+// stage: the up-sweep of merge level l+1 (smoother A^{-1} and restriction), the stage-(l+1)
+// system solved by gamma calls of this function, each on the current residual
+// r_c - M_{l+2} e (gamma = 1: one call, the V-cycle), then the down-sweep (prolongation).
+template <typename R>
+int mg_level(hps_ctx* c, int l, int nrhs, int k) {
+  using C = c_t<R>;
+  if (l == c->L_exact) return coarse_solve<R>(c, nrhs, k);
+  cudaStream_t st = c->stream;
+  const Level& Lv = c->levels[l + 1];
+  const Stage& P0 = c->stages[l];
+  const Stage& P1 = c->stages[l + 1];
+  const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
+  // up-sweep: rho'_E = rho_E - U f
+  HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
+                    Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
+  if (c->gamma <= 1) {
+    int rc = mg_level<R>(c, l + 1, nrhs, k);
+    if (rc != HPS_OK) return rc;
+  } else {
+    const long long rows = (long long)P1.nsub * P1.n;
+    C* v1 = static_cast<C*>(P1.vec);
+    C* gR = static_cast<C*>(P1.gR);
+    C* gE = static_cast<C*>(P1.gE);
+    HPS_CK(c, cudaMemcpyAsync(gR, v1, sizeof(C) * rows * nrhs, cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < c->gamma; ++it) {
+      if (it > 0) {  // P1.vec = r_c - M_{l+2} e:  (M e)_r = e_{nb(r)} + (T e)_r
+        HPS_CK(c, gemm<R>(c, P1.d_tdesc, P1.nsub, P1.T, P1.n, gE, nrhs, nullptr, 0, c->gW, nrhs, 1.0, nullptr, P1.n,
+                          nrhs, nrhs, P1.n));
+        HPS_CK(c, stage_residual<R>(v1, gR, gE, static_cast<const C*>(c->gW), P1.d_nb, rows, nrhs, st));
+      }
+      int rc = mg_level<R>(c, l + 1, nrhs, k);
+      if (rc != HPS_OK) return rc;
+      HPS_CK(c, accumulate<R>(gE, v1, rows * nrhs, it == 0, it == c->gamma - 1 ? v1 : nullptr, st));
+    }
+  }
+  // down-sweep: children's outer rows from the merged solution, x = Dm [child1; child2], x into the interface rows
+  C* v0 = static_cast<C*>(P0.vec);
+  HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(P1.vec), Lv.d_up, (long long)P1.nsub * P1.n, nrhs, st)));
+  HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
+                    2 * m, nrhs, nrhs, 2 * n));
+  HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(c->sw_x), Lv.d_xmap, (long long)NP * 2 * m, nrhs, st)));
+  return HPS_OK;
+}
+
+// One MG application on the stage-0 sweep vector: rho in S0.vec on entry, z in S0.vec on return.
 template <typename R>
 int mg_core(hps_ctx* c, int nrhs, int k) {
-  using C = c_t<R>;
-  cudaStream_t st = c->stream;
-  // up-sweep: rho'_E = rho_E - U f (one GEMM per level)
-  for (int l = 1; l <= c->L_exact; ++l) {
-    const Level& Lv = c->levels[l];
-    const Stage& P0 = c->stages[l - 1];
-    const Stage& P1 = c->stages[l];
-    const int m = Lv.m, p = Lv.p, NP = Lv.npairs;
-    HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
-                      Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
-  }
-  int rc = coarse_solve<R>(c, nrhs, k);
-  if (rc != HPS_OK) return rc;
-  // down-sweep: children's outer rows from the merged solution, x = Dm [child1; child2], x into the interface rows
-  for (int l = c->L_exact; l >= 1; --l) {
-    const Level& Lv = c->levels[l];
-    const Stage& P0 = c->stages[l - 1];
-    const Stage& P1 = c->stages[l];
-    const int n = Lv.n, m = Lv.m, NP = Lv.npairs;
-    C* v0 = static_cast<C*>(P0.vec);
-    HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(P1.vec), Lv.d_up, (long long)P1.nsub * P1.n, nrhs, st)));
-    HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
-                      2 * m, nrhs, nrhs, 2 * n));
-    HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(c->sw_x), Lv.d_xmap, (long long)NP * 2 * m, nrhs, st)));
-  }
-  return HPS_OK;
+  return mg_level<R>(c, 0, nrhs, k);
 }
 
 }  // namespace
@@ -694,6 +759,7 @@ template <typename R>
 int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) {
   using C = c_t<R>;
   int rc = ensure_sweep_buffers(c, nrhs);
+  if (rc == HPS_OK) rc = ensure_gamma_buffers(c, nrhs);
   if (rc != HPS_OK) return rc;
   cudaStream_t st = c->stream;
   const Stage& S0 = c->stages[0];
@@ -707,6 +773,7 @@ int mg_apply(hps_ctx* c, const double2* rho_es, double2* z_es, int nrhs, int k) 
 
 int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int k) {
   int rc = ensure_sweep_buffers(c, nrhs);
+  if (rc == HPS_OK) rc = ensure_gamma_buffers(c, nrhs);
   if (rc != HPS_OK) return rc;
   if (c->precision != HPS_MIXED) return fail(c, HPS_EINVAL, "internal: df64 outer needs the FP32 tree");
   // every buffer the V-cycle touches exists before a capture
@@ -745,7 +812,7 @@ int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int k)
   }
   HPS_CK(c, cudaEventRecord(c->gs_in, st));
   HPS_CK(c, cudaStreamWaitEvent(c->gs, c->gs_in, 0));
-  if (!(c->mg_exec && c->mg_nrhs == nrhs && c->mg_k == k && c->mg_gen == c->vc_gen)) {
+  if (!(c->mg_exec && c->mg_nrhs == nrhs && c->mg_k == k && c->mg_gamma == c->gamma && c->mg_gen == c->vc_gen)) {
     if (c->mg_exec) cudaGraphExecDestroy(c->mg_exec);
     c->mg_exec = nullptr;
     // one capture at a time in the process (contexts of several host threads)
@@ -776,6 +843,7 @@ int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int k)
     }
     c->mg_nrhs = nrhs;
     c->mg_k = k;
+    c->mg_gamma = c->gamma;
     c->mg_gen = c->vc_gen;
     c->mg_count = captured;
   }

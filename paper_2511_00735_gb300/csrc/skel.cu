@@ -255,6 +255,42 @@ cudaError_t swap_add(c_t<R>* out, const c_t<R>* a, const c_t<R>* b, const int* n
   return cudaGetLastError();
 }
 
+template <typename R>
+__global__ void stage_residual_kernel(c_t<R>* __restrict__ out, const c_t<R>* __restrict__ r,
+                                      const c_t<R>* __restrict__ e, const c_t<R>* __restrict__ w,
+                                      const int* __restrict__ nbr, long long rows, int nrhs) {
+  const long long tot = rows * nrhs;
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < tot; l += (long long)gridDim.x * NT) {
+    const int m = nbr[l / nrhs];
+    c_t<R> v = czero<R>();
+    if (m >= 0) v = csub(r[l], cadd(e[(long long)m * nrhs + (l % nrhs)], w[l]));
+    out[l] = v;
+  }
+}
+template <typename R>
+cudaError_t stage_residual(c_t<R>* out, const c_t<R>* r, const c_t<R>* e, const c_t<R>* w, const int* nbr,
+                           long long rows, int nrhs, cudaStream_t s) {
+  stage_residual_kernel<R><<<nblocks(rows * nrhs, NT, 8192), NT, 0, s>>>(out, r, e, w, nbr, rows, nrhs);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void accumulate_kernel(c_t<R>* __restrict__ acc, const c_t<R>* __restrict__ x, long long n, int first,
+                                  c_t<R>* __restrict__ out) {
+  for (long long l = blockIdx.x * (long long)NT + threadIdx.x; l < n; l += (long long)gridDim.x * NT) {
+    const c_t<R> v = first ? x[l] : cadd(acc[l], x[l]);
+    acc[l] = v;
+    if (out) out[l] = v;
+  }
+}
+template <typename R>
+cudaError_t accumulate(c_t<R>* acc, const c_t<R>* x, long long n, bool first, c_t<R>* out, cudaStream_t s) {
+  accumulate_kernel<R><<<nblocks(n, NT, 8192), NT, 0, s>>>(acc, x, n, first ? 1 : 0, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Block-vector Krylov primitives.  V holds nvec vectors of `rows` rows, vector
 // i at V + i*vstride.  Reductions are two-pass and deterministic.
@@ -702,6 +738,9 @@ cudaError_t eye2(c_t<R>* W, int m, int nmat, cudaStream_t s) {
   template cudaError_t lsq<R>(c_t<R>*, const R*, const R*, c_t<R>*, c_t<R>*, R*, c_t<R>*, int, int,        \
                               cudaStream_t);                  \
   template cudaError_t zero<R>(c_t<R>*, long long, cudaStream_t);                                                       \
+  template cudaError_t stage_residual<R>(c_t<R>*, const c_t<R>*, const c_t<R>*, const c_t<R>*, const int*, long long,  \
+                                         int, cudaStream_t);                                                            \
+  template cudaError_t accumulate<R>(c_t<R>*, const c_t<R>*, long long, bool, c_t<R>*, cudaStream_t);                                                       \
   template cudaError_t cg_pass<R>(int, const CgPass<R>&, cudaStream_t);                                                 \
   template bool cg_pass_fits<R>(int, int);                                                                               \
   template cudaError_t bcombine<R>(c_t<R>*, const c_t<R>*, long long, int, const c_t<R>*, long long, int, cudaStream_t); \

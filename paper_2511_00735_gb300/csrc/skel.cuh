@@ -46,8 +46,16 @@ cudaError_t launch_leaf(const LeafParams& p, int grid, cudaStream_t s);
 // Robust route for elements whose interior block is not positive definite:
 // W[b] = [S_i | -R] (n_i x (n_i + nb)) for elems[b], then (after W's right part
 // holds Y_i = S_i^{-1}(-R)) the leaf map of elems[b] into p.T.
-cudaError_t robust_assemble(const LeafParams& p, const int* elems, int count, double2* W, cudaStream_t s);
+// `extra` more columns of W (ld = ni + nb + extra) hold the interior right-hand sides
+// Bx[(e * extra + r) * ni + I] of each element (zero when Bx is null).
+cudaError_t robust_assemble(const LeafParams& p, const int* elems, int count, double2* W, cudaStream_t s,
+                            int extra = 0, const double2* Bx = nullptr);
 cudaError_t robust_finish(const LeafParams& p, const int* elems, int count, const double2* W, cudaStream_t s);
+// Element fields of the pivoted route from W = [S_i | -R | b~_r] after Gauss-Jordan (nrhs extra
+// columns): u_i -> Ui [E][nrhs][ni] and u_G -> UG [E][nrhs][nb] for incoming data F [E][nrhs][nb]
+// (null = 0), or, when H is given, H = I_o u (F = 0) -> H [E * nb][nrhs] instead of UG.
+cudaError_t robust_field(const LeafParams& p, const int* elems, int count, int nrhs, const double2* W,
+                         const double2* F, double2* Ui, double2* UG, double2* H, cudaStream_t s);
 
 // skel.cu -- FP64 element-side operators
 cudaError_t es_matvec(const double2* T, const int* nbr, const double2* x, const double2* c0, double2* y, int E,
@@ -93,6 +101,14 @@ cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws
                 int nrhs, cudaStream_t s);
 template <typename R>
 cudaError_t zero(c_t<R>* x, long long n, cudaStream_t s);
+// gamma-cycle residual of a stage system in outgoing coordinates:
+// out_p = nb(p) >= 0 ? r_p - (e_{nb(p)} + w_p) : 0   (w = T e per subdomain)
+template <typename R>
+cudaError_t stage_residual(c_t<R>* out, const c_t<R>* r, const c_t<R>* e, const c_t<R>* w, const int* nbr,
+                           long long rows, int nrhs, cudaStream_t s);
+// acc = first ? x : acc + x; when out is given it also receives the new acc
+template <typename R>
+cudaError_t accumulate(c_t<R>* acc, const c_t<R>* x, long long n, bool first, c_t<R>* out, cudaStream_t s);
 
 // Fused passes of the coarse GMRES (Arnoldi with two classical Gram-Schmidt passes); each is
 // one launch whose last block reduces the block partials in fixed order (deterministic) and

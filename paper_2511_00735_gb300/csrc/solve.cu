@@ -246,6 +246,13 @@ int hps_precond_apply(hps_ctx* c, const void* r, void* z, int nrhs, int inner_it
   return HPS_OK;
 }
 
+int hps_set_gamma(hps_ctx* c, int gamma) {
+  if (!c) return HPS_EINVAL;
+  if (gamma < 1 || gamma > 8) return fail(c, HPS_EINVAL, "1 <= gamma <= 8 coarse calls per level");
+  c->gamma = gamma;
+  return HPS_OK;
+}
+
 int hps_set_outer_arith(hps_ctx* c, int mode) {
   if (!c) return HPS_EINVAL;
   if (mode != HPS_OUTER_DEFAULT && mode != HPS_OUTER_FP64 && mode != HPS_OUTER_DF64)
@@ -257,7 +264,6 @@ int hps_set_outer_arith(hps_ctx* c, int mode) {
 int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double tol, int inner_iters, int restart,
                     int max_outer, void* g_out, hps_info* info) {
   CHECK_CTX(c);
-  if (s) return fail(c, HPS_EUNSUPPORTED, "sources s != 0 are not handled by this build (pass NULL)");
   if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
   if (inner_iters >= 0 && !c->have_tree) return fail(c, HPS_ENOTBUILT, "hps_merge_levels first (or inner_iters < 0)");
   if (!t || !g_out || nrhs < 1 || nrhs > 64 || !(tol > 0) || restart < 1 || restart > 200 || max_outer < 1 ||
@@ -284,6 +290,23 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
     PhaseScope ps(c, HPS_PH_RHS);
     HPS_CK(c, user_to_rows(c->fg_t, t_dev, nullptr, c->n_bdry, nrhs, c->n_bdry, st));
     HPS_CK(c, es_rhs(c->d_T, c->d_es_nb, c->d_es_bdry, c->fg_t, c->fg_rhs, c->E, c->nb, nrhs, grid, st));
+    if (s) {  // RHS -= H: the interior contributions of the sources (section 3.1, eq. ItIOperator)
+      const size_t n_s = (size_t)nrhs * c->E * (c->N + 1) * (c->N + 1);
+      const double2* sd = stage_in(c, s, n_s, &c->vol_s, &c->vol_s_elems);
+      if (!sd) return fail(c, HPS_ENOMEM, "staging of the sources");
+      const size_t nh = (size_t)c->n_es * nrhs;
+      if (nh > c->vol_H_elems) {
+        dev_free(c, c->vol_H);
+        c->vol_H = static_cast<double2*>(dev_alloc(c, sizeof(double2) * nh));
+        c->vol_H_elems = c->vol_H ? nh : 0;
+        if (!c->vol_H) return fail(c, HPS_ENOMEM, "interior contributions");
+      }
+      HPS_CK(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), st));
+      rc = source_H(c, sd, nrhs, c->vol_H);
+      if (rc) return rc;
+      rc = subtract_H(c, c->fg_rhs, c->vol_H, nrhs);
+      if (rc) return rc;
+    }
     if (df) HPS_CK(c, df_from_d(c->df_T, c->d_T, (long long)c->E * c->nb * c->nb, st));
   }
   if (df) HPS_CK(c, df_from_d(c->df_rhs, c->fg_rhs, vs, st));

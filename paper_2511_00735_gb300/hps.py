@@ -33,7 +33,7 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
            "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace",
-           "hps_set_outer_arith"]
+           "hps_set_outer_arith", "hps_set_gamma", "hps_volume_solution"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
         "hps_build_leaves_batch": (i, [C.POINTER(vp), i, i]),
         "hps_release_workspace": (i, [vp]),
         "hps_set_outer_arith": (i, [vp, i]),
+        "hps_set_gamma": (i, [vp, i]),
+        "hps_volume_solution": (i, [vp, vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -202,6 +204,10 @@ class Solver:
         """Outer FGMRES arithmetic: OUTER_FP64, OUTER_DF64 (mixed leaves only) or OUTER_DEFAULT."""
         self._check(self.lib.hps_set_outer_arith(self.h, mode))
 
+    def set_gamma(self, gamma: int):
+        """Coarse calls per level of the preconditioner: 1 = V-cycle, gamma > 1 = gamma-cycle."""
+        self._check(self.lib.hps_set_gamma(self.h, int(gamma)))
+
     def node_coords(self):
         n = self.E * (self.N + 1) ** 2
         x, y = np.empty(n), np.empty(n)
@@ -282,8 +288,9 @@ class Solver:
         return out
 
     def gmres_solve(self, t, tol: float = 1e-10, inner_iters: int = 5, restart: int = 60, max_outer: int = 20,
-                    out=None, raise_on_notconv: bool = True):
-        """Solve M g = RHS(t); t is [nrhs][n_bdry] complex128 (torch CUDA tensor or numpy array).
+                    out=None, raise_on_notconv: bool = True, s=None):
+        """Solve M g = RHS(t, s); t is [nrhs][n_bdry] complex128 (torch CUDA tensor or numpy array),
+        s (optional) the sources [nrhs][E][(N+1)^2] complex128.
         Returns (g, info dict); g has the same kind (device/host) as t unless `out` is given."""
         nrhs = t.shape[0]
         if out is None:
@@ -292,7 +299,8 @@ class Solver:
         its = (C.c_int * nrhs)()
         res = (C.c_double * nrhs)()
         info = HPSInfo(0, 0, 0.0, C.cast(its, C.POINTER(C.c_int)), C.cast(res, C.POINTER(C.c_double)), 0.0, 0.0)
-        st = self.lib.hps_gmres_solve(self.h, C.c_void_p(_ptr(t)), None, nrhs, float(tol), int(inner_iters),
+        sp = None if s is None else C.c_void_p(_ptr(s))
+        st = self.lib.hps_gmres_solve(self.h, C.c_void_p(_ptr(t)), sp, nrhs, float(tol), int(inner_iters),
                                       int(restart), int(max_outer), C.c_void_p(_ptr(out)), C.byref(info))
         if st != HPS_OK and not (st == HPS_ENOTCONV and not raise_on_notconv):
             self._check(st)
@@ -300,6 +308,19 @@ class Solver:
              "max_rel_residual": info.max_rel_residual, "iterations": list(its), "rel_residual": list(res),
              "ms_rhs": info.ms_rhs, "ms_solve": info.ms_solve}
         return out, d
+
+
+    def volume_solution(self, g, t=None, s=None, out=None):
+        """Element fields u [nrhs][E][(N+1)^2] from the skeleton solution g (and t, s)."""
+        nrhs = g.shape[0]
+        n1 = self.N + 1
+        if out is None:
+            out = self._cplx((nrhs, self.E, n1 * n1)) if hasattr(g, "data_ptr") else np.empty(
+                (nrhs, self.E, n1 * n1), dtype=np.complex128)
+        tp = None if t is None else C.c_void_p(_ptr(t))
+        sp = None if s is None else C.c_void_p(_ptr(s))
+        self._check(self.lib.hps_volume_solution(self.h, tp, sp, C.c_void_p(_ptr(g)), nrhs, C.c_void_p(_ptr(out))))
+        return out
 
 
 def build_leaves_batch(solvers, precision: int = HPS_FP64):

@@ -148,6 +148,49 @@ def test_precond_apply(solver, cfg_small, L_exact, coarse):
         assert rel(z[k], zo) < 1e-10, (L_exact, coarse, k)
 
 
+@pytest.mark.parametrize("L_exact", [1, 2, 3])
+@pytest.mark.parametrize("gamma", [2, 3])
+@pytest.mark.parametrize("precision", [H.HPS_FP64, H.HPS_MIXED])
+def test_precond_gamma_cycle(solver, cfg_small, L_exact, gamma, precision):
+    """gamma coarse calls per level (section 4.3) against the oracle's gamma-cycle."""
+    prob, op = cfg_small
+    H.setup(solver, prob, precision)
+    solver.merge_levels(L_exact)
+    tree = MergeTree(op.mesh, op.Ts, None, L_exact)
+    r = np.random.default_rng(70 + L_exact).standard_normal((2, op.mesh.n_skel)) * (0.6 - 1j)
+    solver.set_gamma(gamma)
+    try:
+        z = host(solver.precond_apply(dev(r), inner_iters=3))
+    finally:
+        solver.set_gamma(1)
+    tol = 1e-10 if precision == H.HPS_FP64 else 2e-5
+    for k in range(2):
+        zo = tree.mg(r[k], "gmres", 3, gamma)
+        assert rel(z[k], zo) < tol, (L_exact, gamma, k)
+
+
+def test_solve_gamma_cycle_mixed(solver):
+    """FGMRES with the gamma = 2 cycle on the mixed path (the V-cycle graph with repeated coarse
+    calls) reaches the dense solution and takes no more iterations than the V-cycle."""
+    prob = inputs.single_bump(8, 12, 30.0, 2, seed=21, L_exact=4)
+    op = OracleProblem(prob)
+    M = assemble_M(op.mesh, op.Ts)
+    t = H.setup(solver, prob, H.HPS_MIXED)
+    solver.merge_levels(prob.L_exact)
+    its = {}
+    try:
+        for gamma in (1, 2):
+            solver.set_gamma(gamma)
+            g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=2)
+            assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10
+            for k in range(prob.nrhs):
+                assert rel(g[k], np.linalg.solve(M, op.rhs[k])) < 1e-8
+            its[gamma] = info["outer_iterations"]
+    finally:
+        solver.set_gamma(1)
+    assert its[2] <= its[1], its
+
+
 def test_precond_exact_is_inverse(solver, cfg_small):
     prob, op = cfg_small
     H.setup(solver, prob)
