@@ -527,7 +527,7 @@ cudaError_t launch_gemm(const GemmArgs<R>& a, int mmax, int nmax, cudaStream_t s
   // FP32 products on the tensor cores (3xTF32): the merges of the upper levels and the
   // block-vector products of the sweeps and the coarse solve with long rows
   if constexpr (sizeof(R) == 4) {
-    if (a.err && mmax >= 64 && kmax >= 64 && (nmax >= 64 || (nmax <= 16 && kmax >= 64)) && a.nbatch <= 65535)
+    if (a.err && mmax >= 64 && kmax >= 64 && (nmax >= 64 || nmax <= 32) && a.nbatch <= 65535)
       return launch_tc_gemm(a, mmax, nmax, kmax, a.err, s);
   }
   // block-vector products (the sweeps' and the coarse solve's right-hand sides)

@@ -317,11 +317,13 @@ cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kma
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
   if (nmax <= 16) return launch_tc<16>(a, mmax, nmax, kmax, err, s);
+  if (nmax <= 32) return launch_tc<32>(a, mmax, nmax, kmax, err, s);
   return launch_tc<64>(a, mmax, nmax, kmax, err, s);
 }
 
 void optin_tc() {
   smem_optin(tc_gemm_kernel<16>);
+  smem_optin(tc_gemm_kernel<32>);
   smem_optin(tc_gemm_kernel<64>);
 }
 

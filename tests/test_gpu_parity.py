@@ -191,6 +191,22 @@ def test_solve_gamma_cycle_mixed(solver):
     assert its[2] <= its[1], its
 
 
+@pytest.mark.parametrize("nrhs", [16, 32, 48])
+def test_precond_mixed_tensor_core_sweeps(solver, nrhs):
+    """FP32 tree on a 16x16, N=8 mesh: the upper sweep and coarse products (rows and k >= 64) run
+    on the tensor cores with 16 or 32 column tiles (48: SIMT); the V-cycle against the oracle's
+    (section 4.3)."""
+    prob = inputs.single_bump(16, 8, 20.0, 1, seed=9, L_exact=6)
+    op = OracleProblem(prob)
+    H.setup(solver, prob, H.HPS_MIXED)
+    solver.merge_levels(prob.L_exact)
+    tree = MergeTree(op.mesh, op.Ts, None, prob.L_exact)
+    r = np.random.default_rng(nrhs).standard_normal((nrhs, op.mesh.n_skel)) * (1 + 0.25j)
+    z = host(solver.precond_apply(dev(r), inner_iters=4))
+    for k in (0, nrhs // 2, nrhs - 1):
+        assert rel(z[k], tree.mg(r[k], "gmres", 4)) < 2e-5, k
+
+
 def test_precond_exact_is_inverse(solver, cfg_small):
     prob, op = cfg_small
     H.setup(solver, prob)
