@@ -114,7 +114,7 @@ const char* hps_strerror(int status);
 
 /* Structured mesh of nx x ny square elements with tensor GLL grids of order N
  * (section 3).  Requires nx == ny == 2^k (k >= 1) so that the nested-dissection
- * levels alternate x, y, x, y (section 4.2, Fig. 1), and 2 <= N <= 16.
+ * levels alternate x, y, x, y (section 4.2, Fig. 1), and 2 <= N <= 24.
  * Builds every index map on the host and uploads it.  Invalidates coefficient,
  * leaves and tree. */
 int hps_mesh(hps_ctx* ctx, int nx, int ny, int N);
@@ -151,7 +151,9 @@ int hps_set_coeff(hps_ctx* ctx, double kappa, double eta, const double* b);
  * Elements whose interior operator is provably positive definite
  * (kappa^2 (1-b) (h/2)^2 below the smallest interior Dirichlet eigenvalue of
  * the reference element, with a 2% margin) eliminate the interior by a real
- * L D L^T factorisation; the others (near or past an interior resonance) use
+ * L D L^T factorisation (N <= 16; for 17 <= N <= 24, whose factor does not fit
+ * on chip, by conjugate gradients preconditioned by fast diagonalisation, as
+ * hps_volume_solution); the others (near or past an interior resonance) use
  * a pivoted complex elimination of the edge rows first.  HPS_ENUMERIC if an
  * element system is singular. */
 int hps_build_leaves(hps_ctx* ctx, int precision);

@@ -164,7 +164,7 @@ void free_numeric(hps_ctx* c) {
   FREE(c->gW);
   c->gamma_nrhs = 0;
   for (auto& l : c->levels) {
-    FREE(l.W); FREE(l.U); FREE(l.Dm);
+    FREE(l.W); FREE(l.U); FREE(l.Dm); FREE(l.Ut); FREE(l.Dmt);
   }
   FREE(c->coarse.Winv); FREE(c->coarse.d_desc);
   FREE(c->gemm_ws); c->gemm_ws_elems = 0;
@@ -187,7 +187,7 @@ void free_tree(hps_ctx* c) {
     FREE(s.d_es); FREE(s.d_nb); FREE(s.d_tdesc);
   }
   for (auto& l : c->levels) {
-    FREE(l.d_dst); FREE(l.d_up); FREE(l.d_xmap); FREE(l.d_mdesc); FREE(l.d_sdesc);
+    FREE(l.d_dst); FREE(l.d_up); FREE(l.d_xmap); FREE(l.d_mdesc); FREE(l.d_sdesc); FREE(l.d_tsdesc);
   }
   c->stages.clear();
   c->levels.clear();
@@ -441,7 +441,7 @@ int hps_mesh(hps_ctx* c, int nx, int ny, int N) {
   CHECK_CTX(c);
   if (nx != ny || nx < 2 || (nx & (nx - 1)) != 0)
     return fail(c, HPS_EINVAL, "nx == ny == 2^k with k >= 1 required");
-  if (N < 2 || N > 16) return fail(c, HPS_EINVAL, "2 <= N <= 16 required");
+  if (N < 2 || N > 24) return fail(c, HPS_EINVAL, "2 <= N <= 24 required");
   cudaStreamSynchronize(c->stream);
   free_tree(c);
   free_solver(c);
@@ -696,7 +696,7 @@ int hps_build_leaves(hps_ctx* c, int precision) {
       for (void* s : v) dev_free(c, s);
     }
   } sg{c, scratch};
-  {
+  if (c->N <= LEAF_SMEM_MAX_N) {
     const int grid = std::min(c->E, std::max(1, c->num_sms));
     double* Ascr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * c->nb * c->nb));
     double* Zscr = static_cast<double*>(dev_alloc(c, sizeof(double) * (size_t)grid * 2 * p.ni * c->nb));
@@ -711,7 +711,14 @@ int hps_build_leaves(hps_ctx* c, int precision) {
     HPS_CK(c, launch_leaf(p, grid, st));
   }
   HPS_CK(c, cudaEventSynchronize(ev_counts));
+  const int n_good = c->pin_counts[0];
   const int n_bad = c->pin_counts[1];
+  if (c->N > LEAF_SMEM_MAX_N) {
+    // the packed factor of L~_ii does not fit shared memory: the interior solver's route
+    PhaseScope ps(c, HPS_PH_LEAF);
+    const int rc = fd_leaf_maps(c, d_good, n_good);
+    if (rc != HPS_OK) return rc;
+  }
   if (n_bad > 0) {
     const size_t per = sizeof(double2) * (size_t)p.ni * (p.ni + p.nb);
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_bad, ((size_t)512 << 20) / per));
@@ -788,7 +795,8 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
     if (!ctxs[i]->have_coeff) return fail(c0, HPS_ENOTBUILT, "hps_set_coeff on every context first");
   }
   // classify every element of every context; group the Cholesky-route ones by GLL order
-  std::vector<LeafElem> groups[17];
+  std::vector<LeafElem> groups[LEAF_SMEM_MAX_N + 1];
+  std::vector<std::vector<int>> big(n);  // positive-definite elements of orders above the leaf kernel's
   std::vector<std::vector<int>> bad(n);
   for (int i = 0; i < n; ++i) {
     hps_ctx* c = ctxs[i];
@@ -805,7 +813,9 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
     HPS_CK(c0, cudaStreamSynchronize(c->stream));
     if (cerr) return fail(c0, HPS_EINVAL, "non-finite coefficient sample in the batch");
     for (int e = 0; e < c->E; ++e) {
-      if (route[e] == 0) {
+      if (route[e] == 0 && c->N > LEAF_SMEM_MAX_N) {
+        big[i].push_back(e);
+      } else if (route[e] == 0) {
         LeafElem d;
         d.c = c->d_c + (size_t)e * n1 * n1;
         d.T = c->d_T + (size_t)e * c->nb * c->nb;
@@ -822,7 +832,18 @@ int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
   int flag = 0;
   {
     PhaseScope ps(c0, HPS_PH_LEAF);
-    for (int N = 2; N <= 16; ++N) {
+    for (int i = 0; i < n; ++i) {
+      if (big[i].empty()) continue;
+      hps_ctx* c = ctxs[i];
+      int* d_big = static_cast<int*>(dev_alloc(c, sizeof(int) * big[i].size()));
+      if (!d_big) return fail(c0, HPS_ENOMEM, "element list");
+      HPS_CK(c0, cudaMemcpyAsync(d_big, big[i].data(), sizeof(int) * big[i].size(), cudaMemcpyHostToDevice,
+                                 c->stream));
+      const int rc = fd_leaf_maps(c, d_big, (int)big[i].size());
+      dev_free(c, d_big);
+      if (rc != HPS_OK) return fail(c0, rc, std::string("context ") + std::to_string(i) + ": " + c->err);
+    }
+    for (int N = 2; N <= LEAF_SMEM_MAX_N; ++N) {
       if (groups[N].empty()) continue;
       // reference tables of order N from any context with that order
       hps_ctx* cn = nullptr;

@@ -47,6 +47,10 @@ struct Level {               // merge l: stage l-1 -> stage l
   int* d_xmap = nullptr;     // [npairs * 2m] row of x -> child row (interface rows)
   GemmDesc* d_mdesc = nullptr;  // [N_MROLE][npairs]
   GemmDesc* d_sdesc = nullptr;  // [N_SROLE][npairs]
+  // FP32 tree, interface >= 32 complex: U and Dm kept tiled (tile_operator, tc.cu) for the sweeps
+  GemmDesc* d_tsdesc = nullptr;  // [N_SROLE][npairs]: the sweep descriptors with a_r = first block, a_c = blocks per row tile
+  void* Ut = nullptr;           // tiled U  (replaces U)
+  void* Dmt = nullptr;          // tiled Dm (replaces Dm)
 };
 
 struct Coarse {
@@ -211,6 +215,10 @@ void free_vol_staging(hps_ctx* c);  // staged sources and the H buffer (volume.c
 // H of every element for sources s (device [nrhs][E][(N+1)^2]) -> H_es [n_es][nrhs] (volume.cu)
 int source_H(hps_ctx* c, const double2* s, int nrhs, double2* H_es);
 int subtract_H(hps_ctx* c, double2* rho, const double2* H_es, int nrhs);
+// Leaf maps of the listed positive-definite elements (device list of count) by the interior
+// solver: the route for orders whose factor does not fit shared memory (volume.cu)
+int fd_leaf_maps(hps_ctx* c, const int* elems, int count);
+constexpr int LEAF_SMEM_MAX_N = 16;  // largest order of the shared-memory leaf kernel
 const double2* stage_in(hps_ctx* c, const void* src, size_t elems, double2** buf, size_t* cap);
 void free_graph(hps_ctx* c);
 int ensure_sweep_buffers(hps_ctx* c, int nrhs);

@@ -90,6 +90,34 @@ cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long
   return launch_gemm<R>(a, mmax, nmax, c->stream, kmax);
 }
 
+// The sweep products of a tiled level (FP32 tree): A = the tiled operator, tensor cores.
+cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, const void* B, long long ldb,
+                       const void* C0, long long ldc0, void* C, long long ldc, double alpha, const int* maps, int mmax,
+                       int nmax, int n_launch, int kmax) {
+  GemmArgs<float> a;
+  a.A = static_cast<const float2*>(A);
+  a.B = static_cast<const float2*>(B);
+  a.C0 = static_cast<const float2*>(C0);
+  a.C = static_cast<float2*>(C);
+  a.lda = 0;
+  a.ldb = ldb;
+  a.ldc0 = ldc0;
+  a.ldc = ldc;
+  a.alpha = mk<float>(float(alpha), 0.f);
+  a.beta = mk<float>(1.f, 0.f);
+  a.desc = d;
+  a.nbatch = nb;
+  a.maps = maps;
+  a.n_launch = n_launch;
+  a.ws = static_cast<float2*>(c->gemm_ws);
+  a.ws_elems = (long long)c->gemm_ws_elems;
+  a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
+  a.err = c->d_gemm_err;
+  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, a.err, c->stream);
+}
+
+bool level_tiled(const Level& Lv) { return 2 * Lv.m >= 64; }
+
 GemmDesc D(int a_r, int a_c, int b_r, int b_c, int c0_r, int c0_c, int c_r, int c_c, int m, int n, int k, int rmap = -1,
            int cmap = -1) {
   GemmDesc d;
@@ -269,6 +297,21 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     Lv.d_mdesc = dev_upload(c, md);
     Lv.d_sdesc = dev_upload(c, sd);
     if (!Lv.d_mdesc || !Lv.d_sdesc) return fail(c, HPS_ENOMEM, "descriptors");
+    if (level_tiled(Lv)) {
+      // the same sweep products on the tiled operators: a_r = the pair's first block, a_c =
+      // blocks per row tile
+      const int nrt_u = (2 * p + TILE_M - 1) / TILE_M, nkt_u = (2 * m + TILE_K - 1) / TILE_K;
+      const int nrt_d = (2 * m + TILE_M - 1) / TILE_M, nkt_d = (2 * n + TILE_K - 1) / TILE_K;
+      std::vector<GemmDesc> td(sd);
+      for (int P = 0; P < NP; ++P) {
+        td[SUP * NP + P].a_r = P * nrt_u * nkt_u;
+        td[SUP * NP + P].a_c = nkt_u;
+        td[SDN * NP + P].a_r = P * nrt_d * nkt_d;
+        td[SDN * NP + P].a_c = nkt_d;
+      }
+      Lv.d_tsdesc = dev_upload(c, td);
+      if (!Lv.d_tsdesc) return fail(c, HPS_ENOMEM, "descriptors");
+    }
   }
   }  // plan
   // ---- allocations ----
@@ -365,6 +408,21 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     HPS_CK(c, gemm<R>(c, md + PD3 * NP, NP, nullptr, 0, nullptr, 0, G, 2 * m, Lv.Dm, 2 * n, 1.0, nullptr, 2 * m, m, m));
     HPS_CK(c, gemm<R>(c, md + PD2 * NP, NP, G, 2 * m, T0, n, nullptr, 0, Lv.Dm, 2 * n, -1.0, nullptr, 2 * m, p, p, m));
     HPS_CK(c, gemm<R>(c, md + PD4 * NP, NP, G, 2 * m, T0, n, nullptr, 0, Lv.Dm, 2 * n, -1.0, nullptr, 2 * m, p, p, m));
+    if (sizeof(R) == 4 && level_tiled(Lv)) {
+      // the sweeps stream U and Dm block by block: keep them tiled, drop the row-major copies
+      const size_t bu = (size_t)NP * ((2 * p + TILE_M - 1) / TILE_M) * ((2 * m + TILE_K - 1) / TILE_K) * TILE_M * TILE_K;
+      const size_t bd = (size_t)NP * ((2 * m + TILE_M - 1) / TILE_M) * ((2 * n + TILE_K - 1) / TILE_K) * TILE_M * TILE_K;
+      Lv.Ut = dev_alloc(c, sizeof(float2) * bu);
+      Lv.Dmt = dev_alloc(c, sizeof(float2) * bd);
+      if (!Lv.Ut || !Lv.Dmt) return fail(c, HPS_ENOMEM, "tiled sweep operators");
+      HPS_CK(c, tile_operator(static_cast<float2*>(Lv.Ut), static_cast<const float2*>(Lv.U), NP, 2 * p, 2 * m, 2 * m,
+                              (long long)2 * p * 2 * m, c->stream));
+      HPS_CK(c, tile_operator(static_cast<float2*>(Lv.Dmt), static_cast<const float2*>(Lv.Dm), NP, 2 * m, 2 * n,
+                              2 * n, (long long)2 * m * 2 * n, c->stream));
+      dev_free(c, Lv.U);
+      dev_free(c, Lv.Dm);
+      Lv.U = Lv.Dm = nullptr;
+    }
   }
   // ---- coarse level ----
   {
@@ -716,8 +774,12 @@ int mg_level(hps_ctx* c, int l, int nrhs, int k) {
   const Stage& P1 = c->stages[l + 1];
   const int n = Lv.n, m = Lv.m, p = Lv.p, NP = Lv.npairs;
   // up-sweep: rho'_E = rho_E - U f
-  HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
-                    Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
+  if (Lv.Ut)
+    HPS_CK(c, gemm_tiled(c, Lv.d_tsdesc + SUP * NP, NP, Lv.Ut, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
+                         Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
+  else
+    HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
+                      Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
   if (c->gamma <= 1) {
     int rc = mg_level<R>(c, l + 1, nrhs, k);
     if (rc != HPS_OK) return rc;
@@ -741,8 +803,12 @@ int mg_level(hps_ctx* c, int l, int nrhs, int k) {
   // down-sweep: children's outer rows from the merged solution, x = Dm [child1; child2], x into the interface rows
   C* v0 = static_cast<C*>(P0.vec);
   HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(P1.vec), Lv.d_up, (long long)P1.nsub * P1.n, nrhs, st)));
-  HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
-                    2 * m, nrhs, nrhs, 2 * n));
+  if (Lv.Dmt)
+    HPS_CK(c, gemm_tiled(c, Lv.d_tsdesc + SDN * NP, NP, Lv.Dmt, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
+                         2 * m, nrhs, nrhs, 2 * n));
+  else
+    HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
+                      2 * m, nrhs, nrhs, 2 * n));
   HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(c->sw_x), Lv.d_xmap, (long long)NP * 2 * m, nrhs, st)));
   return HPS_OK;
 }

@@ -279,15 +279,248 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TT::TCOLS) : "memory");
 }
 
+// Sweep products on operators stored tiled (tile_operator): each pair's operator is laid out as
+// blocks of 128 rows x 8 complex k, each block one contiguous 8 KB in the MMA's core-matrix
+// order and zero-padded past the operator's rows and k, so a CTA's k-chunk is one sequential
+// 8 KB read (the row-major operator gave 64-byte pieces of 128 rows per chunk).  The blocks come
+// in by asynchronous copies (cp.async, 16 bytes per thread and instruction) into a ring of TCP_S
+// raw stages, TCP_S - 1 chunks ahead of the one being multiplied; each chunk is then split from
+// its raw stage into the hi/lo tiles of the 3xTF32 product (same offsets) and multiplied as in
+// tc_gemm_kernel.  GemmDesc.a_r is the pair's first block and a_c its blocks per row tile.
+constexpr int TCP_ARAW = TC_M * TC_KC * 8;  // bytes of one operator block (8 KB)
+
+template <int NC> struct TcpTile {
+  static constexpr int S = NC <= 32 ? 4 : 3;               // raw stages
+  static constexpr int BRAW = TC_KC * NC * 8;             // bytes of one raw B stage
+  static constexpr int RAW = TCP_ARAW + BRAW;             // bytes of one raw stage (a multiple of 1024)
+  static constexpr size_t SMEM = (size_t)S * RAW + (size_t)2 * TcTile<NC>::STAGE * sizeof(float) + 1024;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int TCS_NT = 256;  // 8 warps: the splitting work is spread over twice the threads
+
+template <int NC>
+__global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, int* err, int ksplit, int kc, int mmax,
+                                                             int nmax) {
+  using TT = TcTile<NC>;
+  using TP = TcpTile<NC>;
+  constexpr int NR = TT::NR, B_TILE = TT::B_TILE, STAGE = TT::STAGE, TCP_S = TP::S;
+  constexpr int G = NR / 16;          // 16-column groups of the accumulator
+  constexpr int GH = G / 2;           // groups per warp quarter (two warps share each TMEM lane quarter)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* base = reinterpret_cast<float*>(ring + (size_t)TCP_S * TP::RAW);  // 1024-aligned: RAW is a multiple of 1024
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int bb = blockIdx.z % a.nbatch, sp = blockIdx.z / a.nbatch;
+  const GemmDesc d = a.desc[bb];
+  const int n = d.n < 0 ? a.n_launch : d.n, m = d.m;
+  const int kb = ksplit > 1 ? sp * kc : 0;
+  const int kk = ksplit > 1 ? min(d.k, kb + kc) : d.k;  // this split covers complex k in [kb, kk)
+  const int row0 = blockIdx.y * TC_M, col0 = blockIdx.x * NC;
+  if (row0 >= m || col0 >= n) return;  // uniform over the block, before any tensor-memory use
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "n"(TT::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  // epilogue roles: warp w reads TMEM lane quarter w % 4 (output rows) and column groups
+  // [h * GH, (h + 1) * GH), h = w / 4; its row data is loaded now so its latency hides behind
+  // the k loop
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = 32 * quarter + lane, gi = row0 + row;
+  const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
+  const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
+  const long long orow = gi < m ? (long long)d.c_r + (rmap ? rmap[gi] : gi) : 0;
+  const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+  constexpr int NCH = NC / 2;  // complex columns of this warp's half
+  float2 c0v[NCH];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int gj = col0 + half * NCH + j;
+    c0v[j] = (ksplit == 1 && a.C0 && gi < m && gj < n) ? cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj])
+                                                       : make_float2(0.f, 0.f);
+  }
+
+  // this CTA's blocks: row tile blockIdx.y of its pair, chunks from kb / TC_KC on
+  const float2* Ab = a.A + ((long long)d.a_r + (long long)blockIdx.y * d.a_c + kb / TC_KC) * (TC_M * TC_KC);
+  const int nk = kk > kb ? (kk - kb + TC_KC - 1) / TC_KC : 0;
+  const uint32_t ring_s = smem_u32(ring);
+  // chunk kt (if any) into raw stage kt % TCP_S; always one commit group per call
+  auto issue = [&](int kt) {
+    if (kt < nk) {
+      const int k0 = kb + kt * TC_KC;
+      const uint32_t ra = ring_s + (uint32_t)((kt % TCP_S) * TP::RAW);
+      unsigned char* rap = ring + (size_t)(kt % TCP_S) * TP::RAW;
+      const char* src = reinterpret_cast<const char*>(Ab + (long long)kt * (TC_M * TC_KC));
+#pragma unroll
+      for (int i = 0; i < TCP_ARAW / (16 * TCS_NT); ++i) {
+        const int o = (tid + i * TCS_NT) * 16;
+        cp_async16(ra + o, src + o);
+      }
+      for (int l = tid; l < TC_KC * NC; l += TCS_NT) {
+        const int kc2 = l / NC, nc = l % NC;
+        const int gk = k0 + kc2, gj = col0 + nc;
+        const uint32_t off = (uint32_t)(TCP_ARAW + l * 8);
+        if (gk < kk && gj < n) {
+          const long long br = (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+          cp_async8(ra + off, a.B + br * a.ldb + d.b_c + gj);
+        } else {
+          *reinterpret_cast<float2*>(rap + off) = make_float2(0.f, 0.f);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  bool ok = true;
+#pragma unroll 1
+  for (int kt = 0; kt < TCP_S - 1; ++kt) issue(kt);
+  for (int kt = 0; kt < nk && ok; ++kt) {
+    const int s = kt & 1;
+    // raw stage (kt - 1) % TCP_S was read by every thread before the last barrier: refill it
+    issue(kt + TCP_S - 1);
+    cp_async_wait<TCP_S - 1>();  // this thread's copies of chunk kt have landed
+    if (kt >= 2 && !mbar_wait(smem_u32(&mbar[s]), ((kt >> 1) - 1) & 1)) {
+      s_fail = 1;  // every thread sees the same timeout: the loop ends uniformly below
+    }
+    __syncthreads();
+    if (s_fail) {
+      ok = false;
+      break;
+    }
+    const unsigned char* rap = ring + (size_t)(kt % TCP_S) * TP::RAW;
+    float* Ah = base + s * STAGE;
+    float* Al = Ah + A_TILE;
+    float* Bh = Al + A_TILE;
+    float* Bl = Bh + B_TILE;
+    // A: the raw block is already in the tile's core-matrix order; split each (re, im) in place
+#pragma unroll
+    for (int u = 0; u < TCP_ARAW / (8 * TCS_NT); ++u) {
+      const int o = tid + u * TCS_NT;  // float2 index
+      const float2 v = reinterpret_cast<const float2*>(rap)[o];
+      uint2 h, lo;
+      split_tf32(v.x, h.x, lo.x);
+      split_tf32(v.y, h.y, lo.y);
+      reinterpret_cast<uint2*>(Ah)[o] = h;
+      reinterpret_cast<uint2*>(Al)[o] = lo;
+    }
+    // B': complex (kc, nc) -> real column 2nc gets (Re b, -Im b), column 2nc+1 gets (Im b, Re b)
+    for (int l = tid; l < TC_KC * NC; l += TCS_NT) {
+      const int kc2 = l / NC, nc = l % NC;
+      const float2 v = *reinterpret_cast<const float2*>(rap + TCP_ARAW + l * 8);
+      uint2 h0, l0, h1, l1;
+      split_tf32(v.x, h0.x, l0.x);
+      split_tf32(-v.y, h0.y, l0.y);
+      split_tf32(v.y, h1.x, l1.x);
+      h1.y = h0.x;
+      l1.y = l0.x;
+      const uint32_t o0 = core_off(2 * nc, 2 * kc2) / 4, o1 = core_off(2 * nc + 1, 2 * kc2) / 4;
+      *reinterpret_cast<uint2*>(Bh + o0) = h0;
+      *reinterpret_cast<uint2*>(Bl + o0) = l0;
+      *reinterpret_cast<uint2*>(Bh + o1) = h1;
+      *reinterpret_cast<uint2*>(Bl + o1) = l1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+#pragma unroll
+      for (int ks = 0; ks < TC_KR / 8; ++ks) {
+        const uint32_t step = ks * 2 * LBO;  // two core matrices = 8 real k
+        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bh + step), TT::IDESC, (kt > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(ah + step), smem_desc(bl + step), TT::IDESC, 1u);
+        mma_tf32(tmem, smem_desc(al + step), smem_desc(bh + step), TT::IDESC, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[s]))
+                   : "memory");
+    }
+  }
+  cp_async_wait<0>();  // no copy of this CTA is left in flight (the last groups may be empty)
+  if (ok && nk > 0 && !mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) s_fail = 1;
+  __syncthreads();
+  ok = ok && !s_fail;  // uniform over the block (tcgen05.ld is warp-collective)
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // let the MMAs already issued finish before the tensor memory is released
+    if (nk > 0) mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (ok) {
+    float2* W = ksplit > 1 ? a.ws + (((long long)sp * a.nbatch + bb) * mmax) * nmax : nullptr;
+#pragma unroll
+    for (int gq = 0; gq < GH; ++gq) {
+      const int c0 = (half * GH + gq) * 16;  // real column of this group
+      uint32_t v[16];
+      if (nk > 0) {
+        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
+      }
+      if (gi < m) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int gj = col0 + c0 / 2 + j;
+          if (gj >= n) continue;
+          const float2 acc = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+          if (W) {
+            W[(long long)gi * nmax + gj] = acc;
+            continue;
+          }
+          const float2 o = cadd(cmul(a.alpha, acc), c0v[gq * 8 + j]);
+          a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = o;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TT::TCOLS) : "memory");
+}
+
 template <int NC>
 constexpr size_t tc_gemm_smem() { return (size_t)2 * TcTile<NC>::STAGE * sizeof(float) + 1024; }
 
-template <int NC>
+template <int NC, bool PIPE>
 cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
   const int gx = (nmax + NC - 1) / NC, gy = (mmax + TC_M - 1) / TC_M;
   const long long blocks = (long long)gx * gy * a.nbatch;
-  // split K until about three CTAs per SM are busy (a CTA streams its k range serially)
-  const long long target = 3LL * a.num_sms;
+  // split K until about three (pipelined kernel: two) CTAs per SM are busy (a CTA streams its
+  // k range serially)
+  const long long target = (PIPE ? 2LL : 3LL) * a.num_sms;
   int ksplit = 1;
   if (kmax >= 8 * TC_KC && a.ws && blocks < target) {
     ksplit = (int)((target + blocks - 1) / blocks);
@@ -305,7 +538,8 @@ cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, in
   }
   if ((long long)a.nbatch * ksplit > 65535) return cudaErrorInvalidValue;
   dim3 grid(gx, gy, a.nbatch * ksplit);
-  tc_gemm_kernel<NC><<<grid, TC_NT, tc_gemm_smem<NC>(), s>>>(a, err, ksplit, kc, mmax, nmax);
+  if constexpr (PIPE) tcs_gemm_kernel<NC><<<grid, TCS_NT, TcpTile<NC>::SMEM, s>>>(a, err, ksplit, kc, mmax, nmax);
+  else tc_gemm_kernel<NC><<<grid, TC_NT, tc_gemm_smem<NC>(), s>>>(a, err, ksplit, kc, mmax, nmax);
   note_launch();
   if (ksplit > 1) return splitk_reduce(a, ksplit, mmax, nmax, s);
   return cudaGetLastError();
@@ -316,15 +550,58 @@ cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, in
 cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
-  if (nmax <= 16) return launch_tc<16>(a, mmax, nmax, kmax, err, s);
-  if (nmax <= 32) return launch_tc<32>(a, mmax, nmax, kmax, err, s);
-  return launch_tc<64>(a, mmax, nmax, kmax, err, s);
+  if (nmax <= 16) return launch_tc<16, false>(a, mmax, nmax, kmax, err, s);
+  if (nmax <= 32) return launch_tc<32, false>(a, mmax, nmax, kmax, err, s);
+  return launch_tc<64, false>(a, mmax, nmax, kmax, err, s);
+}
+
+cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+  if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
+  if (a.nbatch > 65535) return cudaErrorInvalidValue;
+  if (nmax <= 16) return launch_tc<16, true>(a, mmax, nmax, kmax, err, s);
+  if (nmax <= 32) return launch_tc<32, true>(a, mmax, nmax, kmax, err, s);
+  return launch_tc<64, true>(a, mmax, nmax, kmax, err, s);
+}
+
+// TL[P][rt][kt] = 128 x 8 complex block of A_P (rows rt*128.., k kt*8..), core-matrix order,
+// zero past the operator's rows and k.
+__global__ void tile_operator_kernel(float2* __restrict__ TL, const float2* __restrict__ A, int npairs, int rows,
+                                     int K, int lda, long long pair_stride, int nrt, int nkt) {
+  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const long long blk = l / (TC_M * TC_KC);
+    const int w = (int)(l % (TC_M * TC_KC));  // float2 position inside the block
+    const int kt = (int)(blk % nkt), rt = (int)((blk / nkt) % nrt), P = (int)(blk / ((long long)nkt * nrt));
+    // invert core_off(r, 2 kc) / 8: row group r/8 (SBO = 512 B), k group (2 kc)/4 (LBO = 128 B),
+    // row r%8 (16 B), pair (2 kc)%4 / 2 (8 B)
+    const int byte = w * 8;
+    const int rg = byte / (int)SBO, rem = byte % (int)SBO;
+    const int kg = rem / (int)LBO, rem2 = rem % (int)LBO;
+    const int r = rg * 8 + rem2 / 16, kc = kg * 2 + (rem2 % 16) / 8;
+    const int gi = rt * TC_M + r, gk = kt * TC_KC + kc;
+    TL[l] = (gi < rows && gk < K) ? A[(long long)P * pair_stride + (long long)gi * lda + gk] : make_float2(0.f, 0.f);
+  }
+}
+
+cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int K, int lda, long long pair_stride,
+                          cudaStream_t s) {
+  const int nrt = (rows + TC_M - 1) / TC_M, nkt = (K + TC_KC - 1) / TC_KC;
+  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  if (blocks < 1) return cudaSuccess;
+  tile_operator_kernel<<<(int)blocks, 256, 0, s>>>(TL, A, npairs, rows, K, lda, pair_stride, nrt, nkt);
+  note_launch();
+  return cudaGetLastError();
 }
 
 void optin_tc() {
   smem_optin(tc_gemm_kernel<16>);
   smem_optin(tc_gemm_kernel<32>);
   smem_optin(tc_gemm_kernel<64>);
+  smem_optin(tcs_gemm_kernel<16>);
+  smem_optin(tcs_gemm_kernel<32>);
+  smem_optin(tcs_gemm_kernel<64>);
 }
 
 }  // namespace hps

@@ -51,7 +51,10 @@ struct VolParams {
   const double* tab;     // [S q^2 | U q^2 | lam q | sqrt(w_i) q | corner weights wl q, wr q]
   const double2* T;      // leaf maps [E][nb][nb]
   const int* elems;      // positive-definite route elements
-  const int* count_dev;  // their count (device)
+  const int* count_dev;  // their count (device); null: count_host
+  int count_host = 0;
+  int b_shared = 0;      // interior solve: one right-hand-side set B [nrhs][ni] for every element
+  int x_by_pos = 0;      // interior solve: X indexed by list position instead of element
 };
 
 // deterministic block sums of VCH per-thread partials; out[j] valid after the call
@@ -117,9 +120,11 @@ __global__ void __launch_bounds__(VT) interior_solve_kernel(VolParams p, const d
   }
   for (int l = tid; l < ni; l += nth) L32[l] = (float)(1.0 / (tl[l / q] + tl[l % q]));
   const double h2 = 0.25 * p.h * p.h;
-  const int nel = *p.count_dev;
+  const int nel = p.count_dev ? *p.count_dev : p.count_host;
   for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
     const int e = p.elems[ei];
+    const long long eb = p.b_shared ? 0 : e;   // element index of B
+    const long long ex = p.x_by_pos ? ei : e;  // element index of X
     __syncthreads();
     for (int l = tid; l < ni; l += nth) {
       const int a = l / q, b = l % q;
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(VT) interior_solve_kernel(VolParams p, const d
         double2 b = make_double2(0.0, 0.0);
         if (j < cr) {
           const double s = 1.0 / (tv2[l / q] * tv2[l % q]);
-          b = cscale(B[((long long)e * nrhs + r0 + j) * ni + l], s);
+          b = cscale(B[(eb * nrhs + r0 + j) * ni + l], s);
           bn[j] += b.x * b.x + b.y * b.y;
         }
         R64[f] = b;
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(VT) interior_solve_kernel(VolParams p, const d
             ax.y = fma(Xj[a * q + k].y, s2, ax.y);
           }
           const double s = 1.0 / (tv2[a] * tv2[b]);
-          const double2 bb = cscale(B[((long long)e * nrhs + r0 + j) * ni + l], s);
+          const double2 bb = cscale(B[(eb * nrhs + r0 + j) * ni + l], s);
           const double2 rr = csub(bb, ax);
           R64[f] = rr;
           rn64[j] += rr.x * rr.x + rr.y * rr.y;
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(VT) interior_solve_kernel(VolParams p, const d
       for (int f = tid; f < tot; f += nth) {
         const int j = f / ni, l = f % ni;
         const double s = 1.0 / (tv2[l / q] * tv2[l % q]);
-        X[((long long)e * nrhs + r0 + j) * ni + l] = cscale(X64[f], s);
+        X[(ex * nrhs + r0 + j) * ni + l] = cscale(X64[f], s);
       }
     }
   }
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(VT) pd_edges_kernel(VolParams p, const double2
   for (int l = tid; l < n1; l += nth) sw[l] = p.wh[l];
   const bool volume = UG != nullptr;
   const double inv2e = 0.5 / p.eta;
-  const int nel = *p.count_dev;
+  const int nel = p.count_dev ? *p.count_dev : p.count_host;
   for (int ei = blockIdx.x; ei < nel; ei += gridDim.x) {
     const int e = p.elems[ei];
     __syncthreads();
@@ -561,7 +566,123 @@ int robust_fields(hps_ctx* c, int nrhs, const double2* Bt, const double2* F, dou
   return rc;
 }
 
+// ---- leaf maps for orders whose packed factor does not fit shared memory (N > 16) ----
+// Z = L~_ii^{-1} L~_iG by the interior solver, A = Dn_GG - Dn_Gi Z, P = A + i eta I,
+// T = I - 2 i eta P^{-1} (the block elimination of section 3.1 that the leaf kernel runs in shared
+// memory).  L~_iG couples an interior node only to the edge nodes of its own row and column of
+// the tensor grid, with the h-invariant Kronecker weights K^[a][0 or N] w^_b (and transposed).
+__global__ void fd_coupling_kernel(VolParams p, double2* __restrict__ B) {
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
+  const long long tot = (long long)nb * ni;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(l / ni), I = (int)(l % ni);
+    const int side = g / q, k = g % q + 1, a = I / q + 1, b = I % q + 1;
+    double v = 0.0;
+    if (side == 0 && b == k) v = p.Kh[a * n1 + 0] * p.wh[b];
+    else if (side == 1 && b == k) v = p.Kh[a * n1 + N] * p.wh[b];
+    else if (side == 2 && a == k) v = p.wh[a] * p.Kh[b * n1 + 0];
+    else if (side == 3 && a == k) v = p.wh[a] * p.Kh[b * n1 + N];
+    B[l] = make_double2(v, 0.0);
+  }
+}
+
+// W[pos] = [P | I] (nb x 2 nb) from Z [pos][nb][ni] (the interior solves of the coupling columns)
+__global__ void __launch_bounds__(VT) fd_leaf_p_kernel(VolParams p, const double2* __restrict__ Z,
+                                                      double2* __restrict__ W) {
+  const int N = p.N, q = p.q, ni = p.ni, nb = p.nb, n1 = N + 1;
+  __shared__ double sD[25 * 25];
+  const double dsc = 2.0 / p.h;
+  for (int l = threadIdx.x; l < n1 * n1; l += blockDim.x) sD[l] = dsc * p.Dh[l];
+  __syncthreads();
+  for (int pos = blockIdx.x; pos < p.count_host; pos += gridDim.x) {
+    const double2* Zp = Z + (long long)pos * nb * ni;
+    double2* Wp = W + (long long)pos * nb * 2 * nb;
+    for (int f = threadIdx.x; f < nb * nb; f += blockDim.x) {
+      const int g = f / nb, g2 = f % nb;
+      const int sg = g / q, kg = g % q, s2 = g2 / q, k2 = g2 % q;
+      // Dn_GG: each edge node couples to itself and to the opposite node of its line
+      double dgg = 0.0;
+      if (kg == k2) {
+        const bool xline = sg < 2 && s2 < 2, yline = sg >= 2 && s2 >= 2;
+        if (xline || yline) {
+          const int lo = xline ? 0 : 2;
+          const int row = (sg == lo) ? 0 : N, col = (s2 == lo) ? 0 : N;
+          dgg = (sg == lo ? -1.0 : 1.0) * sD[row * n1 + col];
+        }
+      }
+      const double2 dz = dn_interior(sD, N, q, Zp + (long long)g2 * ni, g);
+      double2 v = make_double2(dgg - dz.x, -dz.y);
+      if (g == g2) v.y += p.eta;
+      Wp[(long long)g * 2 * nb + g2] = v;
+      Wp[(long long)g * 2 * nb + nb + g2] = make_double2(g == g2 ? 1.0 : 0.0, 0.0);
+    }
+  }
+}
+
+// T = I - 2 i eta P^{-1} from the right half of W into the leaf maps of the listed elements
+__global__ void fd_leaf_t_kernel(VolParams p, const double2* __restrict__ W, double2* __restrict__ T) {
+  const int nb = p.nb;
+  const long long tot = (long long)p.count_host * nb * nb;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const int pos = (int)(l / ((long long)nb * nb));
+    const int rem = (int)(l % ((long long)nb * nb));
+    const int g = rem / nb, g2 = rem % nb;
+    const double2 y = W[((long long)pos * nb + g) * 2 * nb + nb + g2];
+    // -2 i eta (x + i y) = 2 eta y - 2 i eta x
+    T[(long long)p.elems[pos] * nb * nb + rem] =
+        make_double2((g == g2 ? 1.0 : 0.0) + 2.0 * p.eta * y.y, -2.0 * p.eta * y.x);
+  }
+}
+
 }  // namespace
+
+// Leaf maps of the listed positive-definite elements by the interior solver (any order N).
+int fd_leaf_maps(hps_ctx* c, const int* elems, int count) {
+  if (count <= 0) return HPS_OK;
+  const int nb = c->nb, ni = c->q * c->q;
+  const size_t per = sizeof(double2) * ((size_t)nb * ni + (size_t)nb * 2 * nb);
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(count, ((size_t)1 << 30) / per));
+  double2* Bc = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)nb * ni));
+  double2* Z = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)chunk * nb * ni));
+  double2* W = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)chunk * nb * 2 * nb));
+  int* piv = static_cast<int*>(dev_alloc(c, sizeof(int) * (size_t)chunk * GJ_NB));
+  double2* lu = static_cast<double2*>(dev_alloc(c, sizeof(double2) * (size_t)chunk * GJ_NB * GJ_NB));
+  struct Release {
+    hps_ctx* c;
+    std::vector<void*> v;
+    ~Release() {
+      cudaStreamSynchronize(c->stream);
+      for (void* x : v) dev_free(c, x);
+    }
+  } rel{c, {Bc, Z, W, piv, lu}};
+  if (!Bc || !Z || !W || !piv || !lu) return fail(c, HPS_ENOMEM, "leaf workspace (interior solver route)");
+  cudaStream_t st = c->stream;
+  VolParams p = vol_params(c, nb);
+  fd_coupling_kernel<<<grid_for((long long)nb * ni), 256, 0, st>>>(p, Bc);
+  note_launch();
+  HPS_CK(c, cudaGetLastError());
+  for (int b0 = 0; b0 < count; b0 += chunk) {
+    const int nch = std::min(chunk, count - b0);
+    VolParams pc = p;
+    pc.elems = elems + b0;
+    pc.count_dev = nullptr;
+    pc.count_host = nch;
+    pc.b_shared = 1;
+    pc.x_by_pos = 1;
+    const int grid = std::max(1, std::min(nch, 2 * c->num_sms));
+    interior_solve_kernel<<<grid, VT, interior_smem_bytes(c->q), st>>>(pc, Bc, Z);
+    note_launch();
+    HPS_CK(c, cudaGetLastError());
+    fd_leaf_p_kernel<<<std::max(1, std::min(nch, 4 * c->num_sms)), VT, 0, st>>>(pc, Z, W);
+    note_launch();
+    HPS_CK(c, cudaGetLastError());
+    HPS_CK(c, gj_invert<double>(W, nb, nch, piv, lu, c->d_flag, st));
+    fd_leaf_t_kernel<<<grid_for((long long)nch * nb * nb), 256, 0, st>>>(pc, W, c->d_T);
+    note_launch();
+    HPS_CK(c, cudaGetLastError());
+  }
+  return HPS_OK;
+}
 
 // The per-element work arrays (sized by the number of right-hand sides).  The staged sources and
 // the H buffer have their own sizes and are released by free_vol_staging only: a solve stages

@@ -81,6 +81,45 @@ def test_leaf_maps(solver, nx, N, kappa):
         assert rel(Tg[e], To) < 1e-11, e
 
 
+@pytest.mark.parametrize("nx,N,kappa", [(2, 20, 5.0), (4, 24, 15.0), (2, 17, 8.0)])
+def test_leaf_maps_high_order(solver, nx, N, kappa):
+    """Orders above 16 (section 8(b) asks for N <= 24): the interior solver's leaf route
+    (CG with fast diagonalisation, FP64 refinement) against the oracle's dense element solve."""
+    prob = inputs.single_bump(nx, N, kappa, 1, seed=7)
+    H.setup(solver, prob)
+    Tg = solver.leaf_T(0, nx * nx)
+    mesh = Mesh(nx, nx, N)
+    c = coefficient(mesh, kappa, prob.bumps)
+    for e in range(mesh.E):
+        assert rel(Tg[e], leaf_itI(N, mesh.h, c[e], kappa)["T"]) < 1e-11, e
+
+
+@pytest.mark.parametrize("precision", [H.HPS_FP64, H.HPS_MIXED])
+def test_solve_order_24(solver, precision):
+    """A 4x4, N=24 problem end to end (leaves by the interior solver, merges, FGMRES) against
+    the oracle's dense skeleton solve; the elements away from the bump are past the
+    positive-definite bound (kappa^2 (h/2)^2 = 6.25) and take the pivoted route."""
+    prob = inputs.single_bump(4, 24, 20.0, 2, seed=13, L_exact=2)
+    op = OracleProblem(prob)
+    M = assemble_M(op.mesh, op.Ts)
+    t = H.setup(solver, prob, precision)
+    solver.merge_levels(prob.L_exact)
+    g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=5)
+    assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10
+    for k in range(prob.nrhs):
+        assert rel(g[k], np.linalg.solve(M, op.rhs[k])) < 1e-8
+
+
+@pytest.mark.parametrize("nx,N,kappa", [(2, 20, 100.0)])
+def test_leaf_maps_robust_route_high_order(solver, nx, N, kappa):
+    prob = inputs.Problem(nx=nx, N=N, kappa=kappa, eta=kappa, bumps=[inputs.PAPER_BUMP], thetas=[0.3])
+    H.setup(solver, prob)
+    op = OracleProblem(prob)
+    Tg = solver.leaf_T(0, nx * nx)
+    for e in range(nx * nx):
+        assert rel(Tg[e], op.Ts[e]) < 1e-10, e
+
+
 @pytest.mark.parametrize("nx,N,kappa", [(8, 8, 150.0), (8, 8, 36.0), (4, 12, 60.0)])
 def test_leaf_maps_robust_route(solver, nx, N, kappa):
     # kappa^2 (1 - b) (h/2)^2 past the interior Dirichlet bound: the pivoted route (all
@@ -324,7 +363,7 @@ def test_bad_arguments(solver):
     with pytest.raises(H.HPSError):
         solver.mesh(6, 8)
     with pytest.raises(H.HPSError):
-        solver.mesh(4, 17)
+        solver.mesh(4, 25)
     solver.mesh(4, 8)
     with pytest.raises(H.HPSError):
         solver.build_leaves()          # no coefficient yet
