@@ -79,6 +79,9 @@ enum { HPS_FP64 = 0, HPS_MIXED = 1 };
 /* Arithmetic of the outer FGMRES (hps_set_outer_arith). */
 enum { HPS_OUTER_DEFAULT = -1, HPS_OUTER_FP64 = 0, HPS_OUTER_DF64 = 1 };
 
+/* Arithmetic of the sweep products of an HPS_MIXED tree (hps_set_sweep_arith). */
+enum { HPS_SWEEP_DEFAULT = -1, HPS_SWEEP_FP32 = 0, HPS_SWEEP_BF16X3 = 1 };
+
 /* Per-solve report of hps_gmres_solve. */
 typedef struct {
   int outer_iterations;     /* FGMRES iterations (max over right-hand sides)         */
@@ -258,6 +261,26 @@ int hps_set_gamma(hps_ctx* ctx, int gamma);
  * HPS_EINVAL for other values.  DF64 needs HPS_MIXED leaves: with HPS_FP64
  * leaves hps_gmres_solve returns HPS_EINVAL (there is no silent fallback). */
 int hps_set_outer_arith(hps_ctx* ctx, int mode);
+
+/* Arithmetic of the preconditioner's sweep products (section 4.3: the up-sweep
+ * rho' = rho - U f and the down-sweep x = Dm [.;.] of every merge level, which
+ * the V-cycle applies once per FGMRES iteration) for trees built by later
+ * hps_merge_levels calls with HPS_MIXED leaves; the FP64 tree ignores it:
+ *   HPS_SWEEP_FP32     FP32 products (3xTF32 on the tensor cores where the
+ *                      operator has at least 32 interface rows per child);
+ *   HPS_SWEEP_BF16X3   the operators U, Dm of those levels are stored as bf16
+ *                      pairs x = hi + lo (hi = bf16(x), lo = bf16(x - hi),
+ *                      2^-16 relative) and multiplied as hi*hi + hi*lo + lo*hi
+ *                      with FP32 accumulation: about 3 * 2^-16 relative error
+ *                      per product, the same 8 bytes per complex entry as FP32,
+ *                      no splitting of the operator at application time.  The
+ *                      preconditioner is applied inside flexible GMRES whose
+ *                      residuals are formed in FP64, so the solution's accuracy
+ *                      is unchanged; only the iteration count can differ;
+ *   HPS_SWEEP_DEFAULT  HPS_SWEEP_BF16X3 (the initial state).
+ * HPS_EINVAL for other values.  The tree in use keeps the arithmetic it was
+ * built with. */
+int hps_set_sweep_arith(hps_ctx* ctx, int mode);
 
 /* Profiling phases of hps_profile_read. */
 enum {

@@ -137,13 +137,19 @@ template <typename R> struct GemmArgs {
 // 128 rows x 64 complex columns; *err is set when a bounded wait gives up.
 cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s);
 // The same product with A stored tiled by tile_operator (descriptor a_r = the pair's first block,
-// a_c = blocks per row tile of 128 rows; lda unused).
-cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s);
+// a_c = blocks per row tile of 128 rows; lda unused); bf16x3: A tiled by tile_operator_bf16x3
+// and multiplied as hi*hi + hi*lo + lo*hi of bf16 splits (about 3 * 2^-16 relative error).
+cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
+                                 cudaStream_t s);
 // TL[P][row tile][k chunk] = 128 x 8 complex blocks of the operators A_P (rows x K, leading
 // dimension lda, pair P at A + P * pair_stride), each contiguous in the tensor-core tile order,
 // zero-padded past rows and K.
 cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int K, int lda, long long pair_stride,
                           cudaStream_t s);
+// The same blocks as bf16 hi and lo tiles (hi = bf16(x), lo = bf16(x - hi)) in the 16-bit
+// core-matrix order; a block occupies the same 8 KB.
+cudaError_t tile_operator_bf16x3(float2* TL, const float2* A, int npairs, int rows, int K, int lda,
+                                 long long pair_stride, cudaStream_t s);
 constexpr int TILE_M = 128, TILE_K = 8;  // rows and complex k of one operator block
 // Fixed-order sum of ksplit partial tiles from a.ws with the descriptor epilogue (blas.cu).
 cudaError_t splitk_reduce(const GemmArgs<float>& a, int ksplit, int mmax, int nmax, cudaStream_t s);

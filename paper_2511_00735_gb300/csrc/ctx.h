@@ -174,6 +174,10 @@ struct hps_ctx {
   // df64 outer FGMRES (HPS_OUTER_DF64): basis, residual and iterate as float pairs,
   // preconditioned directions in FP32, a df64 copy of the leaf maps
   int outer_arith = HPS_OUTER_DEFAULT;
+  // arithmetic of the sweep products of an FP32 tree (hps_set_sweep_arith), read when the tree
+  // is built; sweep_bf16x3: the current tree's tiled sweep operators are bf16 hi/lo blocks
+  int sweep_arith = HPS_SWEEP_DEFAULT;
+  bool sweep_bf16x3 = false;
   bool fg_df = false;
   float4 *df_V = nullptr, *df_x = nullptr, *df_w = nullptr, *df_rhs = nullptr, *df_part = nullptr, *df_T = nullptr;
   float4* df_coef = nullptr;       // Gram-Schmidt update coefficients [2 restart + 3][nrhs]

@@ -113,7 +113,7 @@ cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, con
   a.ws_elems = (long long)c->gemm_ws_elems;
   a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
   a.err = c->d_gemm_err;
-  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, a.err, c->stream);
+  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, c->sweep_bf16x3, a.err, c->stream);
 }
 
 bool level_tiled(const Level& Lv) { return 2 * Lv.m >= 64; }
@@ -415,10 +415,11 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
       Lv.Ut = dev_alloc(c, sizeof(float2) * bu);
       Lv.Dmt = dev_alloc(c, sizeof(float2) * bd);
       if (!Lv.Ut || !Lv.Dmt) return fail(c, HPS_ENOMEM, "tiled sweep operators");
-      HPS_CK(c, tile_operator(static_cast<float2*>(Lv.Ut), static_cast<const float2*>(Lv.U), NP, 2 * p, 2 * m, 2 * m,
-                              (long long)2 * p * 2 * m, c->stream));
-      HPS_CK(c, tile_operator(static_cast<float2*>(Lv.Dmt), static_cast<const float2*>(Lv.Dm), NP, 2 * m, 2 * n,
-                              2 * n, (long long)2 * m * 2 * n, c->stream));
+      auto tile = c->sweep_bf16x3 ? tile_operator_bf16x3 : tile_operator;
+      HPS_CK(c, tile(static_cast<float2*>(Lv.Ut), static_cast<const float2*>(Lv.U), NP, 2 * p, 2 * m, 2 * m,
+                     (long long)2 * p * 2 * m, c->stream));
+      HPS_CK(c, tile(static_cast<float2*>(Lv.Dmt), static_cast<const float2*>(Lv.Dm), NP, 2 * m, 2 * n, 2 * n,
+                     (long long)2 * m * 2 * n, c->stream));
       dev_free(c, Lv.U);
       dev_free(c, Lv.Dm);
       Lv.U = Lv.Dm = nullptr;
@@ -545,6 +546,8 @@ int build_tree(hps_ctx* c, int L_exact, int exact_coarse) {
   if (c->plan_L == L_exact) free_numeric(c);  // same mesh and depth: keep the plan
   else free_tree(c);
   PhaseScope ps(c, HPS_PH_MERGE);
+  // the format of this tree's tiled sweep operators (FP32 tree only)
+  c->sweep_bf16x3 = c->precision != HPS_FP64 && c->sweep_arith != HPS_SWEEP_FP32;
   int rc = c->precision == HPS_FP64 ? build_tree_t<double>(c, L_exact, exact_coarse)
                                     : build_tree_t<float>(c, L_exact, exact_coarse);
   if (rc != HPS_OK) {

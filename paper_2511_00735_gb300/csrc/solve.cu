@@ -261,6 +261,14 @@ int hps_set_outer_arith(hps_ctx* c, int mode) {
   return HPS_OK;
 }
 
+int hps_set_sweep_arith(hps_ctx* c, int mode) {
+  if (!c) return HPS_EINVAL;
+  if (mode != HPS_SWEEP_DEFAULT && mode != HPS_SWEEP_FP32 && mode != HPS_SWEEP_BF16X3)
+    return fail(c, HPS_EINVAL, "sweep arithmetic: HPS_SWEEP_DEFAULT, HPS_SWEEP_FP32 or HPS_SWEEP_BF16X3");
+  c->sweep_arith = mode;
+  return HPS_OK;
+}
+
 int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double tol, int inner_iters, int restart,
                     int max_outer, void* g_out, hps_info* info) {
   CHECK_CTX(c);

@@ -22,6 +22,8 @@
 // i.e. output rows) and applies the same descriptor epilogue as the SIMT GEMM
 // (alpha, beta * C0 with a two-segment C0, row and column maps).  Every mbarrier wait is
 // bounded; a wait that gives up sets *err and the tile is left unwritten.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "common.cuh"
@@ -511,6 +513,396 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TT::TCOLS) : "memory");
 }
 
+// Sweep products with the operator stored pre-split in bf16 ("bf16x3").
+//
+// The sweep operators U and Dm are formed once per tree and then only multiplied, so they are
+// stored, block by block (128 rows x 8 complex k), as the bf16 tile hi = bf16(x) followed by the
+// bf16 tile lo = bf16(x - hi) in the 16-bit K-major no-swizzle layout (8-row x 16-byte core
+// matrices): one bulk copy brings a k chunk of A into shared memory exactly as the MMA reads it,
+// and no thread touches A.  The block vector B is split the same way in the kernel (and
+// real-expanded as in the FP32 kernels); the product accumulates hi*hi + hi*lo + lo*hi with
+// kind::f16 MMAs (bf16 inputs, FP32 accumulator in tensor memory).  hi + lo represents x to
+// 2^-16 relative and the dropped lo*lo term is below 2^-16, so each product carries a relative
+// error of about 3 * 2^-16 against the FP32 product.
+//
+// Persistent and warp-specialised, 256 threads, two CTAs per SM:
+//   warp 0      producer: per k chunk one cp.async.bulk of the A block (completing on the
+//               stage's full barrier with its byte count) and cp.async of the raw B chunk
+//               (cp.async.mbarrier.arrive on the same barrier), TCB_S stages ahead;
+//   warp 1      one thread issues the chunk's three MMAs once its B tiles are split, commits
+//               them to the stage's empty barrier (the producer then refills the stage) and a
+//               tile's last chunk to its accumulator's full barrier; two accumulators in tensor
+//               memory alternate by tile, so a tile's epilogue overlaps the next tile's MMAs;
+//   warps 2-3   split the raw B chunk into the stage's bf16 hi/lo B' tiles;
+//   warps 4-7   epilogue (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. output
+//               rows), C0 prefetched before the accumulator is ready; then release it.
+// Every wait is bounded; a wait that gives up (or that starts after another role gave up) ends
+// the role's loops, *err is set, and the copies and MMAs in flight are waited for before the
+// tensor memory is released.
+constexpr int TCB_S = 6;     // stages
+constexpr int TCB_NT = 256;  // 8 warps
+
+template <int NC> struct TcbTile {
+  static constexpr int NR = 2 * NC;                      // real output columns
+  static constexpr int A_BYTES = TC_M * TC_KR * 2 * 2;    // bf16 hi + lo tiles of one block (8 KB)
+  static constexpr int BRAW = TC_KC * NC * 8;             // raw complex B chunk
+  static constexpr int BT = NR * TC_KR * 2;               // one bf16 B' tile
+  static constexpr int STAGE = A_BYTES + BRAW + 2 * BT;   // a multiple of 1024
+  static constexpr int TCOLS = 2 * NR < 32 ? 32 : 2 * NR; // two accumulators
+  // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+  static constexpr size_t SMEM = (size_t)TCB_S * STAGE + 1024;
+};
+static_assert(TcbTile<16>::STAGE % 1024 == 0 && TcbTile<32>::STAGE % 1024 == 0, "stage alignment");
+static_assert(TcbTile<16>::A_BYTES == TC_M * TC_KC * 8, "a bf16x3 block occupies one FP32 block");
+
+constexpr uint32_t LBO16 = 128;  // 16-bit tiles: bytes between core matrices along k
+constexpr uint32_t SBO16 = 256;  // and between 8-row groups (16 real k = two core matrices)
+
+// byte offset of the 16-bit element (r, k) of a tile
+__device__ __forceinline__ uint32_t core_off16(int r, int k) {
+  return (uint32_t)(r >> 3) * SBO16 + (uint32_t)(k >> 3) * LBO16 + (uint32_t)(r & 7) * 16 + (uint32_t)(k & 7) * 2;
+}
+__device__ __forceinline__ uint64_t smem_desc16(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(LBO16 >> 4) << 16) | ((uint64_t)(SBO16 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void split_bf16(float x, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  hi = __bfloat16_as_ushort(h);
+  lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));  // x - h is exact in FP32
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
+  asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                   tmem),
+               "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(b)) : "memory");
+}
+// arrive on b once every cp.async this thread issued so far has landed (the arrival is counted in
+// the barrier's initial count)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// 8-byte asynchronous copy that reads nbytes (0 or 8) from src and zero-fills the rest, so that
+// padding reaches shared memory through the same completion mechanism as the data
+__device__ __forceinline__ void cp_async8z(uint32_t dst, const void* src, uint32_t nbytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
+}
+// one arrival with the expected byte count, then a bulk copy that completes those bytes on b
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+// tile t of a persistent launch: row tile, column tile, batch entry and k split
+struct TileInfo {
+  int bb, sp, rt, ct, m, n, kb, kk, nk;
+  bool live;
+};
+__device__ __forceinline__ TileInfo tile_info(const GemmArgs<float>& a, int NC, int t, int gx, int gy, int ksplit,
+                                              int kc) {
+  TileInfo ti;
+  const int z = t / (gx * gy), rem = t % (gx * gy);
+  ti.rt = rem / gx;
+  ti.ct = rem % gx;
+  ti.bb = z % a.nbatch;
+  ti.sp = z / a.nbatch;
+  const GemmDesc& d = a.desc[ti.bb];
+  ti.n = d.n < 0 ? a.n_launch : d.n;
+  ti.m = d.m;
+  ti.kb = ksplit > 1 ? ti.sp * kc : 0;
+  ti.kk = ksplit > 1 ? min(d.k, ti.kb + kc) : d.k;
+  ti.nk = ti.kk > ti.kb ? (ti.kk - ti.kb + TC_KC - 1) / TC_KC : 0;
+  ti.live = ti.rt * TC_M < ti.m && ti.ct * NC < ti.n;
+  return ti;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, int* err, int ksplit, int kc,
+                                                             int mmax, int nmax, int gx, int gy, int ntiles) {
+  using TB = TcbTile<NC>;
+  constexpr int NR = TB::NR, STAGE = TB::STAGE, A_BYTES = TB::A_BYTES, BRAW = TB::BRAW, BT = TB::BT;
+  constexpr int G = NR / 16;  // 16-column groups of an accumulator
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[TCB_S], conv[TCB_S], empty[TCB_S], accf[2], acce[2], fin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail_store;
+  volatile int& s_fail = s_fail_store;
+  unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  if (tid == 0) {
+    s_fail = 0;
+    for (int i = 0; i < TCB_S; ++i) {
+      mbar_init(&full[i], 33);  // the 32 producer lanes' cp.async arrivals + the bulk copy's expect_tx arrival
+      mbar_init(&conv[i], 2);   // the two B-splitting warps
+      mbar_init(&empty[i], 1);  // tcgen05.commit of the chunk's MMAs
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);  // tcgen05.commit of a tile's last chunk
+      mbar_init(&acce[i], 4);  // the four epilogue warps
+    }
+    mbar_init(&fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "n"(TB::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  // bounded wait with a warp-uniform result (the warps' tcgen05.ld are warp-collective)
+  auto wait = [&](uint64_t* b, uint32_t parity) -> bool {
+    bool ok = !s_fail && mbar_wait(smem_u32(b), parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) s_fail = 1;
+    return ok;
+  };
+  auto wait1 = [&](uint64_t* b, uint32_t parity) -> bool {  // single-thread role
+    if (!s_fail && mbar_wait(smem_u32(b), parity)) return true;
+    s_fail = 1;
+    return false;
+  };
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    long long g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
+      if (!ti.live) continue;
+      const GemmDesc d = a.desc[ti.bb];
+      const float2* Ab = a.A + ((long long)d.a_r + (long long)ti.rt * d.a_c + ti.kb / TC_KC) * (TC_M * TC_KC);
+      const int col0 = ti.ct * NC;
+      for (int kt = 0; kt < ti.nk; ++kt, ++g) {
+        const int st = (int)(g % TCB_S);
+        if (g >= TCB_S && !wait(&empty[st], (uint32_t)(((g / TCB_S) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        unsigned char* sp = ring + (size_t)st * STAGE;
+        if (lane == 0) bulk_load(smem_u32(sp), Ab + (long long)kt * (TC_M * TC_KC), A_BYTES, &full[st]);
+        const uint32_t rb = smem_u32(sp + A_BYTES);
+        const int k0 = ti.kb + kt * TC_KC;
+        for (int l = lane; l < TC_KC * NC; l += 32) {
+          const int kc2 = l / NC, nc = l % NC;
+          const int gk = k0 + kc2, gj = col0 + nc;
+          if (gk < ti.kk && gj < ti.n) {
+            const long long br =
+                (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+            cp_async8z(rb + l * 8, a.B + br * a.ldb + d.b_c + gj, 8u);
+          } else {
+            cp_async8z(rb + l * 8, a.B, 0u);  // zero fill, nothing read
+          }
+        }
+        cp_async_arrive(&full[st]);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // no bulk copy may still be landing when the CTA ends: the last chunk of each stage has
+    // completed its full barrier (at once unless a role gave up before consuming it)
+    if (lane == 0)
+      for (long long gg = g - TCB_S > 0 ? g - TCB_S : 0; gg < g; ++gg)
+        mbar_wait(smem_u32(&full[gg % TCB_S]), (uint32_t)((gg / TCB_S) & 1));
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long g = 0;
+      int tc = 0;  // tiles with a k range so far (they alternate between the accumulators)
+      bool ok = true, issued = false;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
+        if (!ti.live || ti.nk == 0) continue;
+        const int buf = tc & 1;
+        if (tc >= 2 && !wait1(&acce[buf], (uint32_t)(((tc >> 1) - 1) & 1))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(buf * NR);
+        for (int kt = 0; kt < ti.nk; ++kt, ++g) {
+          const int st = (int)(g % TCB_S);
+          const uint32_t par = (uint32_t)((g / TCB_S) & 1);
+          if (!wait1(&full[st], par) || !wait1(&conv[st], par)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(ring + (size_t)st * STAGE), sb = sa + A_BYTES + BRAW;
+          const uint64_t ah = smem_desc16(sa), al = smem_desc16(sa + A_BYTES / 2);
+          const uint64_t bh = smem_desc16(sb), bl = smem_desc16(sb + BT);
+          mma_bf16(acc, ah, bh, TB::IDESC, kt > 0 ? 1u : 0u);
+          mma_bf16(acc, ah, bl, TB::IDESC, 1u);
+          mma_bf16(acc, al, bh, TB::IDESC, 1u);
+          tc_commit(&empty[st]);
+          issued = true;
+        }
+        if (!ok) break;
+        tc_commit(&accf[buf]);
+        ++tc;
+      }
+      // every MMA issued by this thread has completed before the tensor memory is released
+      if (issued) {
+        tc_commit(&fin);
+        mbar_wait(smem_u32(&fin), 0);
+      }
+    }
+  } else if (warp <= 3) {
+    // ---------------- B splitters ----------------
+    const int ct = tid - 64;
+    long long g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
+      if (!ti.live) continue;
+      for (int kt = 0; kt < ti.nk; ++kt, ++g) {
+        const int st = (int)(g % TCB_S);
+        if (!wait(&full[st], (uint32_t)((g / TCB_S) & 1))) {
+          ok = false;
+          break;
+        }
+        unsigned char* sp = ring + (size_t)st * STAGE;
+        const float2* raw = reinterpret_cast<const float2*>(sp + A_BYTES);
+        unsigned char* bh = sp + A_BYTES + BRAW;
+        unsigned char* bl = bh + BT;
+        // complex (kc, nc) -> B'^T row 2nc: (Re b, -Im b), row 2nc+1: (Im b, Re b) at real k 2kc, 2kc+1
+        for (int l = ct; l < TC_KC * NC; l += 64) {
+          const int kc2 = l / NC, nc = l % NC;
+          const float2 v = raw[l];
+          uint32_t rh, rl, ih, il;
+          split_bf16(v.x, rh, rl);
+          split_bf16(v.y, ih, il);
+          const uint32_t nh = ih ^ 0x8000u, nl = il ^ 0x8000u;  // bf16 split of -Im b
+          const uint32_t o0 = core_off16(2 * nc, 2 * kc2), o1 = core_off16(2 * nc + 1, 2 * kc2);
+          *reinterpret_cast<uint32_t*>(bh + o0) = rh | (nh << 16);
+          *reinterpret_cast<uint32_t*>(bl + o0) = rl | (nl << 16);
+          *reinterpret_cast<uint32_t*>(bh + o1) = ih | (rh << 16);
+          *reinterpret_cast<uint32_t*>(bl + o1) = il | (rl << 16);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[st]);
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int quarter = warp & 3;
+    int tc = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
+      if (!ti.live) continue;
+      const GemmDesc d = a.desc[ti.bb];
+      const int row0 = ti.rt * TC_M, col0 = ti.ct * NC;
+      const int row = 32 * quarter + lane, gi = row0 + row;
+      const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
+      const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
+      const long long orow = gi < ti.m ? (long long)d.c_r + (rmap ? rmap[gi] : gi) : 0;
+      const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+      float2* W = ksplit > 1 ? a.ws + (((long long)ti.sp * a.nbatch + ti.bb) * mmax) * nmax : nullptr;
+      // beta * C0 of this row, loaded while the tile's MMAs run
+      float2 c0v[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int gj = col0 + j;
+        c0v[j] = (!W && a.C0 && gi < ti.m && gj < ti.n) ? cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj])
+                                                        : make_float2(0.f, 0.f);
+      }
+      const int buf = tc & 1;
+      if (ti.nk > 0) {
+        if (!wait(&accf[buf], (uint32_t)((tc >> 1) & 1))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+#pragma unroll
+      for (int gq = 0; gq < G; ++gq) {
+        uint32_t v[16];
+        if (ti.nk > 0) {
+          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(buf * NR + gq * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0u;
+        }
+        if (gi < ti.m) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int jc = gq * 8 + j, gj = col0 + jc;
+            if (gj >= ti.n) continue;
+            const float2 acc = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+            if (W) {
+              W[(long long)gi * nmax + gj] = acc;
+              continue;
+            }
+            a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = cadd(cmul(a.alpha, acc), c0v[jc]);
+          }
+        }
+      }
+      if (ti.nk > 0) {
+        // the accumulator is read: the MMAs of the tile after next may overwrite it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[buf]);
+        ++tc;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && s_fail) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TB::TCOLS) : "memory");
+}
+
+template <int NC>
+cudaError_t launch_tcb(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+  const int gx = (nmax + NC - 1) / NC, gy = (mmax + TC_M - 1) / TC_M;
+  const long long tiles = (long long)gx * gy * a.nbatch;
+  // persistent CTAs, two per SM; split K while there are fewer tiles than CTAs
+  const long long slots = 2LL * a.num_sms;
+  int ksplit = 1;
+  if (kmax >= 8 * TC_KC && a.ws && tiles < slots) {
+    ksplit = (int)((slots + tiles - 1) / tiles);
+    ksplit = ksplit < kmax / (4 * TC_KC) ? ksplit : kmax / (4 * TC_KC);
+    ksplit = ksplit < 16 ? ksplit : 16;
+    while (ksplit > 1 && (long long)ksplit * a.nbatch * mmax * nmax > a.ws_elems) --ksplit;
+  }
+  int kc = kmax;
+  if (ksplit > 1) {
+    kc = (kmax + ksplit - 1) / ksplit;
+    kc = (kc + TC_KC - 1) / TC_KC * TC_KC;
+    ksplit = (kmax + kc - 1) / kc;
+  }
+  const long long ntiles = tiles * ksplit;
+  if (ntiles == 0) return cudaSuccess;
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int grid = (int)(ntiles < slots ? ntiles : slots);
+  tcb_gemm_kernel<NC><<<grid, TCB_NT, TcbTile<NC>::SMEM, s>>>(a, err, ksplit, kc, mmax, nmax, gx, gy, (int)ntiles);
+  note_launch();
+  if (ksplit > 1) return splitk_reduce(a, ksplit, mmax, nmax, s);
+  return cudaGetLastError();
+}
+
 template <int NC>
 constexpr size_t tc_gemm_smem() { return (size_t)2 * TcTile<NC>::STAGE * sizeof(float) + 1024; }
 
@@ -555,8 +947,13 @@ cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kma
   return launch_tc<64, false>(a, mmax, nmax, kmax, err, s);
 }
 
-cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
+                                 cudaStream_t s) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
+  if (bf16x3) {  // more than 32 columns: 32-column tiles side by side
+    if (nmax <= 16) return launch_tcb<16>(a, mmax, nmax, kmax, err, s);
+    return launch_tcb<32>(a, mmax, nmax, kmax, err, s);
+  }
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
   if (nmax <= 16) return launch_tc<16, true>(a, mmax, nmax, kmax, err, s);
   if (nmax <= 32) return launch_tc<32, true>(a, mmax, nmax, kmax, err, s);
@@ -583,6 +980,30 @@ __global__ void tile_operator_kernel(float2* __restrict__ TL, const float2* __re
   }
 }
 
+// The same blocks pre-split for the bf16x3 sweep kernel: block = [hi tile | lo tile], each 128
+// rows x 16 real k of bf16 in the 16-bit core-matrix order (one 32-bit word = the (Re, Im) pair
+// of one complex entry).  Thread l writes word l % 1024 of both tiles of block l / 1024.
+__global__ void tile_operator_bf16x3_kernel(uint32_t* __restrict__ TL, const float2* __restrict__ A, int npairs,
+                                            int rows, int K, int lda, long long pair_stride, int nrt, int nkt) {
+  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    const long long blk = l / (TC_M * TC_KC);
+    const int u = (int)(l % (TC_M * TC_KC));  // word inside one tile
+    const int kt = (int)(blk % nkt), rt = (int)((blk / nkt) % nrt), P = (int)(blk / ((long long)nkt * nrt));
+    // invert core_off16(r, 2 kc) / 4: row group r/8 (SBO16 = 256 B = 64 words), k group
+    // (2 kc)/8 (LBO16 = 128 B = 32 words), row r%8 (4 words), pair kc%4
+    const int rg = u / 64, kg = (u % 64) / 32, w = u % 32;
+    const int r = rg * 8 + w / 4, kc = kg * 4 + w % 4;
+    const int gi = rt * TC_M + r, gk = kt * TC_KC + kc;
+    const float2 x = (gi < rows && gk < K) ? A[(long long)P * pair_stride + (long long)gi * lda + gk] : make_float2(0.f, 0.f);
+    uint32_t rh, rl, ih, il;
+    split_bf16(x.x, rh, rl);
+    split_bf16(x.y, ih, il);
+    TL[blk * (2 * TC_M * TC_KC) + u] = rh | (ih << 16);
+    TL[blk * (2 * TC_M * TC_KC) + TC_M * TC_KC + u] = rl | (il << 16);
+  }
+}
+
 cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int K, int lda, long long pair_stride,
                           cudaStream_t s) {
   const int nrt = (rows + TC_M - 1) / TC_M, nkt = (K + TC_KC - 1) / TC_KC;
@@ -595,10 +1016,25 @@ cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int
   return cudaGetLastError();
 }
 
+cudaError_t tile_operator_bf16x3(float2* TL, const float2* A, int npairs, int rows, int K, int lda,
+                                 long long pair_stride, cudaStream_t s) {
+  const int nrt = (rows + TC_M - 1) / TC_M, nkt = (K + TC_KC - 1) / TC_KC;
+  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  if (blocks < 1) return cudaSuccess;
+  tile_operator_bf16x3_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<uint32_t*>(TL), A, npairs, rows, K, lda,
+                                                         pair_stride, nrt, nkt);
+  note_launch();
+  return cudaGetLastError();
+}
+
 void optin_tc() {
   smem_optin(tc_gemm_kernel<16>);
   smem_optin(tc_gemm_kernel<32>);
   smem_optin(tc_gemm_kernel<64>);
+  smem_optin(tcb_gemm_kernel<16>);
+  smem_optin(tcb_gemm_kernel<32>);
   smem_optin(tcs_gemm_kernel<16>);
   smem_optin(tcs_gemm_kernel<32>);
   smem_optin(tcs_gemm_kernel<64>);

@@ -23,6 +23,9 @@ HPS_MIXED = 1
 OUTER_DEFAULT = -1  # outer FGMRES arithmetic (hps_set_outer_arith)
 OUTER_FP64 = 0
 OUTER_DF64 = 1
+SWEEP_DEFAULT = -1  # sweep-product arithmetic of an HPS_MIXED tree (hps_set_sweep_arith)
+SWEEP_FP32 = 0
+SWEEP_BF16X3 = 1
 
 _STATUS = {0: "HPS_OK", -1: "HPS_EINVAL", -2: "HPS_ENOMEM", -3: "HPS_ENOTBUILT", -4: "HPS_ENOTCONV",
            -5: "HPS_ETIMEOUT", -6: "HPS_ECUDA", -7: "HPS_ENODEV", -8: "HPS_EUNSUPPORTED", -9: "HPS_ENUMERIC"}
@@ -33,7 +36,7 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
            "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace",
-           "hps_set_outer_arith", "hps_set_gamma", "hps_volume_solution"]
+           "hps_set_outer_arith", "hps_set_gamma", "hps_volume_solution", "hps_set_sweep_arith"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -93,6 +96,7 @@ def load_library(path: str = LIB_PATH):
         "hps_release_workspace": (i, [vp]),
         "hps_set_outer_arith": (i, [vp, i]),
         "hps_set_gamma": (i, [vp, i]),
+        "hps_set_sweep_arith": (i, [vp, i]),
         "hps_volume_solution": (i, [vp, vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
@@ -203,6 +207,11 @@ class Solver:
     def set_outer_arith(self, mode: int):
         """Outer FGMRES arithmetic: OUTER_FP64, OUTER_DF64 (mixed leaves only) or OUTER_DEFAULT."""
         self._check(self.lib.hps_set_outer_arith(self.h, mode))
+
+    def set_sweep_arith(self, mode: int):
+        """Sweep-product arithmetic of HPS_MIXED trees built after this call: SWEEP_FP32,
+        SWEEP_BF16X3 or SWEEP_DEFAULT (bf16x3)."""
+        self._check(self.lib.hps_set_sweep_arith(self.h, mode))
 
     def set_gamma(self, gamma: int):
         """Coarse calls per level of the preconditioner: 1 = V-cycle, gamma > 1 = gamma-cycle."""
