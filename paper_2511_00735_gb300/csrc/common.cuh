@@ -136,8 +136,8 @@ template <typename R> struct GemmArgs {
 // FP32 complex GEMM on the tensor cores (tc.cu): batched like launch_gemm, for tiles of
 // 128 rows x 64 complex columns; *err is set when a bounded wait gives up.
 cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s);
-// The same product with A stored tiled by tile_operator (descriptor a_r = the pair's first block,
-// a_c = blocks per row tile of 128 rows; lda unused); bf16x3: A tiled by tile_operator_bf16x3
+// The same product with A stored tiled by tile_operator (descriptor a_r = the pair's first unit
+// of the tiled layout, a_c = its k chunks; lda unused); bf16x3: A tiled by tile_operator_bf16x3
 // and multiplied as hi*hi + hi*lo + lo*hi of bf16 splits (about 3 * 2^-16 relative error).
 cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
                                  cudaStream_t s);
@@ -151,6 +151,25 @@ cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int
 cudaError_t tile_operator_bf16x3(float2* TL, const float2* A, int npairs, int rows, int K, int lda,
                                  long long pair_stride, cudaStream_t s);
 constexpr int TILE_M = 128, TILE_K = 8;  // rows and complex k of one operator block
+// Tiled operator layout (tile_operator, tile_operator_bf16x3): per pair, row tile rt and k
+// chunk kt make one block of 128 rows x 8 complex k in the tensor-core order, blocks ordered
+// (rt, kt); the blocks of the last row tile keep only its rows rounded up to 8 (a compact block
+// is the prefix of a full one).  Offsets count 512-byte units (8 rows x 8 complex k).
+constexpr int TILE_UNIT = 64;  // float2 per unit
+__host__ __device__ inline int tiled_row_tiles(int rows) { return (rows + TILE_M - 1) / TILE_M; }
+__host__ __device__ inline int tiled_last_rows(int rows) {
+  return (rows - TILE_M * (tiled_row_tiles(rows) - 1) + 7) / 8 * 8;
+}
+__host__ __device__ inline long long tiled_pair_units(int rows, int K) {
+  const int nkt = (K + TILE_K - 1) / TILE_K;
+  return (long long)nkt * ((tiled_row_tiles(rows) - 1) * (TILE_M / 8) + tiled_last_rows(rows) / 8);
+}
+// unit offset, inside its pair, of block (rt, kt) of an operator with `rows` rows and nkt k
+// chunks; rows_blk = the rows the block stores
+__host__ __device__ inline long long tiled_block_unit(int rows, int nkt, int rt, int kt, int& rows_blk) {
+  rows_blk = rt < tiled_row_tiles(rows) - 1 ? TILE_M : tiled_last_rows(rows);
+  return (long long)rt * nkt * (TILE_M / 8) + (long long)kt * (rows_blk / 8);
+}
 // Fixed-order sum of ksplit partial tiles from a.ws with the descriptor epilogue (blas.cu).
 cudaError_t splitk_reduce(const GemmArgs<float>& a, int ksplit, int mmax, int nmax, cudaStream_t s);
 void optin_tc();

@@ -116,7 +116,10 @@ cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, con
   return launch_tc_gemm_tiled(a, mmax, nmax, kmax, c->sweep_bf16x3, a.err, c->stream);
 }
 
-bool level_tiled(const Level& Lv) { return 2 * Lv.m >= 64; }
+// sweep operators kept tiled for the tensor cores (FP32 tree): every level with bf16x3 sweeps;
+// with FP32 sweeps the levels with at least 32 interface rows per child (the small levels stay
+// on the SIMT products)
+bool level_tiled(const hps_ctx* c, const Level& Lv) { return c->sweep_bf16x3 || 2 * Lv.m >= 64; }
 
 GemmDesc D(int a_r, int a_c, int b_r, int b_c, int c0_r, int c0_c, int c_r, int c_c, int m, int n, int k, int rmap = -1,
            int cmap = -1) {
@@ -297,17 +300,18 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     Lv.d_mdesc = dev_upload(c, md);
     Lv.d_sdesc = dev_upload(c, sd);
     if (!Lv.d_mdesc || !Lv.d_sdesc) return fail(c, HPS_ENOMEM, "descriptors");
-    if (level_tiled(Lv)) {
-      // the same sweep products on the tiled operators: a_r = the pair's first block, a_c =
-      // blocks per row tile
-      const int nrt_u = (2 * p + TILE_M - 1) / TILE_M, nkt_u = (2 * m + TILE_K - 1) / TILE_K;
-      const int nrt_d = (2 * m + TILE_M - 1) / TILE_M, nkt_d = (2 * n + TILE_K - 1) / TILE_K;
+    {
+      // the same sweep products on the tiled operators (every level: whether a level is tiled
+      // depends on the sweep arithmetic of each tree): a_r = the pair's first 512-byte unit,
+      // a_c = its k chunks
+      const long long pu = tiled_pair_units(2 * p, 2 * m), pd = tiled_pair_units(2 * m, 2 * n);
+      if ((long long)NP * std::max(pu, pd) > 0x7fffffffLL) return fail(c, HPS_EUNSUPPORTED, "tiled operator size");
       std::vector<GemmDesc> td(sd);
       for (int P = 0; P < NP; ++P) {
-        td[SUP * NP + P].a_r = P * nrt_u * nkt_u;
-        td[SUP * NP + P].a_c = nkt_u;
-        td[SDN * NP + P].a_r = P * nrt_d * nkt_d;
-        td[SDN * NP + P].a_c = nkt_d;
+        td[SUP * NP + P].a_r = (int)(P * pu);
+        td[SUP * NP + P].a_c = (2 * m + TILE_K - 1) / TILE_K;
+        td[SDN * NP + P].a_r = (int)(P * pd);
+        td[SDN * NP + P].a_c = (2 * n + TILE_K - 1) / TILE_K;
       }
       Lv.d_tsdesc = dev_upload(c, td);
       if (!Lv.d_tsdesc) return fail(c, HPS_ENOMEM, "descriptors");
@@ -408,10 +412,10 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
     HPS_CK(c, gemm<R>(c, md + PD3 * NP, NP, nullptr, 0, nullptr, 0, G, 2 * m, Lv.Dm, 2 * n, 1.0, nullptr, 2 * m, m, m));
     HPS_CK(c, gemm<R>(c, md + PD2 * NP, NP, G, 2 * m, T0, n, nullptr, 0, Lv.Dm, 2 * n, -1.0, nullptr, 2 * m, p, p, m));
     HPS_CK(c, gemm<R>(c, md + PD4 * NP, NP, G, 2 * m, T0, n, nullptr, 0, Lv.Dm, 2 * n, -1.0, nullptr, 2 * m, p, p, m));
-    if (sizeof(R) == 4 && level_tiled(Lv)) {
+    if (sizeof(R) == 4 && level_tiled(c, Lv)) {
       // the sweeps stream U and Dm block by block: keep them tiled, drop the row-major copies
-      const size_t bu = (size_t)NP * ((2 * p + TILE_M - 1) / TILE_M) * ((2 * m + TILE_K - 1) / TILE_K) * TILE_M * TILE_K;
-      const size_t bd = (size_t)NP * ((2 * m + TILE_M - 1) / TILE_M) * ((2 * n + TILE_K - 1) / TILE_K) * TILE_M * TILE_K;
+      const size_t bu = (size_t)NP * tiled_pair_units(2 * p, 2 * m) * TILE_UNIT;
+      const size_t bd = (size_t)NP * tiled_pair_units(2 * m, 2 * n) * TILE_UNIT;
       Lv.Ut = dev_alloc(c, sizeof(float2) * bu);
       Lv.Dmt = dev_alloc(c, sizeof(float2) * bd);
       if (!Lv.Ut || !Lv.Dmt) return fail(c, HPS_ENOMEM, "tiled sweep operators");

@@ -367,8 +367,10 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
                                                        : make_float2(0.f, 0.f);
   }
 
-  // this CTA's blocks: row tile blockIdx.y of its pair, chunks from kb / TC_KC on
-  const float2* Ab = a.A + ((long long)d.a_r + (long long)blockIdx.y * d.a_c + kb / TC_KC) * (TC_M * TC_KC);
+  // this CTA's blocks: row tile blockIdx.y of its pair, chunks from kb / TC_KC on, rows_blk rows each
+  int rows_blk;
+  const float2* Ab =
+      a.A + ((long long)d.a_r + tiled_block_unit(m, d.a_c, blockIdx.y, kb / TC_KC, rows_blk)) * TILE_UNIT;
   const int nk = kk > kb ? (kk - kb + TC_KC - 1) / TC_KC : 0;
   const uint32_t ring_s = smem_u32(ring);
   // chunk kt (if any) into raw stage kt % TCP_S; always one commit group per call
@@ -377,11 +379,11 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
       const int k0 = kb + kt * TC_KC;
       const uint32_t ra = ring_s + (uint32_t)((kt % TCP_S) * TP::RAW);
       unsigned char* rap = ring + (size_t)(kt % TCP_S) * TP::RAW;
-      const char* src = reinterpret_cast<const char*>(Ab + (long long)kt * (TC_M * TC_KC));
+      const char* src = reinterpret_cast<const char*>(Ab + (long long)kt * rows_blk * TC_KC);
 #pragma unroll
       for (int i = 0; i < TCP_ARAW / (16 * TCS_NT); ++i) {
         const int o = (tid + i * TCS_NT) * 16;
-        cp_async16(ra + o, src + o);
+        if (o < rows_blk * TC_KC * 8) cp_async16(ra + o, src + o);  // rows past a compact block: unused
       }
       for (int l = tid; l < TC_KC * NC; l += TCS_NT) {
         const int kc2 = l / NC, nc = l % NC;
@@ -528,21 +530,24 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
 // Persistent and warp-specialised, 256 threads, two CTAs per SM:
 //   warp 0      producer: per k chunk one cp.async.bulk of the A block (completing on the
 //               stage's full barrier with its byte count) and cp.async of the raw B chunk
-//               (cp.async.mbarrier.arrive on the same barrier), TCB_S stages ahead;
+//               (cp.async.mbarrier.arrive on the same barrier; one more bulk copy when the
+//               chunk is contiguous), up to S stages ahead;
 //   warp 1      one thread issues the chunk's three MMAs once its B tiles are split, commits
 //               them to the stage's empty barrier (the producer then refills the stage) and a
 //               tile's last chunk to its accumulator's full barrier; two accumulators in tensor
 //               memory alternate by tile, so a tile's epilogue overlaps the next tile's MMAs;
 //   warps 2-3   split the raw B chunk into the stage's bf16 hi/lo B' tiles;
-//   warps 4-7   epilogue (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. output
-//               rows), C0 prefetched before the accumulator is ready; then release it.
+//   warps 4-7   epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its 32 output
+//               rows), releases the accumulator and writes the rows through a shared-memory
+//               transpose, so that C0 loads and C stores run along rows (coalesced); its C0
+//               values are loaded before the accumulator is ready.
 // Every wait is bounded; a wait that gives up (or that starts after another role gave up) ends
 // the role's loops, *err is set, and the copies and MMAs in flight are waited for before the
 // tensor memory is released.
-constexpr int TCB_S = 6;     // stages
 constexpr int TCB_NT = 256;  // 8 warps
 
 template <int NC> struct TcbTile {
+  static constexpr int S = NC <= 16 ? 6 : 5;             // stages
   static constexpr int NR = 2 * NC;                      // real output columns
   static constexpr int A_BYTES = TC_M * TC_KR * 2 * 2;    // bf16 hi + lo tiles of one block (8 KB)
   static constexpr int BRAW = TC_KC * NC * 8;             // raw complex B chunk
@@ -552,7 +557,9 @@ template <int NC> struct TcbTile {
   // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-  static constexpr size_t SMEM = (size_t)TCB_S * STAGE + 1024;
+  static constexpr int EPI_LD = NC + 1;                   // epilogue staging row (padded), complex
+  static constexpr int EPI = 4 * 32 * EPI_LD * 8;         // staging of the four epilogue warps
+  static constexpr size_t SMEM = (size_t)S * STAGE + EPI + 1024;
 };
 static_assert(TcbTile<16>::STAGE % 1024 == 0 && TcbTile<32>::STAGE % 1024 == 0, "stage alignment");
 static_assert(TcbTile<16>::A_BYTES == TC_M * TC_KC * 8, "a bf16x3 block occupies one FP32 block");
@@ -595,9 +602,12 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
 __device__ __forceinline__ void cp_async8z(uint32_t dst, const void* src, uint32_t nbytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
 }
-// one arrival with the expected byte count, then a bulk copy that completes those bytes on b
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* b) {
+// one arrival on b that also expects `bytes` of bulk copies to complete on it
+__device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16) completing on b
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* b) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(smem_u32(b))
                : "memory");
@@ -635,6 +645,7 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
                                                              int mmax, int nmax, int gx, int gy, int ntiles) {
   using TB = TcbTile<NC>;
   constexpr int NR = TB::NR, STAGE = TB::STAGE, A_BYTES = TB::A_BYTES, BRAW = TB::BRAW, BT = TB::BT;
+  constexpr int TCB_S = TB::S;
   constexpr int G = NR / 16;  // 16-column groups of an accumulator
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[TCB_S], conv[TCB_S], empty[TCB_S], accf[2], acce[2], fin;
@@ -646,7 +657,7 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
   if (tid == 0) {
     s_fail = 0;
     for (int i = 0; i < TCB_S; ++i) {
-      mbar_init(&full[i], 33);  // the 32 producer lanes' cp.async arrivals + the bulk copy's expect_tx arrival
+      mbar_init(&full[i], 33);  // the 32 producer lanes' cp.async arrivals + the bulk copies' expect_tx arrival
       mbar_init(&conv[i], 2);   // the two B-splitting warps
       mbar_init(&empty[i], 1);  // tcgen05.commit of the chunk's MMAs
     }
@@ -688,7 +699,10 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
       const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
       if (!ti.live) continue;
       const GemmDesc d = a.desc[ti.bb];
-      const float2* Ab = a.A + ((long long)d.a_r + (long long)ti.rt * d.a_c + ti.kb / TC_KC) * (TC_M * TC_KC);
+      int rows_blk;  // rows stored in this row tile's blocks (a multiple of 8)
+      const float2* Ab =
+          a.A + ((long long)d.a_r + tiled_block_unit(ti.m, d.a_c, ti.rt, ti.kb / TC_KC, rows_blk)) * TILE_UNIT;
+      const uint32_t half = (uint32_t)rows_blk * (TC_KR * 2);  // bytes of the block's hi (and of its lo) tile
       const int col0 = ti.ct * NC;
       for (int kt = 0; kt < ti.nk; ++kt, ++g) {
         const int st = (int)(g % TCB_S);
@@ -697,21 +711,37 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
           break;
         }
         unsigned char* sp = ring + (size_t)st * STAGE;
-        if (lane == 0) bulk_load(smem_u32(sp), Ab + (long long)kt * (TC_M * TC_KC), A_BYTES, &full[st]);
         const uint32_t rb = smem_u32(sp + A_BYTES);
         const int k0 = ti.kb + kt * TC_KC;
-        for (int l = lane; l < TC_KC * NC; l += 32) {
-          const int kc2 = l / NC, nc = l % NC;
-          const int gk = k0 + kc2, gj = col0 + nc;
-          if (gk < ti.kk && gj < ti.n) {
-            const long long br =
-                (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
-            cp_async8z(rb + l * 8, a.B + br * a.ldb + d.b_c + gj, 8u);
-          } else {
-            cp_async8z(rb + l * 8, a.B, 0u);  // zero fill, nothing read
+        // the B chunk is one contiguous 16-byte aligned run when its 8 rows lie in one segment,
+        // inside the split, and are whole rows of NC columns of a B with NC columns per row
+        const long long br0 = (d.kb2 > 0 && k0 >= d.kb2) ? (long long)d.b_r2 + (k0 - d.kb2) : (long long)d.b_r + k0;
+        const float2* bsrc = a.B + br0 * a.ldb + d.b_c + col0;
+        const bool bulk_b = k0 + TC_KC <= ti.kk && !(d.kb2 > 0 && k0 < d.kb2 && k0 + TC_KC > d.kb2) &&
+                            a.ldb == NC && col0 + NC <= ti.n && (reinterpret_cast<uintptr_t>(bsrc) & 15) == 0;
+        if (lane == 0) {
+          // hi tile to the stage's first 4 KB, lo tile to the second; rows past a compact block
+          // keep stale values and only feed accumulator rows that are not stored
+          const char* src = reinterpret_cast<const char*>(Ab + (long long)kt * rows_blk * TC_KC);
+          expect_tx(&full[st], 2 * half + (bulk_b ? (uint32_t)BRAW : 0u));
+          bulk_copy(smem_u32(sp), src, half, &full[st]);
+          bulk_copy(smem_u32(sp) + A_BYTES / 2, src + half, half, &full[st]);
+          if (bulk_b) bulk_copy(rb, bsrc, BRAW, &full[st]);
+        }
+        if (!bulk_b) {
+          for (int l = lane; l < TC_KC * NC; l += 32) {
+            const int kc2 = l / NC, nc = l % NC;
+            const int gk = k0 + kc2, gj = col0 + nc;
+            if (gk < ti.kk && gj < ti.n) {
+              const long long br =
+                  (d.kb2 > 0 && gk >= d.kb2) ? (long long)d.b_r2 + (gk - d.kb2) : (long long)d.b_r + gk;
+              cp_async8z(rb + l * 8, a.B + br * a.ldb + d.b_c + gj, 8u);
+            } else {
+              cp_async8z(rb + l * 8, a.B, 0u);  // zero fill, nothing read
+            }
           }
         }
-        cp_async_arrive(&full[st]);
+        cp_async_arrive(&full[st]);  // every lane arrives (at once when it issued no copy)
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -799,27 +829,32 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
     }
   } else {
     // ---------------- epilogue ----------------
+    constexpr int LD = TB::EPI_LD, RPI = 32 / NC;  // rows per pass of the warp (NC = 16: two)
     const int quarter = warp & 3;
+    float2* stg = reinterpret_cast<float2*>(ring + (size_t)TCB_S * STAGE) + quarter * 32 * LD;
+    const int lr = lane / NC, jc = lane % NC;  // this lane's row (within a pass) and column
     int tc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
       if (!ti.live) continue;
       const GemmDesc d = a.desc[ti.bb];
-      const int row0 = ti.rt * TC_M, col0 = ti.ct * NC;
-      const int row = 32 * quarter + lane, gi = row0 + row;
+      const int row0 = ti.rt * TC_M + 32 * quarter, col0 = ti.ct * NC, gj = col0 + jc;
       const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
       const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
-      const long long orow = gi < ti.m ? (long long)d.c_r + (rmap ? rmap[gi] : gi) : 0;
-      const long long cr = (d.mc2 > 0 && gi >= d.mc2) ? (long long)d.c0_r2 + (gi - d.mc2) : (long long)d.c0_r + gi;
+      // output and C0 rows of row row0 + lane, shuffled to the lanes that write them
+      const int gl = row0 + lane;
+      const long long orow_l = gl < ti.m ? (long long)d.c_r + (rmap ? rmap[gl] : gl) : 0;
+      const long long cr_l = (d.mc2 > 0 && gl >= d.mc2) ? (long long)d.c0_r2 + (gl - d.mc2) : (long long)d.c0_r + gl;
       float2* W = ksplit > 1 ? a.ws + (((long long)ti.sp * a.nbatch + ti.bb) * mmax) * nmax : nullptr;
-      // beta * C0 of this row, loaded while the tile's MMAs run
+      // beta * C0 along rows, loaded while the tile's MMAs run
       float2 c0v[NC];
 #pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        const int gj = col0 + j;
-        c0v[j] = (!W && a.C0 && gi < ti.m && gj < ti.n) ? cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj])
-                                                        : make_float2(0.f, 0.f);
+      for (int i = 0; i < NC; ++i) {
+        const int r = i * RPI + lr;
+        const long long cr = __shfl_sync(0xffffffffu, cr_l, r);
+        c0v[i] = (!W && a.C0 && row0 + r < ti.m && gj < ti.n) ? cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj])
+                                                              : make_float2(0.f, 0.f);
       }
       const int buf = tc & 1;
       if (ti.nk > 0) {
@@ -829,6 +864,7 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
+      // accumulator rows (thread = row) -> staging
 #pragma unroll
       for (int gq = 0; gq < G; ++gq) {
         uint32_t v[16];
@@ -844,19 +880,9 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = 0u;
         }
-        if (gi < ti.m) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int jc = gq * 8 + j, gj = col0 + jc;
-            if (gj >= ti.n) continue;
-            const float2 acc = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
-            if (W) {
-              W[(long long)gi * nmax + gj] = acc;
-              continue;
-            }
-            a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = cadd(cmul(a.alpha, acc), c0v[jc]);
-          }
-        }
+        for (int j = 0; j < 8; ++j)
+          stg[lane * LD + gq * 8 + j] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
       }
       if (ti.nk > 0) {
         // the accumulator is read: the MMAs of the tile after next may overwrite it
@@ -865,6 +891,21 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         if (lane == 0) mbar_arrive(&acce[buf]);
         ++tc;
       }
+      __syncwarp();
+      // staging -> C (or the split-K workspace) along rows
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const int r = i * RPI + lr, gi = row0 + r;
+        const long long orow = __shfl_sync(0xffffffffu, orow_l, r);
+        if (gi < ti.m && gj < ti.n) {
+          const float2 acc = stg[r * LD + jc];
+          if (W)
+            W[(long long)gi * nmax + gj] = acc;
+          else
+            a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = cadd(cmul(a.alpha, acc), c0v[i]);
+        }
+      }
+      __syncwarp();  // the staging is rewritten by the next tile
     }
   }
   __syncthreads();
@@ -960,15 +1001,37 @@ cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, i
   return launch_tc<64, true>(a, mmax, nmax, kmax, err, s);
 }
 
-// TL[P][rt][kt] = 128 x 8 complex block of A_P (rows rt*128.., k kt*8..), core-matrix order,
-// zero past the operator's rows and k.
+// Block (P, rt, kt) of the tiled layout and the entry w of that block for entry l of the whole
+// layout (entries in layout order: a unit of 64 entries = 512 bytes in both formats).
+__device__ __forceinline__ void tiled_entry(long long l, int rows, int nrt, int nkt, long long pair_entries,
+                                            long long& blk_entry, int& P, int& rt, int& kt, int& w) {
+  P = (int)(l / pair_entries);
+  const long long off = l % pair_entries;
+  const long long full = (long long)(nrt - 1) * nkt * (TC_M * TC_KC);  // entries of the full row tiles
+  int bs;
+  if (off < full) {
+    bs = TC_M * TC_KC;
+    rt = (int)(off / ((long long)nkt * bs));
+    const long long rem = off % ((long long)nkt * bs);
+    kt = (int)(rem / bs);
+    w = (int)(rem % bs);
+  } else {
+    bs = tiled_last_rows(rows) * TC_KC;
+    rt = nrt - 1;
+    kt = (int)((off - full) / bs);
+    w = (int)((off - full) % bs);
+  }
+  blk_entry = l - w;  // first entry of the block
+}
+
+// FP32 blocks: entry w = float2 w of the block in core_off order
 __global__ void tile_operator_kernel(float2* __restrict__ TL, const float2* __restrict__ A, int npairs, int rows,
-                                     int K, int lda, long long pair_stride, int nrt, int nkt) {
-  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
+                                     int K, int lda, long long pair_stride, int nrt, int nkt, long long pair_entries) {
+  const long long tot = (long long)npairs * pair_entries;
   for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
-    const long long blk = l / (TC_M * TC_KC);
-    const int w = (int)(l % (TC_M * TC_KC));  // float2 position inside the block
-    const int kt = (int)(blk % nkt), rt = (int)((blk / nkt) % nrt), P = (int)(blk / ((long long)nkt * nrt));
+    long long be;
+    int P, rt, kt, w;
+    tiled_entry(l, rows, nrt, nkt, pair_entries, be, P, rt, kt, w);
     // invert core_off(r, 2 kc) / 8: row group r/8 (SBO = 512 B), k group (2 kc)/4 (LBO = 128 B),
     // row r%8 (16 B), pair (2 kc)%4 / 2 (8 B)
     const int byte = w * 8;
@@ -980,53 +1043,55 @@ __global__ void tile_operator_kernel(float2* __restrict__ TL, const float2* __re
   }
 }
 
-// The same blocks pre-split for the bf16x3 sweep kernel: block = [hi tile | lo tile], each 128
-// rows x 16 real k of bf16 in the 16-bit core-matrix order (one 32-bit word = the (Re, Im) pair
-// of one complex entry).  Thread l writes word l % 1024 of both tiles of block l / 1024.
+// bf16x3 blocks: [hi tile | lo tile], each rows_blk x 16 real k of bf16 in the 16-bit core-matrix
+// order; one 32-bit word = the (Re, Im) pair of one complex entry, entry w = word w of both tiles
 __global__ void tile_operator_bf16x3_kernel(uint32_t* __restrict__ TL, const float2* __restrict__ A, int npairs,
-                                            int rows, int K, int lda, long long pair_stride, int nrt, int nkt) {
-  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
+                                            int rows, int K, int lda, long long pair_stride, int nrt, int nkt,
+                                            long long pair_entries) {
+  const long long tot = (long long)npairs * pair_entries;
   for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
-    const long long blk = l / (TC_M * TC_KC);
-    const int u = (int)(l % (TC_M * TC_KC));  // word inside one tile
-    const int kt = (int)(blk % nkt), rt = (int)((blk / nkt) % nrt), P = (int)(blk / ((long long)nkt * nrt));
-    // invert core_off16(r, 2 kc) / 4: row group r/8 (SBO16 = 256 B = 64 words), k group
-    // (2 kc)/8 (LBO16 = 128 B = 32 words), row r%8 (4 words), pair kc%4
-    const int rg = u / 64, kg = (u % 64) / 32, w = u % 32;
-    const int r = rg * 8 + w / 4, kc = kg * 4 + w % 4;
+    long long be;
+    int P, rt, kt, w;
+    tiled_entry(l, rows, nrt, nkt, pair_entries, be, P, rt, kt, w);
+    const int rows_blk = rt < nrt - 1 ? TC_M : tiled_last_rows(rows);
+    // invert core_off16(r, 2 kc) / 4: row group r/8 (SBO16 = 64 words), k group (2 kc)/8
+    // (LBO16 = 32 words), row r%8 (4 words), pair kc%4
+    const int rg = w / 64, kg = (w % 64) / 32, wi = w % 32;
+    const int r = rg * 8 + wi / 4, kc = kg * 4 + wi % 4;
     const int gi = rt * TC_M + r, gk = kt * TC_KC + kc;
     const float2 x = (gi < rows && gk < K) ? A[(long long)P * pair_stride + (long long)gi * lda + gk] : make_float2(0.f, 0.f);
     uint32_t rh, rl, ih, il;
     split_bf16(x.x, rh, rl);
     split_bf16(x.y, ih, il);
-    TL[blk * (2 * TC_M * TC_KC) + u] = rh | (ih << 16);
-    TL[blk * (2 * TC_M * TC_KC) + TC_M * TC_KC + u] = rl | (il << 16);
+    uint32_t* blk = TL + 2 * be;  // a block of e entries takes 2e words
+    blk[w] = rh | (ih << 16);
+    blk[rows_blk * TC_KC + w] = rl | (il << 16);
   }
+}
+
+template <typename Kern, typename T>
+cudaError_t launch_tile(Kern kern, T* TL, const float2* A, int npairs, int rows, int K, int lda, long long pair_stride,
+                        cudaStream_t s) {
+  const int nrt = tiled_row_tiles(rows), nkt = (K + TC_KC - 1) / TC_KC;
+  const long long pair_entries = tiled_pair_units(rows, K) * TILE_UNIT;
+  const long long tot = (long long)npairs * pair_entries;
+  long long blocks = (tot + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  if (blocks < 1) return cudaSuccess;
+  kern<<<(int)blocks, 256, 0, s>>>(TL, A, npairs, rows, K, lda, pair_stride, nrt, nkt, pair_entries);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int K, int lda, long long pair_stride,
                           cudaStream_t s) {
-  const int nrt = (rows + TC_M - 1) / TC_M, nkt = (K + TC_KC - 1) / TC_KC;
-  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
-  long long blocks = (tot + 255) / 256;
-  if (blocks > 65536) blocks = 65536;
-  if (blocks < 1) return cudaSuccess;
-  tile_operator_kernel<<<(int)blocks, 256, 0, s>>>(TL, A, npairs, rows, K, lda, pair_stride, nrt, nkt);
-  note_launch();
-  return cudaGetLastError();
+  return launch_tile(tile_operator_kernel, TL, A, npairs, rows, K, lda, pair_stride, s);
 }
 
 cudaError_t tile_operator_bf16x3(float2* TL, const float2* A, int npairs, int rows, int K, int lda,
                                  long long pair_stride, cudaStream_t s) {
-  const int nrt = (rows + TC_M - 1) / TC_M, nkt = (K + TC_KC - 1) / TC_KC;
-  const long long tot = (long long)npairs * nrt * nkt * (TC_M * TC_KC);
-  long long blocks = (tot + 255) / 256;
-  if (blocks > 65536) blocks = 65536;
-  if (blocks < 1) return cudaSuccess;
-  tile_operator_bf16x3_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<uint32_t*>(TL), A, npairs, rows, K, lda,
-                                                         pair_stride, nrt, nkt);
-  note_launch();
-  return cudaGetLastError();
+  return launch_tile(tile_operator_bf16x3_kernel, reinterpret_cast<uint32_t*>(TL), A, npairs, rows, K, lda,
+                     pair_stride, s);
 }
 
 void optin_tc() {

@@ -187,14 +187,26 @@ def test_precond_apply(solver, cfg_small, L_exact, coarse):
         assert rel(z[k], zo) < 1e-10, (L_exact, coarse, k)
 
 
+# one bf16x3 sweep product: x = hi + lo to 2^-16 relative for each operand, and the dropped
+# lo*lo term is below 2^-16: at most 3 * 2^-16 relative against the FP32 product
+BF16X3_PRODUCT = 3 * 2.0 ** -16
+
+
 @pytest.mark.parametrize("L_exact", [1, 2, 3])
 @pytest.mark.parametrize("gamma", [2, 3])
-@pytest.mark.parametrize("precision", [H.HPS_FP64, H.HPS_MIXED])
-def test_precond_gamma_cycle(solver, cfg_small, L_exact, gamma, precision):
-    """gamma coarse calls per level (section 4.3) against the oracle's gamma-cycle."""
+@pytest.mark.parametrize("precision,sweep", [(H.HPS_FP64, H.SWEEP_DEFAULT), (H.HPS_MIXED, H.SWEEP_FP32),
+                                             (H.HPS_MIXED, H.SWEEP_BF16X3)])
+def test_precond_gamma_cycle(solver, cfg_small, L_exact, gamma, precision, sweep):
+    """gamma coarse calls per level (section 4.3) against the oracle's gamma-cycle.  Tolerance:
+    FP64 1e-10; FP32 tree 2e-5; bf16x3 sweeps add one product error per up- and down-sweep of
+    every call of every level (level l runs gamma^l times), doubled."""
     prob, op = cfg_small
     H.setup(solver, prob, precision)
-    solver.merge_levels(L_exact)
+    solver.set_sweep_arith(sweep)
+    try:
+        solver.merge_levels(L_exact)
+    finally:
+        solver.set_sweep_arith(H.SWEEP_DEFAULT)
     tree = MergeTree(op.mesh, op.Ts, None, L_exact)
     r = np.random.default_rng(70 + L_exact).standard_normal((2, op.mesh.n_skel)) * (0.6 - 1j)
     solver.set_gamma(gamma)
@@ -202,7 +214,12 @@ def test_precond_gamma_cycle(solver, cfg_small, L_exact, gamma, precision):
         z = host(solver.precond_apply(dev(r), inner_iters=3))
     finally:
         solver.set_gamma(1)
-    tol = 1e-10 if precision == H.HPS_FP64 else 2e-5
+    if precision == H.HPS_FP64:
+        tol = 1e-10
+    elif sweep == H.SWEEP_FP32:
+        tol = 2e-5
+    else:
+        tol = 2e-5 + 2 * 2 * BF16X3_PRODUCT * sum(gamma ** lv for lv in range(L_exact))
     for k in range(2):
         zo = tree.mg(r[k], "gmres", 3, gamma)
         assert rel(z[k], zo) < tol, (L_exact, gamma, k)
@@ -230,19 +247,14 @@ def test_solve_gamma_cycle_mixed(solver):
     assert its[2] <= its[1], its
 
 
-# one bf16x3 sweep product: x = hi + lo to 2^-16 relative for each operand, and the dropped
-# lo*lo term is below 2^-16: at most 3 * 2^-16 relative against the FP32 product
-BF16X3_PRODUCT = 3 * 2.0 ** -16
-
-
 @pytest.mark.parametrize("sweep", [H.SWEEP_FP32, H.SWEEP_BF16X3])
 @pytest.mark.parametrize("nrhs", [16, 32, 48])
 def test_precond_mixed_tensor_core_sweeps(solver, nrhs, sweep):
     """FP32 tree on a 16x16, N=8 mesh: the upper sweep and coarse products (rows and k >= 64) run
-    on the tensor cores (FP32 sweeps: 16, 32 or 64 column tiles; bf16x3 sweeps: 16 or 32 column
-    tiles, side by side for 48); the V-cycle against the oracle's (section 4.3).  Tolerance: 2e-5
-    for the FP32 tree; bf16x3 adds one product error on each of the up- and down-sweep of the one
-    level with 2m >= 64 (m = 56), doubled for its growth through the coarse correction."""
+    on the tensor cores (FP32 sweeps: 16, 32 or 64 column tiles; bf16x3 sweeps, on all six
+    levels: 16 or 32 column tiles, side by side for 48); the V-cycle against the oracle's (section
+    4.3).  Tolerance: 2e-5 for the FP32 tree; bf16x3 adds one product error on each up- and
+    down-sweep, doubled for its growth through the coarse correction."""
     prob = inputs.single_bump(16, 8, 20.0, 1, seed=9, L_exact=6)
     op = OracleProblem(prob)
     H.setup(solver, prob, H.HPS_MIXED)
@@ -254,15 +266,16 @@ def test_precond_mixed_tensor_core_sweeps(solver, nrhs, sweep):
     tree = MergeTree(op.mesh, op.Ts, None, prob.L_exact)
     r = np.random.default_rng(nrhs).standard_normal((nrhs, op.mesh.n_skel)) * (1 + 0.25j)
     z = host(solver.precond_apply(dev(r), inner_iters=4))
-    tol = 2e-5 if sweep == H.SWEEP_FP32 else 2e-5 + 2 * 2 * BF16X3_PRODUCT
+    tol = 2e-5 if sweep == H.SWEEP_FP32 else 2e-5 + 2 * 2 * prob.L_exact * BF16X3_PRODUCT
     for k in (0, nrhs // 2, nrhs - 1):
         assert rel(z[k], tree.mg(r[k], "gmres", 4)) < tol, k
 
 
 def test_bf16x3_sweeps_against_fp32_sweeps_and_solve(solver):
-    """32x32, N=16, kappa=60, 32 RHS, L_exact=8: the sweep products of merge levels 4-8 (m >= 60)
-    run on the bf16x3 kernel.  The V-cycle differs from the FP32-sweep V-cycle (itself pinned to
-    the oracle above) by at most 2 products' error per tiled level (up and down), doubled; both
+    """32x32, N=16, kappa=60, 32 RHS, L_exact=8: the sweep products of every merge level run on the
+    bf16x3 kernel (levels 1-3 with compact row tiles of 32-120 rows).  The V-cycle differs from
+    the FP32-sweep V-cycle (itself pinned to the oracle above) by at most 2 products' error per
+    level (up and down), doubled; both
     solves reach the FP64 residual 1e-10 and their solutions agree to the solve tolerance's
     conditioning; bf16x3 takes at most two more FGMRES iterations."""
     prob = inputs.single_bump(32, 16, 60.0, 32, seed=5, L_exact=8)
@@ -279,9 +292,8 @@ def test_bf16x3_sweeps_against_fp32_sweeps_and_solve(solver):
             its[sweep] = info["outer_iterations"]
     finally:
         solver.set_sweep_arith(H.SWEEP_DEFAULT)
-    tiled_levels = 5
     for k in (0, 13, 31):
-        assert rel(z[H.SWEEP_BF16X3][k], z[H.SWEEP_FP32][k]) < 2 * 2 * tiled_levels * BF16X3_PRODUCT, k
+        assert rel(z[H.SWEEP_BF16X3][k], z[H.SWEEP_FP32][k]) < 2 * 2 * prob.L_exact * BF16X3_PRODUCT, k
         assert rel(g[H.SWEEP_BF16X3][k], g[H.SWEEP_FP32][k]) < 1e-8, k
     assert its[H.SWEEP_BF16X3] <= its[H.SWEEP_FP32] + 2, its
 
