@@ -537,10 +537,11 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
 //               tile's last chunk to its accumulator's full barrier; two accumulators in tensor
 //               memory alternate by tile, so a tile's epilogue overlaps the next tile's MMAs;
 //   warps 2-3   split the raw B chunk into the stage's bf16 hi/lo B' tiles;
-//   warps 4-7   epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its 32 output
-//               rows), releases the accumulator and writes the rows through a shared-memory
-//               transpose, so that C0 loads and C stores run along rows (coalesced); its C0
-//               values are loaded before the accumulator is ready.
+//   warps 4-7   epilogue: warp w owns tensor-memory lanes 32 (w % 4) .. + 31 (its 32 output
+//               rows).  It copies the tile's C0 rows into its shared-memory staging
+//               asynchronously while the MMAs run, then combines them with the accumulator
+//               rows in place (thread = row), releases the accumulator and writes the staging
+//               out along rows, so that C0 loads and C stores are coalesced.
 // Every wait is bounded; a wait that gives up (or that starts after another role gave up) ends
 // the role's loops, *err is set, and the copies and MMAs in flight are waited for before the
 // tensor memory is released.
@@ -557,7 +558,7 @@ template <int NC> struct TcbTile {
   // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-  static constexpr int EPI_LD = NC + 1;                   // epilogue staging row (padded), complex
+  static constexpr int EPI_LD = NC + 2;                   // epilogue staging row (padded, 16-byte aligned), complex
   static constexpr int EPI = 4 * 32 * EPI_LD * 8;         // staging of the four epilogue warps
   static constexpr size_t SMEM = (size_t)S * STAGE + EPI + 1024;
 };
@@ -601,6 +602,10 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
 // padding reaches shared memory through the same completion mechanism as the data
 __device__ __forceinline__ void cp_async8z(uint32_t dst, const void* src, uint32_t nbytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
+}
+// the same with 16 bytes (16-byte aligned addresses; nbytes 0, 8 or 16)
+__device__ __forceinline__ void cp_async16z(uint32_t dst, const void* src, uint32_t nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
 }
 // one arrival on b that also expects `bytes` of bulk copies to complete on it
 __device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
@@ -829,33 +834,53 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
     }
   } else {
     // ---------------- epilogue ----------------
-    constexpr int LD = TB::EPI_LD, RPI = 32 / NC;  // rows per pass of the warp (NC = 16: two)
+    constexpr int LD = TB::EPI_LD;
     const int quarter = warp & 3;
     float2* stg = reinterpret_cast<float2*>(ring + (size_t)TCB_S * STAGE) + quarter * 32 * LD;
-    const int lr = lane / NC, jc = lane % NC;  // this lane's row (within a pass) and column
     int tc = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const TileInfo ti = tile_info(a, NC, t, gx, gy, ksplit, kc);
       if (!ti.live) continue;
       const GemmDesc d = a.desc[ti.bb];
-      const int row0 = ti.rt * TC_M + 32 * quarter, col0 = ti.ct * NC, gj = col0 + jc;
+      const int row0 = ti.rt * TC_M + 32 * quarter, col0 = ti.ct * NC;
       const int* rmap = d.rmap >= 0 ? a.maps + d.rmap : nullptr;
       const int* cmap = d.cmap >= 0 ? a.maps + d.cmap : nullptr;
-      // output and C0 rows of row row0 + lane, shuffled to the lanes that write them
+      // output and C0 rows of row row0 + lane, shuffled to the lanes that move them
       const int gl = row0 + lane;
       const long long orow_l = gl < ti.m ? (long long)d.c_r + (rmap ? rmap[gl] : gl) : 0;
       const long long cr_l = (d.mc2 > 0 && gl >= d.mc2) ? (long long)d.c0_r2 + (gl - d.mc2) : (long long)d.c0_r + gl;
       float2* W = ksplit > 1 ? a.ws + (((long long)ti.sp * a.nbatch + ti.bb) * mmax) * nmax : nullptr;
-      // beta * C0 along rows, loaded while the tile's MMAs run
-      float2 c0v[NC];
-#pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        const int r = i * RPI + lr;
-        const long long cr = __shfl_sync(0xffffffffu, cr_l, r);
-        c0v[i] = (!W && a.C0 && row0 + r < ti.m && gj < ti.n) ? cmul(a.beta, a.C0[cr * a.ldc0 + d.c0_c + gj])
-                                                              : make_float2(0.f, 0.f);
+      const bool has_c0 = !W && a.C0;
+      // rows move along the lanes, two complex (16 bytes) per lane when every row of C0 and of the
+      // output starts on a 16-byte boundary and no column map applies, else one (8 bytes)
+      const bool vec = !cmap && (col0 % 2) == 0 &&
+                       (W ? (nmax % 2 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0)
+                          : (a.ldc % 2 == 0 && d.c_c % 2 == 0 && (reinterpret_cast<uintptr_t>(a.C) & 15) == 0)) &&
+                       (!has_c0 || (a.ldc0 % 2 == 0 && d.c0_c % 2 == 0 && (reinterpret_cast<uintptr_t>(a.C0) & 15) == 0));
+      // C0 into the staging by asynchronous copies issued while the tile's MMAs run (zero where
+      // there is no C0 term or no such row / column)
+      if (vec) {
+        constexpr int LPR = NC / 2, RPP = 32 / LPR;  // lanes per row, rows per pass
+        const int lr = lane / LPR, jc = (lane % LPR) * 2, gj = col0 + jc;
+#pragma unroll 4
+        for (int i = 0; i < 32 / RPP; ++i) {
+          const int r = i * RPP + lr;
+          const long long cr = __shfl_sync(0xffffffffu, cr_l, r);
+          const uint32_t nb = (has_c0 && row0 + r < ti.m) ? (gj + 1 < ti.n ? 16u : gj < ti.n ? 8u : 0u) : 0u;
+          cp_async16z(smem_u32(stg + r * LD + jc), nb ? a.C0 + cr * a.ldc0 + d.c0_c + gj : a.B, nb);
+        }
+      } else {
+        const int lr = lane / NC, jc = lane % NC, gj = col0 + jc;
+#pragma unroll 4
+        for (int i = 0; i < NC; ++i) {
+          const int r = i * (32 / NC) + lr;
+          const long long cr = __shfl_sync(0xffffffffu, cr_l, r);
+          const bool in = has_c0 && row0 + r < ti.m && gj < ti.n;
+          cp_async8z(smem_u32(stg + r * LD + jc), in ? a.C0 + cr * a.ldc0 + d.c0_c + gj : a.B, in ? 8u : 0u);
+        }
       }
+      cp_async_commit();
       const int buf = tc & 1;
       if (ti.nk > 0) {
         if (!wait(&accf[buf], (uint32_t)((tc >> 1) & 1))) {
@@ -864,7 +889,9 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
-      // accumulator rows (thread = row) -> staging
+      cp_async_wait<0>();
+      __syncwarp();
+      // staging[row] = alpha * accumulator row + beta * C0 row (thread = row, 16-byte accesses)
 #pragma unroll
       for (int gq = 0; gq < G; ++gq) {
         uint32_t v[16];
@@ -881,8 +908,18 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
           for (int j = 0; j < 16; ++j) v[j] = 0u;
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          stg[lane * LD + gq * 8 + j] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        for (int j = 0; j < 4; ++j) {
+          float4* q = reinterpret_cast<float4*>(stg + lane * LD + gq * 8 + 2 * j);
+          const float2 a0 = make_float2(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]));
+          const float2 a1 = make_float2(__uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+          float2 o0 = a0, o1 = a1;
+          if (!W) {
+            const float4 c = *q;
+            o0 = cadd(cmul(a.alpha, a0), cmul(a.beta, make_float2(c.x, c.y)));
+            o1 = cadd(cmul(a.alpha, a1), cmul(a.beta, make_float2(c.z, c.w)));
+          }
+          *q = make_float4(o0.x, o0.y, o1.x, o1.y);
+        }
       }
       if (ti.nk > 0) {
         // the accumulator is read: the MMAs of the tile after next may overwrite it
@@ -893,16 +930,33 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
       }
       __syncwarp();
       // staging -> C (or the split-K workspace) along rows
-#pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        const int r = i * RPI + lr, gi = row0 + r;
-        const long long orow = __shfl_sync(0xffffffffu, orow_l, r);
-        if (gi < ti.m && gj < ti.n) {
-          const float2 acc = stg[r * LD + jc];
-          if (W)
-            W[(long long)gi * nmax + gj] = acc;
-          else
-            a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = cadd(cmul(a.alpha, acc), c0v[i]);
+      if (vec) {
+        constexpr int LPR = NC / 2, RPP = 32 / LPR;
+        const int lr = lane / LPR, jc = (lane % LPR) * 2, gj = col0 + jc;
+#pragma unroll 8
+        for (int i = 0; i < 32 / RPP; ++i) {
+          const int r = i * RPP + lr, gi = row0 + r;
+          const long long orow = __shfl_sync(0xffffffffu, orow_l, r);
+          if (gi < ti.m && gj < ti.n) {
+            const float4 o = *reinterpret_cast<const float4*>(stg + r * LD + jc);
+            float2* dst = W ? W + (long long)gi * nmax + gj : a.C + orow * a.ldc + d.c_c + gj;
+            if (gj + 1 < ti.n) *reinterpret_cast<float4*>(dst) = o;
+            else *dst = make_float2(o.x, o.y);
+          }
+        }
+      } else {
+        const int lr = lane / NC, jc = lane % NC, gj = col0 + jc;
+#pragma unroll 8
+        for (int i = 0; i < NC; ++i) {
+          const int r = i * (32 / NC) + lr, gi = row0 + r;
+          const long long orow = __shfl_sync(0xffffffffu, orow_l, r);
+          if (gi < ti.m && gj < ti.n) {
+            const float2 o = stg[r * LD + jc];
+            if (W)
+              W[(long long)gi * nmax + gj] = o;
+            else
+              a.C[orow * a.ldc + d.c_c + (cmap ? cmap[gj] : gj)] = o;
+          }
         }
       }
       __syncwarp();  // the staging is rewritten by the next tile
