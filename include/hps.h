@@ -79,6 +79,9 @@ enum { HPS_FP64 = 0, HPS_MIXED = 1 };
 /* Arithmetic of the outer FGMRES (hps_set_outer_arith). */
 enum { HPS_OUTER_DEFAULT = -1, HPS_OUTER_FP64 = 0, HPS_OUTER_DF64 = 1 };
 
+/* Method of the double-float Arnoldi matvec (hps_set_arnoldi_matvec). */
+enum { HPS_MV_DEFAULT = -1, HPS_MV_SIMT = 0, HPS_MV_TENSOR = 1 };
+
 /* Arithmetic of the sweep products of an HPS_MIXED tree (hps_set_sweep_arith). */
 enum { HPS_SWEEP_DEFAULT = -1, HPS_SWEEP_FP32 = 0, HPS_SWEEP_BF16X3 = 1 };
 
@@ -261,6 +264,30 @@ int hps_set_gamma(hps_ctx* ctx, int gamma);
  * HPS_EINVAL for other values.  DF64 needs HPS_MIXED leaves: with HPS_FP64
  * leaves hps_gmres_solve returns HPS_EINVAL (there is no silent fallback). */
 int hps_set_outer_arith(hps_ctx* ctx, int mode);
+
+/* Method of the Arnoldi matvec w = Pi M z of later HPS_OUTER_DF64 solves on ctx
+ * (section 4.3: the skeleton operator applied once per FGMRES iteration), with
+ * the FP64 leaf maps, the preconditioned direction z in FP32 and w in
+ * double-float:
+ *   HPS_MV_SIMT     error-free FP32 products and TwoSum accumulation on the
+ *                   FP32 pipes (about 48 significant bits);
+ *   HPS_MV_TENSOR   exact splitting on the tensor cores (Ozaki, Ogita, Oishi,
+ *                   Rump 2012): the rows of T and the columns of the expanded z
+ *                   cut into seven 7-bit slices aligned to their largest entry,
+ *                   the 28 slice products with s + t <= 8 formed exactly in
+ *                   bf16 MMAs with FP32 accumulation, summed in double-float;
+ *                   error below about 2^-45 |T_i.|max |z_.r|max (4q) per entry.
+ *                   Used when 4q <= 92 and nrhs <= 32, else HPS_MV_SIMT;
+ *   HPS_MV_DEFAULT  HPS_MV_TENSOR (the initial state).
+ * HPS_EINVAL for other values. */
+int hps_set_arnoldi_matvec(hps_ctx* ctx, int method);
+
+/* The Arnoldi matvec as the current method forms it, for checking it: y = Pi M x
+ * with x rounded to FP32 first (the Arnoldi multiplies FP32 directions) and the
+ * double-float result returned in FP64.  x, y: [nrhs][n_skel] complex128 in the
+ * hps_skel_matvec layout, device pointers; 1 <= nrhs <= 64.  HPS_ENOTBUILT
+ * before hps_build_leaves; HPS_ETIMEOUT if a tensor-core wait gave up. */
+int hps_skel_matvec_mixed(hps_ctx* ctx, const void* x, void* y, int nrhs);
 
 /* Arithmetic of the preconditioner's sweep products (section 4.3: the up-sweep
  * rho' = rho - U f and the down-sweep x = Dm [.;.] of every merge level, which

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhps.so")
-SOURCES = ["leaf.cu", "blas.cu", "skel.cu", "merge.cu", "api.cu", "solve.cu", "noalloc.cu", "df64.cu", "tc.cu", "volume.cu"]
+SOURCES = ["leaf.cu", "blas.cu", "skel.cu", "merge.cu", "api.cu", "solve.cu", "noalloc.cu", "df64.cu", "tc.cu", "volume.cu", "ozk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-diag-suppress", "177"]

@@ -344,6 +344,7 @@ void optin_all_once() {
   optin_df64();
   optin_skel();
   optin_tc();
+  optin_ozk();
   optin_volume();
   done[dev] = true;
 }

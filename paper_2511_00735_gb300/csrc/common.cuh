@@ -137,7 +137,8 @@ template <typename R> struct GemmArgs {
 // 128 rows x 64 complex columns; *err is set when a bounded wait gives up.
 cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s);
 // The same product with A stored tiled by tile_operator (descriptor a_r = the pair's first unit
-// of the tiled layout, a_c = its k chunks; lda unused); bf16x3: A tiled by tile_operator_bf16x3
+// of the tiled layout, a_c = its k chunks; lda = the rows the layout was tiled with, the same
+// for every pair of the launch, while a descriptor's m may be smaller); bf16x3: A tiled by tile_operator_bf16x3
 // and multiplied as hi*hi + hi*lo + lo*hi of bf16 splits (about 3 * 2^-16 relative error).
 cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
                                  cudaStream_t s);
@@ -173,6 +174,16 @@ __host__ __device__ inline long long tiled_block_unit(int rows, int nkt, int rt,
 // Fixed-order sum of ksplit partial tiles from a.ws with the descriptor epilogue (blas.cu).
 cudaError_t splitk_reduce(const GemmArgs<float>& a, int ksplit, int mmax, int nmax, cudaStream_t s);
 void optin_tc();
+// The double-float Arnoldi matvec y = Pi M z on the tensor cores by exact splitting (ozk.cu):
+// T (FP64 leaf maps) cut once per solve into bf16 slices (OA, ozk_slices_elems entries), z FP32,
+// y double-float; rows 4q <= 92, 1 <= nrhs <= 32.
+bool ozk_supported(int nb, int nrhs);
+size_t ozk_slices_elems(int E, int nb);
+cudaError_t ozk_slice_T(const double2* T, uint16_t* OA, int E, int nb, cudaStream_t s);
+cudaError_t ozk_matvec(const uint16_t* OA, const int* nbr, const float2* z, float4* y, int E, int nb, int nrhs,
+                       int num_sms, int* err, cudaStream_t s);
+cudaError_t round_to_f2(float2* dst, const double2* src, long long n, cudaStream_t s);
+void optin_ozk();
 
 // kmax > 0 enables splitting K across blocks when the grid would not fill the GPU.
 template <typename R>

@@ -174,6 +174,11 @@ struct hps_ctx {
   // df64 outer FGMRES (HPS_OUTER_DF64): basis, residual and iterate as float pairs,
   // preconditioned directions in FP32, a df64 copy of the leaf maps
   int outer_arith = HPS_OUTER_DEFAULT;
+  // the double-float Arnoldi matvec (hps_set_arnoldi_matvec) and the bf16 slices of the leaf
+  // maps it multiplies on the tensor cores (cut from d_T at the start of every solve)
+  int arnoldi_mv = HPS_MV_DEFAULT;
+  uint16_t* ozk_A = nullptr;
+  size_t ozk_A_elems = 0;
   // arithmetic of the sweep products of an FP32 tree (hps_set_sweep_arith), read when the tree
   // is built; sweep_bf16x3: the current tree's tiled sweep operators are bf16 hi/lo blocks
   int sweep_arith = HPS_SWEEP_DEFAULT;

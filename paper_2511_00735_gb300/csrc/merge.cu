@@ -99,7 +99,7 @@ cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, con
   a.B = static_cast<const float2*>(B);
   a.C0 = static_cast<const float2*>(C0);
   a.C = static_cast<float2*>(C);
-  a.lda = 0;
+  a.lda = mmax;  // the rows of the tiled layout (every pair of a launch is tiled alike)
   a.ldb = ldb;
   a.ldc0 = ldc0;
   a.ldc = ldc;

@@ -31,7 +31,7 @@ void free_fg(hps_ctx* c) {
   void** bufs[] = {(void**)&c->fg_V, (void**)&c->fg_Z, (void**)&c->fg_x, (void**)&c->fg_w, (void**)&c->fg_rhs,
                    (void**)&c->fg_t, (void**)&c->fg_h, (void**)&c->fg_part, (void**)&c->fg_y, (void**)&c->fg_floor,
                    (void**)&c->df_V, (void**)&c->df_Z, (void**)&c->df_x, (void**)&c->df_w, (void**)&c->df_rhs, (void**)&c->df_part,
-                   (void**)&c->df_T, (void**)&c->df_coef};
+                   (void**)&c->df_T, (void**)&c->df_coef, (void**)&c->ozk_A};
   for (void** b : bufs) {
     dev_free(c, *b);
     *b = nullptr;
@@ -44,6 +44,32 @@ void free_fg(hps_ctx* c) {
   c->pin_floor = nullptr;
   c->pin_coef = nullptr;
   c->fg_restart = c->fg_nrhs = 0;
+  c->ozk_A_elems = 0;
+}
+
+// the tensor-core Arnoldi matvec for nrhs right-hand sides (else the SIMT double-float one)
+bool use_ozk(const hps_ctx* c, int nrhs) { return c->arnoldi_mv != HPS_MV_SIMT && ozk_supported(c->nb, nrhs); }
+
+// cut the current leaf maps into the tensor-core matvec's bf16 slices
+int ozk_prepare(hps_ctx* c) {
+  const size_t need = ozk_slices_elems(c->E, c->nb);
+  if (need > c->ozk_A_elems) {
+    dev_free(c, c->ozk_A);
+    c->ozk_A = static_cast<uint16_t*>(dev_alloc(c, sizeof(uint16_t) * need));
+    c->ozk_A_elems = c->ozk_A ? need : 0;
+    if (!c->ozk_A) return fail(c, HPS_ENOMEM, "leaf-map slices");
+  }
+  HPS_CK(c, ozk_slice_T(c->d_T, c->ozk_A, c->E, c->nb, c->stream));
+  return HPS_OK;
+}
+
+// w = Pi M z in double-float for the FP32 directions z (ES rows)
+int arnoldi_matvec(hps_ctx* c, const float2* z, float4* w, int nrhs, int grid) {
+  if (use_ozk(c, nrhs))
+    HPS_CK(c, ozk_matvec(c->ozk_A, c->d_es_nb, z, w, c->E, c->nb, nrhs, c->num_sms, c->d_gemm_err, c->stream));
+  else
+    HPS_CK(c, df_matvec<float2>(c->df_T, c->d_es_nb, z, nullptr, w, c->E, c->nb, nrhs, grid, c->stream));
+  return HPS_OK;
 }
 
 
@@ -232,6 +258,58 @@ int hps_skel_matvec(hps_ctx* c, const void* x, void* y, int nrhs) {
   return HPS_OK;
 }
 
+int hps_skel_matvec_mixed(hps_ctx* c, const void* x, void* y, int nrhs) {
+  CHECK_CTX(c);
+  if (!c->have_leaves) return fail(c, HPS_ENOTBUILT, "hps_build_leaves first");
+  if (!x || !y || nrhs < 1 || nrhs > 64) return fail(c, HPS_EINVAL, "pointers, 1 <= nrhs <= 64");
+  int rc = ensure_pv(c, nrhs);
+  if (rc) return rc;
+  const size_t vs = (size_t)c->n_es * nrhs;
+  float2* z = static_cast<float2*>(dev_alloc(c, sizeof(float2) * vs));
+  float4* w = static_cast<float4*>(dev_alloc(c, sizeof(float4) * vs));
+  const bool ozk = use_ozk(c, nrhs);
+  if (!ozk && !c->df_T)  // no double-float workspace yet: a later solve reallocates it, df_T included
+    c->df_T = static_cast<float4*>(dev_alloc(c, sizeof(float4) * (size_t)c->E * c->nb * c->nb));
+  if (!z || !w || (!ozk && !c->df_T)) {
+    dev_free(c, z);
+    dev_free(c, w);
+    return fail(c, HPS_ENOMEM, "mixed matvec buffers");
+  }
+  cudaStream_t st = c->stream;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (rc == HPS_OK && e != cudaSuccess) rc = cuda_fail(c, e, what);
+  };
+  if (ozk) rc = ozk_prepare(c);
+  else ck(df_from_d(c->df_T, c->d_T, (long long)c->E * c->nb * c->nb, st), "df_from_d");
+  if (rc == HPS_OK) ck(user_to_rows(c->pv_in, static_cast<const double2*>(x), c->d_es_in, c->n_es, nrhs, c->n_skel, st),
+                       "user_to_rows");
+  if (rc == HPS_OK) ck(round_to_f2(z, c->pv_in, (long long)vs, st), "round_to_f2");
+  if (rc == HPS_OK) rc = arnoldi_matvec(c, z, w, nrhs, std::min(c->E, 8 * c->num_sms));
+  if (rc == HPS_OK) ck(df_to_d(c->pv_out, w, (long long)vs, st), "df_to_d");
+  if (rc == HPS_OK)
+    ck(rows_to_user(static_cast<double2*>(y), c->pv_out, c->d_es_out, c->n_es, nrhs, c->n_skel, st), "rows_to_user");
+  int gerr = 0;
+  if (rc == HPS_OK) {
+    ck(cudaMemcpyAsync(&gerr, c->d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error flag");
+    ck(cudaStreamSynchronize(st), "synchronize");
+  }
+  dev_free(c, z);
+  dev_free(c, w);
+  if (rc == HPS_OK && gerr) {
+    cudaMemsetAsync(c->d_gemm_err, 0, sizeof(int), st);
+    return fail(c, HPS_ETIMEOUT, "the tensor-core matvec timed out waiting for its copies or MMAs");
+  }
+  return rc;
+}
+
+int hps_set_arnoldi_matvec(hps_ctx* c, int method) {
+  if (!c) return HPS_EINVAL;
+  if (method != HPS_MV_DEFAULT && method != HPS_MV_SIMT && method != HPS_MV_TENSOR)
+    return fail(c, HPS_EINVAL, "Arnoldi matvec: HPS_MV_DEFAULT, HPS_MV_SIMT or HPS_MV_TENSOR");
+  c->arnoldi_mv = method;
+  return HPS_OK;
+}
+
 int hps_precond_apply(hps_ctx* c, const void* r, void* z, int nrhs, int inner_iters) {
   CHECK_CTX(c);
   if (!c->have_tree) return fail(c, HPS_ENOTBUILT, "hps_merge_levels first");
@@ -315,7 +393,14 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
       rc = subtract_H(c, c->fg_rhs, c->vol_H, nrhs);
       if (rc) return rc;
     }
-    if (df) HPS_CK(c, df_from_d(c->df_T, c->d_T, (long long)c->E * c->nb * c->nb, st));
+    if (df) {
+      if (use_ozk(c, nrhs)) {
+        rc = ozk_prepare(c);
+        if (rc) return rc;
+      } else {
+        HPS_CK(c, df_from_d(c->df_T, c->d_T, (long long)c->E * c->nb * c->nb, st));
+      }
+    }
   }
   if (df) HPS_CK(c, df_from_d(c->df_rhs, c->fg_rhs, vs, st));
   double2* hbuf = c->fg_h;
@@ -472,7 +557,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
         }
         {
           PhaseScope ps(c, HPS_PH_MATVEC);
-          HPS_CK(c, df_matvec<float2>(c->df_T, c->d_es_nb, Zj, nullptr, c->df_w, c->E, c->nb, nrhs, grid, st));
+          if ((rc = arnoldi_matvec(c, Zj, c->df_w, nrhs, grid)) != HPS_OK) return rc;
         }
         {
           PhaseScope ps(c, HPS_PH_ORTHO);
@@ -657,7 +742,7 @@ int hps_gmres_solve(hps_ctx* c, const void* t, const void* s, int nrhs, double t
         }
         {
           PhaseScope ps(c, HPS_PH_MATVEC);
-          HPS_CK(c, df_matvec<float2>(c->df_T, c->d_es_nb, Zj, nullptr, c->df_w, c->E, c->nb, nrhs, grid, st));
+          if ((rc = arnoldi_matvec(c, Zj, c->df_w, nrhs, grid)) != HPS_OK) return rc;
         }
         PhaseScope ps(c, HPS_PH_ORTHO);
         HPS_CK(c, df_bdot(c->df_V, vs, j + 1, c->df_w, n, nrhs, c->df_part, h1, st));

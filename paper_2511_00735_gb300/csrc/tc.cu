@@ -27,9 +27,11 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace hps {
 namespace {
+using namespace tcg;
 
 constexpr int TC_NT = 128;
 constexpr int TC_M = 128;              // output rows per CTA = TMEM lanes
@@ -50,9 +52,6 @@ template <int NC> struct TcTile {
   static constexpr uint32_t IDESC =
       (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 };
-constexpr long long WAIT_LIMIT = 1LL << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // byte offset of element (r, k) in a tile: core matrix (r/8, k/4), row r%8, column k%4
 __device__ __forceinline__ uint32_t core_off(int r, int k) {
@@ -83,15 +82,6 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t done = 0;
-  for (long long it = 0; it < WAIT_LIMIT && !done; ++it)
-    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                 : "=r"(done)
-                 : "r"(mbar), "r"(parity)
-                 : "memory");
-  return done != 0;
-}
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
   asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
@@ -298,15 +288,6 @@ template <int NC> struct TcpTile {
   static constexpr size_t SMEM = (size_t)S * RAW + (size_t)2 * TcTile<NC>::STAGE * sizeof(float) + 1024;
 };
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int TCS_NT = 256;  // 8 warps: the splitting work is spread over twice the threads
 
@@ -370,7 +351,7 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
   // this CTA's blocks: row tile blockIdx.y of its pair, chunks from kb / TC_KC on, rows_blk rows each
   int rows_blk;
   const float2* Ab =
-      a.A + ((long long)d.a_r + tiled_block_unit(m, d.a_c, blockIdx.y, kb / TC_KC, rows_blk)) * TILE_UNIT;
+      a.A + ((long long)d.a_r + tiled_block_unit((int)a.lda, d.a_c, blockIdx.y, kb / TC_KC, rows_blk)) * TILE_UNIT;
   const int nk = kk > kb ? (kk - kb + TC_KC - 1) / TC_KC : 0;
   const uint32_t ring_s = smem_u32(ring);
   // chunk kt (if any) into raw stage kt % TCP_S; always one commit group per call
@@ -565,61 +546,10 @@ template <int NC> struct TcbTile {
 static_assert(TcbTile<16>::STAGE % 1024 == 0 && TcbTile<32>::STAGE % 1024 == 0, "stage alignment");
 static_assert(TcbTile<16>::A_BYTES == TC_M * TC_KC * 8, "a bf16x3 block occupies one FP32 block");
 
-constexpr uint32_t LBO16 = 128;  // 16-bit tiles: bytes between core matrices along k
-constexpr uint32_t SBO16 = 256;  // and between 8-row groups (16 real k = two core matrices)
-
-// byte offset of the 16-bit element (r, k) of a tile
-__device__ __forceinline__ uint32_t core_off16(int r, int k) {
-  return (uint32_t)(r >> 3) * SBO16 + (uint32_t)(k >> 3) * LBO16 + (uint32_t)(r & 7) * 16 + (uint32_t)(k & 7) * 2;
-}
-__device__ __forceinline__ uint64_t smem_desc16(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(LBO16 >> 4) << 16) | ((uint64_t)(SBO16 >> 4) << 32) |
-         ((uint64_t)1 << 46);
-}
 __device__ __forceinline__ void split_bf16(float x, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
   hi = __bfloat16_as_ushort(h);
   lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));  // x - h is exact in FP32
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
-  asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
-                   tmem),
-               "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(b)) : "memory");
-}
-// arrive on b once every cp.async this thread issued so far has landed (the arrival is counted in
-// the barrier's initial count)
-__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-// 8-byte asynchronous copy that reads nbytes (0 or 8) from src and zero-fills the rest, so that
-// padding reaches shared memory through the same completion mechanism as the data
-__device__ __forceinline__ void cp_async8z(uint32_t dst, const void* src, uint32_t nbytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
-}
-// the same with 16 bytes (16-byte aligned addresses; nbytes 0, 8 or 16)
-__device__ __forceinline__ void cp_async16z(uint32_t dst, const void* src, uint32_t nbytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
-}
-// one arrival on b that also expects `bytes` of bulk copies to complete on it
-__device__ __forceinline__ void expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16) completing on b
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* b) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(smem_u32(b))
-               : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* b) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
-               : "memory");
 }
 
 // tile t of a persistent launch: row tile, column tile, batch entry and k split
@@ -706,7 +636,7 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
       const GemmDesc d = a.desc[ti.bb];
       int rows_blk;  // rows stored in this row tile's blocks (a multiple of 8)
       const float2* Ab =
-          a.A + ((long long)d.a_r + tiled_block_unit(ti.m, d.a_c, ti.rt, ti.kb / TC_KC, rows_blk)) * TILE_UNIT;
+          a.A + ((long long)d.a_r + tiled_block_unit((int)a.lda, d.a_c, ti.rt, ti.kb / TC_KC, rows_blk)) * TILE_UNIT;
       const uint32_t half = (uint32_t)rows_blk * (TC_KR * 2);  // bytes of the block's hi (and of its lo) tile
       const int col0 = ti.ct * NC;
       for (int kt = 0; kt < ti.nk; ++kt, ++g) {

@@ -26,6 +26,9 @@ OUTER_DF64 = 1
 SWEEP_DEFAULT = -1  # sweep-product arithmetic of an HPS_MIXED tree (hps_set_sweep_arith)
 SWEEP_FP32 = 0
 SWEEP_BF16X3 = 1
+MV_DEFAULT = -1  # double-float Arnoldi matvec method (hps_set_arnoldi_matvec)
+MV_SIMT = 0
+MV_TENSOR = 1
 
 _STATUS = {0: "HPS_OK", -1: "HPS_EINVAL", -2: "HPS_ENOMEM", -3: "HPS_ENOTBUILT", -4: "HPS_ENOTCONV",
            -5: "HPS_ETIMEOUT", -6: "HPS_ECUDA", -7: "HPS_ENODEV", -8: "HPS_EUNSUPPORTED", -9: "HPS_ENUMERIC"}
@@ -36,7 +39,8 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_build_leaves", "hps_leaf_T", "hps_merge_levels", "hps_stage_T", "hps_rhs", "hps_skel_matvec",
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
            "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace",
-           "hps_set_outer_arith", "hps_set_gamma", "hps_volume_solution", "hps_set_sweep_arith"]
+           "hps_set_outer_arith", "hps_set_gamma", "hps_volume_solution", "hps_set_sweep_arith",
+           "hps_set_arnoldi_matvec", "hps_skel_matvec_mixed"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
 
@@ -97,6 +101,8 @@ def load_library(path: str = LIB_PATH):
         "hps_set_outer_arith": (i, [vp, i]),
         "hps_set_gamma": (i, [vp, i]),
         "hps_set_sweep_arith": (i, [vp, i]),
+        "hps_set_arnoldi_matvec": (i, [vp, i]),
+        "hps_skel_matvec_mixed": (i, [vp, vp, vp, i]),
         "hps_volume_solution": (i, [vp, vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
@@ -213,6 +219,11 @@ class Solver:
         SWEEP_BF16X3 or SWEEP_DEFAULT (bf16x3)."""
         self._check(self.lib.hps_set_sweep_arith(self.h, mode))
 
+    def set_arnoldi_matvec(self, method: int):
+        """Double-float Arnoldi matvec of later HPS_OUTER_DF64 solves: MV_TENSOR (exact splitting
+        on the tensor cores), MV_SIMT or MV_DEFAULT (tensor)."""
+        self._check(self.lib.hps_set_arnoldi_matvec(self.h, method))
+
     def set_gamma(self, gamma: int):
         """Coarse calls per level of the preconditioner: 1 = V-cycle, gamma > 1 = gamma-cycle."""
         self._check(self.lib.hps_set_gamma(self.h, int(gamma)))
@@ -288,6 +299,13 @@ class Solver:
         nrhs = x.shape[0]
         out = self._cplx((nrhs, self.n_skel))
         self._check(self.lib.hps_skel_matvec(self.h, _ptr(x), _ptr(out), nrhs))
+        return out
+
+    def matvec_mixed(self, x):
+        """The Arnoldi matvec of the mixed path: Pi M x with x rounded to FP32, result in FP64."""
+        nrhs = x.shape[0]
+        out = self._cplx((nrhs, self.n_skel))
+        self._check(self.lib.hps_skel_matvec_mixed(self.h, _ptr(x), _ptr(out), nrhs))
         return out
 
     def precond_apply(self, r, inner_iters: int = 5):

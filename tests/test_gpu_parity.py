@@ -158,6 +158,65 @@ def test_rhs_and_matvec(solver, cfg_small):
     assert rel(y, yo) < 1e-12
 
 
+def fp32_round(x):
+    return (x.real.astype(np.float32) + 1j * x.imag.astype(np.float32)).astype(np.complex128)
+
+
+@pytest.mark.parametrize("nx,N,kappa,nrhs", [(4, 8, 10.0, 3), (4, 12, 20.0, 16), (2, 16, 30.0, 20), (2, 24, 40.0, 32)])
+def test_arnoldi_matvec_tensor_and_simt_vs_oracle(solver, nx, N, kappa, nrhs):
+    """The mixed path's Arnoldi matvec (section 4.3, Pi M z with z in FP32) by exact splitting on
+    the tensor cores and by double-float SIMT products, against the oracle's FP64 operator on the
+    same FP32-rounded z.  Bound of the splitting: the 28 slice products with s + t <= 8 are exact,
+    the dropped ones and the slices' truncation are below 2^-42 max|T_i.| max|z_.r| per k term
+    (Ozaki et al. 2012), summed over the 8q real k; the SIMT path is double-float throughout."""
+    prob = inputs.single_bump(nx, N, kappa, 1, seed=N)
+    op = OracleProblem(prob)
+    H.setup(solver, prob, H.HPS_MIXED)
+    rng = np.random.default_rng(nrhs)
+    # right-hand sides of very different scales and an all-zero one
+    x = rng.standard_normal((nrhs, op.mesh.n_skel)) * (1 - 0.7j) * np.logspace(-20, 20, nrhs)[:, None]
+    x[nrhs // 2] = 0.0
+    xr = fp32_round(x)
+    yo = apply_M(op.mesh, op.Ts, xr.T).T
+    q = 4 * (N - 1)
+    tmax = max(np.max(np.abs(T)) for T in op.Ts)
+    try:
+        for method, bound in ((H.MV_TENSOR, 2.0 ** -42 * 2 * q), (H.MV_SIMT, 2.0 ** -44 * 2 * q)):
+            solver.set_arnoldi_matvec(method)
+            y = host(solver.matvec_mixed(dev(x)))
+            for k in range(nrhs):
+                zmax = np.max(np.abs(xr[k]))
+                err = np.max(np.abs(y[k] - yo[k]))
+                assert err <= bound * tmax * zmax * 2 + 1e-300, (method, k, err, tmax * zmax)
+                if zmax > 0:
+                    assert rel(y[k], yo[k]) < 1e-12, (method, k)
+                else:
+                    assert np.all(y[k] == 0)
+    finally:
+        solver.set_arnoldi_matvec(H.MV_DEFAULT)
+
+
+def test_mixed_solve_tensor_matvec_vs_simt(solver):
+    """FGMRES on the mixed path with the tensor-core Arnoldi matvec and with the SIMT one: both
+    reach the FP64 residual 1e-10, agree to the solve tolerance's conditioning and take the same
+    number of iterations within one."""
+    prob = inputs.single_bump(16, 16, 40.0, 24, seed=13, L_exact=6)
+    t = H.setup(solver, prob, H.HPS_MIXED)
+    solver.merge_levels(prob.L_exact)
+    g, its = {}, {}
+    try:
+        for method in (H.MV_SIMT, H.MV_TENSOR):
+            solver.set_arnoldi_matvec(method)
+            g[method], info = solver.gmres_solve(t, tol=1e-10, inner_iters=prob.inner_iters, restart=20, max_outer=40)
+            assert info["converged"] == prob.nrhs and info["max_rel_residual"] <= 1e-10, method
+            its[method] = info["outer_iterations"]
+    finally:
+        solver.set_arnoldi_matvec(H.MV_DEFAULT)
+    for k in range(prob.nrhs):
+        assert rel(g[H.MV_TENSOR][k], g[H.MV_SIMT][k]) < 1e-8, k
+    assert abs(its[H.MV_TENSOR] - its[H.MV_SIMT]) <= 1, its
+
+
 # ---------------------------------------------------------------- merges
 @pytest.mark.parametrize("nx,N,kappa", [(2, 6, 6.0), (4, 8, 10.0), (8, 4, 10.0)])
 def test_stage_maps(solver, nx, N, kappa):
