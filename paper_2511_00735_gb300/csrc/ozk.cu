@@ -25,14 +25,17 @@
 // z_{nb(p)}.
 //
 // One persistent CTA per SM (the seven accumulators of an element take 7 x 2 NC tensor-memory
-// columns), 256 threads:
+// columns), 448 threads:
 //   warp 0   (one thread) bulk copies: the element's z rows into one of two buffers, the A slices
 //            of each k chunk (sliced once per solve by ozk_slice_T) into a ring of OZ_STAGES;
 //   warp 1   (one thread) the chunk's 28 MMAs, committed to the stage's empty barrier and,
 //            after the element's last chunk, to the accumulator barrier;
-//   warps 2-3 the column exponents of the element's z, then per chunk the 7 bf16 slices of B';
-//   warps 4-7 the epilogue: lane quarter w % 4 = rows 32 (w % 4) .. + 31, double-float sum of
-//            the accumulators, the neighbour term, df64 stores; then the accumulators are free.
+//   warps 2-5 the column exponents of the element's z, then per chunk the 7 bf16 slices of B'
+//            (integer bit extraction);
+//   warps 6-13 the epilogue, two warps per lane quarter w % 4 = rows 32 (w % 4) .. + 31, each
+//            on half the columns: each thread copies its half of the neighbour row z_{nb(p)}
+//            into shared memory while the MMAs run, then sums the accumulators in double-float,
+//            adds the neighbour term and stores df64; then the accumulators are free.
 // Every wait is bounded; a wait that gives up sets *err and the roles drain.
 #include <cuda_bf16.h>
 
@@ -56,7 +59,9 @@ constexpr int OZ_KR = 16;         // real k per chunk = one kind::f16 MMA
 constexpr int OZ_M = 128;         // MMA rows (the element's 4q <= 92 edge rows, the rest unused)
 constexpr int OZ_ROWS = 96;       // most rows a chunk's A slices keep (rows rounded up to 8)
 constexpr int OZ_STAGES = 3;
-constexpr int OZ_NT = 256;
+constexpr int OZ_SLICERS = 4;                 // warps 2-5
+constexpr int OZ_EPI = 8;                     // warps 6-13: two per tensor-memory lane quarter
+constexpr int OZ_NT = 32 * (2 + OZ_SLICERS + OZ_EPI);
 constexpr int OZ_NBMAX = 92;      // 4q at GLL order 24
 
 template <int NC> struct OzTile {
@@ -67,48 +72,58 @@ template <int NC> struct OzTile {
   static constexpr int B_SLICE = N * OZ_KR * 2;          // one slice of B' for one chunk
   static constexpr int STAGE = ((A_REGION + OZ_S * B_SLICE) + 1023) / 1024 * 1024;
   static constexpr int ZBUF = OZ_NBMAX * NC * 8;         // one element's z rows (FP32 complex)
-  static constexpr size_t SMEM = (size_t)OZ_STAGES * STAGE + 2 * (size_t)ZBUF + 1024;
+  static constexpr int NLD = NC / 2 + 1;                 // neighbour staging row (half the columns)
+  static constexpr int NBUF = OZ_EPI * 32 * NLD * 8;     // the epilogue warps' neighbour rows
+  static constexpr size_t SMEM = (size_t)OZ_STAGES * STAGE + 2 * (size_t)ZBUF + NBUF + 1024;
   static constexpr int TCOLS = OZ_G * N <= 256 ? 256 : 512;
   // kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M = 128
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
 };
 
-// the slices of x below 2^e (|x| < 2^e): x 2^-e = sum_s alpha_s 2^(-7 s) + rest, each slice
-// alpha_s 2^(e - 7 s) returned as bf16 bits (exact: |alpha_s| < 128); truncation toward zero
-__device__ __forceinline__ void slice7(double x, int e, uint16_t* out) {
-  double r = ldexp(x, -e);
+// bf16 bits of sign * alpha 2^p (0 <= alpha < 128 an integer; exact, alpha has <= 7 bits),
+// assembled from the integer: leading bit at 2^(p + msb), the bits below it as the mantissa;
+// a value below the normal range (never for entries within 2^-77 of their row's or column's
+// largest) becomes 0
+__device__ __forceinline__ uint16_t slice_bits(uint32_t alpha, int p, uint32_t sign) {
+  const int msb = 31 - __clz(alpha | 1u);          // alpha = 0 gives 0 below
+  const int be = p + msb + 127;                     // biased exponent
+  const uint32_t mant = (alpha << (7 - msb)) & 0x7Fu;
+  const uint32_t bits = (sign << 15) | ((uint32_t)be << 7) | mant;
+  return (alpha != 0 && be > 0 && be < 255) ? (uint16_t)bits : (uint16_t)0;
+}
+// The OZ_S slices of a value with integer magnitude m times 2^pe, below 2^e:
+// q = floor(|x| 2^(49 - e)) < 2^49, alpha_s = bits 49 - 7s .. 55 - 7s of q (|x| truncated
+// toward zero in 7-bit chunks), slice s = sign * alpha_s 2^(e - 7 s).  Integer operations only.
+__device__ __forceinline__ void slices_of(uint64_t m, int pe, uint32_t sign, int e, uint16_t* out) {
+  const int shift = pe + (OZ_BITS * OZ_S) - e;  // q = m 2^shift
+  uint64_t q = 0;
+  if (m != 0) q = shift >= 0 ? (shift < 64 ? m << shift : 0) : (-shift < 64 ? m >> -shift : 0);
 #pragma unroll
-  for (int s = 1; s <= OZ_S; ++s) {
-    const double t = r * (double)(1 << OZ_BITS);
-    const double al = trunc(t);
-    r = t - al;
-    out[s - 1] = __bfloat16_as_ushort(__float2bfloat16_rn((float)ldexp(al, e - OZ_BITS * s)));
-  }
+  for (int s = 1; s <= OZ_S; ++s)
+    out[s - 1] = slice_bits((uint32_t)(q >> (OZ_BITS * (OZ_S - s))) & ((1u << OZ_BITS) - 1), e - OZ_BITS * s, sign);
+}
+// the slices of x (|x| < 2^e); subnormal x counts as 0
+__device__ __forceinline__ void slice7(double x, int e, uint16_t* out) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = ex == 0 ? 0 : ((b & ((1ull << 52) - 1)) | (1ull << 52));
+  slices_of(m, ex - 1075, (uint32_t)(b >> 63), e, out);
 }
 __device__ __forceinline__ void slice7f(float x, int e, uint16_t* out) {
-  float r = ldexpf(x, -e);
-#pragma unroll
-  for (int s = 1; s <= OZ_S; ++s) {
-    const float t = r * (float)(1 << OZ_BITS);
-    const float al = truncf(t);
-    r = t - al;
-    out[s - 1] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf(al, e - OZ_BITS * s)));
-  }
+  const uint32_t b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xFF);
+  const uint64_t m = ex == 0 ? 0 : ((b & 0x7FFFFFu) | 0x800000u);
+  slices_of(m, ex - 150, b >> 31, e, out);
 }
-// smallest e with |x| < 2^e for every |x| <= m (0 when m == 0)
+// smallest e with |x| < 2^e for every |x| <= m (0 when m == 0): m = f 2^e, 0.5 <= f < 1
 __device__ __forceinline__ int exp_above(double m) {
   if (!(m > 0.0)) return 0;
-  int e;
-  frexp(m, &e);  // m = f 2^e, 0.5 <= f < 1
-  return e;
+  return (int)((((unsigned long long)__double_as_longlong(m)) >> 52) & 0x7FF) - 1022;
 }
-
 __device__ __forceinline__ int exp_above_f(float m) {
   if (!(m > 0.f)) return 0;
-  int e;
-  frexpf(m, &e);
-  return e;
+  return (int)((__float_as_uint(m) >> 23) & 0xFF) - 126;
 }
 
 // A slices: OA[e][kc][s][rows_pad x 16 bf16 in core_off16 order], zero past 4q rows and 8q k.
@@ -170,15 +185,15 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
     s_fail = 0;
     for (int i = 0; i < OZ_STAGES; ++i) {
       mbar_init(&full[i], 1);  // the producer's expect_tx arrival
-      mbar_init(&conv[i], 2);  // the two B-slicing warps
+      mbar_init(&conv[i], OZ_SLICERS);  // the B-slicing warps
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&zfull[i], 1);
-      mbar_init(&zfree[i], 2);
+      mbar_init(&zfree[i], OZ_SLICERS);
     }
     mbar_init(&accf, 1);
-    mbar_init(&acce, 4);
+    mbar_init(&acce, OZ_EPI);
     mbar_init(&fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
         mbar_wait(smem_u32(&fin), 0);
       }
     }
-  } else if (warp <= 3) {
+  } else if (warp <= 1 + OZ_SLICERS) {
     // ---------------- column exponents and B' slices ----------------
     const int tb = tid - 64;
     long long g = 0;
@@ -280,7 +295,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
       const int zb = ie & 1;
       if (!wait(&zfull[zb], (uint32_t)((ie >> 1) & 1))) break;
       const float2* zs = zbuf + (size_t)zb * OZ_NBMAX * NC;
-      // this thread only ever slices right-hand side rr (l = tb mod 64 below): its column
+      // this thread only ever slices right-hand side rr (l = tb mod 32 OZ_SLICERS below): its column
       // exponent, shared by the columns 2 rr and 2 rr + 1 of B'
       const int rr = tb % NC;
       int F = 0;
@@ -301,7 +316,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
         }
         unsigned char* sb = ring + (size_t)st * STAGE + A_REGION;
         // complex (kk, r) of the chunk -> B'^T rows 2r: (Re, -Im), 2r+1: (Im, Re) at real k 2kk, 2kk+1
-        for (int l = tb; l < (OZ_KR / 2) * NC; l += 64) {
+        for (int l = tb; l < (OZ_KR / 2) * NC; l += 32 * OZ_SLICERS) {
           const int kk = l / NC, r = rr, k = c * (OZ_KR / 2) + kk;
           const float2 v = (k < nb && r < nrhs) ? zs[k * nrhs + r] : make_float2(0.f, 0.f);
           uint16_t re[OZ_S], im[OZ_S];
@@ -325,15 +340,25 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
     }
   } else {
     // ---------------- epilogue ----------------
-    const int quarter = warp & 3, i = 32 * quarter + lane;
+    constexpr int NLD = TB::NLD;
+    // warp w: lane quarter w % 4 (rows), column half (w - 6) / 4
+    const int quarter = warp & 3, i = 32 * quarter + lane, half = (warp - 2 - OZ_SLICERS) / 4;
+    const int r0 = half * (NC / 2), r1 = min(nrhs, r0 + NC / 2);
+    // this thread's half of its neighbour row z_{nb(p)}, copied in while the element's MMAs run
+    float2* nrow = reinterpret_cast<float2*>(ring + (size_t)OZ_STAGES * STAGE + 2 * (size_t)TB::ZBUF) +
+                   ((warp - 2 - OZ_SLICERS) * 32 + lane) * NLD;
     int ie = 0;
     for (int e = blockIdx.x; e < E; e += gridDim.x, ++ie) {
       const long long p = (long long)e * nb + i;
       const int q = i < nb ? nbr[p] : -1;
+      if (q >= 0)
+        for (int r = r0; r < r1; ++r) cp_async8z(smem_u32(nrow + (r - r0)), z + (long long)q * nrhs + r, 8u);
+      cp_async_commit();
       if (!wait(&accf, (uint32_t)(ie & 1))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      cp_async_wait<0>();
 #pragma unroll 1
-      for (int gq = 0; gq < N / 16; ++gq) {
+      for (int gq = half * (N / 32); gq < (half + 1) * (N / 32); ++gq) {
         float hs[16], lo[16];
 #pragma unroll
         for (int d = 0; d < OZ_G; ++d) {
@@ -366,7 +391,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
             if (r >= nrhs) continue;
             float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q >= 0) {
-              const float2 zn = z[(long long)q * nrhs + r];
+              const float2 zn = nrow[r - r0];
               float t, er;
               two_sum(hs[2 * j2], zn.x, t, er);
               const float lre = __fadd_rn(lo[2 * j2], er);
@@ -384,6 +409,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce);
     }
+    cp_async_wait<0>();  // no copy lands after the CTA ends
   }
   __syncthreads();
   if (tid == 0 && s_fail) atomicExch(err, 1);
