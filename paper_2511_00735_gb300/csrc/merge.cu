@@ -93,7 +93,7 @@ cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long
 // The sweep products of a tiled level (FP32 tree): A = the tiled operator, tensor cores.
 cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, const void* B, long long ldb,
                        const void* C0, long long ldc0, void* C, long long ldc, double alpha, const int* maps, int mmax,
-                       int nmax, int n_launch, int kmax) {
+                       int nmax, int n_launch, int kmax, bool bf16x3) {
   GemmArgs<float> a;
   a.A = static_cast<const float2*>(A);
   a.B = static_cast<const float2*>(B);
@@ -113,7 +113,7 @@ cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, con
   a.ws_elems = (long long)c->gemm_ws_elems;
   a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
   a.err = c->d_gemm_err;
-  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, c->sweep_bf16x3, a.err, c->stream);
+  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, bf16x3, a.err, c->stream);
 }
 
 // sweep operators kept tiled for the tensor cores (FP32 tree): every level with bf16x3 sweeps;
@@ -783,7 +783,7 @@ int mg_level(hps_ctx* c, int l, int nrhs, int k) {
   // up-sweep: rho'_E = rho_E - U f
   if (Lv.Ut)
     HPS_CK(c, gemm_tiled(c, Lv.d_tsdesc + SUP * NP, NP, Lv.Ut, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
-                         Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
+                         Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m, c->sweep_bf16x3));
   else
     HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
                       Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
@@ -812,7 +812,7 @@ int mg_level(hps_ctx* c, int l, int nrhs, int k) {
   HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(P1.vec), Lv.d_up, (long long)P1.nsub * P1.n, nrhs, st)));
   if (Lv.Dmt)
     HPS_CK(c, gemm_tiled(c, Lv.d_tsdesc + SDN * NP, NP, Lv.Dmt, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
-                         2 * m, nrhs, nrhs, 2 * n));
+                         2 * m, nrhs, nrhs, 2 * n, c->sweep_bf16x3));
   else
     HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
                       2 * m, nrhs, nrhs, 2 * n));

@@ -19,20 +19,22 @@
 // scale, so one FP32 accumulator per d holds their sum exactly while it stays below 2^24 (K <=
 // 148 real k for every d <= 8: every GLL order up to 18; above, the two smallest groups may
 // round by a unit of 2^(-7 d), far below the result's last bit).  The products with
-// d <= OZ_D are formed (28 kind::f16 MMAs per k chunk of 16), the rest dropped; the dropped
+// d <= OZ_D are formed (per k chunk of 16 and A slice s, the B slices t = 1 .. 8 - s side by side
+// in one or two kind::f16 MMAs of N up to 256), the rest dropped; the dropped
 // part and the slice truncation are below about 2^-45 of max|A_i.| max|B'_.j| K.  The seven
 // accumulators are summed in double-float by TwoSum from the largest, then the neighbour term
 // z_{nb(p)}.
 //
 // One persistent CTA per SM (the seven accumulators of an element take 7 x 2 NC tensor-memory
-// columns), 448 threads:
+// columns), 512 threads:
 //   warp 0   (one thread) bulk copies: the element's z rows into one of two buffers, the A slices
-//            of each k chunk (sliced once per solve by ozk_slice_T) into a ring of OZ_STAGES;
-//   warp 1   (one thread) the chunk's 28 MMAs, committed to the stage's empty barrier and,
+//            of each k chunk (sliced once per solve by ozk_slice_T) into a ring of stages;
+//   warp 1   (one thread) the chunk's MMAs (10 for 32 right-hand sides), committed to the stage's
+//            empty barrier and,
 //            after the element's last chunk, to the accumulator barrier;
-//   warps 2-5 the column exponents of the element's z, then per chunk the 7 bf16 slices of B'
+//   warps 2-7 the column exponents of the element's z, then per chunk the 7 bf16 slices of B'
 //            (integer bit extraction);
-//   warps 6-13 the epilogue, two warps per lane quarter w % 4 = rows 32 (w % 4) .. + 31, each
+//   warps 8-15 the epilogue, two warps per lane quarter w % 4 = rows 32 (w % 4) .. + 31, each
 //            on half the columns: each thread copies its half of the neighbour row z_{nb(p)}
 //            into shared memory while the MMAs run, then sums the accumulators in double-float,
 //            adds the neighbour term and stores df64; then the accumulators are free.
@@ -56,29 +58,34 @@ constexpr int OZ_S = 7;           // slices per operand
 constexpr int OZ_D = 8;           // products with s + t <= OZ_D are formed
 constexpr int OZ_G = OZ_D - 1;    // accumulators: d = 2 .. OZ_D
 constexpr int OZ_KR = 16;         // real k per chunk = one kind::f16 MMA
-constexpr int OZ_M = 128;         // MMA rows (the element's 4q <= 92 edge rows, the rest unused)
-constexpr int OZ_ROWS = 96;       // most rows a chunk's A slices keep (rows rounded up to 8)
-constexpr int OZ_STAGES = 3;
-constexpr int OZ_SLICERS = 4;                 // warps 2-5
-constexpr int OZ_EPI = 8;                     // warps 6-13: two per tensor-memory lane quarter
+// MMA rows MM: 64 when the element's 4q edge rows fit (GLL order <= 16), else 128 (the rest unused)
+// rows of an M = 64 accumulator per tensor-memory lane quarter (lanes 32 w .. 32 w + RPQ - 1)
+constexpr int OZ_M64_RPQ = 16;
+constexpr int OZ_SLICERS = 6;                 // warps 2-7
+constexpr int OZ_EPI = 8;                     // warps 8-15: two per tensor-memory lane quarter
 constexpr int OZ_NT = 32 * (2 + OZ_SLICERS + OZ_EPI);
 constexpr int OZ_NBMAX = 92;      // 4q at GLL order 24
 
-template <int NC> struct OzTile {
+template <int NC, int MM> struct OzTile {
   static constexpr int N = 2 * NC;                       // MMA N: real columns
   // A region: 7 slices of up to 96 rows x 16 bf16 back to back, plus room for the MMA's reads of
   // 128 rows from the last slice
-  static constexpr int A_REGION = OZ_S * OZ_ROWS * OZ_KR * 2 + (OZ_M - 8) * OZ_KR * 2;
+  static constexpr int ROWS = MM == 64 ? 64 : 96;         // most rows a chunk's A slices keep
+  static constexpr int S = MM == 64 ? 5 : 3;              // stages
+  static constexpr int NBM = MM == 64 ? 64 : OZ_NBMAX;    // most edge rows of an element
+  static constexpr int A_REGION = OZ_S * ROWS * OZ_KR * 2 + (MM - 8) * OZ_KR * 2;
   static constexpr int B_SLICE = N * OZ_KR * 2;          // one slice of B' for one chunk
   static constexpr int STAGE = ((A_REGION + OZ_S * B_SLICE) + 1023) / 1024 * 1024;
-  static constexpr int ZBUF = OZ_NBMAX * NC * 8;         // one element's z rows (FP32 complex)
+  static constexpr int ZBUF = NBM * NC * 8;              // one element's z rows (FP32 complex)
   static constexpr int NLD = NC / 2 + 1;                 // neighbour staging row (half the columns)
   static constexpr int NBUF = OZ_EPI * 32 * NLD * 8;     // the epilogue warps' neighbour rows
-  static constexpr size_t SMEM = (size_t)OZ_STAGES * STAGE + 2 * (size_t)ZBUF + NBUF + 1024;
+  static constexpr size_t SMEM = (size_t)S * STAGE + 2 * (size_t)ZBUF + NBUF + 1024;
   static constexpr int TCOLS = OZ_G * N <= 256 ? 256 : 512;
-  // kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M = 128
-  static constexpr uint32_t IDESC =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
+  // kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
+  static constexpr int TPM = 256 / N;                     // B slices per MMA (N <= 256)
+  static __device__ __forceinline__ uint32_t idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MM >> 4) << 24);
+  }
 };
 
 // bf16 bits of sign * alpha 2^p (0 <= alpha < 128 an integer; exact, alpha has <= 7 bits),
@@ -161,13 +168,14 @@ __global__ void ozk_slice_T_kernel(const double2* __restrict__ T, uint16_t* __re
   }
 }
 
-template <int NC>
+template <int NC, int MM>
 __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __restrict__ OA,
                                                               const int* __restrict__ nbr,
                                                               const float2* __restrict__ z, float4* __restrict__ y,
                                                               int E, int nb, int nrhs, int rows_pad, int nkc,
                                                               int* err) {
-  using TB = OzTile<NC>;
+  using TB = OzTile<NC, MM>;
+  constexpr int OZ_STAGES = TB::S;
   constexpr int N = TB::N, STAGE = TB::STAGE, B_SLICE = TB::B_SLICE, A_REGION = TB::A_REGION;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[OZ_STAGES], conv[OZ_STAGES], empty[OZ_STAGES], zfull[2], zfree[2], accf,
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
         const int zb = ie & 1;
         if (ie >= 2 && !wait1(&zfree[zb], (uint32_t)(((ie >> 1) - 1) & 1))) break;
         expect_tx(&zfull[zb], z_bytes);
-        bulk_copy(smem_u32(zbuf + (size_t)zb * OZ_NBMAX * NC), z + (long long)e * nb * nrhs, z_bytes, &zfull[zb]);
+        bulk_copy(smem_u32(zbuf + (size_t)zb * TB::NBM * NC), z + (long long)e * nb * nrhs, z_bytes, &zfull[zb]);
         for (int c = 0; c < nkc; ++c, ++g) {
           const int st = (int)(g % OZ_STAGES);
           if (g >= OZ_STAGES && !wait1(&empty[st], (uint32_t)(((g / OZ_STAGES) - 1) & 1))) {
@@ -264,14 +272,19 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = smem_u32(ring + (size_t)st * STAGE), sb = sa + A_REGION;
+          // A slice s times the B slices t = 1 .. OZ_D - s at once: the B slices lie side by side
+          // along N and their accumulators d = s + t too, so one MMA of N = (number of t) x 2 NC
+          // (at most 256) covers several products; the s = 1 MMAs of the first chunk start every
+          // accumulator
 #pragma unroll
-          for (int d = 2; d <= OZ_D; ++d) {
-            const int s0 = d - OZ_S > 1 ? d - OZ_S : 1, s1 = d - 1 < OZ_S ? d - 1 : OZ_S;
+          for (int s = 1; s <= OZ_S; ++s) {
+            const int tmax = OZ_D - s < OZ_S ? OZ_D - s : OZ_S;
 #pragma unroll
-            for (int s = s0; s <= s1; ++s) {
-              const int t = d - s;
-              mma_bf16(tmem + (uint32_t)((d - 2) * N), smem_desc16(sa + (uint32_t)(s - 1) * a_slice),
-                       smem_desc16(sb + (uint32_t)(t - 1) * B_SLICE), TB::IDESC, (c > 0 || s > s0) ? 1u : 0u);
+            for (int t0 = 1; t0 <= tmax; t0 += TB::TPM) {
+              const int nt = tmax - t0 + 1 < TB::TPM ? tmax - t0 + 1 : TB::TPM;
+              mma_bf16(tmem + (uint32_t)((s + t0 - 2) * N), smem_desc16(sa + (uint32_t)(s - 1) * a_slice),
+                       smem_desc16(sb + (uint32_t)(t0 - 1) * B_SLICE), TB::idesc(nt * N),
+                       (c > 0 || s > 1) ? 1u : 0u);
             }
           }
           tc_commit(&empty[st]);
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
     for (int e = blockIdx.x; e < E && ok; e += gridDim.x, ++ie) {
       const int zb = ie & 1;
       if (!wait(&zfull[zb], (uint32_t)((ie >> 1) & 1))) break;
-      const float2* zs = zbuf + (size_t)zb * OZ_NBMAX * NC;
+      const float2* zs = zbuf + (size_t)zb * TB::NBM * NC;
       // this thread only ever slices right-hand side rr (l = tb mod 32 OZ_SLICERS below): its column
       // exponent, shared by the columns 2 rr and 2 rr + 1 of B'
       const int rr = tb % NC;
@@ -341,8 +354,10 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
   } else {
     // ---------------- epilogue ----------------
     constexpr int NLD = TB::NLD;
-    // warp w: lane quarter w % 4 (rows), column half (w - 6) / 4
-    const int quarter = warp & 3, i = 32 * quarter + lane, half = (warp - 2 - OZ_SLICERS) / 4;
+    // warp w: lane quarter w % 4 (rows), column half (w - 8) / 4
+    const int quarter = warp & 3, half = (warp - 2 - OZ_SLICERS) / 4;
+    // accumulator row of this lane (past every element row when the lane holds none)
+    const int i = MM == 128 ? 32 * quarter + lane : (lane < OZ_M64_RPQ ? OZ_M64_RPQ * quarter + lane : 1 << 20);
     const int r0 = half * (NC / 2), r1 = min(nrhs, r0 + NC / 2);
     // this thread's half of its neighbour row z_{nb(p)}, copied in while the element's MMAs run
     float2* nrow = reinterpret_cast<float2*>(ring + (size_t)OZ_STAGES * STAGE + 2 * (size_t)TB::ZBUF) +
@@ -357,37 +372,36 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
       if (!wait(&accf, (uint32_t)(ie & 1))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       cp_async_wait<0>();
+      // 8-column blocks of this warp's half: the 7 accumulators' loads issued together, one wait
 #pragma unroll 1
-      for (int gq = half * (N / 32); gq < (half + 1) * (N / 32); ++gq) {
-        float hs[16], lo[16];
+      for (int gb = half * (N / 16); gb < (half + 1) * (N / 16); ++gb) {
+        uint32_t v[OZ_G][8];
 #pragma unroll
         for (int d = 0; d < OZ_G; ++d) {
-          uint32_t v[16];
-          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(d * N + gq * 16);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(ta));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(d * N + gb * 8);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+                         "=r"(v[d][6]), "=r"(v[d][7])
+                       : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float hs[8], lo[8];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float x = __uint_as_float(v[j]);
-            if (d == 0) {
-              hs[j] = x;
-              lo[j] = 0.f;
-            } else {
-              float t, er;
-              two_sum(hs[j], x, t, er);
-              hs[j] = t;
-              lo[j] = __fadd_rn(lo[j], er);
-            }
+        for (int j = 0; j < 8; ++j) {
+          hs[j] = __uint_as_float(v[0][j]);
+          lo[j] = 0.f;
+#pragma unroll
+          for (int d = 1; d < OZ_G; ++d) {
+            float t, er;
+            two_sum(hs[j], __uint_as_float(v[d][j]), t, er);
+            hs[j] = t;
+            lo[j] = __fadd_rn(lo[j], er);
           }
         }
         if (i < nb) {
 #pragma unroll
-          for (int j2 = 0; j2 < 8; ++j2) {
-            const int r = gq * 8 + j2;
+          for (int j2 = 0; j2 < 4; ++j2) {
+            const int r = gb * 4 + j2;
             if (r >= nrhs) continue;
             float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q >= 0) {
@@ -443,10 +457,19 @@ cudaError_t ozk_matvec(const uint16_t* OA, const int* nbr, const float2* z, floa
   if (!ozk_supported(nb, nrhs)) return cudaErrorInvalidValue;
   const int rows_pad = (nb + 7) / 8 * 8, nkc = (2 * nb + OZ_KR - 1) / OZ_KR;
   const int grid = std::min(E, num_sms);
-  if (nrhs <= 16)
-    ozk_matvec_kernel<16><<<grid, OZ_NT, OzTile<16>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
-  else
-    ozk_matvec_kernel<32><<<grid, OZ_NT, OzTile<32>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
+  if (rows_pad <= 64) {
+    if (nrhs <= 16)
+      ozk_matvec_kernel<16, 64><<<grid, OZ_NT, OzTile<16, 64>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
+    else
+      ozk_matvec_kernel<32, 64><<<grid, OZ_NT, OzTile<32, 64>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
+  } else {
+    if (nrhs <= 16)
+      ozk_matvec_kernel<16, 128><<<grid, OZ_NT, OzTile<16, 128>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc,
+                                                                          err);
+    else
+      ozk_matvec_kernel<32, 128><<<grid, OZ_NT, OzTile<32, 128>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc,
+                                                                          err);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -465,8 +488,10 @@ cudaError_t round_to_f2(float2* dst, const double2* src, long long n, cudaStream
 }
 
 void optin_ozk() {
-  smem_optin(ozk_matvec_kernel<16>);
-  smem_optin(ozk_matvec_kernel<32>);
+  smem_optin(ozk_matvec_kernel<16, 64>);
+  smem_optin(ozk_matvec_kernel<32, 64>);
+  smem_optin(ozk_matvec_kernel<16, 128>);
+  smem_optin(ozk_matvec_kernel<32, 128>);
 }
 
 }  // namespace hps
