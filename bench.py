@@ -634,7 +634,8 @@ def run_systems(args):
 # ---------------------------------------------------------------------------- one phase (profilers)
 def run_phase(args):
     """One phase of a workload in isolation, for ncu: `leaf` (R leaf builds), `merge` (leaves, then
-    R merge-tree builds), `matvec` (R FP64 skeleton matvecs), `precond` (R preconditioner
+    R merge-tree builds), `matvec` (R FP64 skeleton matvecs), `mixed_matvec` (R of the mixed
+    path's Arnoldi matvecs, --mv tensor|simt), `precond` (R preconditioner
     applications) or `solve` (one full step).  --nx 32 runs the 32x32, N = 16, kappa = 50 problem."""
     import torch
 
@@ -677,6 +678,15 @@ def run_phase(args):
             prof.start()
             for _ in range(args.repeat):
                 s.matvec(x)
+        elif args.phase == "mixed_matvec":
+            # the mixed path's Arnoldi matvec (FP32 input, double-float product) by the chosen method
+            s.set_arnoldi_matvec(H.MV_TENSOR if args.mv == "tensor" else H.MV_SIMT)
+            x = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
+            s.matvec_mixed(x)
+            torch.cuda.synchronize()
+            prof.start()
+            for _ in range(args.repeat):
+                s.matvec_mixed(x)
         elif args.phase == "precond":
             s.merge_levels(prob.L_exact)
             r = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
@@ -731,7 +741,8 @@ def main():
                     help="scattering128 (default) / scattering64: the timed step above; batch: the 512-problem "
                          "mix; serve: a Poisson stream; table1: the memory-time trade-off over exact levels and "
                          "coarse steps; phase: one phase in isolation (for profilers)")
-    ap.add_argument("--phase", default="leaf", choices=["leaf", "merge", "matvec", "precond", "solve"])
+    ap.add_argument("--phase", default="leaf", choices=["leaf", "merge", "matvec", "mixed_matvec", "precond", "solve"])
+    ap.add_argument("--mv", default="tensor", choices=["tensor", "simt"], help="phase mixed_matvec: method")
     ap.add_argument("--nx", type=int, default=0, help="phase: element grid (0: 128)")
     ap.add_argument("--repeat", type=int, default=1, help="phase: repetitions")
     ap.add_argument("--count", type=int, default=0, help="problems (batch) or requests (serve)")
