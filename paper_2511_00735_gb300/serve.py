@@ -194,6 +194,16 @@ class Server:
             return t, batch
         return None
 
+    def _fail_oldest(self, e):
+        """Under the lock: report the oldest pending request as failed with the error e."""
+        if not self.pending:
+            return
+        r = self.pending.pop(0)
+        r.info = {"error": repr(e), "rel_residual": [float("inf")], "batched_with": 1}
+        r.done = time.perf_counter() - self.t_origin
+        self.completed.append(r)
+        self.lock.notify_all()
+
     def _worker(self):
         while True:
             with self.lock:
@@ -201,7 +211,11 @@ class Server:
                 while job is None:
                     if self.stop:
                         return
-                    job = self._pick()
+                    try:
+                        job = self._pick()
+                    except Exception as e:  # a context that cannot be created fails its requests
+                        self._fail_oldest(e)
+                        job = None
                     if job is None:
                         self.lock.wait(0.01)
             tree, batch = job
@@ -309,4 +323,5 @@ def run_stream(reqs, server: Server, time_scale: float = 1.0, timeout: float = 3
             "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "max_rel_residual": res, "peak_device_bytes": server.peak_bytes,
-            "mean_batch": float(np.mean([r.info["batched_with"] for r in done])) if done else None}
+            "mean_batch": float(np.mean([r.info["batched_with"] for r in done])) if done else None,
+            "errors": sorted({r.info["error"][:300] for r in done if "error" in r.info})[:5]}
