@@ -50,7 +50,7 @@ FP64_PEAK_NOMINAL = 1.25e12  # GB300 FP64 (nominal, vector = tensor rate)
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # ncu dram read + write of one leaf_ir_kernel launch per element (64x64, N=16 capture, scaled by
 # the elements of a launch); None whenever leaf.cu changed since the capture
-LEAF_TRAFFIC_BYTES_PER_ELEMENT = 225.0e6 / 4096
+LEAF_TRAFFIC_BYTES_PER_ELEMENT = (12.34e6 + 229.55e6) / 4096
 
 
 def make_problem(workload: str, seed: int, nrhs: int):

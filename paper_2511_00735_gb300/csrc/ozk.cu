@@ -61,33 +61,32 @@ constexpr int OZ_KR = 16;         // real k per chunk = one kind::f16 MMA
 // MMA rows MM: 64 when the element's 4q edge rows fit (GLL order <= 16), else 128 (the rest unused)
 // rows of an M = 64 accumulator per tensor-memory lane quarter (lanes 32 w .. 32 w + RPQ - 1)
 constexpr int OZ_M64_RPQ = 16;
-constexpr int OZ_NCH = 16;                    // complex right-hand sides per item (MMA N = 32)
-constexpr int OZ_SLICERS = 4;                 // warps 2-5: one B entry per thread and chunk
-constexpr int OZ_EPI = 8;                     // warps 6-13: two per tensor-memory lane quarter
+constexpr int OZ_SLICERS = 6;                 // warps 2-7
+constexpr int OZ_EPI = 8;                     // warps 8-15: two per tensor-memory lane quarter
 constexpr int OZ_NT = 32 * (2 + OZ_SLICERS + OZ_EPI);
 constexpr int OZ_NBMAX = 92;      // 4q at GLL order 24
 
-template <int MM> struct OzTile {
-  static constexpr int N = 2 * OZ_NCH;                   // MMA N of one item: real columns
-  // A region: 7 slices of up to ROWS rows x 16 bf16 back to back, plus room for the MMA's reads
-  // of MM rows from the last slice
+template <int NC, int MM> struct OzTile {
+  static constexpr int N = 2 * NC;                       // MMA N: real columns
+  // A region: 7 slices of up to 96 rows x 16 bf16 back to back, plus room for the MMA's reads of
+  // 128 rows from the last slice
   static constexpr int ROWS = MM == 64 ? 64 : 96;         // most rows a chunk's A slices keep
-  static constexpr int S = MM == 64 ? 6 : 4;              // stages
+  static constexpr int S = MM == 64 ? 5 : 3;              // stages
   static constexpr int NBM = MM == 64 ? 64 : OZ_NBMAX;    // most edge rows of an element
   static constexpr int A_REGION = OZ_S * ROWS * OZ_KR * 2 + (MM - 8) * OZ_KR * 2;
   static constexpr int B_SLICE = N * OZ_KR * 2;          // one slice of B' for one chunk
   static constexpr int STAGE = ((A_REGION + OZ_S * B_SLICE) + 1023) / 1024 * 1024;
-  static constexpr int ZBUF = NBM * 2 * OZ_NCH * 8;      // one element's z rows (up to 32 RHS)
-  static constexpr int NLD = OZ_NCH / 2 + 1;             // neighbour staging row of one warp's columns
-  static constexpr int NBUF = OZ_EPI * 32 * NLD * 8;
+  static constexpr int ZBUF = NBM * NC * 8;              // one element's z rows (FP32 complex)
+  static constexpr int NLD = NC / 2 + 1;                 // neighbour staging row (half the columns)
+  static constexpr int NBUF = OZ_EPI * 32 * NLD * 8;     // the epilogue warps' neighbour rows
   static constexpr size_t SMEM = (size_t)S * STAGE + 2 * (size_t)ZBUF + NBUF + 1024;
-  static constexpr int SET = OZ_G * N;                   // tensor-memory columns of one accumulator set
-  static constexpr int TCOLS = 512;                      // two sets
+  static constexpr int TCOLS = OZ_G * N <= 256 ? 256 : 512;
+  // kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
+  static constexpr int TPM = 256 / N;                     // B slices per MMA (N <= 256)
   static __device__ __forceinline__ uint32_t idesc(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MM >> 4) << 24);
   }
 };
-static_assert(2 * OzTile<64>::SET <= OzTile<64>::TCOLS, "two accumulator sets");
 
 // bf16 bits of sign * alpha 2^p (0 <= alpha < 128 an integer; exact, alpha has <= 7 bits),
 // assembled from the integer: leading bit at 2^(p + msb), the bits below it as the mantissa;
@@ -169,39 +168,40 @@ __global__ void ozk_slice_T_kernel(const double2* __restrict__ T, uint16_t* __re
   }
 }
 
-template <int MM>
+template <int NC, int MM>
 __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __restrict__ OA,
                                                               const int* __restrict__ nbr,
                                                               const float2* __restrict__ z, float4* __restrict__ y,
                                                               int E, int nb, int nrhs, int rows_pad, int nkc,
                                                               int* err) {
-  using TB = OzTile<MM>;
-  constexpr int N = TB::N, STAGE = TB::STAGE, A_REGION = TB::A_REGION, S = TB::S, SET = TB::SET;
+  using TB = OzTile<NC, MM>;
+  constexpr int OZ_STAGES = TB::S;
+  constexpr int N = TB::N, STAGE = TB::STAGE, B_SLICE = TB::B_SLICE, A_REGION = TB::A_REGION;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], zfull[2], zfree[2], accf[2], acce[2], fin;
+  __shared__ __align__(8) uint64_t full[OZ_STAGES], conv[OZ_STAGES], empty[OZ_STAGES], zfull[2], zfree[2], accf,
+      acce, fin;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail_store;
   volatile int& s_fail = s_fail_store;
   unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float2* zbuf = reinterpret_cast<float2*>(ring + (size_t)S * STAGE);  // [2][nb][nrhs]
+  float2* zbuf = reinterpret_cast<float2*>(ring + (size_t)OZ_STAGES * STAGE);  // [2][nb][nrhs]
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int nh = nrhs > OZ_NCH ? 2 : 1;                     // items (right-hand-side halves) per element
   const uint32_t a_slice = (uint32_t)rows_pad * OZ_KR * 2;  // bytes of one A slice of a chunk
   const uint32_t a_bytes = OZ_S * a_slice;
   const uint32_t z_bytes = (uint32_t)nb * nrhs * 8;
   if (tid == 0) {
     s_fail = 0;
-    for (int i = 0; i < S; ++i) {
+    for (int i = 0; i < OZ_STAGES; ++i) {
       mbar_init(&full[i], 1);  // the producer's expect_tx arrival
-      mbar_init(&conv[i], OZ_SLICERS);
+      mbar_init(&conv[i], OZ_SLICERS);  // the B-slicing warps
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&zfull[i], 1);
       mbar_init(&zfree[i], OZ_SLICERS);
-      mbar_init(&accf[i], 1);
-      mbar_init(&acce[i], OZ_EPI);
     }
+    mbar_init(&accf, 1);
+    mbar_init(&acce, OZ_EPI);
     mbar_init(&fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -237,64 +237,62 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
         const int zb = ie & 1;
         if (ie >= 2 && !wait1(&zfree[zb], (uint32_t)(((ie >> 1) - 1) & 1))) break;
         expect_tx(&zfull[zb], z_bytes);
-        bulk_copy(smem_u32(zbuf + (size_t)zb * TB::NBM * 2 * OZ_NCH), z + (long long)e * nb * nrhs, z_bytes,
-                  &zfull[zb]);
-        // the element's A slices once per item: the two halves of the right-hand sides
-        for (int h = 0; h < nh && ok; ++h)
-          for (int c = 0; c < nkc; ++c, ++g) {
-            const int st = (int)(g % S);
-            if (g >= S && !wait1(&empty[st], (uint32_t)(((g / S) - 1) & 1))) {
-              ok = false;
-              break;
-            }
-            expect_tx(&full[st], a_bytes);
-            bulk_copy(smem_u32(ring + (size_t)st * STAGE), OA + ((long long)e * nkc + c) * OZ_S * rows_pad * OZ_KR,
-                      a_bytes, &full[st]);
+        bulk_copy(smem_u32(zbuf + (size_t)zb * TB::NBM * NC), z + (long long)e * nb * nrhs, z_bytes, &zfull[zb]);
+        for (int c = 0; c < nkc; ++c, ++g) {
+          const int st = (int)(g % OZ_STAGES);
+          if (g >= OZ_STAGES && !wait1(&empty[st], (uint32_t)(((g / OZ_STAGES) - 1) & 1))) {
+            ok = false;
+            break;
           }
+          expect_tx(&full[st], a_bytes);
+          bulk_copy(smem_u32(ring + (size_t)st * STAGE), OA + ((long long)e * nkc + c) * OZ_S * rows_pad * OZ_KR,
+                    a_bytes, &full[st]);
+        }
       }
       // no bulk copy may still be landing when the CTA ends
-      for (long long gg = g - S > 0 ? g - S : 0; gg < g; ++gg)
-        mbar_wait(smem_u32(&full[gg % S]), (uint32_t)((gg / S) & 1));
+      for (long long gg = g - OZ_STAGES > 0 ? g - OZ_STAGES : 0; gg < g; ++gg)
+        mbar_wait(smem_u32(&full[gg % OZ_STAGES]), (uint32_t)((gg / OZ_STAGES) & 1));
       for (int j = ie - 2 > 0 ? ie - 2 : 0; j < ie; ++j) mbar_wait(smem_u32(&zfull[j & 1]), (uint32_t)((j >> 1) & 1));
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       long long g = 0;
-      int it = 0;
+      int ie = 0;
       bool ok = true, issued = false;
-      for (int e = blockIdx.x; e < E && ok; e += gridDim.x)
-        for (int h = 0; h < nh && ok; ++h, ++it) {
-          const int set = it & 1;
-          if (it >= 2 && !wait1(&acce[set], (uint32_t)(((it >> 1) - 1) & 1))) {
+      for (int e = blockIdx.x; e < E && ok; e += gridDim.x, ++ie) {
+        if (ie >= 1 && !wait1(&acce, (uint32_t)((ie - 1) & 1))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < nkc; ++c, ++g) {
+          const int st = (int)(g % OZ_STAGES);
+          const uint32_t par = (uint32_t)((g / OZ_STAGES) & 1);
+          if (!wait1(&full[st], par) || !wait1(&conv[st], par)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          for (int c = 0; c < nkc; ++c, ++g) {
-            const int st = (int)(g % S);
-            const uint32_t par = (uint32_t)((g / S) & 1);
-            if (!wait1(&full[st], par) || !wait1(&conv[st], par)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(ring + (size_t)st * STAGE), sb = sa + A_REGION;
-            // A slice s times the B slices t = 1 .. OZ_D - s at once: the B slices lie side by
-            // side along N and their accumulators d = s + t too; the s = 1 MMA of the first chunk
-            // starts every accumulator of the set
+          const uint32_t sa = smem_u32(ring + (size_t)st * STAGE), sb = sa + A_REGION;
+          // A slice s times the B slices t = 1 .. OZ_D - s at once: the B slices lie side by side
+          // along N and their accumulators d = s + t too, so one MMA of N = (number of t) x 2 NC
+          // (at most 256) covers several products; the s = 1 MMAs of the first chunk start every
+          // accumulator
 #pragma unroll
-            for (int s = 1; s <= OZ_S; ++s) {
-              const int nt = OZ_D - s < OZ_S ? OZ_D - s : OZ_S;
-              mma_bf16(tmem + (uint32_t)(set * SET + (s - 1) * N), smem_desc16(sa + (uint32_t)(s - 1) * a_slice),
-                       smem_desc16(sb), TB::idesc(nt * N), (c > 0 || s > 1) ? 1u : 0u);
+          for (int s = 1; s <= OZ_S; ++s) {
+            const int tmax = OZ_D - s < OZ_S ? OZ_D - s : OZ_S;
+#pragma unroll
+            for (int t0 = 1; t0 <= tmax; t0 += TB::TPM) {
+              const int nt = tmax - t0 + 1 < TB::TPM ? tmax - t0 + 1 : TB::TPM;
+              mma_bf16(tmem + (uint32_t)((s + t0 - 2) * N), smem_desc16(sa + (uint32_t)(s - 1) * a_slice),
+                       smem_desc16(sb + (uint32_t)(t0 - 1) * B_SLICE), TB::idesc(nt * N),
+                       (c > 0 || s > 1) ? 1u : 0u);
             }
-            tc_commit(&empty[st]);
-            issued = true;
           }
-          if (!ok) break;
-          tc_commit(&accf[set]);
+          tc_commit(&empty[st]);
+          issued = true;
         }
+        if (!ok) break;
+        tc_commit(&accf);
+      }
       if (issued) {
         tc_commit(&fin);
         mbar_wait(smem_u32(&fin), 0);
@@ -302,52 +300,52 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
     }
   } else if (warp <= 1 + OZ_SLICERS) {
     // ---------------- column exponents and B' slices ----------------
-    // thread tb slices the chunk's complex k = kk for the item's right-hand side rl
-    const int tb = tid - 64, kk = tb / OZ_NCH, rl = tb % OZ_NCH;
+    const int tb = tid - 64;
     long long g = 0;
     int ie = 0;
     bool ok = true;
     for (int e = blockIdx.x; e < E && ok; e += gridDim.x, ++ie) {
       const int zb = ie & 1;
       if (!wait(&zfull[zb], (uint32_t)((ie >> 1) & 1))) break;
-      const float2* zs = zbuf + (size_t)zb * TB::NBM * 2 * OZ_NCH;
-      for (int h = 0; h < nh && ok; ++h) {
-        const int r = h * OZ_NCH + rl;
-        // the column exponent of right-hand side r, shared by the columns 2 rl and 2 rl + 1 of B'
-        int F = 0;
-        if (r < nrhs) {
-          float m = 0.f;
-          for (int k = 0; k < nb; ++k) {
-            const float2 v = zs[k * nrhs + r];
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-          }
-          F = exp_above_f(m);
+      const float2* zs = zbuf + (size_t)zb * TB::NBM * NC;
+      // this thread only ever slices right-hand side rr (l = tb mod 32 OZ_SLICERS below): its column
+      // exponent, shared by the columns 2 rr and 2 rr + 1 of B'
+      const int rr = tb % NC;
+      int F = 0;
+      if (rr < nrhs) {
+        float m = 0.f;
+        for (int k = 0; k < nb; ++k) {
+          const float2 v = zs[k * nrhs + rr];
+          m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
-        for (int c = 0; c < nkc; ++c, ++g) {
-          const int st = (int)(g % S);
-          // the stage's A has landed, so its previous MMAs are done: its B' may be rewritten
-          if (!wait(&full[st], (uint32_t)((g / S) & 1))) {
-            ok = false;
-            break;
-          }
-          unsigned char* sb = ring + (size_t)st * STAGE + A_REGION;
-          // complex (kk, rl) -> B'^T rows 2 rl: (Re, -Im), 2 rl + 1: (Im, Re) at real k 2 kk, 2 kk + 1
-          const int k = c * (OZ_KR / 2) + kk;
+        F = exp_above_f(m);
+      }
+      for (int c = 0; c < nkc; ++c, ++g) {
+        const int st = (int)(g % OZ_STAGES);
+        // the stage's A has landed, so its previous MMAs are done: its B' may be rewritten
+        if (!wait(&full[st], (uint32_t)((g / OZ_STAGES) & 1))) {
+          ok = false;
+          break;
+        }
+        unsigned char* sb = ring + (size_t)st * STAGE + A_REGION;
+        // complex (kk, r) of the chunk -> B'^T rows 2r: (Re, -Im), 2r+1: (Im, Re) at real k 2kk, 2kk+1
+        for (int l = tb; l < (OZ_KR / 2) * NC; l += 32 * OZ_SLICERS) {
+          const int kk = l / NC, r = rr, k = c * (OZ_KR / 2) + kk;
           const float2 v = (k < nb && r < nrhs) ? zs[k * nrhs + r] : make_float2(0.f, 0.f);
           uint16_t re[OZ_S], im[OZ_S];
           slice7f(v.x, F, re);
           slice7f(v.y, F, im);
-          const uint32_t o0 = core_off16(2 * rl, 2 * kk), o1 = core_off16(2 * rl + 1, 2 * kk);
+          const uint32_t o0 = core_off16(2 * r, 2 * kk), o1 = core_off16(2 * r + 1, 2 * kk);
 #pragma unroll
           for (int t = 0; t < OZ_S; ++t) {
-            unsigned char* bt = sb + t * TB::B_SLICE;
+            unsigned char* bt = sb + t * B_SLICE;
             *reinterpret_cast<uint32_t*>(bt + o0) = (uint32_t)re[t] | ((uint32_t)(im[t] ^ 0x8000u) << 16);
             *reinterpret_cast<uint32_t*>(bt + o1) = (uint32_t)im[t] | ((uint32_t)re[t] << 16);
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&conv[st]);
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[st]);
       }
       if (!ok) break;
       __syncwarp();
@@ -356,82 +354,74 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
   } else {
     // ---------------- epilogue ----------------
     constexpr int NLD = TB::NLD;
-    // warp w: lane quarter w % 4 (rows), column half hw = (w - 6) / 4 of the item's 16 right-hand sides
-    const int quarter = warp & 3, hw = (warp - 2 - OZ_SLICERS) / 4;
+    // warp w: lane quarter w % 4 (rows), column half (w - 8) / 4
+    const int quarter = warp & 3, half = (warp - 2 - OZ_SLICERS) / 4;
     // accumulator row of this lane (past every element row when the lane holds none)
     const int i = MM == 128 ? 32 * quarter + lane : (lane < OZ_M64_RPQ ? OZ_M64_RPQ * quarter + lane : 1 << 20);
-    // this thread's part of its neighbour row z_{nb(p)}, copied in while the item's MMAs run
-    float2* nrow = reinterpret_cast<float2*>(ring + (size_t)S * STAGE + 2 * (size_t)TB::ZBUF) +
+    const int r0 = half * (NC / 2), r1 = min(nrhs, r0 + NC / 2);
+    // this thread's half of its neighbour row z_{nb(p)}, copied in while the element's MMAs run
+    float2* nrow = reinterpret_cast<float2*>(ring + (size_t)OZ_STAGES * STAGE + 2 * (size_t)TB::ZBUF) +
                    ((warp - 2 - OZ_SLICERS) * 32 + lane) * NLD;
-    int it = 0;
-    bool ok = true;
-    for (int e = blockIdx.x; e < E && ok; e += gridDim.x) {
+    int ie = 0;
+    for (int e = blockIdx.x; e < E; e += gridDim.x, ++ie) {
       const long long p = (long long)e * nb + i;
       const int q = i < nb ? nbr[p] : -1;
-      for (int h = 0; h < nh; ++h, ++it) {
-        const int set = it & 1, rb = h * OZ_NCH + hw * (OZ_NCH / 2);  // first right-hand side of this warp
-        if (q >= 0)
-          for (int j = 0; j < OZ_NCH / 2 && rb + j < nrhs; ++j)
-            cp_async8z(smem_u32(nrow + j), z + (long long)q * nrhs + rb + j, 8u);
-        cp_async_commit();
-        if (!wait(&accf[set], (uint32_t)((it >> 1) & 1))) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        cp_async_wait<0>();
-        // two 8-column blocks: the 7 accumulators' loads issued together, one wait
+      if (q >= 0)
+        for (int r = r0; r < r1; ++r) cp_async8z(smem_u32(nrow + (r - r0)), z + (long long)q * nrhs + r, 8u);
+      cp_async_commit();
+      if (!wait(&accf, (uint32_t)(ie & 1))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      cp_async_wait<0>();
+      // 8-column blocks of this warp's half: the 7 accumulators' loads issued together, one wait
 #pragma unroll 1
-        for (int gb = 0; gb < 2; ++gb) {
-          uint32_t v[OZ_G][8];
+      for (int gb = half * (N / 16); gb < (half + 1) * (N / 16); ++gb) {
+        uint32_t v[OZ_G][8];
 #pragma unroll
-          for (int d = 0; d < OZ_G; ++d) {
-            const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) +
-                                (uint32_t)(set * SET + d * N + hw * (N / 2) + gb * 8);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
-                           "=r"(v[d][6]), "=r"(v[d][7])
-                         : "r"(ta));
-          }
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          float hs[8], lo[8];
+        for (int d = 0; d < OZ_G; ++d) {
+          const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(d * N + gb * 8);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+                         "=r"(v[d][6]), "=r"(v[d][7])
+                       : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float hs[8], lo[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            hs[j] = __uint_as_float(v[0][j]);
-            lo[j] = 0.f;
+        for (int j = 0; j < 8; ++j) {
+          hs[j] = __uint_as_float(v[0][j]);
+          lo[j] = 0.f;
 #pragma unroll
-            for (int d = 1; d < OZ_G; ++d) {
-              float t, er;
-              two_sum(hs[j], __uint_as_float(v[d][j]), t, er);
-              hs[j] = t;
-              lo[j] = __fadd_rn(lo[j], er);
-            }
-          }
-          if (i < nb) {
-#pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) {
-              const int jl = gb * 4 + j2, r = rb + jl;
-              if (r >= nrhs) continue;
-              float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (q >= 0) {
-                const float2 zn = nrow[jl];
-                float t, er;
-                two_sum(hs[2 * j2], zn.x, t, er);
-                const float lre = __fadd_rn(lo[2 * j2], er);
-                two_sum(t, lre, o.x, o.z);
-                two_sum(hs[2 * j2 + 1], zn.y, t, er);
-                const float lim = __fadd_rn(lo[2 * j2 + 1], er);
-                two_sum(t, lim, o.y, o.w);
-              }
-              y[p * nrhs + r] = o;
-            }
+          for (int d = 1; d < OZ_G; ++d) {
+            float t, er;
+            two_sum(hs[j], __uint_as_float(v[d][j]), t, er);
+            hs[j] = t;
+            lo[j] = __fadd_rn(lo[j], er);
           }
         }
-        // the set is read: the item after next may overwrite it
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acce[set]);
+        if (i < nb) {
+#pragma unroll
+          for (int j2 = 0; j2 < 4; ++j2) {
+            const int r = gb * 4 + j2;
+            if (r >= nrhs) continue;
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q >= 0) {
+              const float2 zn = nrow[r - r0];
+              float t, er;
+              two_sum(hs[2 * j2], zn.x, t, er);
+              const float lre = __fadd_rn(lo[2 * j2], er);
+              two_sum(t, lre, o.x, o.z);
+              two_sum(hs[2 * j2 + 1], zn.y, t, er);
+              const float lim = __fadd_rn(lo[2 * j2 + 1], er);
+              two_sum(t, lim, o.y, o.w);
+            }
+            y[p * nrhs + r] = o;
+          }
+        }
       }
+      // the accumulators are read: the next element's MMAs may overwrite them
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce);
     }
     cp_async_wait<0>();  // no copy lands after the CTA ends
   }
@@ -467,10 +457,19 @@ cudaError_t ozk_matvec(const uint16_t* OA, const int* nbr, const float2* z, floa
   if (!ozk_supported(nb, nrhs)) return cudaErrorInvalidValue;
   const int rows_pad = (nb + 7) / 8 * 8, nkc = (2 * nb + OZ_KR - 1) / OZ_KR;
   const int grid = std::min(E, num_sms);
-  if (rows_pad <= 64)
-    ozk_matvec_kernel<64><<<grid, OZ_NT, OzTile<64>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
-  else
-    ozk_matvec_kernel<128><<<grid, OZ_NT, OzTile<128>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
+  if (rows_pad <= 64) {
+    if (nrhs <= 16)
+      ozk_matvec_kernel<16, 64><<<grid, OZ_NT, OzTile<16, 64>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
+    else
+      ozk_matvec_kernel<32, 64><<<grid, OZ_NT, OzTile<32, 64>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc, err);
+  } else {
+    if (nrhs <= 16)
+      ozk_matvec_kernel<16, 128><<<grid, OZ_NT, OzTile<16, 128>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc,
+                                                                          err);
+    else
+      ozk_matvec_kernel<32, 128><<<grid, OZ_NT, OzTile<32, 128>::SMEM, s>>>(OA, nbr, z, y, E, nb, nrhs, rows_pad, nkc,
+                                                                          err);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -489,8 +488,10 @@ cudaError_t round_to_f2(float2* dst, const double2* src, long long n, cudaStream
 }
 
 void optin_ozk() {
-  smem_optin(ozk_matvec_kernel<64>);
-  smem_optin(ozk_matvec_kernel<128>);
+  smem_optin(ozk_matvec_kernel<16, 64>);
+  smem_optin(ozk_matvec_kernel<32, 64>);
+  smem_optin(ozk_matvec_kernel<16, 128>);
+  smem_optin(ozk_matvec_kernel<32, 128>);
 }
 
 }  // namespace hps
