@@ -51,6 +51,12 @@ FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 lanes x FMA x 2
 # ncu dram read + write of one leaf_ir_kernel launch per element (64x64, N=16 capture, scaled by
 # the elements of a launch); None whenever leaf.cu changed since the capture
 LEAF_TRAFFIC_BYTES_PER_ELEMENT = (12.34e6 + 229.55e6) / 4096
+# ncu dram read + write of the bf16x3 sweep kernel over one V-cycle's launches divided by their
+# algorithmic bytes (64x64, N=16, 32 RHS capture: the ratio scales the full-size launches);
+# None until captured, and whenever tc.cu's sweep kernel changed since
+SWEEP_TRAFFIC_RATIO = 1748.66e6 / 1893.34e6
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense tensor rates: tf32 / bf16
+KPROF_APPLIES = 8  # preconditioner applications of the per-kernel timing pass
 
 
 def make_problem(workload: str, seed: int, nrhs: int):
@@ -221,6 +227,7 @@ def run_gpu(args, rank, world, local_rank, dist):
     t_dev = torch.from_numpy(t_host).to(dev)
     g_dev = torch.empty((prob.nrhs, s.n_skel), dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
+    s.set_autotune(H.TUNE_ON if args.autotune == "on" else H.TUNE_OFF)
 
     def step(precision, b, t, out):
         s.set_coeff(prob.kappa, b, prob.eta)
@@ -283,6 +290,28 @@ def run_gpu(args, rank, world, local_rank, dist):
                "iterations": r60_infos[0]["outer_iterations"], "max_rel_residual": r60_infos[0]["max_rel_residual"],
                "note": "warm solve (cached tree) with restart 60; compare with warm"}
 
+    # ---- per-launch timing of the sweep products and the merge GEMMs ----
+    # Inside the step the V-cycle replays as one CUDA graph, whose launches cannot be bracketed
+    # one by one: the same tree (rebuilt once) and KPROF_APPLIES direct applications of the same
+    # V-cycle on a random block of nrhs right-hand sides, each launch of a class between CUDA
+    # events on the context's stream (the stream the kernels are launched on).
+    kern = None
+    if prec == H.HPS_MIXED:
+        s.set_coeff(prob.kappa, b_dev, prob.eta)
+        s.build_leaves(prec)
+        s.profile_kernels(True)
+        s.merge_levels(prob.L_exact)
+        gen = torch.Generator(device=dev).manual_seed(7)
+        rr = torch.complex(torch.randn((nrhs, s.n_skel), generator=gen, device=dev, dtype=torch.float64),
+                           torch.randn((nrhs, s.n_skel), generator=gen, device=dev, dtype=torch.float64))
+        for _ in range(KPROF_APPLIES):
+            s.precond_apply(rr, inner_iters=prob.inner_iters)
+        kern = s.profile_kernels_read()
+        s.profile_kernels(False)
+        kern["applies"] = KPROF_APPLIES
+        kern["precond_calls_per_step"] = prof["precond"][2] / args.steps
+    tune_table = H.autotune_table() if args.autotune == "on" else ""
+
     # ---- the plain FP64 GPU path on the same workload (comparison) ----
     fp64 = None
     if prec == H.HPS_MIXED and not args.no_fp64:
@@ -303,7 +332,8 @@ def run_gpu(args, rank, world, local_rank, dist):
     return dict(outer=args.outer if args.outer != "default" else ("df64" if prec == H.HPS_MIXED else "fp64"),
                 prob=prob, ms=ms, wall_ms=wall_ms, value=value, its=its, res=res, conv=conv, prof=prof,
                 launches=launches, clk=clk, e2e_ms=e2e_ms, e2e_wall=e2e_wall, e2e_conv=e2e_conv, h2d=h2d, d2h=d2h,
-                warm_ms=warm_ms, warm_conv=warm_conv, warm_laps=warm_laps, fp64=fp64, laps=laps, r60=r60)
+                warm_ms=warm_ms, warm_conv=warm_conv, warm_laps=warm_laps, fp64=fp64, laps=laps, r60=r60,
+                kern=kern, tune_table=tune_table)
 
 
 # ---------------------------------------------------------------------------- CPU oracle
@@ -651,6 +681,7 @@ def run_phase(args):
         L = 2 * int(round(np.log2(args.nx)))
         prob = inputs.single_bump(args.nx, 16, 100.0 * args.nx / 64.0, args.nrhs, seed=1, L_exact=max(L - 2, 0))
     s = H.Solver(0)
+    s.set_autotune(H.TUNE_ON if args.autotune == "on" else H.TUNE_OFF)  # tuned in the untimed first call
     t = H.setup(s, prob, prec, build=False)
     td = torch.from_numpy(t).cuda()
     torch.cuda.synchronize()
@@ -706,6 +737,8 @@ def run_phase(args):
             "wall_s": time.perf_counter() - t0, "bytes_held": s.bytes_held()}
     if info:
         line.update(iterations=info["outer_iterations"], max_rel_residual=info["max_rel_residual"])
+    if args.autotune == "on":
+        line["autotune"] = H.autotune_table().splitlines()
     s.close()
     print(json.dumps(line), flush=True)
 
@@ -733,6 +766,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--restart", type=int, default=20, help="FGMRES restart length (the paper's Table 1: 60)")
     ap.add_argument("--max-outer", type=int, default=40, help="FGMRES restart cycles at most")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="tile autotuner of the tensor-core GEMMs (tuned in the warm-up steps)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the 64x64 extra line")
@@ -821,15 +856,46 @@ def main():
     nrhs = prob.nrhs
     prof = r["prof"]
     E, N = prob.nx * prob.nx, prob.N
-    # the dominant single-launch kernel of a step: the leaf build (one launch per step); the V-cycle
-    # (one graph of sweep kernels per application, HBM-bound) is reported beside it
-    leaf_ms, leaf_launch, leaf_calls = prof["leaf"]
+    # the dominant kernel of a step: the bf16x3 sweep GEMM (2 L_exact launches per V-cycle, about a
+    # fifth of the step), timed launch by launch in the pass after the timed region; the leaf
+    # kernel (one launch per step) and the V-cycle as a whole are reported beside it
+    kern = r.get("kern")
     roof = None
+    if kern and kern["sweep"][1]:
+        ms_k, n_k, by_k, fl_k = kern["sweep"]
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        per = ms_k / n_k
+        bpl = by_k / n_k
+        calls = kern["precond_calls_per_step"]
+        roof = {"kernel": "tcb_gemm_kernel (bf16x3 sweep products of the V-cycle, every merge level, up and down)",
+                "bound": "hbm", "achieved": bpl / (per / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bpl / (per / 1e3) / 1e9 / hbm,
+                "traffic": SWEEP_TRAFFIC_RATIO * bpl if SWEEP_TRAFFIC_RATIO else None,
+                "traffic_unit": "bytes per launch (ncu dram read + write / algorithmic bytes of a 64x64 capture x "
+                                "this launch's algorithmic bytes)",
+                "algorithmic_bytes_per_launch": bpl, "ms_per_launch": per, "launches_timed": n_k,
+                "bytes_model": "per product: the tiled operator (8 B per complex entry), B, C0 when present and C, "
+                               "each once",
+                "timing": f"CUDA events around each launch on the launching stream, {kern['applies']} direct "
+                          "V-cycle applications of the bench tree after the timed region",
+                "share_of_step_est": ms_k / kern["applies"] * calls * args.steps / r["ms"],
+                "peak_source": "measured" if not peaks.get("fallback") else "fallback 6.8 TB/s"}
+    mg = None
+    if kern and kern["merge_gemm"][1]:
+        ms_m, n_m, by_m, fl_m = kern["merge_gemm"]
+        tf32 = peaks.get("bf16_tflops", 1900.0) * TF32_OVER_BF16
+        mg = {"kernel": "merge GEMMs (3xTF32 tc_gemm_kernel above 64 rows, SIMT below)", "bound": "tensor",
+              "achieved": fl_m / (ms_m / 1e3) / 1e12, "peak": tf32, "unit": "TFLOP/s",
+              "frac": fl_m / (ms_m / 1e3) / 1e12 / tf32, "launches": n_m, "ms_per_merge_phase": ms_m,
+              "flops_model": "8 m n k per complex product (3xTF32 issues three tf32 MMAs per product)",
+              "peak_source": "measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)"}
+    leaf_ms, leaf_launch, leaf_calls = prof["leaf"]
+    leaf_roof = None
     if leaf_calls:
         per = leaf_ms / leaf_calls
         lit = leaf_flops_paper(N) * E
         ex = leaf_flops(N) * E
-        roof = {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, double-float refinement and inverse)",
+        leaf_roof = {"kernel": "leaf_ir_kernel (leaf ItI maps: FP32 factor, double-float refinement and inverse)",
                 "bound": "alu", "achieved": lit / (per / 1e3) / 1e12, "peak": FP32_PEAK_NOMINAL / 1e12,
                 "unit": "TFLOP/s", "frac": lit / (per / 1e3) / FP32_PEAK_NOMINAL,
                 "traffic": LEAF_TRAFFIC_BYTES_PER_ELEMENT * E if LEAF_TRAFFIC_BYTES_PER_ELEMENT else None,
@@ -865,6 +931,7 @@ def main():
         "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": desc, "global_batch": nrhs * world, "precision": args.precision,
+                   "autotune": args.autotune,
                    "outer": r["outer"], "tol": args.tol, "restart": args.restart,
                    "parallelism": "replicas" if world > 1 else "single",
                    "residual": "FP64 (FP64 leaf maps and norms) at every restart and for the returned solution",
@@ -888,6 +955,9 @@ def main():
         "launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "roofline": roof,
         "roofline_vcycle": vc,
+        "roofline_leaf": leaf_roof,
+        "roofline_merge_gemm": mg,
+        "autotune": {"mode": args.autotune, "table": r.get("tune_table", "").splitlines()},
         "cpu_baseline": cpu,
         "clocks": r["clk"],
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),

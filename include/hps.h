@@ -335,6 +335,65 @@ int hps_profile(hps_ctx* ctx, int enable);
  * NULL.  Synchronises the context's stream. */
 int hps_profile_read(hps_ctx* ctx, double* ms, long long* launches, long long* calls);
 
+/* Kernel classes of hps_profile_kernels_read. */
+enum {
+  HPS_KC_SWEEP = 0,    /* the V-cycle's sweep products on the tensor cores (the tiled
+                          operators of every merge level, up- and down-sweep); work =
+                          algorithmic bytes: the operator (8 B per complex entry), the
+                          block vector B, C0 when present and C, each once            */
+  HPS_KC_MERGE_GEMM,   /* the batched complex GEMMs of hps_merge_levels (section 4.1 /
+                          Algorithm 1: S, X1, X2, T_pair, U, Dm); work = algorithmic
+                          flops 8 m n k per product                                     */
+  HPS_NKC
+};
+
+/* enable != 0: clear the per-class counters and bracket every launch of the
+ * classes above with CUDA events on the context's stream (launches being
+ * captured into the V-cycle's CUDA graph inside hps_gmres_solve are not
+ * bracketed: time the class through hps_precond_apply, which launches
+ * directly); enable == 0: stop.  Two event records per launch, no
+ * synchronisation. */
+int hps_profile_kernels(hps_ctx* ctx, int enable);
+
+/* Per class (host arrays [HPS_NKC], any may be NULL): device milliseconds,
+ * bracketed launches, algorithmic bytes and algorithmic flops accumulated
+ * since the last hps_profile_kernels(ctx, 1).  Synchronises the context's
+ * stream. */
+int hps_profile_kernels_read(hps_ctx* ctx, double* ms, long long* launches, double* bytes, double* flops);
+
+/* Tile autotuner of the tensor-core GEMMs (the merge products, the sweep
+ * products and the coarse products): per GEMM shape (kernel family, rows,
+ * columns, k, batch entries, SM count) it times a short list of candidate
+ * launch configurations -- column-tile width, CTAs per SM of the persistent
+ * kernels, and how far k is split to fill the GPU -- with CUDA events on the
+ * context's stream and keeps the fastest in a process-wide table that every
+ * context shares.
+ *   HPS_TUNE_OFF       (default) the fixed heuristics (candidate 0 of each list)
+ *   HPS_TUNE_ON        table lookups; a shape not in the table is tuned on its
+ *                      first launch outside graph capture whose output does not
+ *                      alias its inputs (each candidate runs once untimed and
+ *                      twice timed, then the winner once more, so the call's
+ *                      result is the winner's); a product that cannot be
+ *                      re-run, or that is being captured, takes candidate 0
+ *   HPS_TUNE_FORCE + i candidate i (modulo the list's length) for every shape,
+ *                      without timing (tests of every candidate's numerics)
+ * Switching the mode re-captures the V-cycle graph on its next use; with
+ * HPS_TUNE_ON the first V-cycle after that runs without the graph, so that
+ * its sweep shapes are tuned before they are captured.  Candidates differ
+ * only in tiling and in the order of the k summation (split k), so results
+ * agree to FP32 rounding.  Tuning synchronises the stream once per new shape. */
+enum { HPS_TUNE_OFF = 0, HPS_TUNE_ON = 1, HPS_TUNE_FORCE = 16 };
+int hps_set_autotune(hps_ctx* ctx, int mode);
+
+/* The process-wide tuning table as text, one line per shape ("family m n k
+ * batch sms -> candidate: nc, CTAs per SM, split; ms of candidate 0 and of
+ * the winner"), NUL-terminated and cut to len bytes; returns the number of
+ * shapes in the table (buf may be NULL to count). */
+int hps_autotune_table(char* buf, int len);
+
+/* Empty the process-wide tuning table. */
+void hps_autotune_clear(void);
+
 /* Leaf ItI maps without any device allocation (no counterpart in the paper:
  * a deployment variant of hps_build_leaves).  For callers that cannot
  * allocate device memory while they run, e.g. a process whose device memory

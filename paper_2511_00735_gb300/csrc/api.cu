@@ -38,9 +38,10 @@ static cudaEvent_t get_event(hps_ctx* c) {
   return e;
 }
 
-PhaseScope::PhaseScope(hps_ctx* ctx, int phase) : c(ctx), ph(phase), prev(tl_phase_launch) {
+PhaseScope::PhaseScope(hps_ctx* ctx, int phase) : c(ctx), ph(phase), prev(tl_phase_launch), prev_phase(ctx->cur_phase) {
   tl_phase_launch = &c->prof_launch[ph];
   c->prof_calls[ph] += 1;
+  c->cur_phase = ph;
   if (c->prof) {
     a = get_event(c);
     if (a) cudaEventRecord(a, c->stream);
@@ -49,6 +50,7 @@ PhaseScope::PhaseScope(hps_ctx* ctx, int phase) : c(ctx), ph(phase), prev(tl_pha
 
 PhaseScope::~PhaseScope() {
   tl_phase_launch = prev;
+  c->cur_phase = prev_phase;
   if (c->prof && a) {
     cudaEvent_t b = get_event(c);
     if (b) {
@@ -58,6 +60,49 @@ PhaseScope::~PhaseScope() {
       c->ev_pool.push_back(a);
     }
   }
+}
+
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown: treat as capturing (no event records)
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+KernScope::KernScope(hps_ctx* ctx, int kclass, double bytes, double flops) : c(ctx), kc(kclass) {
+  if (!c->kprof || kc < 0 || kc >= HPS_NKC || stream_capturing(c->stream)) return;
+  a = get_event(c);
+  if (!a) return;
+  cudaEventRecord(a, c->stream);
+  c->kprof_bytes[kc] += bytes;
+  c->kprof_flops[kc] += flops;
+  c->kprof_launch[kc] += 1;
+}
+
+KernScope::~KernScope() {
+  if (!a) return;
+  cudaEvent_t b = get_event(c);
+  if (b) {
+    cudaEventRecord(b, c->stream);
+    c->kprof_ev.push_back({kc, a, b});
+  } else {
+    c->ev_pool.push_back(a);
+  }
+}
+
+static void kprof_collect(hps_ctx* c) {
+  if (c->kprof_ev.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& ke : c->kprof_ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ke.a, ke.b) == cudaSuccess) c->kprof_ms[ke.kc] += ms;
+    else cudaGetLastError();
+    c->ev_pool.push_back(ke.a);
+    c->ev_pool.push_back(ke.b);
+  }
+  c->kprof_ev.clear();
 }
 
 static void prof_collect(hps_ctx* c) {
@@ -423,6 +468,10 @@ int hps_destroy(hps_ctx* c) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
   }
+  for (auto& ke : c->kprof_ev) {
+    cudaEventDestroy(ke.a);
+    cudaEventDestroy(ke.b);
+  }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return HPS_OK;
@@ -785,6 +834,46 @@ int hps_profile_read(hps_ctx* c, double* ms, long long* launches, long long* cal
   }
   return HPS_OK;
 }
+
+int hps_profile_kernels(hps_ctx* c, int enable) {
+  CHECK_CTX(c);
+  kprof_collect(c);
+  if (enable) {
+    for (int i = 0; i < HPS_NKC; ++i) {
+      c->kprof_ms[i] = c->kprof_bytes[i] = c->kprof_flops[i] = 0.0;
+      c->kprof_launch[i] = 0;
+    }
+  }
+  c->kprof = enable != 0;
+  return HPS_OK;
+}
+
+int hps_profile_kernels_read(hps_ctx* c, double* ms, long long* launches, double* bytes, double* flops) {
+  CHECK_CTX(c);
+  kprof_collect(c);
+  for (int i = 0; i < HPS_NKC; ++i) {
+    if (ms) ms[i] = c->kprof_ms[i];
+    if (launches) launches[i] = c->kprof_launch[i];
+    if (bytes) bytes[i] = c->kprof_bytes[i];
+    if (flops) flops[i] = c->kprof_flops[i];
+  }
+  return HPS_OK;
+}
+
+int hps_set_autotune(hps_ctx* c, int mode) {
+  CHECK_CTX(c);
+  if (mode != HPS_TUNE_OFF && mode != HPS_TUNE_ON && (mode < HPS_TUNE_FORCE || mode >= HPS_TUNE_FORCE + 64))
+    return fail(c, HPS_EINVAL, "mode: HPS_TUNE_OFF, HPS_TUNE_ON or HPS_TUNE_FORCE + i (0 <= i < 64)");
+  if (mode != c->tune) {
+    c->tune = mode;
+    ++c->vc_gen;  // the V-cycle graph holds the old launch configurations: capture it again
+  }
+  return HPS_OK;
+}
+
+int hps_autotune_table(char* buf, int len) { return autotune_table(buf, len); }
+
+void hps_autotune_clear(void) { autotune_clear(); }
 
 int hps_build_leaves_batch(hps_ctx** ctxs, int n, int precision) {
   if (!ctxs || n < 1) return HPS_EINVAL;

@@ -131,6 +131,7 @@ template <typename R> struct GemmArgs {
   long long ws_elems = 0;
   int num_sms = 148;
   int* err = nullptr;    // device flag for the tensor-core path's bounded waits; null: SIMT only
+  int tune = 0;          // host only: the tile autotuner's mode for this launch (HPS_TUNE_*)
 };
 
 // FP32 complex GEMM on the tensor cores (tc.cu): batched like launch_gemm, for tiles of
@@ -142,6 +143,10 @@ cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kma
 // and multiplied as hi*hi + hi*lo + lo*hi of bf16 splits (about 3 * 2^-16 relative error).
 cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
                                  cudaStream_t s);
+// The tile autotuner's process-wide table (tc.cu): as text into buf (NUL-terminated, at most
+// len bytes), returning the number of shapes; and emptied.
+int autotune_table(char* buf, int len);
+void autotune_clear();
 // TL[P][row tile][k chunk] = 128 x 8 complex blocks of the operators A_P (rows x K, leading
 // dimension lda, pair P at A + P * pair_stride), each contiguous in the tensor-core tile order,
 // zero-padded past rows and K.

@@ -206,6 +206,20 @@ struct hps_ctx {
   double prof_ms[HPS_NPHASE] = {0};
   long long prof_launch[HPS_NPHASE] = {0};
   long long prof_calls[HPS_NPHASE] = {0};
+  int cur_phase = -1;  // the innermost open PhaseScope's phase (-1: none)
+  // kernel-class timing (hps_profile_kernels): events around each launch of a class
+  struct KernEv {
+    int kc;
+    cudaEvent_t a, b;
+  };
+  bool kprof = false;
+  std::vector<KernEv> kprof_ev;
+  double kprof_ms[HPS_NKC] = {0}, kprof_bytes[HPS_NKC] = {0}, kprof_flops[HPS_NKC] = {0};
+  long long kprof_launch[HPS_NKC] = {0};
+  // tile autotuner mode (hps_set_autotune); the V-cycle key of the last uncaptured tuning pass
+  int tune = HPS_TUNE_OFF;
+  long long tune_pass_gen = -1;
+  int tune_pass_nrhs = 0, tune_pass_k = -1, tune_pass_gamma = 0;
 };
 
 namespace hps {
@@ -250,8 +264,19 @@ struct PhaseScope {
   int ph;
   cudaEvent_t a = nullptr;
   long long* prev;
+  int prev_phase;
   PhaseScope(hps_ctx* ctx, int phase);
   ~PhaseScope();
+};
+// With kernel-class timing on and the context's stream not capturing, brackets the launches
+// made in its scope with CUDA events on the context's stream and credits their algorithmic
+// bytes and flops to the class.
+struct KernScope {
+  hps_ctx* c;
+  int kc;
+  cudaEvent_t a = nullptr;
+  KernScope(hps_ctx* ctx, int kclass, double bytes, double flops);
+  ~KernScope();
 };
 }  // namespace hps
 

@@ -87,6 +87,13 @@ cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long
   a.ws_elems = (long long)c->gemm_ws_elems;
   a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
   a.err = c->d_gemm_err;  // FP32 GEMMs may take the tensor cores (their waits report through it)
+  a.tune = c->tune;
+  if (c->kprof && c->cur_phase == HPS_PH_MERGE) {
+    const double e = (double)sizeof(c_t<R>) * nb;
+    const double bytes = e * ((double)mmax * kmax + (double)kmax * nmax + (C0 ? 2.0 : 1.0) * mmax * nmax);
+    KernScope ks(c, HPS_KC_MERGE_GEMM, bytes, 8.0 * mmax * nmax * kmax * nb);
+    return launch_gemm<R>(a, mmax, nmax, c->stream, kmax);
+  }
   return launch_gemm<R>(a, mmax, nmax, c->stream, kmax);
 }
 
@@ -113,6 +120,13 @@ cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, con
   a.ws_elems = (long long)c->gemm_ws_elems;
   a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
   a.err = c->d_gemm_err;
+  a.tune = c->tune;
+  if (c->kprof) {
+    // algorithmic bytes: the operator (8 B per complex entry in both formats), B, C0, C once each
+    const double bytes = 8.0 * nb * ((double)mmax * kmax + (double)kmax * nmax + (C0 ? 2.0 : 1.0) * mmax * nmax);
+    KernScope ks(c, HPS_KC_SWEEP, bytes, 8.0 * mmax * nmax * kmax * nb);
+    return launch_tc_gemm_tiled(a, mmax, nmax, kmax, bf16x3, a.err, c->stream);
+  }
   return launch_tc_gemm_tiled(a, mmax, nmax, kmax, bf16x3, a.err, c->stream);
 }
 
@@ -883,9 +897,22 @@ int mg_apply_df(hps_ctx* c, const float4* rho_es, float2* z_es, int nrhs, int k)
       return body();
     }
   }
+  const bool recapture =
+      !(c->mg_exec && c->mg_nrhs == nrhs && c->mg_k == k && c->mg_gamma == c->gamma && c->mg_gen == c->vc_gen);
+  if (recapture && c->tune == HPS_TUNE_ON &&
+      !(c->tune_pass_gen == c->vc_gen && c->tune_pass_nrhs == nrhs && c->tune_pass_k == k &&
+        c->tune_pass_gamma == c->gamma)) {
+    // one direct application first, so that the autotuner times this V-cycle's shapes (it
+    // cannot while they are captured); the next application captures the tuned launches
+    c->tune_pass_gen = c->vc_gen;
+    c->tune_pass_nrhs = nrhs;
+    c->tune_pass_k = k;
+    c->tune_pass_gamma = c->gamma;
+    return body();
+  }
   HPS_CK(c, cudaEventRecord(c->gs_in, st));
   HPS_CK(c, cudaStreamWaitEvent(c->gs, c->gs_in, 0));
-  if (!(c->mg_exec && c->mg_nrhs == nrhs && c->mg_k == k && c->mg_gamma == c->gamma && c->mg_gen == c->vc_gen)) {
+  if (recapture) {
     if (c->mg_exec) cudaGraphExecDestroy(c->mg_exec);
     c->mg_exec = nullptr;
     // one capture at a time in the process (contexts of several host threads)

@@ -25,7 +25,14 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
 
+#include "../../include/hps.h"
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -899,15 +906,17 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TB::TCOLS) : "memory");
 }
 
+// cpsm persistent CTAs per SM (1 or 2); split K while there are fewer tiles than split_mult x
+// the CTAs (0: never)
 template <int NC>
-cudaError_t launch_tcb(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+cudaError_t launch_tcb(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s, int cpsm,
+                       int split_mult) {
   const int gx = (nmax + NC - 1) / NC, gy = (mmax + TC_M - 1) / TC_M;
   const long long tiles = (long long)gx * gy * a.nbatch;
-  // persistent CTAs, two per SM; split K while there are fewer tiles than CTAs
-  const long long slots = 2LL * a.num_sms;
+  const long long slots = (long long)cpsm * a.num_sms, target = split_mult * slots;
   int ksplit = 1;
-  if (kmax >= 8 * TC_KC && a.ws && tiles < slots) {
-    ksplit = (int)((slots + tiles - 1) / tiles);
+  if (kmax >= 8 * TC_KC && a.ws && tiles < target) {
+    ksplit = (int)((target + tiles - 1) / tiles);
     ksplit = ksplit < kmax / (4 * TC_KC) ? ksplit : kmax / (4 * TC_KC);
     ksplit = ksplit < 16 ? ksplit : 16;
     while (ksplit > 1 && (long long)ksplit * a.nbatch * mmax * nmax > a.ws_elems) --ksplit;
@@ -931,13 +940,14 @@ cudaError_t launch_tcb(const GemmArgs<float>& a, int mmax, int nmax, int kmax, i
 template <int NC>
 constexpr size_t tc_gemm_smem() { return (size_t)2 * TcTile<NC>::STAGE * sizeof(float) + 1024; }
 
+// split K until about split_mult CTAs per SM are busy (a CTA streams its k range serially;
+// 0: never split)
 template <int NC, bool PIPE>
-cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s,
+                      int split_mult) {
   const int gx = (nmax + NC - 1) / NC, gy = (mmax + TC_M - 1) / TC_M;
   const long long blocks = (long long)gx * gy * a.nbatch;
-  // split K until about three (pipelined kernel: two) CTAs per SM are busy (a CTA streams its
-  // k range serially)
-  const long long target = (PIPE ? 2LL : 3LL) * a.num_sms;
+  const long long target = (long long)split_mult * a.num_sms;
   int ksplit = 1;
   if (kmax >= 8 * TC_KC && a.ws && blocks < target) {
     ksplit = (int)((target + blocks - 1) / blocks);
@@ -962,27 +972,174 @@ cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, in
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- tile autotuner
+// A launch configuration of one kernel family: column-tile width nc (complex columns), CTAs per
+// SM of the persistent bf16x3 kernel, and the split-K target (multiples of the CTAs or SMs).
+// Candidate 0 of every list is the fixed heuristic (HPS_TUNE_OFF).
+enum TuneFamily { TF_TC = 0, TF_TCS = 1, TF_TCB = 2 };
+const char* const kFamilyName[3] = {"tc", "tcs", "tcb"};
+struct TuneCand {
+  int nc, cpsm, split;
+};
+
+// the narrowest column tile of the family that covers nmax in one tile
+int natural_nc(int fam, int nmax) {
+  if (fam == TF_TCB) return nmax <= 16 ? 16 : 32;
+  return nmax <= 16 ? 16 : nmax <= 32 ? 32 : 64;
+}
+
+std::vector<TuneCand> tune_candidates(int fam, int nmax) {
+  const int nc0 = natural_nc(fam, nmax), nc1 = nc0 / 2;  // half-width tiles: twice the tiles
+  std::vector<TuneCand> v;
+  if (fam == TF_TCB) {
+    v = {{nc0, 2, 1}, {nc0, 2, 0}, {nc0, 1, 1}, {nc0, 2, 2}};
+    if (nc1 >= 16) {
+      v.push_back({nc1, 2, 1});
+      v.push_back({nc1, 2, 0});
+    }
+  } else {
+    const int def = fam == TF_TCS ? 2 : 3;
+    v = {{nc0, 1, def}, {nc0, 1, 0}, {nc0, 1, 2 * def}};
+    if (nc1 >= 16) {
+      v.push_back({nc1, 1, def});
+      v.push_back({nc1, 1, 0});
+    }
+  }
+  return v;
+}
+
+cudaError_t run_candidate(int fam, const TuneCand& t, const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err,
+                          cudaStream_t s) {
+  if (fam == TF_TCB) {
+    if (t.nc == 16) return launch_tcb<16>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
+    return launch_tcb<32>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
+  }
+  if (a.nbatch > 65535) return cudaErrorInvalidValue;
+  if (fam == TF_TCS) {
+    if (t.nc == 16) return launch_tc<16, true>(a, mmax, nmax, kmax, err, s, t.split);
+    if (t.nc == 32) return launch_tc<32, true>(a, mmax, nmax, kmax, err, s, t.split);
+    return launch_tc<64, true>(a, mmax, nmax, kmax, err, s, t.split);
+  }
+  if (t.nc == 16) return launch_tc<16, false>(a, mmax, nmax, kmax, err, s, t.split);
+  if (t.nc == 32) return launch_tc<32, false>(a, mmax, nmax, kmax, err, s, t.split);
+  return launch_tc<64, false>(a, mmax, nmax, kmax, err, s, t.split);
+}
+
+using TuneKey = std::tuple<int, int, int, int, int, int>;  // family, mmax, nmax, kmax, nbatch, SMs
+struct TuneEntry {
+  int idx;
+  float ms0, ms_best;  // two launches of candidate 0 and of the winner
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+
+// Times each candidate (one untimed launch, then two between events) and returns the winner;
+// -1 when a launch or the timing failed (nothing cached).
+int tune_shape(int fam, const std::vector<TuneCand>& cands, const GemmArgs<float>& a, int mmax, int nmax, int kmax,
+               int* err, cudaStream_t s, float& ms0, float& ms_best) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return -1;
+  }
+  int best = -1;
+  ms0 = ms_best = 0.f;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    if (run_candidate(fam, cands[i], a, mmax, nmax, kmax, err, s) != cudaSuccess) {
+      cudaGetLastError();
+      if (i == 0) break;  // the heuristic itself failed: leave the error to the caller's launch
+      continue;
+    }
+    cudaEventRecord(e0, s);
+    cudaError_t r = run_candidate(fam, cands[i], a, mmax, nmax, kmax, err, s);
+    if (r == cudaSuccess) r = run_candidate(fam, cands[i], a, mmax, nmax, kmax, err, s);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (r != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (i == 0) ms0 = ms;
+    if (best < 0 || ms < ms_best) {
+      best = (int)i;
+      ms_best = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+cudaError_t tuned_launch(int fam, const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
+  const std::vector<TuneCand> cands = tune_candidates(fam, nmax);
+  if (a.tune >= HPS_TUNE_FORCE)
+    return run_candidate(fam, cands[(size_t)(a.tune - HPS_TUNE_FORCE) % cands.size()], a, mmax, nmax, kmax, err, s);
+  if (a.tune != HPS_TUNE_ON) return run_candidate(fam, cands[0], a, mmax, nmax, kmax, err, s);
+  const TuneKey key{fam, mmax, nmax, kmax, a.nbatch, a.num_sms};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return run_candidate(fam, cands[it->second.idx], a, mmax, nmax, kmax, err, s);
+  }
+  // tuning re-runs the product: only outside capture, and only when C aliases neither input
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;
+  }
+  const void* c = a.C;
+  if (cs != cudaStreamCaptureStatusNone || c == (const void*)a.C0 || c == (const void*)a.B || c == (const void*)a.A)
+    return run_candidate(fam, cands[0], a, mmax, nmax, kmax, err, s);
+  float ms0 = 0.f, msb = 0.f;
+  const int best = tune_shape(fam, cands, a, mmax, nmax, kmax, err, s, ms0, msb);
+  if (best < 0) return run_candidate(fam, cands[0], a, mmax, nmax, kmax, err, s);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = TuneEntry{best, ms0, msb};
+  }
+  return run_candidate(fam, cands[best], a, mmax, nmax, kmax, err, s);  // the call's result is the winner's
+}
+
 }  // namespace
 
 cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
-  if (nmax <= 16) return launch_tc<16, false>(a, mmax, nmax, kmax, err, s);
-  if (nmax <= 32) return launch_tc<32, false>(a, mmax, nmax, kmax, err, s);
-  return launch_tc<64, false>(a, mmax, nmax, kmax, err, s);
+  return tuned_launch(TF_TC, a, mmax, nmax, kmax, err, s);
 }
 
 cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
                                  cudaStream_t s) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
-  if (bf16x3) {  // more than 32 columns: 32-column tiles side by side
-    if (nmax <= 16) return launch_tcb<16>(a, mmax, nmax, kmax, err, s);
-    return launch_tcb<32>(a, mmax, nmax, kmax, err, s);
-  }
+  if (bf16x3) return tuned_launch(TF_TCB, a, mmax, nmax, kmax, err, s);  // wide B: tiles side by side
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
-  if (nmax <= 16) return launch_tc<16, true>(a, mmax, nmax, kmax, err, s);
-  if (nmax <= 32) return launch_tc<32, true>(a, mmax, nmax, kmax, err, s);
-  return launch_tc<64, true>(a, mmax, nmax, kmax, err, s);
+  return tuned_launch(TF_TCS, a, mmax, nmax, kmax, err, s);
+}
+
+int autotune_table(char* buf, int len) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string out;
+  for (const auto& kv : g_tune) {
+    const auto& k = kv.first;
+    const TuneCand t = tune_candidates(std::get<0>(k), std::get<2>(k))[kv.second.idx];
+    char line[192];
+    snprintf(line, sizeof line, "%s m=%d n=%d k=%d batch=%d sms=%d -> #%d nc=%d cta/sm=%d split=%d; %.4f -> %.4f ms\n",
+             kFamilyName[std::get<0>(k)], std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k),
+             std::get<5>(k), kv.second.idx, t.nc, t.cpsm, t.split, kv.second.ms0 / 2, kv.second.ms_best / 2);
+    out += line;
+  }
+  if (buf && len > 0) {
+    const size_t n = out.size() < (size_t)(len - 1) ? out.size() : (size_t)(len - 1);
+    out.copy(buf, n);
+    buf[n] = 0;
+  }
+  return (int)g_tune.size();
+}
+
+void autotune_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
 }
 
 // Block (P, rt, kt) of the tiled layout and the entry w of that block for entry l of the whole

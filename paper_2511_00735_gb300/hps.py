@@ -29,6 +29,9 @@ SWEEP_BF16X3 = 1
 MV_DEFAULT = -1  # double-float Arnoldi matvec method (hps_set_arnoldi_matvec)
 MV_SIMT = 0
 MV_TENSOR = 1
+TUNE_OFF = 0
+TUNE_ON = 1
+TUNE_FORCE = 16  # + i: candidate i of every launch configuration list
 
 _STATUS = {0: "HPS_OK", -1: "HPS_EINVAL", -2: "HPS_ENOMEM", -3: "HPS_ENOTBUILT", -4: "HPS_ENOTCONV",
            -5: "HPS_ETIMEOUT", -6: "HPS_ECUDA", -7: "HPS_ENODEV", -8: "HPS_EUNSUPPORTED", -9: "HPS_ENUMERIC"}
@@ -40,9 +43,11 @@ EXPORTS = ["hps_create", "hps_destroy", "hps_set_allocator", "hps_last_error", "
            "hps_precond_apply", "hps_gmres_solve", "hps_kernel_launches", "hps_profile", "hps_profile_read",
            "hps_leaf_maps_noalloc", "hps_build_leaves_batch", "hps_release_workspace",
            "hps_set_outer_arith", "hps_set_gamma", "hps_volume_solution", "hps_set_sweep_arith",
-           "hps_set_arnoldi_matvec", "hps_skel_matvec_mixed"]
+           "hps_set_arnoldi_matvec", "hps_skel_matvec_mixed", "hps_profile_kernels", "hps_profile_kernels_read",
+           "hps_set_autotune", "hps_autotune_table", "hps_autotune_clear"]
 
 PHASES = ["leaf", "merge", "rhs", "matvec", "precond", "ortho", "other"]
+KERNEL_CLASSES = ["sweep", "merge_gemm"]
 
 
 class HPSError(RuntimeError):
@@ -104,6 +109,11 @@ def load_library(path: str = LIB_PATH):
         "hps_set_arnoldi_matvec": (i, [vp, i]),
         "hps_skel_matvec_mixed": (i, [vp, vp, vp, i]),
         "hps_volume_solution": (i, [vp, vp, vp, vp, i, vp]),
+        "hps_profile_kernels": (i, [vp, i]),
+        "hps_profile_kernels_read": (i, [vp, vp, vp, vp, vp]),
+        "hps_set_autotune": (i, [vp, i]),
+        "hps_autotune_table": (i, [C.c_char_p, i]),
+        "hps_autotune_clear": (None, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +298,22 @@ class Solver:
         self._check(self.lib.hps_profile_read(self.h, _ptr(ms), _ptr(la), _ptr(ca)))
         return {ph: (float(ms[i]), int(la[i]), int(ca[i])) for i, ph in enumerate(PHASES)}
 
+    def profile_kernels(self, enable: bool = True):
+        """Bracket every launch of the kernel classes (KERNEL_CLASSES) with CUDA events."""
+        self._check(self.lib.hps_profile_kernels(self.h, int(bool(enable))))
+
+    def profile_kernels_read(self):
+        """{class: (device ms, launches, algorithmic bytes, algorithmic flops)} since profile_kernels(True)."""
+        n = len(KERNEL_CLASSES)
+        ms, by, fl = np.zeros(n), np.zeros(n), np.zeros(n)
+        la = np.zeros(n, dtype=np.int64)
+        self._check(self.lib.hps_profile_kernels_read(self.h, _ptr(ms), _ptr(la), _ptr(by), _ptr(fl)))
+        return {k: (float(ms[i]), int(la[i]), float(by[i]), float(fl[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def set_autotune(self, mode: int):
+        """Tile autotuner of the tensor-core GEMMs: TUNE_OFF, TUNE_ON or TUNE_FORCE + i."""
+        self._check(self.lib.hps_set_autotune(self.h, int(mode)))
+
     # -- skeleton operators (device tensors [nrhs][n]) ------------------------
     def rhs(self, t):
         nrhs = t.shape[0]
@@ -385,3 +411,17 @@ def setup(solver: Solver, prob, precision: int = HPS_FP64, build: bool = True):
     t = np.stack([inputs.plane_wave_impedance(th, prob.kappa, prob.eta, bx, by, bnx, bny)
                   for th in prob.thetas])
     return np.ascontiguousarray(t)
+
+
+def autotune_table() -> str:
+    """The process-wide tile-autotuner table as text (one line per tuned GEMM shape)."""
+    lib = load_library()
+    n = lib.hps_autotune_table(None, 0)
+    buf = C.create_string_buffer(256 * (n + 1))
+    lib.hps_autotune_table(buf, len(buf))
+    return buf.value.decode()
+
+
+def autotune_clear():
+    """Empty the process-wide tile-autotuner table."""
+    load_library().hps_autotune_clear()

@@ -519,3 +519,114 @@ def test_64x64_N16_mixed_residual_in_fp64(solver):
     # the reported residual is the FP64 residual of the returned solution (summation order aside)
     assert np.max(np.abs(res - np.array(info["rel_residual"]))) <= 1e-15
     assert np.max(res) <= 1e-10 + 1e-15
+
+
+def _level_shapes(nx, q, L_exact):
+    """(pairs, n, m, p) of merge levels 1..L_exact of an nx x nx mesh: a child's boundary length n,
+    its interface length m (the merged side, alternately vertical and horizontal), p = n - m."""
+    a = b = 1
+    out = []
+    for lev in range(1, L_exact + 1):
+        n = 2 * (a + b) * q
+        m = (b if lev % 2 == 1 else a) * q
+        out.append(((nx * nx) >> lev, n, m, n - m))
+        if lev % 2 == 1:
+            a *= 2
+        else:
+            b *= 2
+    return out
+
+
+@pytest.mark.parametrize("cand", range(6))
+@pytest.mark.parametrize("sweep,nrhs", [(H.SWEEP_BF16X3, 32), (H.SWEEP_BF16X3, 48), (H.SWEEP_FP32, 32)])
+def test_autotune_every_candidate_vs_oracle(solver, cand, sweep, nrhs):
+    """Every launch configuration the tile autotuner can pick (forced with TUNE_FORCE + i: column
+    tiles of half width, one CTA per SM, no or twice the k split) for the merge GEMMs and the sweep
+    products of the 16x16, N=8 tree: the V-cycle against the oracle's to the tolerance of the
+    default configuration (the candidates differ only in tiling and in the k summation order)."""
+    prob = inputs.single_bump(16, 8, 20.0, 1, seed=9, L_exact=6)
+    op = OracleProblem(prob)
+    H.setup(solver, prob, H.HPS_MIXED)
+    solver.set_sweep_arith(sweep)
+    solver.set_autotune(H.TUNE_FORCE + cand)
+    try:
+        solver.merge_levels(prob.L_exact)
+        r = np.random.default_rng(100 + cand).standard_normal((nrhs, op.mesh.n_skel)) * (1 - 0.5j)
+        z = host(solver.precond_apply(dev(r), inner_iters=4))
+    finally:
+        solver.set_autotune(H.TUNE_OFF)
+        solver.set_sweep_arith(H.SWEEP_DEFAULT)
+    tree = MergeTree(op.mesh, op.Ts, None, prob.L_exact)
+    tol = 2e-5 if sweep == H.SWEEP_FP32 else 2e-5 + 2 * 2 * prob.L_exact * BF16X3_PRODUCT
+    for k in (0, nrhs - 1):
+        assert rel(z[k], tree.mg(r[k], "gmres", 4)) < tol, (cand, k)
+
+
+def test_autotune_on_tunes_once_and_solves(solver):
+    """TUNE_ON on the 32x32, N=16, kappa=60 tree with 32 RHS: the merges and the first V-cycle tune
+    their GEMM shapes (the table gains tc and tcb entries), a second tree build and V-cycle add none,
+    the tuned V-cycle agrees with the untuned one within twice the FP32/bf16x3 tree's error bound,
+    and FGMRES reaches the FP64 residual 1e-10 within one iteration of the untuned solve."""
+    prob = inputs.single_bump(32, 16, 60.0, 32, seed=5, L_exact=8)
+    t = H.setup(solver, prob, H.HPS_MIXED)
+    r = np.random.default_rng(81).standard_normal((32, solver.n_skel)) * (1 + 0.2j)
+    H.autotune_clear()
+    z, its = {}, {}
+    try:
+        for mode in (H.TUNE_OFF, H.TUNE_ON):
+            solver.set_autotune(mode)
+            solver.merge_levels(prob.L_exact)
+            z[mode] = host(solver.precond_apply(dev(r), inner_iters=prob.inner_iters))
+            g, info = solver.gmres_solve(t, tol=1e-10, inner_iters=prob.inner_iters, restart=20)
+            assert info["converged"] == 32 and info["max_rel_residual"] <= 1e-10, mode
+            its[mode] = info["outer_iterations"]
+        table = H.autotune_table()
+        n_shapes = len(table.splitlines())
+        assert any(line.startswith("tcb ") for line in table.splitlines()), table
+        assert any(line.startswith("tc ") for line in table.splitlines()), table
+        solver.merge_levels(prob.L_exact)
+        solver.precond_apply(dev(r), inner_iters=prob.inner_iters)
+        assert len(H.autotune_table().splitlines()) == n_shapes
+    finally:
+        solver.set_autotune(H.TUNE_OFF)
+    tol = 2 * (2e-5 + 2 * 2 * prob.L_exact * BF16X3_PRODUCT)
+    for k in (0, 17, 31):
+        assert rel(z[H.TUNE_ON][k], z[H.TUNE_OFF][k]) < tol, k
+    assert abs(its[H.TUNE_ON] - its[H.TUNE_OFF]) <= 1, its
+
+
+def test_profile_kernels_sweep_and_merge_classes(solver):
+    """hps_profile_kernels on the 16x16, N=8 mixed tree (bf16x3 sweeps on all six levels) with 24
+    RHS: two direct V-cycles bracket 2 x 2 x 6 sweep launches whose algorithmic bytes are the
+    operators U [2p x 2m] and Dm [2m x 2n] of every pair at 8 B per complex entry plus B, C0 (up-sweep
+    only) and C at 8 B per entry each; the tree build brackets its merge GEMMs with positive flops;
+    launches captured into the solve's V-cycle graph are not bracketed."""
+    prob = inputs.single_bump(16, 8, 20.0, 1, seed=9, L_exact=6)
+    t = H.setup(solver, prob, H.HPS_MIXED)
+    nrhs = 24
+    r = np.random.default_rng(3).standard_normal((nrhs, solver.n_skel)) + 0j
+    solver.profile_kernels(True)
+    try:
+        solver.merge_levels(prob.L_exact)
+        for _ in range(2):
+            solver.precond_apply(dev(r), inner_iters=3)
+        d = solver.profile_kernels_read()
+    finally:
+        solver.profile_kernels(False)
+    want = 0.0
+    for npairs, n, m, p in _level_shapes(16, prob.N - 1, prob.L_exact):
+        want += 8.0 * npairs * (2 * p * 2 * m + 2 * m * nrhs + 2 * 2 * p * nrhs)  # up: C0 and C of 2p rows
+        want += 8.0 * npairs * (2 * m * 2 * n + 2 * n * nrhs + 2 * m * nrhs)      # down
+    ms, launches, nbytes, flops = d["sweep"]
+    assert launches == 2 * 2 * prob.L_exact and ms > 0
+    assert nbytes == pytest.approx(2 * want, rel=1e-12)
+    ms_m, launches_m, _, flops_m = d["merge_gemm"]
+    assert launches_m > 0 and flops_m > 0 and ms_m > 0
+    # a solve replays the V-cycle as a graph: none of its sweep launches is bracketed
+    solver.profile_kernels(True)
+    try:
+        solver.gmres_solve(t, tol=1e-10, inner_iters=3, restart=20)
+        d2 = solver.profile_kernels_read()
+    finally:
+        solver.profile_kernels(False)
+    assert d2["sweep"][1] == 0
