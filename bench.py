@@ -666,7 +666,8 @@ def run_phase(args):
     """One phase of a workload in isolation, for ncu: `leaf` (R leaf builds), `merge` (leaves, then
     R merge-tree builds), `matvec` (R FP64 skeleton matvecs), `mixed_matvec` (R of the mixed
     path's Arnoldi matvecs, --mv tensor|simt), `precond` (R preconditioner
-    applications) or `solve` (one full step).  --nx 32 runs the 32x32, N = 16, kappa = 50 problem."""
+    applications), `solve` (one FGMRES solve on a built tree) or `step` (R whole bench steps
+    after one untimed step).  --nx 32 runs the 32x32, N = 16, kappa = 50 problem."""
     import torch
 
     from paper_2511_00735_gb300 import hps as H
@@ -718,6 +719,22 @@ def run_phase(args):
             prof.start()
             for _ in range(args.repeat):
                 s.matvec_mixed(x)
+        elif args.phase == "step":
+            # one whole bench step (coefficient, leaves, merges, FGMRES) after one untimed step
+            X, Y = s.node_coords()
+            b = torch.from_numpy(np.ascontiguousarray(inputs.eval_b(prob.bumps, X, Y))).cuda()
+
+            def one():
+                s.set_coeff(prob.kappa, b, prob.eta)
+                s.build_leaves(prec)
+                s.merge_levels(prob.L_exact)
+                return s.gmres_solve(td, tol=args.tol, inner_iters=prob.inner_iters, restart=args.restart,
+                                     max_outer=args.max_outer, raise_on_notconv=False)[1]
+            one()
+            torch.cuda.synchronize()
+            prof.start()
+            for _ in range(args.repeat):
+                info = one()
         elif args.phase == "precond":
             s.merge_levels(prob.L_exact)
             r = torch.randn((prob.nrhs, s.n_skel), dtype=torch.complex128, device="cuda")
@@ -776,7 +793,8 @@ def main():
                     help="scattering128 (default) / scattering64: the timed step above; batch: the 512-problem "
                          "mix; serve: a Poisson stream; table1: the memory-time trade-off over exact levels and "
                          "coarse steps; phase: one phase in isolation (for profilers)")
-    ap.add_argument("--phase", default="leaf", choices=["leaf", "merge", "matvec", "mixed_matvec", "precond", "solve"])
+    ap.add_argument("--phase", default="leaf",
+                    choices=["leaf", "merge", "matvec", "mixed_matvec", "precond", "solve", "step"])
     ap.add_argument("--mv", default="tensor", choices=["tensor", "simt"], help="phase mixed_matvec: method")
     ap.add_argument("--nx", type=int, default=0, help="phase: element grid (0: 128)")
     ap.add_argument("--repeat", type=int, default=1, help="phase: repetitions")

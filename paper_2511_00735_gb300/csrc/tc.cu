@@ -83,12 +83,51 @@ __device__ __forceinline__ void a_elem(int e, int& r, int& kc) {
   kc = (cm % KG) * 2 + (w & 1);
 }
 
+// Complex entry (kc, nc) of a TC_KC x NC chunk of B handled for index l.  Within the 32
+// consecutive l of one warp instruction, lane bits 0-1 give nc % 4, bit 2 gives kc % 2 and bits
+// 3-4 give nc / 4 % 4; with b_rows' row order the warp's 8-byte B' stores then cover all 16
+// bank pairs twice (the minimum of 2 wavefronts; 32 consecutive nc gave 8), and its loads still
+// read 16 consecutive columns of two rows.
+__device__ __forceinline__ void b_elem(int l, int NC, int& kc, int& nc) {
+  const int w = l >> 5, ln = l & 31, ncq = NC >> 4;
+  nc = (ln & 3) | ((ln >> 3) << 2) | ((w % ncq) << 4);
+  kc = ((ln >> 2) & 1) | ((w / ncq) << 1);
+}
+
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
   const float r = x - __uint_as_float(hi);
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
 }
 
+
+// The B' tiles of complex (kc, nc) = v: real column 2nc gets (Re b, -Im b), column 2nc+1 gets
+// (Im b, Re b) at real k = 2kc, 2kc+1; lanes with bit 3 set store the odd row first, so that
+// each store instruction mixes even and odd rows (see b_elem).
+__device__ __forceinline__ void b_rows(float* Bh, float* Bl, int kc, int nc, float2 v, int l) {
+  uint2 h0, l0, h1, l1;
+  split_tf32(v.x, h0.x, l0.x);
+  split_tf32(-v.y, h0.y, l0.y);
+  split_tf32(v.y, h1.x, l1.x);
+  h1.y = h0.x;
+  l1.y = l0.x;
+  // row 2nc + 1 lies 16 bytes (4 floats) after row 2nc in the same core matrix
+  const uint32_t sw = (l >> 3) & 1;
+  const uint32_t oa = core_off(2 * nc, 2 * kc) / 4 + 4 * sw, ob = oa + 4 - 8 * sw;
+  uint2 ha, la, hb, lb;
+  ha.x = sw ? h1.x : h0.x;
+  ha.y = sw ? h1.y : h0.y;
+  hb.x = sw ? h0.x : h1.x;
+  hb.y = sw ? h0.y : h1.y;
+  la.x = sw ? l1.x : l0.x;
+  la.y = sw ? l1.y : l0.y;
+  lb.x = sw ? l0.x : l1.x;
+  lb.y = sw ? l0.y : l1.y;
+  *reinterpret_cast<uint2*>(Bh + oa) = ha;
+  *reinterpret_cast<uint2*>(Bl + oa) = la;
+  *reinterpret_cast<uint2*>(Bh + ob) = hb;
+  *reinterpret_cast<uint2*>(Bl + ob) = lb;
+}
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
   asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
@@ -149,7 +188,8 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
     }
 #pragma unroll
     for (int u = 0; u < B_PER; ++u) {
-      const int l = tid + u * TC_NT, kc = l / NC, nc = l % NC;
+      int kc, nc;
+      b_elem(tid + u * TC_NT, NC, kc, nc);
       const int gk = k0 + kc, gj = col0 + nc;
       float2 v = make_float2(0.f, 0.f);
       if (gk < kk && gj < n) {
@@ -187,23 +227,12 @@ __global__ void __launch_bounds__(TC_NT, 3) tc_gemm_kernel(GemmArgs<float> a, in
       *reinterpret_cast<uint2*>(Ah + off) = h;
       *reinterpret_cast<uint2*>(Al + off) = lo;
     }
-    // B': complex (kc, nc) -> real column 2nc gets (Re b, -Im b), column 2nc+1 gets (Im b, Re b)
-    // at real k = 2kc, 2kc+1
+    // B': the fetched complex entries split into the hi/lo tiles
 #pragma unroll
     for (int u = 0; u < B_PER; ++u) {
-      const int l = tid + u * TC_NT, kc = l / NC, nc = l % NC;
-      const float2 v = rb[u];
-      uint2 h0, l0, h1, l1;
-      split_tf32(v.x, h0.x, l0.x);
-      split_tf32(-v.y, h0.y, l0.y);
-      split_tf32(v.y, h1.x, l1.x);
-      h1.y = h0.x;
-      l1.y = l0.x;
-      const uint32_t o0 = core_off(2 * nc, 2 * kc) / 4, o1 = core_off(2 * nc + 1, 2 * kc) / 4;
-      *reinterpret_cast<uint2*>(Bh + o0) = h0;
-      *reinterpret_cast<uint2*>(Bl + o0) = l0;
-      *reinterpret_cast<uint2*>(Bh + o1) = h1;
-      *reinterpret_cast<uint2*>(Bl + o1) = l1;
+      int kc, nc;
+      b_elem(tid + u * TC_NT, NC, kc, nc);
+      b_rows(Bh, Bl, kc, nc, rb[u], tid + u * TC_NT);
     }
     if (kt + 1 < nk) fetch(kt + 1);  // in flight while this chunk is multiplied
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -419,21 +448,11 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
       reinterpret_cast<uint2*>(Ah)[o] = h;
       reinterpret_cast<uint2*>(Al)[o] = lo;
     }
-    // B': complex (kc, nc) -> real column 2nc gets (Re b, -Im b), column 2nc+1 gets (Im b, Re b)
+    // B': the raw chunk (row-major TC_KC x NC complex) split into the hi/lo tiles
     for (int l = tid; l < TC_KC * NC; l += TCS_NT) {
-      const int kc2 = l / NC, nc = l % NC;
-      const float2 v = *reinterpret_cast<const float2*>(rap + TCP_ARAW + l * 8);
-      uint2 h0, l0, h1, l1;
-      split_tf32(v.x, h0.x, l0.x);
-      split_tf32(-v.y, h0.y, l0.y);
-      split_tf32(v.y, h1.x, l1.x);
-      h1.y = h0.x;
-      l1.y = l0.x;
-      const uint32_t o0 = core_off(2 * nc, 2 * kc2) / 4, o1 = core_off(2 * nc + 1, 2 * kc2) / 4;
-      *reinterpret_cast<uint2*>(Bh + o0) = h0;
-      *reinterpret_cast<uint2*>(Bl + o0) = l0;
-      *reinterpret_cast<uint2*>(Bh + o1) = h1;
-      *reinterpret_cast<uint2*>(Bl + o1) = l1;
+      int kc2, nc;
+      b_elem(l, NC, kc2, nc);
+      b_rows(Bh, Bl, kc2, nc, *reinterpret_cast<const float2*>(rap + TCP_ARAW + (kc2 * NC + nc) * 8), l);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -734,6 +753,13 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
     }
   } else if (warp <= 3) {
     // ---------------- B splitters ----------------
+    // Thread ct takes the chunk's entries l = ct + 64 u (BPT of them): it loads all of them
+    // before it stores any, so their shared-memory latencies overlap.  Entry l is complex
+    // (kc, nc) with, for lane bits ln = l % 32 and w = l / 32, nc % 4 = ln % 4, kc % 4 = ln / 4 % 4,
+    // nc / 4 % 2 = ln / 16 and the rest of nc and kc from w; a lane with ln / 16 = 1 stores its
+    // odd B'^T row first.  Each store instruction of a warp then writes 32 distinct banks
+    // (bank ((2nc + row parity) % 8) * 4 + kc % 4).
+    constexpr int BPT = TC_KC * NC / 64, NCW = NC / 8;
     const int ct = tid - 64;
     long long g = 0;
     bool ok = true;
@@ -750,19 +776,30 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         const float2* raw = reinterpret_cast<const float2*>(sp + A_BYTES);
         unsigned char* bh = sp + A_BYTES + BRAW;
         unsigned char* bl = bh + BT;
+        const int sw = lane >> 4;
+        float2 v[BPT];
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+          const int w = (ct + 64 * u) >> 5;
+          const int nc = (lane & 3) | (sw << 2) | ((w % NCW) << 3), kc2 = ((lane >> 2) & 3) | ((w / NCW) << 2);
+          v[u] = raw[kc2 * NC + nc];
+        }
         // complex (kc, nc) -> B'^T row 2nc: (Re b, -Im b), row 2nc+1: (Im b, Re b) at real k 2kc, 2kc+1
-        for (int l = ct; l < TC_KC * NC; l += 64) {
-          const int kc2 = l / NC, nc = l % NC;
-          const float2 v = raw[l];
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+          const int w = (ct + 64 * u) >> 5;
+          const int nc = (lane & 3) | (sw << 2) | ((w % NCW) << 3), kc2 = ((lane >> 2) & 3) | ((w / NCW) << 2);
           uint32_t rh, rl, ih, il;
-          split_bf16(v.x, rh, rl);
-          split_bf16(v.y, ih, il);
+          split_bf16(v[u].x, rh, rl);
+          split_bf16(v[u].y, ih, il);
           const uint32_t nh = ih ^ 0x8000u, nl = il ^ 0x8000u;  // bf16 split of -Im b
-          const uint32_t o0 = core_off16(2 * nc, 2 * kc2), o1 = core_off16(2 * nc + 1, 2 * kc2);
-          *reinterpret_cast<uint32_t*>(bh + o0) = rh | (nh << 16);
-          *reinterpret_cast<uint32_t*>(bl + o0) = rl | (nl << 16);
-          *reinterpret_cast<uint32_t*>(bh + o1) = ih | (rh << 16);
-          *reinterpret_cast<uint32_t*>(bl + o1) = il | (rl << 16);
+          const uint32_t e_h = rh | (nh << 16), e_l = rl | (nl << 16), o_h = ih | (rh << 16), o_l = il | (rl << 16);
+          // row 2nc + 1 lies 16 bytes after row 2nc in the same core matrix
+          const uint32_t oa = core_off16(2 * nc, 2 * kc2) + 16u * sw, ob = oa + 16u - 32u * sw;
+          *reinterpret_cast<uint32_t*>(bh + oa) = sw ? o_h : e_h;
+          *reinterpret_cast<uint32_t*>(bl + oa) = sw ? o_l : e_l;
+          *reinterpret_cast<uint32_t*>(bh + ob) = sw ? e_h : o_h;
+          *reinterpret_cast<uint32_t*>(bl + ob) = sw ? e_l : o_l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
