@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
   } else if (warp <= 1 + OZ_SLICERS) {
     // ---------------- column exponents and B' slices ----------------
     const int tb = tid - 64;
+    constexpr int SPT = ((OZ_KR / 2) * NC + 32 * OZ_SLICERS - 1) / (32 * OZ_SLICERS);  // entries per thread
     long long g = 0;
     int ie = 0;
     bool ok = true;
@@ -328,19 +329,32 @@ __global__ void __launch_bounds__(OZ_NT, 1) ozk_matvec_kernel(const uint16_t* __
           break;
         }
         unsigned char* sb = ring + (size_t)st * STAGE + A_REGION;
-        // complex (kk, r) of the chunk -> B'^T rows 2r: (Re, -Im), 2r+1: (Im, Re) at real k 2kk, 2kk+1
-        for (int l = tb; l < (OZ_KR / 2) * NC; l += 32 * OZ_SLICERS) {
-          const int kk = l / NC, r = rr, k = c * (OZ_KR / 2) + kk;
-          const float2 v = (k < nb && r < nrhs) ? zs[k * nrhs + r] : make_float2(0.f, 0.f);
-          uint16_t re[OZ_S], im[OZ_S];
-          slice7f(v.x, F, re);
-          slice7f(v.y, F, im);
+        // complex (kk, r) of the chunk -> B'^T rows 2r: (Re, -Im), 2r+1: (Im, Re) at real k 2kk, 2kk+1;
+        // a thread loads all its entries (l = tb + 32 OZ_SLICERS u) before it slices any, so the
+        // loads and the independent slicing chains overlap
+        float2 v[SPT];
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+          const int l = tb + 32 * OZ_SLICERS * u, kk = l / NC, k = c * (OZ_KR / 2) + kk;
+          v[u] = (l < (OZ_KR / 2) * NC && k < nb && rr < nrhs) ? zs[k * nrhs + rr] : make_float2(0.f, 0.f);
+        }
+        uint16_t re[SPT][OZ_S], im[SPT][OZ_S];
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+          slice7f(v[u].x, F, re[u]);
+          slice7f(v[u].y, F, im[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < SPT; ++u) {
+          const int l = tb + 32 * OZ_SLICERS * u;
+          if (l >= (OZ_KR / 2) * NC) break;
+          const int kk = l / NC, r = rr;
           const uint32_t o0 = core_off16(2 * r, 2 * kk), o1 = core_off16(2 * r + 1, 2 * kk);
 #pragma unroll
           for (int t = 0; t < OZ_S; ++t) {
             unsigned char* bt = sb + t * B_SLICE;
-            *reinterpret_cast<uint32_t*>(bt + o0) = (uint32_t)re[t] | ((uint32_t)(im[t] ^ 0x8000u) << 16);
-            *reinterpret_cast<uint32_t*>(bt + o1) = (uint32_t)im[t] | ((uint32_t)re[t] << 16);
+            *reinterpret_cast<uint32_t*>(bt + o0) = (uint32_t)re[u][t] | ((uint32_t)(im[u][t] ^ 0x8000u) << 16);
+            *reinterpret_cast<uint32_t*>(bt + o1) = (uint32_t)im[u][t] | ((uint32_t)re[u][t] << 16);
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
