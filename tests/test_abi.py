@@ -66,3 +66,19 @@ def test_plain_c_consumer(libpath, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip() in ("no device", "device")
+
+
+def test_autotune_table_and_null_context_without_device(libpath):
+    # the tuning table is process-wide host state: empty until a tensor-core GEMM is tuned, and
+    # readable (count only, or into a buffer cut to its length) without a device; the per-context
+    # calls reject a null context
+    lib = ctypes.CDLL(libpath)
+    lib.hps_autotune_clear.restype = None
+    lib.hps_autotune_clear()
+    assert lib.hps_autotune_table(None, 0) == 0
+    buf = ctypes.create_string_buffer(b"x" * 16)
+    assert lib.hps_autotune_table(buf, 16) == 0
+    assert buf.value == b""
+    assert lib.hps_set_autotune(None, 1) == -1
+    assert lib.hps_profile_kernels(None, 1) == -1
+    assert lib.hps_profile_kernels_read(None, None, None, None, None) == -1
