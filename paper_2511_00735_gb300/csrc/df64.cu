@@ -29,6 +29,19 @@ inline int nblocks(long long work, int cap) {
   return (int)(b > cap ? cap : b);
 }
 
+// Blocks of `kernel` (threads per block, dynamic shared memory) that the current device runs at
+// once: one full wave.  Streaming kernels sized to whole waves leave no partly filled last wave.
+template <typename K>
+int full_wave(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1 || sms < 1) {
+    cudaGetLastError();
+    return 0;  // unknown: the caller keeps its own count
+  }
+  return per * sms;
+}
+
 using dfops::dot2;
 using dfops::fast2;
 using dfops::two_sum;
@@ -400,7 +413,12 @@ __global__ void __launch_bounds__(NT2, 3) df_dots2_partial_kernel(const float4* 
   }
 }
 
-int df_dots2_blocks(long long rows) { return bdot_blocks(rows); }
+// at most bdot_blocks(rows) (the partial buffers are sized by it) and at most one full wave, so
+// that the vector groups (blockIdx.y) run in whole waves
+int df_dots2_blocks(long long rows) {
+  const int b = bdot_blocks(rows), w = full_wave(df_dots2_partial_kernel, NT2, 0);
+  return w > 0 && w < b ? w : b;
+}
 
 cudaError_t df_dots2(const float4* V, long long vstride, int nvec, const float4* y0, const float4* y1, long long rows,
                      int nrhs, float4* partial, double2* out, cudaStream_t s) {
@@ -454,8 +472,10 @@ __global__ void df_update2_kernel(const float4* __restrict__ V, long long vstrid
 
 cudaError_t df_update2(const float4* V, long long vstride, int nvec, const float4* vt, const float4* w,
                        const float4* coef, float4* out_v, float4* out_w, long long rows, int nrhs, cudaStream_t s) {
-  df_update2_kernel<<<nblocks(rows * nrhs, 4096), NT, 0, s>>>(V, vstride, nvec, vt, w, coef, out_v, out_w, rows,
-                                                             nrhs);
+  // grid-stride over the elements with one full wave of blocks
+  const int wave = full_wave(df_update2_kernel, NT, 0);
+  df_update2_kernel<<<nblocks(rows * nrhs, wave > 0 ? wave : 4096), NT, 0, s>>>(V, vstride, nvec, vt, w, coef, out_v,
+                                                                                 out_w, rows, nrhs);
   note_launch();
   return cudaGetLastError();
 }
