@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(256, 1) leaf_kernel(LeafParams p) {
 // ---------------------------------------------------------------------------
 constexpr int IR_MAX = 10;
 constexpr int TB = 16;     // row block of the triangular solves
+constexpr int TBL = TB + 1;  // row stride of a stored diagonal-block inverse (staggered banks)
 constexpr int PB = 16;     // panel width of the FP32 L D L^T
 constexpr int IR_NT = 512;  // threads per CTA
 
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
   float2* swd = sKd + n1 * n1;                         // [n1] weights in double-float
   float2* cwd = swd + n1;                              // [n1*n1] c h^2/4 w_i w_j of this element, double-float
   float2* sDe = cwd + n1 * n1;                         // [2][n1] rows 0 and N of D in double-float
+  float* Binv = reinterpret_cast<float*>(sDe + 2 * n1);  // [ceil(ni/TB)][TB][TBL] inverses of U's diagonal blocks
   const int tid = threadIdx.x, nth = blockDim.x;
   double* A = p.Ascr + (long long)blockIdx.x * nb * nb;
   // the refinement's iterate Z in double-float (the FP64 scratch holds the pairs)
@@ -423,6 +425,27 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
         __syncthreads();
       }
     }
+    // ---- inverses of U's TB x TB diagonal blocks (unit lower): thread (block, column c)
+    //      solves U_bb x = e_c by forward substitution; zero outside the block's rows ----
+    for (int l = tid; l < (ni + TB - 1) / TB * TB; l += nth) {
+      const int b = l / TB, c = l % TB, r0 = b * TB, nr = min(TB, ni - r0);
+      float x[TB];
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        float v = t == c ? 1.f : 0.f;
+        if (t > c && t < nr) {
+          const float* Ut = Lp + pk(r0 + t, r0);
+#pragma unroll
+          for (int u = 0; u < t; ++u)
+            if (u >= c) v -= Ut[u] * x[u];
+        }
+        x[t] = v;
+      }
+      float* Bi = Binv + b * TB * TBL;
+#pragma unroll
+      for (int t = 0; t < TB; ++t) Bi[t * TBL + c] = (t < nr && c < nr) ? x[t] : 0.f;
+    }
+    __syncthreads();
     // ---- refinement: Z <- Z + (L D L^T)^{-1} (L~_iG - L~_ii Z) ----
     double rel_prev = 1.0;
     bool done = false;
@@ -522,26 +545,25 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
             *yo = v;
           }
           __syncthreads();
-          if (tid < nb) {
-            float yb[TB];
+          {
+            // the block's triangle through its stored inverse: warp w takes columns 4w .. 4w + 3,
+            // eight lanes per column, lane rows t0 and t0 + 8 (the column is read by its eight
+            // lanes before any of them writes: the warp is synchronised in between)
+            const int col = 4 * (tid / 32) + (tid % 32) / 8, t0 = tid % 8;
+            const bool cv = col < nb;
+            const float* Bi = Binv + (r0 / TB) * TB * TBL;
+            float yv[TB];
 #pragma unroll
-            for (int t = 0; t < TB; ++t) yb[t] = t < nr ? Y[(r0 + t) * ldy + tid] : 0.f;
+            for (int u = 0; u < TB; ++u) yv[u] = (cv && u < nr) ? Y[(r0 + u) * ldy + col] : 0.f;
+            float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-            for (int t = 1; t < TB; ++t) {
-              if (t < nr) {
-                const float* Ut = Lp + pk(r0 + t, r0);
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int u = 0; u < t; u += 2) {
-                  s0 += Ut[u] * yb[u];
-                  if (u + 1 < t) s1 += Ut[u + 1] * yb[u + 1];
-                }
-                yb[t] -= s0 + s1;
-              }
+            for (int u = 0; u < TB; ++u) {
+              if (u <= t0) o0 = fmaf(Bi[t0 * TBL + u], yv[u], o0);
+              if (u <= t0 + 8) o1 = fmaf(Bi[(t0 + 8) * TBL + u], yv[u], o1);
             }
-#pragma unroll
-            for (int t = 0; t < TB; ++t)
-              if (t < nr) Y[(r0 + t) * ldy + tid] = yb[t];
+            __syncwarp();
+            if (cv && t0 < nr) Y[(r0 + t0) * ldy + col] = o0;
+            if (cv && t0 + 8 < nr) Y[(r0 + t0 + 8) * ldy + col] = o1;
           }
           __syncthreads();
         }
@@ -550,8 +572,9 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
           Y[I * ldy + l % nb] /= Lp[pk(I, I)];
         }
         __syncthreads();
-        for (int r1 = ni; r1 > 0; r1 -= TB) {
-          const int r0 = max(0, r1 - TB), nr = r1 - r0;
+        // the same row blocks as the forward pass (their inverses are stored), last first
+        for (int bb = (ni + TB - 1) / TB - 1; bb >= 0; --bb) {
+          const int r0 = bb * TB, nr = min(TB, ni - r0), r1 = r0 + nr;
           if (r1 < ni && gact && gr < nr) {
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
@@ -566,23 +589,23 @@ __global__ void __launch_bounds__(IR_NT, 1) leaf_ir_kernel(LeafParams p) {
             *xo = v;
           }
           __syncthreads();
-          if (tid < nb) {
-            float xb[TB];
+          {
+            // U_bb^T x = y through the transposed inverse, laid out as in the forward pass
+            const int col = 4 * (tid / 32) + (tid % 32) / 8, t0 = tid % 8;
+            const bool cv = col < nb;
+            const float* Bi = Binv + (r0 / TB) * TB * TBL;
+            float xv[TB];
 #pragma unroll
-            for (int t = 0; t < TB; ++t) xb[t] = t < nr ? Y[(r0 + t) * ldy + tid] : 0.f;
+            for (int u = 0; u < TB; ++u) xv[u] = (cv && u < nr) ? Y[(r0 + u) * ldy + col] : 0.f;
+            float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-            for (int t = TB - 2; t >= 0; --t) {
-              float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-              for (int u = t + 1; u < TB; u += 2) {
-                if (u < nr) s0 += Lp[pk(r0 + u, r0 + t)] * xb[u];
-                if (u + 1 < TB && u + 1 < nr) s1 += Lp[pk(r0 + u + 1, r0 + t)] * xb[u + 1];
-              }
-              xb[t] -= s0 + s1;
+            for (int u = 0; u < TB; ++u) {
+              if (u >= t0) o0 = fmaf(Bi[u * TBL + t0], xv[u], o0);
+              if (u >= t0 + 8) o1 = fmaf(Bi[u * TBL + t0 + 8], xv[u], o1);
             }
-#pragma unroll
-            for (int t = 0; t < TB; ++t)
-              if (t < nr) Y[(r0 + t) * ldy + tid] = xb[t];
+            __syncwarp();
+            if (cv && t0 < nr) Y[(r0 + t0) * ldy + col] = o0;
+            if (cv && t0 + 8 < nr) Y[(r0 + t0 + 8) * ldy + col] = o1;
           }
           __syncthreads();
         }
@@ -1029,7 +1052,7 @@ size_t leaf_ir_smem_bytes(int N) {
   const int q = N - 1, ni = q * q, nb = 4 * q, n1 = N + 1;
   const size_t reg0 = std::max((size_t)ir_npk_pad(ni) * 4 + (size_t)ni * ir_ldy(nb) * 4, (size_t)nb * 2 * nb * 16);
   return (reg0 + 15) / 16 * 16 + sizeof(double) * (3 * n1 * n1 + n1 + 2 * (IR_NT / 32)) +
-         sizeof(float2) * (2 * n1 * n1 + 3 * n1);
+         sizeof(float2) * (2 * n1 * n1 + 3 * n1) + sizeof(float) * (size_t)((ni + TB - 1) / TB) * TB * TBL;
 }
 
 namespace {
