@@ -211,7 +211,7 @@ void free_numeric(hps_ctx* c) {
   for (auto& l : c->levels) {
     FREE(l.W); FREE(l.U); FREE(l.Dm); FREE(l.Ut); FREE(l.Dmt);
   }
-  FREE(c->coarse.Winv); FREE(c->coarse.d_desc);
+  FREE(c->coarse.Winv); FREE(c->coarse.d_desc); FREE(c->coarse.Tt);
   FREE(c->gemm_ws); c->gemm_ws_elems = 0;
   FREE(c->ws_X1); FREE(c->ws_X2); FREE(c->d_piv); FREE(c->d_lu);
   FREE(c->sw_x); FREE(c->ws_G); FREE(c->d_eye);
@@ -237,6 +237,7 @@ void free_tree(hps_ctx* c) {
   c->stages.clear();
   c->levels.clear();
   FREE(c->coarse.d_cdesc); FREE(c->coarse.d_cnb); FREE(c->coarse.d_upos); FREE(c->coarse.d_ucnb);
+  FREE(c->coarse.d_tcdesc);
   c->coarse = Coarse();
   FREE(c->plan_map0);
   c->plan_L = -1;

@@ -139,9 +139,12 @@ template <typename R> struct GemmArgs {
 cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s);
 // The same product with A stored tiled by tile_operator (descriptor a_r = the pair's first unit
 // of the tiled layout, a_c = its k chunks; lda = the rows the layout was tiled with, the same
-// for every pair of the launch, while a descriptor's m may be smaller); bf16x3: A tiled by tile_operator_bf16x3
-// and multiplied as hi*hi + hi*lo + lo*hi of bf16 splits (about 3 * 2^-16 relative error).
-cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
+// for every pair of the launch, while a descriptor's m may be smaller).  terms = 0: FP32 blocks
+// (tile_operator), 3xTF32; terms = 2: A tiled by tile_operator_bf16x3 and multiplied as
+// hi*hi + hi*lo + lo*hi of bf16 splits (about 3 * 2^-16 relative error); terms = 3: A tiled by
+// tile_operator_bf16x6, the six products of three-term bf16 splits with term indices summing to
+// at most 2 (about FP32 accuracy).
+cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int terms, int* err,
                                  cudaStream_t s);
 // The tile autotuner's process-wide table (tc.cu): as text into buf (NUL-terminated, at most
 // len bytes), returning the number of shapes; and emptied.
@@ -155,6 +158,10 @@ cudaError_t tile_operator(float2* TL, const float2* A, int npairs, int rows, int
 // The same blocks as bf16 hi and lo tiles (hi = bf16(x), lo = bf16(x - hi)) in the 16-bit
 // core-matrix order; a block occupies the same 8 KB.
 cudaError_t tile_operator_bf16x3(float2* TL, const float2* A, int npairs, int rows, int K, int lda,
+                                 long long pair_stride, cudaStream_t s);
+// The same blocks as three bf16 term tiles (hi, mid = bf16(x - hi), lo = bf16(x - hi - mid)):
+// 12 bytes per entry, 1.5 times the FP32 layout's bytes (block offsets scale the same way).
+cudaError_t tile_operator_bf16x6(void* TL, const float2* A, int npairs, int rows, int K, int lda,
                                  long long pair_stride, cudaStream_t s);
 constexpr int TILE_M = 128, TILE_K = 8;  // rows and complex k of one operator block
 // Tiled operator layout (tile_operator, tile_operator_bf16x3): per pair, row tile rt and k

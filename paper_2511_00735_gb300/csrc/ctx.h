@@ -62,6 +62,10 @@ struct Coarse {
   int* d_ucnb = nullptr;     // [n_int] stage row across from unknown u
   void* Winv = nullptr;      // exact coarse: [n_int][2 n_int] -> right half = M_c^{-1}
   GemmDesc* d_desc = nullptr;  // exact coarse: the one GEMM descriptor
+  // FP32 tree with bf16 sweeps: each subdomain's T_int,int tiled as three-term bf16 blocks (the
+  // coarse GMRES products at FP32 accuracy on the sweep kernel), and its tiled descriptors
+  void* Tt = nullptr;
+  GemmDesc* d_tcdesc = nullptr;
   bool exact = false;
   std::vector<int> upos_h, ucnb_h;  // host copies of d_upos, d_ucnb (exact coarse assembly)
 };

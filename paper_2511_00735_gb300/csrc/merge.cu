@@ -100,7 +100,7 @@ cudaError_t gemm(hps_ctx* c, const GemmDesc* d, int nb, const void* A, long long
 // The sweep products of a tiled level (FP32 tree): A = the tiled operator, tensor cores.
 cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, const void* B, long long ldb,
                        const void* C0, long long ldc0, void* C, long long ldc, double alpha, const int* maps, int mmax,
-                       int nmax, int n_launch, int kmax, bool bf16x3) {
+                       int nmax, int n_launch, int kmax, int terms) {
   GemmArgs<float> a;
   a.A = static_cast<const float2*>(A);
   a.B = static_cast<const float2*>(B);
@@ -121,13 +121,13 @@ cudaError_t gemm_tiled(hps_ctx* c, const GemmDesc* d, int nb, const void* A, con
   a.num_sms = c->num_sms > 0 ? c->num_sms : 148;
   a.err = c->d_gemm_err;
   a.tune = c->tune;
-  if (c->kprof) {
+  if (c->kprof && terms != 3) {  // the sweep products (the coarse products take terms = 3)
     // algorithmic bytes: the operator (8 B per complex entry in both formats), B, C0, C once each
     const double bytes = 8.0 * nb * ((double)mmax * kmax + (double)kmax * nmax + (C0 ? 2.0 : 1.0) * mmax * nmax);
     KernScope ks(c, HPS_KC_SWEEP, bytes, 8.0 * mmax * nmax * kmax * nb);
-    return launch_tc_gemm_tiled(a, mmax, nmax, kmax, bf16x3, a.err, c->stream);
+    return launch_tc_gemm_tiled(a, mmax, nmax, kmax, terms, a.err, c->stream);
   }
-  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, bf16x3, a.err, c->stream);
+  return launch_tc_gemm_tiled(a, mmax, nmax, kmax, terms, a.err, c->stream);
 }
 
 // sweep operators kept tiled for the tensor cores (FP32 tree): every level with bf16x3 sweeps;
@@ -476,6 +476,18 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
       }
     cc.n_int = (int)upos.size();
     for (int u = 0; u < cc.n_int; ++u) ucnb.push_back(cnb[upos[u]]);
+    {
+      // the same products on the tiled operators: a_r = the subdomain's first unit, a_c = its k chunks
+      const long long units = tiled_pair_units(max_int, max_int);
+      if ((long long)Sc.nsub * units > 0x7fffffffLL) return fail(c, HPS_EUNSUPPORTED, "tiled coarse operator size");
+      std::vector<GemmDesc> tcd(cdesc);
+      for (int s2 = 0; s2 < Sc.nsub; ++s2) {
+        tcd[s2].a_r = (int)(s2 * units);
+        tcd[s2].a_c = (max_int + TILE_K - 1) / TILE_K;
+      }
+      cc.d_tcdesc = dev_upload(c, tcd);
+      if (!cc.d_tcdesc) return fail(c, HPS_ENOMEM, "coarse descriptors");
+    }
     cc.d_cdesc = dev_upload(c, cdesc);
     cc.d_cnb = dev_upload(c, cnb);
     cc.d_upos = dev_upload(c, upos);
@@ -547,6 +559,16 @@ int build_tree_t(hps_ctx* c, int L_exact, int exact) {
       HPS_CK(c, cudaStreamSynchronize(c->stream));
       dev_free(c, piv);
       dev_free(c, lu);
+    }
+    if (sizeof(R) == 4 && !cc.exact && c->sweep_bf16x3 && cc.max_int > 0) {
+      // the coarse GMRES streams T_int,int once per step: keep it tiled in three bf16 terms
+      // (12 bytes per entry) for the sweep kernel's six-product path
+      const size_t bytes = (size_t)Sc.nsub * tiled_pair_units(cc.max_int, cc.max_int) * TILE_UNIT * 12;
+      cc.Tt = dev_alloc(c, bytes);
+      if (!cc.Tt) return fail(c, HPS_ENOMEM, "tiled coarse operator");
+      HPS_CK(c, tile_operator_bf16x6(cc.Tt, static_cast<const float2*>(Sc.T), Sc.nsub, cc.max_int, cc.max_int, Sc.n,
+                                     (long long)Sc.n * Sc.n, c->stream));
+      ++c->vc_gen;
     }
   }
   int flag = 0;
@@ -743,8 +765,12 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
     HPS_CK(c, cg_pass<R>(CG_START, p, st));
     for (int j = 0; j < k; ++j) {
       p.j = j;
-      HPS_CK(c, gemm<R>(c, cc.d_cdesc, Sc.nsub, Sc.T, Sc.n, w, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int,
-                        nrhs, nrhs, cc.max_int));
+      if (cc.Tt)
+        HPS_CK(c, gemm_tiled(c, cc.d_tcdesc, Sc.nsub, cc.Tt, w, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int,
+                             nrhs, nrhs, cc.max_int, 3));
+      else
+        HPS_CK(c, gemm<R>(c, cc.d_cdesc, Sc.nsub, Sc.T, Sc.n, w, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int,
+                          nrhs, nrhs, cc.max_int));
       HPS_CK(c, cg_pass<R>(CG_APPLY, p, st));
       HPS_CK(c, cg_pass<R>(CG_PROJECT, p, st));
       HPS_CK(c, cg_pass<R>(CG_CLOSE, p, st));
@@ -761,8 +787,12 @@ int coarse_solve(hps_ctx* c, int nrhs, int k) {
   HPS_CK(c, bscale<R>(V, w, nrm, nullptr, rows, nrhs, st));
   for (int j = 0; j < k; ++j) {
     C* Vj = V + j * vs;
-    HPS_CK(c, gemm<R>(c, cc.d_cdesc, Sc.nsub, Sc.T, Sc.n, Vj, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int, nrhs,
-                      nrhs, cc.max_int));
+    if (cc.Tt)
+      HPS_CK(c, gemm_tiled(c, cc.d_tcdesc, Sc.nsub, cc.Tt, Vj, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int, nrhs,
+                           nrhs, cc.max_int, 3));
+    else
+      HPS_CK(c, gemm<R>(c, cc.d_cdesc, Sc.nsub, Sc.T, Sc.n, Vj, nrhs, nullptr, 0, W, nrhs, 1.0, nullptr, cc.max_int,
+                        nrhs, nrhs, cc.max_int));
     HPS_CK(c, swap_add<R>(w, Vj, W, cc.d_cnb, rows, nrhs, st));
     HPS_CK(c, bdot<R>(V, vs, j + 1, w, rows, nrhs, part, h1, 0, st));
     HPS_CK(c, (bupdate<R, R>(w, V, vs, j + 1, h1, rows, nrhs, R(-1), st)));
@@ -797,7 +827,7 @@ int mg_level(hps_ctx* c, int l, int nrhs, int k) {
   // up-sweep: rho'_E = rho_E - U f
   if (Lv.Ut)
     HPS_CK(c, gemm_tiled(c, Lv.d_tsdesc + SUP * NP, NP, Lv.Ut, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
-                         Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m, c->sweep_bf16x3));
+                         Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m, c->sweep_bf16x3 ? 2 : 0));
   else
     HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SUP * NP, NP, Lv.U, 2 * m, P0.vec, nrhs, P0.vec, nrhs, P1.vec, nrhs, -1.0,
                       Lv.d_dst, 2 * p, nrhs, nrhs, 2 * m));
@@ -826,7 +856,7 @@ int mg_level(hps_ctx* c, int l, int nrhs, int k) {
   HPS_CK(c, (scatter_rows<R, R>(v0, static_cast<const C*>(P1.vec), Lv.d_up, (long long)P1.nsub * P1.n, nrhs, st)));
   if (Lv.Dmt)
     HPS_CK(c, gemm_tiled(c, Lv.d_tsdesc + SDN * NP, NP, Lv.Dmt, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
-                         2 * m, nrhs, nrhs, 2 * n, c->sweep_bf16x3));
+                         2 * m, nrhs, nrhs, 2 * n, c->sweep_bf16x3 ? 2 : 0));
   else
     HPS_CK(c, gemm<R>(c, Lv.d_sdesc + SDN * NP, NP, Lv.Dm, 2 * n, v0, nrhs, nullptr, 0, c->sw_x, nrhs, 1.0, nullptr,
                       2 * m, nrhs, nrhs, 2 * n));

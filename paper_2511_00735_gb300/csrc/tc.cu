@@ -554,13 +554,16 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
 // tensor memory is released.
 constexpr int TCB_NT = 256;  // 8 warps
 
-template <int NC> struct TcbTile {
-  static constexpr int S = NC <= 16 ? 6 : 5;             // stages
+// TERMS = 2: x = hi + lo (bf16x3, 3 products); TERMS = 3: x = hi + mid + lo, the products with
+// term indices i + j <= 2 (6 products, about FP32 accuracy: "bf16x6")
+template <int NC, int TERMS = 2> struct TcbTile {
+  static constexpr int S = TERMS == 3 ? (NC <= 16 ? 4 : 3) : (NC <= 16 ? 6 : 5);  // stages
   static constexpr int NR = 2 * NC;                      // real output columns
-  static constexpr int A_BYTES = TC_M * TC_KR * 2 * 2;    // bf16 hi + lo tiles of one block (8 KB)
+  static constexpr int A_TILE = TC_M * TC_KR * 2;         // one bf16 term tile of a block (4 KB)
+  static constexpr int A_BYTES = TERMS * A_TILE;          // the block's term tiles
   static constexpr int BRAW = TC_KC * NC * 8;             // raw complex B chunk
   static constexpr int BT = NR * TC_KR * 2;               // one bf16 B' tile
-  static constexpr int STAGE = A_BYTES + BRAW + 2 * BT;   // a multiple of 1024
+  static constexpr int STAGE = A_BYTES + BRAW + TERMS * BT;  // a multiple of 1024
   static constexpr int TCOLS = 2 * NR < 32 ? 32 : 2 * NR; // two accumulators
   // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
   static constexpr uint32_t IDESC =
@@ -570,12 +573,25 @@ template <int NC> struct TcbTile {
   static constexpr size_t SMEM = (size_t)S * STAGE + EPI + 1024;
 };
 static_assert(TcbTile<16>::STAGE % 1024 == 0 && TcbTile<32>::STAGE % 1024 == 0, "stage alignment");
+static_assert(TcbTile<16, 3>::STAGE % 1024 == 0 && TcbTile<32, 3>::STAGE % 1024 == 0, "stage alignment");
+static_assert(2 * TcbTile<16, 3>::SMEM <= 228 * 1024 && 2 * TcbTile<32, 3>::SMEM <= 228 * 1024, "two CTAs per SM");
 static_assert(TcbTile<16>::A_BYTES == TC_M * TC_KC * 8, "a bf16x3 block occupies one FP32 block");
 
 __device__ __forceinline__ void split_bf16(float x, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
   hi = __bfloat16_as_ushort(h);
   lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));  // x - h is exact in FP32
+}
+// x = t[0] + t[1] + ... + t[TERMS - 1] + r in bf16 terms, each the rounding of what the previous
+// ones leave (every difference is exact in FP32); |r| <= 2^-(8 TERMS) |x| about
+template <int TERMS>
+__device__ __forceinline__ void split_terms(float x, uint32_t (&t)[TERMS]) {
+#pragma unroll
+  for (int i = 0; i < TERMS; ++i) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    t[i] = __bfloat16_as_ushort(h);
+    x -= __bfloat162float(h);
+  }
 }
 
 // tile t of a persistent launch: row tile, column tile, batch entry and k split
@@ -601,11 +617,12 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs<float>& a, int NC, 
   return ti;
 }
 
-template <int NC>
+template <int NC, int TERMS>
 __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, int* err, int ksplit, int kc,
                                                              int mmax, int nmax, int gx, int gy, int ntiles) {
-  using TB = TcbTile<NC>;
+  using TB = TcbTile<NC, TERMS>;
   constexpr int NR = TB::NR, STAGE = TB::STAGE, A_BYTES = TB::A_BYTES, BRAW = TB::BRAW, BT = TB::BT;
+  constexpr int A_TILE = TB::A_TILE;
   constexpr int TCB_S = TB::S;
   constexpr int G = NR / 16;  // 16-column groups of an accumulator
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -661,9 +678,11 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
       if (!ti.live) continue;
       const GemmDesc d = a.desc[ti.bb];
       int rows_blk;  // rows stored in this row tile's blocks (a multiple of 8)
-      const float2* Ab =
-          a.A + ((long long)d.a_r + tiled_block_unit((int)a.lda, d.a_c, ti.rt, ti.kb / TC_KC, rows_blk)) * TILE_UNIT;
-      const uint32_t half = (uint32_t)rows_blk * (TC_KR * 2);  // bytes of the block's hi (and of its lo) tile
+      // the tiled layout in bytes: an entry takes TERMS 4-byte words (a unit: 64 entries)
+      const char* Ab = reinterpret_cast<const char*>(a.A) +
+                       ((long long)d.a_r + tiled_block_unit((int)a.lda, d.a_c, ti.rt, ti.kb / TC_KC, rows_blk)) *
+                           (TILE_UNIT * 4 * TERMS);
+      const uint32_t half = (uint32_t)rows_blk * (TC_KR * 2);  // bytes of one term tile of the block
       const int col0 = ti.ct * NC;
       for (int kt = 0; kt < ti.nk; ++kt, ++g) {
         const int st = (int)(g % TCB_S);
@@ -681,12 +700,12 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         const bool bulk_b = k0 + TC_KC <= ti.kk && !(d.kb2 > 0 && k0 < d.kb2 && k0 + TC_KC > d.kb2) &&
                             a.ldb == NC && col0 + NC <= ti.n && (reinterpret_cast<uintptr_t>(bsrc) & 15) == 0;
         if (lane == 0) {
-          // hi tile to the stage's first 4 KB, lo tile to the second; rows past a compact block
-          // keep stale values and only feed accumulator rows that are not stored
-          const char* src = reinterpret_cast<const char*>(Ab + (long long)kt * rows_blk * TC_KC);
-          expect_tx(&full[st], 2 * half + (bulk_b ? (uint32_t)BRAW : 0u));
-          bulk_copy(smem_u32(sp), src, half, &full[st]);
-          bulk_copy(smem_u32(sp) + A_BYTES / 2, src + half, half, &full[st]);
+          // term tile i to the stage's 4 KB slot i; rows past a compact block keep stale values
+          // and only feed accumulator rows that are not stored
+          const char* src = Ab + (long long)kt * rows_blk * TC_KC * 4 * TERMS;
+          expect_tx(&full[st], TERMS * half + (bulk_b ? (uint32_t)BRAW : 0u));
+#pragma unroll
+          for (int i = 0; i < TERMS; ++i) bulk_copy(smem_u32(sp) + i * A_TILE, src + i * half, half, &full[st]);
           if (bulk_b) bulk_copy(rb, bsrc, BRAW, &full[st]);
         }
         if (!bulk_b) {
@@ -733,11 +752,15 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = smem_u32(ring + (size_t)st * STAGE), sb = sa + A_BYTES + BRAW;
-          const uint64_t ah = smem_desc16(sa), al = smem_desc16(sa + A_BYTES / 2);
-          const uint64_t bh = smem_desc16(sb), bl = smem_desc16(sb + BT);
-          mma_bf16(acc, ah, bh, TB::IDESC, kt > 0 ? 1u : 0u);
-          mma_bf16(acc, ah, bl, TB::IDESC, 1u);
-          mma_bf16(acc, al, bh, TB::IDESC, 1u);
+          // the products of A term i and B term j with i + j < TERMS
+          bool first = kt == 0;
+#pragma unroll
+          for (int i = 0; i < TERMS; ++i)
+#pragma unroll
+            for (int j = 0; i + j < TERMS; ++j) {
+              mma_bf16(acc, smem_desc16(sa + i * A_TILE), smem_desc16(sb + j * BT), TB::IDESC, first ? 0u : 1u);
+              first = false;
+            }
           tc_commit(&empty[st]);
           issued = true;
         }
@@ -774,8 +797,7 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         }
         unsigned char* sp = ring + (size_t)st * STAGE;
         const float2* raw = reinterpret_cast<const float2*>(sp + A_BYTES);
-        unsigned char* bh = sp + A_BYTES + BRAW;
-        unsigned char* bl = bh + BT;
+        unsigned char* bh = sp + A_BYTES + BRAW;  // B' term tile j at bh + j BT
         const int sw = lane >> 4;
         float2 v[BPT];
 #pragma unroll
@@ -789,17 +811,18 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
         for (int u = 0; u < BPT; ++u) {
           const int w = (ct + 64 * u) >> 5;
           const int nc = (lane & 3) | (sw << 2) | ((w % NCW) << 3), kc2 = ((lane >> 2) & 3) | ((w / NCW) << 2);
-          uint32_t rh, rl, ih, il;
-          split_bf16(v[u].x, rh, rl);
-          split_bf16(v[u].y, ih, il);
-          const uint32_t nh = ih ^ 0x8000u, nl = il ^ 0x8000u;  // bf16 split of -Im b
-          const uint32_t e_h = rh | (nh << 16), e_l = rl | (nl << 16), o_h = ih | (rh << 16), o_l = il | (rl << 16);
+          uint32_t re[TERMS], im[TERMS];
+          split_terms<TERMS>(v[u].x, re);
+          split_terms<TERMS>(v[u].y, im);
           // row 2nc + 1 lies 16 bytes after row 2nc in the same core matrix
           const uint32_t oa = core_off16(2 * nc, 2 * kc2) + 16u * sw, ob = oa + 16u - 32u * sw;
-          *reinterpret_cast<uint32_t*>(bh + oa) = sw ? o_h : e_h;
-          *reinterpret_cast<uint32_t*>(bl + oa) = sw ? o_l : e_l;
-          *reinterpret_cast<uint32_t*>(bh + ob) = sw ? e_h : o_h;
-          *reinterpret_cast<uint32_t*>(bl + ob) = sw ? e_l : o_l;
+#pragma unroll
+          for (int j = 0; j < TERMS; ++j) {
+            // term j of -Im b is the sign flip of term j of Im b
+            const uint32_t e = re[j] | ((im[j] ^ 0x8000u) << 16), o = im[j] | (re[j] << 16);
+            *reinterpret_cast<uint32_t*>(bh + j * BT + oa) = sw ? o : e;
+            *reinterpret_cast<uint32_t*>(bh + j * BT + ob) = sw ? e : o;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -945,7 +968,7 @@ __global__ void __launch_bounds__(TCB_NT, 2) tcb_gemm_kernel(GemmArgs<float> a, 
 
 // cpsm persistent CTAs per SM (1 or 2); split K while there are fewer tiles than split_mult x
 // the CTAs (0: never)
-template <int NC>
+template <int NC, int TERMS>
 cudaError_t launch_tcb(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err, cudaStream_t s, int cpsm,
                        int split_mult) {
   const int gx = (nmax + NC - 1) / NC, gy = (mmax + TC_M - 1) / TC_M;
@@ -968,7 +991,8 @@ cudaError_t launch_tcb(const GemmArgs<float>& a, int mmax, int nmax, int kmax, i
   if (ntiles == 0) return cudaSuccess;
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = (int)(ntiles < slots ? ntiles : slots);
-  tcb_gemm_kernel<NC><<<grid, TCB_NT, TcbTile<NC>::SMEM, s>>>(a, err, ksplit, kc, mmax, nmax, gx, gy, (int)ntiles);
+  tcb_gemm_kernel<NC, TERMS><<<grid, TCB_NT, TcbTile<NC, TERMS>::SMEM, s>>>(a, err, ksplit, kc, mmax, nmax, gx, gy,
+                                                                            (int)ntiles);
   note_launch();
   if (ksplit > 1) return splitk_reduce(a, ksplit, mmax, nmax, s);
   return cudaGetLastError();
@@ -1013,22 +1037,22 @@ cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, in
 // A launch configuration of one kernel family: column-tile width nc (complex columns), CTAs per
 // SM of the persistent bf16x3 kernel, and the split-K target (multiples of the CTAs or SMs).
 // Candidate 0 of every list is the fixed heuristic (HPS_TUNE_OFF).
-enum TuneFamily { TF_TC = 0, TF_TCS = 1, TF_TCB = 2 };
-const char* const kFamilyName[3] = {"tc", "tcs", "tcb"};
+enum TuneFamily { TF_TC = 0, TF_TCS = 1, TF_TCB = 2, TF_TCB6 = 3 };
+const char* const kFamilyName[4] = {"tc", "tcs", "tcb", "tcb6"};
 struct TuneCand {
   int nc, cpsm, split;
 };
 
 // the narrowest column tile of the family that covers nmax in one tile
 int natural_nc(int fam, int nmax) {
-  if (fam == TF_TCB) return nmax <= 16 ? 16 : 32;
+  if (fam == TF_TCB || fam == TF_TCB6) return nmax <= 16 ? 16 : 32;
   return nmax <= 16 ? 16 : nmax <= 32 ? 32 : 64;
 }
 
 std::vector<TuneCand> tune_candidates(int fam, int nmax) {
   const int nc0 = natural_nc(fam, nmax), nc1 = nc0 / 2;  // half-width tiles: twice the tiles
   std::vector<TuneCand> v;
-  if (fam == TF_TCB) {
+  if (fam == TF_TCB || fam == TF_TCB6) {
     v = {{nc0, 2, 1}, {nc0, 2, 0}, {nc0, 1, 1}, {nc0, 2, 2}};
     if (nc1 >= 16) {
       v.push_back({nc1, 2, 1});
@@ -1048,8 +1072,12 @@ std::vector<TuneCand> tune_candidates(int fam, int nmax) {
 cudaError_t run_candidate(int fam, const TuneCand& t, const GemmArgs<float>& a, int mmax, int nmax, int kmax, int* err,
                           cudaStream_t s) {
   if (fam == TF_TCB) {
-    if (t.nc == 16) return launch_tcb<16>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
-    return launch_tcb<32>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
+    if (t.nc == 16) return launch_tcb<16, 2>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
+    return launch_tcb<32, 2>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
+  }
+  if (fam == TF_TCB6) {
+    if (t.nc == 16) return launch_tcb<16, 3>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
+    return launch_tcb<32, 3>(a, mmax, nmax, kmax, err, s, t.cpsm, t.split);
   }
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
   if (fam == TF_TCS) {
@@ -1146,10 +1174,11 @@ cudaError_t launch_tc_gemm(const GemmArgs<float>& a, int mmax, int nmax, int kma
   return tuned_launch(TF_TC, a, mmax, nmax, kmax, err, s);
 }
 
-cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, bool bf16x3, int* err,
+cudaError_t launch_tc_gemm_tiled(const GemmArgs<float>& a, int mmax, int nmax, int kmax, int terms, int* err,
                                  cudaStream_t s) {
   if (a.nbatch <= 0 || mmax <= 0 || nmax <= 0) return cudaSuccess;
-  if (bf16x3) return tuned_launch(TF_TCB, a, mmax, nmax, kmax, err, s);  // wide B: tiles side by side
+  if (terms == 2) return tuned_launch(TF_TCB, a, mmax, nmax, kmax, err, s);  // wide B: tiles side by side
+  if (terms == 3) return tuned_launch(TF_TCB6, a, mmax, nmax, kmax, err, s);
   if (a.nbatch > 65535) return cudaErrorInvalidValue;
   return tuned_launch(TF_TCS, a, mmax, nmax, kmax, err, s);
 }
@@ -1247,6 +1276,29 @@ __global__ void tile_operator_bf16x3_kernel(uint32_t* __restrict__ TL, const flo
   }
 }
 
+// bf16x6 blocks: [hi | mid | lo] tiles of the same layout, one word per entry in each
+__global__ void tile_operator_bf16x6_kernel(uint32_t* __restrict__ TL, const float2* __restrict__ A, int npairs,
+                                            int rows, int K, int lda, long long pair_stride, int nrt, int nkt,
+                                            long long pair_entries) {
+  const long long tot = (long long)npairs * pair_entries;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < tot; l += (long long)gridDim.x * blockDim.x) {
+    long long be;
+    int P, rt, kt, w;
+    tiled_entry(l, rows, nrt, nkt, pair_entries, be, P, rt, kt, w);
+    const int rows_blk = rt < nrt - 1 ? TC_M : tiled_last_rows(rows);
+    const int rg = w / 64, kg = (w % 64) / 32, wi = w % 32;
+    const int r = rg * 8 + wi / 4, kc = kg * 4 + wi % 4;
+    const int gi = rt * TC_M + r, gk = kt * TC_KC + kc;
+    const float2 x = (gi < rows && gk < K) ? A[(long long)P * pair_stride + (long long)gi * lda + gk] : make_float2(0.f, 0.f);
+    uint32_t re[3], im[3];
+    split_terms<3>(x.x, re);
+    split_terms<3>(x.y, im);
+    uint32_t* blk = TL + 3 * be;  // a block of e entries takes 3e words
+#pragma unroll
+    for (int i = 0; i < 3; ++i) blk[i * rows_blk * TC_KC + w] = re[i] | (im[i] << 16);
+  }
+}
+
 template <typename Kern, typename T>
 cudaError_t launch_tile(Kern kern, T* TL, const float2* A, int npairs, int rows, int K, int lda, long long pair_stride,
                         cudaStream_t s) {
@@ -1272,12 +1324,20 @@ cudaError_t tile_operator_bf16x3(float2* TL, const float2* A, int npairs, int ro
                      pair_stride, s);
 }
 
+cudaError_t tile_operator_bf16x6(void* TL, const float2* A, int npairs, int rows, int K, int lda,
+                                 long long pair_stride, cudaStream_t s) {
+  return launch_tile(tile_operator_bf16x6_kernel, static_cast<uint32_t*>(TL), A, npairs, rows, K, lda, pair_stride,
+                     s);
+}
+
 void optin_tc() {
   smem_optin(tc_gemm_kernel<16>);
   smem_optin(tc_gemm_kernel<32>);
   smem_optin(tc_gemm_kernel<64>);
-  smem_optin(tcb_gemm_kernel<16>);
-  smem_optin(tcb_gemm_kernel<32>);
+  smem_optin(tcb_gemm_kernel<16, 2>);
+  smem_optin(tcb_gemm_kernel<32, 2>);
+  smem_optin(tcb_gemm_kernel<16, 3>);
+  smem_optin(tcb_gemm_kernel<32, 3>);
   smem_optin(tcs_gemm_kernel<16>);
   smem_optin(tcs_gemm_kernel<32>);
   smem_optin(tcs_gemm_kernel<64>);
