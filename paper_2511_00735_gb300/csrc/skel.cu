@@ -516,11 +516,18 @@ cudaError_t lsq(c_t<R>* H, const R* beta, const R* floor, c_t<R>* y, c_t<R>* gws
 // ---------------------------------------------------------------------------
 constexpr int CG_GROUP = 16;
 
+// one block per rper rows, at most two per SM: a block loops over rows gridDim.x * rper apart, so
+// that the passes' two-level reductions handle a few hundred partials, not one per 8 rows
 int cg_pass_blocks(long long rows, int nrhs) {
   int rpad = 1;
   while (rpad < nrhs) rpad <<= 1;
   const long long rper = NT / rpad;
-  const long long b = (rows + rper - 1) / rper;
+  long long b = (rows + rper - 1) / rper;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    cudaGetLastError();  // unknown SM count: one block per rper rows
+  else if (sms > 0 && b > 2LL * sms)
+    b = 2LL * sms;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -532,13 +539,13 @@ __global__ void __launch_bounds__(NT) cg_pass_kernel(CgPass<R> p, int rpad) {
   __shared__ int is_last;
   const int r = threadIdx.x % rpad, lrow = threadIdx.x / rpad, rper = NT / rpad;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const long long row = (long long)blockIdx.x * rper + lrow;
   const int nvec = (MODE == CG_START || MODE == CG_CLOSE) ? 1 : p.j + 1;  // dot products per column
   const int nupd = (MODE == CG_PROJECT || MODE == CG_CLOSE) ? p.j + 1 : 0;
   C acc[CG_KMAX];
 #pragma unroll
   for (int i = 0; i < CG_KMAX; ++i) acc[i] = czero<R>();
-  if (r < p.nrhs && row < p.rows) {
+  for (long long row = (long long)blockIdx.x * rper + lrow; r < p.nrhs && row < p.rows;
+       row += (long long)gridDim.x * rper) {
     const long long l = row * p.nrhs + r;
     C x, vj = czero<R>();
     if (MODE == CG_START) {
