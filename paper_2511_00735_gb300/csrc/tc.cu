@@ -532,18 +532,20 @@ __global__ void __launch_bounds__(TCS_NT, 2) tcs_gemm_kernel(GemmArgs<float> a, 
 // real-expanded as in the FP32 kernels); the product accumulates hi*hi + hi*lo + lo*hi with
 // kind::f16 MMAs (bf16 inputs, FP32 accumulator in tensor memory).  hi + lo represents x to
 // 2^-16 relative and the dropped lo*lo term is below 2^-16, so each product carries a relative
-// error of about 3 * 2^-16 against the FP32 product.
+// error of about 3 * 2^-16 against the FP32 product.  The same kernel with three terms (hi, mid,
+// lo; "bf16x6") forms the six products whose term indices sum to at most 2 and keeps FP32
+// accuracy (the coarse GMRES operator products).
 //
 // Persistent and warp-specialised, 256 threads, two CTAs per SM:
 //   warp 0      producer: per k chunk one cp.async.bulk of the A block (completing on the
 //               stage's full barrier with its byte count) and cp.async of the raw B chunk
 //               (cp.async.mbarrier.arrive on the same barrier; one more bulk copy when the
 //               chunk is contiguous), up to S stages ahead;
-//   warp 1      one thread issues the chunk's three MMAs once its B tiles are split, commits
+//   warp 1      one thread issues the chunk's three (six) MMAs once its B tiles are split, commits
 //               them to the stage's empty barrier (the producer then refills the stage) and a
 //               tile's last chunk to its accumulator's full barrier; two accumulators in tensor
 //               memory alternate by tile, so a tile's epilogue overlaps the next tile's MMAs;
-//   warps 2-3   split the raw B chunk into the stage's bf16 hi/lo B' tiles;
+//   warps 2-3   split the raw B chunk into the stage's bf16 term B' tiles;
 //   warps 4-7   epilogue: warp w owns tensor-memory lanes 32 (w % 4) .. + 31 (its 32 output
 //               rows).  It copies the tile's C0 rows into its shared-memory staging
 //               asynchronously while the MMAs run, then combines them with the accumulator
@@ -1035,7 +1037,8 @@ cudaError_t launch_tc(const GemmArgs<float>& a, int mmax, int nmax, int kmax, in
 
 // ---------------------------------------------------------------- tile autotuner
 // A launch configuration of one kernel family: column-tile width nc (complex columns), CTAs per
-// SM of the persistent bf16x3 kernel, and the split-K target (multiples of the CTAs or SMs).
+// SM of the persistent bf16 kernels (tcb: two terms, tcb6: three), and the split-K target
+// (multiples of the CTAs or SMs).
 // Candidate 0 of every list is the fixed heuristic (HPS_TUNE_OFF).
 enum TuneFamily { TF_TC = 0, TF_TCS = 1, TF_TCB = 2, TF_TCB6 = 3 };
 const char* const kFamilyName[4] = {"tc", "tcs", "tcb", "tcb6"};
